@@ -1,0 +1,209 @@
+"""Pins of the oracle's dictionary decode (Eq. dict_recon), feature objective
+(Eq. feat_loss with lambda_f of Eq. full_obj), exact gradients and Adam step, against
+special cases, library routines (scipy softmax, torch.optim.Adam), closed forms, the
+paper's printed numbers and central finite differences."""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy.special import softmax
+
+import oracle
+from workloads import random_scene
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand(seed, n=30, d=6, M=9, D=20):
+    rng = np.random.default_rng(seed)
+    Q = rng.normal(size=(n, d))
+    K = rng.normal(size=(M, d)) / np.sqrt(d)
+    V = rng.normal(size=(M, D)) / np.sqrt(d)
+    F = rng.normal(size=(n, D))
+    F /= np.linalg.norm(F, axis=1, keepdims=True)
+    return rng, Q, K, V, F
+
+
+def test_softmax_matches_scipy_and_rows_sum_to_one():
+    _, Q, K, V, _ = _rand(0)
+    c = 0.7
+    S, A, Fh = oracle.decode(Q, K, V, c)
+    np.testing.assert_allclose(S, c * Q @ K.T, rtol=1e-13)
+    np.testing.assert_allclose(A, softmax(c * Q @ K.T, axis=1), rtol=1e-12)
+    np.testing.assert_allclose(A.sum(1), 1.0, atol=1e-15)
+    np.testing.assert_allclose(Fh, A @ V, rtol=1e-12, atol=1e-15)
+
+
+def test_decode_special_cases():
+    _, Q, K, V, _ = _rand(1)
+    # M = 1: every pixel decodes to the single atom
+    _, A, Fh = oracle.decode(Q, K[:1], V[:1], 1.0)
+    np.testing.assert_allclose(Fh, np.repeat(V[:1], Q.shape[0], 0), rtol=1e-14)
+    # equal keys, and zero queries: the mean atom
+    Keq = np.repeat(K[:1], K.shape[0], 0)
+    _, _, Fh = oracle.decode(Q, Keq, V, 1.0)
+    np.testing.assert_allclose(Fh, np.repeat(V.mean(0, keepdims=True), Q.shape[0], 0), rtol=1e-12, atol=1e-15)
+    _, _, Fh = oracle.decode(np.zeros_like(Q), K, V, 1.0)
+    np.testing.assert_allclose(Fh, np.repeat(V.mean(0, keepdims=True), Q.shape[0], 0), rtol=1e-12, atol=1e-15)
+    # a scaled one-hot logit selects that atom
+    d = Q.shape[1]
+    Kid = np.zeros((d, d))
+    Kid[np.arange(d), np.arange(d)] = 1.0
+    Vd = V[:d]
+    q = np.zeros((d, d))
+    q[np.arange(d), np.arange(d)] = 1.0
+    _, _, Fh = oracle.decode(q, Kid, Vd, 200.0)
+    np.testing.assert_allclose(Fh, Vd, atol=1e-12)
+
+
+def test_loss_special_cases_and_trust_region_closed_form():
+    _, Q, K, V, F = _rand(2)
+    cfg = oracle.LossConfig()
+    mask = np.ones(F.shape[0], np.uint8)
+    parts, cos_p = oracle.loss(F, F, mask, V, V, cfg, Q.shape[1])
+    assert abs(parts["cos"]) < 1e-15 and parts["l2"] == 0.0 and parts["tr"] == 0.0 and abs(parts["total"]) < 1e-14
+    np.testing.assert_allclose(cos_p, 1.0, atol=1e-15)
+    # inside the trust radius: no penalty
+    rng = np.random.default_rng(0)
+    dirs = rng.normal(size=V.shape)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    parts, _ = oracle.loss(F, F, mask, V + 0.09 * dirs, V, cfg, Q.shape[1])
+    assert parts["tr"] == 0.0
+    # one atom displaced by t > delta along an axis: lambda_f lambda_D (t - delta)
+    t = 0.37
+    V1 = V.copy()
+    V1[3, 5] += t
+    parts, _ = oracle.loss(F, F, mask, V1, V, cfg, Q.shape[1])
+    np.testing.assert_allclose(parts["tr"], t - cfg.delta, rtol=1e-12)
+    np.testing.assert_allclose(parts["total"], cfg.lambda_f * cfg.lambda_D * (t - cfg.delta), rtol=1e-12)
+    # its gradient has length lambda_f lambda_D along that axis
+    S, A, Fh = oracle.decode(Q, K, V1, 1.0)
+    _, _, dV_tr = oracle.backward(Q, K, V1, V, A, Fh, F, np.zeros_like(mask), cfg)
+    exp = np.zeros_like(V)
+    exp[3, 5] = cfg.lambda_f * cfg.lambda_D
+    np.testing.assert_allclose(dV_tr, exp, atol=1e-15)
+
+
+def test_paper_hyperparameters_are_the_defaults():
+    g = json.load(open(os.path.join(GOLDEN, "paper_hyperparameters.json")))
+    cfg = oracle.LossConfig()
+    for k in ("lambda_f", "lambda_cos", "lambda_2", "lambda_D", "delta"):
+        assert getattr(cfg, k) == g[k], k
+    # the room workload's trust-region weight of 1.0 is lambda_f * lambda_D
+    assert cfg.lambda_f * cfg.lambda_D == pytest.approx(1.0)
+
+
+def test_l2_normalisation_reading_matches_paper_table_and_oracle():
+    """For unit vectors |a-b|^2 = 2(1 - cos).  Table II's LSeg columns satisfy
+    L_2 ~= 2 L_cos / D only if the L2 term is averaged over the D elements; the oracle's
+    loss must obey the identity exactly for unit-norm inputs."""
+    g = json.load(open(os.path.join(GOLDEN, "table2_lseg.json")))
+    for r in g["rows"]:
+        assert r["L_2"] == pytest.approx(2 * r["L_cos"] / g["D"], rel=0.12), r
+        assert not (r["L_2"] == pytest.approx(2 * r["L_cos"], rel=0.5))
+    rng = np.random.default_rng(4)
+    D = 64
+    a = rng.normal(size=(50, D))
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    b = rng.normal(size=(50, D))
+    b /= np.linalg.norm(b, axis=1, keepdims=True)
+    V = rng.normal(size=(3, D))
+    parts, _ = oracle.loss(a, b, np.ones(50, np.uint8), V, V, oracle.LossConfig(), 4)
+    np.testing.assert_allclose(parts["l2"], 2 * parts["cos"] / D, rtol=1e-12)
+
+
+def _total_loss(Q, K, V, V0, F, mask, cfg):
+    _, _, Fh = oracle.decode(Q, K, V, cfg.c(Q.shape[1]))
+    return oracle.loss(Fh, F, mask, V, V0, cfg, Q.shape[1])[0]["total"]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_decode_gradients_match_central_differences(seed):
+    rng, Q, K, V, F = _rand(10 + seed, n=24, d=5, M=7, D=11)
+    mask = (rng.uniform(size=Q.shape[0]) > 0.3).astype(np.uint8)
+    # trust-region centres: some atoms well inside, some well outside the radius
+    disp = rng.normal(size=V.shape)
+    disp /= np.linalg.norm(disp, axis=1, keepdims=True)
+    radii = np.where(np.arange(V.shape[0]) % 2 == 0, 0.03, 0.4)
+    V0 = V - radii[:, None] * disp
+    cfg = oracle.LossConfig()
+    _, A, Fh = oracle.decode(Q, K, V, cfg.c(Q.shape[1]))
+    dQ, dK, dV = oracle.backward(Q, K, V, V0, A, Fh, F, mask, cfg)
+    for name, X, G in (("Q", Q, dQ), ("K", K, dK), ("V", V, dV)):
+        num = np.zeros_like(X)
+        for idx in np.ndindex(*X.shape):
+            h = 1e-6 * max(1.0, abs(X[idx]))
+            Xp, Xm = X.copy(), X.copy()
+            Xp[idx] += h
+            Xm[idx] -= h
+            args = dict(Q=Q, K=K, V=V)
+            args[name] = Xp
+            lp = _total_loss(args["Q"], args["K"], args["V"], V0, F, mask, cfg)
+            args[name] = Xm
+            lm = _total_loss(args["Q"], args["K"], args["V"], V0, F, mask, cfg)
+            num[idx] = (lp - lm) / (2 * h)
+        np.testing.assert_allclose(G, num, rtol=2e-6, atol=2e-9, err_msg=name)
+    # pixels outside the loss set get no query gradient
+    assert np.all(dQ[mask == 0] == 0.0)
+
+
+def test_empty_loss_set():
+    _, Q, K, V, F = _rand(5)
+    mask = np.zeros(Q.shape[0], np.uint8)
+    cfg = oracle.LossConfig()
+    _, A, Fh = oracle.decode(Q, K, V, cfg.c(Q.shape[1]))
+    parts, _ = oracle.loss(Fh, F, mask, V, V, cfg, Q.shape[1])
+    assert parts["total"] == 0.0 and parts["n_valid"] == 0
+    dQ, dK, dV = oracle.backward(Q, K, V, V, A, Fh, F, mask, cfg)
+    assert not dQ.any() and not dK.any() and not dV.any()
+
+
+def test_full_chain_query_gradient_matches_central_differences():
+    """d loss / d f through render -> decode -> loss; the blend weights do not depend on f."""
+    s = random_scene(7, n=40, d=4, M=6, D=10, width=20, height=16, log_scale=-2.2, mask_drop=0.2)
+    cfg = oracle.LossConfig()
+    proj = oracle.project_scene(s)
+    out = oracle.iteration(s, cfg, proj=proj)
+    df = out["df"]
+    touched = np.nonzero(np.abs(df).sum(1) > 0)[0][:8]
+    assert len(touched) >= 4
+
+    def total(f):
+        Q = oracle.render_frame(proj, f, s.camera)[0]
+        return _total_loss(Q, s.K, s.V, s.V0, s.F, s.mask, cfg)
+
+    f0 = s.f.astype(np.float64)
+    for g in touched:
+        for k in range(s.d):
+            h = 1e-6
+            fp, fm = f0.copy(), f0.copy()
+            fp[g, k] += h
+            fm[g, k] -= h
+            num = (total(fp) - total(fm)) / (2 * h)
+            assert num == pytest.approx(df[g, k], rel=1e-5, abs=1e-9)
+
+
+def test_adam_first_step_is_sign_and_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    p = rng.normal(size=50)
+    g = rng.normal(size=50)
+    m, v = np.zeros(50), np.zeros(50)
+    p1 = p.copy()
+    oracle.adam(p1, g, m, v, 1, 0.01)
+    # bias correction makes the first step -lr g / (|g| + eps), i.e. -lr sign(g) for |g| >> eps
+    np.testing.assert_allclose(p1 - p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    big = np.abs(g) > 1e-2
+    np.testing.assert_allclose((p1 - p)[big], -0.01 * np.sign(g[big]), rtol=1e-6)
+    # three steps against torch.optim.Adam (float64, CPU)
+    p2 = p.copy()
+    m, v = np.zeros(50), np.zeros(50)
+    tp = torch.tensor(p.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=0.01, betas=(0.9, 0.999), eps=1e-8)
+    for step in range(1, 4):
+        gs = rng.normal(size=50)
+        oracle.adam(p2, gs, m, v, step, 0.01)
+        tp.grad = torch.tensor(gs, dtype=torch.float64)
+        opt.step()
+    np.testing.assert_allclose(p2, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
