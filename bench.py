@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Throughput of the per-keyframe latent-feature optimisation step (LatentAM, arxiv 2602.12314).
+
+One step = one fwd+bwd+Adam iteration of the whole hot path on one keyframe through the
+C ABI (latentam_step, iters = 1, queries learnable = Stage I with R1 = 1): projection,
+binning + depth sort, query splatting, dictionary decode, feature loss with the trust
+region, decode backward, splat backward, Adam on (f, K, V).
+
+Workload (the single-keyframe room configuration): 300k Gaussians on the surfaces of a
+6x5x3 m room with 20 boxes, 640x480 pinhole view, d = 32, M = 256, D = 512, FP32 end to
+end; seeded synthetic data standing in for the paper's RGB-D + CLIP/SAM keyframes.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision fp32|bf16] [--impl reference]
+
+Under torchrun (N > 1) every rank optimises its own keyframe (replicas, weak scaling); the
+timed region is bracketed by a barrier and a device synchronisation and the slowest rank's
+time is used.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd latent optim iters/sec at 640x480,D=512 (FP32 vs BF16 batched); % roofline"
+WORKLOAD = ("room keyframe: 300k Gaussians (6x5x3 m room, 20 boxes), 640x480, d=32, M=256, D=512; "
+            "one fwd+bwd+Adam iteration incl. projection and depth/tile sort (Stage I, R1=1)")
+SM_FP32_LANES = 128  # FP32 FMA lanes per SM
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"latentam_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "1"):
+                        reasons.add(name)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        hi = max(mx)
+        loaded = [s for s in sm if s > 0.5 * hi] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": hi, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _scene(seed):
+    from workloads import room_scene
+    return room_scene(seed)
+
+
+def _oracle_iteration(scene, cfg):
+    """One oracle iteration: forward, backward and the Adam update of f, K, V."""
+    import numpy as np
+
+    import oracle
+    out = oracle.iteration(scene, cfg)
+    for name, x, g in (("f", scene.f, out["df"]), ("K", scene.K, out["dK"]), ("V", scene.V, out["dV"])):
+        p = x.astype(np.float64).copy()
+        m, v = np.zeros_like(p), np.zeros_like(p)
+        oracle.adam(p.reshape(-1), g.reshape(-1), m.reshape(-1), v.reshape(-1), 1, 0.01)
+    return out
+
+
+def run_reference(args, world, rank):
+    """The oracle (plain FP64 C, OpenMP) as it stands, timed on this machine's host cores on a
+    bounded sample of the workload: the 160x120 central crop of the keyframe (all 300k
+    Gaussians), iterations/s extrapolated to the full 640x480 frame by pixel count."""
+    if rank != 0:
+        return
+    import oracle
+    s = _scene(args.seed)
+    full = s.camera.n_pixels
+    crop = s.crop(240, 180, 160, 120)
+    frac = crop.camera.n_pixels / full
+    cfg = oracle.LossConfig()
+    oracle.build()
+    for _ in range(max(args.warmup, 0)):
+        _oracle_iteration(crop, cfg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_iteration(crop, cfg)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt * frac
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"{args.steps} oracle iterations on the 160x120 central crop (all 300k Gaussians); "
+              f"iters/s scaled by the pixel fraction {frac:.4f} to the 640x480 frame")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " [FP64 CPU oracle]"},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def decode_flops(n, M, D, d):
+    """Algorithmic FLOPs of decode + loss + decode backward (direct form, attention kept):
+    S (2nMd) + Fhat (2nMD) + dA (2nMD) + dQ (2nMd) + dV (2nMD) + dK (2nMd)."""
+    return 6.0 * n * M * D + 6.0 * n * M * d
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2602_12314_gb300 import _lib as L
+    from paper_2602_12314_gb300 import api
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = api.FP32 if args.precision == "fp32" else api.BF16
+    scene = _scene(args.seed + rank)
+    ctx = api.Context(local)
+    target_dtype = torch.float32 if prec == api.FP32 else torch.bfloat16
+    st = api.LatentStep(ctx, scene, precision=prec, target_dtype=target_dtype)
+    for _ in range(max(args.warmup, 3)):
+        st.step(1, learn_f=True, want_loss=False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident timed region --------------------------------------------------
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = L.load().latentam_launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        st.step(1, learn_f=True, want_loss=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = L.load().latentam_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+
+    # ---- end to end through the public API, host buffers ----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.as_tensor(np.ascontiguousarray(getattr(scene, k)), dtype=torch.float32).pin_memory()
+                for k in ("means", "quats", "scales", "opacities")}
+        host["F"] = torch.as_tensor(scene.F, dtype=torch.float32).to(target_dtype).pin_memory()
+        host["mask"] = torch.as_tensor(scene.mask, dtype=torch.uint8).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = 8 * L.LOSS_PARTS
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            for k, t in host.items():
+                getattr(st, k).copy_(t, non_blocking=True)
+            st.step(1, learn_f=True, want_loss=True)  # reads the loss back (synchronises)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * args.steps / (ems / 1e3), "unit": "iters/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant stage (decode + loss + decode backward) -------------------
+    peaks, peak_src = _peaks()
+    n, M, D, d = scene.camera.n_pixels, scene.M, scene.D, scene.d
+    dec_ms, dec_cnt = prof["decode"]
+    dec_avg_s = dec_ms / max(dec_cnt, 1) / 1e3
+    flops = decode_flops(n, M, D, d)
+    props = torch.cuda.get_device_properties(local)
+    if prec == api.FP32:
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = props.multi_processor_count * SM_FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "decode stage (dec_rows_fwd + dec_rows_bwd + atb_splitk)",
+                "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x {SM_FP32_LANES} lanes x 2 x "
+                               f"{sm_mhz:.0f} MHz (max SM clock)",
+                "traffic": None, "algorithmic_per_launch": flops}
+    else:
+        peak = float(peaks["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 kernels)", "achieved": flops / dec_avg_s / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "peak_source": f"bf16 sustained, {peak_src}", "traffic": None,
+                "algorithmic_per_launch": flops}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        crop = scene.crop(240, 180, 160, 120)
+        frac = crop.camera.n_pixels / n
+        t0 = time.perf_counter()
+        _oracle_iteration(crop, oracle.LossConfig())
+        dt = time.perf_counter() - t0
+        cpu = {"value": frac / dt, "unit": "iters/s", "cores": int(os.environ.get("OMP_NUM_THREADS",
+                                                                                   os.cpu_count() or 1)),
+               "kind": "oracle",
+               "sample": "one FP64 oracle iteration (fwd, bwd, Adam) on the 160x120 central crop with all 300k "
+                         f"Gaussians, {dt:.2f} s; scaled by the pixel fraction {frac:.4f} to the full frame"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == api.FP32 else "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": world,
+                   "n_pixels": n, "gaussians": scene.n, "d": d, "M": M, "D": D,
+                   "l2": "inputs larger than L2 (target features %.0f MB per step)" % (scene.F.nbytes / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,287 @@
+/*
+ * latentam.h — C ABI of the GB300 (sm_103a) implementation of LatentAM's per-keyframe
+ * latent-feature optimisation step (arxiv 2602.12314, Sec. III-B and III-C, Algorithm 1
+ * Stage I/II):
+ *
+ *   query splatting   Q = R_f(G, T)                 Eq. (alpha_blending), Eq. (render_query)
+ *   dictionary decode Fhat = softmax(c Q K^T) V     Eq. (dict_recon)
+ *   feature objective lambda_f L_f                  Eq. (feat_loss), Eq. (full_obj)
+ *   backward to the queries f and the dictionary (K, V), then an Adam update.
+ *
+ * Conventions shared by every call
+ *  - Every tensor argument is a DEVICE pointer owned by the caller, row-major and
+ *    contiguous, 16-byte aligned (float4 access); the library never frees it.  Pointer
+ *    members of the structs below follow the same rule.  Host pointers are marked "host".
+ *  - The library owns only the context: a growable device workspace (sort buffers,
+ *    decode intermediates, loss accumulators).  A context belongs to one device and must
+ *    not be used by two host threads at once.
+ *  - All work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream)
+ *    and returns without waiting, except where a call says it synchronises.
+ *  - Gradients are OVERWRITTEN, never accumulated; callers zero nothing.
+ *  - Shapes outside the supported set return LATENTAM_ERR_UNSUPPORTED_SHAPE; there is no
+ *    slow or CPU fallback.  On any error nothing is guaranteed about the outputs.
+ *    latentam_last_error() returns a message for the calling host thread.
+ *  - Supported: query dimension d in {16, 32, 64}; dictionary size M a multiple of 32 in
+ *    [32, 1024]; value dimension D a multiple of 128 in [128, 2048]; image sides
+ *    1..16384; N < 2^31 Gaussians; pair count < 2^31.
+ *
+ * Readings of the paper where it is silent (shared with the test oracle, stated here
+ * because they define the results):
+ *  - footprint (the 3DGS renderer Sec. III-A cites): EWA projection with a 0.3 px^2
+ *    dilation, alpha = min(0.99, o exp(-d^T Sigma'^-1 d / 2)), contributions with
+ *    alpha < 1/255 skipped, blending stops before a contribution that would take the
+ *    transmittance below 1e-4; pixel centres at integer coordinates; 16x16 tiles; a
+ *    Gaussian's tile rectangle is the axis-aligned box of its alpha >= 1/255 ellipse.
+ *  - front-to-back order: the camera depth of the mean, evaluated in double precision as
+ *    ((R20 x + R21 y) + R22 z) + t2 and rounded to binary32, ascending; ties by index.
+ *  - Gaussians with depth <= z_near or opacity < 1/255 are culled; an uncovered pixel
+ *    renders Q_p = 0.
+ *  - decode with free keys K (M x d) and values V (M x D), logit scale c (1/sqrt(d) by
+ *    default); the paper's W/D/tau form is the special case K = W D^T / |D|, V = D.
+ *  - loss: lambda_f [lambda_cos mean_valid(1 - cos_p) + lambda_2 mean_{valid x D}(Fhat - F)^2
+ *    + lambda_D sum_j ReLU(|V_j - V0_j| - delta)], cos_p = <Fhat_p, F_p> /
+ *    max(|Fhat_p| |F_p|, 1e-8); the trust region acts on the value rows only.
+ */
+#ifndef LATENTAM_H
+#define LATENTAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LATENTAM_API __attribute__((visibility("default")))
+#else
+#define LATENTAM_API
+#endif
+
+#define LATENTAM_TILE 16
+#define LATENTAM_ABI_VERSION 1
+
+typedef int32_t latentam_status;
+#define LATENTAM_OK 0
+#define LATENTAM_ERR_INVALID_ARG (-1)       /* null/misaligned pointer, bad count or config */
+#define LATENTAM_ERR_UNSUPPORTED_SHAPE (-2) /* d, M, D or image size outside the supported set */
+#define LATENTAM_ERR_OUT_OF_MEMORY (-3)     /* workspace allocation failed */
+#define LATENTAM_ERR_CUDA (-4)              /* a CUDA runtime call or launch failed */
+#define LATENTAM_ERR_CAPACITY (-5)          /* caller buffer too small; required size reported */
+#define LATENTAM_ERR_TIMEOUT (-6)           /* a bounded device-side wait gave up */
+
+typedef int32_t latentam_precision;
+#define LATENTAM_PREC_FP32 0 /* decode on FP32 CUDA cores, FP32 throughout */
+#define LATENTAM_PREC_BF16 1 /* decode contractions on tcgen05 tensor cores: BF16 operands, FP32 accumulation */
+
+typedef int32_t latentam_dtype;
+#define LATENTAM_DTYPE_F32 0
+#define LATENTAM_DTYPE_BF16 1
+
+typedef struct CUstream_st* latentam_stream; /* cudaStream_t */
+typedef struct latentam_ctx latentam_ctx;
+
+/* Pinhole camera (host struct).  p_cam = R p_world + t with R row-major; camera x right,
+ * y down, z forward; pixel (x, y) = x + y * width. */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float z_near;
+    int32_t width, height;
+} latentam_camera;
+
+/* Gaussian primitives G_i = {p_i, q_i, s_i, alpha_i} of Eq. (gs_repr_basic) (colour unused). */
+typedef struct {
+    int32_t n;               /* N */
+    const float* means;      /* N x 3 world positions p_i */
+    const float* quats;      /* N x 4 orientations q_i = (w, x, y, z); normalised internally */
+    const float* scales;     /* N x 3 linear scales s_i */
+    const float* opacities;  /* N opacities alpha_i in [0, 1] */
+} latentam_gaussians;
+
+/* Per-Gaussian projection, written by latentam_project (caller-owned, N entries each). */
+typedef struct {
+    float* xy;              /* N x 2 pixel-space mean */
+    float* conic_opacity;   /* N x 4: (Sigma'^-1)_00, (Sigma'^-1)_01, (Sigma'^-1)_11, opacity */
+    float* depth;           /* N camera depth (binary32 sort key, see readings) */
+    int32_t* rect;          /* N x 4 tile rectangle x0, y0, x1, y1 (half-open; all 0 if culled/off-screen) */
+    int32_t* tiles_touched; /* N number of tiles in rect */
+} latentam_projected;
+
+/* (tile, Gaussian) pairs grouped by tile, each group front to back. */
+typedef struct {
+    int32_t* pair_ids;      /* capacity entries: Gaussian index of each pair */
+    int64_t capacity;       /* length of pair_ids */
+    int32_t* tile_ranges;   /* num_tiles x 2: [start, end) of each tile's pairs */
+    int64_t num_pairs;      /* out: number of pairs P (also on CAPACITY errors) */
+} latentam_bins;
+
+/* Weights of Eq. (feat_loss) and lambda_f of Eq. (full_obj); Sec. IV-A values:
+ * lambda_f 5, lambda_cos 0.5, lambda_2 0.5, lambda_D 0.2, delta 0.1. */
+typedef struct {
+    float lambda_f, lambda_cos, lambda_2, lambda_D, delta;
+    float logit_scale; /* c of the decode; <= 0 selects 1/sqrt(d) */
+} latentam_loss_cfg;
+
+/* Adam: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr mhat / (sqrt(vhat) + eps),
+ * with bias corrections 1 - b^step.  Sec. IV-A gives lr = 0.01 for the dictionary. */
+typedef struct {
+    float lr_f, lr_dict, beta1, beta2, eps;
+    int32_t step; /* step number of the NEXT update (1 for the first) */
+} latentam_adam_cfg;
+
+/* loss_parts layout (device doubles, written by the loss calls):
+ * [0] mean over valid pixels of (1 - cos_p)   [1] mean over valid pixels x D of (Fhat - F)^2
+ * [2] sum_j ReLU(|V_j - V0_j| - delta)         [3] total lambda_f L_f
+ * [4] number of valid pixels |Omega| */
+#define LATENTAM_LOSS_PARTS 5
+
+/* ---- context ---------------------------------------------------------------------- */
+
+/* Create a context bound to CUDA device `device` (made current on each call).  Returns
+ * INVALID_ARG if out is NULL, CUDA if the device is absent or not sm_103. */
+LATENTAM_API latentam_status latentam_ctx_create(int32_t device, latentam_ctx** out);
+/* Synchronise the device and free the workspace.  NULL is accepted. */
+LATENTAM_API latentam_status latentam_ctx_destroy(latentam_ctx* ctx);
+/* Message describing the last error on the calling host thread ("" if none). */
+LATENTAM_API const char* latentam_last_error(void);
+/* ABI version (LATENTAM_ABI_VERSION). */
+LATENTAM_API int32_t latentam_version(void);
+/* Number of kernels this library has launched in this process (all contexts). */
+LATENTAM_API int64_t latentam_launch_count(void);
+/* Number of 16x16 tiles of the camera's image, ceil(W/16) * ceil(H/16). */
+LATENTAM_API int32_t latentam_num_tiles(const latentam_camera* cam);
+
+/* ---- stage timers -------------------------------------------------------------------- */
+
+/* CUDA-event timers around each stage of the step, on the stream it runs on.  While
+ * enabled every call records an event pair per stage (no effect on results; do not enable
+ * during stream capture).  latentam_profile_read synchronises the device, writes the
+ * accumulated milliseconds and launch-group counts of the LATENTAM_NUM_STAGES stages into
+ * ms / counts (host arrays, nullable) and clears them when reset != 0. */
+#define LATENTAM_STAGE_PROJECT 0
+#define LATENTAM_STAGE_SORT 1
+#define LATENTAM_STAGE_RENDER_FWD 2
+#define LATENTAM_STAGE_DECODE 3     /* decode + loss + decode backward (all its kernels) */
+#define LATENTAM_STAGE_RENDER_BWD 4
+#define LATENTAM_STAGE_ADAM 5
+#define LATENTAM_NUM_STAGES 6
+LATENTAM_API latentam_status latentam_profile_enable(latentam_ctx* ctx, int32_t enable);
+LATENTAM_API latentam_status latentam_profile_read(latentam_ctx* ctx, double* ms, int64_t* counts, int32_t reset);
+
+/* ---- splatting (Sec. III-A, Eq. alpha_blending; Sec. III-B, Eq. render_query) ------- */
+
+/* Project every Gaussian: EWA screen-space covariance, conic, opacity, depth key and
+ * the tile rectangle of its alpha >= 1/255 footprint.  One thread per Gaussian. */
+LATENTAM_API latentam_status latentam_project(latentam_ctx* ctx, const latentam_gaussians* g,
+                                 const latentam_camera* cam, const latentam_projected* out,
+                                 latentam_stream stream);
+
+/* Bin and sort: order visible Gaussians by depth key (stable radix sort, so ties keep
+ * index order), emit one pair per covered tile, stable radix sort of the pairs by tile,
+ * then per-tile ranges.  SYNCHRONISES `stream` once to read the pair count P into
+ * bins->num_pairs; if P > bins->capacity returns LATENTAM_ERR_CAPACITY and writes no
+ * pairs (retry with a larger buffer). */
+LATENTAM_API latentam_status latentam_sort(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
+                              const latentam_camera* cam, latentam_bins* bins,
+                              latentam_stream stream);
+
+/* Front-to-back blend of the d-dimensional queries f (N x d) of each tile's Gaussians:
+ * Q (H*W x d), final transmittance T_final (H*W) and number of contributions n_contrib
+ * (H*W).  One 16x16-pixel CTA per tile, Gaussians staged through shared memory. */
+LATENTAM_API latentam_status latentam_render_fwd(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
+                                    const latentam_camera* cam, const latentam_bins* bins,
+                                    const float* f, int32_t d, float* Q, float* T_final,
+                                    int32_t* n_contrib, latentam_stream stream);
+
+/* Gradient of the blend with respect to the queries: df_i = sum_p w_ip dQ_p with the
+ * blend weights w_ip = alpha_ip T_ip recomputed front to back (no division), reduced
+ * over each warp before one atomic add per warp and channel.  n_contrib is the output
+ * of latentam_render_fwd for the same inputs.  df is N x d (overwritten). */
+LATENTAM_API latentam_status latentam_render_bwd(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
+                                    const latentam_camera* cam, const latentam_bins* bins,
+                                    const int32_t* n_contrib, const float* dQ, int32_t d,
+                                    float* df, latentam_stream stream);
+
+/* ---- dictionary decode (Sec. III-B, Eq. dict_recon) --------------------------------- */
+
+/* Fhat = softmax_rows(c Q K^T) V for Q (n x d), K (M x d), V (M x D).  F_hat (n x D) and
+ * row_stats (n x 2: row maximum of the logits, softmax denominator) may each be NULL. */
+LATENTAM_API latentam_status latentam_decode_fwd(latentam_ctx* ctx, const float* Q, int64_t n, int32_t d,
+                                    const float* K, const float* V, int32_t M, int32_t D,
+                                    float logit_scale, latentam_precision prec, float* F_hat,
+                                    float* row_stats, latentam_stream stream);
+
+/* Feature objective and its gradients in one pass: decode, lambda_f L_f against the
+ * target F (n x D, dtype F_dtype) on the pixels with mask != 0 (NULL mask = all), then
+ * dQ (n x d), dK (M x d), dV (M x D, including the trust-region subgradient against V0).
+ * loss_parts: device doubles (LATENTAM_LOSS_PARTS).  Any of dQ/dK/dV may be NULL. */
+LATENTAM_API latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const float* Q, int64_t n, int32_t d,
+                                         const float* K, const float* V, const float* V0,
+                                         int32_t M, int32_t D, const void* F,
+                                         latentam_dtype F_dtype, const uint8_t* mask,
+                                         const latentam_loss_cfg* cfg, latentam_precision prec,
+                                         double* loss_parts, float* dQ, float* dK, float* dV,
+                                         latentam_stream stream);
+
+/* The whole backward of one keyframe: latentam_decode_loss_bwd on the rendered Q, then
+ * latentam_render_bwd into df (skipped when df is NULL, as in Stage II where the
+ * Gaussians are fixed).  dQ_scratch (H*W x d) receives the query-image gradient. */
+LATENTAM_API latentam_status latentam_backward(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
+                                  const latentam_camera* cam, const latentam_bins* bins,
+                                  const int32_t* n_contrib, const float* Q, int32_t d,
+                                  const float* K, const float* V, const float* V0, int32_t M,
+                                  int32_t D, const void* F, latentam_dtype F_dtype,
+                                  const uint8_t* mask, const latentam_loss_cfg* cfg,
+                                  latentam_precision prec, double* loss_parts, float* dQ_scratch,
+                                  float* df, float* dK, float* dV, latentam_stream stream);
+
+/* ---- optimiser ----------------------------------------------------------------------- */
+
+/* One Adam update of `count` tensors in a single launch: params[i], grads[i], m[i], v[i]
+ * are device arrays of sizes[i] floats (host arrays of pointers); lrs[i] (host) is the
+ * learning rate of tensor i.  Step number and betas from cfg. */
+LATENTAM_API latentam_status latentam_adam(latentam_ctx* ctx, int32_t count, float* const* params,
+                              const float* const* grads, float* const* m, float* const* v,
+                              const int64_t* sizes, const float* lrs,
+                              const latentam_adam_cfg* cfg, latentam_stream stream);
+
+/* ---- the step (Algorithm 1, optimisation stages) ------------------------------------- */
+
+/* One keyframe's state for latentam_step. */
+typedef struct {
+    latentam_gaussians gaussians;
+    latentam_camera camera;
+    const void* F;          /* H*W x D target features */
+    latentam_dtype F_dtype;
+    const uint8_t* mask;    /* H*W loss-set mask, NULL = all pixels */
+} latentam_frame;
+
+/* Learnable state: queries f (N x d) and dictionary K (M x d), V (M x D), the trust-region
+ * centre V0 (M x D), and the Adam moments of each (same shapes). */
+typedef struct {
+    float* f;
+    float* K;
+    float* V;
+    const float* V0;
+    float *m_f, *v_f, *m_K, *v_K, *m_V, *v_V;
+    int32_t d, M, D;
+} latentam_params;
+
+/* `iters` iterations of: render (Q from f) -> decode + loss -> backward -> Adam on
+ * (f if learn_f, K, V).  Projection and binning run once (the geometry is fixed during
+ * the step).  With learn_f == 0 (Stage II) Q is rendered once and f is left untouched.
+ * adam->step is the step number of the first update; it is incremented per iteration in
+ * the caller's struct.  loss_host (host, nullable, LATENTAM_LOSS_PARTS doubles) receives
+ * the loss of the LAST iteration (evaluated before its update); passing it synchronises
+ * the stream at the end.  Also synchronises once for the pair count (latentam_sort). */
+LATENTAM_API latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame,
+                              latentam_params* params, const latentam_loss_cfg* cfg,
+                              latentam_adam_cfg* adam, int32_t iters, int32_t learn_f,
+                              latentam_precision prec, double* loss_host, latentam_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LATENTAM_H */

@@ -113,8 +113,10 @@ def camera_struct(cam) -> _Camera:
         c.R[k] = float(R[k])
     for k in range(3):
         c.t[k] = float(t[k])
-    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
-    c.z_near = float(cam.z_near)
+    # camera scalars enter every implementation as binary32 values
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    c.fx, c.fy, c.cx, c.cy = f32(cam.fx), f32(cam.fy), f32(cam.cx), f32(cam.cy)
+    c.z_near = f32(cam.z_near)
     c.width, c.height = int(cam.width), int(cam.height)
     return c
 

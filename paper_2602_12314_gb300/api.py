@@ -1,0 +1,375 @@
+"""Python binding of the C ABI in include/latentam.h (same names, torch tensors in and out).
+
+Argument marshalling only: tensors must live on the context's CUDA device; every step of
+the computation runs in liblatentam.so's kernels.  The calls are enqueued on the current
+torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+
+import torch
+
+from . import _lib as L
+
+FP32 = L.PREC_FP32
+BF16 = L.PREC_BF16
+
+
+def _lib():
+    return L.load()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(None)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_f32(t, device):
+    return torch.as_tensor(t, dtype=torch.float32, device=device).contiguous()
+
+
+def camera_struct(cam) -> L.Camera:
+    """From any object with R (3x3), t (3), fx, fy, cx, cy, width, height[, z_near]."""
+    c = L.Camera()
+    R = [float(x) for x in torch.as_tensor(cam.R, dtype=torch.float64).reshape(-1).tolist()]
+    t = [float(x) for x in torch.as_tensor(cam.t, dtype=torch.float64).reshape(-1).tolist()]
+    for k in range(9):
+        c.R[k] = R[k]
+    for k in range(3):
+        c.t[k] = t[k]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.z_near = float(getattr(cam, "z_near", 0.2))
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def num_tiles(camera) -> int:
+    c = camera if isinstance(camera, L.Camera) else camera_struct(camera)
+    return int(_lib().latentam_num_tiles(ctypes.byref(c)))
+
+
+@dataclasses.dataclass
+class LossConfig:
+    """Eq. (feat_loss) weights and lambda_f of Eq. (full_obj); defaults from Sec. IV-A.
+    logit_scale <= 0 selects 1/sqrt(d)."""
+    lambda_f: float = 5.0
+    lambda_cos: float = 0.5
+    lambda_2: float = 0.5
+    lambda_D: float = 0.2
+    delta: float = 0.1
+    logit_scale: float = 0.0
+
+    def struct(self) -> L.LossCfg:
+        s = L.LossCfg()
+        s.lambda_f, s.lambda_cos, s.lambda_2 = self.lambda_f, self.lambda_cos, self.lambda_2
+        s.lambda_D, s.delta, s.logit_scale = self.lambda_D, self.delta, self.logit_scale
+        return s
+
+
+@dataclasses.dataclass
+class AdamConfig:
+    lr_f: float = 0.01
+    lr_dict: float = 0.01
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    step: int = 1
+
+    def struct(self) -> L.AdamCfg:
+        s = L.AdamCfg()
+        s.lr_f, s.lr_dict, s.beta1, s.beta2, s.eps, s.step = (self.lr_f, self.lr_dict, self.beta1, self.beta2,
+                                                               self.eps, int(self.step))
+        return s
+
+
+class Context:
+    """A latentam_ctx bound to one CUDA device (its workspace lives there)."""
+
+    def __init__(self, device: int | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("latentam needs a CUDA device (GB300, sm_103a); there is no CPU fallback")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        lib = _lib()
+        h = ctypes.c_void_p()
+        L.check(lib.latentam_ctx_create(self.device, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("context destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            L.check(_lib().latentam_ctx_destroy(self._h))
+            self._h = None
+
+    def profile(self, enable: bool = True):
+        """Turn the per-stage CUDA-event timers on or off."""
+        L.check(_lib().latentam_profile_enable(self.handle, int(bool(enable))))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{stage: (total ms, launch groups)} accumulated since the last reset (synchronises)."""
+        ms = (ctypes.c_double * len(L.STAGES))()
+        cnt = (ctypes.c_int64 * len(L.STAGES))()
+        L.check(_lib().latentam_profile_read(self.handle, ms, cnt, int(bool(reset))))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(L.STAGES)}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclasses.dataclass
+class Projection:
+    xy: torch.Tensor             # (N, 2)
+    conic_opacity: torch.Tensor  # (N, 4)
+    depth: torch.Tensor          # (N,)
+    rect: torch.Tensor           # (N, 4) int32
+    tiles_touched: torch.Tensor  # (N,) int32
+
+    @property
+    def n(self) -> int:
+        return self.depth.shape[0]
+
+    def struct(self) -> L.Projected:
+        return L.Projected(self.xy.data_ptr(), self.conic_opacity.data_ptr(), self.depth.data_ptr(),
+                           self.rect.data_ptr(), self.tiles_touched.data_ptr())
+
+
+@dataclasses.dataclass
+class TileBins:
+    pair_ids: torch.Tensor     # (capacity,) int32, first num_pairs valid
+    tile_ranges: torch.Tensor  # (tiles, 2) int32
+    num_pairs: int
+
+    def struct(self) -> L.Bins:
+        b = L.Bins()
+        b.pair_ids = self.pair_ids.data_ptr()
+        b.capacity = self.pair_ids.numel()
+        b.tile_ranges = self.tile_ranges.data_ptr()
+        b.num_pairs = self.num_pairs
+        return b
+
+
+def _gaussians_struct(means, quats, scales, opacities) -> L.Gaussians:
+    g = L.Gaussians()
+    g.n = means.shape[0]
+    g.means, g.quats, g.scales, g.opacities = (means.data_ptr(), quats.data_ptr(), scales.data_ptr(),
+                                               opacities.data_ptr())
+    return g
+
+
+def project(ctx: Context, means, quats, scales, opacities, camera) -> Projection:
+    dev = torch.device("cuda", ctx.device)
+    means, quats, scales, opacities = (_dev_f32(x, dev) for x in (means, quats, scales, opacities))
+    N = means.shape[0]
+    proj = Projection(torch.empty((N, 2), dtype=torch.float32, device=dev),
+                      torch.empty((N, 4), dtype=torch.float32, device=dev),
+                      torch.empty((N,), dtype=torch.float32, device=dev),
+                      torch.empty((N, 4), dtype=torch.int32, device=dev),
+                      torch.empty((N,), dtype=torch.int32, device=dev))
+    g = _gaussians_struct(means, quats, scales, opacities)
+    cam = camera if isinstance(camera, L.Camera) else camera_struct(camera)
+    ps = proj.struct()
+    L.check(_lib().latentam_project(ctx.handle, ctypes.byref(g), ctypes.byref(cam), ctypes.byref(ps), _stream()))
+    return proj
+
+
+def sort(ctx: Context, proj: Projection, camera, capacity: int | None = None) -> TileBins:
+    """Bin and depth-sort; synchronises once to learn the pair count (retries when the
+    initial buffer is too small)."""
+    dev = torch.device("cuda", ctx.device)
+    cam = camera if isinstance(camera, L.Camera) else camera_struct(camera)
+    tiles = num_tiles(cam)
+    cap = capacity if capacity is not None else max(1024, 4 * proj.n)
+    ranges = torch.empty((tiles, 2), dtype=torch.int32, device=dev)
+    for _ in range(2):
+        bins = TileBins(torch.empty((max(cap, 1),), dtype=torch.int32, device=dev), ranges, 0)
+        bs = bins.struct()
+        ps = proj.struct()
+        st = _lib().latentam_sort(ctx.handle, proj.n, ctypes.byref(ps), ctypes.byref(cam), ctypes.byref(bs), _stream())
+        bins.num_pairs = int(bs.num_pairs)
+        if st == L.ERR_CAPACITY:
+            cap = bins.num_pairs
+            continue
+        L.check(st)
+        return bins
+    raise RuntimeError("pair capacity retry failed")
+
+
+def render_fwd(ctx: Context, proj: Projection, camera, bins: TileBins, f: torch.Tensor):
+    """Q (H*W, d), T_final (H*W,), n_contrib (H*W,) int32."""
+    cam = camera if isinstance(camera, L.Camera) else camera_struct(camera)
+    f = f.contiguous()
+    d = f.shape[1]
+    npix = cam.width * cam.height
+    Q = torch.empty((npix, d), dtype=torch.float32, device=f.device)
+    T = torch.empty((npix,), dtype=torch.float32, device=f.device)
+    nc = torch.empty((npix,), dtype=torch.int32, device=f.device)
+    ps, bs = proj.struct(), bins.struct()
+    L.check(_lib().latentam_render_fwd(ctx.handle, proj.n, ctypes.byref(ps), ctypes.byref(cam), ctypes.byref(bs),
+                                       _ptr(f), d, _ptr(Q), _ptr(T), _ptr(nc), _stream()))
+    return Q, T, nc
+
+
+def render_bwd(ctx: Context, proj: Projection, camera, bins: TileBins, n_contrib, dQ) -> torch.Tensor:
+    cam = camera if isinstance(camera, L.Camera) else camera_struct(camera)
+    dQ = dQ.contiguous().float()
+    d = dQ.shape[1]
+    df = torch.empty((proj.n, d), dtype=torch.float32, device=dQ.device)
+    ps, bs = proj.struct(), bins.struct()
+    L.check(_lib().latentam_render_bwd(ctx.handle, proj.n, ctypes.byref(ps), ctypes.byref(cam), ctypes.byref(bs),
+                                       _ptr(n_contrib), _ptr(dQ), d, _ptr(df), _stream()))
+    return df
+
+
+def decode_fwd(ctx: Context, Q, K, V, logit_scale: float = 0.0, precision: int = FP32, want_stats: bool = True):
+    """Fhat = softmax(c Q K^T) V and the per-row (max, sum) of the softmax."""
+    Q, K, V = Q.contiguous(), K.contiguous(), V.contiguous()
+    n, d = Q.shape
+    M, D = V.shape
+    Fh = torch.empty((n, D), dtype=torch.float32, device=Q.device)
+    stats = torch.empty((n, 2), dtype=torch.float32, device=Q.device) if want_stats else None
+    L.check(_lib().latentam_decode_fwd(ctx.handle, _ptr(Q), n, d, _ptr(K), _ptr(V), M, D, float(logit_scale),
+                                       int(precision), _ptr(Fh), _ptr(stats), _stream()))
+    return Fh, stats
+
+
+def _target_dtype(F):
+    if F.dtype == torch.float32:
+        return L.DTYPE_F32
+    if F.dtype == torch.bfloat16:
+        return L.DTYPE_BF16
+    raise TypeError("target features must be float32 or bfloat16")
+
+
+def decode_loss_bwd(ctx: Context, Q, K, V, V0, F, mask=None, cfg: LossConfig | None = None, precision: int = FP32,
+                    need_dQ: bool = True):
+    """(loss_parts (5,) float64 on device, dQ, dK, dV) of lambda_f L_f, Eq. (feat_loss)."""
+    cfg = cfg or LossConfig()
+    Q, K, V, V0, F = (x.contiguous() for x in (Q, K, V, V0, F))
+    n, d = Q.shape
+    M, D = V.shape
+    dev = Q.device
+    parts = torch.empty((L.LOSS_PARTS,), dtype=torch.float64, device=dev)
+    dQ = torch.empty((n, d), dtype=torch.float32, device=dev) if need_dQ else None
+    dK = torch.empty((M, d), dtype=torch.float32, device=dev)
+    dV = torch.empty((M, D), dtype=torch.float32, device=dev)
+    m = mask.contiguous().to(torch.uint8) if mask is not None else None
+    cs = cfg.struct()
+    L.check(_lib().latentam_decode_loss_bwd(ctx.handle, _ptr(Q), n, d, _ptr(K), _ptr(V), _ptr(V0), M, D, _ptr(F),
+                                            _target_dtype(F), _ptr(m), ctypes.byref(cs), int(precision), _ptr(parts),
+                                            _ptr(dQ), _ptr(dK), _ptr(dV), _stream()))
+    return parts, dQ, dK, dV
+
+
+def backward(ctx: Context, proj: Projection, camera, bins: TileBins, n_contrib, Q, K, V, V0, F, mask=None,
+             cfg: LossConfig | None = None, precision: int = FP32, need_df: bool = True):
+    """(loss_parts, df or None, dK, dV, dQ or None) of one keyframe."""
+    cfg = cfg or LossConfig()
+    cam = camera if isinstance(camera, L.Camera) else camera_struct(camera)
+    Q, K, V, V0, F = (x.contiguous() for x in (Q, K, V, V0, F))
+    npix, d = Q.shape
+    M, D = V.shape
+    dev = Q.device
+    parts = torch.empty((L.LOSS_PARTS,), dtype=torch.float64, device=dev)
+    dQ = torch.empty((npix, d), dtype=torch.float32, device=dev) if need_df else None
+    df = torch.empty((proj.n, d), dtype=torch.float32, device=dev) if need_df else None
+    dK = torch.empty((M, d), dtype=torch.float32, device=dev)
+    dV = torch.empty((M, D), dtype=torch.float32, device=dev)
+    m = mask.contiguous().to(torch.uint8) if mask is not None else None
+    cs = cfg.struct()
+    ps, bs = proj.struct(), bins.struct()
+    L.check(_lib().latentam_backward(ctx.handle, proj.n, ctypes.byref(ps), ctypes.byref(cam), ctypes.byref(bs),
+                                     _ptr(n_contrib), _ptr(Q), d, _ptr(K), _ptr(V), _ptr(V0), M, D, _ptr(F),
+                                     _target_dtype(F), _ptr(m), ctypes.byref(cs), int(precision), _ptr(parts),
+                                     _ptr(dQ), _ptr(df), _ptr(dK), _ptr(dV), _stream()))
+    return parts, df, dK, dV, dQ
+
+
+def adam(ctx: Context, params, grads, ms, vs, lrs, cfg: AdamConfig):
+    """In-place Adam on up to 8 float32 tensors in one launch (cfg.step is NOT advanced)."""
+    k = len(params)
+    arr = lambda ts: (ctypes.c_void_p * k)(*[t.data_ptr() for t in ts])  # noqa: E731
+    sizes = (ctypes.c_int64 * k)(*[t.numel() for t in params])
+    lr = (ctypes.c_float * k)(*[float(x) for x in lrs])
+    cs = cfg.struct()
+    L.check(_lib().latentam_adam(ctx.handle, k, arr(params), arr(grads), arr(ms), arr(vs), sizes, lr,
+                                 ctypes.byref(cs), _stream()))
+
+
+class LatentStep:
+    """Device-resident state of one keyframe's latent-feature optimisation (Algorithm 1,
+    Stage I with learn_f = True / Stage II with learn_f = False) driven through
+    latentam_step."""
+
+    def __init__(self, ctx: Context, scene, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
+                 precision: int = FP32, target_dtype=torch.float32):
+        dev = torch.device("cuda", ctx.device)
+        self.ctx = ctx
+        self.cfg = cfg or LossConfig()
+        self.adam_cfg = adam_cfg or AdamConfig()
+        self.precision = int(precision)
+        t = lambda a: _dev_f32(a, dev)  # noqa: E731
+        self.means, self.quats, self.scales, self.opacities = (t(scene.means), t(scene.quats), t(scene.scales),
+                                                               t(scene.opacities))
+        self.f, self.K, self.V, self.V0 = t(scene.f), t(scene.K), t(scene.V), t(scene.V0)
+        self.F = t(scene.F).to(target_dtype).contiguous()
+        self.mask = torch.as_tensor(scene.mask, dtype=torch.uint8, device=dev).contiguous()
+        self.moments = {k: torch.zeros_like(getattr(self, k)) for k in ("f", "K", "V")}
+        self.moments.update({"v" + k: torch.zeros_like(getattr(self, k)) for k in ("f", "K", "V")})
+        self.camera = camera_struct(scene.camera)
+        self.d, self.M, self.D = self.f.shape[1], self.V.shape[0], self.V.shape[1]
+
+    def frame_struct(self) -> L.Frame:
+        fr = L.Frame()
+        fr.gaussians = _gaussians_struct(self.means, self.quats, self.scales, self.opacities)
+        fr.camera = self.camera
+        fr.F = self.F.data_ptr()
+        fr.F_dtype = _target_dtype(self.F)
+        fr.mask = self.mask.data_ptr()
+        return fr
+
+    def params_struct(self) -> L.Params:
+        p = L.Params()
+        p.f, p.K, p.V, p.V0 = self.f.data_ptr(), self.K.data_ptr(), self.V.data_ptr(), self.V0.data_ptr()
+        m = self.moments
+        p.m_f, p.v_f, p.m_K, p.v_K, p.m_V, p.v_V = (m["f"].data_ptr(), m["vf"].data_ptr(), m["K"].data_ptr(),
+                                                    m["vK"].data_ptr(), m["V"].data_ptr(), m["vV"].data_ptr())
+        p.d, p.M, p.D = self.d, self.M, self.D
+        return p
+
+    def step(self, iters: int = 1, learn_f: bool = True, want_loss: bool = True):
+        """Runs `iters` fwd+bwd+Adam iterations; returns the last iteration's loss parts
+        (host floats) when want_loss, else None (no synchronisation at the end)."""
+        fr, pr = self.frame_struct(), self.params_struct()
+        cs = self.cfg.struct()
+        ac = self.adam_cfg.struct()
+        out = (ctypes.c_double * L.LOSS_PARTS)() if want_loss else None
+        L.check(_lib().latentam_step(self.ctx.handle, ctypes.byref(fr), ctypes.byref(pr), ctypes.byref(cs),
+                                     ctypes.byref(ac), int(iters), int(bool(learn_f)), self.precision,
+                                     out, _stream()))
+        self.adam_cfg.step = int(ac.step)
+        if out is None:
+            return None
+        return dict(cos=out[0], l2=out[1], tr=out[2], total=out[3], n_valid=out[4])
+
+
+def default_logit_scale(d: int) -> float:
+    return 1.0 / math.sqrt(d)

@@ -1,0 +1,507 @@
+// C ABI of include/latentam.h: argument validation, the context and its workspace, and the
+// composition of the kernels into the calls of the latent-feature optimisation step.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "internal.cuh"
+
+namespace lat {
+
+static thread_local char g_err[512] = "";
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+latentam_status cuda_error(cudaError_t e, const char* what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return LATENTAM_ERR_CUDA;
+}
+
+void* ws(latentam_ctx* ctx, Slot s, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (ctx->slot_bytes[s] >= bytes) return ctx->slot_ptr[s];
+    size_t nb = std::max(bytes, ctx->slot_bytes[s] + ctx->slot_bytes[s] / 4);
+    nb = (nb + 4095) & ~(size_t)4095;
+    if (ctx->slot_ptr[s]) {
+        // work already enqueued may still read the old buffer
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            cuda_error(e, "workspace regrow sync");
+            return nullptr;
+        }
+        cudaFree(ctx->slot_ptr[s]);
+        ctx->slot_ptr[s] = nullptr;
+        ctx->slot_bytes[s] = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, nb);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        set_error("workspace allocation of %zu bytes failed: %s", nb, cudaGetErrorString(e));
+        return nullptr;
+    }
+    ctx->slot_ptr[s] = p;
+    ctx->slot_bytes[s] = nb;
+    return p;
+}
+
+static void prof_fold(latentam_ctx* ctx, int stage) {
+    StageProfile& P = ctx->prof[stage];
+    for (int i = 0; i < P.used; ++i) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(P.ev[2 * i + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]) == cudaSuccess)
+            P.acc_ms += ms;
+        P.count += 1;
+    }
+    (void)cudaGetLastError();
+    P.used = 0;
+}
+
+int prof_begin(latentam_ctx* ctx, int stage, cudaStream_t st) {
+    StageProfile& P = ctx->prof[stage];
+    if (P.used == kProfPairs) prof_fold(ctx, stage);
+    const int i = P.used;
+    while (P.created < 2 * (i + 1)) {
+        if (cudaEventCreate(&P.ev[P.created]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return -1;
+        }
+        ++P.created;
+    }
+    if (cudaEventRecord(P.ev[2 * i], st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -1;
+    }
+    P.used = i + 1;
+    return i;
+}
+
+void prof_end(latentam_ctx* ctx, int stage, int idx, cudaStream_t st) {
+    if (cudaEventRecord(ctx->prof[stage].ev[2 * idx + 1], st) != cudaSuccess) (void)cudaGetLastError();
+}
+
+}  // namespace lat
+
+using namespace lat;
+
+namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+latentam_status enter(latentam_ctx* ctx) {
+    g_err[0] = '\0';
+    if (!ctx) {
+        set_error("null context");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+    return LATENTAM_OK;
+}
+
+latentam_status check_camera(const latentam_camera* cam) {
+    if (!cam) {
+        set_error("null camera");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384) {
+        set_error("image %dx%d outside 1..16384", cam->width, cam->height);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f) || !(cam->z_near > 0.f)) {
+        set_error("camera needs fx, fy, z_near > 0");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    return LATENTAM_OK;
+}
+
+latentam_status check_d(int d) {
+    if (d != 16 && d != 32 && d != 64) {
+        set_error("query dimension d=%d not in {16, 32, 64}", d);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    return LATENTAM_OK;
+}
+
+latentam_status check_dict(int M, int D) {
+    if (M < 32 || M > 1024 || M % 32 != 0) {
+        set_error("dictionary size M=%d must be a multiple of 32 in [32, 1024]", M);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    if (D < 128 || D > 2048 || D % 128 != 0) {
+        set_error("value dimension D=%d must be a multiple of 128 in [128, 2048]", D);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    return LATENTAM_OK;
+}
+
+#define REQUIRE(cond, ...)                       \
+    do {                                         \
+        if (!(cond)) {                           \
+            set_error(__VA_ARGS__);              \
+            return LATENTAM_ERR_INVALID_ARG;     \
+        }                                        \
+    } while (0)
+
+latentam_status check_projected(const latentam_projected* p) {
+    REQUIRE(p && p->xy && p->conic_opacity && p->depth && p->rect && p->tiles_touched, "incomplete projection buffers");
+    REQUIRE(aligned16(p->conic_opacity) && aligned16(p->rect) && (reinterpret_cast<uintptr_t>(p->xy) & 7u) == 0,
+            "projection buffers must be 16-byte aligned");
+    return LATENTAM_OK;
+}
+
+latentam_status check_bins(const latentam_bins* b, bool need_pairs) {
+    REQUIRE(b && b->tile_ranges && aligned16(b->tile_ranges), "tile_ranges missing or not 16-byte aligned");
+    REQUIRE(b->capacity >= 0, "negative pair capacity");
+    if (need_pairs) REQUIRE(b->num_pairs >= 0 && b->num_pairs <= b->capacity, "bins hold no sorted pairs");
+    REQUIRE(b->pair_ids || b->capacity == 0, "pair_ids missing");
+    return LATENTAM_OK;
+}
+
+float logit_scale(const latentam_loss_cfg* cfg, int d) {
+    return (cfg && cfg->logit_scale > 0.f) ? cfg->logit_scale : 1.0f / sqrtf((float)d);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t latentam_version(void) { return LATENTAM_ABI_VERSION; }
+
+int64_t latentam_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* latentam_last_error(void) { return g_err; }
+
+int32_t latentam_num_tiles(const latentam_camera* cam) {
+    if (!cam || cam->width < 1 || cam->height < 1) return 0;
+    return ((cam->width + kTile - 1) / kTile) * ((cam->height + kTile - 1) / kTile);
+}
+
+latentam_status latentam_ctx_create(int32_t device, latentam_ctx** out) {
+    g_err[0] = '\0';
+    if (!out) {
+        set_error("null output pointer");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) {
+        set_error("device %d not present (%d devices)", device, count);
+        return LATENTAM_ERR_CUDA;
+    }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceProperties");
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        set_error("device %d is sm_%d%d; this library is built for sm_103a (GB300) only", device, prop.major,
+                  prop.minor);
+        return LATENTAM_ERR_CUDA;
+    }
+    latentam_ctx* c = new (std::nothrow) latentam_ctx;
+    if (!c) {
+        set_error("host allocation failed");
+        return LATENTAM_ERR_OUT_OF_MEMORY;
+    }
+    memset(c, 0, sizeof(*c));
+    c->device = device;
+    c->num_sms = prop.multiProcessorCount;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    *out = c;
+    return LATENTAM_OK;
+}
+
+latentam_status latentam_ctx_destroy(latentam_ctx* ctx) {
+    g_err[0] = '\0';
+    if (!ctx) return LATENTAM_OK;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    for (int s = 0; s < WS_NUM_SLOTS; ++s)
+        if (ctx->slot_ptr[s]) cudaFree(ctx->slot_ptr[s]);
+    for (int s = 0; s < LATENTAM_NUM_STAGES; ++s)
+        for (int i = 0; i < ctx->prof[s].created; ++i) cudaEventDestroy(ctx->prof[s].ev[i]);
+    delete ctx;
+    if (e != cudaSuccess) return cuda_error(e, "synchronise before destroy");
+    return LATENTAM_OK;
+}
+
+latentam_status latentam_profile_enable(latentam_ctx* ctx, int32_t enable) {
+    LAT_TRY(enter(ctx));
+    ctx->profiling = enable != 0;
+    return LATENTAM_OK;
+}
+
+latentam_status latentam_profile_read(latentam_ctx* ctx, double* ms, int64_t* counts, int32_t reset) {
+    LAT_TRY(enter(ctx));
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_error(e, "profile synchronise");
+    for (int s = 0; s < LATENTAM_NUM_STAGES; ++s) {
+        prof_fold(ctx, s);
+        if (ms) ms[s] = ctx->prof[s].acc_ms;
+        if (counts) counts[s] = ctx->prof[s].count;
+        if (reset) {
+            ctx->prof[s].acc_ms = 0.0;
+            ctx->prof[s].count = 0;
+        }
+    }
+    return LATENTAM_OK;
+}
+
+latentam_status latentam_project(latentam_ctx* ctx, const latentam_gaussians* g, const latentam_camera* cam,
+                                 const latentam_projected* out, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_camera(cam));
+    REQUIRE(g && g->n >= 0, "bad Gaussian set");
+    LAT_TRY(check_projected(out));
+    if (g->n > 0) REQUIRE(g->means && g->quats && g->scales && g->opacities, "null Gaussian attribute");
+    StageTimer tm(ctx, LATENTAM_STAGE_PROJECT, (cudaStream_t)stream);
+    return launch_project(*g, cam_params(*cam), *out, (cudaStream_t)stream);
+}
+
+latentam_status latentam_sort(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
+                              const latentam_camera* cam, latentam_bins* bins, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_camera(cam));
+    REQUIRE(n >= 0, "negative Gaussian count");
+    LAT_TRY(check_projected(proj));
+    LAT_TRY(check_bins(bins, false));
+    StageTimer tm(ctx, LATENTAM_STAGE_SORT, (cudaStream_t)stream);
+    return bin_and_sort(ctx, n, *proj, cam_params(*cam), bins, (cudaStream_t)stream);
+}
+
+latentam_status latentam_render_fwd(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
+                                    const latentam_camera* cam, const latentam_bins* bins, const float* f, int32_t d,
+                                    float* Q, float* T_final, int32_t* n_contrib, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_camera(cam));
+    LAT_TRY(check_d(d));
+    LAT_TRY(check_projected(proj));
+    LAT_TRY(check_bins(bins, true));
+    REQUIRE(n >= 0 && (n == 0 || f), "bad queries");
+    REQUIRE(Q && T_final && n_contrib, "null output");
+    REQUIRE(aligned16(f) && aligned16(Q), "f and Q must be 16-byte aligned");
+    StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, (cudaStream_t)stream);
+    return launch_render_fwd(cam_params(*cam), *proj, *bins, f, d, Q, T_final, n_contrib, (cudaStream_t)stream);
+}
+
+latentam_status latentam_render_bwd(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
+                                    const latentam_camera* cam, const latentam_bins* bins, const int32_t* n_contrib,
+                                    const float* dQ, int32_t d, float* df, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_camera(cam));
+    LAT_TRY(check_d(d));
+    LAT_TRY(check_projected(proj));
+    LAT_TRY(check_bins(bins, true));
+    REQUIRE(n >= 0 && n_contrib && dQ && (df || n == 0), "null argument");
+    REQUIRE(aligned16(dQ), "dQ must be 16-byte aligned");
+    if (n == 0) return LATENTAM_OK;
+    StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, (cudaStream_t)stream);
+    return launch_render_bwd(cam_params(*cam), *proj, *bins, n_contrib, dQ, d, df, n, (cudaStream_t)stream);
+}
+
+latentam_status latentam_decode_fwd(latentam_ctx* ctx, const float* Q, int64_t n, int32_t d, const float* K,
+                                    const float* V, int32_t M, int32_t D, float logit_scale_, latentam_precision prec,
+                                    float* F_hat, float* row_stats, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_d(d));
+    LAT_TRY(check_dict(M, D));
+    REQUIRE(n >= 0 && (n == 0 || Q) && K && V, "null argument");
+    REQUIRE(aligned16(Q) && aligned16(V) && aligned16(F_hat), "Q, V, F_hat must be 16-byte aligned");
+    const float c = logit_scale_ > 0.f ? logit_scale_ : 1.0f / sqrtf((float)d);
+    StageTimer tm(ctx, LATENTAM_STAGE_DECODE, (cudaStream_t)stream);
+    if (prec == LATENTAM_PREC_FP32)
+        return decode_fwd_f32(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, (cudaStream_t)stream);
+    if (prec == LATENTAM_PREC_BF16)
+        return decode_fwd_bf16(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, (cudaStream_t)stream);
+    set_error("unknown precision %d", prec);
+    return LATENTAM_ERR_INVALID_ARG;
+}
+
+latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const float* Q, int64_t n, int32_t d, const float* K,
+                                         const float* V, const float* V0, int32_t M, int32_t D, const void* F,
+                                         latentam_dtype F_dtype, const uint8_t* mask, const latentam_loss_cfg* cfg,
+                                         latentam_precision prec, double* loss_parts, float* dQ, float* dK, float* dV,
+                                         latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_d(d));
+    LAT_TRY(check_dict(M, D));
+    REQUIRE(cfg && loss_parts, "null config or loss output");
+    REQUIRE(n >= 0 && (n == 0 || (Q && F)) && K && V && V0, "null argument");
+    REQUIRE(F_dtype == LATENTAM_DTYPE_F32 || F_dtype == LATENTAM_DTYPE_BF16, "unknown target dtype %d", F_dtype);
+    REQUIRE(aligned16(Q) && aligned16(V) && aligned16(V0) && aligned16(F) && aligned16(dQ) && aligned16(dV),
+            "Q, V, V0, F, dQ, dV must be 16-byte aligned");
+    DecodeArgs a;
+    a.Q = Q;
+    a.n = n;
+    a.d = d;
+    a.K = K;
+    a.V = V;
+    a.V0 = V0;
+    a.M = M;
+    a.D = D;
+    a.c = logit_scale(cfg, d);
+    a.F = F;
+    a.F_dtype = F_dtype;
+    a.mask = mask;
+    a.cfg = *cfg;
+    a.loss_parts = loss_parts;
+    a.dQ = dQ;
+    a.dK = dK;
+    a.dV = dV;
+    StageTimer tm(ctx, LATENTAM_STAGE_DECODE, (cudaStream_t)stream);
+    if (prec == LATENTAM_PREC_FP32) return decode_loss_bwd_f32(ctx, a, (cudaStream_t)stream);
+    if (prec == LATENTAM_PREC_BF16) return decode_loss_bwd_bf16(ctx, a, (cudaStream_t)stream);
+    set_error("unknown precision %d", prec);
+    return LATENTAM_ERR_INVALID_ARG;
+}
+
+latentam_status latentam_backward(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
+                                  const latentam_camera* cam, const latentam_bins* bins, const int32_t* n_contrib,
+                                  const float* Q, int32_t d, const float* K, const float* V, const float* V0,
+                                  int32_t M, int32_t D, const void* F, latentam_dtype F_dtype, const uint8_t* mask,
+                                  const latentam_loss_cfg* cfg, latentam_precision prec, double* loss_parts,
+                                  float* dQ_scratch, float* df, float* dK, float* dV, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_camera(cam));
+    REQUIRE(dQ_scratch || !df, "df needs dQ_scratch");
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    LAT_TRY(latentam_decode_loss_bwd(ctx, Q, npix, d, K, V, V0, M, D, F, F_dtype, mask, cfg, prec, loss_parts,
+                                     df ? dQ_scratch : nullptr, dK, dV, stream));
+    if (!df) return LATENTAM_OK;
+    return latentam_render_bwd(ctx, n, proj, cam, bins, n_contrib, dQ_scratch, d, df, stream);
+}
+
+latentam_status latentam_adam(latentam_ctx* ctx, int32_t count, float* const* params, const float* const* grads,
+                              float* const* m, float* const* v, const int64_t* sizes, const float* lrs,
+                              const latentam_adam_cfg* cfg, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    REQUIRE(cfg && count >= 0 && (count == 0 || (params && grads && m && v && sizes && lrs)), "null argument");
+    AdamTensor t[8];
+    REQUIRE(count <= 8, "at most 8 tensors per call");
+    for (int k = 0; k < count; ++k) {
+        REQUIRE(sizes[k] >= 0 && (sizes[k] == 0 || (params[k] && grads[k] && m[k] && v[k])), "bad tensor %d", k);
+        t[k] = AdamTensor{params[k], grads[k], m[k], v[k], sizes[k], lrs[k]};
+    }
+    StageTimer tm(ctx, LATENTAM_STAGE_ADAM, (cudaStream_t)stream);
+    return launch_adam(ctx, t, count, cfg->beta1, cfg->beta2, cfg->eps, cfg->step, (cudaStream_t)stream);
+}
+
+latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, latentam_params* params,
+                              const latentam_loss_cfg* cfg, latentam_adam_cfg* adam, int32_t iters, int32_t learn_f,
+                              latentam_precision prec, double* loss_host, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    REQUIRE(frame && params && cfg && adam && iters >= 0, "null argument");
+    LAT_TRY(check_camera(&frame->camera));
+    LAT_TRY(check_d(params->d));
+    LAT_TRY(check_dict(params->M, params->D));
+    const latentam_gaussians& g = frame->gaussians;
+    REQUIRE(g.n >= 0, "negative Gaussian count");
+    REQUIRE(params->f && params->K && params->V && params->V0 && params->m_K && params->v_K && params->m_V &&
+                params->v_V && (!learn_f || (params->m_f && params->v_f)),
+            "null parameter or moment");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int d = params->d, M = params->M, D = params->D;
+    const int N = g.n;
+    const latentam_camera& cam = frame->camera;
+    const int64_t npix = (int64_t)cam.width * cam.height;
+    const int64_t tiles = latentam_num_tiles(&cam);
+
+    // projection + bins in the context's own buffers (256-byte aligned sub-buffers)
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t o_xy = 0, o_co = o_xy + up(8 * (size_t)N), o_dp = o_co + up(16 * (size_t)N),
+                 o_rc = o_dp + up(4 * (size_t)N), o_tt = o_rc + up(16 * (size_t)N), o_tr = o_tt + up(4 * (size_t)N),
+                 o_end = o_tr + up(8 * (size_t)tiles);
+    char* pb = static_cast<char*>(ws(ctx, WS_STEP_PROJ, o_end));
+    if (!pb) return LATENTAM_ERR_OUT_OF_MEMORY;
+    latentam_projected proj{reinterpret_cast<float*>(pb + o_xy), reinterpret_cast<float*>(pb + o_co),
+                            reinterpret_cast<float*>(pb + o_dp), reinterpret_cast<int32_t*>(pb + o_rc),
+                            reinterpret_cast<int32_t*>(pb + o_tt)};
+    latentam_bins bins{};
+    bins.tile_ranges = reinterpret_cast<int32_t*>(pb + o_tr);
+    bins.pair_ids = static_cast<int32_t*>(ctx->slot_ptr[WS_STEP_PAIRS]);
+    bins.capacity = (int64_t)(ctx->slot_bytes[WS_STEP_PAIRS] / sizeof(int32_t));
+    if (N > 0) REQUIRE(g.means && g.quats && g.scales && g.opacities, "null Gaussian attribute");
+    {
+        StageTimer tm(ctx, LATENTAM_STAGE_PROJECT, st);
+        LAT_TRY(launch_project(g, cam_params(cam), proj, st));
+    }
+    latentam_status s;
+    {
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+        s = bin_and_sort(ctx, N, proj, cam_params(cam), &bins, st);
+    }
+    if (s == LATENTAM_ERR_CAPACITY) {
+        bins.pair_ids = static_cast<int32_t*>(ws(ctx, WS_STEP_PAIRS, sizeof(int32_t) * (size_t)bins.num_pairs));
+        if (!bins.pair_ids) return LATENTAM_ERR_OUT_OF_MEMORY;
+        bins.capacity = bins.num_pairs;
+        // the projection buffers are intact; only the binning is redone
+        pb = static_cast<char*>(ctx->slot_ptr[WS_STEP_PROJ]);
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+        s = bin_and_sort(ctx, N, proj, cam_params(cam), &bins, st);
+    }
+    LAT_TRY(s);
+
+    // images and gradients
+    const size_t i_q = 0, i_t = i_q + up(4 * (size_t)npix * d), i_n = i_t + up(4 * (size_t)npix),
+                 i_dq = i_n + up(4 * (size_t)npix), i_end = i_dq + up(4 * (size_t)npix * d);
+    char* ib = static_cast<char*>(ws(ctx, WS_STEP_IMG, i_end));
+    const size_t g_df = 0, g_dk = g_df + up(4 * (size_t)N * d), g_dv = g_dk + up(4 * (size_t)M * d),
+                 g_lp = g_dv + up(4 * (size_t)M * D), g_end = g_lp + up(8 * LATENTAM_LOSS_PARTS);
+    char* gb = static_cast<char*>(ws(ctx, WS_STEP_GRAD, g_end));
+    if (!ib || !gb) return LATENTAM_ERR_OUT_OF_MEMORY;
+    float* Q = reinterpret_cast<float*>(ib + i_q);
+    float* T = reinterpret_cast<float*>(ib + i_t);
+    int32_t* nc = reinterpret_cast<int32_t*>(ib + i_n);
+    float* dQ = reinterpret_cast<float*>(ib + i_dq);
+    float* df = reinterpret_cast<float*>(gb + g_df);
+    float* dK = reinterpret_cast<float*>(gb + g_dk);
+    float* dV = reinterpret_cast<float*>(gb + g_dv);
+    double* lp = reinterpret_cast<double*>(gb + g_lp);
+    const CamParams cp = cam_params(cam);
+    for (int it = 0; it < iters; ++it) {
+        if (it == 0 || learn_f) {
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, st);
+            LAT_TRY(launch_render_fwd(cp, proj, bins, params->f, d, Q, T, nc, st));
+        }
+        LAT_TRY(latentam_decode_loss_bwd(ctx, Q, npix, d, params->K, params->V, params->V0, M, D, frame->F,
+                                         frame->F_dtype, frame->mask, cfg, prec, lp, learn_f ? dQ : nullptr, dK, dV,
+                                         stream));
+        if (learn_f && N > 0) {
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, st);
+            LAT_TRY(launch_render_bwd(cp, proj, bins, nc, dQ, d, df, N, st));
+        }
+        AdamTensor t[3];
+        int cnt = 0;
+        if (learn_f) t[cnt++] = AdamTensor{params->f, df, params->m_f, params->v_f, (int64_t)N * d, adam->lr_f};
+        t[cnt++] = AdamTensor{params->K, dK, params->m_K, params->v_K, (int64_t)M * d, adam->lr_dict};
+        t[cnt++] = AdamTensor{params->V, dV, params->m_V, params->v_V, (int64_t)M * D, adam->lr_dict};
+        {
+            StageTimer tm(ctx, LATENTAM_STAGE_ADAM, st);
+            LAT_TRY(launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, st));
+        }
+        adam->step += 1;
+    }
+    if (loss_host) {
+        cudaError_t e = cudaMemcpyAsync(loss_host, lp, sizeof(double) * LATENTAM_LOSS_PARTS, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_error(e, "copy loss");
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_error(e, "synchronise step");
+    }
+    return LATENTAM_OK;
+}
+
+}  // extern "C"

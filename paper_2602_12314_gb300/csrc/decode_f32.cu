@@ -1,0 +1,572 @@
+// Dictionary decode (Sec. III-B, Eq. dict_recon), feature objective (Eq. feat_loss,
+// Eq. full_obj) and its backward, plain FP32 form on the CUDA cores.
+//
+//   rows kernel (32 pixels / CTA):  S = c Q K^T -> row softmax A -> Fhat = A V
+//        -> per-pixel cos / L2 against F -> dFhat = a_p Fhat_p + b_p F_p  (loss written FP64)
+//   rows-backward kernel:           dA = dFhat V^T -> dS = A (dA - <A, dA>) -> dQ = c dS K
+//   dictionary kernels (split-K):   dV = A^T dFhat + trust-region term, dK = c dS^T Q
+//
+// dL/dFhat_p = a_p Fhat_p + b_p F_p with
+//   a_p = lambda_f/|Omega| (lambda_cos cos_p / |Fhat_p|^2 + 2 lambda_2 / D)
+//   b_p = lambda_f/|Omega| (-lambda_cos / (|Fhat_p| |F_p|) - 2 lambda_2 / D),
+// and <A_p, dA_p> = <Fhat_p, dFhat_p> = a_p |Fhat_p|^2 + b_p <Fhat_p, F_p>.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace lat {
+namespace {
+
+constexpr int kRows = 32;      // pixels per CTA in the row kernels
+constexpr int kThreads = 256;  // 8 warps x 4 rows
+constexpr int kAtomChunk = 128;
+constexpr int kColChunk = 512;  // 32 lanes x 4 floats x 4 groups
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float4 load_target4(const void* F, latentam_dtype dt, size_t idx4) {
+    if (dt == LATENTAM_DTYPE_F32) return reinterpret_cast<const float4*>(F)[idx4];
+    const uint2 raw = reinterpret_cast<const uint2*>(F)[idx4];
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+    const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Accumulators: [0] sum over valid pixels of (1 - cos), [1] sum of squared errors,
+// [2] trust-region sum, [3] |Omega|.
+struct LossAcc {
+    double* acc;
+};
+
+__global__ void count_mask_kernel(const uint8_t* __restrict__ mask, int64_t n, double* __restrict__ acc) {
+    __shared__ int s[kThreads / 32];
+    int c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += mask ? (mask[i] != 0) : 1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += s[w];
+        atomicAdd(&acc[3], (double)t);
+    }
+}
+
+// Trust-region term of Eq. (feat_loss) on the value rows: one warp per atom.  coef[j] =
+// lambda_f lambda_D / |V_j - V0_j| when the atom is outside the radius, else 0.
+__global__ void trust_region_kernel(const float* __restrict__ V, const float* __restrict__ V0, int M, int D,
+                                    float delta, float weight, float* __restrict__ coef, double* __restrict__ acc) {
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= M) return;
+    float s = 0.f;
+    for (int k = lane; k < D; k += 32) {
+        const float t = V[(size_t)j * D + k] - V0[(size_t)j * D + k];
+        s += t * t;
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+        const float nrm = sqrtf(s);
+        const bool out = nrm > delta;
+        coef[j] = out ? weight / nrm : 0.f;
+        if (out) atomicAdd(&acc[2], (double)(nrm - delta));
+    }
+}
+
+// ---- rows kernel: S, softmax, Fhat, loss coefficients, dFhat ---------------------------
+// smem: sA[kRows][M] | sKt[d][kAtomChunk + 1] | sQ[kRows][d] | stats
+template <int DQ, bool TRAIN>
+__global__ void __launch_bounds__(kThreads) dec_rows_fwd(const float* __restrict__ Q, int64_t n, const float* __restrict__ K,
+                                                          const float* __restrict__ V, int M, int D, float c,
+                                                          const void* __restrict__ F, latentam_dtype F_dtype,
+                                                          const uint8_t* __restrict__ mask, latentam_loss_cfg cfg,
+                                                          double* __restrict__ acc, float* __restrict__ A_out,
+                                                          float* __restrict__ Fh_out, float* __restrict__ row_out,
+                                                          float* __restrict__ stats_out) {
+    extern __shared__ float smem[];
+    float* sA = smem;                                  // kRows * M
+    float* sKt = sA + kRows * M;                       // DQ * (kAtomChunk + 1)
+    float* sQ = sKt + DQ * (kAtomChunk + 1);           // kRows * DQ
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    // stage the query tile
+    for (int e = t; e < kRows * DQ; e += kThreads) {
+        const int r = e / DQ;
+        sQ[e] = (row0 + r < n) ? Q[(row0 + r) * DQ + (e % DQ)] : 0.f;
+    }
+    // S = c Q K^T, atoms in chunks of 128 (lane owns atoms lane + 32u)
+    for (int j0 = 0; j0 < M; j0 += kAtomChunk) {
+        const int jc = min(kAtomChunk, M - j0);
+        __syncthreads();
+        for (int e = t; e < jc * DQ; e += kThreads) {
+            const int jj = e / DQ, k = e % DQ;
+            sKt[k * (kAtomChunk + 1) + jj] = K[(size_t)(j0 + jj) * DQ + k];
+        }
+        __syncthreads();
+        float s[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[r][u] = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < DQ; ++k) {
+            float kv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) kv[u] = sKt[k * (kAtomChunk + 1) + lane + 32 * u];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float q = sQ[(warp * 4 + r) * DQ + k];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) s[r][u] += q * kv[u];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (lane + 32 * u < jc) sA[(warp * 4 + r) * M + j0 + lane + 32 * u] = c * s[r][u];
+    }
+    __syncthreads();
+    // row softmax (warp per 4 rows)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int rr = warp * 4 + r;
+        float* a = sA + rr * M;
+        float m = -INFINITY;
+        for (int j = lane; j < M; j += 32) m = fmaxf(m, a[j]);
+        m = warp_max(m);
+        float l = 0.f;
+        for (int j = lane; j < M; j += 32) {
+            const float e = __expf(a[j] - m);
+            a[j] = e;
+            l += e;
+        }
+        l = warp_sum(l);
+        const float il = 1.0f / l;
+        const int64_t p = row0 + rr;
+        for (int j = lane; j < M; j += 32) {
+            const float v = a[j] * il;
+            a[j] = v;
+            if (TRAIN && p < n) A_out[p * M + j] = v;
+        }
+        if (lane == 0 && stats_out && p < n) {
+            stats_out[2 * p] = m;
+            stats_out[2 * p + 1] = l;
+        }
+    }
+    __syncthreads();
+    // Fhat = A V in column chunks; thread owns rows 4 warp + r, columns c0 + 4 lane + 128 g
+    float pdot[4] = {0.f, 0.f, 0.f, 0.f}, pnh[4] = {0.f, 0.f, 0.f, 0.f}, pnf[4] = {0.f, 0.f, 0.f, 0.f},
+          perr[4] = {0.f, 0.f, 0.f, 0.f};
+    const float4* V4 = reinterpret_cast<const float4*>(V);
+    const int D4 = D / 4;
+    for (int c0 = 0; c0 < D; c0 += kColChunk) {
+        const int ng = min(4, (D - c0) / 128);
+        float4 accv[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int g = 0; g < 4; ++g) accv[r][g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < M; ++j) {
+            float a[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = sA[(warp * 4 + r) * M + j];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (g < ng) {
+                    const float4 v = __ldg(&V4[(size_t)j * D4 + (c0 / 4) + lane + 32 * g]);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        accv[r][g].x += a[r] * v.x;
+                        accv[r][g].y += a[r] * v.y;
+                        accv[r][g].z += a[r] * v.z;
+                        accv[r][g].w += a[r] * v.w;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t p = row0 + warp * 4 + r;
+            if (p >= n) continue;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (g >= ng) continue;
+                const size_t idx4 = (size_t)p * D4 + (c0 / 4) + lane + 32 * g;
+                const float4 h = accv[r][g];
+                reinterpret_cast<float4*>(Fh_out)[idx4] = h;
+                if (TRAIN) {
+                    const float4 f = load_target4(F, F_dtype, idx4);
+                    pdot[r] += h.x * f.x + h.y * f.y + h.z * f.z + h.w * f.w;
+                    pnh[r] += h.x * h.x + h.y * h.y + h.z * h.z + h.w * h.w;
+                    pnf[r] += f.x * f.x + f.y * f.y + f.z * f.z + f.w * f.w;
+                    const float ex = h.x - f.x, ey = h.y - f.y, ez = h.z - f.z, ew = h.w - f.w;
+                    perr[r] += ex * ex + ey * ey + ez * ez + ew * ew;
+                }
+            }
+        }
+    }
+    if (!TRAIN) return;
+    // per-pixel coefficients of dL/dFhat; loss sums in FP64
+    const double nv = acc[3];
+    const float scale = nv > 0.0 ? (float)((double)cfg.lambda_f / nv) : 0.f;
+    double loc_cos = 0.0, loc_err = 0.0;
+    float ra[4], rb[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float dot = warp_sum(pdot[r]), nh2 = warp_sum(pnh[r]), nf2 = warp_sum(pnf[r]), e2 = warp_sum(perr[r]);
+        const int64_t p = row0 + warp * 4 + r;
+        const bool valid = p < n && (mask == nullptr || mask[p] != 0);
+        const float den = sqrtf(nh2) * sqrtf(nf2);
+        const float cs = dot / fmaxf(den, 1e-8f);
+        float a = 0.f, b = 0.f;
+        if (valid) {
+            loc_cos += 1.0 - (double)cs;
+            loc_err += (double)e2;
+            const float l2c = 2.0f * cfg.lambda_2 / (float)D;
+            if (den > 1e-8f) {
+                a = scale * (cfg.lambda_cos * cs / nh2 + l2c);
+                b = scale * (-cfg.lambda_cos / den - l2c);
+            } else {
+                a = scale * l2c;
+                b = scale * (-cfg.lambda_cos / 1e-8f - l2c);
+            }
+        }
+        ra[r] = a;
+        rb[r] = b;
+        if (lane == 0 && p < n) {
+            row_out[4 * p] = a;
+            row_out[4 * p + 1] = b;
+            row_out[4 * p + 2] = a * nh2 + b * dot;  // <A_p, dA_p>
+            row_out[4 * p + 3] = cs;
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&acc[0], loc_cos);
+        atomicAdd(&acc[1], loc_err);
+    }
+    // dFhat = a Fhat + b F in place over the Fhat buffer (rows of this warp only)
+    for (int c0 = 0; c0 < D; c0 += 128) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t p = row0 + warp * 4 + r;
+            if (p >= n) continue;
+            const size_t idx4 = (size_t)p * D4 + (c0 / 4) + lane;
+            const float4 h = reinterpret_cast<const float4*>(Fh_out)[idx4];
+            const float4 f = load_target4(F, F_dtype, idx4);
+            reinterpret_cast<float4*>(Fh_out)[idx4] =
+                make_float4(ra[r] * h.x + rb[r] * f.x, ra[r] * h.y + rb[r] * f.y, ra[r] * h.z + rb[r] * f.z,
+                            ra[r] * h.w + rb[r] * f.w);
+        }
+    }
+}
+
+// ---- rows-backward kernel: dA, dS, dQ ----------------------------------------------------
+// smem: sdS[kRows][M] | sV[kAtomChunk][33] | sdF[kRows][33]
+template <int DQ>
+__global__ void __launch_bounds__(kThreads) dec_rows_bwd(const float* __restrict__ dFh, const float* __restrict__ A,
+                                                          const float* __restrict__ row, const float* __restrict__ K,
+                                                          const float* __restrict__ V, int64_t n, int M, int D, float c,
+                                                          float* __restrict__ dS_out, float* __restrict__ dQ) {
+    extern __shared__ float smem[];
+    float* sdS = smem;                     // kRows * M
+    float* sV = sdS + kRows * M;           // kAtomChunk * 33
+    float* sdF = sV + kAtomChunk * 33;     // kRows * 33
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    for (int j0 = 0; j0 < M; j0 += kAtomChunk) {
+        const int jc = min(kAtomChunk, M - j0);
+        float s[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[r][u] = 0.f;
+        for (int k0 = 0; k0 < D; k0 += 32) {
+            __syncthreads();
+            for (int e = t; e < jc * 32; e += kThreads) {
+                const int jj = e >> 5, k = e & 31;
+                sV[jj * 33 + k] = V[(size_t)(j0 + jj) * D + k0 + k];
+            }
+            for (int e = t; e < kRows * 32; e += kThreads) {
+                const int r = e >> 5, k = e & 31;
+                sdF[r * 33 + k] = (row0 + r < n) ? dFh[(row0 + r) * D + k0 + k] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                float vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) vv[u] = (lane + 32 * u < jc) ? sV[(lane + 32 * u) * 33 + k] : 0.f;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float g = sdF[(warp * 4 + r) * 33 + k];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) s[r][u] += g * vv[u];
+                }
+            }
+        }
+        // dS = A (dA - <A, dA>)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t p = row0 + warp * 4 + r;
+            const float rd = p < n ? row[4 * p + 2] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + lane + 32 * u;
+                if (lane + 32 * u >= jc) continue;
+                float ds = 0.f;
+                if (p < n) {
+                    ds = A[p * M + j] * (s[r][u] - rd);
+                    dS_out[p * M + j] = ds;
+                }
+                sdS[(warp * 4 + r) * M + j] = ds;
+            }
+        }
+    }
+    __syncthreads();
+    if (!dQ) return;
+    // dQ = c dS K : thread -> row t / 8, columns (t % 8) * DQ/8 ...
+    constexpr int CPT = DQ / 8;
+    const int r = t >> 3, cb = (t & 7) * CPT;
+    float q[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) q[i] = 0.f;
+    for (int j = 0; j < M; ++j) {
+        const float ds = sdS[r * M + j];
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) q[i] += ds * __ldg(&K[(size_t)j * DQ + cb + i]);
+    }
+    const int64_t p = row0 + r;
+    if (p < n)
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) dQ[p * DQ + cb + i] = c * q[i];
+}
+
+// ---- split-K C = X^T Y over pixels: X (n x ldx, columns [x0, x0+64)), Y (n x ldy) ----------
+// Block tile: 64 atoms x (32 * VEC) columns; thread: 8 atoms x VEC columns.
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) atb_splitk(const float* __restrict__ X, int ldx, int nx,
+                                                        const float* __restrict__ Y, int ldy, int ny, int64_t n,
+                                                        int64_t rows_per_split, float* __restrict__ part) {
+    constexpr int CT = 32 * VEC;
+    __shared__ __align__(16) float sX[32][64];
+    __shared__ __align__(16) float sY[32][CT];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * CT;
+    const int64_t p_begin = (int64_t)blockIdx.z * rows_per_split;
+    const int64_t p_end = min(n, p_begin + rows_per_split);
+    float acc[8][VEC];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[i][v] = 0.f;
+    for (int64_t p0 = p_begin; p0 < p_end; p0 += 32) {
+        __syncthreads();
+        for (int e = t; e < 32 * 64; e += kThreads) {
+            const int pr = e >> 6, j = e & 63;
+            const int64_t p = p0 + pr;
+            sX[pr][j] = (p < p_end && x0 + j < nx) ? X[p * ldx + x0 + j] : 0.f;
+        }
+        for (int e = t; e < 32 * CT; e += kThreads) {
+            const int pr = e / CT, k = e % CT;
+            const int64_t p = p0 + pr;
+            sY[pr][k] = (p < p_end && y0 + k < ny) ? Y[p * ldy + y0 + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int pr = 0; pr < 32; ++pr) {
+            float xv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) xv[i] = sX[pr][warp * 8 + i];
+            float yv[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) yv[v] = sY[pr][lane * VEC + v];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[i][v] += xv[i] * yv[v];
+        }
+    }
+    const size_t base = (size_t)blockIdx.z * nx * ny;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int j = x0 + warp * 8 + i;
+        if (j >= nx) continue;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const int k = y0 + lane * VEC + v;
+            if (k < ny) part[base + (size_t)j * ny + k] = acc[i][v];
+        }
+    }
+}
+
+// out[j][k] = scale * sum_s part[s][j][k] (+ coef[j] (V - V0)[j][k] when coef != NULL)
+__global__ void reduce_splits(const float* __restrict__ part, int splits, int nx, int ny, float scale,
+                              const float* __restrict__ coef, const float* __restrict__ V,
+                              const float* __restrict__ V0, float* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)nx * ny;
+    if (e >= total) return;
+    float s = 0.f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * total + e];
+    s *= scale;
+    if (coef) {
+        const int j = (int)(e / ny);
+        s += coef[j] * (V[e] - V0[e]);
+    }
+    out[e] = s;
+}
+
+__global__ void finalize_loss(const double* __restrict__ acc, int D, latentam_loss_cfg cfg, double* __restrict__ parts) {
+    const double nv = acc[3];
+    const double lcos = nv > 0 ? acc[0] / nv : 0.0;
+    const double l2 = nv > 0 ? acc[1] / (nv * D) : 0.0;
+    const double tr = acc[2];
+    parts[0] = lcos;
+    parts[1] = l2;
+    parts[2] = tr;
+    parts[3] = (double)cfg.lambda_f * ((double)cfg.lambda_cos * lcos + (double)cfg.lambda_2 * l2 +
+                                       (double)cfg.lambda_D * tr);
+    parts[4] = nv;
+}
+
+size_t rows_fwd_smem(int d, int M) { return sizeof(float) * ((size_t)kRows * M + (size_t)d * (kAtomChunk + 1) + (size_t)kRows * d); }
+size_t rows_bwd_smem(int M) { return sizeof(float) * ((size_t)kRows * M + (size_t)kAtomChunk * 33 + (size_t)kRows * 33); }
+
+template <int DQ, bool TRAIN>
+latentam_status launch_rows_fwd(const float* Q, int64_t n, const float* K, const float* V, int M, int D, float c,
+                                const void* F, latentam_dtype F_dtype, const uint8_t* mask,
+                                const latentam_loss_cfg& cfg, double* acc, float* A_out, float* Fh, float* row,
+                                float* stats, cudaStream_t st) {
+    const size_t smem = rows_fwd_smem(DQ, M);
+    auto kern = dec_rows_fwd<DQ, TRAIN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "dec_rows_fwd smem attribute");
+    const unsigned blocks = (unsigned)((n + kRows - 1) / kRows);
+    kern<<<blocks, kThreads, smem, st>>>(Q, n, K, V, M, D, c, F, F_dtype, mask, cfg, acc, A_out, Fh, row, stats);
+    LAT_CHECK_LAUNCH("dec_rows_fwd");
+    return LATENTAM_OK;
+}
+
+template <int DQ>
+latentam_status launch_rows_bwd(const float* dFh, const float* A, const float* row, const float* K, const float* V,
+                                int64_t n, int M, int D, float c, float* dS, float* dQ, cudaStream_t st) {
+    const size_t smem = rows_bwd_smem(M);
+    auto kern = dec_rows_bwd<DQ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "dec_rows_bwd smem attribute");
+    const unsigned blocks = (unsigned)((n + kRows - 1) / kRows);
+    kern<<<blocks, kThreads, smem, st>>>(dFh, A, row, K, V, n, M, D, c, dS, dQ);
+    LAT_CHECK_LAUNCH("dec_rows_bwd");
+    return LATENTAM_OK;
+}
+
+// C (nx x ny) = scale * X^T Y (+ trust-region term), split over pixels.
+latentam_status atb(latentam_ctx* ctx, const float* X, int ldx, int nx, const float* Y, int ldy, int ny, int64_t n,
+                    float scale, const float* coef, const float* V, const float* V0, float* out, cudaStream_t st) {
+    const int vec = ny >= 128 ? 4 : 1;
+    const int ct = 32 * vec;
+    const int bx = (nx + 63) / 64, by = (ny + ct - 1) / ct;
+    const int target = 2 * ctx->num_sms;
+    int64_t splits = std::max<int64_t>(1, (target + bx * by - 1) / (bx * by));
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, (n + 255) / 256));
+    const int64_t rps = ((n + splits - 1) / splits + 31) / 32 * 32;
+    splits = std::max<int64_t>(1, (n + rps - 1) / rps);
+    float* part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * (size_t)splits * nx * ny));
+    if (!part) return LATENTAM_ERR_OUT_OF_MEMORY;
+    dim3 grid((unsigned)bx, (unsigned)by, (unsigned)splits);
+    if (vec == 4)
+        atb_splitk<4><<<grid, kThreads, 0, st>>>(X, ldx, nx, Y, ldy, ny, n, rps, part);
+    else
+        atb_splitk<1><<<grid, kThreads, 0, st>>>(X, ldx, nx, Y, ldy, ny, n, rps, part);
+    LAT_CHECK_LAUNCH("atb_splitk");
+    const int64_t total = (int64_t)nx * ny;
+    reduce_splits<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, (int)splits, nx, ny, scale, coef, V, V0, out);
+    LAT_CHECK_LAUNCH("reduce_splits");
+    return LATENTAM_OK;
+}
+
+template <int DQ>
+latentam_status loss_bwd_t(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
+    const int64_t n = a.n;
+    const int M = a.M, D = a.D;
+    double* acc = static_cast<double*>(ws(ctx, WS_LOSS, sizeof(double) * 8));
+    float* A = static_cast<float*>(ws(ctx, WS_DEC_A, sizeof(float) * (size_t)std::max<int64_t>(n, 1) * M));
+    float* dF = static_cast<float*>(ws(ctx, WS_DEC_DF, sizeof(float) * (size_t)std::max<int64_t>(n, 1) * D));
+    float* dS = static_cast<float*>(ws(ctx, WS_DEC_DS, sizeof(float) * (size_t)std::max<int64_t>(n, 1) * M));
+    float* row = static_cast<float*>(ws(ctx, WS_DEC_ROW, sizeof(float) * 4 * (size_t)std::max<int64_t>(n, 1)));
+    float* coef = static_cast<float*>(ws(ctx, WS_DEC_AUX3, sizeof(float) * (size_t)M));
+    if (!acc || !A || !dF || !dS || !row || !coef) return LATENTAM_ERR_OUT_OF_MEMORY;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 8, st);
+    if (e != cudaSuccess) return cuda_error(e, "memset loss");
+    if (n > 0) {
+        const unsigned cb = (unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 4 * ctx->num_sms);
+        count_mask_kernel<<<cb, kThreads, 0, st>>>(a.mask, n, acc);
+        LAT_CHECK_LAUNCH("count_mask_kernel");
+    }
+    trust_region_kernel<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(a.V, a.V0, M, D, a.cfg.delta,
+                                                                 a.cfg.lambda_f * a.cfg.lambda_D, coef, acc);
+    LAT_CHECK_LAUNCH("trust_region_kernel");
+    if (n > 0) {
+        LAT_TRY((launch_rows_fwd<DQ, true>(a.Q, n, a.K, a.V, M, D, a.c, a.F, a.F_dtype, a.mask, a.cfg, acc, A, dF, row,
+                                           nullptr, st)));
+        if (a.dQ || a.dK)
+            LAT_TRY(launch_rows_bwd<DQ>(dF, A, row, a.K, a.V, n, M, D, a.c, dS, a.dQ, st));
+    }
+    if (a.dV) LAT_TRY(atb(ctx, A, M, M, dF, D, D, n, 1.0f, coef, a.V, a.V0, a.dV, st));
+    if (a.dK) LAT_TRY(atb(ctx, dS, M, M, a.Q, DQ, DQ, n, a.c, nullptr, nullptr, nullptr, a.dK, st));
+    finalize_loss<<<1, 1, 0, st>>>(acc, D, a.cfg, a.loss_parts);
+    LAT_CHECK_LAUNCH("finalize_loss");
+    return LATENTAM_OK;
+}
+
+template <int DQ>
+latentam_status decode_fwd_t(latentam_ctx* ctx, const float* Q, int64_t n, const float* K, const float* V, int M,
+                             int D, float c, float* F_hat, float* row_stats, cudaStream_t st) {
+    if (n == 0) return LATENTAM_OK;
+    float* Fh = F_hat;
+    if (!Fh) {
+        Fh = static_cast<float*>(ws(ctx, WS_DEC_DF, sizeof(float) * (size_t)n * D));
+        if (!Fh) return LATENTAM_ERR_OUT_OF_MEMORY;
+    }
+    latentam_loss_cfg cfg{};
+    return launch_rows_fwd<DQ, false>(Q, n, K, V, M, D, c, nullptr, LATENTAM_DTYPE_F32, nullptr, cfg, nullptr, nullptr,
+                                      Fh, nullptr, row_stats, st);
+}
+
+}  // namespace
+
+latentam_status decode_loss_bwd_f32(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
+    switch (a.d) {
+        case 16: return loss_bwd_t<16>(ctx, a, st);
+        case 32: return loss_bwd_t<32>(ctx, a, st);
+        case 64: return loss_bwd_t<64>(ctx, a, st);
+        default: set_error("query dimension d=%d not in {16, 32, 64}", a.d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+}
+
+latentam_status decode_fwd_f32(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V,
+                               int M, int D, float c, float* F_hat, float* row_stats, cudaStream_t st) {
+    switch (d) {
+        case 16: return decode_fwd_t<16>(ctx, Q, n, K, V, M, D, c, F_hat, row_stats, st);
+        case 32: return decode_fwd_t<32>(ctx, Q, n, K, V, M, D, c, F_hat, row_stats, st);
+        case 64: return decode_fwd_t<64>(ctx, Q, n, K, V, M, D, c, F_hat, row_stats, st);
+        default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+}
+
+}  // namespace lat

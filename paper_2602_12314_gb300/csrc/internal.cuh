@@ -1,0 +1,194 @@
+// Internal declarations of the sm_103a implementation behind include/latentam.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "latentam.h"
+
+namespace lat {
+
+// Constants of the splat footprint (readings listed in latentam.h).
+constexpr int kTile = LATENTAM_TILE;
+constexpr int kTilePixels = kTile * kTile;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kDilation = 0.3f;
+
+struct CamParams {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy, z_near;
+    int W, H, tiles_x, tiles_y;
+};
+
+inline CamParams cam_params(const latentam_camera& c) {
+    CamParams p;
+    for (int i = 0; i < 9; ++i) p.R[i] = c.R[i];
+    for (int i = 0; i < 3; ++i) p.t[i] = c.t[i];
+    p.fx = c.fx;
+    p.fy = c.fy;
+    p.cx = c.cx;
+    p.cy = c.cy;
+    p.z_near = c.z_near;
+    p.W = c.width;
+    p.H = c.height;
+    p.tiles_x = (c.width + kTile - 1) / kTile;
+    p.tiles_y = (c.height + kTile - 1) / kTile;
+    return p;
+}
+
+// Workspace slots owned by the context.
+enum Slot : int {
+    WS_SORT_K0 = 0,
+    WS_SORT_K1,
+    WS_SORT_V0,
+    WS_SORT_V1,
+    WS_SORT_HIST,
+    WS_SCAN_SUMS,
+    WS_OFFSETS,
+    WS_COUNTERS,
+    WS_DEC_A,      // n x M attention (FP32 form) / bf16 copies (tensor form)
+    WS_DEC_DF,     // n x D Fhat, then dFhat
+    WS_DEC_DS,     // n x M softmax-input gradient
+    WS_DEC_ROW,    // n x 4 per-pixel coefficients
+    WS_DEC_PART,   // split-K partial sums of dK / dV
+    WS_DEC_AUX,    // transposed / converted operands of the tensor-core path
+    WS_DEC_AUX2,
+    WS_DEC_AUX3,
+    WS_LOSS,       // double accumulators
+    WS_STEP_PROJ,  // latentam_step's own projection, bins, images and gradients
+    WS_STEP_PAIRS,
+    WS_STEP_IMG,
+    WS_STEP_GRAD,
+    WS_NUM_SLOTS
+};
+
+}  // namespace lat
+
+namespace lat {
+constexpr int kProfPairs = 256;  // event pairs per stage before folding
+struct StageProfile {
+    cudaEvent_t ev[2 * kProfPairs];
+    int created;
+    int used;
+    double acc_ms;
+    int64_t count;
+};
+}  // namespace lat
+
+struct latentam_ctx {
+    int device;
+    int num_sms;
+    int cc_major, cc_minor;
+    void* slot_ptr[lat::WS_NUM_SLOTS];
+    size_t slot_bytes[lat::WS_NUM_SLOTS];
+    int profiling;
+    lat::StageProfile prof[LATENTAM_NUM_STAGES];
+};
+
+namespace lat {
+
+// Error reporting (thread-local message, see latentam_last_error).
+void set_error(const char* fmt, ...);
+latentam_status cuda_error(cudaError_t e, const char* what);
+
+// Workspace slot of at least `bytes` bytes (grows by synchronising the device and
+// reallocating; contents are not preserved).  Returns NULL and sets the error on failure.
+void* ws(latentam_ctx* ctx, Slot s, size_t bytes);
+
+// Stage timer: records an event pair on `st` around its scope when profiling is enabled.
+int prof_begin(latentam_ctx* ctx, int stage, cudaStream_t st);
+void prof_end(latentam_ctx* ctx, int stage, int idx, cudaStream_t st);
+struct StageTimer {
+    latentam_ctx* ctx;
+    int stage;
+    cudaStream_t st;
+    int idx;
+    StageTimer(latentam_ctx* c, int s, cudaStream_t stream) : ctx(c), stage(s), st(stream), idx(-1) {
+        if (c && c->profiling) idx = prof_begin(c, s, stream);
+    }
+    ~StageTimer() {
+        if (idx >= 0) prof_end(ctx, stage, idx, st);
+    }
+};
+
+// Called after every kernel launch: counts it and turns a launch error into a status.
+void count_launch();
+#define LAT_CHECK_LAUNCH(what)                                          \
+    do {                                                                \
+        ::lat::count_launch();                                          \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return ::lat::cuda_error(e_, what);      \
+    } while (0)
+
+#define LAT_TRY(expr)                                 \
+    do {                                              \
+        latentam_status s_ = (expr);                  \
+        if (s_ != LATENTAM_OK) return s_;             \
+    } while (0)
+
+// ---- launchers (each .cu file implements its own) ----------------------------------
+
+latentam_status launch_project(const latentam_gaussians& g, const CamParams& cam,
+                               const latentam_projected& out, cudaStream_t st);
+
+// Exclusive scan of n uint32 values; *total_dev (device, nullable) receives the sum.
+latentam_status scan_exclusive_u32(latentam_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
+                                   uint32_t* total_dev, cudaStream_t st);
+// Stable LSD radix sort of n (key, value) pairs on key bits [0, bits).  keys[0]/vals[0]
+// hold the input (vals_iota: value = index, vals[0] is then only scratch); keys[1]/vals[1]
+// are scratch.  *result receives the index of the buffer pair holding the sorted output.
+latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uint32_t* const vals[2], bool vals_iota,
+                                 int64_t n, int bits, int* result, cudaStream_t st);
+latentam_status bin_and_sort(latentam_ctx* ctx, int32_t n, const latentam_projected& proj,
+                             const CamParams& cam, latentam_bins* bins, cudaStream_t st);
+
+latentam_status launch_render_fwd(const CamParams& cam, const latentam_projected& proj,
+                                  const latentam_bins& bins, const float* f, int d, float* Q,
+                                  float* T_final, int32_t* n_contrib, cudaStream_t st);
+latentam_status launch_render_bwd(const CamParams& cam, const latentam_projected& proj,
+                                  const latentam_bins& bins, const int32_t* n_contrib,
+                                  const float* dQ, int d, float* df, int32_t n, cudaStream_t st);
+
+struct DecodeArgs {
+    const float* Q;
+    int64_t n;
+    int d;
+    const float* K;
+    const float* V;
+    const float* V0;
+    int M, D;
+    float c;                 // logit scale
+    const void* F;
+    latentam_dtype F_dtype;
+    const uint8_t* mask;
+    latentam_loss_cfg cfg;
+    double* loss_parts;
+    float* dQ;
+    float* dK;
+    float* dV;
+};
+
+latentam_status decode_fwd_f32(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K,
+                               const float* V, int M, int D, float c, float* F_hat, float* row_stats,
+                               cudaStream_t st);
+latentam_status decode_loss_bwd_f32(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st);
+latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st);
+latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K,
+                                const float* V, int M, int D, float c, float* F_hat, float* row_stats,
+                                cudaStream_t st);
+
+struct AdamTensor {
+    float* p;
+    const float* g;
+    float* m;
+    float* v;
+    int64_t n;
+    float lr;
+};
+latentam_status launch_adam(latentam_ctx* ctx, const AdamTensor* t, int count, float beta1, float beta2,
+                            float eps, int step, cudaStream_t st);
+
+}  // namespace lat

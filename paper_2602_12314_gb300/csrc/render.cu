@@ -1,0 +1,239 @@
+// Query rendering Q = R_f(G, T) (Sec. III-B, Eq. render_query): the depth-ordered alpha
+// blending of Eq. (alpha_blending) applied to the d-dimensional query vectors f_i, and its
+// backward with respect to f.
+//
+// One CTA per 16x16 tile, one thread per pixel.  The tile's Gaussians are staged through
+// shared memory in batches of 256 (mean, conic/opacity, query as float4 rows), so every
+// query row is read from L2/HBM once per tile and broadcast to the 256 pixels.
+#include "internal.cuh"
+
+namespace lat {
+namespace {
+
+constexpr int kBatch = kTilePixels;  // 256 Gaussians staged per round
+
+// alpha of a splat at a pixel centre, or -1 when the exponent is positive.  Every rounding
+// is explicit (no contraction), so the forward and backward kernels take bit-identical
+// decisions for the same inputs.
+__device__ __forceinline__ float splat_alpha(float2 m, float4 co, float px, float py) {
+    const float dx = __fsub_rn(m.x, px), dy = __fsub_rn(m.y, py);
+    const float quad = __fadd_rn(__fmul_rn(__fmul_rn(co.x, dx), dx), __fmul_rn(__fmul_rn(co.z, dy), dy));
+    const float power = __fsub_rn(__fmul_rn(-0.5f, quad), __fmul_rn(__fmul_rn(co.y, dx), dy));
+    if (power > 0.0f) return -1.0f;
+    return fminf(kAlphaMax, __fmul_rn(co.w, __expf(power)));
+}
+
+template <int DQ>
+__global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, const int2* __restrict__ ranges,
+                                                                 const int32_t* __restrict__ pair_ids,
+                                                                 const float2* __restrict__ xy,
+                                                                 const float4* __restrict__ conic_opac,
+                                                                 const float4* __restrict__ f, float4* __restrict__ Q,
+                                                                 float* __restrict__ T_final,
+                                                                 int32_t* __restrict__ n_contrib) {
+    constexpr int DV = DQ / 4;
+    __shared__ float2 s_xy[kBatch];
+    __shared__ float4 s_co[kBatch];
+    __shared__ float4 s_f[kBatch][DV];
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int t = threadIdx.x;
+    const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
+    const bool inside = px < cam.W && py < cam.H;
+    const float fpx = (float)px, fpy = (float)py;
+    const int2 range = ranges[tile];
+    float4 acc[DV];
+#pragma unroll
+    for (int k = 0; k < DV; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float T = 1.0f;
+    int count = 0;
+    bool done = !inside;
+    for (int start = range.x; start < range.y; start += kBatch) {
+        if (__syncthreads_count(done) == kTilePixels) break;
+        const int k = start + t;
+        if (k < range.y) {
+            const int g = pair_ids[k];
+            s_xy[t] = xy[g];
+            s_co[t] = conic_opac[g];
+#pragma unroll
+            for (int c = 0; c < DV; ++c) s_f[t][c] = f[(size_t)g * DV + c];
+        }
+        __syncthreads();
+        const int cnt = min(kBatch, range.y - start);
+        for (int j = 0; j < cnt && !done; ++j) {
+            const float alpha = splat_alpha(s_xy[j], s_co[j], fpx, fpy);
+            if (alpha < kAlphaMin) continue;
+            const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+            if (test_T < kTMin) {
+                done = true;
+                break;
+            }
+            const float w = __fmul_rn(alpha, T);
+#pragma unroll
+            for (int c = 0; c < DV; ++c) {
+                const float4 v = s_f[j][c];
+                acc[c].x += w * v.x;
+                acc[c].y += w * v.y;
+                acc[c].z += w * v.z;
+                acc[c].w += w * v.w;
+            }
+            T = test_T;
+            ++count;
+        }
+    }
+    if (inside) {
+        const size_t p = (size_t)py * cam.W + px;
+#pragma unroll
+        for (int c = 0; c < DV; ++c) Q[p * DV + c] = acc[c];
+        T_final[p] = T;
+        n_contrib[p] = count;
+    }
+}
+
+// Reduce-scatter of 32 per-lane channels over the warp: lane l ends with the warp-wide
+// sum of channel l (31 shuffles instead of 32 x 5).
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    return v[0];
+}
+
+template <int DQ>
+__global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, const int2* __restrict__ ranges,
+                                                                 const int32_t* __restrict__ pair_ids,
+                                                                 const float2* __restrict__ xy,
+                                                                 const float4* __restrict__ conic_opac,
+                                                                 const int32_t* __restrict__ n_contrib,
+                                                                 const float4* __restrict__ dQ, float* __restrict__ df) {
+    constexpr int DV = DQ / 4;
+    constexpr int NG = DQ / 32 > 0 ? DQ / 32 : 1;  // 32-channel groups
+    __shared__ float2 s_xy[kBatch];
+    __shared__ float4 s_co[kBatch];
+    __shared__ int s_id[kBatch];
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int t = threadIdx.x, lane = t & 31;
+    const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
+    const bool inside = px < cam.W && py < cam.H;
+    const float fpx = (float)px, fpy = (float)py;
+    const int2 range = ranges[tile];
+    float g[DQ];
+    int remaining = 0;
+    if (inside) {
+        const size_t p = (size_t)py * cam.W + px;
+#pragma unroll
+        for (int c = 0; c < DV; ++c) {
+            const float4 v = dQ[p * DV + c];
+            g[4 * c] = v.x;
+            g[4 * c + 1] = v.y;
+            g[4 * c + 2] = v.z;
+            g[4 * c + 3] = v.w;
+        }
+        remaining = n_contrib[p];
+    } else {
+#pragma unroll
+        for (int c = 0; c < DQ; ++c) g[c] = 0.f;
+    }
+    float T = 1.0f;
+    bool done = remaining == 0;
+    for (int start = range.x; start < range.y; start += kBatch) {
+        if (__syncthreads_count(done) == kTilePixels) break;
+        const int k = start + t;
+        if (k < range.y) {
+            const int gid = pair_ids[k];
+            s_xy[t] = xy[gid];
+            s_co[t] = conic_opac[gid];
+            s_id[t] = gid;
+        }
+        __syncthreads();
+        const int cnt = min(kBatch, range.y - start);
+        for (int j = 0; j < cnt; ++j) {
+            // identical arithmetic to the forward pass, so the same contributions are taken
+            float w = 0.0f;
+            if (!done) {
+                const float alpha = splat_alpha(s_xy[j], s_co[j], fpx, fpy);
+                if (alpha >= kAlphaMin) {
+                    w = __fmul_rn(alpha, T);
+                    T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+                    if (--remaining == 0) done = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, w != 0.0f)) {
+                const int gid = s_id[j];
+#pragma unroll
+                for (int grp = 0; grp < NG; ++grp) {
+                    float v[32];
+                    if (DQ >= 32) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) v[c] = w * g[grp * 32 + c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) v[c] = c < DQ ? w * g[c] : 0.0f;
+                    }
+                    // lane l now holds channel l summed over the warp (channels >= DQ are zero)
+                    const float s = warp_reduce_scatter32(v, lane);
+                    if (lane < (DQ < 32 ? DQ : 32)) atomicAdd(&df[(size_t)gid * DQ + grp * 32 + lane], s);
+                }
+            }
+        }
+    }
+}
+
+template <int DQ>
+latentam_status render_fwd_t(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
+                             const float* f, float* Q, float* T_final, int32_t* n_contrib, cudaStream_t st) {
+    const int tiles = cam.tiles_x * cam.tiles_y;
+    render_fwd_kernel<DQ><<<tiles, kTilePixels, 0, st>>>(
+        cam, reinterpret_cast<const int2*>(bins.tile_ranges), bins.pair_ids, reinterpret_cast<const float2*>(proj.xy),
+        reinterpret_cast<const float4*>(proj.conic_opacity), reinterpret_cast<const float4*>(f),
+        reinterpret_cast<float4*>(Q), T_final, n_contrib);
+    LAT_CHECK_LAUNCH("render_fwd_kernel");
+    return LATENTAM_OK;
+}
+
+template <int DQ>
+latentam_status render_bwd_t(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
+                             const int32_t* n_contrib, const float* dQ, float* df, int32_t n, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(df, 0, sizeof(float) * (size_t)n * DQ, st);
+    if (e != cudaSuccess) return cuda_error(e, "memset df");
+    const int tiles = cam.tiles_x * cam.tiles_y;
+    render_bwd_kernel<DQ><<<tiles, kTilePixels, 0, st>>>(
+        cam, reinterpret_cast<const int2*>(bins.tile_ranges), bins.pair_ids, reinterpret_cast<const float2*>(proj.xy),
+        reinterpret_cast<const float4*>(proj.conic_opacity), n_contrib, reinterpret_cast<const float4*>(dQ), df);
+    LAT_CHECK_LAUNCH("render_bwd_kernel");
+    return LATENTAM_OK;
+}
+
+}  // namespace
+
+latentam_status launch_render_fwd(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
+                                  const float* f, int d, float* Q, float* T_final, int32_t* n_contrib,
+                                  cudaStream_t st) {
+    switch (d) {
+        case 16: return render_fwd_t<16>(cam, proj, bins, f, Q, T_final, n_contrib, st);
+        case 32: return render_fwd_t<32>(cam, proj, bins, f, Q, T_final, n_contrib, st);
+        case 64: return render_fwd_t<64>(cam, proj, bins, f, Q, T_final, n_contrib, st);
+        default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+}
+
+latentam_status launch_render_bwd(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
+                                  const int32_t* n_contrib, const float* dQ, int d, float* df, int32_t n,
+                                  cudaStream_t st) {
+    switch (d) {
+        case 16: return render_bwd_t<16>(cam, proj, bins, n_contrib, dQ, df, n, st);
+        case 32: return render_bwd_t<32>(cam, proj, bins, n_contrib, dQ, df, n, st);
+        case 64: return render_bwd_t<64>(cam, proj, bins, n_contrib, dQ, df, n, st);
+        default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+}
+
+}  // namespace lat

@@ -1,0 +1,342 @@
+// Tile binning and sorting of the splats (the depth-ordered lists that Eq. alpha_blending
+// walks, Sec. III-A):
+//   1. stable LSD radix sort of the Gaussians by binary32 depth key (ties keep index order)
+//   2. exclusive scan of tiles-touched in that order -> pair offsets and the pair count P
+//   3. emission of one (tile, Gaussian) pair per covered tile, in depth order
+//   4. stable radix sort of the pairs on the ceil(log2(tiles)) tile bits only
+//   5. per-tile [start, end) ranges
+// Sorting depth first and then only the few tile bits replaces a 64-bit (tile|depth)
+// sort of all pairs: 4 passes over N Gaussians plus 1-2 passes over P pairs.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace lat {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 4096
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive scan of one 4096-item tile per block; block totals to sums[blockIdx].
+__global__ void __launch_bounds__(kScanThreads) scan_tiles(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                           uint32_t* __restrict__ sums, int64_t n) {
+    __shared__ uint32_t warp_tot[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)t * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        tsum += v[k];
+    }
+    const uint32_t incl = warp_incl_scan(tsum, lane);
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_tot[lane];
+        uint32_t wi = warp_incl_scan(w, lane);
+        warp_tot[lane] = wi - w;
+        if (lane == 31 && sums) sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[warp] + incl - tsum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+// In-place exclusive scan of up to 4096 block sums by a single block; total to *total.
+__global__ void __launch_bounds__(kScanThreads) scan_sums(uint32_t* __restrict__ sums, int n, uint32_t* __restrict__ total) {
+    __shared__ uint32_t warp_tot[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t v[kScanItems];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = t * kScanItems + k;
+        v[k] = i < n ? sums[i] : 0u;
+        tsum += v[k];
+    }
+    const uint32_t incl = warp_incl_scan(tsum, lane);
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_tot[lane];
+        uint32_t wi = warp_incl_scan(w, lane);
+        warp_tot[lane] = wi - w;
+        if (lane == 31 && total) *total = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[warp] + incl - tsum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = t * kScanItems + k;
+        if (i < n) sums[i] = run;
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_add(uint32_t* __restrict__ out, const uint32_t* __restrict__ sums, int64_t n) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    const uint32_t add = sums[blockIdx.x];
+    for (int k = threadIdx.x; k < kScanTile; k += kScanThreads)
+        if (base + k < n) out[base + k] += add;
+}
+
+// ---- radix sort ---------------------------------------------------------------------
+
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 2048; warp w owns items [256 w, 256 w + 256)
+constexpr int kRadix = 256;
+
+__global__ void __launch_bounds__(kRsThreads) radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                         uint32_t mask, uint32_t* __restrict__ hist, int nblocks) {
+    __shared__ uint32_t h[kRadix];
+    const int t = threadIdx.x;
+    h[t] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll
+    for (int k = 0; k < kRsItems; ++k) {
+        const int64_t i = base + k * kRsThreads + t;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)t * nblocks + blockIdx.x] = h[t];
+}
+
+__global__ void __launch_bounds__(kRsThreads) radix_scatter(const uint32_t* __restrict__ keys_in,
+                                                            const uint32_t* __restrict__ vals_in,
+                                                            uint32_t* __restrict__ keys_out,
+                                                            uint32_t* __restrict__ vals_out, int64_t n, int shift,
+                                                            uint32_t mask, const uint32_t* __restrict__ hist_scanned,
+                                                            int nblocks) {
+    __shared__ uint32_t s_off[kRadix];
+    __shared__ uint32_t s_cnt[kRsThreads / 32][kRadix];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    s_off[t] = hist_scanned[(int64_t)t * nblocks + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kRsThreads / 32; ++w) s_cnt[w][t] = 0;
+    __syncthreads();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t kk[kRsItems], vv[kRsItems], dd[kRsItems], rr[kRsItems];
+    const int64_t base = (int64_t)blockIdx.x * kRsTile + warp * (32 * kRsItems);
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+        const int64_t i = base + it * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t key = valid ? keys_in[i] : 0u;
+        const uint32_t val = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
+        const uint32_t dig = valid ? ((key >> shift) & mask) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+        const uint32_t rank = __popc(peers & lt_mask);
+        const uint32_t before = valid ? s_cnt[warp][dig] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) s_cnt[warp][dig] = before + __popc(peers);
+        __syncwarp();
+        kk[it] = key;
+        vv[it] = val;
+        dd[it] = dig;
+        rr[it] = before + rank;
+    }
+    __syncthreads();
+    {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kRsThreads / 32; ++w) {
+            const uint32_t c = s_cnt[w][t];
+            s_cnt[w][t] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+        const int64_t i = base + it * 32 + lane;
+        if (i < n) {
+            const uint32_t pos = s_off[dd[it]] + s_cnt[warp][dd[it]] + rr[it];
+            keys_out[pos] = kk[it];
+            vals_out[pos] = vv[it];
+        }
+    }
+}
+
+// ---- binning ---------------------------------------------------------------------------
+
+__global__ void depth_keys(int N, const float* __restrict__ depth, const int32_t* __restrict__ tiles,
+                           uint32_t* __restrict__ keys) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    // visible Gaussians have depth > z_near > 0, whose binary32 bits order like the values
+    keys[i] = tiles[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
+}
+
+__global__ void gather_tiles(int N, const uint32_t* __restrict__ order, const int32_t* __restrict__ tiles,
+                             uint32_t* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) out[k] = (uint32_t)tiles[order[k]];
+}
+
+__global__ void emit_pairs(int N, const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
+                           const int4* __restrict__ rect, int tiles_x, uint32_t* __restrict__ pair_tile,
+                           uint32_t* __restrict__ pair_gauss) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const uint32_t g = order[k];
+    const int4 r = rect[g];
+    uint32_t o = offsets[k];
+    for (int ty = r.y; ty < r.w; ++ty)
+        for (int tx = r.x; tx < r.z; ++tx) {
+            pair_tile[o] = (uint32_t)(ty * tiles_x + tx);
+            pair_gauss[o] = g;
+            ++o;
+        }
+}
+
+__global__ void tile_ranges(const uint32_t* __restrict__ keys, int64_t P, int2* __restrict__ ranges) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = (int)i;
+    if (i == P - 1 || keys[i + 1] != t) ranges[t].y = (int)(i + 1);
+}
+
+int ceil_log2(int64_t v) {
+    int b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+}  // namespace
+
+latentam_status scan_exclusive_u32(latentam_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
+                                   uint32_t* total_dev, cudaStream_t st) {
+    if (n <= 0) {
+        if (total_dev) {
+            cudaError_t e = cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), st);
+            if (e != cudaSuccess) return cuda_error(e, "scan memset");
+        }
+        return LATENTAM_OK;
+    }
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > kScanTile) {
+        set_error("scan of %lld items exceeds the supported %lld", (long long)n, (long long)kScanTile * kScanTile);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    uint32_t* sums = static_cast<uint32_t*>(ws(ctx, WS_SCAN_SUMS, sizeof(uint32_t) * (size_t)(nb + 1)));
+    if (!sums) return LATENTAM_ERR_OUT_OF_MEMORY;
+    scan_tiles<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, sums, n);
+    LAT_CHECK_LAUNCH("scan_tiles");
+    scan_sums<<<1, kScanThreads, 0, st>>>(sums, (int)nb, total_dev);
+    LAT_CHECK_LAUNCH("scan_sums");
+    if (nb > 1) {
+        scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, sums, n);
+        LAT_CHECK_LAUNCH("scan_add");
+    }
+    return LATENTAM_OK;
+}
+
+latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uint32_t* const vals[2], bool vals_iota,
+                                 int64_t n, int bits, int* result, cudaStream_t st) {
+    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    *result = passes % 2;
+    if (n <= 0) return LATENTAM_OK;
+    const int64_t nb = (n + kRsTile - 1) / kRsTile;
+    const int64_t hist_n = nb * kRadix;
+    uint32_t* hist = static_cast<uint32_t*>(ws(ctx, WS_SORT_HIST, sizeof(uint32_t) * (size_t)hist_n));
+    if (!hist) return LATENTAM_ERR_OUT_OF_MEMORY;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        const int pb = std::min(8, std::max(bits - shift, 1));
+        const uint32_t mask = (1u << pb) - 1u;
+        const int src = p % 2, dst = 1 - src;
+        const uint32_t* vin = (p == 0 && vals_iota) ? nullptr : vals[src];
+        radix_hist<<<(unsigned)nb, kRsThreads, 0, st>>>(keys[src], n, shift, mask, hist, (int)nb);
+        LAT_CHECK_LAUNCH("radix_hist");
+        LAT_TRY(scan_exclusive_u32(ctx, hist, hist, hist_n, nullptr, st));
+        radix_scatter<<<(unsigned)nb, kRsThreads, 0, st>>>(keys[src], vin, keys[dst], vals[dst], n, shift, mask, hist,
+                                                          (int)nb);
+        LAT_CHECK_LAUNCH("radix_scatter");
+    }
+    return LATENTAM_OK;
+}
+
+latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projected& proj,
+                             const CamParams& cam, latentam_bins* bins, cudaStream_t st) {
+    const int64_t num_tiles = (int64_t)cam.tiles_x * cam.tiles_y;
+    cudaError_t e = cudaMemsetAsync(bins->tile_ranges, 0, sizeof(int2) * (size_t)num_tiles, st);
+    if (e != cudaSuccess) return cuda_error(e, "memset tile_ranges");
+    if (N == 0) {
+        bins->num_pairs = 0;
+        return LATENTAM_OK;
+    }
+    const size_t nbytes = sizeof(uint32_t) * (size_t)N;
+    uint32_t* dk[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_K0, nbytes)),
+                       static_cast<uint32_t*>(ws(ctx, WS_SORT_K1, nbytes))};
+    uint32_t* dv[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_V0, nbytes)),
+                       static_cast<uint32_t*>(ws(ctx, WS_SORT_V1, nbytes))};
+    uint32_t* off = static_cast<uint32_t*>(ws(ctx, WS_OFFSETS, sizeof(uint32_t) * ((size_t)N + 1)));
+    uint32_t* cnt = static_cast<uint32_t*>(ws(ctx, WS_COUNTERS, 64));
+    if (!dk[0] || !dk[1] || !dv[0] || !dv[1] || !off || !cnt) return LATENTAM_ERR_OUT_OF_MEMORY;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((N + threads - 1) / threads);
+    // 1. Gaussians by depth key (index order kept among equal keys)
+    depth_keys<<<blocks, threads, 0, st>>>(N, proj.depth, proj.tiles_touched, dk[0]);
+    LAT_CHECK_LAUNCH("depth_keys");
+    int r = 0;
+    LAT_TRY(radix_sort_pairs(ctx, dk, dv, true, N, 32, &r, st));
+    const uint32_t* order = dv[r];
+    // 2. pair offsets in depth order
+    uint32_t* counts = dk[1 - r];
+    gather_tiles<<<blocks, threads, 0, st>>>(N, order, proj.tiles_touched, counts);
+    LAT_CHECK_LAUNCH("gather_tiles");
+    LAT_TRY(scan_exclusive_u32(ctx, counts, off, N, cnt, st));
+    uint32_t P32 = 0;
+    e = cudaMemcpyAsync(&P32, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_error(e, "read pair count");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "sync for pair count");
+    const int64_t P = (int64_t)P32;
+    bins->num_pairs = P;
+    if (P > bins->capacity) {
+        set_error("pair buffer holds %lld pairs, %lld needed", (long long)bins->capacity, (long long)P);
+        return LATENTAM_ERR_CAPACITY;
+    }
+    if (P == 0) return LATENTAM_OK;
+    // 3. emission in depth order; 4. stable sort on the tile bits.  The depth order stays in
+    // its own slot (WS_SORT_V*), the key slots may be regrown: their contents are consumed.
+    const size_t pbytes = sizeof(uint32_t) * (size_t)P;
+    uint32_t* pk[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_K0, std::max(pbytes, nbytes))),
+                       static_cast<uint32_t*>(ws(ctx, WS_SORT_K1, std::max(pbytes, nbytes)))};
+    uint32_t* pv[2] = {static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX, pbytes)),
+                       static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX2, pbytes))};
+    if (!pk[0] || !pk[1] || !pv[0] || !pv[1]) return LATENTAM_ERR_OUT_OF_MEMORY;
+    order = static_cast<const uint32_t*>(ctx->slot_ptr[r == 0 ? WS_SORT_V0 : WS_SORT_V1]);
+    emit_pairs<<<blocks, threads, 0, st>>>(N, order, off, reinterpret_cast<const int4*>(proj.rect), cam.tiles_x,
+                                           pk[0], pv[0]);
+    LAT_CHECK_LAUNCH("emit_pairs");
+    const int tile_bits = std::max(1, ceil_log2(num_tiles));
+    LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, st));
+    e = cudaMemcpyAsync(bins->pair_ids, pv[r], pbytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "copy pair ids");
+    // 5. ranges
+    tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(pk[r], P, reinterpret_cast<int2*>(bins->tile_ranges));
+    LAT_CHECK_LAUNCH("tile_ranges");
+    return LATENTAM_OK;
+}
+
+}  // namespace lat

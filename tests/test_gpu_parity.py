@@ -1,0 +1,387 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP32 form): relative error <= 1e-4 on rendered queries and decoded features,
+<= 1e-3 on gradients, bit-exact on integer/index outputs.  Pixels that the oracle flags as
+ambiguous (a candidate within a relative 5e-5 of alpha = 1/255 or within 1e-3 of the
+T = 1e-4 stop, where a float32 evaluation may legitimately decide the other way) are
+compared only for validity; they must stay rare.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import random_scene, room_scene, tiny_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_Q = 1e-4
+REL_G = 1e-3
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2602_12314_gb300 import api as _api
+    return _api
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _scenes():
+    return {
+        "tiny": tiny_scene(0),
+        "ragged": random_scene(11, n=3000, d=32, M=96, D=256, width=72, height=50, log_scale=-2.8, mask_drop=0.15),
+        "room_crop": room_scene(1, n=300_000).crop(272, 208, 96, 64),
+        "d64": random_scene(12, n=1500, d=64, M=64, D=384, width=40, height=33, log_scale=-2.6),
+    }
+
+
+SCENES = _scenes()
+
+
+def _dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def _gpu_front(api, ctx, s):
+    proj = api.project(ctx, s.means, s.quats, s.scales, s.opacities, s.camera)
+    bins = api.sort(ctx, proj, s.camera)
+    return proj, bins
+
+
+def _rel_rows(a, b, floor):
+    num = np.linalg.norm(a - b, axis=1)
+    den = np.maximum(np.linalg.norm(b, axis=1), floor)
+    return num / den
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_project_matches_oracle(api, ctx, name):
+    s = SCENES[name]
+    proj, _ = _gpu_front(api, ctx, s)
+    o = oracle.project_scene(s)
+    vis = o["visible"].astype(bool)
+    depth = proj.depth.cpu().numpy()
+    # the depth key is evaluated with the same double-precision operations: bit-exact
+    np.testing.assert_array_equal(depth, o["depth"].astype(np.float32))
+    rect = proj.rect.cpu().numpy()
+    ok = ~o["rect_ambiguous"].astype(bool)
+    np.testing.assert_array_equal(rect[ok], o["rect"][ok])
+    tt = proj.tiles_touched.cpu().numpy()
+    np.testing.assert_array_equal(tt[ok], ((o["rect"][:, 2] - o["rect"][:, 0]) * (o["rect"][:, 3] - o["rect"][:, 1]))[ok])
+    xy = proj.xy.cpu().numpy()
+    np.testing.assert_allclose(xy[vis], o["xy"][vis], rtol=1e-5, atol=1e-3)
+    co = proj.conic_opacity.cpu().numpy()
+    np.testing.assert_allclose(co[vis, :3], o["conic"][vis], rtol=2e-4, atol=1e-6)
+    np.testing.assert_array_equal(co[vis, 3], s.opacities[vis])
+    assert (tt[~vis] == 0).all()
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_sort_matches_oracle_tile_lists(api, ctx, name):
+    s = SCENES[name]
+    proj, bins = _gpu_front(api, ctx, s)
+    o = oracle.project_scene(s)
+    off, ids = oracle.tile_lists(o, s.camera)
+    amb = set(np.nonzero(o["rect_ambiguous"])[0].tolist())
+    pairs = bins.pair_ids[:bins.num_pairs].cpu().numpy()
+    ranges = bins.tile_ranges.cpu().numpy()
+    assert ranges.shape[0] == len(off) - 1
+    for t in range(len(off) - 1):
+        want = [g for g in ids[off[t]:off[t + 1]].tolist() if g not in amb]
+        got = [g for g in pairs[ranges[t, 0]:ranges[t, 1]].tolist() if g not in amb]
+        assert got == want, f"tile {t}"
+    if not amb:
+        assert bins.num_pairs == len(ids)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_render_fwd_matches_oracle(api, ctx, name):
+    s = SCENES[name]
+    proj, bins = _gpu_front(api, ctx, s)
+    Q, T, nc = api.render_fwd(ctx, proj, s.camera, bins, _dev(s.f))
+    o = oracle.project_scene(s)
+    Qo, To, nco, amb = oracle.render_frame(o, s.f, s.camera)
+    assert amb.mean() < 0.02
+    ok = ~amb
+    Qg = Q.cpu().numpy().astype(np.float64)
+    rel = _rel_rows(Qg[ok], Qo[ok], floor=1e-3 * np.sqrt(s.d))
+    assert rel.max() <= REL_Q, rel.max()
+    np.testing.assert_array_equal(nc.cpu().numpy()[ok], nco[ok])
+    np.testing.assert_allclose(T.cpu().numpy()[ok], To[ok], rtol=1e-3, atol=1e-7)
+    # ambiguous pixels: still a valid blend (transmittance in range, bounded contribution count)
+    Tg = T.cpu().numpy()
+    assert (Tg >= 1e-4).all() and (Tg <= 1.0).all()
+    assert (np.abs(nc.cpu().numpy()[amb] - nco[amb]) <= 1).all()
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_render_bwd_matches_oracle(api, ctx, name):
+    s = SCENES[name]
+    proj, bins = _gpu_front(api, ctx, s)
+    _, _, nc = api.render_fwd(ctx, proj, s.camera, bins, _dev(s.f))
+    o = oracle.project_scene(s)
+    _, _, _, amb = oracle.render_frame(o, s.f, s.camera)
+    rng = np.random.default_rng(5)
+    dQ = rng.normal(size=(s.camera.n_pixels, s.d))
+    dQ[amb] = 0.0  # the blend weights of ambiguous pixels are not unique
+    df = api.render_bwd(ctx, proj, s.camera, bins, nc, _dev(dQ)).cpu().numpy().astype(np.float64)
+    dfo = oracle.render_frame_bwd(o, dQ, s.camera, s.n, s.d)
+    err = np.linalg.norm(df - dfo) / np.linalg.norm(dfo)
+    assert err <= REL_G, err
+    rows = np.abs(dfo).sum(1) > 0
+    rel = _rel_rows(df[rows], dfo[rows], floor=1e-3 * np.abs(dfo).max())
+    assert rel.max() <= 5 * REL_G, rel.max()
+    assert np.all(df[~rows] == 0.0)
+
+
+def _oracle_Q(s):
+    o = oracle.project_scene(s)
+    Qo, _, _, amb = oracle.render_frame(o, s.f, s.camera)
+    return Qo, amb
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_decode_fwd_matches_oracle(api, ctx, name):
+    s = SCENES[name]
+    Qo, _ = _oracle_Q(s)
+    Q32 = Qo.astype(np.float32)
+    c = 1.0 / np.sqrt(s.d)
+    Fh, stats = api.decode_fwd(ctx, _dev(Q32), _dev(s.K), _dev(s.V), c, api.FP32)
+    S, A, Fo = oracle.decode(Q32, s.K, s.V, c)
+    rel = _rel_rows(Fh.cpu().numpy().astype(np.float64), Fo, floor=1e-6)
+    assert rel.max() <= REL_Q, rel.max()
+    st = stats.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(st[:, 0], S.max(1), rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(st[:, 1], np.exp(S - S.max(1, keepdims=True)).sum(1), rtol=1e-5)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_decode_loss_bwd_matches_oracle(api, ctx, name):
+    s = SCENES[name]
+    Qo, _ = _oracle_Q(s)
+    Q32 = Qo.astype(np.float32)
+    rng = np.random.default_rng(3)
+    # trust-region centres: half the atoms outside the radius
+    V0 = (s.V + (rng.normal(size=s.V.shape) * 0.05 * (np.arange(s.M) % 2)[:, None])).astype(np.float32)
+    cfg = oracle.LossConfig()
+    out = oracle.decode(Q32, s.K, s.V, cfg.c(s.d))
+    parts_o, _ = oracle.loss(out[2], s.F, s.mask, s.V, V0, cfg, s.d)
+    dQo, dKo, dVo = oracle.backward(Q32, s.K, s.V, V0, out[1], out[2], s.F, s.mask, cfg)
+    parts, dQ, dK, dV = api.decode_loss_bwd(ctx, _dev(Q32), _dev(s.K), _dev(s.V), _dev(V0), _dev(s.F),
+                                            _dev(s.mask, torch.uint8), api.LossConfig(), api.FP32)
+    p = parts.cpu().numpy()
+    assert p[4] == parts_o["n_valid"]
+    np.testing.assert_allclose(p[:4], [parts_o["cos"], parts_o["l2"], parts_o["tr"], parts_o["total"]], rtol=1e-5,
+                               atol=1e-9)
+    for name_, g, go in (("dQ", dQ, dQo), ("dK", dK, dKo), ("dV", dV, dVo)):
+        g = g.cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(g - go) / np.linalg.norm(go)
+        assert err <= REL_G, (name_, err)
+        rel = _rel_rows(g, go, floor=1e-2 * np.abs(go).max())
+        assert rel.max() <= 5 * REL_G, (name_, rel.max())
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged", "room_crop"])
+def test_full_backward_chain_matches_oracle(api, ctx, name):
+    """Render -> decode -> loss -> gradients on the GPU's own render (latentam_backward)."""
+    s = SCENES[name]
+    proj, bins = _gpu_front(api, ctx, s)
+    Q, _, nc = api.render_fwd(ctx, proj, s.camera, bins, _dev(s.f))
+    parts, df, dK, dV, _ = api.backward(ctx, proj, s.camera, bins, nc, Q, _dev(s.K), _dev(s.V), _dev(s.V0), _dev(s.F),
+                                        _dev(s.mask, torch.uint8), api.LossConfig(), api.FP32)
+    o = oracle.iteration(s, oracle.LossConfig())
+    np.testing.assert_allclose(parts.cpu().numpy()[3], o["loss"]["total"], rtol=1e-4)
+    for name_, g, go in (("df", df, o["df"]), ("dK", dK, o["dK"]), ("dV", dV, o["dV"])):
+        g = g.cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(g - go) / np.linalg.norm(go)
+        assert err <= REL_G, (name_, err)
+
+
+def test_autograd_matches_c_abi(api, ctx):
+    from paper_2602_12314_gb300 import autograd
+    s = SCENES["ragged"]
+    proj, bins = _gpu_front(api, ctx, s)
+    f = _dev(s.f).requires_grad_(True)
+    K = _dev(s.K).requires_grad_(True)
+    V = _dev(s.V).requires_grad_(True)
+    loss = autograd.latent_loss(f, K, V, ctx, proj, s.camera, bins, _dev(s.V0), _dev(s.F), _dev(s.mask, torch.uint8))
+    (2.0 * loss).backward()
+    Q, _, nc = api.render_fwd(ctx, proj, s.camera, bins, _dev(s.f))
+    parts, df, dK, dV, _ = api.backward(ctx, proj, s.camera, bins, nc, Q, _dev(s.K), _dev(s.V), _dev(s.V0), _dev(s.F),
+                                        _dev(s.mask, torch.uint8))
+    assert float(loss) == pytest.approx(float(parts[3]), rel=1e-6)
+    torch.testing.assert_close(f.grad, 2 * df, rtol=1e-5, atol=1e-8)
+    torch.testing.assert_close(K.grad, 2 * dK, rtol=1e-5, atol=1e-8)
+    torch.testing.assert_close(V.grad, 2 * dV, rtol=1e-5, atol=1e-8)
+
+
+def test_adam_matches_oracle(api, ctx):
+    rng = np.random.default_rng(9)
+    shapes = [(1000, 32), (256, 32), (256, 512)]
+    ps = [rng.normal(size=sh) for sh in shapes]
+    cfg = api.AdamConfig(step=1)
+    dev_p = [_dev(p) for p in ps]
+    ms = [torch.zeros_like(p) for p in dev_p]
+    vs = [torch.zeros_like(p) for p in dev_p]
+    op = [p.astype(np.float32).astype(np.float64) for p in ps]
+    om = [np.zeros(sh) for sh in shapes]
+    ov = [np.zeros(sh) for sh in shapes]
+    lrs = [0.003, 0.01, 0.01]
+    for step in range(1, 4):
+        gs = [rng.normal(size=sh).astype(np.float32) for sh in shapes]
+        cfg.step = step
+        api.adam(ctx, dev_p, [_dev(g) for g in gs], ms, vs, lrs, cfg)
+        for k in range(3):
+            oracle.adam(op[k].reshape(-1), gs[k].astype(np.float64).reshape(-1), om[k].reshape(-1),
+                        ov[k].reshape(-1), step, lrs[k])
+    for k in range(3):
+        np.testing.assert_allclose(dev_p[k].cpu().numpy(), op[k], rtol=1e-5, atol=1e-6)
+
+
+def test_step_one_iteration_matches_oracle(api, ctx):
+    """latentam_step (one Stage-I iteration): loss before the update, then Adam on f, K, V."""
+    s = SCENES["tiny"]
+    st = api.LatentStep(ctx, s, precision=api.FP32)
+    loss = st.step(iters=1, learn_f=True)
+    o = oracle.iteration(s, oracle.LossConfig())
+    assert loss["total"] == pytest.approx(o["loss"]["total"], rel=1e-4)
+    lr = 0.01
+    for name_, dev_t, x0, g in (("f", st.f, s.f, o["df"]), ("K", st.K, s.K, o["dK"]), ("V", st.V, s.V, o["dV"])):
+        x = x0.astype(np.float64).copy()
+        m, v = np.zeros_like(x), np.zeros_like(x)
+        oracle.adam(x.reshape(-1), g.reshape(-1), m.reshape(-1), v.reshape(-1), 1, lr)
+        got = dev_t.cpu().numpy().astype(np.float64)
+        # the first Adam step is -lr g/(|g| + eps): compare where the gradient's sign is well determined
+        well = np.abs(g) > 1e-2 * np.abs(g).max()
+        np.testing.assert_allclose(got[well], x[well], rtol=0, atol=1e-4 * lr + 1e-6, err_msg=name_)
+        assert np.all(np.abs(got - x0) <= lr * 1.0001 + 1e-6), name_
+
+
+def test_stage2_leaves_queries_untouched(api, ctx):
+    s = SCENES["ragged"]
+    st = api.LatentStep(ctx, s, precision=api.FP32)
+    f0 = st.f.clone()
+    l1 = st.step(iters=3, learn_f=False)
+    assert torch.equal(st.f, f0)
+    assert st.adam_cfg.step == 4
+    assert np.isfinite(l1["total"])
+
+
+# ---- edge cases ------------------------------------------------------------------------
+
+def test_empty_and_culled_scenes(api, ctx):
+    s = random_scene(3, n=50, d=16, M=32, D=128, width=20, height=17)
+    s.means[:, 2] = -10.0  # every Gaussian behind the camera
+    proj, bins = _gpu_front(api, ctx, s)
+    assert bins.num_pairs == 0
+    Q, T, nc = api.render_fwd(ctx, proj, s.camera, bins, _dev(s.f))
+    assert float(Q.abs().max()) == 0.0 and bool((T == 1).all()) and int(nc.max()) == 0
+    df = api.render_bwd(ctx, proj, s.camera, bins, nc, torch.ones_like(Q))
+    assert float(df.abs().max()) == 0.0
+    s0 = random_scene(3, n=0, d=16, M=32, D=128, width=5, height=3)
+    proj0, bins0 = _gpu_front(api, ctx, s0)
+    Q0, T0, _ = api.render_fwd(ctx, proj0, s0.camera, bins0, torch.zeros((0, 16), device="cuda"))
+    assert bins0.num_pairs == 0 and bool((T0 == 1).all())
+
+
+def test_single_pixel_and_all_masked(api, ctx):
+    s = random_scene(4, n=200, d=32, M=32, D=128, width=1, height=1, spread=0.05)
+    proj, bins = _gpu_front(api, ctx, s)
+    Q, T, nc = api.render_fwd(ctx, proj, s.camera, bins, _dev(s.f))
+    o = oracle.project_scene(s)
+    Qo, To, nco, amb = oracle.render_frame(o, s.f, s.camera)
+    if not amb[0]:
+        assert _rel_rows(Q.cpu().numpy().astype(np.float64), Qo, 1e-3).max() <= REL_Q
+    # no valid pixel: zero loss terms, only the trust-region gradient remains
+    mask = np.zeros(1, np.uint8)
+    V0 = s.V.copy()
+    V0[0] += 1.0
+    parts, dQ, dK, dV = api.decode_loss_bwd(ctx, Q, _dev(s.K), _dev(s.V), _dev(V0), _dev(s.F), _dev(mask, torch.uint8))
+    p = parts.cpu().numpy()
+    assert p[4] == 0 and p[0] == 0 and p[1] == 0
+    assert float(dQ.abs().max()) == 0.0 and float(dK.abs().max()) == 0.0
+    tr = np.zeros_like(s.V, dtype=np.float64)
+    delta = s.V[0] - V0[0]
+    tr[0] = 5.0 * 0.2 * delta / np.linalg.norm(delta)
+    np.testing.assert_allclose(dV.cpu().numpy(), tr, atol=1e-6)
+
+
+def test_unsupported_shapes_fail_loudly(api, ctx):
+    from paper_2602_12314_gb300 import _lib as L
+    Q = torch.zeros((10, 24), device="cuda")
+    with pytest.raises(L.LatentamError) as e:
+        api.decode_fwd(ctx, Q, torch.zeros((32, 24), device="cuda"), torch.zeros((32, 128), device="cuda"))
+    assert e.value.status == L.ERR_UNSUPPORTED_SHAPE
+    Q = torch.zeros((10, 32), device="cuda")
+    with pytest.raises(L.LatentamError) as e:
+        api.decode_fwd(ctx, Q, torch.zeros((33, 32), device="cuda"), torch.zeros((33, 128), device="cuda"))
+    assert e.value.status == L.ERR_UNSUPPORTED_SHAPE
+
+
+def test_max_dictionary_shape(api, ctx):
+    """Largest supported dictionary (M = 1024, D = 2048) on a small pixel set."""
+    rng = np.random.default_rng(0)
+    n, d, M, D = 70, 32, 1024, 2048
+    Q = rng.normal(size=(n, d)).astype(np.float32)
+    K = (rng.normal(size=(M, d)) / np.sqrt(d)).astype(np.float32)
+    V = (rng.normal(size=(M, D)) / np.sqrt(d)).astype(np.float32)
+    F = rng.normal(size=(n, D)).astype(np.float32)
+    mask = np.ones(n, np.uint8)
+    cfg = oracle.LossConfig()
+    _, A, Fo = oracle.decode(Q, K, V, cfg.c(d))
+    dQo, dKo, dVo = oracle.backward(Q, K, V, V, A, Fo, F, mask, cfg)
+    parts, dQ, dK, dV = api.decode_loss_bwd(ctx, _dev(Q), _dev(K), _dev(V), _dev(V), _dev(F), _dev(mask, torch.uint8))
+    for g, go in ((dQ, dQo), (dK, dKo), (dV, dVo)):
+        g = g.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(g - go) / np.linalg.norm(go) <= REL_G
+
+
+# ---- full size (the benchmark's workload and launch configuration) -----------------------
+
+@pytest.fixture(scope="module")
+def room():
+    return room_scene(0)
+
+
+def test_full_size_sampled_pixels(api, ctx, room):
+    """640x480, 300k Gaussians: the rendered queries and decoded features at 400 sampled
+    pixels against the oracle's brute-force evaluation of those pixels."""
+    s = room
+    proj, bins = _gpu_front(api, ctx, s)
+    Q, T, nc = api.render_fwd(ctx, proj, s.camera, bins, _dev(s.f))
+    Fh, _ = api.decode_fwd(ctx, Q, _dev(s.K), _dev(s.V), 1.0 / np.sqrt(s.d), api.FP32)
+    rng = np.random.default_rng(1)
+    idx = rng.choice(s.camera.n_pixels, size=400, replace=False)
+    px, py = idx % s.camera.width, idx // s.camera.width
+    o = oracle.project_scene(s)
+    Qo, To, nco, amb = oracle.render_pixels(o, s.f, px, py)
+    ok = ~amb
+    assert ok.mean() > 0.97
+    Qg = Q.cpu().numpy()[idx].astype(np.float64)
+    assert _rel_rows(Qg[ok], Qo[ok], 1e-3 * np.sqrt(s.d)).max() <= REL_Q
+    np.testing.assert_array_equal(nc.cpu().numpy()[idx][ok], nco[ok])
+    _, _, Fo = oracle.decode(Qo[ok].astype(np.float32), s.K, s.V, 1.0 / np.sqrt(s.d))
+    Fg = Fh.cpu().numpy()[idx][ok].astype(np.float64)
+    assert _rel_rows(Fg, Fo, 1e-6).max() <= REL_Q
+
+
+def test_full_size_gradients(api, ctx, room):
+    """640x480, 300k Gaussians, M = 256, D = 512: df, dK, dV of the whole frame against the
+    oracle's full-frame backward."""
+    s = room
+    proj, bins = _gpu_front(api, ctx, s)
+    Q, _, nc = api.render_fwd(ctx, proj, s.camera, bins, _dev(s.f))
+    parts, df, dK, dV, _ = api.backward(ctx, proj, s.camera, bins, nc, Q, _dev(s.K), _dev(s.V), _dev(s.V0), _dev(s.F),
+                                        _dev(s.mask, torch.uint8))
+    o = oracle.iteration(s, oracle.LossConfig())
+    assert float(parts[3]) == pytest.approx(o["loss"]["total"], rel=1e-4)
+    for name_, g, go in (("df", df, o["df"]), ("dK", dK, o["dK"]), ("dV", dV, o["dV"])):
+        g = g.cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(g - go) / np.linalg.norm(go)
+        assert err <= REL_G, (name_, err)
