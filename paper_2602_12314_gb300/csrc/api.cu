@@ -155,8 +155,10 @@ latentam_status check_dict(int M, int D) {
         }                                        \
     } while (0)
 
-latentam_status check_projected(const latentam_projected* p) {
-    REQUIRE(p && p->xy && p->conic_opacity && p->depth && p->rect && p->tiles_touched, "incomplete projection buffers");
+latentam_status check_projected(const latentam_projected* p, int64_t n) {
+    REQUIRE(p, "null projection");
+    if (n == 0) return LATENTAM_OK;  // empty sets may carry null buffers
+    REQUIRE(p->xy && p->conic_opacity && p->depth && p->rect && p->tiles_touched, "incomplete projection buffers");
     REQUIRE(aligned16(p->conic_opacity) && aligned16(p->rect) && (reinterpret_cast<uintptr_t>(p->xy) & 7u) == 0,
             "projection buffers must be 16-byte aligned");
     return LATENTAM_OK;
@@ -266,7 +268,7 @@ latentam_status latentam_project(latentam_ctx* ctx, const latentam_gaussians* g,
     LAT_TRY(enter(ctx));
     LAT_TRY(check_camera(cam));
     REQUIRE(g && g->n >= 0, "bad Gaussian set");
-    LAT_TRY(check_projected(out));
+    LAT_TRY(check_projected(out, g->n));
     if (g->n > 0) REQUIRE(g->means && g->quats && g->scales && g->opacities, "null Gaussian attribute");
     StageTimer tm(ctx, LATENTAM_STAGE_PROJECT, (cudaStream_t)stream);
     return launch_project(*g, cam_params(*cam), *out, (cudaStream_t)stream);
@@ -277,7 +279,7 @@ latentam_status latentam_sort(latentam_ctx* ctx, int32_t n, const latentam_proje
     LAT_TRY(enter(ctx));
     LAT_TRY(check_camera(cam));
     REQUIRE(n >= 0, "negative Gaussian count");
-    LAT_TRY(check_projected(proj));
+    LAT_TRY(check_projected(proj, n));
     LAT_TRY(check_bins(bins, false));
     StageTimer tm(ctx, LATENTAM_STAGE_SORT, (cudaStream_t)stream);
     return bin_and_sort(ctx, n, *proj, cam_params(*cam), bins, (cudaStream_t)stream);
@@ -289,7 +291,7 @@ latentam_status latentam_render_fwd(latentam_ctx* ctx, int32_t n, const latentam
     LAT_TRY(enter(ctx));
     LAT_TRY(check_camera(cam));
     LAT_TRY(check_d(d));
-    LAT_TRY(check_projected(proj));
+    LAT_TRY(check_projected(proj, n));
     LAT_TRY(check_bins(bins, true));
     REQUIRE(n >= 0 && (n == 0 || f), "bad queries");
     REQUIRE(Q && T_final && n_contrib, "null output");
@@ -304,7 +306,7 @@ latentam_status latentam_render_bwd(latentam_ctx* ctx, int32_t n, const latentam
     LAT_TRY(enter(ctx));
     LAT_TRY(check_camera(cam));
     LAT_TRY(check_d(d));
-    LAT_TRY(check_projected(proj));
+    LAT_TRY(check_projected(proj, n));
     LAT_TRY(check_bins(bins, true));
     REQUIRE(n >= 0 && n_contrib && dQ && (df || n == 0), "null argument");
     REQUIRE(aligned16(dQ), "dQ must be 16-byte aligned");
