@@ -484,7 +484,7 @@ latentam_status atb(latentam_ctx* ctx, const float* X, int ldx, int nx, const fl
     const int target = 2 * ctx->num_sms;
     int64_t splits = std::max<int64_t>(1, (target + bx * by - 1) / (bx * by));
     splits = std::min<int64_t>(splits, std::max<int64_t>(1, (n + 255) / 256));
-    const int64_t rps = ((n + splits - 1) / splits + 31) / 32 * 32;
+    const int64_t rps = std::max<int64_t>(32, ((n + splits - 1) / splits + 31) / 32 * 32);
     splits = std::max<int64_t>(1, (n + rps - 1) / rps);
     float* part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * (size_t)splits * nx * ny));
     if (!part) return LATENTAM_ERR_OUT_OF_MEMORY;
