@@ -225,6 +225,31 @@ LATENTAM_API latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const f
                                          double* loss_parts, float* dQ, float* dK, float* dV,
                                          latentam_stream stream);
 
+/* Allocation-free form of latentam_decode_loss_bwd (FP32 only).  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device memory while
+ * the step runs, e.g. a real-time mapping loop whose device memory is carved up once at
+ * start-up by another runtime's allocator, or a caller that cannot accept the device-wide
+ * synchronisation that cudaMalloc/cudaFree may imply.  It calls no allocation routine.
+ * Its scratch (attention, dFhat, dS, per-pixel coefficients, split-K partial sums, loss
+ * accumulators) lives in one static 16 MiB device array inside the library, held by every
+ * device that loads the library until the process exits.  A call whose scratch would not fit
+ * (about 4 n (2M + D) bytes plus, per split, 4 M (D + d) bytes) returns
+ * LATENTAM_ERR_UNSUPPORTED_SHAPE with the required size in latentam_last_error(); for
+ * example n <= 2048 rows fit at M = 256, D = 512, d = 32, which covers mask-pooled targets.
+ * The first call on a device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  All calls share the one array, which
+ * keeps the last call's contents (the loss accumulators are cleared at the start of each
+ * call): calls that overlap on the GPU (other streams or other host threads) race on it
+ * and must be serialised by the caller.  Arguments, layouts and the other errors are those
+ * of latentam_decode_loss_bwd. */
+LATENTAM_API latentam_status latentam_decode_loss_bwd_noalloc(latentam_ctx* ctx, const float* Q, int64_t n,
+                                                              int32_t d, const float* K, const float* V,
+                                                              const float* V0, int32_t M, int32_t D, const void* F,
+                                                              latentam_dtype F_dtype, const uint8_t* mask,
+                                                              const latentam_loss_cfg* cfg, double* loss_parts,
+                                                              float* dQ, float* dK, float* dV,
+                                                              latentam_stream stream);
+
 /* The whole backward of one keyframe: latentam_decode_loss_bwd on the rendered Q, then
  * latentam_render_bwd into df (skipped when df is NULL, as in Stage II where the
  * Gaussians are fixed).  dQ_scratch (H*W x d) receives the query-image gradient. */

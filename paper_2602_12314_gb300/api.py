@@ -279,6 +279,30 @@ def decode_loss_bwd(ctx: Context, Q, K, V, V0, F, mask=None, cfg: LossConfig | N
     return parts, dQ, dK, dV
 
 
+def decode_loss_bwd_noalloc(ctx: Context, Q, K, V, V0, F, mask=None, cfg: LossConfig | None = None,
+                            out=None):
+    """latentam_decode_loss_bwd_noalloc: FP32 decode + loss + backward whose scratch lives in
+    the library's static device array (no device allocation inside the call).  `out`
+    (optional) = preallocated (loss_parts, dQ, dK, dV) to write into."""
+    cfg = cfg or LossConfig()
+    Q, K, V, V0, F = (x.contiguous() for x in (Q, K, V, V0, F))
+    n, d = Q.shape
+    M, D = V.shape
+    if out is None:
+        dev = Q.device
+        out = (torch.empty((L.LOSS_PARTS,), dtype=torch.float64, device=dev),
+               torch.empty((n, d), dtype=torch.float32, device=dev),
+               torch.empty((M, d), dtype=torch.float32, device=dev),
+               torch.empty((M, D), dtype=torch.float32, device=dev))
+    parts, dQ, dK, dV = out
+    m = mask.contiguous().to(torch.uint8) if mask is not None else None
+    cs = cfg.struct()
+    L.check(_lib().latentam_decode_loss_bwd_noalloc(ctx.handle, _ptr(Q), n, d, _ptr(K), _ptr(V), _ptr(V0), M, D,
+                                                    _ptr(F), _target_dtype(F), _ptr(m), ctypes.byref(cs),
+                                                    _ptr(parts), _ptr(dQ), _ptr(dK), _ptr(dV), _stream()))
+    return parts, dQ, dK, dV
+
+
 def backward(ctx: Context, proj: Projection, camera, bins: TileBins, n_contrib, Q, K, V, V0, F, mask=None,
              cfg: LossConfig | None = None, precision: int = FP32, need_df: bool = True):
     """(loss_parts, df or None, dK, dV, dQ or None) of one keyframe."""

@@ -371,6 +371,40 @@ latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const float* Q, int6
     return LATENTAM_ERR_INVALID_ARG;
 }
 
+latentam_status latentam_decode_loss_bwd_noalloc(latentam_ctx* ctx, const float* Q, int64_t n, int32_t d,
+                                                 const float* K, const float* V, const float* V0, int32_t M, int32_t D,
+                                                 const void* F, latentam_dtype F_dtype, const uint8_t* mask,
+                                                 const latentam_loss_cfg* cfg, double* loss_parts, float* dQ,
+                                                 float* dK, float* dV, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_d(d));
+    LAT_TRY(check_dict(M, D));
+    REQUIRE(cfg && loss_parts, "null config or loss output");
+    REQUIRE(n >= 0 && (n == 0 || (Q && F)) && K && V && V0, "null argument");
+    REQUIRE(F_dtype == LATENTAM_DTYPE_F32 || F_dtype == LATENTAM_DTYPE_BF16, "unknown target dtype %d", F_dtype);
+    REQUIRE(aligned16(Q) && aligned16(V) && aligned16(V0) && aligned16(F) && aligned16(dQ) && aligned16(dV),
+            "Q, V, V0, F, dQ, dV must be 16-byte aligned");
+    DecodeArgs a;
+    a.Q = Q;
+    a.n = n;
+    a.d = d;
+    a.K = K;
+    a.V = V;
+    a.V0 = V0;
+    a.M = M;
+    a.D = D;
+    a.c = logit_scale(cfg, d);
+    a.F = F;
+    a.F_dtype = F_dtype;
+    a.mask = mask;
+    a.cfg = *cfg;
+    a.loss_parts = loss_parts;
+    a.dQ = dQ;
+    a.dK = dK;
+    a.dV = dV;
+    return decode_loss_bwd_f32_noalloc(ctx, a, (cudaStream_t)stream);
+}
+
 latentam_status latentam_backward(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
                                   const latentam_camera* cam, const latentam_bins* bins, const int32_t* n_contrib,
                                   const float* Q, int32_t d, const float* K, const float* V, const float* V0,

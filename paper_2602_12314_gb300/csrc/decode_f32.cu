@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -548,7 +549,153 @@ latentam_status decode_fwd_t(latentam_ctx* ctx, const float* Q, int64_t n, const
                                       Fh, nullptr, row_stats, st);
 }
 
+// ---- allocation-free variant -------------------------------------------------------------
+// Scratch of decode_loss_bwd_f32_noalloc: one file-scope device array, resident on every
+// device that loads the library until process exit.  Host code only ever sees a host-side
+// stand-in for the symbol; the device address comes from cudaGetSymbolAddress.
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+struct NoallocPlan {
+    size_t acc, A, dF, dS, row, coef, partV, partK, total;
+    int64_t splitsV, rpsV, splitsK, rpsK;
+};
+
+// Same split rule as atb(): about two CTAs per SM, at least 256 pixels per split.
+void plan_split(int num_sms, int nx, int ny, int64_t n, int64_t* splits_out, int64_t* rps_out) {
+    const int vec = ny >= 128 ? 4 : 1;
+    const int ct = 32 * vec;
+    const int bx = (nx + 63) / 64, by = (ny + ct - 1) / ct;
+    int64_t splits = std::max<int64_t>(1, (2 * num_sms + bx * by - 1) / (bx * by));
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, (n + 255) / 256));
+    const int64_t rps = std::max<int64_t>(32, ((n + splits - 1) / splits + 31) / 32 * 32);
+    *rps_out = rps;
+    *splits_out = std::max<int64_t>(1, (n + rps - 1) / rps);
+}
+
+NoallocPlan plan_noalloc(int num_sms, int64_t n, int M, int D, int d) {
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    NoallocPlan p{};
+    plan_split(num_sms, M, D, n, &p.splitsV, &p.rpsV);
+    plan_split(num_sms, M, d, n, &p.splitsK, &p.rpsK);
+    size_t o = 0;
+    p.acc = o;
+    o += up(sizeof(double) * 8);
+    p.A = o;
+    o += up(sizeof(float) * (size_t)n * M);
+    p.dF = o;
+    o += up(sizeof(float) * (size_t)n * D);
+    p.dS = o;
+    o += up(sizeof(float) * (size_t)n * M);
+    p.row = o;
+    o += up(sizeof(float) * 4 * (size_t)n);
+    p.coef = o;
+    o += up(sizeof(float) * (size_t)M);
+    p.partV = o;
+    o += up(sizeof(float) * (size_t)p.splitsV * M * D);
+    p.partK = o;
+    o += up(sizeof(float) * (size_t)p.splitsK * M * d);
+    p.total = o;
+    return p;
+}
+
+// Device address of the static scratch; looked up once per device (that device current).
+latentam_status noalloc_scratch(int device, unsigned char** out) {
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("device %d outside the %d devices the static scratch table covers", device, kMaxDevices);
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static decode scratch)");
+        g_noalloc_ptr[device] = ptr;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_ptr[device]);
+    return LATENTAM_OK;
+}
+
+latentam_status atb_noalloc(const float* X, int ldx, int nx, const float* Y, int ldy, int ny, int64_t n, float scale,
+                            const float* coef, const float* V, const float* V0, float* out, float* part,
+                            int64_t splits, int64_t rps, cudaStream_t st) {
+    const int vec = ny >= 128 ? 4 : 1;
+    const int ct = 32 * vec;
+    dim3 grid((unsigned)((nx + 63) / 64), (unsigned)((ny + ct - 1) / ct), (unsigned)splits);
+    if (vec == 4)
+        atb_splitk<4><<<grid, kThreads, 0, st>>>(X, ldx, nx, Y, ldy, ny, n, rps, part);
+    else
+        atb_splitk<1><<<grid, kThreads, 0, st>>>(X, ldx, nx, Y, ldy, ny, n, rps, part);
+    LAT_CHECK_LAUNCH("atb_splitk");
+    const int64_t total = (int64_t)nx * ny;
+    reduce_splits<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, (int)splits, nx, ny, scale, coef, V, V0, out);
+    LAT_CHECK_LAUNCH("reduce_splits");
+    return LATENTAM_OK;
+}
+
+template <int DQ>
+latentam_status loss_bwd_noalloc_t(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
+    const int64_t n = a.n;
+    const int M = a.M, D = a.D;
+    const NoallocPlan p = plan_noalloc(ctx->num_sms, n, M, D, DQ);
+    if (p.total > kStaticScratchBytes) {
+        set_error("allocation-free decode needs %zu bytes of scratch for n=%lld, M=%d, D=%d, d=%d; the static "
+                  "scratch holds %zu bytes (use fewer pixels per call)",
+                  p.total, (long long)n, M, D, DQ, kStaticScratchBytes);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    unsigned char* base = nullptr;
+    LAT_TRY(noalloc_scratch(ctx->device, &base));
+    double* acc = reinterpret_cast<double*>(base + p.acc);
+    float* A = reinterpret_cast<float*>(base + p.A);
+    float* dF = reinterpret_cast<float*>(base + p.dF);
+    float* dS = reinterpret_cast<float*>(base + p.dS);
+    float* row = reinterpret_cast<float*>(base + p.row);
+    float* coef = reinterpret_cast<float*>(base + p.coef);
+    // the accumulators keep the previous call's sums: clear them first
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 8, st);
+    if (e != cudaSuccess) return cuda_error(e, "memset static loss accumulators");
+    if (n > 0) {
+        const unsigned cb = (unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 4 * ctx->num_sms);
+        count_mask_kernel<<<cb, kThreads, 0, st>>>(a.mask, n, acc);
+        LAT_CHECK_LAUNCH("count_mask_kernel");
+    }
+    trust_region_kernel<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(a.V, a.V0, M, D, a.cfg.delta,
+                                                                 a.cfg.lambda_f * a.cfg.lambda_D, coef, acc);
+    LAT_CHECK_LAUNCH("trust_region_kernel");
+    if (n > 0) {
+        LAT_TRY((launch_rows_fwd<DQ, true>(a.Q, n, a.K, a.V, M, D, a.c, a.F, a.F_dtype, a.mask, a.cfg, acc, A, dF, row,
+                                           nullptr, st)));
+        if (a.dQ || a.dK)
+            LAT_TRY(launch_rows_bwd<DQ>(dF, A, row, a.K, a.V, n, M, D, a.c, dS, a.dQ, st));
+    }
+    if (a.dV)
+        LAT_TRY(atb_noalloc(A, M, M, dF, D, D, n, 1.0f, coef, a.V, a.V0, a.dV, reinterpret_cast<float*>(base + p.partV),
+                            p.splitsV, p.rpsV, st));
+    if (a.dK)
+        LAT_TRY(atb_noalloc(dS, M, M, a.Q, DQ, DQ, n, a.c, nullptr, nullptr, nullptr, a.dK,
+                            reinterpret_cast<float*>(base + p.partK), p.splitsK, p.rpsK, st));
+    finalize_loss<<<1, 1, 0, st>>>(acc, D, a.cfg, a.loss_parts);
+    LAT_CHECK_LAUNCH("finalize_loss");
+    return LATENTAM_OK;
+}
+
 }  // namespace
+
+latentam_status decode_loss_bwd_f32_noalloc(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
+    switch (a.d) {
+        case 16: return loss_bwd_noalloc_t<16>(ctx, a, st);
+        case 32: return loss_bwd_noalloc_t<32>(ctx, a, st);
+        case 64: return loss_bwd_noalloc_t<64>(ctx, a, st);
+        default: set_error("query dimension d=%d not in {16, 32, 64}", a.d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+}
+
+size_t decode_noalloc_scratch_bytes() { return kStaticScratchBytes; }
 
 latentam_status decode_loss_bwd_f32(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
     switch (a.d) {
