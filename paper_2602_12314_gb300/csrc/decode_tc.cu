@@ -1,17 +1,695 @@
-// Tensor-core (tcgen05) form of the dictionary decode: BF16 operands, FP32 accumulation.
-#include "internal.cuh"
+// Dictionary decode (Eq. dict_recon), feature objective (Eq. feat_loss, Eq. full_obj) and
+// its backward on the tcgen05 tensor cores: BF16 operands, FP32 accumulation in TMEM, FP32
+// softmax and loss arithmetic, FP64 frame sums.  Six contractions share tc_gemm_kernel:
+//
+//   G1  S = Q K^T            epilogue: row softmax (logit scale c) -> A, A^T (BF16), row stats
+//   G2  Fhat = A V           epilogue: cos / L2 against F, a_p, b_p -> dFhat, dFhat^T (BF16)
+//   G3  dA = dFhat V^T       epilogue: dS = A (dA - <A, dA>) -> dS, dS^T (BF16)
+//   G4  dQ = c dS K          epilogue: FP32 dQ
+//   G5  dV = A^T dFhat       split over pixels -> FP32 partials -> sum + trust-region term
+//   G6  dK = c dS^T Q        split over pixels -> FP32 partials -> sum
+//
+// Every operand is K-major (the epilogues write the transposed copies the pixel-reduction
+// contractions need), so all tiles are plain 128-byte-swizzled TMA boxes.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "tc_gemm.cuh"
 
 namespace lat {
+namespace {
 
-latentam_status decode_loss_bwd_bf16(latentam_ctx*, const DecodeArgs&, cudaStream_t) {
-    set_error("BF16 decode not available in this build");
-    return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+using tc::kTileM;
+using bf16 = __nv_bfloat16;
+
+constexpr int kPad = 64;  // query / key rows padded to one 64-wide K chunk
+
+// ---- operand preparation ----------------------------------------------------------------
+
+// Qb[p][0..63] = bf16(Q[p][0..d)) zero-padded; Qt[k][p] = bf16(Q[p][k]).
+__global__ void prep_queries(const float* __restrict__ Q, int64_t n, int d, bf16* __restrict__ Qb,
+                             bf16* __restrict__ Qt, int64_t ldt) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t w[kPad / 2];
+#pragma unroll
+    for (int k = 0; k < kPad; k += 2) {
+        const float a = k < d ? Q[p * d + k] : 0.f;
+        const float b = k + 1 < d ? Q[p * d + k + 1] : 0.f;
+        w[k / 2] = tc::pack_bf16x2(a, b);
+        if (k < d) Qt[(int64_t)k * ldt + p] = __float2bfloat16_rn(a);
+        if (k + 1 < d) Qt[(int64_t)(k + 1) * ldt + p] = __float2bfloat16_rn(b);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(Qb + p * kPad);
+#pragma unroll
+    for (int v = 0; v < kPad / 8; ++v) dst[v] = make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
 }
 
-latentam_status decode_fwd_bf16(latentam_ctx*, const float*, int64_t, int, const float*, const float*, int, int, float,
-                                float*, float*, cudaStream_t) {
-    set_error("BF16 decode not available in this build");
-    return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+// Kb[j][0..63] (zero-padded), Kt[k][j], Vb[j][c], Vt[c][j]: BF16 copies of the dictionary.
+__global__ void prep_dict(const float* __restrict__ K, const float* __restrict__ V, int M, int d, int D,
+                          bf16* __restrict__ Kb, bf16* __restrict__ Kt, bf16* __restrict__ Vb, bf16* __restrict__ Vt) {
+    const int64_t total = (int64_t)M * D + (int64_t)M * kPad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < (int64_t)M * D) {
+            const int j = (int)(e / D), c = (int)(e % D);
+            const bf16 v = __float2bfloat16_rn(V[e]);
+            Vb[e] = v;
+            Vt[(int64_t)c * M + j] = v;
+        } else {
+            const int64_t f = e - (int64_t)M * D;
+            const int j = (int)(f / kPad), k = (int)(f % kPad);
+            const float v = k < d ? K[(int64_t)j * d + k] : 0.f;
+            Kb[f] = __float2bfloat16_rn(v);
+            if (k < d) Kt[(int64_t)k * M + j] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// Accumulators: [0] sum (1 - cos) over valid pixels, [1] sum of squared errors, [2] trust
+// region, [3] |Omega|; int at acc + 8: device error flag of the tensor-core kernels.
+__global__ void tc_count_mask(const uint8_t* __restrict__ mask, int64_t n, double* __restrict__ acc) {
+    __shared__ int s[8];
+    int c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += mask ? (mask[i] != 0) : 1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+        atomicAdd(&acc[3], (double)t);
+    }
+}
+
+// Trust region on the value rows (FP32 values): coef[j] = lambda_f lambda_D / |V_j - V0_j|
+// outside the radius, else 0; the ReLU sum goes to acc[2].
+__global__ void tc_trust_region(const float* __restrict__ V, const float* __restrict__ V0, int M, int D, float delta,
+                                float weight, float* __restrict__ coef, double* __restrict__ acc) {
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= M) return;
+    float s = 0.f;
+    for (int k = lane; k < D; k += 32) {
+        const float t = V[(size_t)j * D + k] - V0[(size_t)j * D + k];
+        s += t * t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const float nrm = sqrtf(s);
+        const bool out = nrm > delta;
+        coef[j] = out ? weight / nrm : 0.f;
+        if (out) atomicAdd(&acc[2], (double)(nrm - delta));
+    }
+}
+
+// out[j][k] = scale * sum_z part[z][j][k] (+ coef[j] (V - V0)[j][k]) for k < ncols (of ld columns)
+__global__ void tc_reduce_parts(const float* __restrict__ part, int splits, int rows, int ld, int ncols, float scale,
+                                const float* __restrict__ coef, const float* __restrict__ V,
+                                const float* __restrict__ V0, float* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rows * ncols) return;
+    const int j = (int)(e / ncols), k = (int)(e % ncols);
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[((int64_t)z * rows + j) * ld + k];
+    s *= scale;
+    if (coef) s += coef[j] * (V[e] - V0[e]);
+    out[e] = s;
+}
+
+__global__ void tc_finalize(const double* __restrict__ acc, const int* __restrict__ err, int D, latentam_loss_cfg cfg,
+                            double* __restrict__ parts) {
+    const double nv = acc[3];
+    const double lcos = nv > 0 ? acc[0] / nv : 0.0;
+    const double l2 = nv > 0 ? acc[1] / (nv * D) : 0.0;
+    parts[0] = lcos;
+    parts[1] = l2;
+    parts[2] = acc[2];
+    parts[3] = (double)cfg.lambda_f *
+               ((double)cfg.lambda_cos * lcos + (double)cfg.lambda_2 * l2 + (double)cfg.lambda_D * acc[2]);
+    parts[4] = nv;
+    if (*err) parts[3] = __longlong_as_double(0x7ff8000000000000ll);  // a device wait gave up: NaN loss
+}
+
+// ---- epilogues ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void store_row_bf16x32(bf16* dst, const float (&v)[32]) {
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        d4[q] = make_uint4(tc::pack_bf16x2(v[8 * q], v[8 * q + 1]), tc::pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
+                           tc::pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), tc::pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
+}
+
+__device__ __forceinline__ void load_row_bf16x32(const bf16* src, float (&v)[32]) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 u = s4[q];
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[h]));
+            v[8 * q + 2 * h] = f.x;
+            v[8 * q + 2 * h + 1] = f.y;
+        }
+    }
+}
+
+__device__ __forceinline__ void load_target32(const void* F, latentam_dtype dt, int64_t off, float (&v)[32]) {
+    if (dt == LATENTAM_DTYPE_BF16) {
+        load_row_bf16x32(reinterpret_cast<const bf16*>(F) + off, v);
+    } else {
+        const float4* s4 = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(F) + off);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 f = s4[q];
+            v[4 * q] = f.x;
+            v[4 * q + 1] = f.y;
+            v[4 * q + 2] = f.z;
+            v[4 * q + 3] = f.w;
+        }
+    }
+}
+
+// G1: row softmax of c S over the M atoms.
+struct SoftmaxParams {
+    int64_t n, ldt;
+    int M;
+    float c;
+    bf16* A;       // n x M
+    bf16* At;      // M x ldt
+    float* stats;  // n x 2 (row max of c S, softmax denominator), nullable
+};
+
+template <int BN_>
+struct SoftmaxEpi {
+    static constexpr int BN = BN_, STAGES = 1, BOX_B = BN_ <= 256 ? BN_ : 256;
+    using Params = SoftmaxParams;
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
+        const int64_t pix = (int64_t)m0 + row;
+        const bool valid = pix < p.n;
+        float v[32];
+        float mx = -INFINITY;
+        for (int c0 = 0; c0 < p.M; c0 += 32) {
+            tc::tmem_ld32(taddr + c0, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) mx = fmaxf(mx, v[i]);
+        }
+        const float cm = p.c * mx;
+        float sum = 0.f;
+        for (int c0 = 0; c0 < p.M; c0 += 32) {
+            tc::tmem_ld32(taddr + c0, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sum += __expf(p.c * v[i] - cm);
+        }
+        const float il = 1.0f / sum;
+        for (int c0 = 0; c0 < p.M; c0 += 32) {
+            tc::tmem_ld32(taddr + c0, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = __expf(p.c * v[i] - cm) * il;
+            if (valid) {
+                store_row_bf16x32(p.A + pix * p.M + c0, v);
+                if (p.At)
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) p.At[(int64_t)(c0 + i) * p.ldt + pix] = __float2bfloat16_rn(v[i]);
+            }
+        }
+        if (valid && p.stats) {
+            p.stats[2 * pix] = cm;
+            p.stats[2 * pix + 1] = sum;
+        }
+    }
+};
+
+// G2: Fhat = A V, the per-pixel loss terms and dL/dFhat = a_p Fhat + b_p F.
+struct FhatParams {
+    int64_t n, ldt;
+    int D;
+    const void* F;
+    latentam_dtype F_dtype;
+    const uint8_t* mask;
+    latentam_loss_cfg cfg;
+    double* acc;
+    bf16* dF;     // n x D
+    bf16* dFt;    // D x ldt
+    float* row;   // n x 4: a_p, b_p, <A_p, dA_p>, cos_p
+    float* Fout;  // n x D FP32 Fhat (inference form: no loss) or NULL
+};
+
+template <int BN_>
+struct FhatEpi {
+    static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_;
+    using Params = FhatParams;
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
+        const int64_t pix = (int64_t)m0 + row;
+        const bool valid = pix < p.n;
+        float h[32], f[32];
+        if (p.Fout) {
+            for (int c0 = 0; c0 < p.D; c0 += 32) {
+                tc::tmem_ld32(taddr + c0, h);
+                if (valid) {
+                    float4* d4 = reinterpret_cast<float4*>(p.Fout + pix * p.D + c0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) d4[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+                }
+            }
+            return;
+        }
+        float dot = 0.f, nh2 = 0.f, nf2 = 0.f, e2 = 0.f;
+        for (int c0 = 0; c0 < p.D; c0 += 32) {
+            tc::tmem_ld32(taddr + c0, h);
+            if (valid) {
+                load_target32(p.F, p.F_dtype, pix * p.D + c0, f);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    dot += h[i] * f[i];
+                    nh2 += h[i] * h[i];
+                    nf2 += f[i] * f[i];
+                    const float e = h[i] - f[i];
+                    e2 += e * e;
+                }
+            }
+        }
+        const bool in_loss = valid && (p.mask == nullptr || p.mask[pix] != 0);
+        const double nv = p.acc[3];
+        const float scale = nv > 0.0 ? (float)((double)p.cfg.lambda_f / nv) : 0.f;
+        const float den = sqrtf(nh2) * sqrtf(nf2);
+        const float cs = dot / fmaxf(den, 1e-8f);
+        float a = 0.f, b = 0.f;
+        if (in_loss) {
+            const float l2c = 2.0f * p.cfg.lambda_2 / (float)p.D;
+            if (den > 1e-8f) {
+                a = scale * (p.cfg.lambda_cos * cs / nh2 + l2c);
+                b = scale * (-p.cfg.lambda_cos / den - l2c);
+            } else {
+                a = scale * l2c;
+                b = scale * (-p.cfg.lambda_cos / 1e-8f - l2c);
+            }
+        }
+        if (valid) {
+            p.row[4 * pix] = a;
+            p.row[4 * pix + 1] = b;
+            p.row[4 * pix + 2] = a * nh2 + b * dot;
+            p.row[4 * pix + 3] = cs;
+        }
+        double lc = in_loss ? 1.0 - (double)cs : 0.0, le = in_loss ? (double)e2 : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lc += __shfl_xor_sync(0xffffffffu, lc, o);
+            le += __shfl_xor_sync(0xffffffffu, le, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&p.acc[0], lc);
+            atomicAdd(&p.acc[1], le);
+        }
+        for (int c0 = 0; c0 < p.D; c0 += 32) {
+            tc::tmem_ld32(taddr + c0, h);
+            if (valid) {
+                load_target32(p.F, p.F_dtype, pix * p.D + c0, f);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) h[i] = a * h[i] + b * f[i];
+                store_row_bf16x32(p.dF + pix * p.D + c0, h);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) p.dFt[(int64_t)(c0 + i) * p.ldt + pix] = __float2bfloat16_rn(h[i]);
+            }
+        }
+    }
+};
+
+// G3: dS = A (dA - <A, dA>).
+struct DsParams {
+    int64_t n, ldt;
+    int M;
+    const bf16* A;
+    const float* row;
+    bf16* dS;   // n x M
+    bf16* dSt;  // M x ldt
+};
+
+template <int BN_>
+struct DsEpi {
+    static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_;
+    using Params = DsParams;
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
+        const int64_t pix = (int64_t)m0 + row;
+        const bool valid = pix < p.n;
+        const float rd = valid ? p.row[4 * pix + 2] : 0.f;
+        float g[32], a[32];
+        for (int c0 = 0; c0 < p.M; c0 += 32) {
+            tc::tmem_ld32(taddr + c0, g);
+            if (valid) {
+                load_row_bf16x32(p.A + pix * p.M + c0, a);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) g[i] = a[i] * (g[i] - rd);
+                store_row_bf16x32(p.dS + pix * p.M + c0, g);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) p.dSt[(int64_t)(c0 + i) * p.ldt + pix] = __float2bfloat16_rn(g[i]);
+            }
+        }
+    }
+};
+
+// G4: dQ = c dS K (the first d of BN columns).
+struct DqParams {
+    int64_t n;
+    int d;
+    float c;
+    float* dQ;
+};
+
+template <int BN_>
+struct DqEpi {
+    static constexpr int BN = BN_, STAGES = 6, BOX_B = BN_;
+    using Params = DqParams;
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
+        const int64_t pix = (int64_t)m0 + row;
+        float v[32];
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            tc::tmem_ld32(taddr + c0, v);
+            if (pix < p.n)
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (c0 + i < p.d) p.dQ[pix * p.d + c0 + i] = p.c * v[i];
+        }
+    }
+};
+
+// G5 / G6: FP32 partial sums of one pixel split, part[z][row][col].
+struct PartParams {
+    int rows, ld, ncols;
+    float* part;
+};
+
+template <int BN_>
+struct PartEpi {
+    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_;
+    using Params = PartParams;
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int n0, int z) {
+        const int j = m0 + row;
+        float v[32];
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            tc::tmem_ld32(taddr + c0, v);
+            if (j < p.rows) {
+                float* dst = p.part + ((int64_t)z * p.rows + j) * p.ld + n0 + c0;
+                if (n0 + c0 + 32 <= p.ncols) {
+                    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (n0 + c0 + i < p.ncols) dst[i] = v[i];
+                }
+            }
+        }
+    }
+};
+
+// ---- host side ---------------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+std::once_flag g_encode_once;
+EncodeTiledFn g_encode = nullptr;
+
+latentam_status encoder(EncodeTiledFn* out) {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+        (void)cudaGetLastError();
+    });
+    if (!g_encode) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return LATENTAM_ERR_CUDA;
+    }
+    *out = g_encode;
+    return LATENTAM_OK;
+}
+
+// Tensor map of a row-major BF16 matrix (rows x inner, row stride ld elements), boxes of
+// 64 x box_rows with 128-byte swizzle; out-of-range elements read as zero.
+latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows) {
+    EncodeTiledFn enc;
+    LAT_TRY(encoder(&enc));
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || (ld * 2) % 16) {
+        set_error("tensor-core operand not 16-byte aligned");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::kChunkK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld operand", (int)r, (long long)rows,
+                  (long long)inner);
+        return LATENTAM_ERR_CUDA;
+    }
+    return LATENTAM_OK;
+}
+
+template <class Epi>
+latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 grid, tc::GemmGrid g,
+                            const typename Epi::Params& p, int* err, cudaStream_t st) {
+    constexpr size_t smem = tc::gemm_smem_bytes<Epi::BN, Epi::STAGES>();
+    static_assert(smem <= 227 * 1024, "tile does not fit in shared memory");
+    auto kern = tc::tc_gemm_kernel<Epi>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "tc_gemm smem attribute");
+    kern<<<grid, tc::kGemmThreads, smem, st>>>(a, b, g, p, err);
+    LAT_CHECK_LAUNCH("tc_gemm_kernel");
+    return LATENTAM_OK;
+}
+
+struct TcBuffers {
+    bf16 *Qb, *Qt, *Kb, *Kt, *Vb, *Vt, *A, *At, *dF, *dFt, *dS, *dSt;
+    float *row, *coef, *part;
+    double* acc;
+    int* err;
+    int64_t ldt;
+    size_t part_floats;
+};
+
+latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int d, int M, int D, bool train, TcBuffers* b) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const int64_t nn = std::max<int64_t>(n, 1);
+    b->ldt = (nn + 7) / 8 * 8;
+    const size_t e2 = sizeof(bf16);
+    size_t o = 0, off[8];
+    off[0] = o, o += up(e2 * nn * kPad);             // Qb
+    off[1] = o, o += up(e2 * (size_t)d * b->ldt);    // Qt
+    off[2] = o, o += up(e2 * (size_t)M * kPad);      // Kb
+    off[3] = o, o += up(e2 * (size_t)d * M);         // Kt
+    off[4] = o, o += up(e2 * (size_t)M * D);         // Vb
+    off[5] = o, o += up(e2 * (size_t)M * D);         // Vt
+    off[6] = o, o += up(sizeof(float) * 4 * nn);     // row
+    off[7] = o, o += up(sizeof(float) * (size_t)M);  // coef
+    char* ops = static_cast<char*>(ws(ctx, WS_DEC_AUX3, o));
+    const size_t rows_bytes = up(e2 * nn * M) + (train ? up(e2 * nn * D) + up(e2 * nn * M) : 0);
+    char* rows = static_cast<char*>(ws(ctx, WS_DEC_A, rows_bytes));
+    const size_t cols_bytes = train ? up(e2 * (size_t)M * b->ldt) + up(e2 * (size_t)D * b->ldt) +
+                                          up(e2 * (size_t)M * b->ldt)
+                                    : 256;
+    char* cols = static_cast<char*>(ws(ctx, WS_DEC_DS, cols_bytes));
+    double* acc = static_cast<double*>(ws(ctx, WS_LOSS, 256));
+    if (!ops || !rows || !cols || !acc) return LATENTAM_ERR_OUT_OF_MEMORY;
+    b->Qb = reinterpret_cast<bf16*>(ops + off[0]);
+    b->Qt = reinterpret_cast<bf16*>(ops + off[1]);
+    b->Kb = reinterpret_cast<bf16*>(ops + off[2]);
+    b->Kt = reinterpret_cast<bf16*>(ops + off[3]);
+    b->Vb = reinterpret_cast<bf16*>(ops + off[4]);
+    b->Vt = reinterpret_cast<bf16*>(ops + off[5]);
+    b->row = reinterpret_cast<float*>(ops + off[6]);
+    b->coef = reinterpret_cast<float*>(ops + off[7]);
+    b->A = reinterpret_cast<bf16*>(rows);
+    b->dF = train ? reinterpret_cast<bf16*>(rows + up(e2 * nn * M)) : nullptr;
+    b->dS = train ? reinterpret_cast<bf16*>(rows + up(e2 * nn * M) + up(e2 * nn * D)) : nullptr;
+    b->At = train ? reinterpret_cast<bf16*>(cols) : nullptr;
+    b->dFt = train ? reinterpret_cast<bf16*>(cols + up(e2 * (size_t)M * b->ldt)) : nullptr;
+    b->dSt = train ? reinterpret_cast<bf16*>(cols + up(e2 * (size_t)M * b->ldt) + up(e2 * (size_t)D * b->ldt))
+                   : nullptr;
+    b->acc = acc;
+    b->err = reinterpret_cast<int*>(acc + 8);
+    b->part = nullptr;
+    b->part_floats = 0;
+    return LATENTAM_OK;
+}
+
+// Split of the pixel reduction (K) of G5/G6 so that about one wave of CTAs runs.
+tc::GemmGrid pixel_split(int64_t n, int tiles_xy, int num_sms, int* z_out) {
+    const int chunks = (int)((n + tc::kChunkK - 1) / tc::kChunkK);
+    int z = std::max(1, (num_sms + tiles_xy - 1) / tiles_xy);
+    z = std::min(z, std::max(1, chunks / 4));
+    const int cpz = (chunks + z - 1) / z;
+    *z_out = (chunks + cpz - 1) / cpz;
+    return tc::GemmGrid{chunks, cpz};
+}
+
+}  // namespace
+
+namespace {
+
+int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+latentam_status check_tc_shape(int M, int D) {
+    if (M > 512 || D > 512) {
+        set_error("the BF16 tensor-core decode holds a full row of S (M=%d) and of Fhat (D=%d) in tensor memory: "
+                  "both must be <= 512",
+                  M, D);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    return LATENTAM_OK;
+}
+
+// Operand preparation + G1 (+ G2 with Fout for the inference form).
+latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V, int M,
+                           int D, float c, const TcBuffers& b, float* stats, cudaStream_t st) {
+    prep_dict<<<std::min(4 * ctx->num_sms, cdiv((int64_t)M * (D + kPad), 256)), 256, 0, st>>>(K, V, M, d, D, b.Kb,
+                                                                                                b.Kt, b.Vb, b.Vt);
+    LAT_CHECK_LAUNCH("prep_dict");
+    prep_queries<<<cdiv(n, 256), 256, 0, st>>>(Q, n, d, b.Qb, b.Qt, b.ldt);
+    LAT_CHECK_LAUNCH("prep_queries");
+    CUtensorMap mQ, mK;
+    LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, kTileM));
+    LAT_TRY(bf16_map(&mK, b.Kb, kPad, M, kPad, 256));
+    SoftmaxParams sp{n, b.ldt, M, c, b.A, b.At, stats};
+    const dim3 grid(cdiv(n, kTileM), 1, 1);
+    const tc::GemmGrid g1{1, 1};
+    if (M <= 256) return launch_gemm<SoftmaxEpi<256>>(mQ, mK, grid, g1, sp, b.err, st);
+    return launch_gemm<SoftmaxEpi<512>>(mQ, mK, grid, g1, sp, b.err, st);
+}
+
+latentam_status tc_fhat(const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp, cudaStream_t st) {
+    CUtensorMap mA, mVt;
+    LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM));
+    LAT_TRY(bf16_map(&mVt, b.Vt, M, D, M, 256));
+    const dim3 grid(cdiv(n, kTileM), 1, 1);
+    const tc::GemmGrid g{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
+    if (D <= 256) return launch_gemm<FhatEpi<256>>(mA, mVt, grid, g, fp, b.err, st);
+    return launch_gemm<FhatEpi<512>>(mA, mVt, grid, g, fp, b.err, st);
+}
+
+}  // namespace
+
+latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
+    const int64_t n = a.n;
+    const int M = a.M, D = a.D, d = a.d;
+    LAT_TRY(check_tc_shape(M, D));
+    TcBuffers b;
+    LAT_TRY(tc_buffers(ctx, n, d, M, D, true, &b));
+    cudaError_t e = cudaMemsetAsync(b.acc, 0, 256, st);
+    if (e != cudaSuccess) return cuda_error(e, "memset accumulators");
+    if (n > 0) {
+        tc_count_mask<<<std::min(4 * ctx->num_sms, cdiv(n, 256)), 256, 0, st>>>(a.mask, n, b.acc);
+        LAT_CHECK_LAUNCH("tc_count_mask");
+    }
+    tc_trust_region<<<cdiv(M, 8), 256, 0, st>>>(a.V, a.V0, M, D, a.cfg.delta, a.cfg.lambda_f * a.cfg.lambda_D, b.coef,
+                                              b.acc);
+    LAT_CHECK_LAUNCH("tc_trust_region");
+    const int BNq = d <= 32 ? 32 : 64;
+    int zV = 1, zK = 1;
+    tc::GemmGrid gV{0, 1}, gK{0, 1};
+    if (n > 0) {
+        gV = pixel_split(n, cdiv(M, kTileM) * cdiv(D, 256), ctx->num_sms, &zV);
+        gK = pixel_split(n, cdiv(M, kTileM), ctx->num_sms, &zK);
+    }
+    const size_t part_floats = std::max((size_t)zV * M * D, (size_t)zK * M * BNq);
+    b.part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * part_floats));
+    if (!b.part) return LATENTAM_ERR_OUT_OF_MEMORY;
+    if (n > 0) {
+        // G1: S = Q K^T -> softmax
+        LAT_TRY(tc_forward(ctx, a.Q, n, d, a.K, a.V, M, D, a.c, b, nullptr, st));
+        // G2: Fhat = A V -> loss terms -> dFhat
+        FhatParams fp{n, b.ldt, D, a.F, a.F_dtype, a.mask, a.cfg, b.acc, b.dF, b.dFt, b.row, nullptr};
+        LAT_TRY(tc_fhat(b, n, M, D, fp, st));
+        // G3: dA = dFhat V^T -> dS
+        CUtensorMap mdF, mV, mdS, mKt;
+        LAT_TRY(bf16_map(&mdF, b.dF, D, n, D, kTileM));
+        LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, 256));
+        DsParams dp{n, b.ldt, M, b.A, b.row, b.dS, b.dSt};
+        const dim3 grow(cdiv(n, kTileM), 1, 1);
+        const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
+        if (M <= 256)
+            LAT_TRY(launch_gemm<DsEpi<256>>(mdF, mV, grow, g3, dp, b.err, st));
+        else
+            LAT_TRY(launch_gemm<DsEpi<512>>(mdF, mV, grow, g3, dp, b.err, st));
+        // G4: dQ = c dS K
+        if (a.dQ) {
+            LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, kTileM));
+            LAT_TRY(bf16_map(&mKt, b.Kt, M, d, M, BNq));
+            DqParams qp{n, d, a.c, a.dQ};
+            const tc::GemmGrid g4{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
+            if (BNq == 32)
+                LAT_TRY(launch_gemm<DqEpi<32>>(mdS, mKt, grow, g4, qp, b.err, st));
+            else
+                LAT_TRY(launch_gemm<DqEpi<64>>(mdS, mKt, grow, g4, qp, b.err, st));
+        }
+    }
+    // G5: dV = A^T dFhat (+ trust region)
+    if (a.dV) {
+        if (n > 0) {
+            CUtensorMap mAt, mdFt;
+            LAT_TRY(bf16_map(&mAt, b.At, n, M, b.ldt, kTileM));
+            LAT_TRY(bf16_map(&mdFt, b.dFt, n, D, b.ldt, 256));
+            PartParams pp{M, D, D, b.part};
+            LAT_TRY(launch_gemm<PartEpi<256>>(mAt, mdFt, dim3(cdiv(M, kTileM), cdiv(D, 256), zV), gV, pp, b.err, st));
+        }
+        tc_reduce_parts<<<cdiv((int64_t)M * D, 256), 256, 0, st>>>(b.part, n > 0 ? zV : 0, M, D, D, 1.0f, b.coef,
+                                                                   a.V, a.V0, a.dV);
+        LAT_CHECK_LAUNCH("tc_reduce_parts");
+    }
+    // G6: dK = c dS^T Q
+    if (a.dK) {
+        if (n > 0) {
+            CUtensorMap mdSt, mQt;
+            LAT_TRY(bf16_map(&mdSt, b.dSt, n, M, b.ldt, kTileM));
+            LAT_TRY(bf16_map(&mQt, b.Qt, n, d, b.ldt, BNq));
+            PartParams pp{M, BNq, BNq, b.part};
+            if (BNq == 32)
+                LAT_TRY(launch_gemm<PartEpi<32>>(mdSt, mQt, dim3(cdiv(M, kTileM), 1, zK), gK, pp, b.err, st));
+            else
+                LAT_TRY(launch_gemm<PartEpi<64>>(mdSt, mQt, dim3(cdiv(M, kTileM), 1, zK), gK, pp, b.err, st));
+        }
+        tc_reduce_parts<<<cdiv((int64_t)M * d, 256), 256, 0, st>>>(b.part, n > 0 ? zK : 0, M, BNq, d, a.c, nullptr,
+                                                                   nullptr, nullptr, a.dK);
+        LAT_CHECK_LAUNCH("tc_reduce_parts");
+    }
+    tc_finalize<<<1, 1, 0, st>>>(b.acc, b.err, D, a.cfg, a.loss_parts);
+    LAT_CHECK_LAUNCH("tc_finalize");
+    return LATENTAM_OK;
+}
+
+latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V,
+                                int M, int D, float c, float* F_hat, float* row_stats, cudaStream_t st) {
+    LAT_TRY(check_tc_shape(M, D));
+    if (n == 0) return LATENTAM_OK;
+    TcBuffers b;
+    LAT_TRY(tc_buffers(ctx, n, d, M, D, false, &b));
+    cudaError_t e = cudaMemsetAsync(b.acc, 0, 256, st);
+    if (e != cudaSuccess) return cuda_error(e, "memset accumulators");
+    b.At = nullptr;
+    LAT_TRY(tc_forward(ctx, Q, n, d, K, V, M, D, c, b, row_stats, st));
+    if (F_hat) {
+        FhatParams fp{n, b.ldt, D, nullptr, LATENTAM_DTYPE_F32, nullptr, latentam_loss_cfg{}, b.acc,
+                      nullptr, nullptr, b.row, F_hat};
+        LAT_TRY(tc_fhat(b, n, M, D, fp, st));
+    }
+    return LATENTAM_OK;
 }
 
 }  // namespace lat

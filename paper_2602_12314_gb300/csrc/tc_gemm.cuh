@@ -1,0 +1,165 @@
+// One tcgen05 GEMM tile kernel shared by every tensor-core contraction of the decode:
+//   C[128 x BN] = A[128 x K] * B[BN x K]^T, A and B BF16 K-major in global memory,
+// TMA-loaded in 64-wide K chunks (128-byte swizzle) through a STAGES-deep mbarrier pipeline,
+// accumulated in FP32 in tensor memory, then handed row by row to an epilogue.
+//
+// Warp roles (192 threads): warp 0 issues the TMA loads, warp 1 owns the TMEM allocation and
+// issues the MMAs (one thread), warps 2..5 run the epilogue; epilogue thread r owns tile row r
+// (TMEM lane r; warp w reads the lane quarter w % 4).
+// blockIdx.x: 128-row tile of A, blockIdx.y: BN-row tile of B, blockIdx.z: split of the K range.
+#pragma once
+
+#include "internal.cuh"
+#include "tc_common.cuh"
+
+namespace lat {
+namespace tc {
+
+constexpr int kGemmThreads = 192;
+constexpr int kTileM = 128;
+constexpr int kChunkK = 64;                       // BF16 elements per 128-byte row
+constexpr uint32_t kTileABytes = kTileM * 128;    // 16 KB
+
+__host__ __device__ constexpr uint32_t tmem_cols_for(int n) {
+    return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
+}
+
+template <int BN, int STAGES>
+__host__ __device__ constexpr size_t gemm_smem_bytes() {
+    return (size_t)STAGES * (kTileABytes + (size_t)BN * 128) + 1024 /* alignment */ + 256 /* barriers */;
+}
+
+struct GemmGrid {
+    int k_chunks;      // total 64-wide K chunks
+    int chunks_per_z;  // chunks handled by one blockIdx.z
+};
+
+// Epi must provide: static constexpr int BN, STAGES, BOX_B (rows per TMA box of B, divides BN,
+// <= 256); struct Params; static __device__ void run(const Params&, uint32_t taddr_row,
+// int row, int m0, int n0, int z) executed by the 128 epilogue threads (warp-convergent).
+template <class Epi>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmGrid g,
+                   typename Epi::Params ep, int* __restrict__ err) {
+    constexpr int BN = Epi::BN;
+    constexpr int STAGES = Epi::STAGES;
+    constexpr int BOX_B = Epi::BOX_B;
+    constexpr int NSUB = BN <= 256 ? 1 : 2;      // MMA instructions per K step (N <= 256 each)
+    constexpr int SUBN = BN / NSUB;
+    constexpr uint32_t B_BYTES = (uint32_t)BN * 128;
+    constexpr uint32_t STAGE_BYTES = kTileABytes + B_BYTES;
+    constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
+    constexpr uint32_t IDESC = idesc_bf16(kTileM, SUBN);
+    static_assert(BN % 16 == 0 && SUBN % 16 == 0 && SUBN <= 256, "MMA N must be a multiple of 16, <= 256");
+    static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accum = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kTileM;
+    const int n0 = blockIdx.y * BN;
+    const int k_begin = blockIdx.z * g.chunks_per_z;
+    const int k_end = min(g.k_chunks, k_begin + g.chunks_per_z);
+    const int nk = k_end - k_begin;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer ----
+            int issued = 0;
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % STAGES;
+                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                if (i >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                uint8_t* sa = smem + s * STAGE_BYTES;
+                uint8_t* sb = sa + kTileABytes;
+                const int kx = (k_begin + i) * kChunkK;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                tma_load_2d(sa, &tmA, &full[s], kx, m0);
+#pragma unroll
+                for (int b = 0; b < BN / BOX_B; ++b) tma_load_2d(sb + b * BOX_B * 128, &tmB, &full[s], kx, n0 + b * BOX_B);
+                ++issued;
+            }
+            // never leave the CTA with copies in flight: drain the stages still being filled
+            if (*abort_flag) {
+                for (int i = max(0, issued - STAGES); i < issued; ++i)
+                    (void)mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u, nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            bool ok = true;
+            for (int i = 0; i < nk && ok; ++i) {
+                const int s = i % STAGES;
+                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                if (!mbar_wait(&full[s], ph, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t sb = sa + kTileABytes;
+#pragma unroll
+                for (int kk = 0; kk < kChunkK / 16; ++kk) {
+#pragma unroll
+                    for (int j = 0; j < NSUB; ++j)
+                        mma_bf16(tmem_base + (uint32_t)(j * SUBN), sw128_desc(sa + kk * 32),
+                                 sw128_desc(sb + (uint32_t)(j * SUBN * 128) + kk * 32), IDESC,
+                                 (i > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+            }
+            if (!ok) *abort_flag = 1;
+            mma_commit(accum);  // accumulator complete (or the pipeline was abandoned)
+        }
+    } else {
+        // ---- epilogue warps ----
+        const bool ready = mbar_wait(accum, 0, abort_flag);
+        tc_fence_after();
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        if (!ready) *abort_flag = 1;
+        // one warp-uniform decision: the epilogue's TMEM loads are warp-collective
+        const bool go = __all_sync(0xffffffffu, ready && nk > 0 && !*abort_flag);
+        if (go) Epi::run(ep, tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z);
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
+    // an abandoned pipeline may still have MMAs in flight: let them finish before freeing TMEM
+    if (*abort_flag && warp == 1 && lane == 0) (void)mbar_wait(accum, 0, nullptr);
+    __syncwarp();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+}  // namespace tc
+}  // namespace lat
