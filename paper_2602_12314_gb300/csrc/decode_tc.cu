@@ -2,15 +2,16 @@
 // its backward on the tcgen05 tensor cores: BF16 operands, FP32 accumulation in TMEM, FP32
 // softmax and loss arithmetic, FP64 frame sums.  Six contractions share tc_gemm_kernel:
 //
-//   G1  S = Q K^T            epilogue: row softmax (logit scale c) -> A, A^T (BF16), row stats
-//   G2  Fhat = A V           epilogue: cos / L2 against F, a_p, b_p -> dFhat, dFhat^T (BF16)
-//   G3  dA = dFhat V^T       epilogue: dS = A (dA - <A, dA>) -> dS, dS^T (BF16)
+//   G1  S = Q K^T            epilogue: row softmax (logit scale c) -> A (BF16), row stats
+//   G2  Fhat = A V           epilogue: cos / L2 against F, a_p, b_p -> dFhat (BF16)
+//   G3  dA = dFhat V^T       epilogue: dS = A (dA - <A, dA>) -> dS (BF16)
 //   G4  dQ = c dS K          epilogue: FP32 dQ
 //   G5  dV = A^T dFhat       split over pixels -> FP32 partials -> sum + trust-region term
 //   G6  dK = c dS^T Q        split over pixels -> FP32 partials -> sum
 //
-// Every operand is K-major (the epilogues write the transposed copies the pixel-reduction
-// contractions need), so all tiles are plain 128-byte-swizzled TMA boxes.
+// Every intermediate is stored once, row-major (pixel x atom / pixel x feature); the
+// contractions that reduce over pixels (G5, G6) and those whose B operand runs along its
+// contiguous dimension (G2, G4) read it as an MN-major operand, so nothing is transposed.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -28,9 +29,8 @@ constexpr int kPad = 64;  // query / key rows padded to one 64-wide K chunk
 
 // ---- operand preparation ----------------------------------------------------------------
 
-// Qb[p][0..63] = bf16(Q[p][0..d)) zero-padded; Qt[k][p] = bf16(Q[p][k]).
-__global__ void prep_queries(const float* __restrict__ Q, int64_t n, int d, bf16* __restrict__ Qb,
-                             bf16* __restrict__ Qt, int64_t ldt) {
+// Qb[p][0..63] = bf16(Q[p][0..d)) zero-padded.
+__global__ void prep_queries(const float* __restrict__ Q, int64_t n, int d, bf16* __restrict__ Qb) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     uint32_t w[kPad / 2];
@@ -39,30 +39,24 @@ __global__ void prep_queries(const float* __restrict__ Q, int64_t n, int d, bf16
         const float a = k < d ? Q[p * d + k] : 0.f;
         const float b = k + 1 < d ? Q[p * d + k + 1] : 0.f;
         w[k / 2] = tc::pack_bf16x2(a, b);
-        if (k < d) Qt[(int64_t)k * ldt + p] = __float2bfloat16_rn(a);
-        if (k + 1 < d) Qt[(int64_t)(k + 1) * ldt + p] = __float2bfloat16_rn(b);
     }
     uint4* dst = reinterpret_cast<uint4*>(Qb + p * kPad);
 #pragma unroll
     for (int v = 0; v < kPad / 8; ++v) dst[v] = make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
 }
 
-// Kb[j][0..63] (zero-padded), Kt[k][j], Vb[j][c], Vt[c][j]: BF16 copies of the dictionary.
+// Kb[j][0..63] (zero-padded) and Vb[j][c]: BF16 copies of the dictionary.
 __global__ void prep_dict(const float* __restrict__ K, const float* __restrict__ V, int M, int d, int D,
-                          bf16* __restrict__ Kb, bf16* __restrict__ Kt, bf16* __restrict__ Vb, bf16* __restrict__ Vt) {
+                          bf16* __restrict__ Kb, bf16* __restrict__ Vb) {
     const int64_t total = (int64_t)M * D + (int64_t)M * kPad;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         if (e < (int64_t)M * D) {
-            const int j = (int)(e / D), c = (int)(e % D);
-            const bf16 v = __float2bfloat16_rn(V[e]);
-            Vb[e] = v;
-            Vt[(int64_t)c * M + j] = v;
+            Vb[e] = __float2bfloat16_rn(V[e]);
         } else {
             const int64_t f = e - (int64_t)M * D;
             const int j = (int)(f / kPad), k = (int)(f % kPad);
             const float v = k < d ? K[(int64_t)j * d + k] : 0.f;
             Kb[f] = __float2bfloat16_rn(v);
-            if (k < d) Kt[(int64_t)k * M + j] = __float2bfloat16_rn(v);
         }
     }
 }
@@ -178,17 +172,17 @@ __device__ __forceinline__ void load_target32(const void* F, latentam_dtype dt, 
 
 // G1: row softmax of c S over the M atoms.
 struct SoftmaxParams {
-    int64_t n, ldt;
+    int64_t n;
     int M;
     float c;
     bf16* A;       // n x M
-    bf16* At;      // M x ldt
     float* stats;  // n x 2 (row max of c S, softmax denominator), nullable
 };
 
 template <int BN_>
 struct SoftmaxEpi {
     static constexpr int BN = BN_, STAGES = 1, BOX_B = BN_ <= 256 ? BN_ : 256;
+    static constexpr bool A_MN = false, B_MN = false;
     using Params = SoftmaxParams;
     static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
         const int64_t pix = (int64_t)m0 + row;
@@ -214,9 +208,6 @@ struct SoftmaxEpi {
             for (int i = 0; i < 32; ++i) v[i] = __expf(p.c * v[i] - cm) * il;
             if (valid) {
                 store_row_bf16x32(p.A + pix * p.M + c0, v);
-                if (p.At)
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) p.At[(int64_t)(c0 + i) * p.ldt + pix] = __float2bfloat16_rn(v[i]);
             }
         }
         if (valid && p.stats) {
@@ -228,7 +219,7 @@ struct SoftmaxEpi {
 
 // G2: Fhat = A V, the per-pixel loss terms and dL/dFhat = a_p Fhat + b_p F.
 struct FhatParams {
-    int64_t n, ldt;
+    int64_t n;
     int D;
     const void* F;
     latentam_dtype F_dtype;
@@ -236,7 +227,6 @@ struct FhatParams {
     latentam_loss_cfg cfg;
     double* acc;
     bf16* dF;     // n x D
-    bf16* dFt;    // D x ldt
     float* row;   // n x 4: a_p, b_p, <A_p, dA_p>, cos_p
     float* Fout;  // n x D FP32 Fhat (inference form: no loss) or NULL
 };
@@ -244,6 +234,7 @@ struct FhatParams {
 template <int BN_>
 struct FhatEpi {
     static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_;
+    static constexpr bool A_MN = false, B_MN = true;  // B = V (atoms x features), features contiguous
     using Params = FhatParams;
     static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
         const int64_t pix = (int64_t)m0 + row;
@@ -314,8 +305,6 @@ struct FhatEpi {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) h[i] = a * h[i] + b * f[i];
                 store_row_bf16x32(p.dF + pix * p.D + c0, h);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) p.dFt[(int64_t)(c0 + i) * p.ldt + pix] = __float2bfloat16_rn(h[i]);
             }
         }
     }
@@ -323,17 +312,17 @@ struct FhatEpi {
 
 // G3: dS = A (dA - <A, dA>).
 struct DsParams {
-    int64_t n, ldt;
+    int64_t n;
     int M;
     const bf16* A;
     const float* row;
     bf16* dS;   // n x M
-    bf16* dSt;  // M x ldt
 };
 
 template <int BN_>
 struct DsEpi {
     static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_;
+    static constexpr bool A_MN = false, B_MN = false;
     using Params = DsParams;
     static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
         const int64_t pix = (int64_t)m0 + row;
@@ -347,8 +336,6 @@ struct DsEpi {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) g[i] = a[i] * (g[i] - rd);
                 store_row_bf16x32(p.dS + pix * p.M + c0, g);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) p.dSt[(int64_t)(c0 + i) * p.ldt + pix] = __float2bfloat16_rn(g[i]);
             }
         }
     }
@@ -365,6 +352,7 @@ struct DqParams {
 template <int BN_>
 struct DqEpi {
     static constexpr int BN = BN_, STAGES = 6, BOX_B = BN_;
+    static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
     using Params = DqParams;
     static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
         const int64_t pix = (int64_t)m0 + row;
@@ -389,6 +377,7 @@ struct PartParams {
 template <int BN_>
 struct PartEpi {
     static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_;
+    static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
     using Params = PartParams;
     static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int n0, int z) {
         const int j = m0 + row;
@@ -477,56 +466,38 @@ latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 gri
 }
 
 struct TcBuffers {
-    bf16 *Qb, *Qt, *Kb, *Kt, *Vb, *Vt, *A, *At, *dF, *dFt, *dS, *dSt;
+    bf16 *Qb, *Kb, *Vb, *A, *dF, *dS;
     float *row, *coef, *part;
     double* acc;
     int* err;
-    int64_t ldt;
-    size_t part_floats;
 };
 
-latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int d, int M, int D, bool train, TcBuffers* b) {
+latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool train, TcBuffers* b) {
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const int64_t nn = std::max<int64_t>(n, 1);
-    b->ldt = (nn + 7) / 8 * 8;
     const size_t e2 = sizeof(bf16);
-    size_t o = 0, off[8];
+    size_t o = 0, off[5];
     off[0] = o, o += up(e2 * nn * kPad);             // Qb
-    off[1] = o, o += up(e2 * (size_t)d * b->ldt);    // Qt
-    off[2] = o, o += up(e2 * (size_t)M * kPad);      // Kb
-    off[3] = o, o += up(e2 * (size_t)d * M);         // Kt
-    off[4] = o, o += up(e2 * (size_t)M * D);         // Vb
-    off[5] = o, o += up(e2 * (size_t)M * D);         // Vt
-    off[6] = o, o += up(sizeof(float) * 4 * nn);     // row
-    off[7] = o, o += up(sizeof(float) * (size_t)M);  // coef
+    off[1] = o, o += up(e2 * (size_t)M * kPad);      // Kb
+    off[2] = o, o += up(e2 * (size_t)M * D);         // Vb
+    off[3] = o, o += up(sizeof(float) * 4 * nn);     // row
+    off[4] = o, o += up(sizeof(float) * (size_t)M);  // coef
     char* ops = static_cast<char*>(ws(ctx, WS_DEC_AUX3, o));
     const size_t rows_bytes = up(e2 * nn * M) + (train ? up(e2 * nn * D) + up(e2 * nn * M) : 0);
     char* rows = static_cast<char*>(ws(ctx, WS_DEC_A, rows_bytes));
-    const size_t cols_bytes = train ? up(e2 * (size_t)M * b->ldt) + up(e2 * (size_t)D * b->ldt) +
-                                          up(e2 * (size_t)M * b->ldt)
-                                    : 256;
-    char* cols = static_cast<char*>(ws(ctx, WS_DEC_DS, cols_bytes));
     double* acc = static_cast<double*>(ws(ctx, WS_LOSS, 256));
-    if (!ops || !rows || !cols || !acc) return LATENTAM_ERR_OUT_OF_MEMORY;
+    if (!ops || !rows || !acc) return LATENTAM_ERR_OUT_OF_MEMORY;
     b->Qb = reinterpret_cast<bf16*>(ops + off[0]);
-    b->Qt = reinterpret_cast<bf16*>(ops + off[1]);
-    b->Kb = reinterpret_cast<bf16*>(ops + off[2]);
-    b->Kt = reinterpret_cast<bf16*>(ops + off[3]);
-    b->Vb = reinterpret_cast<bf16*>(ops + off[4]);
-    b->Vt = reinterpret_cast<bf16*>(ops + off[5]);
-    b->row = reinterpret_cast<float*>(ops + off[6]);
-    b->coef = reinterpret_cast<float*>(ops + off[7]);
+    b->Kb = reinterpret_cast<bf16*>(ops + off[1]);
+    b->Vb = reinterpret_cast<bf16*>(ops + off[2]);
+    b->row = reinterpret_cast<float*>(ops + off[3]);
+    b->coef = reinterpret_cast<float*>(ops + off[4]);
     b->A = reinterpret_cast<bf16*>(rows);
     b->dF = train ? reinterpret_cast<bf16*>(rows + up(e2 * nn * M)) : nullptr;
     b->dS = train ? reinterpret_cast<bf16*>(rows + up(e2 * nn * M) + up(e2 * nn * D)) : nullptr;
-    b->At = train ? reinterpret_cast<bf16*>(cols) : nullptr;
-    b->dFt = train ? reinterpret_cast<bf16*>(cols + up(e2 * (size_t)M * b->ldt)) : nullptr;
-    b->dSt = train ? reinterpret_cast<bf16*>(cols + up(e2 * (size_t)M * b->ldt) + up(e2 * (size_t)D * b->ldt))
-                   : nullptr;
     b->acc = acc;
     b->err = reinterpret_cast<int*>(acc + 8);
     b->part = nullptr;
-    b->part_floats = 0;
     return LATENTAM_OK;
 }
 
@@ -556,32 +527,33 @@ latentam_status check_tc_shape(int M, int D) {
     return LATENTAM_OK;
 }
 
-// Operand preparation + G1 (+ G2 with Fout for the inference form).
+// Operand preparation + G1 (softmax).
 latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V, int M,
                            int D, float c, const TcBuffers& b, float* stats, cudaStream_t st) {
     prep_dict<<<std::min(4 * ctx->num_sms, cdiv((int64_t)M * (D + kPad), 256)), 256, 0, st>>>(K, V, M, d, D, b.Kb,
-                                                                                                b.Kt, b.Vb, b.Vt);
+                                                                                                b.Vb);
     LAT_CHECK_LAUNCH("prep_dict");
-    prep_queries<<<cdiv(n, 256), 256, 0, st>>>(Q, n, d, b.Qb, b.Qt, b.ldt);
+    prep_queries<<<cdiv(n, 256), 256, 0, st>>>(Q, n, d, b.Qb);
     LAT_CHECK_LAUNCH("prep_queries");
     CUtensorMap mQ, mK;
     LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, kTileM));
     LAT_TRY(bf16_map(&mK, b.Kb, kPad, M, kPad, 256));
-    SoftmaxParams sp{n, b.ldt, M, c, b.A, b.At, stats};
+    SoftmaxParams sp{n, M, c, b.A, stats};
     const dim3 grid(cdiv(n, kTileM), 1, 1);
     const tc::GemmGrid g1{1, 1};
     if (M <= 256) return launch_gemm<SoftmaxEpi<256>>(mQ, mK, grid, g1, sp, b.err, st);
     return launch_gemm<SoftmaxEpi<512>>(mQ, mK, grid, g1, sp, b.err, st);
 }
 
+// G2: Fhat = A V, B = V read MN-major in 64 x 64 boxes (features x atoms).
 latentam_status tc_fhat(const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp, cudaStream_t st) {
-    CUtensorMap mA, mVt;
+    CUtensorMap mA, mV;
     LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM));
-    LAT_TRY(bf16_map(&mVt, b.Vt, M, D, M, 256));
+    LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, 64));
     const dim3 grid(cdiv(n, kTileM), 1, 1);
     const tc::GemmGrid g{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
-    if (D <= 256) return launch_gemm<FhatEpi<256>>(mA, mVt, grid, g, fp, b.err, st);
-    return launch_gemm<FhatEpi<512>>(mA, mVt, grid, g, fp, b.err, st);
+    if (D <= 256) return launch_gemm<FhatEpi<256>>(mA, mV, grid, g, fp, b.err, st);
+    return launch_gemm<FhatEpi<512>>(mA, mV, grid, g, fp, b.err, st);
 }
 
 }  // namespace
@@ -591,7 +563,7 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
     const int M = a.M, D = a.D, d = a.d;
     LAT_TRY(check_tc_shape(M, D));
     TcBuffers b;
-    LAT_TRY(tc_buffers(ctx, n, d, M, D, true, &b));
+    LAT_TRY(tc_buffers(ctx, n, M, D, true, &b));
     cudaError_t e = cudaMemsetAsync(b.acc, 0, 256, st);
     if (e != cudaSuccess) return cuda_error(e, "memset accumulators");
     if (n > 0) {
@@ -601,7 +573,7 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
     tc_trust_region<<<cdiv(M, 8), 256, 0, st>>>(a.V, a.V0, M, D, a.cfg.delta, a.cfg.lambda_f * a.cfg.lambda_D, b.coef,
                                               b.acc);
     LAT_CHECK_LAUNCH("tc_trust_region");
-    const int BNq = d <= 32 ? 32 : 64;
+    constexpr int BNq = kPad;  // queries padded to 64 columns
     int zV = 1, zK = 1;
     tc::GemmGrid gV{0, 1}, gK{0, 1};
     if (n > 0) {
@@ -615,39 +587,36 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
         // G1: S = Q K^T -> softmax
         LAT_TRY(tc_forward(ctx, a.Q, n, d, a.K, a.V, M, D, a.c, b, nullptr, st));
         // G2: Fhat = A V -> loss terms -> dFhat
-        FhatParams fp{n, b.ldt, D, a.F, a.F_dtype, a.mask, a.cfg, b.acc, b.dF, b.dFt, b.row, nullptr};
+        FhatParams fp{n, D, a.F, a.F_dtype, a.mask, a.cfg, b.acc, b.dF, b.row, nullptr};
         LAT_TRY(tc_fhat(b, n, M, D, fp, st));
         // G3: dA = dFhat V^T -> dS
-        CUtensorMap mdF, mV, mdS, mKt;
+        CUtensorMap mdF, mV, mdS, mK;
         LAT_TRY(bf16_map(&mdF, b.dF, D, n, D, kTileM));
         LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, 256));
-        DsParams dp{n, b.ldt, M, b.A, b.row, b.dS, b.dSt};
+        DsParams dp{n, M, b.A, b.row, b.dS};
         const dim3 grow(cdiv(n, kTileM), 1, 1);
         const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
         if (M <= 256)
             LAT_TRY(launch_gemm<DsEpi<256>>(mdF, mV, grow, g3, dp, b.err, st));
         else
             LAT_TRY(launch_gemm<DsEpi<512>>(mdF, mV, grow, g3, dp, b.err, st));
-        // G4: dQ = c dS K
+        // G4: dQ = c dS K, B = K padded read MN-major (queries x atoms)
         if (a.dQ) {
             LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, kTileM));
-            LAT_TRY(bf16_map(&mKt, b.Kt, M, d, M, BNq));
+            LAT_TRY(bf16_map(&mK, b.Kb, kPad, M, kPad, 64));
             DqParams qp{n, d, a.c, a.dQ};
             const tc::GemmGrid g4{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
-            if (BNq == 32)
-                LAT_TRY(launch_gemm<DqEpi<32>>(mdS, mKt, grow, g4, qp, b.err, st));
-            else
-                LAT_TRY(launch_gemm<DqEpi<64>>(mdS, mKt, grow, g4, qp, b.err, st));
+            LAT_TRY(launch_gemm<DqEpi<BNq>>(mdS, mK, grow, g4, qp, b.err, st));
         }
     }
-    // G5: dV = A^T dFhat (+ trust region)
+    // G5: dV = A^T dFhat (+ trust region), both operands pixel-major (MN-major)
     if (a.dV) {
         if (n > 0) {
-            CUtensorMap mAt, mdFt;
-            LAT_TRY(bf16_map(&mAt, b.At, n, M, b.ldt, kTileM));
-            LAT_TRY(bf16_map(&mdFt, b.dFt, n, D, b.ldt, 256));
+            CUtensorMap mA, mdF;
+            LAT_TRY(bf16_map(&mA, b.A, M, n, M, 64));
+            LAT_TRY(bf16_map(&mdF, b.dF, D, n, D, 64));
             PartParams pp{M, D, D, b.part};
-            LAT_TRY(launch_gemm<PartEpi<256>>(mAt, mdFt, dim3(cdiv(M, kTileM), cdiv(D, 256), zV), gV, pp, b.err, st));
+            LAT_TRY(launch_gemm<PartEpi<256>>(mA, mdF, dim3(cdiv(M, kTileM), cdiv(D, 256), zV), gV, pp, b.err, st));
         }
         tc_reduce_parts<<<cdiv((int64_t)M * D, 256), 256, 0, st>>>(b.part, n > 0 ? zV : 0, M, D, D, 1.0f, b.coef,
                                                                    a.V, a.V0, a.dV);
@@ -656,14 +625,11 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
     // G6: dK = c dS^T Q
     if (a.dK) {
         if (n > 0) {
-            CUtensorMap mdSt, mQt;
-            LAT_TRY(bf16_map(&mdSt, b.dSt, n, M, b.ldt, kTileM));
-            LAT_TRY(bf16_map(&mQt, b.Qt, n, d, b.ldt, BNq));
+            CUtensorMap mdS, mQ;
+            LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, 64));
+            LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, 64));
             PartParams pp{M, BNq, BNq, b.part};
-            if (BNq == 32)
-                LAT_TRY(launch_gemm<PartEpi<32>>(mdSt, mQt, dim3(cdiv(M, kTileM), 1, zK), gK, pp, b.err, st));
-            else
-                LAT_TRY(launch_gemm<PartEpi<64>>(mdSt, mQt, dim3(cdiv(M, kTileM), 1, zK), gK, pp, b.err, st));
+            LAT_TRY(launch_gemm<PartEpi<BNq>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zK), gK, pp, b.err, st));
         }
         tc_reduce_parts<<<cdiv((int64_t)M * d, 256), 256, 0, st>>>(b.part, n > 0 ? zK : 0, M, BNq, d, a.c, nullptr,
                                                                    nullptr, nullptr, a.dK);
@@ -679,14 +645,12 @@ latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, in
     LAT_TRY(check_tc_shape(M, D));
     if (n == 0) return LATENTAM_OK;
     TcBuffers b;
-    LAT_TRY(tc_buffers(ctx, n, d, M, D, false, &b));
+    LAT_TRY(tc_buffers(ctx, n, M, D, false, &b));
     cudaError_t e = cudaMemsetAsync(b.acc, 0, 256, st);
     if (e != cudaSuccess) return cuda_error(e, "memset accumulators");
-    b.At = nullptr;
     LAT_TRY(tc_forward(ctx, Q, n, d, K, V, M, D, c, b, row_stats, st));
     if (F_hat) {
-        FhatParams fp{n, b.ldt, D, nullptr, LATENTAM_DTYPE_F32, nullptr, latentam_loss_cfg{}, b.acc,
-                      nullptr, nullptr, b.row, F_hat};
+        FhatParams fp{n, D, nullptr, LATENTAM_DTYPE_F32, nullptr, latentam_loss_cfg{}, b.acc, nullptr, b.row, F_hat};
         LAT_TRY(tc_fhat(b, n, M, D, fp, st));
     }
     return LATENTAM_OK;

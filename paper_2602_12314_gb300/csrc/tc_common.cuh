@@ -105,9 +105,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B; a_mn / b_mn select the
+// MN-major (instead of K-major) operand layout.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n, bool a_mn = false, bool b_mn = false) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 // Shared-memory descriptor of a K-major tile written by TMA with 128-byte swizzle: rows of
@@ -116,6 +118,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Shared-memory descriptor of an MN-major tile written by TMA with 128-byte swizzle in boxes of
+// 64 (MN, contiguous) x 64 (K rows): within a box, rows of 64 BF16 (128 B) and 8-row atoms
+// 1024 B apart (SBO); consecutive 64-wide MN blocks (boxes) 8 KB apart (LBO).  `saddr` is the
+// (1024-aligned tile base + k * 128 B) shared address for K row k.
+constexpr uint32_t kMnBoxBytes = 64 * 128;
+__device__ __forceinline__ uint64_t mn128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kMnBoxBytes >> 4) << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
 // 32 consecutive 32-bit TMEM columns of this thread's lane (warp-collective).

@@ -34,9 +34,11 @@ struct GemmGrid {
     int chunks_per_z;  // chunks handled by one blockIdx.z
 };
 
-// Epi must provide: static constexpr int BN, STAGES, BOX_B (rows per TMA box of B, divides BN,
-// <= 256); struct Params; static __device__ void run(const Params&, uint32_t taddr_row,
-// int row, int m0, int n0, int z) executed by the 128 epilogue threads (warp-convergent).
+// Epi must provide: static constexpr int BN, STAGES, BOX_B (rows per TMA box of a K-major B,
+// divides BN, <= 256); static constexpr bool A_MN, B_MN (operand stored MN-major: the tile is
+// loaded as 64 (MN) x 64 (K) boxes of a row-major K x MN matrix, x = MN, y = K); struct
+// Params; static __device__ void run(const Params&, uint32_t taddr_row, int row, int m0,
+// int n0, int z) executed by the 128 epilogue threads (warp-convergent).
 template <class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmGrid g,
@@ -49,9 +51,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     constexpr uint32_t B_BYTES = (uint32_t)BN * 128;
     constexpr uint32_t STAGE_BYTES = kTileABytes + B_BYTES;
     constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
-    constexpr uint32_t IDESC = idesc_bf16(kTileM, SUBN);
+    constexpr bool A_MN = Epi::A_MN, B_MN = Epi::B_MN;
+    constexpr uint32_t IDESC = idesc_bf16(kTileM, SUBN, A_MN, B_MN);
     static_assert(BN % 16 == 0 && SUBN % 16 == 0 && SUBN <= 256, "MMA N must be a multiple of 16, <= 256");
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
+    static_assert(!B_MN || SUBN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -100,9 +104,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 uint8_t* sb = sa + kTileABytes;
                 const int kx = (k_begin + i) * kChunkK;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(sa, &tmA, &full[s], kx, m0);
+                if (A_MN) {
 #pragma unroll
-                for (int b = 0; b < BN / BOX_B; ++b) tma_load_2d(sb + b * BOX_B * 128, &tmB, &full[s], kx, n0 + b * BOX_B);
+                    for (int b = 0; b < kTileM / 64; ++b) tma_load_2d(sa + b * kMnBoxBytes, &tmA, &full[s], m0 + 64 * b, kx);
+                } else {
+                    tma_load_2d(sa, &tmA, &full[s], kx, m0);
+                }
+                if (B_MN) {
+#pragma unroll
+                    for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * kMnBoxBytes, &tmB, &full[s], n0 + 64 * b, kx);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < BN / BOX_B; ++b)
+                        tma_load_2d(sb + b * BOX_B * 128, &tmB, &full[s], kx, n0 + b * BOX_B);
+                }
                 ++issued;
             }
             // never leave the CTA with copies in flight: drain the stages still being filled
@@ -127,11 +142,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 const uint32_t sb = sa + kTileABytes;
 #pragma unroll
                 for (int kk = 0; kk < kChunkK / 16; ++kk) {
+                    const uint64_t da = A_MN ? mn128_desc(sa + kk * 16 * 128) : sw128_desc(sa + kk * 32);
 #pragma unroll
-                    for (int j = 0; j < NSUB; ++j)
-                        mma_bf16(tmem_base + (uint32_t)(j * SUBN), sw128_desc(sa + kk * 32),
-                                 sw128_desc(sb + (uint32_t)(j * SUBN * 128) + kk * 32), IDESC,
-                                 (i > 0 || kk > 0) ? 1u : 0u);
+                    for (int j = 0; j < NSUB; ++j) {
+                        const uint64_t db = B_MN ? mn128_desc(sb + (uint32_t)(j * (SUBN / 64)) * kMnBoxBytes + kk * 16 * 128)
+                                                 : sw128_desc(sb + (uint32_t)(j * SUBN * 128) + kk * 32);
+                        mma_bf16(tmem_base + (uint32_t)(j * SUBN), da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+                    }
                 }
                 mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
             }
