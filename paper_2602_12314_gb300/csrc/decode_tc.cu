@@ -170,6 +170,9 @@ __device__ __forceinline__ void load_target32(const void* F, latentam_dtype dt, 
     }
 }
 
+// Column chunks of 32 are dealt to the epilogue warpgroups round-robin: group g owns the
+// chunks c0 = 32 (g + G k).
+
 // G1: row softmax of c S over the M atoms.
 struct SoftmaxParams {
     int64_t n;
@@ -181,43 +184,44 @@ struct SoftmaxParams {
 
 template <int BN_>
 struct SoftmaxEpi {
-    static constexpr int BN = BN_, STAGES = 1, BOX_B = BN_ <= 256 ? BN_ : 256;
+    static constexpr int BN = BN_, STAGES = 1, BOX_B = BN_ <= 256 ? BN_ : 256, EPI_WG = 2;
     static constexpr bool A_MN = false, B_MN = false;
     using Params = SoftmaxParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int, int g, float* scr) {
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
         float v[32];
         float mx = -INFINITY;
-        for (int c0 = 0; c0 < p.M; c0 += 32) {
+        for (int c0 = 32 * g; c0 < p.M; c0 += 32 * EPI_WG) {
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) mx = fmaxf(mx, v[i]);
         }
+        mx = tc::group_max<EPI_WG>(mx, scr, 0, g, row);
         const float cm = p.c * mx;
         float sum = 0.f;
-        for (int c0 = 0; c0 < p.M; c0 += 32) {
+        for (int c0 = 32 * g; c0 < p.M; c0 += 32 * EPI_WG) {
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) sum += __expf(p.c * v[i] - cm);
         }
+        sum = tc::group_sum<EPI_WG>(sum, scr, 1, g, row);
         const float il = 1.0f / sum;
-        for (int c0 = 0; c0 < p.M; c0 += 32) {
+        for (int c0 = 32 * g; c0 < p.M; c0 += 32 * EPI_WG) {
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = __expf(p.c * v[i] - cm) * il;
-            if (valid) {
-                store_row_bf16x32(p.A + pix * p.M + c0, v);
-            }
+            if (valid) store_row_bf16x32(p.A + pix * p.M + c0, v);
         }
-        if (valid && p.stats) {
+        if (valid && p.stats && g == 0) {
             p.stats[2 * pix] = cm;
             p.stats[2 * pix + 1] = sum;
         }
     }
 };
 
-// G2: Fhat = A V, the per-pixel loss terms and dL/dFhat = a_p Fhat + b_p F.
+// G2: Fhat = A V, the per-pixel loss terms and dL/dFhat = a_p Fhat + b_p F.  The target
+// chunk of the next iteration is loaded before the current one is consumed.
 struct FhatParams {
     int64_t n;
     int D;
@@ -233,15 +237,16 @@ struct FhatParams {
 
 template <int BN_>
 struct FhatEpi {
-    static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_;
+    static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_, EPI_WG = 2;
     static constexpr bool A_MN = false, B_MN = true;  // B = V (atoms x features), features contiguous
     using Params = FhatParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int, int g, float* scr) {
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
-        float h[32], f[32];
+        const int step = 32 * EPI_WG;
+        float h[32], f[32], fn[32];
         if (p.Fout) {
-            for (int c0 = 0; c0 < p.D; c0 += 32) {
+            for (int c0 = 32 * g; c0 < p.D; c0 += step) {
                 tc::tmem_ld32(taddr + c0, h);
                 if (valid) {
                     float4* d4 = reinterpret_cast<float4*>(p.Fout + pix * p.D + c0);
@@ -251,21 +256,27 @@ struct FhatEpi {
             }
             return;
         }
+        const int64_t frow = valid ? pix * p.D : 0;  // invalid rows read row 0 (discarded)
         float dot = 0.f, nh2 = 0.f, nf2 = 0.f, e2 = 0.f;
-        for (int c0 = 0; c0 < p.D; c0 += 32) {
+        load_target32(p.F, p.F_dtype, frow + 32 * g, f);
+        for (int c0 = 32 * g; c0 < p.D; c0 += step) {
+            if (c0 + step < p.D) load_target32(p.F, p.F_dtype, frow + c0 + step, fn);
             tc::tmem_ld32(taddr + c0, h);
-            if (valid) {
-                load_target32(p.F, p.F_dtype, pix * p.D + c0, f);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    dot += h[i] * f[i];
-                    nh2 += h[i] * h[i];
-                    nf2 += f[i] * f[i];
-                    const float e = h[i] - f[i];
-                    e2 += e * e;
-                }
+            for (int i = 0; i < 32; ++i) {
+                dot += h[i] * f[i];
+                nh2 += h[i] * h[i];
+                nf2 += f[i] * f[i];
+                const float e = h[i] - f[i];
+                e2 += e * e;
             }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) f[i] = fn[i];
         }
+        dot = tc::group_sum<EPI_WG>(dot, scr, 0, g, row);
+        nh2 = tc::group_sum<EPI_WG>(nh2, scr, 1, g, row);
+        nf2 = tc::group_sum<EPI_WG>(nf2, scr, 2, g, row);
+        e2 = tc::group_sum<EPI_WG>(e2, scr, 3, g, row);
         const bool in_loss = valid && (p.mask == nullptr || p.mask[pix] != 0);
         const double nv = p.acc[3];
         const float scale = nv > 0.0 ? (float)((double)p.cfg.lambda_f / nv) : 0.f;
@@ -282,30 +293,33 @@ struct FhatEpi {
                 b = scale * (-p.cfg.lambda_cos / 1e-8f - l2c);
             }
         }
-        if (valid) {
+        if (valid && g == 0) {
             p.row[4 * pix] = a;
             p.row[4 * pix + 1] = b;
             p.row[4 * pix + 2] = a * nh2 + b * dot;
             p.row[4 * pix + 3] = cs;
         }
-        double lc = in_loss ? 1.0 - (double)cs : 0.0, le = in_loss ? (double)e2 : 0.0;
+        if (g == 0) {
+            double lc = in_loss ? 1.0 - (double)cs : 0.0, le = in_loss ? (double)e2 : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lc += __shfl_xor_sync(0xffffffffu, lc, o);
-            le += __shfl_xor_sync(0xffffffffu, le, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&p.acc[0], lc);
-            atomicAdd(&p.acc[1], le);
-        }
-        for (int c0 = 0; c0 < p.D; c0 += 32) {
-            tc::tmem_ld32(taddr + c0, h);
-            if (valid) {
-                load_target32(p.F, p.F_dtype, pix * p.D + c0, f);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) h[i] = a * h[i] + b * f[i];
-                store_row_bf16x32(p.dF + pix * p.D + c0, h);
+            for (int o = 16; o > 0; o >>= 1) {
+                lc += __shfl_xor_sync(0xffffffffu, lc, o);
+                le += __shfl_xor_sync(0xffffffffu, le, o);
             }
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&p.acc[0], lc);
+                atomicAdd(&p.acc[1], le);
+            }
+        }
+        load_target32(p.F, p.F_dtype, frow + 32 * g, f);
+        for (int c0 = 32 * g; c0 < p.D; c0 += step) {
+            if (c0 + step < p.D) load_target32(p.F, p.F_dtype, frow + c0 + step, fn);
+            tc::tmem_ld32(taddr + c0, h);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) h[i] = a * h[i] + b * f[i];
+            if (valid) store_row_bf16x32(p.dF + pix * p.D + c0, h);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) f[i] = fn[i];
         }
     }
 };
@@ -316,32 +330,35 @@ struct DsParams {
     int M;
     const bf16* A;
     const float* row;
-    bf16* dS;   // n x M
+    bf16* dS;  // n x M
 };
 
 template <int BN_>
 struct DsEpi {
-    static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_;
+    static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_, EPI_WG = 2;
     static constexpr bool A_MN = false, B_MN = false;
     using Params = DsParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int, int g, float*) {
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
+        const int64_t arow = valid ? pix * p.M : 0;
         const float rd = valid ? p.row[4 * pix + 2] : 0.f;
-        float g[32], a[32];
-        for (int c0 = 0; c0 < p.M; c0 += 32) {
-            tc::tmem_ld32(taddr + c0, g);
-            if (valid) {
-                load_row_bf16x32(p.A + pix * p.M + c0, a);
+        const int step = 32 * EPI_WG;
+        float dA[32], a[32], an[32];
+        load_row_bf16x32(p.A + arow + 32 * g, a);
+        for (int c0 = 32 * g; c0 < p.M; c0 += step) {
+            if (c0 + step < p.M) load_row_bf16x32(p.A + arow + c0 + step, an);
+            tc::tmem_ld32(taddr + c0, dA);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) g[i] = a[i] * (g[i] - rd);
-                store_row_bf16x32(p.dS + pix * p.M + c0, g);
-            }
+            for (int i = 0; i < 32; ++i) dA[i] = a[i] * (dA[i] - rd);
+            if (valid) store_row_bf16x32(p.dS + pix * p.M + c0, dA);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) a[i] = an[i];
         }
     }
 };
 
-// G4: dQ = c dS K (the first d of BN columns).
+// G4: dQ = c dS K (the first d of the 64 padded query columns).
 struct DqParams {
     int64_t n;
     int d;
@@ -351,19 +368,28 @@ struct DqParams {
 
 template <int BN_>
 struct DqEpi {
-    static constexpr int BN = BN_, STAGES = 6, BOX_B = BN_;
+    static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
     using Params = DqParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int) {
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int, int, float*) {
         const int64_t pix = (int64_t)m0 + row;
         float v[32];
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 32) {
+            if (c0 >= p.d) break;  // d is CTA-uniform
             tc::tmem_ld32(taddr + c0, v);
-            if (pix < p.n)
+            if (pix < p.n) {
+                float4* d4 = reinterpret_cast<float4*>(p.dQ + pix * p.d + c0);
+                if (c0 + 32 <= p.d) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    if (c0 + i < p.d) p.dQ[pix * p.d + c0 + i] = p.c * v[i];
+                    for (int q = 0; q < 8; ++q)
+                        d4[q] = make_float4(p.c * v[4 * q], p.c * v[4 * q + 1], p.c * v[4 * q + 2], p.c * v[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)  // d = 16
+                        d4[q] = make_float4(p.c * v[4 * q], p.c * v[4 * q + 1], p.c * v[4 * q + 2], p.c * v[4 * q + 3]);
+                }
+            }
         }
     }
 };
@@ -376,10 +402,10 @@ struct PartParams {
 
 template <int BN_>
 struct PartEpi {
-    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_;
+    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_, EPI_WG = 1;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
     using Params = PartParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int n0, int z) {
+    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int n0, int z, int, float*) {
         const int j = m0 + row;
         float v[32];
 #pragma unroll
@@ -460,7 +486,7 @@ latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 gri
     auto kern = tc::tc_gemm_kernel<Epi>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "tc_gemm smem attribute");
-    kern<<<grid, tc::kGemmThreads, smem, st>>>(a, b, g, p, err);
+    kern<<<grid, tc::gemm_threads(Epi::EPI_WG), smem, st>>>(a, b, g, p, err);
     LAT_CHECK_LAUNCH("tc_gemm_kernel");
     return LATENTAM_OK;
 }

@@ -15,8 +15,8 @@
 namespace lat {
 namespace tc {
 
-constexpr int kGemmThreads = 192;
 constexpr int kTileM = 128;
+constexpr int kScratchBytes = 8 * 2 * kTileM * 4;  // epilogue row-reduction scratch: 8 slots x 2 groups
 constexpr int kChunkK = 64;                       // BF16 elements per 128-byte row
 constexpr uint32_t kTileABytes = kTileM * 128;    // 16 KB
 
@@ -26,7 +26,38 @@ __host__ __device__ constexpr uint32_t tmem_cols_for(int n) {
 
 template <int BN, int STAGES>
 __host__ __device__ constexpr size_t gemm_smem_bytes() {
-    return (size_t)STAGES * (kTileABytes + (size_t)BN * 128) + 1024 /* alignment */ + 256 /* barriers */;
+    return (size_t)STAGES * (kTileABytes + (size_t)BN * 128) + 1024 /* alignment */ + 256 /* barriers */ +
+           kScratchBytes;
+}
+
+__host__ __device__ constexpr int gemm_threads(int epi_warpgroups) { return 64 + 128 * epi_warpgroups; }
+
+// Barrier among the epilogue threads only (named barrier 1).
+__device__ __forceinline__ void epi_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Sum (or max) of one value per row over the G epilogue warpgroups, through shared memory.
+// `slot` (0..7) must differ between reductions of the same tile.
+template <int G>
+__device__ __forceinline__ float group_sum(float v, float* scratch, int slot, int g, int row) {
+    if (G == 1) return v;
+    scratch[(slot * 2 + g) * kTileM + row] = v;
+    epi_sync(128 * G);
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < G; ++k) s += scratch[(slot * 2 + k) * kTileM + row];
+    return s;
+}
+template <int G>
+__device__ __forceinline__ float group_max(float v, float* scratch, int slot, int g, int row) {
+    if (G == 1) return v;
+    scratch[(slot * 2 + g) * kTileM + row] = v;
+    epi_sync(128 * G);
+    float s = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < G; ++k) s = fmaxf(s, scratch[(slot * 2 + k) * kTileM + row]);
+    return s;
 }
 
 struct GemmGrid {
@@ -37,10 +68,12 @@ struct GemmGrid {
 // Epi must provide: static constexpr int BN, STAGES, BOX_B (rows per TMA box of a K-major B,
 // divides BN, <= 256); static constexpr bool A_MN, B_MN (operand stored MN-major: the tile is
 // loaded as 64 (MN) x 64 (K) boxes of a row-major K x MN matrix, x = MN, y = K); struct
-// Params; static __device__ void run(const Params&, uint32_t taddr_row, int row, int m0,
-// int n0, int z) executed by the 128 epilogue threads (warp-convergent).
+// Params; static constexpr int EPI_WG (1 or 2 epilogue warpgroups: warpgroup g owns the
+// 32-column chunks c with c % EPI_WG == g of every row); static __device__ void run(const Params&,
+// uint32_t taddr_row, int row, int m0, int n0, int z, int g, float* scratch) executed by the
+// 128 * EPI_WG epilogue threads (warp-convergent).
 template <class Epi>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmGrid g,
                    typename Epi::Params ep, int* __restrict__ err) {
     constexpr int BN = Epi::BN;
@@ -64,6 +97,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     uint64_t* accum = empty + STAGES;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* decision = abort_flag + 1;
+    float* scratch = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTileM;
@@ -160,11 +195,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const bool ready = mbar_wait(accum, 0, abort_flag);
         tc_fence_after();
         const int quarter = warp & 3;
+        const int group = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
         if (!ready) *abort_flag = 1;
-        // one warp-uniform decision: the epilogue's TMEM loads are warp-collective
-        const bool go = __all_sync(0xffffffffu, ready && nk > 0 && !*abort_flag);
-        if (go) Epi::run(ep, tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z);
+        // one CTA-uniform decision, taken by one thread: the epilogue's TMEM loads are
+        // warp-collective and its row reductions synchronise all epilogue warps
+        epi_sync(128 * Epi::EPI_WG);
+        if (threadIdx.x == 64) *decision = (nk > 0 && !*abort_flag) ? 1 : 0;
+        epi_sync(128 * Epi::EPI_WG);
+        if (*decision)
+            Epi::run(ep, tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch);
         tc_fence_before();
     }
     __syncthreads();
