@@ -184,10 +184,13 @@ struct SoftmaxParams {
 
 template <int BN_>
 struct SoftmaxEpi {
-    static constexpr int BN = BN_, STAGES = 1, BOX_B = BN_ <= 256 ? BN_ : 256, EPI_WG = 2;
+    static constexpr int BN = BN_, STAGES = 1, BOX_B = BN_ <= 256 ? BN_ : 256, EPI_WG = 2, E_BOXES = 0;
     static constexpr bool A_MN = false, B_MN = false;
     using Params = SoftmaxParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int, int g, float* scr) {
+    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+        const uint32_t taddr = ec.taddr;
+        const int row = ec.row, m0 = ec.m0, g = ec.g;
+        float* scr = ec.scratch;
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
         float v[32];
@@ -235,12 +238,25 @@ struct FhatParams {
     float* Fout;  // n x D FP32 Fhat (inference form: no loss) or NULL
 };
 
-template <int BN_>
+// ETILE: the BF16 target rows come through shared memory (TMA, after the MMAs); otherwise
+// (FP32 targets) each thread reads its own row from global memory, one chunk ahead.
+template <int BN_, bool ETILE>
 struct FhatEpi {
     static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_, EPI_WG = 2;
+    static constexpr int E_BOXES = ETILE ? BN_ / 64 : 0;
     static constexpr bool A_MN = false, B_MN = true;  // B = V (atoms x features), features contiguous
     using Params = FhatParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int, int g, float* scr) {
+    static __device__ __forceinline__ void target(const Params& p, const tc::EpiCtx& ec, int64_t frow, int c0,
+                                                  float (&f)[32]) {
+        if (ETILE)
+            ec.row32(c0, f);
+        else
+            load_target32(p.F, p.F_dtype, frow + c0, f);
+    }
+    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+        const uint32_t taddr = ec.taddr;
+        const int row = ec.row, m0 = ec.m0, g = ec.g;
+        float* scr = ec.scratch;
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
         const int step = 32 * EPI_WG;
@@ -257,10 +273,12 @@ struct FhatEpi {
             return;
         }
         const int64_t frow = valid ? pix * p.D : 0;  // invalid rows read row 0 (discarded)
+        if (ETILE)
+            for (int b = 0; b < E_BOXES; ++b) (void)ec.wait_box(b);  // a timeout raises the error flag
         float dot = 0.f, nh2 = 0.f, nf2 = 0.f, e2 = 0.f;
-        load_target32(p.F, p.F_dtype, frow + 32 * g, f);
+        target(p, ec, frow, 32 * g, f);
         for (int c0 = 32 * g; c0 < p.D; c0 += step) {
-            if (c0 + step < p.D) load_target32(p.F, p.F_dtype, frow + c0 + step, fn);
+            if (c0 + step < p.D) target(p, ec, frow, c0 + step, fn);
             tc::tmem_ld32(taddr + c0, h);
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
@@ -311,9 +329,9 @@ struct FhatEpi {
                 atomicAdd(&p.acc[1], le);
             }
         }
-        load_target32(p.F, p.F_dtype, frow + 32 * g, f);
+        target(p, ec, frow, 32 * g, f);
         for (int c0 = 32 * g; c0 < p.D; c0 += step) {
-            if (c0 + step < p.D) load_target32(p.F, p.F_dtype, frow + c0 + step, fn);
+            if (c0 + step < p.D) target(p, ec, frow, c0 + step, fn);
             tc::tmem_ld32(taddr + c0, h);
 #pragma unroll
             for (int i = 0; i < 32; ++i) h[i] = a * h[i] + b * f[i];
@@ -335,25 +353,23 @@ struct DsParams {
 
 template <int BN_>
 struct DsEpi {
+    // the attention rows of the tile come through shared memory
     static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_, EPI_WG = 2;
+    static constexpr int E_BOXES = BN_ / 64;
     static constexpr bool A_MN = false, B_MN = false;
     using Params = DsParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int, int g, float*) {
-        const int64_t pix = (int64_t)m0 + row;
+    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+        const int64_t pix = (int64_t)ec.m0 + ec.row;
         const bool valid = pix < p.n;
-        const int64_t arow = valid ? pix * p.M : 0;
         const float rd = valid ? p.row[4 * pix + 2] : 0.f;
-        const int step = 32 * EPI_WG;
-        float dA[32], a[32], an[32];
-        load_row_bf16x32(p.A + arow + 32 * g, a);
-        for (int c0 = 32 * g; c0 < p.M; c0 += step) {
-            if (c0 + step < p.M) load_row_bf16x32(p.A + arow + c0 + step, an);
-            tc::tmem_ld32(taddr + c0, dA);
+        for (int b = 0; b < E_BOXES; ++b) (void)ec.wait_box(b);
+        float dA[32], a[32];
+        for (int c0 = 32 * ec.g; c0 < p.M; c0 += 32 * EPI_WG) {
+            ec.row32(c0, a);
+            tc::tmem_ld32(ec.taddr + c0, dA);
 #pragma unroll
             for (int i = 0; i < 32; ++i) dA[i] = a[i] * (dA[i] - rd);
             if (valid) store_row_bf16x32(p.dS + pix * p.M + c0, dA);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) a[i] = an[i];
         }
     }
 };
@@ -368,10 +384,12 @@ struct DqParams {
 
 template <int BN_>
 struct DqEpi {
-    static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1;
+    static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
     using Params = DqParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int, int, int, float*) {
+    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+        const uint32_t taddr = ec.taddr;
+        const int row = ec.row, m0 = ec.m0;
         const int64_t pix = (int64_t)m0 + row;
         float v[32];
 #pragma unroll
@@ -402,10 +420,12 @@ struct PartParams {
 
 template <int BN_>
 struct PartEpi {
-    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_, EPI_WG = 1;
+    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
     using Params = PartParams;
-    static __device__ void run(const Params& p, uint32_t taddr, int row, int m0, int n0, int z, int, float*) {
+    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+        const uint32_t taddr = ec.taddr;
+        const int row = ec.row, m0 = ec.m0, n0 = ec.n0, z = ec.z;
         const int j = m0 + row;
         float v[32];
 #pragma unroll
@@ -480,13 +500,13 @@ latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_
 
 template <class Epi>
 latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 grid, tc::GemmGrid g,
-                            const typename Epi::Params& p, int* err, cudaStream_t st) {
+                            const typename Epi::Params& p, int* err, cudaStream_t st, const CUtensorMap* emap = nullptr) {
     constexpr size_t smem = tc::gemm_smem_bytes<Epi::BN, Epi::STAGES>();
     static_assert(smem <= 227 * 1024, "tile does not fit in shared memory");
     auto kern = tc::tc_gemm_kernel<Epi>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "tc_gemm smem attribute");
-    kern<<<grid, tc::gemm_threads(Epi::EPI_WG), smem, st>>>(a, b, g, p, err);
+    kern<<<grid, tc::gemm_threads(Epi::EPI_WG), smem, st>>>(a, b, emap ? *emap : a, g, p, err);
     LAT_CHECK_LAUNCH("tc_gemm_kernel");
     return LATENTAM_OK;
 }
@@ -578,8 +598,15 @@ latentam_status tc_fhat(const TcBuffers& b, int64_t n, int M, int D, const FhatP
     LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, 64));
     const dim3 grid(cdiv(n, kTileM), 1, 1);
     const tc::GemmGrid g{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
-    if (D <= 256) return launch_gemm<FhatEpi<256>>(mA, mV, grid, g, fp, b.err, st);
-    return launch_gemm<FhatEpi<512>>(mA, mV, grid, g, fp, b.err, st);
+    if (fp.Fout == nullptr && fp.F_dtype == LATENTAM_DTYPE_BF16) {
+        // BF16 targets: the tile's target rows are TMA-loaded into shared memory for the epilogue
+        CUtensorMap mF;
+        LAT_TRY(bf16_map(&mF, fp.F, D, n, D, kTileM));
+        if (D <= 256) return launch_gemm<FhatEpi<256, true>>(mA, mV, grid, g, fp, b.err, st, &mF);
+        return launch_gemm<FhatEpi<512, true>>(mA, mV, grid, g, fp, b.err, st, &mF);
+    }
+    if (D <= 256) return launch_gemm<FhatEpi<256, false>>(mA, mV, grid, g, fp, b.err, st);
+    return launch_gemm<FhatEpi<512, false>>(mA, mV, grid, g, fp, b.err, st);
 }
 
 }  // namespace
@@ -622,10 +649,12 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
         DsParams dp{n, M, b.A, b.row, b.dS};
         const dim3 grow(cdiv(n, kTileM), 1, 1);
         const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
+        CUtensorMap mAe;  // attention rows for the epilogue
+        LAT_TRY(bf16_map(&mAe, b.A, M, n, M, kTileM));
         if (M <= 256)
-            LAT_TRY(launch_gemm<DsEpi<256>>(mdF, mV, grow, g3, dp, b.err, st));
+            LAT_TRY(launch_gemm<DsEpi<256>>(mdF, mV, grow, g3, dp, b.err, st, &mAe));
         else
-            LAT_TRY(launch_gemm<DsEpi<512>>(mdF, mV, grow, g3, dp, b.err, st));
+            LAT_TRY(launch_gemm<DsEpi<512>>(mdF, mV, grow, g3, dp, b.err, st, &mAe));
         // G4: dQ = c dS K, B = K padded read MN-major (queries x atoms)
         if (a.dQ) {
             LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, kTileM));

@@ -69,13 +69,45 @@ struct GemmGrid {
 // divides BN, <= 256); static constexpr bool A_MN, B_MN (operand stored MN-major: the tile is
 // loaded as 64 (MN) x 64 (K) boxes of a row-major K x MN matrix, x = MN, y = K); struct
 // Params; static constexpr int EPI_WG (1 or 2 epilogue warpgroups: warpgroup g owns the
-// 32-column chunks c with c % EPI_WG == g of every row); static __device__ void run(const Params&,
-// uint32_t taddr_row, int row, int m0, int n0, int z, int g, float* scratch) executed by the
-// 128 * EPI_WG epilogue threads (warp-convergent).
+// 32-column chunks c with c % EPI_WG == g of every row); static constexpr int E_BOXES (number
+// of 64-column boxes of a row-major BF16 "epilogue operand" (tmE) loaded for the tile's 128
+// rows into the pipeline shared memory once the MMAs are done, 0 for none); static __device__
+// void run(const Params&, const EpiCtx&) executed by the 128 * EPI_WG epilogue threads
+// (warp-convergent).
+struct EpiCtx {
+    uint32_t taddr;        // TMEM address of this thread's row, column 0
+    int row, m0, n0, z;    // tile row owned by this thread, tile origin, K split
+    int g;                 // epilogue warpgroup
+    float* scratch;        // row-reduction scratch
+    const uint8_t* etile;  // epilogue operand tile (128-byte swizzled 64 x 128 boxes), or null
+    uint64_t* ebar;        // one barrier per box
+    volatile int* abort;
+
+    // Wait for box b of the epilogue operand (bounded; false if it gave up).
+    __device__ __forceinline__ bool wait_box(int b) const { return mbar_wait(&ebar[b], 0, abort); }
+    // 32 BF16 values of this thread's row from column c0 (a multiple of 32) of the operand.
+    __device__ __forceinline__ void row32(int c0, float (&v)[32]) const {
+        const uint8_t* base = etile + (c0 >> 6) * (kTileM * 128) + row * 128;
+        const int j0 = (c0 & 63) >> 3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 u = *reinterpret_cast<const uint4*>(base + (((j0 + q) ^ (row & 7)) << 4));
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[h]));
+                v[8 * q + 2 * h] = f.x;
+                v[8 * q + 2 * h + 1] = f.y;
+            }
+        }
+    }
+};
+
 template <class Epi>
 __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmGrid g,
-                   typename Epi::Params ep, int* __restrict__ err) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmE, GemmGrid g, typename Epi::Params ep,
+                   int* __restrict__ err) {
     constexpr int BN = Epi::BN;
     constexpr int STAGES = Epi::STAGES;
     constexpr int BOX_B = Epi::BOX_B;
@@ -89,6 +121,9 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
     static_assert(BN % 16 == 0 && SUBN % 16 == 0 && SUBN <= 256, "MMA N must be a multiple of 16, <= 256");
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
     static_assert(!B_MN || SUBN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
+    constexpr int E_BOXES = Epi::E_BOXES;
+    static_assert(E_BOXES <= 8 && (uint32_t)E_BOXES * kTileM * 128 <= STAGES * STAGE_BYTES,
+                  "the epilogue operand must fit in the pipeline shared memory");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -98,6 +133,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* decision = abort_flag + 1;
+    uint64_t* ebar = reinterpret_cast<uint64_t*>(tmem_slot + 4);  // 8-byte aligned, 8 barriers
     float* scratch = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -113,6 +149,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(accum, 1);
+        for (int b = 0; b < E_BOXES; ++b) mbar_init(&ebar[b], 1);
         *abort_flag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmA);
@@ -159,6 +196,19 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
             if (*abort_flag) {
                 for (int i = max(0, issued - STAGES); i < issued; ++i)
                     (void)mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u, nullptr);
+            } else if (E_BOXES > 0) {
+                // the pipeline buffers are free once every MMA has completed: bring in the
+                // epilogue operand rows of this tile
+                if (mbar_wait(accum, 0, abort_flag) && !*abort_flag) {
+                    prefetch_tmap(&tmE);
+                    for (int b = 0; b < E_BOXES; ++b) {
+                        mbar_expect_tx(&ebar[b], kTileM * 128);
+                        tma_load_2d(smem + b * (kTileM * 128), &tmE, &ebar[b], 64 * b, m0);
+                    }
+                    for (int b = 0; b < E_BOXES; ++b) (void)mbar_wait(&ebar[b], 0, nullptr);
+                } else {
+                    *abort_flag = 1;
+                }
             }
         }
     } else if (warp == 1) {
@@ -203,8 +253,11 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
         epi_sync(128 * Epi::EPI_WG);
         if (threadIdx.x == 64) *decision = (nk > 0 && !*abort_flag) ? 1 : 0;
         epi_sync(128 * Epi::EPI_WG);
-        if (*decision)
-            Epi::run(ep, tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch);
+        if (*decision) {
+            EpiCtx ec{tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch,
+                      E_BOXES > 0 ? smem : nullptr, ebar, abort_flag};
+            Epi::run(ep, ec);
+        }
         tc_fence_before();
     }
     __syncthreads();
