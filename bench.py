@@ -10,7 +10,10 @@ Workload (the single-keyframe room configuration): 300k Gaussians on the surface
 6x5x3 m room with 20 boxes, 640x480 pinhole view, d = 32, M = 256, D = 512, FP32 end to
 end; seeded synthetic data standing in for the paper's RGB-D + CLIP/SAM keyframes.
 
-  python bench.py [--gpus N --steps K --warmup W] [--precision fp32|bf16] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--precision both|fp32|bf16] [--impl reference]
+
+By default both precision forms run: the plain FP32 form (CUDA-core decode) gives the
+headline value, and the BF16 form (tcgen05 tensor-core decode) is reported under "forms".
 
 Under torchrun (N > 1) every rank optimises its own keyframe (replicas, weak scaling); the
 timed region is bracketed by a barrier and a device synchronisation and the slowest rank's
@@ -20,7 +23,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -43,7 +45,8 @@ def _args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    p.add_argument("--precision", choices=["both", "fp32", "bf16"], default="both",
+                   help="both: the FP32 form is the headline value, the BF16 tensor-core form is reported beside it")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -179,20 +182,14 @@ def decode_flops(n, M, D, d):
     return 6.0 * n * M * D + 6.0 * n * M * d
 
 
-def run_ours(args, world, rank, local):
+def _measure(args, world, rank, local, scene, prec, dist):
+    """Time args.steps steps of one precision form; returns its numbers (rank 0 view)."""
     import numpy as np
     import torch
 
     from paper_2602_12314_gb300 import _lib as L
     from paper_2602_12314_gb300 import api
 
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prec = api.FP32 if args.precision == "fp32" else api.BF16
-    scene = _scene(args.seed + rank)
     ctx = api.Context(local)
     target_dtype = torch.float32 if prec == api.FP32 else torch.bfloat16
     st = api.LatentStep(ctx, scene, precision=prec, target_dtype=target_dtype)
@@ -203,6 +200,13 @@ def run_ours(args, world, rank, local):
     def barrier():
         if dist is not None:
             dist.barrier()
+
+    def max_over_ranks(ms):
+        if dist is None:
+            return ms
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     # ---- device-resident timed region --------------------------------------------------
     ctx.profile(True)
@@ -220,14 +224,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier()
     launches = L.load().latentam_launch_count() - launches0
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
     clk = clocks.stop()
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     value = world * args.steps / (ms / 1e3)
 
     # ---- end to end through the public API, host buffers ----------------------------------
@@ -250,18 +250,10 @@ def run_ours(args, world, rank, local):
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        ems = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(e0.elapsed_time(e1))
         e2e = {"value": world * args.steps / (ems / 1e3), "unit": "iters/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
-
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return
+    ctx.close()
 
     # ---- roofline of the dominant stage (decode + loss + decode backward) -------------------
     peaks, peak_src = _peaks()
@@ -280,11 +272,34 @@ def run_ours(args, world, rank, local):
                 "traffic": None, "algorithmic_per_launch": flops}
     else:
         peak = float(peaks["bf16_tflops_sustained"])
-        roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 kernels)", "achieved": flops / dec_avg_s / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "peak_source": f"bf16 sustained, {peak_src}", "traffic": None,
-                "algorithmic_per_launch": flops}
+        roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 GEMM kernels + their epilogues)",
+                "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"bf16 sustained, {peak_src}", "traffic": None, "algorithmic_per_launch": flops}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    return {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": int(launches), "e2e": e2e,
+            "roofline": roof, "clocks": clk, "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "dtype": "f32" if prec == api.FP32 else "bf16"}
 
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2602_12314_gb300 import api
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    scene = _scene(args.seed + rank)
+    forms = ["fp32", "bf16"] if args.precision == "both" else [args.precision]
+    res = {f: _measure(args, world, rank, local, scene, api.FP32 if f == "fp32" else api.BF16, dist) for f in forms}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    head = res[forms[0]]
+    n = scene.camera.n_pixels
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -299,20 +314,23 @@ def run_ours(args, world, rank, local):
                "kind": "oracle",
                "sample": "one FP64 oracle iteration (fwd, bwd, Adam) on the 160x120 central crop with all 300k "
                          f"Gaussians, {dt:.2f} s; scaled by the pixel fraction {frac:.4f} to the full frame"}
-
     line = {
-        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == api.FP32 else "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": world,
-                   "n_pixels": n, "gaussians": scene.n, "d": d, "M": M, "D": D,
-                   "l2": "inputs larger than L2 (target features %.0f MB per step)" % (scene.F.nbytes / 1e6),
+        "metric": METRIC, "value": head["value"], "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": forms[0], "global_batch": world,
+                   "n_pixels": n, "gaussians": scene.n, "d": scene.d, "M": scene.M, "D": scene.D,
+                   "l2": "inputs larger than L2 (target features %.0f MB FP32 / %.0f MB BF16 per step)"
+                         % (scene.F.nbytes / 1e6, scene.F.nbytes / 2e6),
                    "parallelism": f"replicas x{world}"},
-        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"], "cpu_baseline": cpu,
+        "clocks": head["clocks"], "stages_ms_per_step": head["stages_ms_per_step"],
     }
+    if len(forms) > 1:
+        line["forms"] = {f: {k: res[f][k] for k in ("value", "ms_per_step", "dtype", "e2e", "roofline",
+                                                    "gpu_launches", "clocks", "stages_ms_per_step")}
+                         for f in forms}
     print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 
