@@ -1,7 +1,9 @@
 // Adam update of several tensors in one launch (the optimiser of the latent step; the paper
-// gives only lr = 0.01 for the dictionary, Sec. IV-A).  Grid-stride over the concatenation
-// of the tensors, float4 where the sizes allow.
+// gives only lr = 0.01 for the dictionary, Sec. IV-A).  Each tensor gets a share of the
+// blocks in proportion to its size and is streamed as float4.
 #include <math.h>
+
+#include <algorithm>
 
 #include "internal.cuh"
 
@@ -12,25 +14,50 @@ constexpr int kMaxTensors = 8;
 
 struct AdamBatch {
     AdamTensor t[kMaxTensors];
-    int64_t start[kMaxTensors + 1];  // prefix sums of sizes
+    int block_start[kMaxTensors + 1];  // first block of each tensor
     int count;
-    float beta1, beta2, eps, bc1, bc2;
+    float beta1, beta2, eps, inv_bc1, inv_bc2;  // inverse bias corrections 1 / (1 - beta^step)
 };
 
 __device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, const AdamBatch& b) {
     m = b.beta1 * m + (1.0f - b.beta1) * g;
     v = b.beta2 * v + (1.0f - b.beta2) * g * g;
-    const float mh = m / b.bc1, vh = v / b.bc2;
+    const float mh = m * b.inv_bc1, vh = v * b.inv_bc2;
     p -= lr * mh / (sqrtf(vh) + b.eps);
 }
 
+// Each tensor owns a contiguous range of blocks (block_start); a block streams its share of
+// the tensor as float4 when the tensor's arrays are 16-byte aligned, element-wise otherwise.
 __global__ void __launch_bounds__(256) adam_kernel(AdamBatch b) {
-    const int64_t total = b.start[b.count];
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int k = 0;
-        while (k + 1 < b.count && e >= b.start[k + 1]) ++k;
-        const int64_t i = e - b.start[k];
-        const AdamTensor& T = b.t[k];
+    int k = 0;
+    while (k + 1 < b.count && (int)blockIdx.x >= b.block_start[k + 1]) ++k;
+    const AdamTensor& T = b.t[k];
+    const int nblk = b.block_start[k + 1] - b.block_start[k];
+    const int64_t tid = (int64_t)(blockIdx.x - b.block_start[k]) * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)nblk * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(T.p) | reinterpret_cast<uintptr_t>(T.g) |
+                       reinterpret_cast<uintptr_t>(T.m) | reinterpret_cast<uintptr_t>(T.v)) & 15u) == 0;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t n4 = T.n / 4;
+        float4* p4 = reinterpret_cast<float4*>(T.p);
+        const float4* g4 = reinterpret_cast<const float4*>(T.g);
+        float4* m4 = reinterpret_cast<float4*>(T.m);
+        float4* v4 = reinterpret_cast<float4*>(T.v);
+        for (int64_t i = tid; i < n4; i += stride) {
+            float4 p = p4[i], m = m4[i], v = v4[i];
+            const float4 g = g4[i];
+            adam_one(p.x, g.x, m.x, v.x, T.lr, b);
+            adam_one(p.y, g.y, m.y, v.y, T.lr, b);
+            adam_one(p.z, g.z, m.z, v.z, T.lr, b);
+            adam_one(p.w, g.w, m.w, v.w, T.lr, b);
+            p4[i] = p;
+            m4[i] = m;
+            v4[i] = v;
+        }
+        done = n4 * 4;
+    }
+    for (int64_t i = done + tid; i < T.n; i += stride) {
         float p = T.p[i], m = T.m[i], v = T.v[i];
         adam_one(p, T.g[i], m, v, T.lr, b);
         T.p[i] = p;
@@ -57,18 +84,23 @@ latentam_status launch_adam(latentam_ctx* ctx, const AdamTensor* t, int count, f
     b.beta1 = beta1;
     b.beta2 = beta2;
     b.eps = eps;
-    b.bc1 = (float)(1.0 - pow((double)beta1, (double)step));
-    b.bc2 = (float)(1.0 - pow((double)beta2, (double)step));
-    b.start[0] = 0;
+    b.inv_bc1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
+    b.inv_bc2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
+    // blocks in proportion to the tensor sizes (at least one each), about 4 waves in total
+    int64_t total = 0;
     for (int k = 0; k < count; ++k) {
         b.t[k] = t[k];
-        b.start[k + 1] = b.start[k] + t[k].n;
+        total += t[k].n;
     }
-    const int64_t total = b.start[count];
     if (total == 0) return LATENTAM_OK;
-    const int64_t want = (total + 255) / 256;
-    const unsigned blocks = (unsigned)(want < 8LL * ctx->num_sms ? want : 8LL * ctx->num_sms);
-    adam_kernel<<<blocks, 256, 0, st>>>(b);
+    const int64_t budget = 4LL * ctx->num_sms * 8;
+    b.block_start[0] = 0;
+    for (int k = 0; k < count; ++k) {
+        const int64_t want = (t[k].n / 4 + 255) / 256;
+        int64_t nb = std::max<int64_t>(1, std::min<int64_t>(want, (budget * t[k].n + total - 1) / total));
+        b.block_start[k + 1] = b.block_start[k] + (int)nb;
+    }
+    adam_kernel<<<(unsigned)b.block_start[count], 256, 0, st>>>(b);
     LAT_CHECK_LAUNCH("adam_kernel");
     return LATENTAM_OK;
 }

@@ -3,8 +3,9 @@
 // backward with respect to f.
 //
 // One CTA per 16x16 tile, one thread per pixel.  The tile's Gaussians are staged through
-// shared memory in batches of 256 (mean, conic/opacity, query as float4 rows), so every
-// query row is read from L2/HBM once per tile and broadcast to the 256 pixels.
+// shared memory in batches of 256 (mean, exponent coefficients/opacity, query as
+// float4 rows), so every query row is read from L2/HBM once per tile and broadcast to the
+// 256 pixels.
 #include "internal.cuh"
 
 namespace lat {
@@ -12,15 +13,20 @@ namespace {
 
 constexpr int kBatch = kTilePixels;  // 256 Gaussians staged per round
 
+// Staged form of one splat: exponent coefficients q = (-a/2, -b, -c/2, opacity) of the conic
+// (a, b, c).
+__device__ __forceinline__ float4 stage_splat(float4 co) {
+    return make_float4(__fmul_rn(-0.5f, co.x), -co.y, __fmul_rn(-0.5f, co.z), co.w);
+}
+
 // alpha of a splat at a pixel centre, or -1 when the exponent is positive.  Every rounding
-// is explicit (no contraction), so the forward and backward kernels take bit-identical
-// decisions for the same inputs.
-__device__ __forceinline__ float splat_alpha(float2 m, float4 co, float px, float py) {
+// is explicit (fused multiply-adds written out), so the forward and backward kernels take
+// bit-identical decisions for the same inputs.
+__device__ __forceinline__ float splat_alpha(float2 m, float4 q, float px, float py) {
     const float dx = __fsub_rn(m.x, px), dy = __fsub_rn(m.y, py);
-    const float quad = __fadd_rn(__fmul_rn(__fmul_rn(co.x, dx), dx), __fmul_rn(__fmul_rn(co.z, dy), dy));
-    const float power = __fsub_rn(__fmul_rn(-0.5f, quad), __fmul_rn(__fmul_rn(co.y, dx), dy));
+    const float power = __fmaf_rn(dx, __fmaf_rn(q.x, dx, __fmul_rn(q.y, dy)), __fmul_rn(__fmul_rn(q.z, dy), dy));
     if (power > 0.0f) return -1.0f;
-    return fminf(kAlphaMax, __fmul_rn(co.w, __expf(power)));
+    return fminf(kAlphaMax, __fmul_rn(q.w, __expf(power)));
 }
 
 template <int DQ>
@@ -54,7 +60,7 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, 
         if (k < range.y) {
             const int g = pair_ids[k];
             s_xy[t] = xy[g];
-            s_co[t] = conic_opac[g];
+            s_co[t] = stage_splat(conic_opac[g]);
 #pragma unroll
             for (int c = 0; c < DV; ++c) s_f[t][c] = f[(size_t)g * DV + c];
         }
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, 
         if (k < range.y) {
             const int gid = pair_ids[k];
             s_xy[t] = xy[gid];
-            s_co[t] = conic_opac[gid];
+            s_co[t] = stage_splat(conic_opac[gid]);
             s_id[t] = gid;
         }
         __syncthreads();
