@@ -45,7 +45,8 @@ def _args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=["both", "fp32", "bf16"], default="both",
+    p.add_argument("--batch", type=int, default=6, help="keyframes of the batched form (B + 1, B = 5 in Sec. IV-A)")
+    p.add_argument("--precision", choices=["both", "fp32", "bf16", "bf16_batch", "fp32_batch"], default="both",
                    help="both: the FP32 form is the headline value, the BF16 tensor-core form is reported beside it")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -182,8 +183,10 @@ def decode_flops(n, M, D, d):
     return 6.0 * n * M * D + 6.0 * n * M * d
 
 
-def _measure(args, world, rank, local, scene, prec, dist):
-    """Time args.steps steps of one precision form; returns its numbers (rank 0 view)."""
+def _measure(args, world, rank, local, scene, prec, dist, views=None):
+    """Time args.steps steps of one precision form; returns its numbers (rank 0 view).  With
+    `views`, a step is one iteration of the batched step over all those keyframes and the
+    value counts keyframe-iterations per second."""
     import numpy as np
     import torch
 
@@ -192,7 +195,11 @@ def _measure(args, world, rank, local, scene, prec, dist):
 
     ctx = api.Context(local)
     target_dtype = torch.float32 if prec == api.FP32 else torch.bfloat16
-    st = api.LatentStep(ctx, scene, precision=prec, target_dtype=target_dtype)
+    if views is None:
+        st = api.LatentStep(ctx, scene, precision=prec, target_dtype=target_dtype)
+    else:
+        st = api.LatentBatchStep(ctx, views, precision=prec, target_dtype=target_dtype)
+    n_frames = 1 if views is None else len(views)
     for _ in range(max(args.warmup, 3)):
         st.step(1, learn_f=True, want_loss=False)
     torch.cuda.synchronize()
@@ -228,15 +235,19 @@ def _measure(args, world, rank, local, scene, prec, dist):
     clk = clocks.stop()
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    value = world * args.steps / (ms / 1e3)
+    value = world * n_frames * args.steps / (ms / 1e3)
 
     # ---- end to end through the public API, host buffers ----------------------------------
     e2e = None
     if not args.no_e2e:
-        host = {k: torch.as_tensor(np.ascontiguousarray(getattr(scene, k)), dtype=torch.float32).pin_memory()
-                for k in ("means", "quats", "scales", "opacities")}
-        host["F"] = torch.as_tensor(scene.F, dtype=torch.float32).to(target_dtype).pin_memory()
-        host["mask"] = torch.as_tensor(scene.mask, dtype=torch.uint8).pin_memory()
+        if views is None:
+            host = {k: torch.as_tensor(np.ascontiguousarray(getattr(scene, k)), dtype=torch.float32).pin_memory()
+                    for k in ("means", "quats", "scales", "opacities")}
+            host["F"] = torch.as_tensor(scene.F, dtype=torch.float32).to(target_dtype).pin_memory()
+            host["mask"] = torch.as_tensor(scene.mask, dtype=torch.uint8).pin_memory()
+        else:  # the keyframes' targets (the map's geometry stays on the device)
+            host = {"F": torch.cat([torch.as_tensor(v.F) for v in views]).to(target_dtype).pin_memory(),
+                    "mask": torch.cat([torch.as_tensor(v.mask) for v in views]).pin_memory()}
         h2d = sum(t.numel() * t.element_size() for t in host.values())
         d2h = 8 * L.LOSS_PARTS
         barrier()
@@ -251,13 +262,13 @@ def _measure(args, world, rank, local, scene, prec, dist):
         torch.cuda.synchronize()
         barrier()
         ems = max_over_ranks(e0.elapsed_time(e1))
-        e2e = {"value": world * args.steps / (ems / 1e3), "unit": "iters/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": world * n_frames * args.steps / (ems / 1e3), "unit": "iters/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
     ctx.close()
 
     # ---- roofline of the dominant stage (decode + loss + decode backward) -------------------
     peaks, peak_src = _peaks()
-    n, M, D, d = scene.camera.n_pixels, scene.M, scene.D, scene.d
+    n, M, D, d = scene.camera.n_pixels * n_frames, scene.M, scene.D, scene.d
     dec_ms, dec_cnt = prof["decode"]
     dec_avg_s = dec_ms / max(dec_cnt, 1) / 1e3
     flops = decode_flops(n, M, D, d)
@@ -277,6 +288,7 @@ def _measure(args, world, rank, local, scene, prec, dist):
                 "peak_source": f"bf16 sustained, {peak_src}", "traffic": None, "algorithmic_per_launch": flops}
     roof["frac"] = roof["achieved"] / roof["peak"]
     return {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": int(launches), "e2e": e2e,
+            "keyframes_per_step": n_frames,
             "roofline": roof, "clocks": clk, "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "dtype": "f32" if prec == api.FP32 else "bf16"}
 
@@ -292,8 +304,15 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     scene = _scene(args.seed + rank)
-    forms = ["fp32", "bf16"] if args.precision == "both" else [args.precision]
-    res = {f: _measure(args, world, rank, local, scene, api.FP32 if f == "fp32" else api.BF16, dist) for f in forms}
+    forms = ["fp32", "bf16", "bf16_batch"] if args.precision == "both" else [args.precision]
+    res = {}
+    for f in forms:
+        views = None
+        if f.endswith("_batch"):
+            from workloads import room_views
+            views = room_views(args.seed + rank, n_views=args.batch)
+        res[f] = _measure(args, world, rank, local, scene, api.FP32 if f.startswith("fp32") else api.BF16, dist,
+                          views)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -328,8 +347,12 @@ def run_ours(args, world, rank, local):
     }
     if len(forms) > 1:
         line["forms"] = {f: {k: res[f][k] for k in ("value", "ms_per_step", "dtype", "e2e", "roofline",
-                                                    "gpu_launches", "clocks", "stages_ms_per_step")}
+                                                    "gpu_launches", "clocks", "stages_ms_per_step",
+                                                    "keyframes_per_step")}
                          for f in forms}
+        line["forms"]["bf16_batch"]["workload"] = (
+            f"{args.batch} keyframes of the room (the new keyframe + {args.batch - 1} history keyframes) "
+            "sharing the map and the dictionary, one latentam_step_batch iteration; value = keyframe-iterations/s")
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -306,6 +306,46 @@ LATENTAM_API latentam_status latentam_step(latentam_ctx* ctx, const latentam_fra
                               latentam_adam_cfg* adam, int32_t iters, int32_t learn_f,
                               latentam_precision prec, double* loss_host, latentam_stream stream);
 
+/* ---- batched step (Algorithm 1: the new keyframe plus B history keyframes) -------------- */
+
+#define LATENTAM_MAX_BATCH 32
+
+/* One keyframe of a batch: its Gaussians and camera, and the queries it renders.  Frames that
+ * view the same map pass the same f (and the same Gaussians, N and moments): their query
+ * gradients are summed before the single Adam update of f. */
+typedef struct {
+    latentam_gaussians gaussians;
+    latentam_camera camera;
+    float* f;     /* N x d */
+    float* m_f;   /* Adam moments of f */
+    float* v_f;
+} latentam_batch_frame;
+
+/* The dictionary shared by every frame: keys K (M x d), values V (M x D), trust-region centre
+ * V0 (M x D) and the Adam moments of K and V. */
+typedef struct {
+    float* K;
+    float* V;
+    const float* V0;
+    float *m_K, *v_K, *m_V, *v_V;
+    int32_t d, M, D;
+} latentam_dictionary;
+
+/* `iters` iterations over a batch of n_frames (1..LATENTAM_MAX_BATCH) keyframes that share the
+ * dictionary: every frame is projected and binned once (one synchronisation per frame for its
+ * pair count), then each iteration renders every frame into one stacked query image, decodes
+ * all stacked pixels in one call, back-propagates to every frame and takes one Adam step on
+ * (each distinct f if learn_f, K, V).  The objective pools the loss-set pixels of all frames
+ * (one |Omega|) and adds the trust-region term once.  F (sum_k H_k W_k x D, dtype F_dtype) and
+ * mask (sum_k H_k W_k, NULL = all) hold the frames' targets concatenated in frame order.
+ * adam->step and loss_host behave as in latentam_step. */
+LATENTAM_API latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam_batch_frame* frames,
+                                                 int32_t n_frames, const void* F, latentam_dtype F_dtype,
+                                                 const uint8_t* mask, latentam_dictionary* dict,
+                                                 const latentam_loss_cfg* cfg, latentam_adam_cfg* adam,
+                                                 int32_t iters, int32_t learn_f, latentam_precision prec,
+                                                 double* loss_host, latentam_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

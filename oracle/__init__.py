@@ -301,3 +301,28 @@ def iteration(scene, cfg: LossConfig | None = None, f=None, K=None, V=None, proj
     if with_df:
         out["df"] = render_frame_bwd(proj, dQ, scene.camera, np.asarray(f).shape[0], Q.shape[1])
     return out
+
+
+def iteration_batch(scenes, cfg: LossConfig | None = None) -> dict:
+    """One forward + backward over a batch of keyframes sharing the dictionary: each frame
+    rendered untiled, the loss pooled over the loss-set pixels of all frames (targets and
+    masks concatenated in frame order), one trust-region term; df summed over the frames that
+    render the same query array (frames are grouped by the identity of their f)."""
+    cfg = cfg or LossConfig()
+    s0 = scenes[0]
+    projs = [project_scene(s) for s in scenes]
+    Qs = [render_frame(p, s.f, s.camera)[0] for p, s in zip(projs, scenes)]
+    Q = np.concatenate(Qs)
+    F = np.concatenate([s.F for s in scenes])
+    mask = np.concatenate([s.mask for s in scenes])
+    S, A, Fh = decode(Q, s0.K, s0.V, cfg.c(Q.shape[1]))
+    parts, _ = loss(Fh, F, mask, s0.V, s0.V0, cfg, Q.shape[1])
+    dQ, dK, dV = backward(Q, s0.K, s0.V, s0.V0, A, Fh, F, mask, cfg)
+    df = {}
+    off = 0
+    for p, s in zip(projs, scenes):
+        n = s.camera.n_pixels
+        g = render_frame_bwd(p, dQ[off:off + n], s.camera, s.n, Q.shape[1])
+        df[id(s.f)] = df.get(id(s.f), 0.0) + g
+        off += n
+    return dict(Q=Q, loss=parts, dK=dK, dV=dV, dQ=dQ, df=df)

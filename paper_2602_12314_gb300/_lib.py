@@ -79,6 +79,17 @@ class Params(ctypes.Structure):
                 ("m_V", P), ("v_V", P), ("d", I32), ("M", I32), ("D", I32)]
 
 
+class BatchFrame(ctypes.Structure):
+    _fields_ = [("gaussians", Gaussians), ("camera", Camera), ("f", P), ("m_f", P), ("v_f", P)]
+
+
+class Dictionary(ctypes.Structure):
+    _fields_ = [("K", P), ("V", P), ("V0", P), ("m_K", P), ("v_K", P), ("m_V", P), ("v_V", P), ("d", I32),
+                ("M", I32), ("D", I32)]
+
+
+MAX_BATCH = 32
+
 _SIGS = {
     "latentam_version": ([], I32),
     "latentam_launch_count": ([], I64),
@@ -105,6 +116,9 @@ _SIGS = {
                        ctypes.POINTER(I64), ctypes.POINTER(F32), ctypes.POINTER(AdamCfg), P], I32),
     "latentam_step": ([P, ctypes.POINTER(Frame), ctypes.POINTER(Params), ctypes.POINTER(LossCfg),
                        ctypes.POINTER(AdamCfg), I32, I32, I32, ctypes.POINTER(ctypes.c_double), P], I32),
+    "latentam_step_batch": ([P, ctypes.POINTER(BatchFrame), I32, P, I32, P, ctypes.POINTER(Dictionary),
+                             ctypes.POINTER(LossCfg), ctypes.POINTER(AdamCfg), I32, I32, I32,
+                             ctypes.POINTER(ctypes.c_double), P], I32),
 }
 
 EXPORTED = tuple(_SIGS)

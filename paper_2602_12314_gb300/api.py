@@ -395,5 +395,60 @@ class LatentStep:
         return dict(cos=out[0], l2=out[1], tr=out[2], total=out[3], n_valid=out[4])
 
 
+class LatentBatchStep:
+    """Device-resident state of a batch of keyframes sharing one dictionary (the new keyframe
+    plus sampled history keyframes of Algorithm 1), driven through latentam_step_batch.
+    Scenes whose query arrays are the same object render one shared query tensor."""
+
+    def __init__(self, ctx: Context, scenes, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
+                 precision: int = FP32, target_dtype=torch.float32):
+        if not 1 <= len(scenes) <= L.MAX_BATCH:
+            raise ValueError(f"a batch holds 1..{L.MAX_BATCH} keyframes")
+        dev = torch.device("cuda", ctx.device)
+        self.ctx = ctx
+        self.cfg = cfg or LossConfig()
+        self.adam_cfg = adam_cfg or AdamConfig()
+        self.precision = int(precision)
+        t = lambda a: _dev_f32(a, dev)  # noqa: E731
+        s0 = scenes[0]
+        self.K, self.V, self.V0 = t(s0.K), t(s0.V), t(s0.V0)
+        self.mK, self.vK = torch.zeros_like(self.K), torch.zeros_like(self.K)
+        self.mV, self.vV = torch.zeros_like(self.V), torch.zeros_like(self.V)
+        self.d, self.M, self.D = s0.f.shape[1], self.V.shape[0], self.V.shape[1]
+        geo, qs = {}, {}
+        self.frames = []
+        for sc in scenes:
+            gk = id(sc.means)
+            if gk not in geo:
+                geo[gk] = tuple(t(getattr(sc, a)) for a in ("means", "quats", "scales", "opacities"))
+            qk = id(sc.f)
+            if qk not in qs:
+                f = t(sc.f)
+                qs[qk] = (f, torch.zeros_like(f), torch.zeros_like(f))
+            self.frames.append((geo[gk], qs[qk], camera_struct(sc.camera)))
+        self.queries = [q[0] for q in qs.values()]
+        self.F = torch.cat([t(sc.F) for sc in scenes]).to(target_dtype).contiguous()
+        self.mask = torch.cat([torch.as_tensor(sc.mask, dtype=torch.uint8) for sc in scenes]).to(dev).contiguous()
+
+    def step(self, iters: int = 1, learn_f: bool = True, want_loss: bool = True):
+        fr = (L.BatchFrame * len(self.frames))()
+        for k, (g, q, cam) in enumerate(self.frames):
+            fr[k].gaussians = _gaussians_struct(*g)
+            fr[k].camera = cam
+            fr[k].f, fr[k].m_f, fr[k].v_f = q[0].data_ptr(), q[1].data_ptr(), q[2].data_ptr()
+        dic = L.Dictionary(self.K.data_ptr(), self.V.data_ptr(), self.V0.data_ptr(), self.mK.data_ptr(),
+                           self.vK.data_ptr(), self.mV.data_ptr(), self.vV.data_ptr(), self.d, self.M, self.D)
+        cs = self.cfg.struct()
+        ac = self.adam_cfg.struct()
+        out = (ctypes.c_double * L.LOSS_PARTS)() if want_loss else None
+        L.check(_lib().latentam_step_batch(self.ctx.handle, fr, len(self.frames), _ptr(self.F), _target_dtype(self.F),
+                                           _ptr(self.mask), ctypes.byref(dic), ctypes.byref(cs), ctypes.byref(ac),
+                                           int(iters), int(bool(learn_f)), self.precision, out, _stream()))
+        self.adam_cfg.step = int(ac.step)
+        if out is None:
+            return None
+        return dict(cos=out[0], l2=out[1], tr=out[2], total=out[3], n_valid=out[4])
+
+
 def default_logit_scale(d: int) -> float:
     return 1.0 / math.sqrt(d)

@@ -56,6 +56,33 @@ void* ws(latentam_ctx* ctx, Slot s, size_t bytes) {
     return p;
 }
 
+void* frame_ws(latentam_ctx* ctx, int idx, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (ctx->frame_bytes[idx] >= bytes) return ctx->frame_ptr[idx];
+    size_t nb = std::max(bytes, ctx->frame_bytes[idx] + ctx->frame_bytes[idx] / 4);
+    nb = (nb + 4095) & ~(size_t)4095;
+    if (ctx->frame_ptr[idx]) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            cuda_error(e, "frame workspace regrow sync");
+            return nullptr;
+        }
+        cudaFree(ctx->frame_ptr[idx]);
+        ctx->frame_ptr[idx] = nullptr;
+        ctx->frame_bytes[idx] = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, nb);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        set_error("frame workspace allocation of %zu bytes failed: %s", nb, cudaGetErrorString(e));
+        return nullptr;
+    }
+    ctx->frame_ptr[idx] = p;
+    ctx->frame_bytes[idx] = nb;
+    return p;
+}
+
 static void prof_fold(latentam_ctx* ctx, int stage) {
     StageProfile& P = ctx->prof[stage];
     for (int i = 0; i < P.used; ++i) {
@@ -236,6 +263,8 @@ latentam_status latentam_ctx_destroy(latentam_ctx* ctx) {
         if (ctx->slot_ptr[s]) cudaFree(ctx->slot_ptr[s]);
     for (int s = 0; s < LATENTAM_NUM_STAGES; ++s)
         for (int i = 0; i < ctx->prof[s].created; ++i) cudaEventDestroy(ctx->prof[s].ev[i]);
+    for (int i = 0; i < 2 * LATENTAM_MAX_BATCH; ++i)
+        if (ctx->frame_ptr[i]) cudaFree(ctx->frame_ptr[i]);
     delete ctx;
     if (e != cudaSuccess) return cuda_error(e, "synchronise before destroy");
     return LATENTAM_OK;
@@ -541,3 +570,176 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
 }
 
 }  // extern "C"
+
+namespace {
+
+struct FrameState {
+    latentam_projected proj;
+    latentam_bins bins;
+    CamParams cam;
+    int64_t pix_off;  // first row of this frame in the stacked images
+    int group;        // index of its distinct query array
+};
+
+struct QueryGroup {
+    float *f, *m, *v, *df;
+    int32_t n;
+};
+
+}  // namespace
+
+extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam_batch_frame* frames,
+                                               int32_t n_frames, const void* F, latentam_dtype F_dtype,
+                                               const uint8_t* mask, latentam_dictionary* dict,
+                                               const latentam_loss_cfg* cfg, latentam_adam_cfg* adam, int32_t iters,
+                                               int32_t learn_f, latentam_precision prec, double* loss_host,
+                                               latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    REQUIRE(frames && dict && cfg && adam && iters >= 0, "null argument");
+    REQUIRE(n_frames >= 1 && n_frames <= LATENTAM_MAX_BATCH, "n_frames=%d outside 1..%d", n_frames,
+            LATENTAM_MAX_BATCH);
+    LAT_TRY(check_d(dict->d));
+    LAT_TRY(check_dict(dict->M, dict->D));
+    REQUIRE(dict->K && dict->V && dict->V0 && dict->m_K && dict->v_K && dict->m_V && dict->v_V,
+            "null dictionary tensor or moment");
+    REQUIRE(F && (F_dtype == LATENTAM_DTYPE_F32 || F_dtype == LATENTAM_DTYPE_BF16), "bad targets");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int d = dict->d, M = dict->M, D = dict->D;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+
+    // distinct query arrays (frames of one map share them)
+    FrameState fs[LATENTAM_MAX_BATCH];
+    QueryGroup groups[LATENTAM_MAX_BATCH];
+    int n_groups = 0;
+    int64_t total_pix = 0;
+    for (int k = 0; k < n_frames; ++k) {
+        const latentam_batch_frame& fr = frames[k];
+        LAT_TRY(check_camera(&fr.camera));
+        REQUIRE(fr.gaussians.n >= 0 && fr.f && (!learn_f || (fr.m_f && fr.v_f)), "frame %d: bad queries", k);
+        if (fr.gaussians.n > 0)
+            REQUIRE(fr.gaussians.means && fr.gaussians.quats && fr.gaussians.scales && fr.gaussians.opacities,
+                    "frame %d: null Gaussian attribute", k);
+        REQUIRE(aligned16(fr.f), "frame %d: f must be 16-byte aligned", k);
+        int gidx = -1;
+        for (int u = 0; u < n_groups; ++u)
+            if (groups[u].f == fr.f) gidx = u;
+        if (gidx < 0) {
+            gidx = n_groups++;
+            groups[gidx] = QueryGroup{fr.f, fr.m_f, fr.v_f, nullptr, fr.gaussians.n};
+        } else {
+            REQUIRE(groups[gidx].n == fr.gaussians.n && groups[gidx].m == fr.m_f && groups[gidx].v == fr.v_f,
+                    "frames sharing f must share N and the Adam moments");
+        }
+        fs[k].group = gidx;
+        fs[k].pix_off = total_pix;
+        total_pix += (int64_t)fr.camera.width * fr.camera.height;
+    }
+
+    // projection and binning of every frame (once; the geometry is fixed during the step)
+    for (int k = 0; k < n_frames; ++k) {
+        const latentam_batch_frame& fr = frames[k];
+        const int N = fr.gaussians.n;
+        const int64_t tiles = latentam_num_tiles(&fr.camera);
+        const size_t o_xy = 0, o_co = o_xy + up(8 * (size_t)N), o_dp = o_co + up(16 * (size_t)N),
+                     o_rc = o_dp + up(4 * (size_t)N), o_tt = o_rc + up(16 * (size_t)N),
+                     o_tr = o_tt + up(4 * (size_t)N), o_end = o_tr + up(8 * (size_t)tiles);
+        char* pb = static_cast<char*>(frame_ws(ctx, 2 * k, o_end));
+        if (!pb) return LATENTAM_ERR_OUT_OF_MEMORY;
+        fs[k].proj = latentam_projected{reinterpret_cast<float*>(pb + o_xy), reinterpret_cast<float*>(pb + o_co),
+                                        reinterpret_cast<float*>(pb + o_dp), reinterpret_cast<int32_t*>(pb + o_rc),
+                                        reinterpret_cast<int32_t*>(pb + o_tt)};
+        fs[k].cam = cam_params(fr.camera);
+        latentam_bins& bins = fs[k].bins;
+        bins = latentam_bins{};
+        bins.tile_ranges = reinterpret_cast<int32_t*>(pb + o_tr);
+        bins.pair_ids = static_cast<int32_t*>(ctx->frame_ptr[2 * k + 1]);
+        bins.capacity = (int64_t)(ctx->frame_bytes[2 * k + 1] / sizeof(int32_t));
+        {
+            StageTimer tm(ctx, LATENTAM_STAGE_PROJECT, st);
+            LAT_TRY(launch_project(fr.gaussians, fs[k].cam, fs[k].proj, st));
+        }
+        latentam_status s;
+        {
+            StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+            s = bin_and_sort(ctx, N, fs[k].proj, fs[k].cam, &bins, st);
+        }
+        if (s == LATENTAM_ERR_CAPACITY) {
+            bins.pair_ids = static_cast<int32_t*>(frame_ws(ctx, 2 * k + 1, sizeof(int32_t) * (size_t)bins.num_pairs));
+            if (!bins.pair_ids) return LATENTAM_ERR_OUT_OF_MEMORY;
+            bins.capacity = bins.num_pairs;
+            StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+            s = bin_and_sort(ctx, N, fs[k].proj, fs[k].cam, &bins, st);
+        }
+        LAT_TRY(s);
+    }
+
+    // stacked images, per-group query gradients, dictionary gradients
+    const size_t i_q = 0, i_t = i_q + up(4 * (size_t)total_pix * d), i_n = i_t + up(4 * (size_t)total_pix),
+                 i_dq = i_n + up(4 * (size_t)total_pix), i_end = i_dq + up(4 * (size_t)total_pix * d);
+    char* ib = static_cast<char*>(ws(ctx, WS_STEP_IMG, i_end));
+    size_t g_end = 0;
+    size_t g_df[LATENTAM_MAX_BATCH];
+    for (int u = 0; u < n_groups; ++u) {
+        g_df[u] = g_end;
+        g_end += up(4 * (size_t)groups[u].n * d);
+    }
+    const size_t g_dk = g_end, g_dv = g_dk + up(4 * (size_t)M * d), g_lp = g_dv + up(4 * (size_t)M * D);
+    g_end = g_lp + up(8 * LATENTAM_LOSS_PARTS);
+    char* gb = static_cast<char*>(ws(ctx, WS_STEP_GRAD, g_end));
+    if (!ib || !gb) return LATENTAM_ERR_OUT_OF_MEMORY;
+    float* Q = reinterpret_cast<float*>(ib + i_q);
+    float* T = reinterpret_cast<float*>(ib + i_t);
+    int32_t* nc = reinterpret_cast<int32_t*>(ib + i_n);
+    float* dQ = reinterpret_cast<float*>(ib + i_dq);
+    for (int u = 0; u < n_groups; ++u) groups[u].df = reinterpret_cast<float*>(gb + g_df[u]);
+    float* dK = reinterpret_cast<float*>(gb + g_dk);
+    float* dV = reinterpret_cast<float*>(gb + g_dv);
+    double* lp = reinterpret_cast<double*>(gb + g_lp);
+
+    for (int it = 0; it < iters; ++it) {
+        if (it == 0 || learn_f) {
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, st);
+            for (int k = 0; k < n_frames; ++k)
+                LAT_TRY(launch_render_fwd(fs[k].cam, fs[k].proj, fs[k].bins, frames[k].f, d, Q + fs[k].pix_off * d,
+                                          T + fs[k].pix_off, nc + fs[k].pix_off, st));
+        }
+        LAT_TRY(latentam_decode_loss_bwd(ctx, Q, total_pix, d, dict->K, dict->V, dict->V0, M, D, F, F_dtype, mask,
+                                         cfg, prec, lp, learn_f ? dQ : nullptr, dK, dV, stream));
+        if (learn_f) {
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, st);
+            for (int u = 0; u < n_groups; ++u) {
+                cudaError_t e = cudaMemsetAsync(groups[u].df, 0, sizeof(float) * (size_t)groups[u].n * d, st);
+                if (e != cudaSuccess) return cuda_error(e, "memset df");
+            }
+            for (int k = 0; k < n_frames; ++k)
+                if (frames[k].gaussians.n > 0)
+                    LAT_TRY(launch_render_bwd(fs[k].cam, fs[k].proj, fs[k].bins, nc + fs[k].pix_off,
+                                              dQ + fs[k].pix_off * d, d, groups[fs[k].group].df, frames[k].gaussians.n,
+                                              st, /*accumulate=*/true));
+        }
+        {
+            StageTimer tm(ctx, LATENTAM_STAGE_ADAM, st);
+            AdamTensor t[8];
+            int cnt = 0;
+            t[cnt++] = AdamTensor{dict->K, dK, dict->m_K, dict->v_K, (int64_t)M * d, adam->lr_dict};
+            t[cnt++] = AdamTensor{dict->V, dV, dict->m_V, dict->v_V, (int64_t)M * D, adam->lr_dict};
+            for (int u = 0; learn_f && u < n_groups; ++u) {
+                if (cnt == 8) {
+                    LAT_TRY(launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, st));
+                    cnt = 0;
+                }
+                t[cnt++] = AdamTensor{groups[u].f, groups[u].df, groups[u].m, groups[u].v,
+                                      (int64_t)groups[u].n * d, adam->lr_f};
+            }
+            LAT_TRY(launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, st));
+        }
+        adam->step += 1;
+    }
+    if (loss_host) {
+        cudaError_t e = cudaMemcpyAsync(loss_host, lp, sizeof(double) * LATENTAM_LOSS_PARTS, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_error(e, "copy loss");
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_error(e, "synchronise step");
+    }
+    return LATENTAM_OK;
+}

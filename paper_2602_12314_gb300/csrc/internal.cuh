@@ -86,6 +86,9 @@ struct latentam_ctx {
     size_t slot_bytes[lat::WS_NUM_SLOTS];
     int profiling;
     lat::StageProfile prof[LATENTAM_NUM_STAGES];
+    // per-frame buffers of the batched step: [2k] projection + tile ranges, [2k+1] pairs
+    void* frame_ptr[2 * LATENTAM_MAX_BATCH];
+    size_t frame_bytes[2 * LATENTAM_MAX_BATCH];
 };
 
 namespace lat {
@@ -148,9 +151,13 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t n, const latentam_projec
 latentam_status launch_render_fwd(const CamParams& cam, const latentam_projected& proj,
                                   const latentam_bins& bins, const float* f, int d, float* Q,
                                   float* T_final, int32_t* n_contrib, cudaStream_t st);
+// df = (accumulate ? df : 0) + sum_p w_ip dQ_p.
 latentam_status launch_render_bwd(const CamParams& cam, const latentam_projected& proj,
                                   const latentam_bins& bins, const int32_t* n_contrib,
-                                  const float* dQ, int d, float* df, int32_t n, cudaStream_t st);
+                                  const float* dQ, int d, float* df, int32_t n, cudaStream_t st,
+                                  bool accumulate = false);
+// Per-frame buffer `idx` of at least `bytes` (grows like ws()).
+void* frame_ws(latentam_ctx* ctx, int idx, size_t bytes);
 
 struct DecodeArgs {
     const float* Q;

@@ -207,9 +207,12 @@ latentam_status render_fwd_t(const CamParams& cam, const latentam_projected& pro
 
 template <int DQ>
 latentam_status render_bwd_t(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
-                             const int32_t* n_contrib, const float* dQ, float* df, int32_t n, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(df, 0, sizeof(float) * (size_t)n * DQ, st);
-    if (e != cudaSuccess) return cuda_error(e, "memset df");
+                             const int32_t* n_contrib, const float* dQ, float* df, int32_t n, cudaStream_t st,
+                             bool accumulate) {
+    if (!accumulate) {
+        cudaError_t e = cudaMemsetAsync(df, 0, sizeof(float) * (size_t)n * DQ, st);
+        if (e != cudaSuccess) return cuda_error(e, "memset df");
+    }
     const int tiles = cam.tiles_x * cam.tiles_y;
     render_bwd_kernel<DQ><<<tiles, kTilePixels, 0, st>>>(
         cam, reinterpret_cast<const int2*>(bins.tile_ranges), bins.pair_ids, reinterpret_cast<const float2*>(proj.xy),
@@ -233,11 +236,11 @@ latentam_status launch_render_fwd(const CamParams& cam, const latentam_projected
 
 latentam_status launch_render_bwd(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
                                   const int32_t* n_contrib, const float* dQ, int d, float* df, int32_t n,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, bool accumulate) {
     switch (d) {
-        case 16: return render_bwd_t<16>(cam, proj, bins, n_contrib, dQ, df, n, st);
-        case 32: return render_bwd_t<32>(cam, proj, bins, n_contrib, dQ, df, n, st);
-        case 64: return render_bwd_t<64>(cam, proj, bins, n_contrib, dQ, df, n, st);
+        case 16: return render_bwd_t<16>(cam, proj, bins, n_contrib, dQ, df, n, st, accumulate);
+        case 32: return render_bwd_t<32>(cam, proj, bins, n_contrib, dQ, df, n, st, accumulate);
+        case 64: return render_bwd_t<64>(cam, proj, bins, n_contrib, dQ, df, n, st, accumulate);
         default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
     }
 }

@@ -207,3 +207,20 @@ def test_adam_first_step_is_sign_and_matches_torch():
         tp.grad = torch.tensor(gs, dtype=torch.float64)
         opt.step()
     np.testing.assert_allclose(p2, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_batch_iteration_pools_frames():
+    """Pooling the loss over frames: a batch of one frame equals the single-frame iteration,
+    and a batch holding the same frame twice has the same loss, dK, dV and (summed) df."""
+    s = random_scene(8, n=60, d=4, M=6, D=10, width=18, height=14, log_scale=-2.2, mask_drop=0.2)
+    cfg = oracle.LossConfig()
+    one = oracle.iteration(s, cfg)
+    b1 = oracle.iteration_batch([s], cfg)
+    np.testing.assert_allclose(b1["loss"]["total"], one["loss"]["total"], rtol=1e-14)
+    np.testing.assert_allclose(b1["df"][id(s.f)], one["df"], rtol=1e-13, atol=1e-18)
+    b2 = oracle.iteration_batch([s, s], cfg)
+    np.testing.assert_allclose(b2["loss"]["total"], one["loss"]["total"], rtol=1e-12)
+    assert b2["loss"]["n_valid"] == 2 * one["loss"]["n_valid"]
+    for k in ("dK", "dV"):
+        np.testing.assert_allclose(b2[k], one[k], rtol=1e-11, atol=1e-16)
+    np.testing.assert_allclose(b2["df"][id(s.f)], one["df"], rtol=1e-11, atol=1e-16)

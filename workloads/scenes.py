@@ -284,6 +284,41 @@ def room_scene(seed: int = 0, n: int = 300_000, d: int = 32, M: int = 256, D: in
                  f=_f32(f), K=K, V=V, V0=V.copy(), F=_f32(F), mask=mask, camera=cam)
 
 
+def room_views(seed: int = 0, n_views: int = 6, n: int = 300_000, d: int = 32, M: int = 256, D: int = 512,
+               width: int = 640, height: int = 480, fx: float = 525.0, n_boxes: int = 20,
+               size=(6.0, 5.0, 3.0), noise: float = 0.02) -> list:
+    """Several keyframes of one room (the new keyframe plus sampled history keyframes): the
+    Gaussians, queries and dictionary of room_scene(seed) seen from n_views cameras at the
+    room centre with different seeded yaws and heights; each view has its own ray-cast target
+    map (same segment embeddings).  The scenes share their Gaussian and dictionary arrays."""
+    base = room_scene(seed, n=n, d=d, M=M, D=D, width=width, height=height, fx=fx, n_boxes=n_boxes, size=size,
+                      noise=noise)
+    rng = np.random.default_rng(seed + 1000)
+    # rebuild the room's boxes and embeddings exactly as room_scene drew them
+    rng0 = np.random.default_rng(seed)
+    _, boxes = _room_faces(rng0, size, n_boxes)
+    n_ids = n_boxes + 12
+    emb_rng = np.random.default_rng(seed + 2000)
+    emb = _normalise_rows(emb_rng.normal(size=(max(n_ids, 32), D)))
+    views = []
+    for v in range(n_views):
+        if v == 0:
+            cam = base.camera  # the new keyframe; its targets are redrawn with the shared embeddings
+        else:
+            yaw = rng.uniform(0, 2 * math.pi)
+            h = rng.uniform(1.2, 1.8)
+            centre = (size[0] / 2 + rng.uniform(-0.5, 0.5), size[1] / 2 + rng.uniform(-0.5, 0.5), h)
+            cam = _look_camera(centre, (math.cos(yaw), math.sin(yaw), 0.0), (0, 0, -1), fx, fx, width / 2,
+                               height / 2, width, height)
+        label = _raycast_labels(cam, size, boxes, n_boxes)
+        F = emb[np.maximum(label, 0)] + rng.normal(0.0, noise, size=(label.shape[0], D))
+        F = _normalise_rows(F)
+        mask = (label >= 0).astype(np.uint8)
+        F[mask == 0] = 0.0
+        views.append(dataclasses.replace(base, name=f"{base.name}[view {v}]", camera=cam, F=_f32(F), mask=mask))
+    return views
+
+
 def precision_scene(seed: int = 0, **kw) -> Scene:
     """The larger-dims room: 500k Gaussians, d = 32, M = 512, D = 1024, 640x480."""
     args = dict(n=500_000, d=32, M=512, D=1024)
