@@ -72,7 +72,8 @@ typedef int32_t latentam_status;
 
 typedef int32_t latentam_precision;
 #define LATENTAM_PREC_FP32 0 /* decode on FP32 CUDA cores, FP32 throughout */
-#define LATENTAM_PREC_BF16 1 /* decode contractions on tcgen05 tensor cores: BF16 operands, FP32 accumulation */
+#define LATENTAM_PREC_BF16 1 /* decode contractions on tcgen05 tensor cores: BF16 operands, FP32 accumulation;
+                                 M <= 1024 and D <= 1024 (else LATENTAM_ERR_UNSUPPORTED_SHAPE) */
 
 typedef int32_t latentam_dtype;
 #define LATENTAM_DTYPE_F32 0

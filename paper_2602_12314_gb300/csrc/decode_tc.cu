@@ -29,20 +29,21 @@ constexpr int kPad = 64;  // query / key rows padded to one 64-wide K chunk
 
 // ---- operand preparation ----------------------------------------------------------------
 
-// Qb[p][0..63] = bf16(Q[p][0..d)) zero-padded.
+// Qb[p][0..63] = bf16(Q[p][0..d)) zero-padded; thread t writes 8 columns (16 bytes) of row t / 8,
+// so a warp reads and writes contiguous memory.
 __global__ void prep_queries(const float* __restrict__ Q, int64_t n, int d, bf16* __restrict__ Qb) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    uint32_t w[kPad / 2];
-#pragma unroll
-    for (int k = 0; k < kPad; k += 2) {
-        const float a = k < d ? Q[p * d + k] : 0.f;
-        const float b = k + 1 < d ? Q[p * d + k + 1] : 0.f;
-        w[k / 2] = tc::pack_bf16x2(a, b);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * (kPad / 8)) return;
+    const int64_t p = t / (kPad / 8);
+    const int c = (int)(t % (kPad / 8)) * 8;
+    uint4 out = make_uint4(0u, 0u, 0u, 0u);
+    if (c < d) {  // d is a multiple of 8 and Q rows are 16-byte aligned
+        const float4 a = *reinterpret_cast<const float4*>(Q + p * d + c);
+        const float4 b = *reinterpret_cast<const float4*>(Q + p * d + c + 4);
+        out = make_uint4(tc::pack_bf16x2(a.x, a.y), tc::pack_bf16x2(a.z, a.w), tc::pack_bf16x2(b.x, b.y),
+                         tc::pack_bf16x2(b.z, b.w));
     }
-    uint4* dst = reinterpret_cast<uint4*>(Qb + p * kPad);
-#pragma unroll
-    for (int v = 0; v < kPad / 8; ++v) dst[v] = make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+    reinterpret_cast<uint4*>(Qb + p * kPad)[t % (kPad / 8)] = out;
 }
 
 // Kb[j][0..63] (zero-padded) and Vb[j][c]: BF16 copies of the dictionary.
@@ -182,49 +183,65 @@ struct SoftmaxParams {
     float* stats;  // n x 2 (row max of c S, softmax denominator), nullable
 };
 
-template <int BN_>
+// One CTA holds the logits of 256 atoms; when M > 256 the CTAs of a row block form a cluster
+// and combine their (row max, partial denominator) pairs before normalising.
 struct SoftmaxEpi {
-    static constexpr int BN = BN_, STAGES = 1, BOX_B = BN_ <= 256 ? BN_ : 256, EPI_WG = 2, E_BOXES = 0;
+    static constexpr int BN = 256, STAGES = 1, BOX_B = 256, EPI_WG = 2, E_BOXES = 0, XROUNDS = 1;
+    static constexpr int MIN_SMEM = 100 * 1024, MIN_BLOCKS = 2;  // two CTAs per SM: 2 x 256 TMEM columns
     static constexpr bool A_MN = false, B_MN = false;
     using Params = SoftmaxParams;
     static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
         const int row = ec.row, m0 = ec.m0, g = ec.g;
+        const int ncols = min(BN, p.M - ec.n0);  // atoms of this CTA's slice
         float* scr = ec.scratch;
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
         float v[32];
         float mx = -INFINITY;
-        for (int c0 = 32 * g; c0 < p.M; c0 += 32 * EPI_WG) {
+        for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) mx = fmaxf(mx, v[i]);
         }
         mx = tc::group_max<EPI_WG>(mx, scr, 0, g, row);
-        const float cm = p.c * mx;
+        float cm = p.c * mx;  // c > 0
         float sum = 0.f;
-        for (int c0 = 32 * g; c0 < p.M; c0 += 32 * EPI_WG) {
+        for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) sum += __expf(p.c * v[i] - cm);
         }
         sum = tc::group_sum<EPI_WG>(sum, scr, 1, g, row);
+        const float mine[tc::kXchgVals] = {cm, sum, 0.f, 0.f};
+        ec.exchange(mine);
+        if (ec.csize > 1) {
+            float gm = cm;
+            for (int q = 0; q < ec.csize; ++q)
+                if (q != ec.crank) gm = fmaxf(gm, ec.xval(q, 0));
+            float l = 0.f;
+            for (int q = 0; q < ec.csize; ++q)
+                l += q == ec.crank ? sum * __expf(cm - gm) : ec.xval(q, 1) * __expf(ec.xval(q, 0) - gm);
+            cm = gm;
+            sum = l;
+        }
         const float il = 1.0f / sum;
-        for (int c0 = 32 * g; c0 < p.M; c0 += 32 * EPI_WG) {
+        for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = __expf(p.c * v[i] - cm) * il;
-            if (valid) store_row_bf16x32(p.A + pix * p.M + c0, v);
+            if (valid) store_row_bf16x32(p.A + pix * p.M + ec.n0 + c0, v);
         }
-        if (valid && p.stats && g == 0) {
+        if (valid && p.stats && g == 0 && ec.crank == 0) {
             p.stats[2 * pix] = cm;
             p.stats[2 * pix + 1] = sum;
         }
     }
 };
 
-// G2: Fhat = A V, the per-pixel loss terms and dL/dFhat = a_p Fhat + b_p F.  The target
-// chunk of the next iteration is loaded before the current one is consumed.
+// G2: Fhat = A V, the per-pixel loss terms and dL/dFhat = a_p Fhat + b_p F.  One CTA holds
+// 256 features of its rows; when D > 256 the CTAs of a row block form a cluster and add up
+// their per-row partial sums (<Fhat, F>, |Fhat|^2, |F|^2, |Fhat - F|^2) before dFhat is formed.
 struct FhatParams {
     int64_t n;
     int D;
@@ -238,48 +255,68 @@ struct FhatParams {
     float* Fout;  // n x D FP32 Fhat (inference form: no loss) or NULL
 };
 
-// ETILE: the BF16 target rows come through shared memory (TMA, after the MMAs); otherwise
-// (FP32 targets) each thread reads its own row from global memory, one chunk ahead.
-template <int BN_, bool ETILE>
+// ETILE: the BF16 target rows come through shared memory (TMA, after the MMAs) and two CTAs
+// share an SM; otherwise (FP32 targets) each thread reads its own row from global memory, one
+// chunk ahead.
+template <bool ETILE>
 struct FhatEpi {
-    static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_, EPI_WG = 2;
-    static constexpr int E_BOXES = ETILE ? BN_ / 64 : 0;
+    static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 1;
+    static constexpr int MIN_SMEM = 100 * 1024, MIN_BLOCKS = ETILE ? 2 : 1;
+    static constexpr int E_BOXES = ETILE ? BN / 64 : 0;
     static constexpr bool A_MN = false, B_MN = true;  // B = V (atoms x features), features contiguous
     using Params = FhatParams;
-    static __device__ __forceinline__ void target(const Params& p, const tc::EpiCtx& ec, int64_t frow, int c0,
-                                                  float (&f)[32]) {
-        if (ETILE)
-            ec.row32(c0, f);
-        else
-            load_target32(p.F, p.F_dtype, frow + c0, f);
+    // body(c0, h, f) for each 32-column chunk of this thread's share of the slice: h = Fhat
+    // (TMEM), f = target
+    template <class Body>
+    static __device__ __forceinline__ void sweep(const Params& p, const tc::EpiCtx& ec, int64_t frow, int ncols,
+                                                 Body&& body) {
+        constexpr int step = 32 * EPI_WG;
+        float h[32], f[32];
+        if constexpr (ETILE) {
+            for (int c0 = 32 * ec.g; c0 < ncols; c0 += step) {
+                ec.row32(c0, f);
+                tc::tmem_ld32(ec.taddr + c0, h);
+                body(c0, h, f);
+            }
+        } else {
+            float fn[32];
+            load_target32(p.F, p.F_dtype, frow + 32 * ec.g, f);
+            for (int c0 = 32 * ec.g; c0 < ncols; c0 += step) {
+                if (c0 + step < ncols) load_target32(p.F, p.F_dtype, frow + c0 + step, fn);
+                tc::tmem_ld32(ec.taddr + c0, h);
+                body(c0, h, f);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) f[i] = fn[i];
+            }
+        }
     }
     static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
         const int row = ec.row, m0 = ec.m0, g = ec.g;
+        const int ncols = min(BN, p.D - ec.n0);  // features of this CTA's slice
         float* scr = ec.scratch;
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
-        const int step = 32 * EPI_WG;
-        float h[32], f[32], fn[32];
-        if (p.Fout) {
-            for (int c0 = 32 * g; c0 < p.D; c0 += step) {
+        if (p.Fout) {  // inference form, launched without a cluster
+            float h[32];
+            for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
                 tc::tmem_ld32(taddr + c0, h);
                 if (valid) {
-                    float4* d4 = reinterpret_cast<float4*>(p.Fout + pix * p.D + c0);
+                    float4* d4 = reinterpret_cast<float4*>(p.Fout + pix * p.D + ec.n0 + c0);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) d4[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
                 }
             }
+            const float none[tc::kXchgVals] = {0.f, 0.f, 0.f, 0.f};
+            ec.exchange(none);
             return;
         }
-        const int64_t frow = valid ? pix * p.D : 0;  // invalid rows read row 0 (discarded)
+        // invalid rows read row 0 (discarded)
+        const int64_t frow = (valid ? pix * p.D : 0) + ec.n0;
         if (ETILE)
             for (int b = 0; b < E_BOXES; ++b) (void)ec.wait_box(b);  // a timeout raises the error flag
         float dot = 0.f, nh2 = 0.f, nf2 = 0.f, e2 = 0.f;
-        target(p, ec, frow, 32 * g, f);
-        for (int c0 = 32 * g; c0 < p.D; c0 += step) {
-            if (c0 + step < p.D) target(p, ec, frow, c0 + step, fn);
-            tc::tmem_ld32(taddr + c0, h);
+        sweep(p, ec, frow, ncols, [&](int, const float(&h)[32], const float(&f)[32]) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 dot += h[i] * f[i];
@@ -288,13 +325,20 @@ struct FhatEpi {
                 const float e = h[i] - f[i];
                 e2 += e * e;
             }
-#pragma unroll
-            for (int i = 0; i < 32; ++i) f[i] = fn[i];
-        }
+        });
         dot = tc::group_sum<EPI_WG>(dot, scr, 0, g, row);
         nh2 = tc::group_sum<EPI_WG>(nh2, scr, 1, g, row);
         nf2 = tc::group_sum<EPI_WG>(nf2, scr, 2, g, row);
         e2 = tc::group_sum<EPI_WG>(e2, scr, 3, g, row);
+        const float mine[tc::kXchgVals] = {dot, nh2, nf2, e2};
+        ec.exchange(mine);
+        for (int q = 0; q < ec.csize; ++q) {
+            if (q == ec.crank) continue;
+            dot += ec.xval(q, 0);
+            nh2 += ec.xval(q, 1);
+            nf2 += ec.xval(q, 2);
+            e2 += ec.xval(q, 3);
+        }
         const bool in_loss = valid && (p.mask == nullptr || p.mask[pix] != 0);
         const double nv = p.acc[3];
         const float scale = nv > 0.0 ? (float)((double)p.cfg.lambda_f / nv) : 0.f;
@@ -311,13 +355,14 @@ struct FhatEpi {
                 b = scale * (-p.cfg.lambda_cos / 1e-8f - l2c);
             }
         }
-        if (valid && g == 0) {
+        const bool lead = g == 0 && ec.crank == 0;  // one thread per row writes the row's results
+        if (valid && lead) {
             p.row[4 * pix] = a;
             p.row[4 * pix + 1] = b;
             p.row[4 * pix + 2] = a * nh2 + b * dot;
             p.row[4 * pix + 3] = cs;
         }
-        if (g == 0) {
+        if (lead) {
             double lc = in_loss ? 1.0 - (double)cs : 0.0, le = in_loss ? (double)e2 : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -329,16 +374,13 @@ struct FhatEpi {
                 atomicAdd(&p.acc[1], le);
             }
         }
-        target(p, ec, frow, 32 * g, f);
-        for (int c0 = 32 * g; c0 < p.D; c0 += step) {
-            if (c0 + step < p.D) target(p, ec, frow, c0 + step, fn);
-            tc::tmem_ld32(taddr + c0, h);
+        bf16* drow = p.dF + pix * p.D + ec.n0;
+        sweep(p, ec, frow, ncols, [&](int c0, const float(&h)[32], const float(&f)[32]) {
+            float v[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) h[i] = a * h[i] + b * f[i];
-            if (valid) store_row_bf16x32(p.dF + pix * p.D + c0, h);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) f[i] = fn[i];
-        }
+            for (int i = 0; i < 32; ++i) v[i] = a * h[i] + b * f[i];
+            if (valid) store_row_bf16x32(drow + c0, v);
+        });
     }
 };
 
@@ -351,11 +393,12 @@ struct DsParams {
     bf16* dS;  // n x M
 };
 
-template <int BN_>
+// One CTA holds 256 atoms of its rows (M > 256: several CTAs along y, nothing to trade: the
+// row term <A, dA> comes from G2).
 struct DsEpi {
     // the attention rows of the tile come through shared memory
-    static constexpr int BN = BN_, STAGES = BN_ <= 256 ? 4 : 2, BOX_B = 256 < BN_ ? 256 : BN_, EPI_WG = 2;
-    static constexpr int E_BOXES = BN_ / 64;
+    static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 0, MIN_SMEM = 0, MIN_BLOCKS = 2;
+    static constexpr int E_BOXES = BN / 64;
     static constexpr bool A_MN = false, B_MN = false;
     using Params = DsParams;
     static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
@@ -363,13 +406,14 @@ struct DsEpi {
         const bool valid = pix < p.n;
         const float rd = valid ? p.row[4 * pix + 2] : 0.f;
         for (int b = 0; b < E_BOXES; ++b) (void)ec.wait_box(b);
+        const int ncols = min(BN, p.M - ec.n0);
         float dA[32], a[32];
-        for (int c0 = 32 * ec.g; c0 < p.M; c0 += 32 * EPI_WG) {
+        for (int c0 = 32 * ec.g; c0 < ncols; c0 += 32 * EPI_WG) {
             ec.row32(c0, a);
             tc::tmem_ld32(ec.taddr + c0, dA);
 #pragma unroll
             for (int i = 0; i < 32; ++i) dA[i] = a[i] * (dA[i] - rd);
-            if (valid) store_row_bf16x32(p.dS + pix * p.M + c0, dA);
+            if (valid) store_row_bf16x32(p.dS + pix * p.M + ec.n0 + c0, dA);
         }
     }
 };
@@ -384,7 +428,8 @@ struct DqParams {
 
 template <int BN_>
 struct DqEpi {
-    static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0;
+    static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, XROUNDS = 0, MIN_SMEM = 0;
+    static constexpr int MIN_BLOCKS = 1;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
     using Params = DqParams;
     static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
@@ -420,7 +465,8 @@ struct PartParams {
 
 template <int BN_>
 struct PartEpi {
-    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0;
+    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, XROUNDS = 0;
+    static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
     using Params = PartParams;
     static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
@@ -498,15 +544,41 @@ latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_
     return LATENTAM_OK;
 }
 
+// Launch one tile grid of Epi; cluster_y > 1 groups that many consecutive y tiles of each row
+// block into a thread-block cluster (the epilogue's row exchange).
 template <class Epi>
 latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 grid, tc::GemmGrid g,
-                            const typename Epi::Params& p, int* err, cudaStream_t st, const CUtensorMap* emap = nullptr) {
-    constexpr size_t smem = tc::gemm_smem_bytes<Epi::BN, Epi::STAGES>();
+                            const typename Epi::Params& p, int* err, cudaStream_t st, const CUtensorMap* emap = nullptr,
+                            int cluster_y = 1) {
+    constexpr size_t smem = tc::gemm_smem_bytes<Epi>();
     static_assert(smem <= 227 * 1024, "tile does not fit in shared memory");
+    if (cluster_y > tc::kMaxCluster || (int)grid.y % cluster_y != 0 || (cluster_y > 1 && Epi::XROUNDS == 0)) {
+        set_error("bad cluster shape %d for a grid of %u row tiles", cluster_y, grid.y);
+        return LATENTAM_ERR_INVALID_ARG;
+    }
     auto kern = tc::tc_gemm_kernel<Epi>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "tc_gemm smem attribute");
-    kern<<<grid, tc::gemm_threads(Epi::EPI_WG), smem, st>>>(a, b, emap ? *emap : a, g, p, err);
+    static bool attr_set = false;  // per instantiation; setting it twice is harmless
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "tc_gemm smem attribute");
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(tc::gemm_threads(Epi::EPI_WG), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (cluster_y > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1;
+        attr[0].val.clusterDim.y = (unsigned)cluster_y;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, g, p, err);
+    if (e != cudaSuccess) return cuda_error(e, "tc_gemm_kernel launch");
     LAT_CHECK_LAUNCH("tc_gemm_kernel");
     return LATENTAM_OK;
 }
@@ -563,11 +635,14 @@ namespace {
 
 int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Rows of S and of Fhat are spread over clusters of up to kMaxCluster CTAs of 256 columns.
+constexpr int kMaxCols = 256 * tc::kMaxCluster;
+
 latentam_status check_tc_shape(int M, int D) {
-    if (M > 512 || D > 512) {
-        set_error("the BF16 tensor-core decode holds a full row of S (M=%d) and of Fhat (D=%d) in tensor memory: "
-                  "both must be <= 512",
-                  M, D);
+    if (M > kMaxCols || D > kMaxCols) {
+        set_error("the BF16 tensor-core decode spreads a row of S (M=%d) and of Fhat (D=%d) over at most %d CTAs "
+                  "of 256 columns: both must be <= %d",
+                  M, D, tc::kMaxCluster, kMaxCols);
         return LATENTAM_ERR_UNSUPPORTED_SHAPE;
     }
     return LATENTAM_OK;
@@ -579,16 +654,16 @@ latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, 
     prep_dict<<<std::min(4 * ctx->num_sms, cdiv((int64_t)M * (D + kPad), 256)), 256, 0, st>>>(K, V, M, d, D, b.Kb,
                                                                                                 b.Vb);
     LAT_CHECK_LAUNCH("prep_dict");
-    prep_queries<<<cdiv(n, 256), 256, 0, st>>>(Q, n, d, b.Qb);
+    prep_queries<<<cdiv(n * (kPad / 8), 256), 256, 0, st>>>(Q, n, d, b.Qb);
     LAT_CHECK_LAUNCH("prep_queries");
     CUtensorMap mQ, mK;
     LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, kTileM));
     LAT_TRY(bf16_map(&mK, b.Kb, kPad, M, kPad, 256));
     SoftmaxParams sp{n, M, c, b.A, stats};
-    const dim3 grid(cdiv(n, kTileM), 1, 1);
+    const int cy = cdiv(M, 256);
+    const dim3 grid(cdiv(n, kTileM), cy, 1);
     const tc::GemmGrid g1{1, 1};
-    if (M <= 256) return launch_gemm<SoftmaxEpi<256>>(mQ, mK, grid, g1, sp, b.err, st);
-    return launch_gemm<SoftmaxEpi<512>>(mQ, mK, grid, g1, sp, b.err, st);
+    return launch_gemm<SoftmaxEpi>(mQ, mK, grid, g1, sp, b.err, st, nullptr, cy);
 }
 
 // G2: Fhat = A V, B = V read MN-major in 64 x 64 boxes (features x atoms).
@@ -596,17 +671,17 @@ latentam_status tc_fhat(const TcBuffers& b, int64_t n, int M, int D, const FhatP
     CUtensorMap mA, mV;
     LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM));
     LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, 64));
-    const dim3 grid(cdiv(n, kTileM), 1, 1);
+    const int cy = cdiv(D, 256);
+    const dim3 grid(cdiv(n, kTileM), cy, 1);
     const tc::GemmGrid g{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
-    if (fp.Fout == nullptr && fp.F_dtype == LATENTAM_DTYPE_BF16) {
+    if (fp.Fout) return launch_gemm<FhatEpi<false>>(mA, mV, grid, g, fp, b.err, st);  // no row terms
+    if (fp.F_dtype == LATENTAM_DTYPE_BF16) {
         // BF16 targets: the tile's target rows are TMA-loaded into shared memory for the epilogue
         CUtensorMap mF;
         LAT_TRY(bf16_map(&mF, fp.F, D, n, D, kTileM));
-        if (D <= 256) return launch_gemm<FhatEpi<256, true>>(mA, mV, grid, g, fp, b.err, st, &mF);
-        return launch_gemm<FhatEpi<512, true>>(mA, mV, grid, g, fp, b.err, st, &mF);
+        return launch_gemm<FhatEpi<true>>(mA, mV, grid, g, fp, b.err, st, &mF, cy);
     }
-    if (D <= 256) return launch_gemm<FhatEpi<256, false>>(mA, mV, grid, g, fp, b.err, st);
-    return launch_gemm<FhatEpi<512, false>>(mA, mV, grid, g, fp, b.err, st);
+    return launch_gemm<FhatEpi<false>>(mA, mV, grid, g, fp, b.err, st, nullptr, cy);
 }
 
 }  // namespace
@@ -651,10 +726,7 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
         const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
         CUtensorMap mAe;  // attention rows for the epilogue
         LAT_TRY(bf16_map(&mAe, b.A, M, n, M, kTileM));
-        if (M <= 256)
-            LAT_TRY(launch_gemm<DsEpi<256>>(mdF, mV, grow, g3, dp, b.err, st, &mAe));
-        else
-            LAT_TRY(launch_gemm<DsEpi<512>>(mdF, mV, grow, g3, dp, b.err, st, &mAe));
+        LAT_TRY(launch_gemm<DsEpi>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st, &mAe));
         // G4: dQ = c dS K, B = K padded read MN-major (queries x atoms)
         if (a.dQ) {
             LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, kTileM));

@@ -1,6 +1,6 @@
-// sm_103a building blocks for the tensor-core kernels: mbarriers with bounded waits, TMA tile
-// loads, tcgen05 (TMEM allocation, MMA, commit, loads) and the shared-memory matrix
-// descriptors of 128-byte-swizzled, K-major BF16 tiles.
+// sm_103a building blocks for the tensor-core kernels: mbarriers with bounded waits, cluster
+// (distributed shared memory) stores and arrivals, TMA tile loads, tcgen05 (TMEM allocation,
+// MMA, commit, loads) and the shared-memory matrix descriptors of 128-byte-swizzled BF16 tiles.
 #pragma once
 
 #include <cuda.h>
@@ -58,6 +58,60 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
         if (mbar_try_wait(bar, parity)) return true;
         if (abort && *abort) return false;
         if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+        __nanosleep(64);
+    }
+}
+
+// ---- thread-block clusters (distributed shared memory) ----
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster (warp-aligned).
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address, in the shared::cluster window, of this CTA's shared variable `p` in CTA `rank`.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_peer_f32(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// Arrive on an mbarrier of another CTA of the cluster; orders this thread's earlier stores
+// to that CTA before the arrival.
+__device__ __forceinline__ void mbar_arrive_peer(uint32_t bar_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for arrivals from other CTAs of the cluster.  The limit is longer than that of
+// the pipeline waits, so that a peer which gave up on its own pipeline still gets to arrive.
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if (global_timer_ns() - t0 > 4 * kWaitLimitNs) return false;
         __nanosleep(64);
     }
 }

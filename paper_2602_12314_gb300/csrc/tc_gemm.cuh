@@ -7,6 +7,8 @@
 // issues the MMAs (one thread), warps 2..5 run the epilogue; epilogue thread r owns tile row r
 // (TMEM lane r; warp w reads the lane quarter w % 4).
 // blockIdx.x: 128-row tile of A, blockIdx.y: BN-row tile of B, blockIdx.z: split of the K range.
+// When a row reduction spans several BN tiles, the tiles of one row block run as a thread-block
+// cluster along y and trade their per-row partial results through distributed shared memory.
 #pragma once
 
 #include "internal.cuh"
@@ -16,7 +18,10 @@ namespace lat {
 namespace tc {
 
 constexpr int kTileM = 128;
-constexpr int kScratchBytes = 8 * 2 * kTileM * 4;  // epilogue row-reduction scratch: 8 slots x 2 groups
+constexpr int kScratchBytes = 4 * 2 * kTileM * 4;  // epilogue row-reduction scratch: 4 slots x 2 groups
+constexpr int kMaxCluster = 4;                    // CTAs of a cluster that trade row partials
+constexpr int kXchgVals = 4;                      // values per row per CTA in one exchange
+constexpr int kXchgBytes = kMaxCluster * kXchgVals * kTileM * 4;
 constexpr int kChunkK = 64;                       // BF16 elements per 128-byte row
 constexpr uint32_t kTileABytes = kTileM * 128;    // 16 KB
 
@@ -24,10 +29,12 @@ __host__ __device__ constexpr uint32_t tmem_cols_for(int n) {
     return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
 }
 
-template <int BN, int STAGES>
+template <class Epi>
 __host__ __device__ constexpr size_t gemm_smem_bytes() {
-    return (size_t)STAGES * (kTileABytes + (size_t)BN * 128) + 1024 /* alignment */ + 256 /* barriers */ +
-           kScratchBytes;
+    const size_t need = (size_t)Epi::STAGES * (kTileABytes + (size_t)Epi::BN * 128) + 1024 /* alignment */ +
+                        256 /* barriers */ + kScratchBytes + (Epi::XROUNDS > 0 ? kXchgBytes : 0);
+    // MIN_SMEM caps the CTAs resident on one SM (so that their TMEM allocations never wait)
+    return need > (size_t)Epi::MIN_SMEM ? need : (size_t)Epi::MIN_SMEM;
 }
 
 __host__ __device__ constexpr int gemm_threads(int epi_warpgroups) { return 64 + 128 * epi_warpgroups; }
@@ -38,7 +45,7 @@ __device__ __forceinline__ void epi_sync(int nthreads) {
 }
 
 // Sum (or max) of one value per row over the G epilogue warpgroups, through shared memory.
-// `slot` (0..7) must differ between reductions of the same tile.
+// `slot` (0..3) must differ between reductions of the same tile.
 template <int G>
 __device__ __forceinline__ float group_sum(float v, float* scratch, int slot, int g, int row) {
     if (G == 1) return v;
@@ -73,7 +80,9 @@ struct GemmGrid {
 // of 64-column boxes of a row-major BF16 "epilogue operand" (tmE) loaded for the tile's 128
 // rows into the pipeline shared memory once the MMAs are done, 0 for none); static __device__
 // void run(const Params&, const EpiCtx&) executed by the 128 * EPI_WG epilogue threads
-// (warp-convergent).
+// (warp-convergent); static constexpr int XROUNDS (0 or 1: run() calls EpiCtx::exchange exactly
+// that many times, whatever the CTA's rows hold), MIN_SMEM (bytes of shared memory to request
+// at least) and MIN_BLOCKS (CTAs per SM the register allocation must allow).
 struct EpiCtx {
     uint32_t taddr;        // TMEM address of this thread's row, column 0
     int row, m0, n0, z;    // tile row owned by this thread, tile origin, K split
@@ -82,6 +91,30 @@ struct EpiCtx {
     const uint8_t* etile;  // epilogue operand tile (128-byte swizzled 64 x 128 boxes), or null
     uint64_t* ebar;        // one barrier per box
     volatile int* abort;
+    int crank, csize;      // rank of this CTA in its cluster, cluster size
+    uint64_t* xbar;        // arrivals of the other CTAs' row partials
+    float* xbuf;           // [rank][value][row] partials received from the other CTAs
+
+    // Send this row's kXchgVals partials to every other CTA of the cluster and wait for theirs
+    // (read back with xval).  Warpgroup 0 sends; every epilogue thread waits.  Bounded: false
+    // (and the error flag raised) if the partials did not all arrive.
+    __device__ __forceinline__ bool exchange(const float (&v)[kXchgVals]) const {
+        if (csize <= 1) return true;
+        if (g == 0) {
+            for (int q = 0; q < csize; ++q) {
+                if (q == crank) continue;
+#pragma unroll
+                for (int k = 0; k < kXchgVals; ++k)
+                    st_peer_f32(peer_addr(xbuf + (crank * kXchgVals + k) * kTileM + row, (uint32_t)q), v[k]);
+                mbar_arrive_peer(peer_addr(xbar, (uint32_t)q));
+            }
+        }
+        const bool ok = mbar_wait_cluster(xbar, 0);
+        if (!ok) *abort = 1;
+        return ok;
+    }
+    // Partial k of this thread's row from CTA q (q != crank) of the cluster.
+    __device__ __forceinline__ float xval(int q, int k) const { return xbuf[(q * kXchgVals + k) * kTileM + row]; }
 
     // Wait for box b of the epilogue operand (bounded; false if it gave up).
     __device__ __forceinline__ bool wait_box(int b) const { return mbar_wait(&ebar[b], 0, abort); }
@@ -104,7 +137,7 @@ struct EpiCtx {
 };
 
 template <class Epi>
-__global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
+__global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmE, GemmGrid g, typename Epi::Params ep,
                    int* __restrict__ err) {
@@ -124,6 +157,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
     constexpr int E_BOXES = Epi::E_BOXES;
     static_assert(E_BOXES <= 8 && (uint32_t)E_BOXES * kTileM * 128 <= STAGES * STAGE_BYTES,
                   "the epilogue operand must fit in the pipeline shared memory");
+    static_assert(Epi::XROUNDS == 0 || Epi::XROUNDS == 1, "at most one row exchange per tile");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -134,7 +168,12 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* decision = abort_flag + 1;
     uint64_t* ebar = reinterpret_cast<uint64_t*>(tmem_slot + 4);  // 8-byte aligned, 8 barriers
+    uint64_t* xbar = ebar + 8;
     float* scratch = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
+    float* xbuf = scratch + kScratchBytes / 4;
+    uint32_t csize = 1;
+    if (Epi::XROUNDS > 0) asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+    const uint32_t crank = csize > 1 ? cluster_rank() : 0u;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTileM;
@@ -150,6 +189,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
         }
         mbar_init(accum, 1);
         for (int b = 0; b < E_BOXES; ++b) mbar_init(&ebar[b], 1);
+        if (csize > 1) mbar_init(xbar, (uint32_t)kTileM * (csize - 1));
         *abort_flag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmA);
@@ -159,6 +199,8 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // the other CTAs' exchange barriers are initialised before anyone arrives on them
+    if (csize > 1) cluster_sync_all();
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
@@ -203,7 +245,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
                     prefetch_tmap(&tmE);
                     for (int b = 0; b < E_BOXES; ++b) {
                         mbar_expect_tx(&ebar[b], kTileM * 128);
-                        tma_load_2d(smem + b * (kTileM * 128), &tmE, &ebar[b], 64 * b, m0);
+                        tma_load_2d(smem + b * (kTileM * 128), &tmE, &ebar[b], n0 + 64 * b, m0);
                     }
                     for (int b = 0; b < E_BOXES; ++b) (void)mbar_wait(&ebar[b], 0, nullptr);
                 } else {
@@ -253,10 +295,14 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
         epi_sync(128 * Epi::EPI_WG);
         if (threadIdx.x == 64) *decision = (nk > 0 && !*abort_flag) ? 1 : 0;
         epi_sync(128 * Epi::EPI_WG);
+        EpiCtx ec{tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch,
+                  E_BOXES > 0 ? smem : nullptr, ebar, abort_flag, (int)crank, (int)csize, xbar, xbuf};
         if (*decision) {
-            EpiCtx ec{tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch,
-                      E_BOXES > 0 ? smem : nullptr, ebar, abort_flag};
             Epi::run(ep, ec);
+        } else if (Epi::XROUNDS > 0) {
+            // keep the cluster's exchange protocol: the other CTAs wait for this one's partials
+            const float zero[kXchgVals] = {0.f, 0.f, 0.f, 0.f};
+            (void)ec.exchange(zero);
         }
         tc_fence_before();
     }

@@ -49,10 +49,17 @@ def _case(name):
         return random_scene(13, n=2000, d=16, M=512, D=512, width=48, height=40, log_scale=-2.6, mask_drop=0.1)
     if name == "room_crop":
         return room_scene(1, n=300_000).crop(272, 208, 96, 64)
+    # the dictionary shapes of the larger workloads: rows of S and Fhat spread over clusters
+    if name == "M512_D1024":
+        return random_scene(14, n=3000, d=32, M=512, D=1024, width=64, height=48, log_scale=-2.7, mask_drop=0.1)
+    if name == "M1024_D768":
+        return random_scene(15, n=3000, d=32, M=1024, D=768, width=56, height=40, log_scale=-2.7)
+    if name == "M288_D384":  # the last CTA of each cluster holds a partial slice
+        return random_scene(16, n=2000, d=16, M=288, D=384, width=50, height=37, log_scale=-2.6, mask_drop=0.2)
     raise KeyError(name)
 
 
-CASES = ["tiny", "ragged", "d64", "d16_M512", "room_crop"]
+CASES = ["tiny", "ragged", "d64", "d16_M512", "room_crop", "M512_D1024", "M1024_D768", "M288_D384"]
 
 
 def _oracle_Q(s):
@@ -116,6 +123,6 @@ def test_bf16_rejects_oversized_rows(api, ctx):
     from paper_2602_12314_gb300 import _lib as L
     Q = torch.zeros((10, 32), device="cuda")
     with pytest.raises(L.LatentamError) as e:
-        api.decode_fwd(ctx, Q, torch.zeros((1024, 32), device="cuda"), torch.zeros((1024, 128), device="cuda"),
+        api.decode_fwd(ctx, Q, torch.zeros((64, 32), device="cuda"), torch.zeros((64, 1152), device="cuda"),
                        precision=api.BF16)
     assert e.value.status == L.ERR_UNSUPPORTED_SHAPE
