@@ -186,11 +186,11 @@ struct SoftmaxParams {
 // One CTA holds the logits of 256 atoms; when M > 256 the CTAs of a row block form a cluster
 // and combine their (row max, partial denominator) pairs before normalising.
 struct SoftmaxEpi {
-    static constexpr int BN = 256, STAGES = 1, BOX_B = 256, EPI_WG = 2, E_BOXES = 0, XROUNDS = 1;
+    static constexpr int BN = 256, STAGES = 1, BOX_B = 256, EPI_WG = 2, E_BOXES = 0, O_BOXES = 4, XROUNDS = 1;
     static constexpr int MIN_SMEM = 100 * 1024, MIN_BLOCKS = 2;  // two CTAs per SM: 2 x 256 TMEM columns
     static constexpr bool A_MN = false, B_MN = false;
     using Params = SoftmaxParams;
-    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+    static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
         const int row = ec.row, m0 = ec.m0, g = ec.g;
         const int ncols = min(BN, p.M - ec.n0);  // atoms of this CTA's slice
@@ -230,12 +230,13 @@ struct SoftmaxEpi {
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = __expf(p.c * v[i] - cm) * il;
-            if (valid) store_row_bf16x32(p.A + pix * p.M + ec.n0 + c0, v);
+            ec.put32(c0, v);
         }
         if (valid && p.stats && g == 0 && ec.crank == 0) {
             p.stats[2 * pix] = cm;
             p.stats[2 * pix + 1] = sum;
         }
+        return (ncols + 63) / 64;
     }
 };
 
@@ -262,7 +263,7 @@ template <bool ETILE>
 struct FhatEpi {
     static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 1;
     static constexpr int MIN_SMEM = 100 * 1024, MIN_BLOCKS = ETILE ? 2 : 1;
-    static constexpr int E_BOXES = ETILE ? BN / 64 : 0;
+    static constexpr int E_BOXES = ETILE ? BN / 64 : 0, O_BOXES = BN / 64;  // dFhat staged over the target
     static constexpr bool A_MN = false, B_MN = true;  // B = V (atoms x features), features contiguous
     using Params = FhatParams;
     // body(c0, h, f) for each 32-column chunk of this thread's share of the slice: h = Fhat
@@ -290,7 +291,7 @@ struct FhatEpi {
             }
         }
     }
-    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+    static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
         const int row = ec.row, m0 = ec.m0, g = ec.g;
         const int ncols = min(BN, p.D - ec.n0);  // features of this CTA's slice
@@ -309,7 +310,7 @@ struct FhatEpi {
             }
             const float none[tc::kXchgVals] = {0.f, 0.f, 0.f, 0.f};
             ec.exchange(none);
-            return;
+            return 0;
         }
         // invalid rows read row 0 (discarded)
         const int64_t frow = (valid ? pix * p.D : 0) + ec.n0;
@@ -374,13 +375,14 @@ struct FhatEpi {
                 atomicAdd(&p.acc[1], le);
             }
         }
-        bf16* drow = p.dF + pix * p.D + ec.n0;
+        // dFhat overwrites the target chunk it was formed from (same thread, same bytes)
         sweep(p, ec, frow, ncols, [&](int c0, const float(&h)[32], const float(&f)[32]) {
             float v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = a * h[i] + b * f[i];
-            if (valid) store_row_bf16x32(drow + c0, v);
+            ec.put32(c0, v);
         });
+        return (ncols + 63) / 64;
     }
 };
 
@@ -398,10 +400,10 @@ struct DsParams {
 struct DsEpi {
     // the attention rows of the tile come through shared memory
     static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 0, MIN_SMEM = 0, MIN_BLOCKS = 2;
-    static constexpr int E_BOXES = BN / 64;
+    static constexpr int E_BOXES = BN / 64, O_BOXES = BN / 64;  // dS staged over the attention rows
     static constexpr bool A_MN = false, B_MN = false;
     using Params = DsParams;
-    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+    static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const int64_t pix = (int64_t)ec.m0 + ec.row;
         const bool valid = pix < p.n;
         const float rd = valid ? p.row[4 * pix + 2] : 0.f;
@@ -413,8 +415,9 @@ struct DsEpi {
             tc::tmem_ld32(ec.taddr + c0, dA);
 #pragma unroll
             for (int i = 0; i < 32; ++i) dA[i] = a[i] * (dA[i] - rd);
-            if (valid) store_row_bf16x32(p.dS + pix * p.M + ec.n0 + c0, dA);
+            ec.put32(c0, dA);
         }
+        return (ncols + 63) / 64;
     }
 };
 
@@ -428,11 +431,11 @@ struct DqParams {
 
 template <int BN_>
 struct DqEpi {
-    static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, XROUNDS = 0, MIN_SMEM = 0;
-    static constexpr int MIN_BLOCKS = 1;
+    static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, O_BOXES = 0, XROUNDS = 0;
+    static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
     using Params = DqParams;
-    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+    static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
         const int row = ec.row, m0 = ec.m0;
         const int64_t pix = (int64_t)m0 + row;
@@ -454,6 +457,7 @@ struct DqEpi {
                 }
             }
         }
+        return 0;
     }
 };
 
@@ -465,11 +469,12 @@ struct PartParams {
 
 template <int BN_>
 struct PartEpi {
-    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, XROUNDS = 0;
+    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, O_BOXES = 0;
+    static constexpr int XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
     using Params = PartParams;
-    static __device__ void run(const Params& p, const tc::EpiCtx& ec) {
+    static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
         const int row = ec.row, m0 = ec.m0, n0 = ec.n0, z = ec.z;
         const int j = m0 + row;
@@ -490,6 +495,7 @@ struct PartEpi {
                 }
             }
         }
+        return 0;
     }
 };
 
@@ -544,12 +550,13 @@ latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_
     return LATENTAM_OK;
 }
 
-// Launch one tile grid of Epi; cluster_y > 1 groups that many consecutive y tiles of each row
-// block into a thread-block cluster (the epilogue's row exchange).
+// Launch one tile grid of Epi (emap: epilogue operand, omap: staged output); cluster_y > 1
+// groups that many consecutive y tiles of each row block into a thread-block cluster (the
+// epilogue's row exchange).
 template <class Epi>
 latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 grid, tc::GemmGrid g,
                             const typename Epi::Params& p, int* err, cudaStream_t st, const CUtensorMap* emap = nullptr,
-                            int cluster_y = 1) {
+                            const CUtensorMap* omap = nullptr, int cluster_y = 1) {
     constexpr size_t smem = tc::gemm_smem_bytes<Epi>();
     static_assert(smem <= 227 * 1024, "tile does not fit in shared memory");
     if (cluster_y > tc::kMaxCluster || (int)grid.y % cluster_y != 0 || (cluster_y > 1 && Epi::XROUNDS == 0)) {
@@ -577,7 +584,7 @@ latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 gri
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, g, p, err);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, omap ? *omap : a, g, p, err);
     if (e != cudaSuccess) return cuda_error(e, "tc_gemm_kernel launch");
     LAT_CHECK_LAUNCH("tc_gemm_kernel");
     return LATENTAM_OK;
@@ -659,11 +666,13 @@ latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, 
     CUtensorMap mQ, mK;
     LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, kTileM));
     LAT_TRY(bf16_map(&mK, b.Kb, kPad, M, kPad, 256));
+    CUtensorMap mA;  // the attention rows leave through the TMA
+    LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM));
     SoftmaxParams sp{n, M, c, b.A, stats};
     const int cy = cdiv(M, 256);
     const dim3 grid(cdiv(n, kTileM), cy, 1);
     const tc::GemmGrid g1{1, 1};
-    return launch_gemm<SoftmaxEpi>(mQ, mK, grid, g1, sp, b.err, st, nullptr, cy);
+    return launch_gemm<SoftmaxEpi>(mQ, mK, grid, g1, sp, b.err, st, nullptr, &mA, cy);
 }
 
 // G2: Fhat = A V, B = V read MN-major in 64 x 64 boxes (features x atoms).
@@ -675,13 +684,15 @@ latentam_status tc_fhat(const TcBuffers& b, int64_t n, int M, int D, const FhatP
     const dim3 grid(cdiv(n, kTileM), cy, 1);
     const tc::GemmGrid g{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
     if (fp.Fout) return launch_gemm<FhatEpi<false>>(mA, mV, grid, g, fp, b.err, st);  // no row terms
+    CUtensorMap mdF;  // dFhat leaves through the TMA
+    LAT_TRY(bf16_map(&mdF, fp.dF, D, n, D, kTileM));
     if (fp.F_dtype == LATENTAM_DTYPE_BF16) {
         // BF16 targets: the tile's target rows are TMA-loaded into shared memory for the epilogue
         CUtensorMap mF;
         LAT_TRY(bf16_map(&mF, fp.F, D, n, D, kTileM));
-        return launch_gemm<FhatEpi<true>>(mA, mV, grid, g, fp, b.err, st, &mF, cy);
+        return launch_gemm<FhatEpi<true>>(mA, mV, grid, g, fp, b.err, st, &mF, &mdF, cy);
     }
-    return launch_gemm<FhatEpi<false>>(mA, mV, grid, g, fp, b.err, st, nullptr, cy);
+    return launch_gemm<FhatEpi<false>>(mA, mV, grid, g, fp, b.err, st, nullptr, &mdF, cy);
 }
 
 }  // namespace
@@ -724,9 +735,10 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
         DsParams dp{n, M, b.A, b.row, b.dS};
         const dim3 grow(cdiv(n, kTileM), 1, 1);
         const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
-        CUtensorMap mAe;  // attention rows for the epilogue
+        CUtensorMap mAe, mdSo;  // attention rows for the epilogue, dS out through the TMA
         LAT_TRY(bf16_map(&mAe, b.A, M, n, M, kTileM));
-        LAT_TRY(launch_gemm<DsEpi>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st, &mAe));
+        LAT_TRY(bf16_map(&mdSo, b.dS, M, n, M, kTileM));
+        LAT_TRY(launch_gemm<DsEpi>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st, &mAe, &mdSo));
         // G4: dQ = c dS K, B = K padded read MN-major (queries x atoms)
         if (a.dQ) {
             LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, kTileM));

@@ -29,10 +29,19 @@ __host__ __device__ constexpr uint32_t tmem_cols_for(int n) {
     return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
 }
 
+// Shared memory at the start of the tile: the operand pipeline, reused once the MMAs are done
+// for the epilogue operand (E_BOXES boxes of 64 x 128 BF16) and the staged output (O_BOXES).
+template <class Epi>
+__host__ __device__ constexpr uint32_t tile_region_bytes() {
+    const uint32_t pipe = (uint32_t)Epi::STAGES * (kTileABytes + (uint32_t)Epi::BN * 128);
+    const uint32_t boxes = (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * kTileABytes;
+    return pipe > boxes ? pipe : boxes;
+}
+
 template <class Epi>
 __host__ __device__ constexpr size_t gemm_smem_bytes() {
-    const size_t need = (size_t)Epi::STAGES * (kTileABytes + (size_t)Epi::BN * 128) + 1024 /* alignment */ +
-                        256 /* barriers */ + kScratchBytes + (Epi::XROUNDS > 0 ? kXchgBytes : 0);
+    const size_t need = (size_t)tile_region_bytes<Epi>() + 1024 /* alignment */ + 256 /* barriers */ +
+                        kScratchBytes + (Epi::XROUNDS > 0 ? kXchgBytes : 0);
     // MIN_SMEM caps the CTAs resident on one SM (so that their TMEM allocations never wait)
     return need > (size_t)Epi::MIN_SMEM ? need : (size_t)Epi::MIN_SMEM;
 }
@@ -80,7 +89,9 @@ struct GemmGrid {
 // of 64-column boxes of a row-major BF16 "epilogue operand" (tmE) loaded for the tile's 128
 // rows into the pipeline shared memory once the MMAs are done, 0 for none); static __device__
 // void run(const Params&, const EpiCtx&) executed by the 128 * EPI_WG epilogue threads
-// (warp-convergent); static constexpr int XROUNDS (0 or 1: run() calls EpiCtx::exchange exactly
+// (warp-convergent), returning the number of 64-column boxes of output it staged with
+// EpiCtx::put32 (CTA-uniform; stored to tmO at (n0 + 64 b, m0) by TMA); static constexpr int
+// O_BOXES (boxes the epilogue may stage, 0 for none); static constexpr int XROUNDS (0 or 1: run() calls EpiCtx::exchange exactly
 // that many times, whatever the CTA's rows hold), MIN_SMEM (bytes of shared memory to request
 // at least) and MIN_BLOCKS (CTAs per SM the register allocation must allow).
 struct EpiCtx {
@@ -89,6 +100,7 @@ struct EpiCtx {
     int g;                 // epilogue warpgroup
     float* scratch;        // row-reduction scratch
     const uint8_t* etile;  // epilogue operand tile (128-byte swizzled 64 x 128 boxes), or null
+    uint8_t* otile;        // staging tile of the output, same layout (may alias etile)
     uint64_t* ebar;        // one barrier per box
     volatile int* abort;
     int crank, csize;      // rank of this CTA in its cluster, cluster size
@@ -118,6 +130,16 @@ struct EpiCtx {
 
     // Wait for box b of the epilogue operand (bounded; false if it gave up).
     __device__ __forceinline__ bool wait_box(int b) const { return mbar_wait(&ebar[b], 0, abort); }
+    // Stage 32 values of this thread's row as BF16 at column c0 (a multiple of 32) of the output.
+    __device__ __forceinline__ void put32(int c0, const float (&v)[32]) const {
+        uint8_t* base = otile + (c0 >> 6) * (kTileM * 128) + row * 128;
+        const int j0 = (c0 & 63) >> 3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(base + (((j0 + q) ^ (row & 7)) << 4)) =
+                make_uint4(pack_bf16x2(v[8 * q], v[8 * q + 1]), pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
+                           pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
+    }
     // 32 BF16 values of this thread's row from column c0 (a multiple of 32) of the operand.
     __device__ __forceinline__ void row32(int c0, float (&v)[32]) const {
         const uint8_t* base = etile + (c0 >> 6) * (kTileM * 128) + row * 128;
@@ -139,7 +161,8 @@ struct EpiCtx {
 template <class Epi>
 __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmE, GemmGrid g, typename Epi::Params ep,
+                   const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmO, GemmGrid g,
+                   typename Epi::Params ep,
                    int* __restrict__ err) {
     constexpr int BN = Epi::BN;
     constexpr int STAGES = Epi::STAGES;
@@ -155,13 +178,13 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
     static_assert(!B_MN || SUBN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
     constexpr int E_BOXES = Epi::E_BOXES;
-    static_assert(E_BOXES <= 8 && (uint32_t)E_BOXES * kTileM * 128 <= STAGES * STAGE_BYTES,
-                  "the epilogue operand must fit in the pipeline shared memory");
+    constexpr uint32_t TILE_REGION = tile_region_bytes<Epi>();
+    static_assert(E_BOXES <= 8 && Epi::O_BOXES <= 8, "at most 8 boxes of epilogue operand / output");
     static_assert(Epi::XROUNDS == 0 || Epi::XROUNDS == 1, "at most one row exchange per tile");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + TILE_REGION);
     uint64_t* empty = full + STAGES;
     uint64_t* accum = empty + STAGES;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
@@ -169,7 +192,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     volatile int* decision = abort_flag + 1;
     uint64_t* ebar = reinterpret_cast<uint64_t*>(tmem_slot + 4);  // 8-byte aligned, 8 barriers
     uint64_t* xbar = ebar + 8;
-    float* scratch = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
+    float* scratch = reinterpret_cast<float*>(smem + TILE_REGION + 256);
     float* xbuf = scratch + kScratchBytes / 4;
     uint32_t csize = 1;
     if (Epi::XROUNDS > 0) asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
@@ -296,13 +319,26 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
         if (threadIdx.x == 64) *decision = (nk > 0 && !*abort_flag) ? 1 : 0;
         epi_sync(128 * Epi::EPI_WG);
         EpiCtx ec{tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch,
-                  E_BOXES > 0 ? smem : nullptr, ebar, abort_flag, (int)crank, (int)csize, xbar, xbuf};
+                  E_BOXES > 0 ? smem : nullptr, smem, ebar, abort_flag, (int)crank, (int)csize, xbar, xbuf};
+        int out_boxes = 0;
         if (*decision) {
-            Epi::run(ep, ec);
+            out_boxes = Epi::run(ep, ec);
         } else if (Epi::XROUNDS > 0) {
             // keep the cluster's exchange protocol: the other CTAs wait for this one's partials
             const float zero[kXchgVals] = {0.f, 0.f, 0.f, 0.f};
             (void)ec.exchange(zero);
+        }
+        if (Epi::O_BOXES > 0) {
+            // the staged output tile goes out through the TMA once every epilogue thread wrote
+            // its part (coalesced and asynchronous, instead of one row per thread)
+            fence_proxy_async();
+            epi_sync(128 * Epi::EPI_WG);
+            if (threadIdx.x == 64 && out_boxes > 0 && !*abort_flag) {
+                for (int b = 0; b < out_boxes && b < Epi::O_BOXES; ++b)
+                    tma_store_2d(&tmO, smem + b * kTileABytes, n0 + 64 * b, m0);
+                bulk_commit();
+                bulk_wait_read();  // shared memory stays valid until the copies have read it
+            }
         }
         tc_fence_before();
     }
