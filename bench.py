@@ -38,6 +38,23 @@ WORKLOAD = ("room keyframe: 300k Gaussians (6x5x3 m room, 20 boxes), 640x480, d=
             "one fwd+bwd+Adam iteration incl. projection and depth/tile sort (Stage I, R1=1)")
 SM_FP32_LANES = 128  # FP32 FMA lanes per SM
 
+# DRAM traffic (read + write bytes) of the decode stage per pixel, from one ncu capture of every
+# decode launch of a step (profiles/decode_bf16_tc_crop480x360.md: 1,308 MB over 172,800
+# pixels), keyed by a hash of the kernel sources it was taken on: once they change, the figure
+# no longer describes the kernels and the roofline reports no traffic.
+_DECODE_TRAFFIC = {"bf16": ("1e6604f943751c92", 1307.74e6 / 172800)}
+_DECODE_SOURCES = ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh")
+
+
+def _decode_sources_hash():
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2602_12314_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in _DECODE_SOURCES:
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def _args():
     p = argparse.ArgumentParser()
@@ -51,6 +68,8 @@ def _args():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--crop", type=int, nargs=2, metavar=("W", "H"), default=None,
+                   help="profiling only: the central W x H crop of the keyframe (all Gaussians kept)")
     return p.parse_args()
 
 
@@ -126,9 +145,27 @@ def _dist():
     return world, rank, local
 
 
-def _scene(seed):
+def _scene(seed, crop=None):
     from workloads import room_scene
-    return room_scene(seed)
+    s = room_scene(seed)
+    if crop:
+        w, h = crop
+        s = s.crop((s.camera.width - w) // 2, (s.camera.height - h) // 2, w, h)
+    return s
+
+
+def _workload(args):
+    if not args.crop:
+        return WORKLOAD
+    return WORKLOAD.replace("640x480", "central %dx%d crop of the 640x480 frame" % tuple(args.crop))
+
+
+def _config(args, scene, world, precision):
+    return {"workload": _workload(args), "precision": precision, "global_batch": world,
+            "n_pixels": scene.camera.n_pixels, "gaussians": scene.n, "d": scene.d, "M": scene.M, "D": scene.D,
+            "l2": "inputs larger than L2 (target features %.0f MB FP32 / %.0f MB BF16 per step)"
+                  % (scene.F.nbytes / 1e6, scene.F.nbytes / 2e6),
+            "parallelism": f"replicas x{world}"}
 
 
 def _oracle_iteration(scene, cfg):
@@ -151,9 +188,9 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     import oracle
-    s = _scene(args.seed)
+    s = _scene(args.seed, args.crop)
     full = s.camera.n_pixels
-    crop = s.crop(240, 180, 160, 120)
+    crop = s.crop((s.camera.width - 160) // 2, (s.camera.height - 120) // 2, 160, 120)
     frac = crop.camera.n_pixels / full
     cfg = oracle.LossConfig()
     oracle.build()
@@ -171,7 +208,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " [FP64 CPU oracle]"},
+        "config": _config(args, s, world, args.precision),
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -283,9 +320,14 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
                 "traffic": None, "algorithmic_per_launch": flops}
     else:
         peak = float(peaks["bf16_tflops_sustained"])
+        key, per_pixel = _DECODE_TRAFFIC["bf16"]
+        traffic = per_pixel * n if key == _decode_sources_hash() else None
         roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 GEMM kernels + their epilogues)",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"bf16 sustained, {peak_src}", "traffic": None, "algorithmic_per_launch": flops}
+                "peak_source": f"bf16 sustained, {peak_src}", "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of every decode launch of one "
+                                  "step on the 480x360 crop, scaled by pixel count" if traffic else None,
+                "algorithmic_per_launch": flops}
     roof["frac"] = roof["achieved"] / roof["peak"]
     return {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": int(launches), "e2e": e2e,
             "keyframes_per_step": n_frames,
@@ -303,7 +345,7 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    scene = _scene(args.seed + rank)
+    scene = _scene(args.seed + rank, args.crop)
     forms = ["fp32", "bf16", "bf16_batch"] if args.precision == "both" else [args.precision]
     res = {}
     for f in forms:
@@ -323,7 +365,7 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        crop = scene.crop(240, 180, 160, 120)
+        crop = scene.crop((scene.camera.width - 160) // 2, (scene.camera.height - 120) // 2, 160, 120)
         frac = crop.camera.n_pixels / n
         t0 = time.perf_counter()
         _oracle_iteration(crop, oracle.LossConfig())
@@ -337,11 +379,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": head["value"], "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": forms[0], "global_batch": world,
-                   "n_pixels": n, "gaussians": scene.n, "d": scene.d, "M": scene.M, "D": scene.D,
-                   "l2": "inputs larger than L2 (target features %.0f MB FP32 / %.0f MB BF16 per step)"
-                         % (scene.F.nbytes / 1e6, scene.F.nbytes / 2e6),
-                   "parallelism": f"replicas x{world}"},
+        "config": _config(args, scene, world, args.precision),
         "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"], "cpu_baseline": cpu,
         "clocks": head["clocks"], "stages_ms_per_step": head["stages_ms_per_step"],
     }
