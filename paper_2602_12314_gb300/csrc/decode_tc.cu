@@ -186,8 +186,9 @@ struct SoftmaxParams {
 // One CTA holds the logits of 256 atoms; when M > 256 the CTAs of a row block form a cluster
 // and combine their (row max, partial denominator) pairs before normalising.
 struct SoftmaxEpi {
-    static constexpr int BN = 256, STAGES = 1, BOX_B = 256, EPI_WG = 2, E_BOXES = 0, O_BOXES = 4, XROUNDS = 1;
-    static constexpr int MIN_SMEM = 100 * 1024, MIN_BLOCKS = 2;  // two CTAs per SM: 2 x 256 TMEM columns
+    // persistent: one K chunk (the padded queries) per tile
+    static constexpr int BN = 256, BK = 64, STAGES = 1, BOX_B = 256, EPI_WG = 4, E_BOXES = 0, O_BOXES = 4;
+    static constexpr int XROUNDS = 1;
     static constexpr bool A_MN = false, B_MN = false;
     using Params = SoftmaxParams;
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
@@ -261,8 +262,8 @@ struct FhatParams {
 // chunk ahead.
 template <bool ETILE>
 struct FhatEpi {
-    static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 1;
-    static constexpr int MIN_SMEM = 100 * 1024, MIN_BLOCKS = ETILE ? 2 : 1;
+    // persistent, 32-wide K chunks (three ring stages fit beside two epilogue buffers)
+    static constexpr int BN = 256, BK = 32, STAGES = 3, BOX_B = 256, EPI_WG = ETILE ? 4 : 2, XROUNDS = 1;
     static constexpr int E_BOXES = ETILE ? BN / 64 : 0, O_BOXES = BN / 64;  // dFhat staged over the target
     static constexpr bool A_MN = false, B_MN = true;  // B = V (atoms x features), features contiguous
     using Params = FhatParams;
@@ -527,8 +528,10 @@ latentam_status encoder(EncodeTiledFn* out) {
 }
 
 // Tensor map of a row-major BF16 matrix (rows x inner, row stride ld elements), boxes of
-// 64 x box_rows with 128-byte swizzle; out-of-range elements read as zero.
-latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows) {
+// box_inner (64: 128-byte swizzle, 32: 64-byte swizzle) x box_rows; out-of-range elements read
+// as zero.
+latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows,
+                         int box_inner = tc::kChunkK) {
     EncodeTiledFn enc;
     LAT_TRY(encoder(&enc));
     if ((reinterpret_cast<uintptr_t>(base) & 15u) || (ld * 2) % 16) {
@@ -537,10 +540,11 @@ latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_
     }
     const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    const cuuint32_t box[2] = {(cuuint32_t)tc::kChunkK, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle sw = box_inner == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld operand", (int)r, (long long)rows,
@@ -587,6 +591,61 @@ latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 gri
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, omap ? *omap : a, g, p, err);
     if (e != cudaSuccess) return cuda_error(e, "tc_gemm_kernel launch");
     LAT_CHECK_LAUNCH("tc_gemm_kernel");
+    return LATENTAM_OK;
+}
+
+// Launch the persistent form of Epi over row_tiles 128-row tiles and gy column tiles (a
+// cluster of gy CTAs when the epilogue trades row partials): as many CTAs (clusters) as can be
+// resident at once, each walking its share of the row tiles.
+template <class Epi>
+latentam_status launch_persist(latentam_ctx* ctx, const CUtensorMap& a, const CUtensorMap& b, int row_tiles,
+                               int k_chunks, int gy, bool cluster, const typename Epi::Params& p, int* err,
+                               cudaStream_t st, const CUtensorMap* emap = nullptr,
+                               const CUtensorMap* omap = nullptr) {
+    constexpr size_t smem = tc::persist_smem_bytes<Epi>();
+    static_assert(smem <= 227 * 1024, "persistent tile does not fit in shared memory");
+    if (row_tiles <= 0) return LATENTAM_OK;
+    if (gy < 1 || (cluster && (gy > tc::kMaxCluster || Epi::XROUNDS == 0))) {
+        set_error("bad cluster shape %d", gy);
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    auto kern = tc::tc_persist_kernel<Epi>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "tc_persist smem attribute");
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(tc::gemm_threads(Epi::EPI_WG), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    int slots = ctx->num_sms / gy;  // one CTA per SM
+    if (cluster && gy > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1;
+        attr[0].val.clusterDim.y = (unsigned)gy;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        static int cached[tc::kMaxCluster + 1] = {0};
+        if (cached[gy] == 0) {
+            cfg.gridDim = dim3((unsigned)std::max(1, ctx->num_sms / gy), (unsigned)gy, 1);
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess || nc <= 0) {
+                (void)cudaGetLastError();
+                nc = std::max(1, ctx->num_sms / gy);
+            }
+            cached[gy] = nc;
+        }
+        slots = cached[gy];
+    }
+    cfg.gridDim = dim3((unsigned)std::max(1, std::min(row_tiles, slots)), (unsigned)gy, 1);
+    const tc::PersistGrid pg{k_chunks, row_tiles};
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, omap ? *omap : a, pg, p, err);
+    if (e != cudaSuccess) return cuda_error(e, "tc_persist_kernel launch");
+    LAT_CHECK_LAUNCH("tc_persist_kernel");
     return LATENTAM_OK;
 }
 
@@ -670,29 +729,29 @@ latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, 
     LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM));
     SoftmaxParams sp{n, M, c, b.A, stats};
     const int cy = cdiv(M, 256);
-    const dim3 grid(cdiv(n, kTileM), cy, 1);
-    const tc::GemmGrid g1{1, 1};
-    return launch_gemm<SoftmaxEpi>(mQ, mK, grid, g1, sp, b.err, st, nullptr, &mA, cy);
+    return launch_persist<SoftmaxEpi>(ctx, mQ, mK, cdiv(n, kTileM), 1, cy, true, sp, b.err, st, nullptr, &mA);
 }
 
-// G2: Fhat = A V, B = V read MN-major in 64 x 64 boxes (features x atoms).
-latentam_status tc_fhat(const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp, cudaStream_t st) {
+// G2: Fhat = A V (A in 32-wide K chunks, 64-byte swizzle), B = V read MN-major in 64 x 32
+// boxes (features x atoms).
+latentam_status tc_fhat(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp,
+                        cudaStream_t st) {
+    constexpr int BK = FhatEpi<true>::BK;
     CUtensorMap mA, mV;
-    LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM));
-    LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, 64));
-    const int cy = cdiv(D, 256);
-    const dim3 grid(cdiv(n, kTileM), cy, 1);
-    const tc::GemmGrid g{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
-    if (fp.Fout) return launch_gemm<FhatEpi<false>>(mA, mV, grid, g, fp, b.err, st);  // no row terms
+    LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM, BK));
+    LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, BK));
+    const int cy = cdiv(D, 256), tiles = cdiv(n, kTileM), kc = cdiv(M, BK);
+    if (fp.Fout)  // no row terms: independent column tiles
+        return launch_persist<FhatEpi<false>>(ctx, mA, mV, tiles, kc, cy, false, fp, b.err, st);
     CUtensorMap mdF;  // dFhat leaves through the TMA
     LAT_TRY(bf16_map(&mdF, fp.dF, D, n, D, kTileM));
     if (fp.F_dtype == LATENTAM_DTYPE_BF16) {
         // BF16 targets: the tile's target rows are TMA-loaded into shared memory for the epilogue
         CUtensorMap mF;
         LAT_TRY(bf16_map(&mF, fp.F, D, n, D, kTileM));
-        return launch_gemm<FhatEpi<true>>(mA, mV, grid, g, fp, b.err, st, &mF, &mdF, cy);
+        return launch_persist<FhatEpi<true>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, &mF, &mdF);
     }
-    return launch_gemm<FhatEpi<false>>(mA, mV, grid, g, fp, b.err, st, nullptr, &mdF, cy);
+    return launch_persist<FhatEpi<false>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, nullptr, &mdF);
 }
 
 }  // namespace
@@ -727,7 +786,7 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
         LAT_TRY(tc_forward(ctx, a.Q, n, d, a.K, a.V, M, D, a.c, b, nullptr, st));
         // G2: Fhat = A V -> loss terms -> dFhat
         FhatParams fp{n, D, a.F, a.F_dtype, a.mask, a.cfg, b.acc, b.dF, b.row, nullptr};
-        LAT_TRY(tc_fhat(b, n, M, D, fp, st));
+        LAT_TRY(tc_fhat(ctx, b, n, M, D, fp, st));
         // G3: dA = dFhat V^T -> dS
         CUtensorMap mdF, mV, mdS, mK;
         LAT_TRY(bf16_map(&mdF, b.dF, D, n, D, kTileM));
@@ -790,7 +849,7 @@ latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, in
     LAT_TRY(tc_forward(ctx, Q, n, d, K, V, M, D, c, b, row_stats, st));
     if (F_hat) {
         FhatParams fp{n, D, nullptr, LATENTAM_DTYPE_F32, nullptr, latentam_loss_cfg{}, b.acc, nullptr, b.row, F_hat};
-        LAT_TRY(tc_fhat(b, n, M, D, fp, st));
+        LAT_TRY(tc_fhat(ctx, b, n, M, D, fp, st));
     }
     return LATENTAM_OK;
 }

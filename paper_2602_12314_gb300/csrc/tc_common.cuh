@@ -188,13 +188,21 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// Shared-memory descriptor of a K-major tile written by TMA with 64-byte swizzle: rows of 32
+// BF16 (64 B), 8-row atoms 512 B apart.  `saddr` is the (512-aligned tile base + k * 32 B)
+// shared address.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
 // Shared-memory descriptor of an MN-major tile written by TMA with 128-byte swizzle in boxes of
-// 64 (MN, contiguous) x 64 (K rows): within a box, rows of 64 BF16 (128 B) and 8-row atoms
-// 1024 B apart (SBO); consecutive 64-wide MN blocks (boxes) 8 KB apart (LBO).  `saddr` is the
-// (1024-aligned tile base + k * 128 B) shared address for K row k.
-constexpr uint32_t kMnBoxBytes = 64 * 128;
-__device__ __forceinline__ uint64_t mn128_desc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kMnBoxBytes >> 4) << 16) |
+// 64 (MN, contiguous) x BK (K rows): within a box, rows of 64 BF16 (128 B) and 8-row atoms
+// 1024 B apart (SBO); consecutive 64-wide MN blocks (boxes) box_bytes apart (LBO).  `saddr` is
+// the (1024-aligned tile base + k * 128 B) shared address for K row k.
+constexpr uint32_t kMnBoxBytes = 64 * 128;  // a 64 x 64 box
+__device__ __forceinline__ uint64_t mn128_desc(uint32_t saddr, uint32_t box_bytes = kMnBoxBytes) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(box_bytes >> 4) << 16) |
            ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 

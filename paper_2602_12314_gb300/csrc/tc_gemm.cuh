@@ -18,7 +18,9 @@ namespace lat {
 namespace tc {
 
 constexpr int kTileM = 128;
-constexpr int kScratchBytes = 4 * 2 * kTileM * 4;  // epilogue row-reduction scratch: 4 slots x 2 groups
+// epilogue row-reduction scratch: 4 slots x G warpgroups
+__host__ __device__ constexpr int scratch_bytes(int groups) { return 4 * groups * kTileM * 4; }
+constexpr int kScratchBytes = scratch_bytes(2);
 constexpr int kMaxCluster = 4;                    // CTAs of a cluster that trade row partials
 constexpr int kXchgVals = 4;                      // values per row per CTA in one exchange
 constexpr int kXchgBytes = kMaxCluster * kXchgVals * kTileM * 4;
@@ -58,21 +60,21 @@ __device__ __forceinline__ void epi_sync(int nthreads) {
 template <int G>
 __device__ __forceinline__ float group_sum(float v, float* scratch, int slot, int g, int row) {
     if (G == 1) return v;
-    scratch[(slot * 2 + g) * kTileM + row] = v;
+    scratch[(slot * G + g) * kTileM + row] = v;
     epi_sync(128 * G);
     float s = 0.f;
 #pragma unroll
-    for (int k = 0; k < G; ++k) s += scratch[(slot * 2 + k) * kTileM + row];
+    for (int k = 0; k < G; ++k) s += scratch[(slot * G + k) * kTileM + row];
     return s;
 }
 template <int G>
 __device__ __forceinline__ float group_max(float v, float* scratch, int slot, int g, int row) {
     if (G == 1) return v;
-    scratch[(slot * 2 + g) * kTileM + row] = v;
+    scratch[(slot * G + g) * kTileM + row] = v;
     epi_sync(128 * G);
     float s = -INFINITY;
 #pragma unroll
-    for (int k = 0; k < G; ++k) s = fmaxf(s, scratch[(slot * 2 + k) * kTileM + row]);
+    for (int k = 0; k < G; ++k) s = fmaxf(s, scratch[(slot * G + k) * kTileM + row]);
     return s;
 }
 
@@ -106,6 +108,8 @@ struct EpiCtx {
     int crank, csize;      // rank of this CTA in its cluster, cluster size
     uint64_t* xbar;        // arrivals of the other CTAs' row partials
     float* xbuf;           // [rank][value][row] partials received from the other CTAs
+    uint32_t ephase = 0;   // phase parity of the epilogue-operand barriers for this tile
+    uint32_t xphase = 0;   // phase parity of xbar for this tile
 
     // Send this row's kXchgVals partials to every other CTA of the cluster and wait for theirs
     // (read back with xval).  Warpgroup 0 sends; every epilogue thread waits.  Bounded: false
@@ -121,7 +125,7 @@ struct EpiCtx {
                 mbar_arrive_peer(peer_addr(xbar, (uint32_t)q));
             }
         }
-        const bool ok = mbar_wait_cluster(xbar, 0);
+        const bool ok = mbar_wait_cluster(xbar, xphase);
         if (!ok) *abort = 1;
         return ok;
     }
@@ -129,7 +133,7 @@ struct EpiCtx {
     __device__ __forceinline__ float xval(int q, int k) const { return xbuf[(q * kXchgVals + k) * kTileM + row]; }
 
     // Wait for box b of the epilogue operand (bounded; false if it gave up).
-    __device__ __forceinline__ bool wait_box(int b) const { return mbar_wait(&ebar[b], 0, abort); }
+    __device__ __forceinline__ bool wait_box(int b) const { return mbar_wait(&ebar[b], ephase, abort); }
     // Stage 32 values of this thread's row as BF16 at column c0 (a multiple of 32) of the output.
     __device__ __forceinline__ void put32(int c0, const float (&v)[32]) const {
         uint8_t* base = otile + (c0 >> 6) * (kTileM * 128) + row * 128;
@@ -350,6 +354,291 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+
+// ---- persistent form ----------------------------------------------------------------------
+//
+// One CTA per SM (or one cluster of CTAs along y per group of SMs) walks the 128-row tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Two TMEM accumulators of BN columns alternate
+// between tiles, so the MMAs of tile t+1 run while the epilogue of tile t drains the other
+// accumulator; the operand ring runs on across tiles.  The epilogue operand and the staged
+// output of a tile share one of two box buffers: the producer thread, once it has queued the
+// operands of tile t, sends the staged output of tile t-2 out of buffer t % 2 with TMA stores,
+// waits until they have read it, and loads the epilogue operand of tile t there, while the
+// epilogue works on tile t-1 from the other buffer.
+//
+// Barriers (phase parity in brackets; lt = this CTA's tile counter, it = k-chunk counter,
+// e = lt & 1, u = lt >> 1):
+//   full[s] / empty[s]   operand ring                                  [(it / STAGES) & 1]
+//   acc_full[e]          MMAs of tile lt done -> epilogue              [u & 1]
+//   acc_empty[e]         epilogue done reading TMEM -> MMA (tile lt+2) [(u - 1) & 1]
+//   e_full[e][k]         epilogue operand box k of tile lt loaded      [u & 1]
+//   e_free[e]            buffer e free for tile lt's output (no operand) [u & 1]
+//   staged[e]            output of tile lt staged in buffer e          [u & 1]
+//   xbar[e]              cluster row exchange of tile lt               [u & 1]
+struct PersistGrid {
+    int k_chunks;   // Epi::BK-wide K chunks per tile
+    int row_tiles;  // 128-row tiles of A
+};
+
+template <class Epi>
+__host__ __device__ constexpr uint32_t persist_box_bytes() {  // one box buffer
+    return (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * kTileABytes;
+}
+
+// One ring stage: A (128 x BK) and B (BN x BK) BF16.
+template <class Epi>
+__host__ __device__ constexpr uint32_t persist_stage_bytes() {
+    return (uint32_t)(kTileM + Epi::BN) * Epi::BK * 2;
+}
+
+template <class Epi>
+__host__ __device__ constexpr size_t persist_smem_bytes() {
+    return (size_t)Epi::STAGES * persist_stage_bytes<Epi>() + 2 * persist_box_bytes<Epi>() +
+           1024 /* alignment */ + 512 /* barriers */ + scratch_bytes(Epi::EPI_WG) +
+           (Epi::XROUNDS > 0 ? 2 * kXchgBytes : 0);
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
+    tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmO,
+                      PersistGrid pg, typename Epi::Params ep, int* __restrict__ err) {
+    constexpr int BN = Epi::BN;
+    constexpr int STAGES = Epi::STAGES;
+    constexpr int BOX_B = Epi::BOX_B;
+    constexpr int G = Epi::EPI_WG;
+    constexpr int BK = Epi::BK;  // 64: 128-byte swizzled K-major rows; 32: 64-byte swizzled
+    constexpr uint32_t A_BYTES = (uint32_t)kTileM * BK * 2;
+    constexpr uint32_t STAGE_BYTES = persist_stage_bytes<Epi>();
+    constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;
+    constexpr uint32_t MN_BOX = 64u * BK * 2;  // one 64 (MN) x BK (K) box of an MN-major operand
+    constexpr uint32_t BOX_BYTES = persist_box_bytes<Epi>();
+    constexpr bool A_MN = Epi::A_MN, B_MN = Epi::B_MN;
+    constexpr uint32_t IDESC = idesc_bf16(kTileM, BN, A_MN, B_MN);
+    constexpr int E_BOXES = Epi::E_BOXES, O_BOXES = Epi::O_BOXES;
+    static_assert(BN % 16 == 0 && BN <= 256, "two accumulators of BN <= 256 columns fill TMEM");
+    static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
+    static_assert(!B_MN || BN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
+    static_assert(E_BOXES <= 4 && O_BOXES <= 4 && Epi::XROUNDS <= 1 && G <= 4, "epilogue shape");
+    static_assert(BK == 64 || BK == 32, "K chunk of 64 or 32");
+    static_assert(!A_MN, "the persistent tile reads A K-major");
+    static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "stages stay 1024-byte aligned");
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* boxes = smem + PIPE_BYTES;  // [2][BOX_BYTES]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(boxes + 2 * BOX_BYTES);
+    uint64_t* full = bars;                // [STAGES]
+    uint64_t* empty = full + STAGES;      // [STAGES]
+    uint64_t* acc_full = empty + STAGES;  // [2]
+    uint64_t* acc_empty = acc_full + 2;   // [2]
+    uint64_t* e_full = acc_empty + 2;     // [2][4]
+    uint64_t* e_free = e_full + 8;        // [2]
+    uint64_t* staged = e_free + 2;        // [2]
+    uint64_t* xbars = staged + 2;         // [2]
+    uint64_t* drain = xbars + 2;          // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* decision = abort_flag + 1;
+    volatile int* nbox = decision + 1;  // [2]: output boxes staged in each buffer
+    float* scratch = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 512);
+    float* xbufs = scratch + scratch_bytes(G) / 4;
+
+    uint32_t csize = 1;
+    if (Epi::XROUNDS > 0) asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+    const uint32_t crank = csize > 1 ? cluster_rank() : 0u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.y * BN;
+    const int nk = pg.k_chunks;
+    const int first = blockIdx.x, stride = gridDim.x;
+    const int my_tiles = first < pg.row_tiles ? (pg.row_tiles - first + stride - 1) / stride : 0;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int e = 0; e < 2; ++e) {
+            mbar_init(&acc_full[e], 1);
+            mbar_init(&acc_empty[e], 1);
+            for (int b = 0; b < E_BOXES; ++b) mbar_init(&e_full[4 * e + b], 1);
+            mbar_init(&e_free[e], 1);
+            mbar_init(&staged[e], 1);
+            if (csize > 1) mbar_init(&xbars[e], (uint32_t)kTileM * (csize - 1));
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+        if (E_BOXES > 0) prefetch_tmap(&tmE);
+        if (O_BOXES > 0) prefetch_tmap(&tmO);
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (csize > 1) cluster_sync_all();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0 && nk > 0) {
+            // ---- TMA producer: operand ring; output stores and epilogue operands ----
+            int it = 0, lt = 0, stored = 0, e_issued = -1;
+            bool ok = true;
+            // send the staged output of tile t (its buffer is t & 1) and wait until it was read
+            auto store_tile = [&](int t) -> bool {
+                if (!mbar_wait(&staged[t & 1], (uint32_t)(t >> 1) & 1u, abort_flag)) return false;
+                const int nb = nbox[t & 1];
+                const int m0t = (first + t * stride) * kTileM;
+                for (int b = 0; b < nb && b < O_BOXES; ++b)
+                    tma_store_2d(&tmO, boxes + (t & 1) * BOX_BYTES + b * kTileABytes, n0 + 64 * b, m0t);
+                bulk_commit();
+                bulk_wait_read();
+                return true;
+            };
+            for (; lt < my_tiles && ok; ++lt) {
+                const int m0 = (first + lt * stride) * kTileM;
+                for (int i = 0; i < nk; ++i, ++it) {
+                    const int s = it % STAGES;
+                    if (it >= STAGES && !mbar_wait(&empty[s], ((uint32_t)(it / STAGES) & 1u) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sa = smem + s * STAGE_BYTES;
+                    uint8_t* sb = sa + A_BYTES;
+                    const int kx = i * BK;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(sa, &tmA, &full[s], kx, m0);
+                    if (B_MN) {
+#pragma unroll
+                        for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * MN_BOX, &tmB, &full[s], n0 + 64 * b, kx);
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < BN / BOX_B; ++b)
+                            tma_load_2d(sb + b * BOX_B * BK * 2, &tmB, &full[s], kx, n0 + b * BOX_B);
+                    }
+                }
+                if (!ok) break;
+                // buffer lt & 1 last held tile lt - 2
+                if (lt >= 2) {
+                    if (!store_tile(lt - 2)) {
+                        ok = false;
+                        break;
+                    }
+                    stored = lt - 1;
+                }
+                const int e = lt & 1;
+                if (E_BOXES > 0) {
+                    for (int b = 0; b < E_BOXES; ++b) {
+                        mbar_expect_tx(&e_full[4 * e + b], kTileABytes);
+                        tma_load_2d(boxes + e * BOX_BYTES + b * kTileABytes, &tmE, &e_full[4 * e + b], n0 + 64 * b,
+                                    m0);
+                    }
+                    e_issued = lt;
+                } else {
+                    mbar_arrive(&e_free[e]);
+                }
+            }
+            if (ok) {
+                for (int t = stored; t < my_tiles && ok; ++t) ok = store_tile(t);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                // never leave the CTA with copies in flight
+                for (int j = max(0, it - STAGES); j < it; ++j)
+                    (void)mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u, nullptr);
+                for (int t = max(0, e_issued - 1); t <= e_issued; ++t)
+                    for (int b = 0; b < E_BOXES; ++b)
+                        (void)mbar_wait(&e_full[4 * (t & 1) + b], (uint32_t)(t >> 1) & 1u, nullptr);
+                bulk_wait_read();
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && nk > 0) {
+            // ---- MMA issuer ----
+            int it = 0;
+            bool ok = true;
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
+                const int buf = lt & 1, use = lt >> 1;
+                if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)(use - 1) & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dst = tmem_base + (uint32_t)(buf * BN);
+                for (int i = 0; i < nk; ++i, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t da = BK == 64 ? sw128_desc(sa + kk * 32) : sw64_desc(sa + kk * 32);
+                        const uint64_t db = B_MN ? mn128_desc(sb + kk * 16 * 128, MN_BOX)
+                                                 : (BK == 64 ? sw128_desc(sb + kk * 32) : sw64_desc(sb + kk * 32));
+                        mma_bf16(dst, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[buf]);
+            }
+            if (!ok) *abort_flag = 1;
+            // every MMA issued by this thread has completed before TMEM is released
+            mma_commit(drain);
+            (void)mbar_wait(drain, 0, nullptr);
+        }
+    } else {
+        // ---- epilogue warps ----
+        const int quarter = warp & 3;
+        const int group = (warp - 2) >> 2;
+        const int row = quarter * 32 + lane;
+        for (int lt = 0; lt < my_tiles; ++lt) {
+            const int e = lt & 1, use = lt >> 1;
+            const int tile = first + lt * stride;
+            bool ready = nk > 0 && mbar_wait(&acc_full[e], (uint32_t)use & 1u, abort_flag);
+            if (ready && E_BOXES == 0 && O_BOXES > 0) ready = mbar_wait(&e_free[e], (uint32_t)use & 1u, abort_flag);
+            tc_fence_after();
+            if (!ready) *abort_flag = 1;
+            epi_sync(128 * G);
+            if (threadIdx.x == 64) *decision = *abort_flag ? 0 : 1;
+            epi_sync(128 * G);
+            uint8_t* box = boxes + e * BOX_BYTES;
+            EpiCtx ec{tmem_base + (uint32_t)(e * BN) + ((uint32_t)(quarter * 32) << 16),
+                      row, tile * kTileM, n0, 0, group, scratch, E_BOXES > 0 ? box : nullptr, box,
+                      &e_full[4 * e], abort_flag, (int)crank, (int)csize, &xbars[e],
+                      xbufs + e * (kXchgBytes / 4), (uint32_t)use & 1u, (uint32_t)use & 1u};
+            int out_boxes = 0;
+            if (*decision) {
+                out_boxes = Epi::run(ep, ec);
+            } else if (Epi::XROUNDS > 0) {
+                const float zero[kXchgVals] = {0.f, 0.f, 0.f, 0.f};
+                (void)ec.exchange(zero);
+            }
+            // TMEM and the staged output are handed over once every epilogue thread is done
+            tc_fence_before();
+            fence_proxy_async();
+            epi_sync(128 * G);
+            if (threadIdx.x == 64) {
+                mbar_arrive(&acc_empty[e]);
+                nbox[e] = *abort_flag ? 0 : out_boxes;
+                mbar_arrive(&staged[e]);
+            }
+        }
+    }
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 512);
     }
 }
 
