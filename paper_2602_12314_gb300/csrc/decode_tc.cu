@@ -132,14 +132,6 @@ __global__ void tc_finalize(const double* __restrict__ acc, const int* __restric
 
 // ---- epilogues ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void store_row_bf16x32(bf16* dst, const float (&v)[32]) {
-    uint4* d4 = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        d4[q] = make_uint4(tc::pack_bf16x2(v[8 * q], v[8 * q + 1]), tc::pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
-                           tc::pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), tc::pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
-}
-
 __device__ __forceinline__ void load_row_bf16x32(const bf16* src, float (&v)[32]) {
     const uint4* s4 = reinterpret_cast<const uint4*>(src);
 #pragma unroll
@@ -315,35 +307,32 @@ struct FhatEpi {
         }
         // invalid rows read row 0 (discarded)
         const int64_t frow = (valid ? pix * p.D : 0) + ec.n0;
+        // per-row and per-frame inputs first: their latency hides behind the first pass
+        const bool in_loss = valid && (p.mask == nullptr || p.mask[pix] != 0);
+        const float nv = (float)p.acc[3];
         if (ETILE)
             for (int b = 0; b < E_BOXES; ++b) (void)ec.wait_box(b);  // a timeout raises the error flag
-        float dot = 0.f, nh2 = 0.f, nf2 = 0.f, e2 = 0.f;
+        float t[4] = {0.f, 0.f, 0.f, 0.f};  // <Fhat, F>, |Fhat|^2, |F|^2, |Fhat - F|^2
         sweep(p, ec, frow, ncols, [&](int, const float(&h)[32], const float(&f)[32]) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                dot += h[i] * f[i];
-                nh2 += h[i] * h[i];
-                nf2 += f[i] * f[i];
+                t[0] += h[i] * f[i];
+                t[1] += h[i] * h[i];
+                t[2] += f[i] * f[i];
                 const float e = h[i] - f[i];
-                e2 += e * e;
+                t[3] += e * e;
             }
         });
-        dot = tc::group_sum<EPI_WG>(dot, scr, 0, g, row);
-        nh2 = tc::group_sum<EPI_WG>(nh2, scr, 1, g, row);
-        nf2 = tc::group_sum<EPI_WG>(nf2, scr, 2, g, row);
-        e2 = tc::group_sum<EPI_WG>(e2, scr, 3, g, row);
-        const float mine[tc::kXchgVals] = {dot, nh2, nf2, e2};
-        ec.exchange(mine);
+        tc::group_sum4<EPI_WG>(t, scr, g, row);
+        ec.exchange(t);
         for (int q = 0; q < ec.csize; ++q) {
             if (q == ec.crank) continue;
-            dot += ec.xval(q, 0);
-            nh2 += ec.xval(q, 1);
-            nf2 += ec.xval(q, 2);
-            e2 += ec.xval(q, 3);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] += ec.xval(q, k);
         }
-        const bool in_loss = valid && (p.mask == nullptr || p.mask[pix] != 0);
-        const double nv = p.acc[3];
-        const float scale = nv > 0.0 ? (float)((double)p.cfg.lambda_f / nv) : 0.f;
+        const float dot = t[0], nh2 = t[1], nf2 = t[2], e2 = t[3];
+        // FP32 arithmetic per row (FP64 only in the frame sums below)
+        const float scale = nv > 0.f ? p.cfg.lambda_f / nv : 0.f;
         const float den = sqrtf(nh2) * sqrtf(nf2);
         const float cs = dot / fmaxf(den, 1e-8f);
         float a = 0.f, b = 0.f;
@@ -358,22 +347,19 @@ struct FhatEpi {
             }
         }
         const bool lead = g == 0 && ec.crank == 0;  // one thread per row writes the row's results
-        if (valid && lead) {
-            p.row[4 * pix] = a;
-            p.row[4 * pix + 1] = b;
-            p.row[4 * pix + 2] = a * nh2 + b * dot;
-            p.row[4 * pix + 3] = cs;
-        }
+        if (valid && lead)
+            *reinterpret_cast<float4*>(p.row + 4 * pix) = make_float4(a, b, a * nh2 + b * dot, cs);
         if (lead) {
-            double lc = in_loss ? 1.0 - (double)cs : 0.0, le = in_loss ? (double)e2 : 0.0;
+            // warp partial sums in FP32 (32 rows), added to the frame sums in FP64
+            float lc = in_loss ? 1.0f - cs : 0.f, le = in_loss ? e2 : 0.f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 lc += __shfl_xor_sync(0xffffffffu, lc, o);
                 le += __shfl_xor_sync(0xffffffffu, le, o);
             }
             if ((threadIdx.x & 31) == 0) {
-                atomicAdd(&p.acc[0], lc);
-                atomicAdd(&p.acc[1], le);
+                atomicAdd(&p.acc[0], (double)lc);
+                atomicAdd(&p.acc[1], (double)le);
             }
         }
         // dFhat overwrites the target chunk it was formed from (same thread, same bytes)
@@ -617,7 +603,7 @@ latentam_status launch_persist(latentam_ctx* ctx, const CUtensorMap& a, const CU
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(tc::gemm_threads(Epi::EPI_WG), 1, 1);
+    cfg.blockDim = dim3(tc::persist_threads(Epi::EPI_WG), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

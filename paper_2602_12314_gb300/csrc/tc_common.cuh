@@ -82,37 +82,25 @@ __device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
     return r;
 }
 
-__device__ __forceinline__ void st_peer_f32(uint32_t addr, float v) {
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+// Bulk copy of `bytes` (a multiple of 16) from this CTA's shared memory to the shared memory of
+// another CTA of the cluster, completing `bytes` transactions on that CTA's mbarrier.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst_cluster, const void* src, uint32_t bytes,
+                                                  uint32_t bar_cluster) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_cluster),
+                 "r"(smem_u32(src)), "r"(bytes), "r"(bar_cluster)
+                 : "memory");
 }
 
-// Arrive on an mbarrier of another CTA of the cluster; orders this thread's earlier stores
-// to that CTA before the arrival.
-__device__ __forceinline__ void mbar_arrive_peer(uint32_t bar_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for arrivals from other CTAs of the cluster.  The limit is longer than that of
-// the pipeline waits, so that a peer which gave up on its own pipeline still gets to arrive.
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
+// Bounded wait, longer than the pipeline waits, so that a peer CTA which gave up on its own
+// pipeline still gets to deliver before this one gives up.
+__device__ __forceinline__ bool mbar_wait_long(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     while (true) {
-        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if (global_timer_ns() - t0 > 4 * kWaitLimitNs) return false;
-        __nanosleep(64);
+        __nanosleep(32);
     }
 }
 
@@ -127,6 +115,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
             smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
+}
+
+// Prefetch the 2D TMA tile at (x, y) into L2 (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
 }
 
 // 2D TMA tile store from shared memory (bulk-group completion).  Coordinates are never

@@ -21,9 +21,10 @@ constexpr int kTileM = 128;
 // epilogue row-reduction scratch: 4 slots x G warpgroups
 __host__ __device__ constexpr int scratch_bytes(int groups) { return 4 * groups * kTileM * 4; }
 constexpr int kScratchBytes = scratch_bytes(2);
-constexpr int kMaxCluster = 4;                    // CTAs of a cluster that trade row partials
-constexpr int kXchgVals = 4;                      // values per row per CTA in one exchange
-constexpr int kXchgBytes = kMaxCluster * kXchgVals * kTileM * 4;
+constexpr int kMaxCluster = 4;                         // CTAs of a cluster that trade row partials
+constexpr int kXchgVals = 4;                           // values per row per CTA in one exchange
+constexpr int kXchgMsg = kXchgVals * kTileM * 4;       // one CTA's partials of a tile (bytes)
+constexpr int kXchgBytes = kMaxCluster * kXchgMsg;     // one outgoing + (kMaxCluster - 1) incoming
 constexpr int kChunkK = 64;                       // BF16 elements per 128-byte row
 constexpr uint32_t kTileABytes = kTileM * 128;    // 16 KB
 
@@ -43,7 +44,7 @@ __host__ __device__ constexpr uint32_t tile_region_bytes() {
 template <class Epi>
 __host__ __device__ constexpr size_t gemm_smem_bytes() {
     const size_t need = (size_t)tile_region_bytes<Epi>() + 1024 /* alignment */ + 256 /* barriers */ +
-                        kScratchBytes + (Epi::XROUNDS > 0 ? kXchgBytes : 0);
+                        kScratchBytes;
     // MIN_SMEM caps the CTAs resident on one SM (so that their TMEM allocations never wait)
     return need > (size_t)Epi::MIN_SMEM ? need : (size_t)Epi::MIN_SMEM;
 }
@@ -66,6 +67,22 @@ __device__ __forceinline__ float group_sum(float v, float* scratch, int slot, in
 #pragma unroll
     for (int k = 0; k < G; ++k) s += scratch[(slot * G + k) * kTileM + row];
     return s;
+}
+// The four per-row values v[0..3] summed over the G epilogue warpgroups with one barrier
+// (slots 0..3).
+template <int G>
+__device__ __forceinline__ void group_sum4(float (&v)[4], float* scratch, int g, int row) {
+    if (G == 1) return;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) scratch[(k * G + g) * kTileM + row] = v[k];
+    epi_sync(128 * G);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < G; ++j) s += scratch[(k * G + j) * kTileM + row];
+        v[k] = s;
+    }
 }
 template <int G>
 __device__ __forceinline__ float group_max(float v, float* scratch, int slot, int g, int row) {
@@ -106,31 +123,44 @@ struct EpiCtx {
     uint64_t* ebar;        // one barrier per box
     volatile int* abort;
     int crank, csize;      // rank of this CTA in its cluster, cluster size
-    uint64_t* xbar;        // arrivals of the other CTAs' row partials
-    float* xbuf;           // [rank][value][row] partials received from the other CTAs
+    uint64_t* xbar;        // completes when every other CTA's partials of this tile arrived
+    float* xbuf;           // [value][row] outgoing partials, then [peer slot][value][row] incoming
     uint32_t ephase = 0;   // phase parity of the epilogue-operand barriers for this tile
     uint32_t xphase = 0;   // phase parity of xbar for this tile
+    int ngroups = 1;       // epilogue warpgroups
+    int leader = 64;       // first epilogue thread
 
-    // Send this row's kXchgVals partials to every other CTA of the cluster and wait for theirs
-    // (read back with xval).  Warpgroup 0 sends; every epilogue thread waits.  Bounded: false
-    // (and the error flag raised) if the partials did not all arrive.
+    // Give this row's kXchgVals partials to every other CTA of the cluster and wait for theirs
+    // (read back with xval).  Warpgroup 0 stages the CTA's partials in shared memory; one thread
+    // arms this CTA's barrier for the incoming bytes and sends the block to each peer with one
+    // bulk copy that completes on the peer's barrier.  Called by every epilogue thread.
+    // Bounded: false (and the error flag raised) if the partials did not all arrive.
     __device__ __forceinline__ bool exchange(const float (&v)[kXchgVals]) const {
         if (csize <= 1) return true;
         if (g == 0) {
+#pragma unroll
+            for (int k = 0; k < kXchgVals; ++k) xbuf[k * kTileM + row] = v[k];
+            fence_proxy_async();
+        }
+        epi_sync(128 * ngroups);
+        if ((int)threadIdx.x == leader) {
+            mbar_expect_tx(xbar, (uint32_t)((csize - 1) * kXchgMsg));
             for (int q = 0; q < csize; ++q) {
                 if (q == crank) continue;
-#pragma unroll
-                for (int k = 0; k < kXchgVals; ++k)
-                    st_peer_f32(peer_addr(xbuf + (crank * kXchgVals + k) * kTileM + row, (uint32_t)q), v[k]);
-                mbar_arrive_peer(peer_addr(xbar, (uint32_t)q));
+                const int slot = 1 + (crank < q ? crank : crank - 1);  // this CTA's slot at q
+                bulk_copy_to_peer(peer_addr(xbuf + slot * (kXchgMsg / 4), (uint32_t)q), xbuf, kXchgMsg,
+                                  peer_addr(xbar, (uint32_t)q));
             }
         }
-        const bool ok = mbar_wait_cluster(xbar, xphase);
+        const bool ok = mbar_wait_long(xbar, xphase);
         if (!ok) *abort = 1;
         return ok;
     }
     // Partial k of this thread's row from CTA q (q != crank) of the cluster.
-    __device__ __forceinline__ float xval(int q, int k) const { return xbuf[(q * kXchgVals + k) * kTileM + row]; }
+    __device__ __forceinline__ float xval(int q, int k) const {
+        const int slot = 1 + (q < crank ? q : q - 1);
+        return xbuf[slot * (kXchgMsg / 4) + k * kTileM + row];
+    }
 
     // Wait for box b of the epilogue operand (bounded; false if it gave up).
     __device__ __forceinline__ bool wait_box(int b) const { return mbar_wait(&ebar[b], ephase, abort); }
@@ -184,7 +214,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     constexpr int E_BOXES = Epi::E_BOXES;
     constexpr uint32_t TILE_REGION = tile_region_bytes<Epi>();
     static_assert(E_BOXES <= 8 && Epi::O_BOXES <= 8, "at most 8 boxes of epilogue operand / output");
-    static_assert(Epi::XROUNDS == 0 || Epi::XROUNDS == 1, "at most one row exchange per tile");
+    static_assert(Epi::XROUNDS == 0, "row exchanges run in the persistent form");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -195,12 +225,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* decision = abort_flag + 1;
     uint64_t* ebar = reinterpret_cast<uint64_t*>(tmem_slot + 4);  // 8-byte aligned, 8 barriers
-    uint64_t* xbar = ebar + 8;
     float* scratch = reinterpret_cast<float*>(smem + TILE_REGION + 256);
-    float* xbuf = scratch + kScratchBytes / 4;
-    uint32_t csize = 1;
-    if (Epi::XROUNDS > 0) asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
-    const uint32_t crank = csize > 1 ? cluster_rank() : 0u;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTileM;
@@ -216,7 +241,6 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
         }
         mbar_init(accum, 1);
         for (int b = 0; b < E_BOXES; ++b) mbar_init(&ebar[b], 1);
-        if (csize > 1) mbar_init(xbar, (uint32_t)kTileM * (csize - 1));
         *abort_flag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmA);
@@ -226,8 +250,6 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // the other CTAs' exchange barriers are initialised before anyone arrives on them
-    if (csize > 1) cluster_sync_all();
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
@@ -323,15 +345,9 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
         if (threadIdx.x == 64) *decision = (nk > 0 && !*abort_flag) ? 1 : 0;
         epi_sync(128 * Epi::EPI_WG);
         EpiCtx ec{tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch,
-                  E_BOXES > 0 ? smem : nullptr, smem, ebar, abort_flag, (int)crank, (int)csize, xbar, xbuf};
+                  E_BOXES > 0 ? smem : nullptr, smem, ebar, abort_flag, 0, 1, nullptr, nullptr};
         int out_boxes = 0;
-        if (*decision) {
-            out_boxes = Epi::run(ep, ec);
-        } else if (Epi::XROUNDS > 0) {
-            // keep the cluster's exchange protocol: the other CTAs wait for this one's partials
-            const float zero[kXchgVals] = {0.f, 0.f, 0.f, 0.f};
-            (void)ec.exchange(zero);
-        }
+        if (*decision) out_boxes = Epi::run(ep, ec);
         if (Epi::O_BOXES > 0) {
             // the staged output tile goes out through the TMA once every epilogue thread wrote
             // its part (coalesced and asynchronous, instead of one row per thread)
@@ -364,10 +380,14 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
 // blockIdx.x, blockIdx.x + gridDim.x, ...  Two TMEM accumulators of BN columns alternate
 // between tiles, so the MMAs of tile t+1 run while the epilogue of tile t drains the other
 // accumulator; the operand ring runs on across tiles.  The epilogue operand and the staged
-// output of a tile share one of two box buffers: the producer thread, once it has queued the
-// operands of tile t, sends the staged output of tile t-2 out of buffer t % 2 with TMA stores,
-// waits until they have read it, and loads the epilogue operand of tile t there, while the
-// epilogue works on tile t-1 from the other buffer.
+// output of a tile share one of two box buffers: for tile t a second producer thread sends the
+// staged output of tile t-2 out of buffer t % 2 with TMA stores, waits until they have read it,
+// and loads the epilogue operand of tile t there, while the epilogue works on tile t-1 from the
+// other buffer.
+//
+// Warp roles (96 + 128 G threads): warp 0 queues the operand ring, warp 1 owns TMEM and issues
+// the MMAs, warp 2 moves the box buffers (stores out, epilogue operands in), warps 3.. run the
+// epilogue (thread 96 leads it).
 //
 // Barriers (phase parity in brackets; lt = this CTA's tile counter, it = k-chunk counter,
 // e = lt & 1, u = lt >> 1):
@@ -394,15 +414,17 @@ __host__ __device__ constexpr uint32_t persist_stage_bytes() {
     return (uint32_t)(kTileM + Epi::BN) * Epi::BK * 2;
 }
 
+__host__ __device__ constexpr int persist_threads(int epi_warpgroups) { return 96 + 128 * epi_warpgroups; }
+
 template <class Epi>
 __host__ __device__ constexpr size_t persist_smem_bytes() {
     return (size_t)Epi::STAGES * persist_stage_bytes<Epi>() + 2 * persist_box_bytes<Epi>() +
            1024 /* alignment */ + 512 /* barriers */ + scratch_bytes(Epi::EPI_WG) +
-           (Epi::XROUNDS > 0 ? 2 * kXchgBytes : 0);
+           (Epi::XROUNDS > 0 ? 2 * kXchgBytes : 0);  // one exchange buffer per accumulator
 }
 
 template <class Epi>
-__global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
+__global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
     tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmO,
                       PersistGrid pg, typename Epi::Params ep, int* __restrict__ err) {
@@ -467,7 +489,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
             for (int b = 0; b < E_BOXES; ++b) mbar_init(&e_full[4 * e + b], 1);
             mbar_init(&e_free[e], 1);
             mbar_init(&staged[e], 1);
-            if (csize > 1) mbar_init(&xbars[e], (uint32_t)kTileM * (csize - 1));
+            if (csize > 1) mbar_init(&xbars[e], 1);  // this CTA's expect-tx arrival
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -486,22 +508,14 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
 
     if (warp == 0) {
         if (lane == 0 && nk > 0) {
-            // ---- TMA producer: operand ring; output stores and epilogue operands ----
-            int it = 0, lt = 0, stored = 0, e_issued = -1;
+            // ---- TMA producer: operand ring ----
+            int it = 0;
             bool ok = true;
-            // send the staged output of tile t (its buffer is t & 1) and wait until it was read
-            auto store_tile = [&](int t) -> bool {
-                if (!mbar_wait(&staged[t & 1], (uint32_t)(t >> 1) & 1u, abort_flag)) return false;
-                const int nb = nbox[t & 1];
-                const int m0t = (first + t * stride) * kTileM;
-                for (int b = 0; b < nb && b < O_BOXES; ++b)
-                    tma_store_2d(&tmO, boxes + (t & 1) * BOX_BYTES + b * kTileABytes, n0 + 64 * b, m0t);
-                bulk_commit();
-                bulk_wait_read();
-                return true;
-            };
-            for (; lt < my_tiles && ok; ++lt) {
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
                 const int m0 = (first + lt * stride) * kTileM;
+                // the next tile's A rows go to L2 now, so that its ring refills at L2 latency
+                if (lt + 1 < my_tiles)
+                    for (int i = 0; i < nk; ++i) tma_prefetch_2d(&tmA, i * BK, m0 + stride * kTileM);
                 for (int i = 0; i < nk; ++i, ++it) {
                     const int s = it % STAGES;
                     if (it >= STAGES && !mbar_wait(&empty[s], ((uint32_t)(it / STAGES) & 1u) ^ 1u, abort_flag)) {
@@ -522,7 +536,31 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
                             tma_load_2d(sb + b * BOX_B * BK * 2, &tmB, &full[s], kx, n0 + b * BOX_B);
                     }
                 }
-                if (!ok) break;
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                // never leave the CTA with copies in flight
+                for (int j = max(0, it - STAGES); j < it; ++j)
+                    (void)mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u, nullptr);
+            }
+        }
+    } else if (warp == 2) {
+        if (lane == 0 && nk > 0) {
+            // ---- box buffers: staged outputs out, epilogue operands in ----
+            int stored = 0, e_issued = -1;
+            bool ok = true;
+            // send the staged output of tile t (its buffer is t & 1) and wait until it was read
+            auto store_tile = [&](int t) -> bool {
+                if (!mbar_wait(&staged[t & 1], (uint32_t)(t >> 1) & 1u, abort_flag)) return false;
+                const int nb = nbox[t & 1];
+                const int m0t = (first + t * stride) * kTileM;
+                for (int b = 0; b < nb && b < O_BOXES; ++b)
+                    tma_store_2d(&tmO, boxes + (t & 1) * BOX_BYTES + b * kTileABytes, n0 + 64 * b, m0t);
+                bulk_commit();
+                bulk_wait_read();
+                return true;
+            };
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
                 // buffer lt & 1 last held tile lt - 2
                 if (lt >= 2) {
                     if (!store_tile(lt - 2)) {
@@ -533,6 +571,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
                 }
                 const int e = lt & 1;
                 if (E_BOXES > 0) {
+                    const int m0 = (first + lt * stride) * kTileM;
                     for (int b = 0; b < E_BOXES; ++b) {
                         mbar_expect_tx(&e_full[4 * e + b], kTileABytes);
                         tma_load_2d(boxes + e * BOX_BYTES + b * kTileABytes, &tmE, &e_full[4 * e + b], n0 + 64 * b,
@@ -548,9 +587,6 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
             }
             if (!ok) {
                 *abort_flag = 1;
-                // never leave the CTA with copies in flight
-                for (int j = max(0, it - STAGES); j < it; ++j)
-                    (void)mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u, nullptr);
                 for (int t = max(0, e_issued - 1); t <= e_issued; ++t)
                     for (int b = 0; b < E_BOXES; ++b)
                         (void)mbar_wait(&e_full[4 * (t & 1) + b], (uint32_t)(t >> 1) & 1u, nullptr);
@@ -597,9 +633,9 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
             (void)mbar_wait(drain, 0, nullptr);
         }
     } else {
-        // ---- epilogue warps ----
+        // ---- epilogue warps (3 ..) ----
         const int quarter = warp & 3;
-        const int group = (warp - 2) >> 2;
+        const int group = (warp - 3) >> 2;
         const int row = quarter * 32 + lane;
         for (int lt = 0; lt < my_tiles; ++lt) {
             const int e = lt & 1, use = lt >> 1;
@@ -609,13 +645,13 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
             tc_fence_after();
             if (!ready) *abort_flag = 1;
             epi_sync(128 * G);
-            if (threadIdx.x == 64) *decision = *abort_flag ? 0 : 1;
+            if (threadIdx.x == 96) *decision = *abort_flag ? 0 : 1;
             epi_sync(128 * G);
             uint8_t* box = boxes + e * BOX_BYTES;
             EpiCtx ec{tmem_base + (uint32_t)(e * BN) + ((uint32_t)(quarter * 32) << 16),
                       row, tile * kTileM, n0, 0, group, scratch, E_BOXES > 0 ? box : nullptr, box,
                       &e_full[4 * e], abort_flag, (int)crank, (int)csize, &xbars[e],
-                      xbufs + e * (kXchgBytes / 4), (uint32_t)use & 1u, (uint32_t)use & 1u};
+                      xbufs + e * (kXchgBytes / 4), (uint32_t)use & 1u, (uint32_t)use & 1u, G, 96};
             int out_boxes = 0;
             if (*decision) {
                 out_boxes = Epi::run(ep, ec);
@@ -627,7 +663,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), 1)
             tc_fence_before();
             fence_proxy_async();
             epi_sync(128 * G);
-            if (threadIdx.x == 64) {
+            if (threadIdx.x == 96) {
                 mbar_arrive(&acc_empty[e]);
                 nbox[e] = *abort_flag ? 0 : out_boxes;
                 mbar_arrive(&staged[e]);
