@@ -226,6 +226,32 @@ LATENTAM_API latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const f
                                          double* loss_parts, float* dQ, float* dK, float* dV,
                                          latentam_stream stream);
 
+/* ---- the paper's cosine / temperature form of the decode (Sec. III-B, Eq. dict_recon) -------
+ *
+ * Queries Q (n x ds) are projected by W (ds x df); each projection u_p = q_p W is compared with
+ * every atom of the dictionary D (M x df) by cosine similarity after l2 normalisation (norms
+ * floored at 1e-12), divided by the temperature tau (> 0, no default: the paper defers to the
+ * work it follows), and Fhat = softmax_rows(cos / tau) D.  Computed exactly through the
+ * free-key decode with keys k_j = W D_j^T / |D_j|, queries q_p / |q_p W| and logit scale
+ * 1 / tau, so the n x df product Q W is never formed.  Shapes and precisions as for the
+ * free-key calls (ds plays the role of d, df of D, M <= 1024 / df <= 1024 in BF16).  Q, W, D,
+ * D0, F and the gradient buffers must be 16-byte aligned. */
+LATENTAM_API latentam_status latentam_decode_fwd_paper(latentam_ctx* ctx, const float* Q, int64_t n, int32_t ds,
+                                          const float* W, const float* D, int32_t M, int32_t df, float tau,
+                                          latentam_precision prec, float* F_hat, float* row_stats,
+                                          latentam_stream stream);
+
+/* lambda_f L_f of the cosine form against the target F (n x df) on the pixels with
+ * mask != 0, with the trust region on the atoms D against D0 (cfg->logit_scale is not used:
+ * tau is), and the gradients dQ (n x ds), dW (ds x df), dD (M x df), each nullable and
+ * overwritten.  loss_parts: device doubles (LATENTAM_LOSS_PARTS). */
+LATENTAM_API latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, const float* Q, int64_t n, int32_t ds,
+                                               const float* W, const float* D, const float* D0, int32_t M,
+                                               int32_t df, float tau, const void* F, latentam_dtype F_dtype,
+                                               const uint8_t* mask, const latentam_loss_cfg* cfg,
+                                               latentam_precision prec, double* loss_parts, float* dQ,
+                                               float* dW, float* dD, latentam_stream stream);
+
 /* Allocation-free form of latentam_decode_loss_bwd (FP32 only).  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device memory while
  * the step runs, e.g. a real-time mapping loop whose device memory is carved up once at

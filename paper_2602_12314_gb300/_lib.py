@@ -108,6 +108,9 @@ _SIGS = {
     "latentam_decode_fwd": ([P, P, I64, I32, P, P, I32, I32, F32, I32, P, P, P], I32),
     "latentam_decode_loss_bwd": ([P, P, I64, I32, P, P, P, I32, I32, P, I32, P, ctypes.POINTER(LossCfg), I32, P, P,
                                   P, P, P], I32),
+    "latentam_decode_fwd_paper": ([P, P, I64, I32, P, P, I32, I32, F32, I32, P, P, P], I32),
+    "latentam_decode_loss_bwd_paper": ([P, P, I64, I32, P, P, P, I32, I32, F32, P, I32, P, ctypes.POINTER(LossCfg), I32,
+                                        P, P, P, P, P], I32),
     "latentam_decode_loss_bwd_noalloc": ([P, P, I64, I32, P, P, P, I32, I32, P, I32, P, ctypes.POINTER(LossCfg), P, P,
                                           P, P, P], I32),
     "latentam_backward": ([P, I32, ctypes.POINTER(Projected), ctypes.POINTER(Camera), ctypes.POINTER(Bins), P, P,

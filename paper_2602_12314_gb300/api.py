@@ -279,6 +279,40 @@ def decode_loss_bwd(ctx: Context, Q, K, V, V0, F, mask=None, cfg: LossConfig | N
     return parts, dQ, dK, dV
 
 
+def decode_fwd_paper(ctx: Context, Q, W, D, tau: float, precision: int = FP32, want_stats: bool = True):
+    """The paper's cosine / temperature decode (Eq. dict_recon): Fhat = softmax(cos(Q W, D) / tau) D."""
+    Q, W, D = Q.contiguous(), W.contiguous(), D.contiguous()
+    n, ds = Q.shape
+    M, df = D.shape
+    Fh = torch.empty((n, df), dtype=torch.float32, device=Q.device)
+    stats = torch.empty((n, 2), dtype=torch.float32, device=Q.device) if want_stats else None
+    L.check(_lib().latentam_decode_fwd_paper(ctx.handle, _ptr(Q), n, ds, _ptr(W), _ptr(D), M, df, float(tau),
+                                             int(precision), _ptr(Fh), _ptr(stats), _stream()))
+    return Fh, stats
+
+
+def decode_loss_bwd_paper(ctx: Context, Q, W, D, D0, F, tau: float, mask=None, cfg: LossConfig | None = None,
+                          precision: int = FP32, need_dQ: bool = True):
+    """(loss_parts, dQ, dW, dD) of lambda_f L_f for the cosine / temperature decode, with the
+    trust region on the atoms D against D0."""
+    cfg = cfg or LossConfig()
+    Q, W, D, D0, F = (x.contiguous() for x in (Q, W, D, D0, F))
+    n, ds = Q.shape
+    M, df = D.shape
+    dev = Q.device
+    parts = torch.empty((L.LOSS_PARTS,), dtype=torch.float64, device=dev)
+    dQ = torch.empty((n, ds), dtype=torch.float32, device=dev) if need_dQ else None
+    dW = torch.empty((ds, df), dtype=torch.float32, device=dev)
+    dD = torch.empty((M, df), dtype=torch.float32, device=dev)
+    m = mask.contiguous().to(torch.uint8) if mask is not None else None
+    cs = cfg.struct()
+    L.check(_lib().latentam_decode_loss_bwd_paper(ctx.handle, _ptr(Q), n, ds, _ptr(W), _ptr(D), _ptr(D0), M, df,
+                                                  float(tau), _ptr(F), _target_dtype(F), _ptr(m), ctypes.byref(cs),
+                                                  int(precision), _ptr(parts), _ptr(dQ), _ptr(dW), _ptr(dD),
+                                                  _stream()))
+    return parts, dQ, dW, dD
+
+
 def decode_loss_bwd_noalloc(ctx: Context, Q, K, V, V0, F, mask=None, cfg: LossConfig | None = None,
                             out=None):
     """latentam_decode_loss_bwd_noalloc: FP32 decode + loss + backward whose scratch lives in

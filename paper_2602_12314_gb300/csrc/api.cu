@@ -1,5 +1,6 @@
 // C ABI of include/latentam.h: argument validation, the context and its workspace, and the
 // composition of the kernels into the calls of the latent-feature optimisation step.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -398,6 +399,101 @@ latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const float* Q, int6
     if (prec == LATENTAM_PREC_BF16) return decode_loss_bwd_bf16(ctx, a, (cudaStream_t)stream);
     set_error("unknown precision %d", prec);
     return LATENTAM_ERR_INVALID_ARG;
+}
+
+namespace {
+
+latentam_status paper_buffers(latentam_ctx* ctx, int64_t n, int ds, int M, int df, lat::PaperBuffers* b) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t nn = (size_t)std::max<int64_t>(n, 1), f = sizeof(float);
+    size_t off[9], o = 0;
+    off[0] = o, o += up(f * M * ds);    // K
+    off[1] = o, o += up(f * M);         // nrm
+    off[2] = o, o += up(f * ds * ds);   // G
+    off[3] = o, o += up(f * nn * ds);   // Q'
+    off[4] = o, o += up(f * nn);        // r
+    off[5] = o, o += up(f * nn * ds);   // dQ'
+    off[6] = o, o += up(f * M * ds);    // dK
+    off[7] = o, o += up(f * M * df);    // dV
+    off[8] = o, o += up(f * ds * ds);   // C
+    char* base = static_cast<char*>(lat::ws(ctx, lat::WS_PAPER, o));
+    if (!base) return LATENTAM_ERR_OUT_OF_MEMORY;
+    float** dst[9] = {&b->K, &b->nrm, &b->G, &b->Qp, &b->r, &b->dQp, &b->dK, &b->dV, &b->Cm};
+    for (int i = 0; i < 9; ++i) *dst[i] = reinterpret_cast<float*>(base + off[i]);
+    return LATENTAM_OK;
+}
+
+latentam_status check_paper(int64_t n, int ds, const float* Q, const float* W, const float* D, int M, int df,
+                            float tau) {
+    LAT_TRY(check_d(ds));
+    LAT_TRY(check_dict(M, df));
+    REQUIRE(n >= 0 && (n == 0 || Q) && W && D, "null argument");
+    REQUIRE(aligned16(Q) && aligned16(W) && aligned16(D), "Q, W, D must be 16-byte aligned");
+    REQUIRE(tau > 0.f && isfinite(tau), "temperature tau=%g must be positive and finite", (double)tau);
+    return LATENTAM_OK;
+}
+
+}  // namespace
+
+latentam_status latentam_decode_fwd_paper(latentam_ctx* ctx, const float* Q, int64_t n, int32_t ds, const float* W,
+                                          const float* D, int32_t M, int32_t df, float tau, latentam_precision prec,
+                                          float* F_hat, float* row_stats, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_paper(n, ds, Q, W, D, M, df, tau));
+    REQUIRE(aligned16(F_hat), "F_hat must be 16-byte aligned");
+    REQUIRE(prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_BF16, "unknown precision %d", prec);
+    lat::PaperBuffers b;
+    LAT_TRY(paper_buffers(ctx, n, ds, M, df, &b));
+    const lat::PaperArgs a{Q, n, ds, W, D, M, df};
+    cudaStream_t st = (cudaStream_t)stream;
+    StageTimer tm(ctx, LATENTAM_STAGE_DECODE, st);
+    LAT_TRY(lat::paper_prepare(ctx, a, b, st));
+    if (prec == LATENTAM_PREC_FP32) return decode_fwd_f32(ctx, b.Qp, n, ds, b.K, D, M, df, 1.0f / tau, F_hat, row_stats, st);
+    return decode_fwd_bf16(ctx, b.Qp, n, ds, b.K, D, M, df, 1.0f / tau, F_hat, row_stats, st);
+}
+
+latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, const float* Q, int64_t n, int32_t ds,
+                                               const float* W, const float* D, const float* D0, int32_t M,
+                                               int32_t df, float tau, const void* F, latentam_dtype F_dtype,
+                                               const uint8_t* mask, const latentam_loss_cfg* cfg,
+                                               latentam_precision prec, double* loss_parts, float* dQ, float* dW,
+                                               float* dD, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_paper(n, ds, Q, W, D, M, df, tau));
+    REQUIRE(cfg && loss_parts && D0 && (n == 0 || F), "null argument");
+    REQUIRE(F_dtype == LATENTAM_DTYPE_F32 || F_dtype == LATENTAM_DTYPE_BF16, "unknown target dtype %d", F_dtype);
+    REQUIRE(aligned16(D0) && aligned16(F) && aligned16(dQ) && aligned16(dW) && aligned16(dD),
+            "D0, F, dQ, dW, dD must be 16-byte aligned");
+    REQUIRE(prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_BF16, "unknown precision %d", prec);
+    lat::PaperBuffers b;
+    LAT_TRY(paper_buffers(ctx, n, ds, M, df, &b));
+    const lat::PaperArgs pa{Q, n, ds, W, D, M, df};
+    cudaStream_t st = (cudaStream_t)stream;
+    StageTimer tm(ctx, LATENTAM_STAGE_DECODE, st);
+    LAT_TRY(lat::paper_prepare(ctx, pa, b, st));
+    DecodeArgs a;
+    a.Q = b.Qp;
+    a.n = n;
+    a.d = ds;
+    a.K = b.K;
+    a.V = D;
+    a.V0 = D0;
+    a.M = M;
+    a.D = df;
+    a.c = 1.0f / tau;
+    a.F = F;
+    a.F_dtype = F_dtype;
+    a.mask = mask;
+    a.cfg = *cfg;
+    a.loss_parts = loss_parts;
+    a.dQ = (dQ || dW) ? b.dQp : nullptr;  // dW needs dQ' for the query-norm term
+    a.dK = b.dK;
+    a.dV = b.dV;
+    if (prec == LATENTAM_PREC_FP32)
+        LAT_TRY(decode_loss_bwd_f32(ctx, a, st));
+    else
+        LAT_TRY(decode_loss_bwd_bf16(ctx, a, st));
+    return lat::paper_chain(ctx, pa, b, dQ, dW, dD, st);
 }
 
 latentam_status latentam_decode_loss_bwd_noalloc(latentam_ctx* ctx, const float* Q, int64_t n, int32_t d,

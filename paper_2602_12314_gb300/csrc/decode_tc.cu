@@ -102,18 +102,31 @@ __global__ void tc_trust_region(const float* __restrict__ V, const float* __rest
     }
 }
 
-// out[j][k] = scale * sum_z part[z][j][k] (+ coef[j] (V - V0)[j][k]) for k < ncols (of ld columns)
-__global__ void tc_reduce_parts(const float* __restrict__ part, int splits, int rows, int ld, int ncols, float scale,
-                                const float* __restrict__ coef, const float* __restrict__ V,
-                                const float* __restrict__ V0, float* __restrict__ out) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)rows * ncols) return;
-    const int j = (int)(e / ncols), k = (int)(e % ncols);
+// out[j][k] = scale * sum_z part[z][j][k] (+ coef[j] (V - V0)[j][k]) for k < ncols (of ld columns).
+// A block owns 32 consecutive outputs (one per lane); its 8 warps take every 8th split, so the
+// reads of each split are contiguous and many splits are summed in parallel.
+__global__ void __launch_bounds__(256) tc_reduce_parts(const float* __restrict__ part, int splits, int rows, int ld,
+                                                       int ncols, float scale, const float* __restrict__ coef,
+                                                       const float* __restrict__ V, const float* __restrict__ V0,
+                                                       float* __restrict__ out) {
+    __shared__ float acc[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    const bool live = e < (int64_t)rows * ncols;
+    const int j = live ? (int)(e / ncols) : 0, k = live ? (int)(e % ncols) : 0;
     float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += part[((int64_t)z * rows + j) * ld + k];
-    s *= scale;
-    if (coef) s += coef[j] * (V[e] - V0[e]);
-    out[e] = s;
+    if (live)
+        for (int z = w; z < splits; z += 8) s += part[((int64_t)z * rows + j) * ld + k];
+    acc[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && live) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += acc[q][lane];
+        t *= scale;
+        if (coef) t += coef[j] * (V[e] - V0[e]);
+        out[e] = t;
+    }
 }
 
 __global__ void tc_finalize(const double* __restrict__ acc, const int* __restrict__ err, int D, latentam_loss_cfg cfg,
@@ -802,8 +815,8 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
             PartParams pp{M, D, D, b.part};
             LAT_TRY(launch_gemm<PartEpi<256>>(mA, mdF, dim3(cdiv(M, kTileM), cdiv(D, 256), zV), gV, pp, b.err, st));
         }
-        tc_reduce_parts<<<cdiv((int64_t)M * D, 256), 256, 0, st>>>(b.part, n > 0 ? zV : 0, M, D, D, 1.0f, b.coef,
-                                                                   a.V, a.V0, a.dV);
+        tc_reduce_parts<<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, n > 0 ? zV : 0, M, D, D, 1.0f, b.coef, a.V,
+                                                                  a.V0, a.dV);
         LAT_CHECK_LAUNCH("tc_reduce_parts");
     }
     // G6: dK = c dS^T Q
@@ -815,8 +828,8 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
             PartParams pp{M, BNq, BNq, b.part};
             LAT_TRY(launch_gemm<PartEpi<BNq>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zK), gK, pp, b.err, st));
         }
-        tc_reduce_parts<<<cdiv((int64_t)M * d, 256), 256, 0, st>>>(b.part, n > 0 ? zK : 0, M, BNq, d, a.c, nullptr,
-                                                                   nullptr, nullptr, a.dK);
+        tc_reduce_parts<<<cdiv((int64_t)M * d, 32), 256, 0, st>>>(b.part, n > 0 ? zK : 0, M, BNq, d, a.c, nullptr,
+                                                                  nullptr, nullptr, a.dK);
         LAT_CHECK_LAUNCH("tc_reduce_parts");
     }
     tc_finalize<<<1, 1, 0, st>>>(b.acc, b.err, D, a.cfg, a.loss_parts);

@@ -62,6 +62,7 @@ enum Slot : int {
     WS_STEP_PAIRS,
     WS_STEP_IMG,
     WS_STEP_GRAD,
+    WS_PAPER,      // keys, norms, Gram matrix, scaled queries and gradients of the W/D form
     WS_NUM_SLOTS
 };
 
@@ -189,6 +190,24 @@ size_t decode_noalloc_scratch_bytes();
 latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K,
                                 const float* V, int M, int D, float c, float* F_hat, float* row_stats,
                                 cudaStream_t st);
+
+// The paper's W / D / tau form of the decode, computed through the free-key decode.
+struct PaperArgs {
+    const float* Q;  // n x ds
+    int64_t n;
+    int ds;
+    const float* W;  // ds x df
+    const float* D;  // M x df
+    int M, df;
+};
+struct PaperBuffers {
+    float *K, *nrm, *G, *Qp, *r, *dQp, *dK, *dV, *Cm;
+};
+// keys K, norms, G = W W^T, scaled queries Q' and 1/|q W|
+latentam_status paper_prepare(latentam_ctx* ctx, const PaperArgs& a, const PaperBuffers& b, cudaStream_t st);
+// dQ, dW, dD (each nullable) from the free-key gradients dQ' (b.dQp), dK (b.dK), dV (b.dV)
+latentam_status paper_chain(latentam_ctx* ctx, const PaperArgs& a, const PaperBuffers& b, float* dQ, float* dW,
+                            float* dD, cudaStream_t st);
 
 struct AdamTensor {
     float* p;
