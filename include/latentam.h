@@ -171,6 +171,16 @@ LATENTAM_API int32_t latentam_num_tiles(const latentam_camera* cam);
 LATENTAM_API latentam_status latentam_profile_enable(latentam_ctx* ctx, int32_t enable);
 LATENTAM_API latentam_status latentam_profile_read(latentam_ctx* ctx, double* ms, int64_t* counts, int32_t reset);
 
+/* CUDA graphs of the step (on by default).  latentam_step captures one Stage-I iteration
+ * (learn_f != 0: render, decode + loss + backward, render backward, Adam) into a CUDA graph
+ * the second time it sees a configuration (the same buffers, shapes, pair count, scalars and
+ * workspace), instantiates it on a stream of the context, and from then on launches each
+ * iteration as one graph on the caller's stream; the Adam step then lives in a device counter
+ * (set from adam->step before the replays; adam->step is advanced on the host as before).  Up
+ * to four configurations are kept.  With profiling enabled, or learn_f == 0, the iterations run
+ * as plain launches.  Disabling drops the instantiated graphs (synchronises the device). */
+LATENTAM_API latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t enable);
+
 /* ---- splatting (Sec. III-A, Eq. alpha_blending; Sec. III-B, Eq. render_query) ------- */
 
 /* Project every Gaussian: EWA screen-space covariance, conic, opacity, depth key and

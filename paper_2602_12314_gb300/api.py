@@ -111,6 +111,10 @@ class Context:
             L.check(_lib().latentam_ctx_destroy(self._h))
             self._h = None
 
+    def graphs(self, enable: bool = True):
+        """Capture and replay the step's iterations as CUDA graphs (on by default)."""
+        L.check(_lib().latentam_graphs_enable(self.handle, int(bool(enable))))
+
     def profile(self, enable: bool = True):
         """Turn the per-stage CUDA-event timers on or off."""
         L.check(_lib().latentam_profile_enable(self.handle, int(bool(enable))))

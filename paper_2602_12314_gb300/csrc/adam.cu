@@ -17,18 +17,27 @@ struct AdamBatch {
     int block_start[kMaxTensors + 1];  // first block of each tensor
     int count;
     float beta1, beta2, eps, inv_bc1, inv_bc2;  // inverse bias corrections 1 / (1 - beta^step)
+    const int* step_dev;                        // when set: the step is read here (graph replays)
 };
 
-__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, const AdamBatch& b) {
+__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, const AdamBatch& b,
+                                         float inv_bc1, float inv_bc2) {
     m = b.beta1 * m + (1.0f - b.beta1) * g;
     v = b.beta2 * v + (1.0f - b.beta2) * g * g;
-    const float mh = m * b.inv_bc1, vh = v * b.inv_bc2;
+    const float mh = m * inv_bc1, vh = v * inv_bc2;
     p -= lr * mh / (sqrtf(vh) + b.eps);
 }
 
 // Each tensor owns a contiguous range of blocks (block_start); a block streams its share of
 // the tensor as float4 when the tensor's arrays are 16-byte aligned, element-wise otherwise.
 __global__ void __launch_bounds__(256) adam_kernel(AdamBatch b) {
+    float inv_bc1 = b.inv_bc1, inv_bc2 = b.inv_bc2;
+    if (b.step_dev) {
+        // 1 - beta^t = -expm1(t ln beta), free of the cancellation of 1 - powf(beta, t)
+        const float t = (float)*b.step_dev;
+        inv_bc1 = -1.0f / expm1f(t * logf(b.beta1));
+        inv_bc2 = -1.0f / expm1f(t * logf(b.beta2));
+    }
     int k = 0;
     while (k + 1 < b.count && (int)blockIdx.x >= b.block_start[k + 1]) ++k;
     const AdamTensor& T = b.t[k];
@@ -47,10 +56,10 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamBatch b) {
         for (int64_t i = tid; i < n4; i += stride) {
             float4 p = p4[i], m = m4[i], v = v4[i];
             const float4 g = g4[i];
-            adam_one(p.x, g.x, m.x, v.x, T.lr, b);
-            adam_one(p.y, g.y, m.y, v.y, T.lr, b);
-            adam_one(p.z, g.z, m.z, v.z, T.lr, b);
-            adam_one(p.w, g.w, m.w, v.w, T.lr, b);
+            adam_one(p.x, g.x, m.x, v.x, T.lr, b, inv_bc1, inv_bc2);
+            adam_one(p.y, g.y, m.y, v.y, T.lr, b, inv_bc1, inv_bc2);
+            adam_one(p.z, g.z, m.z, v.z, T.lr, b, inv_bc1, inv_bc2);
+            adam_one(p.w, g.w, m.w, v.w, T.lr, b, inv_bc1, inv_bc2);
             p4[i] = p;
             m4[i] = m;
             v4[i] = v;
@@ -59,23 +68,39 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamBatch b) {
     }
     for (int64_t i = done + tid; i < T.n; i += stride) {
         float p = T.p[i], m = T.m[i], v = T.v[i];
-        adam_one(p, T.g[i], m, v, T.lr, b);
+        adam_one(p, T.g[i], m, v, T.lr, b, inv_bc1, inv_bc2);
         T.p[i] = p;
         T.m[i] = m;
         T.v[i] = v;
     }
 }
 
+// The Adam step counter of graph replays: advanced by one on the device before each update.
+__global__ void step_advance(int* step) { *step += 1; }
+__global__ void step_set(int* step, int v) { *step = v; }
+
 }  // namespace
 
+latentam_status launch_step_set(int* step_dev, int value, cudaStream_t st) {
+    step_set<<<1, 1, 0, st>>>(step_dev, value);
+    LAT_CHECK_LAUNCH("step_set");
+    return LATENTAM_OK;
+}
+
+latentam_status launch_step_advance(int* step_dev, cudaStream_t st) {
+    step_advance<<<1, 1, 0, st>>>(step_dev);
+    LAT_CHECK_LAUNCH("step_advance");
+    return LATENTAM_OK;
+}
+
 latentam_status launch_adam(latentam_ctx* ctx, const AdamTensor* t, int count, float beta1, float beta2, float eps,
-                            int step, cudaStream_t st) {
+                            int step, cudaStream_t st, const int* step_dev) {
     if (count <= 0) return LATENTAM_OK;
     if (count > kMaxTensors) {
         set_error("at most %d tensors per Adam launch", kMaxTensors);
         return LATENTAM_ERR_INVALID_ARG;
     }
-    if (step < 1) {
+    if (!step_dev && step < 1) {
         set_error("Adam step must be >= 1 (got %d)", step);
         return LATENTAM_ERR_INVALID_ARG;
     }
@@ -86,6 +111,7 @@ latentam_status launch_adam(latentam_ctx* ctx, const AdamTensor* t, int count, f
     b.eps = eps;
     b.inv_bc1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
     b.inv_bc2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
+    b.step_dev = step_dev;
     // blocks in proportion to the tensor sizes (at least one each), about 4 waves in total
     int64_t total = 0;
     for (int k = 0; k < count; ++k) {

@@ -17,6 +17,52 @@ static std::atomic<int64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Instantiated graphs of the step's iteration, keyed by every pointer, shape and scalar the
+// iteration bakes into its launches (and the workspace generation).
+struct GraphKey {
+    uint64_t v[48];
+    int n = 0;
+    void add(uint64_t x) {
+        if (n < 48) v[n++] = x;
+    }
+    void addp(const void* p) { add(reinterpret_cast<uint64_t>(p)); }
+    void addf(float f) {
+        uint32_t u;
+        memcpy(&u, &f, 4);
+        add(u);
+    }
+    bool operator==(const GraphKey& o) const { return n == o.n && memcmp(v, o.v, sizeof(uint64_t) * n) == 0; }
+};
+struct GraphCache {
+    static constexpr int kSlots = 4;
+    GraphKey key[kSlots];
+    cudaGraphExec_t exec[kSlots] = {};
+    int64_t launches[kSlots] = {};
+    int used = 0, next = 0;
+    GraphKey warm[kSlots];  // configurations run once eagerly (their workspaces are sized)
+    int warm_used = 0, warm_next = 0;
+    GraphKey failed[kSlots];  // configurations whose capture failed: always eager
+    int failed_used = 0, failed_next = 0;
+    static int find(const GraphKey* arr, int used, const GraphKey& k) {
+        for (int i = 0; i < used; ++i)
+            if (arr[i] == k) return i;
+        return -1;
+    }
+    static void put(GraphKey* arr, int& used, int& next, const GraphKey& k) {
+        arr[next] = k;
+        next = (next + 1) % kSlots;
+        if (used < kSlots) ++used;
+    }
+    void clear() {
+        for (int i = 0; i < kSlots; ++i)
+            if (exec[i]) cudaGraphExecDestroy(exec[i]);
+        *this = GraphCache();
+    }
+};
+
+int64_t launch_count_now() { return g_launches.load(std::memory_order_relaxed); }
+void launch_count_add(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
 void set_error(const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -32,6 +78,7 @@ latentam_status cuda_error(cudaError_t e, const char* what) {
 void* ws(latentam_ctx* ctx, Slot s, size_t bytes) {
     if (bytes == 0) bytes = 256;
     if (ctx->slot_bytes[s] >= bytes) return ctx->slot_ptr[s];
+    ++ctx->ws_generation;  // captured graphs that name the old buffer are stale now
     size_t nb = std::max(bytes, ctx->slot_bytes[s] + ctx->slot_bytes[s] / 4);
     nb = (nb + 4095) & ~(size_t)4095;
     if (ctx->slot_ptr[s]) {
@@ -60,6 +107,7 @@ void* ws(latentam_ctx* ctx, Slot s, size_t bytes) {
 void* frame_ws(latentam_ctx* ctx, int idx, size_t bytes) {
     if (bytes == 0) bytes = 256;
     if (ctx->frame_bytes[idx] >= bytes) return ctx->frame_ptr[idx];
+    ++ctx->ws_generation;
     size_t nb = std::max(bytes, ctx->frame_bytes[idx] + ctx->frame_bytes[idx] / 4);
     nb = (nb + 4095) & ~(size_t)4095;
     if (ctx->frame_ptr[idx]) {
@@ -251,6 +299,17 @@ latentam_status latentam_ctx_create(int32_t device, latentam_ctx** out) {
     c->num_sms = prop.multiProcessorCount;
     c->cc_major = prop.major;
     c->cc_minor = prop.minor;
+    c->use_graphs = 1;
+    c->graphs = new (std::nothrow) GraphCache();
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->step_dev, sizeof(int));
+    if (e != cudaSuccess || !c->graphs) {
+        latentam_ctx_destroy(c);
+        if (e != cudaSuccess) return cuda_error(e, "context stream / counter");
+        set_error("host allocation failed");
+        return LATENTAM_ERR_OUT_OF_MEMORY;
+    }
     *out = c;
     return LATENTAM_OK;
 }
@@ -266,8 +325,25 @@ latentam_status latentam_ctx_destroy(latentam_ctx* ctx) {
         for (int i = 0; i < ctx->prof[s].created; ++i) cudaEventDestroy(ctx->prof[s].ev[i]);
     for (int i = 0; i < 2 * LATENTAM_MAX_BATCH; ++i)
         if (ctx->frame_ptr[i]) cudaFree(ctx->frame_ptr[i]);
+    if (ctx->graphs) {
+        ctx->graphs->clear();
+        delete ctx->graphs;
+    }
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->step_dev) cudaFree(ctx->step_dev);
     delete ctx;
     if (e != cudaSuccess) return cuda_error(e, "synchronise before destroy");
+    return LATENTAM_OK;
+}
+
+latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t enable) {
+    LAT_TRY(enter(ctx));
+    ctx->use_graphs = enable != 0;
+    if (!enable) {
+        cudaError_t e = cudaDeviceSynchronize();
+        ctx->graphs->clear();
+        if (e != cudaSuccess) return cuda_error(e, "synchronise before dropping graphs");
+    }
     return LATENTAM_OK;
 }
 
@@ -633,28 +709,93 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
     float* dV = reinterpret_cast<float*>(gb + g_dv);
     double* lp = reinterpret_cast<double*>(gb + g_lp);
     const CamParams cp = cam_params(cam);
-    for (int it = 0; it < iters; ++it) {
-        if (it == 0 || learn_f) {
-            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, st);
-            LAT_TRY(launch_render_fwd(cp, proj, bins, params->f, d, Q, T, nc, st));
+    // one iteration on stream `s`: render, decode + loss + backward, render backward, Adam
+    // (with the step read from step_dev when it is set: graph replays)
+    auto iteration = [&](cudaStream_t s, bool render, const int* step_dev) -> latentam_status {
+        if (render) {
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, s);
+            LAT_TRY(launch_render_fwd(cp, proj, bins, params->f, d, Q, T, nc, s));
         }
         LAT_TRY(latentam_decode_loss_bwd(ctx, Q, npix, d, params->K, params->V, params->V0, M, D, frame->F,
                                          frame->F_dtype, frame->mask, cfg, prec, lp, learn_f ? dQ : nullptr, dK, dV,
-                                         stream));
+                                         s));
         if (learn_f && N > 0) {
-            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, st);
-            LAT_TRY(launch_render_bwd(cp, proj, bins, nc, dQ, d, df, N, st));
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, s);
+            LAT_TRY(launch_render_bwd(cp, proj, bins, nc, dQ, d, df, N, s));
         }
         AdamTensor t[3];
         int cnt = 0;
         if (learn_f) t[cnt++] = AdamTensor{params->f, df, params->m_f, params->v_f, (int64_t)N * d, adam->lr_f};
         t[cnt++] = AdamTensor{params->K, dK, params->m_K, params->v_K, (int64_t)M * d, adam->lr_dict};
         t[cnt++] = AdamTensor{params->V, dV, params->m_V, params->v_V, (int64_t)M * D, adam->lr_dict};
-        {
-            StageTimer tm(ctx, LATENTAM_STAGE_ADAM, st);
-            LAT_TRY(launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, st));
+        StageTimer tm(ctx, LATENTAM_STAGE_ADAM, s);
+        if (step_dev) LAT_TRY(launch_step_advance(const_cast<int*>(step_dev), s));
+        return launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, s, step_dev);
+    };
+    // Stage I iterations (all of them render) replay one captured graph; the configuration is
+    // captured on its second use, once its workspaces have their sizes.
+    int gslot = -1;
+    if (ctx->use_graphs && learn_f && !ctx->profiling && iters > 0) {
+        GraphKey key;
+        const void* ptrs[] = {params->f, params->K, params->V, params->V0, params->m_f, params->v_f, params->m_K,
+                              params->v_K, params->m_V, params->v_V, frame->F, frame->mask, Q, T, nc, dQ, df, dK,
+                              dV, lp, proj.xy, proj.conic_opacity, bins.pair_ids, bins.tile_ranges, st};
+        for (const void* p : ptrs) key.addp(p);
+        const int64_t ints[] = {N, d, M, D, cam.width, cam.height, (int64_t)bins.num_pairs, (int64_t)frame->F_dtype,
+                                (int64_t)prec, (int64_t)ctx->ws_generation};
+        for (int64_t x : ints) key.add((uint64_t)x);
+        for (float f : {cfg->lambda_f, cfg->lambda_cos, cfg->lambda_2, cfg->lambda_D, cfg->delta, cfg->logit_scale,
+                        adam->lr_f, adam->lr_dict, adam->beta1, adam->beta2, adam->eps})
+            key.addf(f);
+        GraphCache& gc = *ctx->graphs;
+        gslot = GraphCache::find(gc.key, gc.used, key);
+        const bool failed = GraphCache::find(gc.failed, gc.failed_used, key) >= 0;
+        if (gslot < 0 && !failed && GraphCache::find(gc.warm, gc.warm_used, key) >= 0) {
+            // capture one iteration on the context's own stream
+            cudaGraph_t graph = nullptr;
+            const int64_t l0 = launch_count_now();
+            cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+            latentam_status cs = e == cudaSuccess ? iteration(ctx->cap_stream, true, ctx->step_dev) : LATENTAM_ERR_CUDA;
+            cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->cap_stream, &graph) : e;
+            const int64_t captured = launch_count_now() - l0;
+            launch_count_add(-captured);  // nothing ran
+            cudaGraphExec_t exec = nullptr;
+            if (cs == LATENTAM_OK && e2 == cudaSuccess && graph &&
+                cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+                const int slot = gc.next;
+                if (gc.exec[slot]) {
+                    cudaStreamSynchronize(st);  // a replay of the graph being dropped may be queued
+                    cudaGraphExecDestroy(gc.exec[slot]);
+                }
+                gc.exec[slot] = exec;
+                gc.key[slot] = key;
+                gc.launches[slot] = captured;
+                gc.next = (gc.next + 1) % GraphCache::kSlots;
+                if (gc.used < GraphCache::kSlots) ++gc.used;
+                gslot = slot;
+            } else {
+                (void)cudaGetLastError();
+                GraphCache::put(gc.failed, gc.failed_used, gc.failed_next, key);
+            }
+            if (graph) cudaGraphDestroy(graph);
+        } else if (gslot < 0 && !failed) {
+            GraphCache::put(gc.warm, gc.warm_used, gc.warm_next, key);
         }
-        adam->step += 1;
+    }
+    if (gslot >= 0) {
+        GraphCache& gc = *ctx->graphs;
+        LAT_TRY(launch_step_set(ctx->step_dev, adam->step - 1, st));
+        for (int it = 0; it < iters; ++it) {
+            cudaError_t e = cudaGraphLaunch(gc.exec[gslot], st);
+            if (e != cudaSuccess) return cuda_error(e, "step graph launch");
+            launch_count_add(gc.launches[gslot]);
+        }
+        adam->step += iters;
+    } else {
+        for (int it = 0; it < iters; ++it) {
+            LAT_TRY(iteration(st, it == 0 || learn_f, nullptr));
+            adam->step += 1;
+        }
     }
     if (loss_host) {
         cudaError_t e = cudaMemcpyAsync(loss_host, lp, sizeof(double) * LATENTAM_LOSS_PARTS, cudaMemcpyDeviceToHost, st);

@@ -70,6 +70,7 @@ enum Slot : int {
 
 namespace lat {
 constexpr int kProfPairs = 256;  // event pairs per stage before folding
+struct GraphCache;  // api.cu
 struct StageProfile {
     cudaEvent_t ev[2 * kProfPairs];
     int created;
@@ -90,6 +91,12 @@ struct latentam_ctx {
     // per-frame buffers of the batched step: [2k] projection + tile ranges, [2k+1] pairs
     void* frame_ptr[2 * LATENTAM_MAX_BATCH];
     size_t frame_bytes[2 * LATENTAM_MAX_BATCH];
+    // CUDA graphs of the step's iteration (see latentam_graphs_enable)
+    int use_graphs;
+    uint64_t ws_generation;  // bumped whenever a workspace buffer moves
+    cudaStream_t cap_stream;
+    int* step_dev;
+    lat::GraphCache* graphs;
 };
 
 namespace lat {
@@ -217,7 +224,10 @@ struct AdamTensor {
     int64_t n;
     float lr;
 };
+// step_dev (nullable): read the step from device memory instead of `step` (graph replays).
 latentam_status launch_adam(latentam_ctx* ctx, const AdamTensor* t, int count, float beta1, float beta2,
-                            float eps, int step, cudaStream_t st);
+                            float eps, int step, cudaStream_t st, const int* step_dev = nullptr);
+latentam_status launch_step_set(int* step_dev, int value, cudaStream_t st);
+latentam_status launch_step_advance(int* step_dev, cudaStream_t st);
 
 }  // namespace lat
