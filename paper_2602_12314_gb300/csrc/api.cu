@@ -20,10 +20,15 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // Instantiated graphs of the step's iteration, keyed by every pointer, shape and scalar the
 // iteration bakes into its launches (and the workspace generation).
 struct GraphKey {
-    uint64_t v[48];
+    static constexpr int kMax = 320;
+    uint64_t v[kMax];
     int n = 0;
+    bool overflow = false;  // a key that did not fit never matches (no graph)
     void add(uint64_t x) {
-        if (n < 48) v[n++] = x;
+        if (n < kMax)
+            v[n++] = x;
+        else
+            overflow = true;
     }
     void addp(const void* p) { add(reinterpret_cast<uint64_t>(p)); }
     void addf(float f) {
@@ -31,7 +36,16 @@ struct GraphKey {
         memcpy(&u, &f, 4);
         add(u);
     }
-    bool operator==(const GraphKey& o) const { return n == o.n && memcmp(v, o.v, sizeof(uint64_t) * n) == 0; }
+    void add_camera(const latentam_camera& c) {
+        for (int i = 0; i < 9; ++i) addf(c.R[i]);
+        for (int i = 0; i < 3; ++i) addf(c.t[i]);
+        for (float f : {c.fx, c.fy, c.cx, c.cy, c.z_near}) addf(f);
+        add((uint64_t)c.width);
+        add((uint64_t)c.height);
+    }
+    bool operator==(const GraphKey& o) const {
+        return !overflow && !o.overflow && n == o.n && memcmp(v, o.v, sizeof(uint64_t) * n) == 0;
+    }
 };
 struct GraphCache {
     static constexpr int kSlots = 4;
@@ -250,6 +264,70 @@ latentam_status check_bins(const latentam_bins* b, bool need_pairs) {
 
 float logit_scale(const latentam_loss_cfg* cfg, int d) {
     return (cfg && cfg->logit_scale > 0.f) ? cfg->logit_scale : 1.0f / sqrtf((float)d);
+}
+
+}  // namespace
+
+namespace {
+
+// Runs `iters` iterations of `iteration(stream, render, step_dev)`.  With `graphable`, a
+// configuration seen once before (its workspaces sized) is captured as one iteration on the
+// context's stream and replayed; the Adam step then comes from ctx->step_dev.
+template <class Iteration>
+latentam_status run_iterations(latentam_ctx* ctx, bool graphable, const GraphKey& key, int iters, bool learn_f,
+                               latentam_adam_cfg* adam, cudaStream_t st, Iteration&& iteration) {
+    int gslot = -1;
+    if (graphable && !key.overflow) {
+        GraphCache& gc = *ctx->graphs;
+        gslot = GraphCache::find(gc.key, gc.used, key);
+        const bool failed = GraphCache::find(gc.failed, gc.failed_used, key) >= 0;
+        if (gslot < 0 && !failed && GraphCache::find(gc.warm, gc.warm_used, key) >= 0) {
+            cudaGraph_t graph = nullptr;
+            const int64_t l0 = launch_count_now();
+            cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+            latentam_status cs = e == cudaSuccess ? iteration(ctx->cap_stream, true, ctx->step_dev) : LATENTAM_ERR_CUDA;
+            cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->cap_stream, &graph) : e;
+            const int64_t captured = launch_count_now() - l0;
+            launch_count_add(-captured);  // nothing ran yet
+            cudaGraphExec_t exec = nullptr;
+            if (cs == LATENTAM_OK && e2 == cudaSuccess && graph &&
+                cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+                const int slot = gc.next;
+                if (gc.exec[slot]) {
+                    cudaStreamSynchronize(st);  // a replay of the graph being dropped may be queued
+                    cudaGraphExecDestroy(gc.exec[slot]);
+                }
+                gc.exec[slot] = exec;
+                gc.key[slot] = key;
+                gc.launches[slot] = captured;
+                gc.next = (gc.next + 1) % GraphCache::kSlots;
+                if (gc.used < GraphCache::kSlots) ++gc.used;
+                gslot = slot;
+            } else {
+                (void)cudaGetLastError();
+                GraphCache::put(gc.failed, gc.failed_used, gc.failed_next, key);
+            }
+            if (graph) cudaGraphDestroy(graph);
+        } else if (gslot < 0 && !failed) {
+            GraphCache::put(gc.warm, gc.warm_used, gc.warm_next, key);
+        }
+    }
+    if (gslot >= 0) {
+        GraphCache& gc = *ctx->graphs;
+        LAT_TRY(launch_step_set(ctx->step_dev, adam->step - 1, st));
+        for (int it = 0; it < iters; ++it) {
+            cudaError_t e = cudaGraphLaunch(gc.exec[gslot], st);
+            if (e != cudaSuccess) return cuda_error(e, "step graph launch");
+            launch_count_add(gc.launches[gslot]);
+        }
+        adam->step += iters;
+        return LATENTAM_OK;
+    }
+    for (int it = 0; it < iters; ++it) {
+        LAT_TRY(iteration(st, it == 0 || learn_f, nullptr));
+        adam->step += 1;
+    }
+    return LATENTAM_OK;
 }
 
 }  // namespace
@@ -732,71 +810,23 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
         if (step_dev) LAT_TRY(launch_step_advance(const_cast<int*>(step_dev), s));
         return launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, s, step_dev);
     };
-    // Stage I iterations (all of them render) replay one captured graph; the configuration is
-    // captured on its second use, once its workspaces have their sizes.
-    int gslot = -1;
-    if (ctx->use_graphs && learn_f && !ctx->profiling && iters > 0) {
-        GraphKey key;
+    // Stage I iterations (all of them render) replay one captured graph
+    GraphKey key;
+    const bool graphable = ctx->use_graphs && learn_f && !ctx->profiling && iters > 0;
+    if (graphable) {
         const void* ptrs[] = {params->f, params->K, params->V, params->V0, params->m_f, params->v_f, params->m_K,
                               params->v_K, params->m_V, params->v_V, frame->F, frame->mask, Q, T, nc, dQ, df, dK,
                               dV, lp, proj.xy, proj.conic_opacity, bins.pair_ids, bins.tile_ranges, st};
         for (const void* p : ptrs) key.addp(p);
-        const int64_t ints[] = {N, d, M, D, cam.width, cam.height, (int64_t)bins.num_pairs, (int64_t)frame->F_dtype,
-                                (int64_t)prec, (int64_t)ctx->ws_generation};
+        const int64_t ints[] = {N, d, M, D, (int64_t)bins.num_pairs, (int64_t)frame->F_dtype, (int64_t)prec,
+                                (int64_t)ctx->ws_generation};
         for (int64_t x : ints) key.add((uint64_t)x);
+        key.add_camera(cam);
         for (float f : {cfg->lambda_f, cfg->lambda_cos, cfg->lambda_2, cfg->lambda_D, cfg->delta, cfg->logit_scale,
                         adam->lr_f, adam->lr_dict, adam->beta1, adam->beta2, adam->eps})
             key.addf(f);
-        GraphCache& gc = *ctx->graphs;
-        gslot = GraphCache::find(gc.key, gc.used, key);
-        const bool failed = GraphCache::find(gc.failed, gc.failed_used, key) >= 0;
-        if (gslot < 0 && !failed && GraphCache::find(gc.warm, gc.warm_used, key) >= 0) {
-            // capture one iteration on the context's own stream
-            cudaGraph_t graph = nullptr;
-            const int64_t l0 = launch_count_now();
-            cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
-            latentam_status cs = e == cudaSuccess ? iteration(ctx->cap_stream, true, ctx->step_dev) : LATENTAM_ERR_CUDA;
-            cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->cap_stream, &graph) : e;
-            const int64_t captured = launch_count_now() - l0;
-            launch_count_add(-captured);  // nothing ran
-            cudaGraphExec_t exec = nullptr;
-            if (cs == LATENTAM_OK && e2 == cudaSuccess && graph &&
-                cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
-                const int slot = gc.next;
-                if (gc.exec[slot]) {
-                    cudaStreamSynchronize(st);  // a replay of the graph being dropped may be queued
-                    cudaGraphExecDestroy(gc.exec[slot]);
-                }
-                gc.exec[slot] = exec;
-                gc.key[slot] = key;
-                gc.launches[slot] = captured;
-                gc.next = (gc.next + 1) % GraphCache::kSlots;
-                if (gc.used < GraphCache::kSlots) ++gc.used;
-                gslot = slot;
-            } else {
-                (void)cudaGetLastError();
-                GraphCache::put(gc.failed, gc.failed_used, gc.failed_next, key);
-            }
-            if (graph) cudaGraphDestroy(graph);
-        } else if (gslot < 0 && !failed) {
-            GraphCache::put(gc.warm, gc.warm_used, gc.warm_next, key);
-        }
     }
-    if (gslot >= 0) {
-        GraphCache& gc = *ctx->graphs;
-        LAT_TRY(launch_step_set(ctx->step_dev, adam->step - 1, st));
-        for (int it = 0; it < iters; ++it) {
-            cudaError_t e = cudaGraphLaunch(gc.exec[gslot], st);
-            if (e != cudaSuccess) return cuda_error(e, "step graph launch");
-            launch_count_add(gc.launches[gslot]);
-        }
-        adam->step += iters;
-    } else {
-        for (int it = 0; it < iters; ++it) {
-            LAT_TRY(iteration(st, it == 0 || learn_f, nullptr));
-            adam->step += 1;
-        }
-    }
+    LAT_TRY(run_iterations(ctx, graphable, key, iters, learn_f != 0, adam, st, iteration));
     if (loss_host) {
         cudaError_t e = cudaMemcpyAsync(loss_host, lp, sizeof(double) * LATENTAM_LOSS_PARTS, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_error(e, "copy loss");
@@ -933,45 +963,68 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
     float* dV = reinterpret_cast<float*>(gb + g_dv);
     double* lp = reinterpret_cast<double*>(gb + g_lp);
 
-    for (int it = 0; it < iters; ++it) {
-        if (it == 0 || learn_f) {
-            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, st);
+    auto iteration = [&](cudaStream_t s, bool render, const int* step_dev) -> latentam_status {
+        if (render) {
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, s);
             for (int k = 0; k < n_frames; ++k)
                 LAT_TRY(launch_render_fwd(fs[k].cam, fs[k].proj, fs[k].bins, frames[k].f, d, Q + fs[k].pix_off * d,
-                                          T + fs[k].pix_off, nc + fs[k].pix_off, st));
+                                          T + fs[k].pix_off, nc + fs[k].pix_off, s));
         }
         LAT_TRY(latentam_decode_loss_bwd(ctx, Q, total_pix, d, dict->K, dict->V, dict->V0, M, D, F, F_dtype, mask,
-                                         cfg, prec, lp, learn_f ? dQ : nullptr, dK, dV, stream));
+                                         cfg, prec, lp, learn_f ? dQ : nullptr, dK, dV, s));
         if (learn_f) {
-            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, st);
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, s);
             for (int u = 0; u < n_groups; ++u) {
-                cudaError_t e = cudaMemsetAsync(groups[u].df, 0, sizeof(float) * (size_t)groups[u].n * d, st);
+                cudaError_t e = cudaMemsetAsync(groups[u].df, 0, sizeof(float) * (size_t)groups[u].n * d, s);
                 if (e != cudaSuccess) return cuda_error(e, "memset df");
             }
             for (int k = 0; k < n_frames; ++k)
                 if (frames[k].gaussians.n > 0)
                     LAT_TRY(launch_render_bwd(fs[k].cam, fs[k].proj, fs[k].bins, nc + fs[k].pix_off,
                                               dQ + fs[k].pix_off * d, d, groups[fs[k].group].df, frames[k].gaussians.n,
-                                              st, /*accumulate=*/true));
+                                              s, /*accumulate=*/true));
         }
-        {
-            StageTimer tm(ctx, LATENTAM_STAGE_ADAM, st);
-            AdamTensor t[8];
-            int cnt = 0;
-            t[cnt++] = AdamTensor{dict->K, dK, dict->m_K, dict->v_K, (int64_t)M * d, adam->lr_dict};
-            t[cnt++] = AdamTensor{dict->V, dV, dict->m_V, dict->v_V, (int64_t)M * D, adam->lr_dict};
-            for (int u = 0; learn_f && u < n_groups; ++u) {
-                if (cnt == 8) {
-                    LAT_TRY(launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, st));
-                    cnt = 0;
-                }
-                t[cnt++] = AdamTensor{groups[u].f, groups[u].df, groups[u].m, groups[u].v,
-                                      (int64_t)groups[u].n * d, adam->lr_f};
+        StageTimer tm(ctx, LATENTAM_STAGE_ADAM, s);
+        if (step_dev) LAT_TRY(launch_step_advance(const_cast<int*>(step_dev), s));
+        AdamTensor t[8];
+        int cnt = 0;
+        t[cnt++] = AdamTensor{dict->K, dK, dict->m_K, dict->v_K, (int64_t)M * d, adam->lr_dict};
+        t[cnt++] = AdamTensor{dict->V, dV, dict->m_V, dict->v_V, (int64_t)M * D, adam->lr_dict};
+        for (int u = 0; learn_f && u < n_groups; ++u) {
+            if (cnt == 8) {
+                LAT_TRY(launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, s, step_dev));
+                cnt = 0;
             }
-            LAT_TRY(launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, st));
+            t[cnt++] = AdamTensor{groups[u].f, groups[u].df, groups[u].m, groups[u].v, (int64_t)groups[u].n * d,
+                                  adam->lr_f};
         }
-        adam->step += 1;
+        return launch_adam(ctx, t, cnt, adam->beta1, adam->beta2, adam->eps, adam->step, s, step_dev);
+    };
+    GraphKey key;
+    const bool graphable = ctx->use_graphs && learn_f && !ctx->profiling && iters > 0;
+    if (graphable) {
+        const void* ptrs[] = {dict->K, dict->V, dict->V0, dict->m_K, dict->v_K, dict->m_V, dict->v_V, F, mask,
+                              Q, T, nc, dQ, dK, dV, lp, st};
+        for (const void* p : ptrs) key.addp(p);
+        const int64_t ints[] = {n_frames, n_groups, d, M, D, (int64_t)F_dtype, (int64_t)prec,
+                                (int64_t)ctx->ws_generation};
+        for (int64_t x : ints) key.add((uint64_t)x);
+        for (int k = 0; k < n_frames; ++k) {
+            const latentam_batch_frame& fr = frames[k];
+            for (const void* p : {(const void*)fr.f, (const void*)fr.m_f, (const void*)fr.v_f,
+                                  (const void*)fs[k].proj.xy, (const void*)fs[k].bins.pair_ids,
+                                  (const void*)fs[k].bins.tile_ranges})
+                key.addp(p);
+            key.add((uint64_t)fr.gaussians.n);
+            key.add((uint64_t)fs[k].bins.num_pairs);
+            key.add_camera(fr.camera);
+        }
+        for (int u = 0; u < n_groups; ++u) key.addp(groups[u].df);
+        for (float f : {cfg->lambda_f, cfg->lambda_cos, cfg->lambda_2, cfg->lambda_D, cfg->delta, cfg->logit_scale,
+                        adam->lr_f, adam->lr_dict, adam->beta1, adam->beta2, adam->eps})
+            key.addf(f);
     }
+    LAT_TRY(run_iterations(ctx, graphable, key, iters, learn_f != 0, adam, st, iteration));
     if (loss_host) {
         cudaError_t e = cudaMemcpyAsync(loss_host, lp, sizeof(double) * LATENTAM_LOSS_PARTS, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_error(e, "copy loss");

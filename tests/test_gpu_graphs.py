@@ -60,3 +60,27 @@ def test_graphs_follow_new_buffers(api):
             loss = st.step(1)
         assert np.isfinite(loss["total"])
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_graph_replays_match_plain_launches(api, prec):
+    from workloads import room_views
+    views = room_views(5, n_views=3, n=40_000, width=96, height=72, fx=78.75)
+    p = api.FP32 if prec == "fp32" else api.BF16
+    tdt = torch.float32 if prec == "fp32" else torch.bfloat16
+    out = []
+    for graphs in (False, True):
+        ctx = api.Context(0)
+        ctx.graphs(graphs)
+        st = api.LatentBatchStep(ctx, views, precision=p, target_dtype=tdt)
+        loss = [st.step(iters=2, learn_f=True)["total"] for _ in range(4)]
+        out.append(({k: getattr(st, k).cpu().numpy().copy() for k in ("K", "V")},
+                    st.queries[0].cpu().numpy().copy(), loss, st.adam_cfg.step))
+        ctx.close()
+    (a, fa, la, sa), (b, fb, lb, sb) = out
+    assert sa == sb == 9
+    tol = 2e-5 if prec == "fp32" else 5e-4
+    for k in ("K", "V"):
+        assert np.linalg.norm(b[k] - a[k]) / np.linalg.norm(a[k]) <= tol / 10, k
+    assert np.linalg.norm(fb - fa) / np.linalg.norm(fa) <= tol / 10
+    np.testing.assert_allclose(lb, la, rtol=tol)
