@@ -138,6 +138,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_barrier(dist):
+    """Barrier over the ranks of a multi-GPU run (no-op for one process)."""
+    if dist is not None:
+        dist.barrier()
+
+
+def max_ms_over_ranks(dist, ms: float, device: str) -> float:
+    """The slowest rank's time: every rank's step time is reduced with MAX (the job is as
+    fast as its slowest replica)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, frames_per_step: int, steps: int, ms: float) -> float:
+    """Whole-job keyframe-iterations per second: all ranks' work over the slowest rank's time."""
+    return world * frames_per_step * steps / (ms / 1e3)
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -242,15 +264,10 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
     torch.cuda.synchronize()
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        rank_barrier(dist)
 
     def max_over_ranks(ms):
-        if dist is None:
-            return ms
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_ms_over_ranks(dist, ms, "cuda")
 
     # ---- device-resident timed region (iterations replayed as CUDA graphs) -----------------
     clocks = ClockSampler(local)
@@ -268,7 +285,7 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
     launches = L.load().latentam_launch_count() - launches0
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     clk = clocks.stop()
-    value = world * n_frames * args.steps / (ms / 1e3)
+    value = job_throughput(world, n_frames, args.steps, ms)
 
     # ---- per-stage CUDA-event timers over a second pass (plain launches) --------------------
     prof_steps = max(1, min(args.steps, 10))
@@ -304,7 +321,7 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
         torch.cuda.synchronize()
         barrier()
         ems = max_over_ranks(e0.elapsed_time(e1))
-        e2e = {"value": world * n_frames * args.steps / (ems / 1e3), "unit": "iters/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_throughput(world, n_frames, args.steps, ems), "unit": "iters/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
     ctx.close()
 
