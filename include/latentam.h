@@ -74,6 +74,11 @@ typedef int32_t latentam_precision;
 #define LATENTAM_PREC_FP32 0 /* decode on FP32 CUDA cores, FP32 throughout */
 #define LATENTAM_PREC_BF16 1 /* decode contractions on tcgen05 tensor cores: BF16 operands, FP32 accumulation;
                                  M <= 1024 and D <= 1024 (else LATENTAM_ERR_UNSUPPORTED_SHAPE) */
+#define LATENTAM_PREC_FP8 2  /* the BF16 form with the value contraction Fhat = A V on E4M3 operands
+                                (kind::f8f6f4): attention rows scaled per pixel by 448 l_p (l_p the
+                                softmax denominator: the row maximum of A is 1 / l_p), V scaled per
+                                feature by 448 / max_j |V_jc|, FP32 accumulation, scales undone in
+                                the epilogue; same shape limits as BF16 */
 
 typedef int32_t latentam_dtype;
 #define LATENTAM_DTYPE_F32 0

@@ -26,6 +26,7 @@ _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED_SHAPE", -3: "OUT_OF_MEMOR
 
 PREC_FP32 = 0
 PREC_BF16 = 1
+PREC_FP8 = 2
 DTYPE_F32 = 0
 DTYPE_BF16 = 1
 LOSS_PARTS = 5

@@ -511,8 +511,9 @@ latentam_status latentam_decode_fwd(latentam_ctx* ctx, const float* Q, int64_t n
     StageTimer tm(ctx, LATENTAM_STAGE_DECODE, (cudaStream_t)stream);
     if (prec == LATENTAM_PREC_FP32)
         return decode_fwd_f32(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, (cudaStream_t)stream);
-    if (prec == LATENTAM_PREC_BF16)
-        return decode_fwd_bf16(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, (cudaStream_t)stream);
+    if (prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8)
+        return decode_fwd_bf16(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, (cudaStream_t)stream,
+                               prec == LATENTAM_PREC_FP8);
     set_error("unknown precision %d", prec);
     return LATENTAM_ERR_INVALID_ARG;
 }
@@ -550,7 +551,8 @@ latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const float* Q, int6
     a.dV = dV;
     StageTimer tm(ctx, LATENTAM_STAGE_DECODE, (cudaStream_t)stream);
     if (prec == LATENTAM_PREC_FP32) return decode_loss_bwd_f32(ctx, a, (cudaStream_t)stream);
-    if (prec == LATENTAM_PREC_BF16) return decode_loss_bwd_bf16(ctx, a, (cudaStream_t)stream);
+    if (prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8)
+        return decode_loss_bwd_bf16(ctx, a, (cudaStream_t)stream, prec == LATENTAM_PREC_FP8);
     set_error("unknown precision %d", prec);
     return LATENTAM_ERR_INVALID_ARG;
 }
@@ -595,7 +597,8 @@ latentam_status latentam_decode_fwd_paper(latentam_ctx* ctx, const float* Q, int
     LAT_TRY(enter(ctx));
     LAT_TRY(check_paper(n, ds, Q, W, D, M, df, tau));
     REQUIRE(aligned16(F_hat), "F_hat must be 16-byte aligned");
-    REQUIRE(prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_BF16, "unknown precision %d", prec);
+    REQUIRE(prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8,
+            "unknown precision %d", prec);
     lat::PaperBuffers b;
     LAT_TRY(paper_buffers(ctx, n, ds, M, df, &b));
     const lat::PaperArgs a{Q, n, ds, W, D, M, df};
@@ -603,7 +606,8 @@ latentam_status latentam_decode_fwd_paper(latentam_ctx* ctx, const float* Q, int
     StageTimer tm(ctx, LATENTAM_STAGE_DECODE, st);
     LAT_TRY(lat::paper_prepare(ctx, a, b, st));
     if (prec == LATENTAM_PREC_FP32) return decode_fwd_f32(ctx, b.Qp, n, ds, b.K, D, M, df, 1.0f / tau, F_hat, row_stats, st);
-    return decode_fwd_bf16(ctx, b.Qp, n, ds, b.K, D, M, df, 1.0f / tau, F_hat, row_stats, st);
+    return decode_fwd_bf16(ctx, b.Qp, n, ds, b.K, D, M, df, 1.0f / tau, F_hat, row_stats, st,
+                           prec == LATENTAM_PREC_FP8);
 }
 
 latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, const float* Q, int64_t n, int32_t ds,
@@ -618,7 +622,8 @@ latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, const float* Q
     REQUIRE(F_dtype == LATENTAM_DTYPE_F32 || F_dtype == LATENTAM_DTYPE_BF16, "unknown target dtype %d", F_dtype);
     REQUIRE(aligned16(D0) && aligned16(F) && aligned16(dQ) && aligned16(dW) && aligned16(dD),
             "D0, F, dQ, dW, dD must be 16-byte aligned");
-    REQUIRE(prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_BF16, "unknown precision %d", prec);
+    REQUIRE(prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8,
+            "unknown precision %d", prec);
     lat::PaperBuffers b;
     LAT_TRY(paper_buffers(ctx, n, ds, M, df, &b));
     const lat::PaperArgs pa{Q, n, ds, W, D, M, df};
@@ -646,7 +651,7 @@ latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, const float* Q
     if (prec == LATENTAM_PREC_FP32)
         LAT_TRY(decode_loss_bwd_f32(ctx, a, st));
     else
-        LAT_TRY(decode_loss_bwd_bf16(ctx, a, st));
+        LAT_TRY(decode_loss_bwd_bf16(ctx, a, st, prec == LATENTAM_PREC_FP8));
     return lat::paper_chain(ctx, pa, b, dQ, dW, dD, st);
 }
 

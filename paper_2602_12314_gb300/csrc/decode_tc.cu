@@ -12,6 +12,7 @@
 // Every intermediate is stored once, row-major (pixel x atom / pixel x feature); the
 // contractions that reduce over pixels (G5, G6) and those whose B operand runs along its
 // contiguous dimension (G2, G4) read it as an MN-major operand, so nothing is transposed.
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -59,6 +60,48 @@ __global__ void prep_dict(const float* __restrict__ K, const float* __restrict__
             const float v = k < d ? K[(int64_t)j * d + k] : 0.f;
             Kb[f] = __float2bfloat16_rn(v);
         }
+    }
+}
+
+// ---- E4M3 operands of the value contraction ----------------------------------------------
+
+// Aq[p][j] = e4m3(A[p][j] * 448 l_p): the largest weight of a softmax row is 1 / l_p (the
+// largest logit contributes exp(0)), so every scaled row peaks at the E4M3 maximum 448.
+// Thread t converts 8 weights (16 bytes in, 8 out).
+__global__ void fp8_rows(const bf16* __restrict__ A, const float* __restrict__ stats, int64_t n, int M,
+                         uint8_t* __restrict__ Aq) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int per_row = M / 8;
+    if (t >= n * per_row) return;
+    const int64_t p = t / per_row;
+    const float s = 448.0f * stats[2 * p + 1];
+    const uint4 u = reinterpret_cast<const uint4*>(A)[t];
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    uint16_t o[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[h]));
+        o[h] = __nv_cvt_float2_to_fp8x2(make_float2(f.x * s, f.y * s), __NV_SATFINITE, __NV_E4M3);
+    }
+    reinterpret_cast<uint2*>(Aq)[t] = make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
+                                                 (uint32_t)o[2] | ((uint32_t)o[3] << 16));
+}
+
+// Vtq[c][j] = e4m3(V[j][c] / inv_t[c]) with inv_t[c] = max_j |V_jc| / 448 (the transpose makes
+// the atoms the contiguous K dimension of the operand).  One thread per feature column.
+__global__ void fp8_values(const float* __restrict__ V, int M, int D, uint8_t* __restrict__ Vtq,
+                           float* __restrict__ inv_t) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= D) return;
+    float mx = 0.f;
+    for (int j = 0; j < M; ++j) mx = fmaxf(mx, fabsf(V[(size_t)j * D + c]));
+    const float it = mx > 0.f ? mx / 448.0f : 1.0f;
+    inv_t[c] = it;
+    const float s = 1.0f / it;
+    for (int j = 0; j < M; j += 2) {
+        const uint16_t o = __nv_cvt_float2_to_fp8x2(make_float2(V[(size_t)j * D + c] * s, V[(size_t)(j + 1) * D + c] * s),
+                                                   __NV_SATFINITE, __NV_E4M3);
+        *reinterpret_cast<uint16_t*>(Vtq + (size_t)c * M + j) = o;
     }
 }
 
@@ -192,7 +235,7 @@ struct SoftmaxParams {
 // and combine their (row max, partial denominator) pairs before normalising.
 struct SoftmaxEpi {
     // persistent: one K chunk (the padded queries) per tile
-    static constexpr int BN = 256, BK = 64, STAGES = 1, BOX_B = 256, EPI_WG = 4, E_BOXES = 0, O_BOXES = 4;
+    static constexpr int BN = 256, BK = 64, ELEM = 2, STAGES = 1, BOX_B = 256, EPI_WG = 4, E_BOXES = 0, O_BOXES = 4;
     static constexpr int XROUNDS = 1;
     static constexpr bool A_MN = false, B_MN = false;
     using Params = SoftmaxParams;
@@ -260,29 +303,56 @@ struct FhatParams {
     bf16* dF;     // n x D
     float* row;   // n x 4: a_p, b_p, <A_p, dA_p>, cos_p
     float* Fout;  // n x D FP32 Fhat (inference form: no loss) or NULL
+    // E4M3 form: row statistics of the softmax (the per-pixel scale 448 l_p) and the
+    // per-feature scale inverses max_j |V_jc| / 448
+    const float* stats;
+    const float* inv_t;
 };
 
-// ETILE: the BF16 target rows come through shared memory (TMA, after the MMAs) and two CTAs
-// share an SM; otherwise (FP32 targets) each thread reads its own row from global memory, one
-// chunk ahead.
-template <bool ETILE>
+// ETILE: the BF16 target rows come through shared memory (TMA, after the MMAs); otherwise
+// (FP32 targets) each thread reads its own row from global memory, one chunk ahead.
+// Q8: the contraction runs on E4M3 operands (attention rows scaled per pixel, values per
+// feature, both K-major) and the accumulator is rescaled before any use.
+template <bool ETILE, bool Q8 = false>
 struct FhatEpi {
-    // persistent, 32-wide K chunks (three ring stages fit beside two epilogue buffers)
-    static constexpr int BN = 256, BK = 32, STAGES = 3, BOX_B = 256, EPI_WG = ETILE ? 4 : 2, XROUNDS = 1;
+    // persistent, 64-byte K chunks (three ring stages fit beside two epilogue buffers)
+    static constexpr int ELEM = Q8 ? 1 : 2, BK = 64 / ELEM;
+    static constexpr int BN = 256, STAGES = 3, BOX_B = 256, EPI_WG = ETILE ? 4 : 2, XROUNDS = 1;
     static constexpr int E_BOXES = ETILE ? BN / 64 : 0, O_BOXES = BN / 64;  // dFhat staged over the target
-    static constexpr bool A_MN = false, B_MN = true;  // B = V (atoms x features), features contiguous
+    // B = V (atoms x features, features contiguous: MN-major) or, for E4M3, V^T (K-major)
+    static constexpr bool A_MN = false, B_MN = !Q8;
     using Params = FhatParams;
+    // Fhat chunk c0 of this thread's row from TMEM (E4M3: times 1 / (scale_p scale_c))
+    static __device__ __forceinline__ void fhat32(const Params& p, const tc::EpiCtx& ec, int c0, float isp,
+                                                  float (&h)[32]) {
+        tc::tmem_ld32(ec.taddr + c0, h);
+        if constexpr (Q8) {
+            const float4* it = reinterpret_cast<const float4*>(p.inv_t + ec.n0 + c0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 v = it[q];
+                h[4 * q] *= isp * v.x;
+                h[4 * q + 1] *= isp * v.y;
+                h[4 * q + 2] *= isp * v.z;
+                h[4 * q + 3] *= isp * v.w;
+            }
+        }
+    }
+    static __device__ __forceinline__ float row_scale_inv(const Params& p, int64_t pix, bool valid) {
+        if constexpr (Q8) return valid ? 1.0f / (448.0f * p.stats[2 * pix + 1]) : 0.f;
+        return 1.f;
+    }
     // body(c0, h, f) for each 32-column chunk of this thread's share of the slice: h = Fhat
     // (TMEM), f = target
     template <class Body>
     static __device__ __forceinline__ void sweep(const Params& p, const tc::EpiCtx& ec, int64_t frow, int ncols,
-                                                 Body&& body) {
+                                                 float isp, Body&& body) {
         constexpr int step = 32 * EPI_WG;
         float h[32], f[32];
         if constexpr (ETILE) {
             for (int c0 = 32 * ec.g; c0 < ncols; c0 += step) {
                 ec.row32(c0, f);
-                tc::tmem_ld32(ec.taddr + c0, h);
+                fhat32(p, ec, c0, isp, h);
                 body(c0, h, f);
             }
         } else {
@@ -290,7 +360,7 @@ struct FhatEpi {
             load_target32(p.F, p.F_dtype, frow + 32 * ec.g, f);
             for (int c0 = 32 * ec.g; c0 < ncols; c0 += step) {
                 if (c0 + step < ncols) load_target32(p.F, p.F_dtype, frow + c0 + step, fn);
-                tc::tmem_ld32(ec.taddr + c0, h);
+                fhat32(p, ec, c0, isp, h);
                 body(c0, h, f);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) f[i] = fn[i];
@@ -298,16 +368,16 @@ struct FhatEpi {
         }
     }
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
-        const uint32_t taddr = ec.taddr;
         const int row = ec.row, m0 = ec.m0, g = ec.g;
         const int ncols = min(BN, p.D - ec.n0);  // features of this CTA's slice
         float* scr = ec.scratch;
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
+        const float isp = row_scale_inv(p, pix, valid);
         if (p.Fout) {  // inference form, launched without a cluster
             float h[32];
             for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
-                tc::tmem_ld32(taddr + c0, h);
+                fhat32(p, ec, c0, isp, h);
                 if (valid) {
                     float4* d4 = reinterpret_cast<float4*>(p.Fout + pix * p.D + ec.n0 + c0);
 #pragma unroll
@@ -326,7 +396,7 @@ struct FhatEpi {
         if (ETILE)
             for (int b = 0; b < E_BOXES; ++b) (void)ec.wait_box(b);  // a timeout raises the error flag
         float t[4] = {0.f, 0.f, 0.f, 0.f};  // <Fhat, F>, |Fhat|^2, |F|^2, |Fhat - F|^2
-        sweep(p, ec, frow, ncols, [&](int, const float(&h)[32], const float(&f)[32]) {
+        sweep(p, ec, frow, ncols, isp, [&](int, const float(&h)[32], const float(&f)[32]) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 t[0] += h[i] * f[i];
@@ -376,7 +446,7 @@ struct FhatEpi {
             }
         }
         // dFhat overwrites the target chunk it was formed from (same thread, same bytes)
-        sweep(p, ec, frow, ncols, [&](int c0, const float(&h)[32], const float(&f)[32]) {
+        sweep(p, ec, frow, ncols, isp, [&](int c0, const float(&h)[32], const float(&f)[32]) {
             float v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = a * h[i] + b * f[i];
@@ -556,6 +626,30 @@ latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_
 // Launch one tile grid of Epi (emap: epilogue operand, omap: staged output); cluster_y > 1
 // groups that many consecutive y tiles of each row block into a thread-block cluster (the
 // epilogue's row exchange).
+// Tensor map of a row-major 8-bit matrix (rows x inner bytes, row stride ld bytes), boxes of
+// 64 x box_rows bytes with 64-byte swizzle.
+latentam_status u8_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows) {
+    EncodeTiledFn enc;
+    LAT_TRY(encoder(&enc));
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || ld % 16) {
+        set_error("tensor-core operand not 16-byte aligned");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld 8-bit operand", (int)r, (long long)rows,
+                  (long long)inner);
+        return LATENTAM_ERR_CUDA;
+    }
+    return LATENTAM_OK;
+}
+
 template <class Epi>
 latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 grid, tc::GemmGrid g,
                             const typename Epi::Params& p, int* err, cudaStream_t st, const CUtensorMap* emap = nullptr,
@@ -653,18 +747,25 @@ struct TcBuffers {
     float *row, *coef, *part;
     double* acc;
     int* err;
+    // E4M3 form
+    uint8_t *Aq, *Vtq;
+    float *stats, *inv_t;
 };
 
-latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool train, TcBuffers* b) {
+latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool train, bool fp8, TcBuffers* b) {
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const int64_t nn = std::max<int64_t>(n, 1);
     const size_t e2 = sizeof(bf16);
-    size_t o = 0, off[5];
-    off[0] = o, o += up(e2 * nn * kPad);             // Qb
-    off[1] = o, o += up(e2 * (size_t)M * kPad);      // Kb
-    off[2] = o, o += up(e2 * (size_t)M * D);         // Vb
-    off[3] = o, o += up(sizeof(float) * 4 * nn);     // row
-    off[4] = o, o += up(sizeof(float) * (size_t)M);  // coef
+    size_t o = 0, off[9];
+    off[0] = o, o += up(e2 * nn * kPad);                      // Qb
+    off[1] = o, o += up(e2 * (size_t)M * kPad);               // Kb
+    off[2] = o, o += up(e2 * (size_t)M * D);                  // Vb
+    off[3] = o, o += up(sizeof(float) * 4 * nn);              // row
+    off[4] = o, o += up(sizeof(float) * (size_t)M);           // coef
+    off[5] = o, o += fp8 ? up((size_t)nn * M) : 0;            // Aq
+    off[6] = o, o += fp8 ? up((size_t)D * M) : 0;             // Vtq
+    off[7] = o, o += fp8 ? up(sizeof(float) * 2 * nn) : 0;    // stats
+    off[8] = o, o += fp8 ? up(sizeof(float) * (size_t)D) : 0; // inv_t
     char* ops = static_cast<char*>(ws(ctx, WS_DEC_AUX3, o));
     const size_t rows_bytes = up(e2 * nn * M) + (train ? up(e2 * nn * D) + up(e2 * nn * M) : 0);
     char* rows = static_cast<char*>(ws(ctx, WS_DEC_A, rows_bytes));
@@ -681,6 +782,10 @@ latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool trai
     b->acc = acc;
     b->err = reinterpret_cast<int*>(acc + 8);
     b->part = nullptr;
+    b->Aq = fp8 ? reinterpret_cast<uint8_t*>(ops + off[5]) : nullptr;
+    b->Vtq = fp8 ? reinterpret_cast<uint8_t*>(ops + off[6]) : nullptr;
+    b->stats = fp8 ? reinterpret_cast<float*>(ops + off[7]) : nullptr;
+    b->inv_t = fp8 ? reinterpret_cast<float*>(ops + off[8]) : nullptr;
     return LATENTAM_OK;
 }
 
@@ -721,6 +826,10 @@ latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, 
     LAT_CHECK_LAUNCH("prep_dict");
     prep_queries<<<cdiv(n * (kPad / 8), 256), 256, 0, st>>>(Q, n, d, b.Qb);
     LAT_CHECK_LAUNCH("prep_queries");
+    if (b.Vtq) {
+        fp8_values<<<cdiv(D, 128), 128, 0, st>>>(V, M, D, b.Vtq, b.inv_t);
+        LAT_CHECK_LAUNCH("fp8_values");
+    }
     CUtensorMap mQ, mK;
     LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, kTileM));
     LAT_TRY(bf16_map(&mK, b.Kb, kPad, M, kPad, 256));
@@ -733,8 +842,12 @@ latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, 
 
 // G2: Fhat = A V (A in 32-wide K chunks, 64-byte swizzle), B = V read MN-major in 64 x 32
 // boxes (features x atoms).
+latentam_status tc_fhat8(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp,
+                         cudaStream_t st);
+
 latentam_status tc_fhat(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp,
                         cudaStream_t st) {
+    if (b.Aq) return tc_fhat8(ctx, b, n, M, D, fp, st);
     constexpr int BK = FhatEpi<true>::BK;
     CUtensorMap mA, mV;
     LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM, BK));
@@ -753,14 +866,38 @@ latentam_status tc_fhat(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M,
     return launch_persist<FhatEpi<false>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, nullptr, &mdF);
 }
 
+// G2 on E4M3 operands: the attention rows scaled per pixel (from the softmax row statistics)
+// and V^T scaled per feature, both in 64-byte K chunks; the epilogue undoes both scales.
+latentam_status tc_fhat8(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp0,
+                         cudaStream_t st) {
+    fp8_rows<<<cdiv(n * (M / 8), 256), 256, 0, st>>>(b.A, b.stats, n, M, b.Aq);
+    LAT_CHECK_LAUNCH("fp8_rows");
+    FhatParams fp = fp0;
+    fp.stats = b.stats;
+    fp.inv_t = b.inv_t;
+    CUtensorMap mA, mV;
+    LAT_TRY(u8_map(&mA, b.Aq, M, n, M, kTileM));
+    LAT_TRY(u8_map(&mV, b.Vtq, M, D, M, 256));
+    const int cy = cdiv(D, 256), tiles = cdiv(n, kTileM), kc = cdiv(M, 64);
+    if (fp.Fout) return launch_persist<FhatEpi<false, true>>(ctx, mA, mV, tiles, kc, cy, false, fp, b.err, st);
+    CUtensorMap mdF;
+    LAT_TRY(bf16_map(&mdF, fp.dF, D, n, D, kTileM));
+    if (fp.F_dtype == LATENTAM_DTYPE_BF16) {
+        CUtensorMap mF;
+        LAT_TRY(bf16_map(&mF, fp.F, D, n, D, kTileM));
+        return launch_persist<FhatEpi<true, true>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, &mF, &mdF);
+    }
+    return launch_persist<FhatEpi<false, true>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, nullptr, &mdF);
+}
+
 }  // namespace
 
-latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
+latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st, bool fp8) {
     const int64_t n = a.n;
     const int M = a.M, D = a.D, d = a.d;
     LAT_TRY(check_tc_shape(M, D));
     TcBuffers b;
-    LAT_TRY(tc_buffers(ctx, n, M, D, true, &b));
+    LAT_TRY(tc_buffers(ctx, n, M, D, true, fp8, &b));
     cudaError_t e = cudaMemsetAsync(b.acc, 0, 256, st);
     if (e != cudaSuccess) return cuda_error(e, "memset accumulators");
     if (n > 0) {
@@ -782,9 +919,9 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
     if (!b.part) return LATENTAM_ERR_OUT_OF_MEMORY;
     if (n > 0) {
         // G1: S = Q K^T -> softmax
-        LAT_TRY(tc_forward(ctx, a.Q, n, d, a.K, a.V, M, D, a.c, b, nullptr, st));
+        LAT_TRY(tc_forward(ctx, a.Q, n, d, a.K, a.V, M, D, a.c, b, b.stats, st));
         // G2: Fhat = A V -> loss terms -> dFhat
-        FhatParams fp{n, D, a.F, a.F_dtype, a.mask, a.cfg, b.acc, b.dF, b.row, nullptr};
+        FhatParams fp{n, D, a.F, a.F_dtype, a.mask, a.cfg, b.acc, b.dF, b.row, nullptr, nullptr, nullptr};
         LAT_TRY(tc_fhat(ctx, b, n, M, D, fp, st));
         // G3: dA = dFhat V^T -> dS
         CUtensorMap mdF, mV, mdS, mK;
@@ -838,16 +975,22 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
 }
 
 latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V,
-                                int M, int D, float c, float* F_hat, float* row_stats, cudaStream_t st) {
+                                int M, int D, float c, float* F_hat, float* row_stats, cudaStream_t st, bool fp8) {
     LAT_TRY(check_tc_shape(M, D));
     if (n == 0) return LATENTAM_OK;
     TcBuffers b;
-    LAT_TRY(tc_buffers(ctx, n, M, D, false, &b));
+    LAT_TRY(tc_buffers(ctx, n, M, D, false, fp8, &b));
     cudaError_t e = cudaMemsetAsync(b.acc, 0, 256, st);
     if (e != cudaSuccess) return cuda_error(e, "memset accumulators");
-    LAT_TRY(tc_forward(ctx, Q, n, d, K, V, M, D, c, b, row_stats, st));
+    float* stats = fp8 ? b.stats : row_stats;
+    LAT_TRY(tc_forward(ctx, Q, n, d, K, V, M, D, c, b, stats, st));
+    if (fp8 && row_stats) {
+        e = cudaMemcpyAsync(row_stats, b.stats, sizeof(float) * 2 * n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_error(e, "copy row statistics");
+    }
     if (F_hat) {
-        FhatParams fp{n, D, nullptr, LATENTAM_DTYPE_F32, nullptr, latentam_loss_cfg{}, b.acc, nullptr, b.row, F_hat};
+        FhatParams fp{n, D, nullptr, LATENTAM_DTYPE_F32, nullptr, latentam_loss_cfg{}, b.acc, nullptr, b.row, F_hat,
+                      nullptr, nullptr};
         LAT_TRY(tc_fhat(ctx, b, n, M, D, fp, st));
     }
     return LATENTAM_OK;

@@ -190,13 +190,14 @@ latentam_status decode_fwd_f32(latentam_ctx* ctx, const float* Q, int64_t n, int
                                const float* V, int M, int D, float c, float* F_hat, float* row_stats,
                                cudaStream_t st);
 latentam_status decode_loss_bwd_f32(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st);
-latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st);
+// fp8: the value contraction (softmax weights times V) on E4M3 operands
+latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st, bool fp8 = false);
 // FP32 decode + loss + backward with all scratch in a static device array (no allocation).
 latentam_status decode_loss_bwd_f32_noalloc(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st);
 size_t decode_noalloc_scratch_bytes();
 latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K,
                                 const float* V, int M, int D, float c, float* F_hat, float* row_stats,
-                                cudaStream_t st);
+                                cudaStream_t st, bool fp8 = false);
 
 // The paper's W / D / tau form of the decode, computed through the free-key decode.
 struct PaperArgs {

@@ -408,10 +408,10 @@ __host__ __device__ constexpr uint32_t persist_box_bytes() {  // one box buffer
     return (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * kTileABytes;
 }
 
-// One ring stage: A (128 x BK) and B (BN x BK) BF16.
+// One ring stage: A (128 x BK) and B (BN x BK) elements of Epi::ELEM bytes (2: BF16, 1: E4M3).
 template <class Epi>
 __host__ __device__ constexpr uint32_t persist_stage_bytes() {
-    return (uint32_t)(kTileM + Epi::BN) * Epi::BK * 2;
+    return (uint32_t)(kTileM + Epi::BN) * Epi::BK * Epi::ELEM;
 }
 
 __host__ __device__ constexpr int persist_threads(int epi_warpgroups) { return 96 + 128 * epi_warpgroups; }
@@ -432,20 +432,23 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
     constexpr int STAGES = Epi::STAGES;
     constexpr int BOX_B = Epi::BOX_B;
     constexpr int G = Epi::EPI_WG;
-    constexpr int BK = Epi::BK;  // 64: 128-byte swizzled K-major rows; 32: 64-byte swizzled
-    constexpr uint32_t A_BYTES = (uint32_t)kTileM * BK * 2;
+    constexpr int BK = Epi::BK;      // K elements per chunk
+    constexpr int ELEM = Epi::ELEM;  // 2: BF16 operands (kind::f16), 1: E4M3 (kind::f8f6f4)
+    constexpr int ROWB = BK * ELEM;  // 128: 128-byte swizzled K-major rows; 64: 64-byte swizzled
+    constexpr uint32_t A_BYTES = (uint32_t)kTileM * ROWB;
     constexpr uint32_t STAGE_BYTES = persist_stage_bytes<Epi>();
     constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;
     constexpr uint32_t MN_BOX = 64u * BK * 2;  // one 64 (MN) x BK (K) box of an MN-major operand
     constexpr uint32_t BOX_BYTES = persist_box_bytes<Epi>();
     constexpr bool A_MN = Epi::A_MN, B_MN = Epi::B_MN;
-    constexpr uint32_t IDESC = idesc_bf16(kTileM, BN, A_MN, B_MN);
+    constexpr uint32_t IDESC = ELEM == 1 ? idesc_e4m3(kTileM, BN) : idesc_bf16(kTileM, BN, A_MN, B_MN);
     constexpr int E_BOXES = Epi::E_BOXES, O_BOXES = Epi::O_BOXES;
     static_assert(BN % 16 == 0 && BN <= 256, "two accumulators of BN <= 256 columns fill TMEM");
+    static_assert(ELEM == 2 || (ELEM == 1 && !B_MN), "E4M3 operands are read K-major");
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
     static_assert(!B_MN || BN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
     static_assert(E_BOXES <= 4 && O_BOXES <= 4 && Epi::XROUNDS <= 1 && G <= 4, "epilogue shape");
-    static_assert(BK == 64 || BK == 32, "K chunk of 64 or 32");
+    static_assert(ROWB == 128 || ROWB == 64, "K chunk rows of 128 or 64 bytes");
     static_assert(!A_MN, "the persistent tile reads A K-major");
     static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "stages stay 1024-byte aligned");
 
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                     } else {
 #pragma unroll
                         for (int b = 0; b < BN / BOX_B; ++b)
-                            tma_load_2d(sb + b * BOX_B * BK * 2, &tmB, &full[s], kx, n0 + b * BOX_B);
+                            tma_load_2d(sb + b * BOX_B * ROWB, &tmB, &full[s], kx, n0 + b * BOX_B);
                     }
                 }
             }
@@ -616,11 +619,14 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                     const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
                     const uint32_t sb = sa + A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t da = BK == 64 ? sw128_desc(sa + kk * 32) : sw64_desc(sa + kk * 32);
+                    for (int kk = 0; kk < ROWB / 32; ++kk) {  // one MMA consumes 32 bytes of K
+                        const uint64_t da = ROWB == 128 ? sw128_desc(sa + kk * 32) : sw64_desc(sa + kk * 32);
                         const uint64_t db = B_MN ? mn128_desc(sb + kk * 16 * 128, MN_BOX)
-                                                 : (BK == 64 ? sw128_desc(sb + kk * 32) : sw64_desc(sb + kk * 32));
-                        mma_bf16(dst, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+                                                 : (ROWB == 128 ? sw128_desc(sb + kk * 32) : sw64_desc(sb + kk * 32));
+                        if (ELEM == 1)
+                            mma_e4m3(dst, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+                        else
+                            mma_bf16(dst, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
                     }
                     mma_commit(&empty[s]);
                 }
