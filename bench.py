@@ -63,7 +63,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--batch", type=int, default=6, help="keyframes of the batched form (B + 1, B = 5 in Sec. IV-A)")
-    p.add_argument("--precision", choices=["both", "fp32", "bf16", "bf16_batch", "fp32_batch"], default="both",
+    p.add_argument("--precision", choices=["both", "fp32", "bf16", "fp8", "bf16_batch", "fp32_batch"], default="both",
                    help="both: the FP32 form is the headline value, the BF16 tensor-core form is reported beside it")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -343,10 +343,12 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
     else:
         peak = float(peaks["bf16_tflops_sustained"])
         key, per_pixel = _DECODE_TRAFFIC["bf16"]
-        traffic = per_pixel * n if key == _decode_sources_hash() else None
+        traffic = per_pixel * n if key == _decode_sources_hash() and prec == api.BF16 else None
         roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 GEMM kernels + their epilogues)",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"bf16 sustained, {peak_src}", "traffic": traffic,
+                "peak_source": f"bf16 sustained, {peak_src}" + (
+                    " (five of the six contractions are BF16; the value contraction runs on E4M3)"
+                    if prec == api.FP8 else ""), "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of every decode launch of one "
                                   "step on the 480x360 crop, scaled by pixel count" if traffic else None,
                 "algorithmic_per_launch": flops}
@@ -354,7 +356,7 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
     return {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": int(launches), "e2e": e2e,
             "keyframes_per_step": n_frames,
             "roofline": roof, "clocks": clk, "stages_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
-            "dtype": "f32" if prec == api.FP32 else "bf16"}
+            "dtype": {api.FP32: "f32", api.BF16: "bf16", api.FP8: "bf16+e4m3"}[prec]}
 
 
 def run_ours(args, world, rank, local):
@@ -368,14 +370,15 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     scene = _scene(args.seed + rank, args.crop)
-    forms = ["fp32", "bf16", "bf16_batch"] if args.precision == "both" else [args.precision]
+    forms = ["fp32", "bf16", "bf16_batch", "fp8"] if args.precision == "both" else [args.precision]
     res = {}
     for f in forms:
         views = None
         if f.endswith("_batch"):
             from workloads import room_views
             views = room_views(args.seed + rank, n_views=args.batch)
-        res[f] = _measure(args, world, rank, local, scene, api.FP32 if f.startswith("fp32") else api.BF16, dist,
+        prec = api.FP32 if f.startswith("fp32") else api.FP8 if f == "fp8" else api.BF16
+        res[f] = _measure(args, world, rank, local, scene, prec, dist,
                           views)
     if rank != 0:
         if dist is not None:
