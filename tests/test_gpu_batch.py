@@ -75,3 +75,42 @@ def test_batch_stage2_keeps_queries(api, ctx, views, prec):
     # four Adam steps of lr 0.01 move every value entry by at most 0.04
     moved = (st.V - V0).abs()
     assert float(moved.max()) <= 0.04 + 1e-5 and float(moved.mean()) > 1e-3
+
+
+def test_uneven_keyframes_own_maps_shared_dictionary(api, ctx):
+    """Keyframes of three resolutions, each with its own map and queries, one dictionary of
+    M = 512 atoms of D = 768 (the batched workload's shapes, scaled down)."""
+    from workloads import keyframe_batch
+    frames = keyframe_batch(7, sizes=((48, 36), (96, 72), (80, 60)), ns=(15_000, 40_000, 25_000))
+    st = api.LatentBatchStep(ctx, frames, precision=api.FP32)
+    assert len(st.queries) == 3
+    loss = st.step(iters=1, learn_f=True)
+    o = oracle.iteration_batch(frames, oracle.LossConfig())
+    assert loss["total"] == pytest.approx(o["loss"]["total"], rel=1e-4)
+    assert loss["n_valid"] == o["loss"]["n_valid"]
+    lr = 0.01
+    checks = [("K", st.K, frames[0].K, o["dK"]), ("V", st.V, frames[0].V, o["dV"])]
+    checks += [(f"f{k}", st.queries[k], frames[k].f, o["df"][id(frames[k].f)]) for k in range(3)]
+    for name, dev_t, x0, g in checks:
+        want = _adam_first(x0, g, lr)
+        got = dev_t.cpu().numpy().astype(np.float64)
+        well = np.abs(g) > 1e-2 * np.abs(g).max()
+        np.testing.assert_allclose(got[well], want[well], rtol=0, atol=1e-4 * lr + 1e-6, err_msg=name)
+    # the tensor-core form of the same batch
+    st16 = api.LatentBatchStep(ctx, frames, precision=api.BF16, target_dtype=torch.bfloat16)
+    l16 = st16.step(iters=1, learn_f=True)
+    assert l16["total"] == pytest.approx(o["loss"]["total"], rel=5e-3)
+
+
+def test_large_dictionary_ten_iterations(api, ctx):
+    """A keyframe with M = 1024 atoms of D = 768 (the large-map workload's dictionary) run for
+    ten Stage-I iterations: the first against the oracle, all finite."""
+    from workloads import room_scene
+    s = room_scene(8, n=60_000, d=32, M=1024, D=768, width=96, height=72, fx=78.75)
+    o = oracle.iteration(s, oracle.LossConfig())
+    for prec, tdt, rel in ((api.FP32, torch.float32, 1e-4), (api.BF16, torch.bfloat16, 5e-3)):
+        st = api.LatentStep(ctx, s, precision=prec, target_dtype=tdt)
+        l0 = st.step(iters=1)
+        assert l0["total"] == pytest.approx(o["loss"]["total"], rel=rel)
+        l9 = st.step(iters=9)
+        assert np.isfinite(l9["total"]) and st.adam_cfg.step == 11

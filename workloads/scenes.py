@@ -319,6 +319,20 @@ def room_views(seed: int = 0, n_views: int = 6, n: int = 300_000, d: int = 32, M
     return views
 
 
+def keyframe_batch(seed: int = 0, sizes=((320, 240), (640, 480), (848, 480)), ns=(100_000, 300_000, 200_000),
+                   d: int = 32, M: int = 512, D: int = 768) -> list:
+    """Keyframes of uneven resolution, each with its own room (independently seeded) and its own
+    active map of Gaussians and queries, sharing one dictionary (the first room's K, V, V0):
+    the shape of the batched workload (several keyframes, one dictionary).  Focal length
+    scales with the image width (fx = 525 at 640)."""
+    frames = []
+    for k, ((w, h), n) in enumerate(zip(sizes, ns)):
+        s = room_scene(seed + 97 * k, n=n, d=d, M=M, D=D, width=w, height=h, fx=525.0 * w / 640.0)
+        frames.append(s)
+    K, V, V0 = frames[0].K, frames[0].V, frames[0].V0
+    return [dataclasses.replace(s, K=K, V=V, V0=V0, name=f"{s.name}[batch {k}]") for k, s in enumerate(frames)]
+
+
 def precision_scene(seed: int = 0, **kw) -> Scene:
     """The larger-dims room: 500k Gaussians, d = 32, M = 512, D = 1024, 640x480."""
     args = dict(n=500_000, d=32, M=512, D=1024)
