@@ -186,6 +186,14 @@ LATENTAM_API latentam_status latentam_profile_read(latentam_ctx* ctx, double* ms
  * as plain launches.  Disabling drops the instantiated graphs (synchronises the device). */
 LATENTAM_API latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t enable);
 
+/* Autotuning of the tensor-core decode (on by default): the first time a context meets a shape
+ * (pixel count, M, D) outside stream capture, the pixel-split factors of the two reductions
+ * over pixels (dV and dK) are chosen by timing three candidates (the one-wave split, half and
+ * twice it) with CUDA events on the caller's stream (this synchronises that stream once); the
+ * fastest is kept for the context's lifetime (32 shapes).  Results differ between splits only
+ * by FP32 summation order.  Disabling clears the choices and uses the one-wave split. */
+LATENTAM_API latentam_status latentam_autotune_enable(latentam_ctx* ctx, int32_t enable);
+
 /* ---- splatting (Sec. III-A, Eq. alpha_blending; Sec. III-B, Eq. render_query) ------- */
 
 /* Project every Gaussian: EWA screen-space covariance, conic, opacity, depth key and

@@ -100,6 +100,7 @@ _SIGS = {
     "latentam_ctx_destroy": ([P], I32),
     "latentam_profile_enable": ([P, I32], I32),
     "latentam_graphs_enable": ([P, I32], I32),
+    "latentam_autotune_enable": ([P, I32], I32),
     "latentam_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I32], I32),
     "latentam_project": ([P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Projected), P], I32),
     "latentam_sort": ([P, I32, ctypes.POINTER(Projected), ctypes.POINTER(Camera), ctypes.POINTER(Bins), P], I32),

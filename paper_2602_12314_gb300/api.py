@@ -116,6 +116,10 @@ class Context:
         """Capture and replay the step's iterations as CUDA graphs (on by default)."""
         L.check(_lib().latentam_graphs_enable(self.handle, int(bool(enable))))
 
+    def autotune(self, enable: bool = True):
+        """Time candidate split factors of the pixel reductions on first use of a shape (on by default)."""
+        L.check(_lib().latentam_autotune_enable(self.handle, int(bool(enable))))
+
     def profile(self, enable: bool = True):
         """Turn the per-stage CUDA-event timers on or off."""
         L.check(_lib().latentam_profile_enable(self.handle, int(bool(enable))))

@@ -378,6 +378,7 @@ latentam_status latentam_ctx_create(int32_t device, latentam_ctx** out) {
     c->cc_major = prop.major;
     c->cc_minor = prop.minor;
     c->use_graphs = 1;
+    c->autotune = 1;
     c->graphs = new (std::nothrow) GraphCache();
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
@@ -422,6 +423,13 @@ latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t enable) {
         ctx->graphs->clear();
         if (e != cudaSuccess) return cuda_error(e, "synchronise before dropping graphs");
     }
+    return LATENTAM_OK;
+}
+
+latentam_status latentam_autotune_enable(latentam_ctx* ctx, int32_t enable) {
+    LAT_TRY(enter(ctx));
+    ctx->autotune = enable != 0;
+    if (!enable) ctx->tune_used = ctx->tune_next = 0;
     return LATENTAM_OK;
 }
 

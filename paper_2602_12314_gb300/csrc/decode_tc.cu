@@ -789,14 +789,59 @@ latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool trai
     return LATENTAM_OK;
 }
 
-// Split of the pixel reduction (K) of G5/G6 so that about one wave of CTAs runs.
-tc::GemmGrid pixel_split(int64_t n, int tiles_xy, int num_sms, int* z_out) {
+// Split of the pixel reduction (K) of G5/G6 into about z parts of at least four 64-pixel
+// chunks; *z_out receives the number of parts.
+tc::GemmGrid pixel_split(int64_t n, int z, int* z_out) {
     const int chunks = (int)((n + tc::kChunkK - 1) / tc::kChunkK);
-    int z = std::max(1, (num_sms + tiles_xy - 1) / tiles_xy);
-    z = std::min(z, std::max(1, chunks / 4));
+    z = std::max(1, std::min(z, std::max(1, chunks / 4)));
     const int cpz = (chunks + z - 1) / z;
     *z_out = (chunks + cpz - 1) / cpz;
     return tc::GemmGrid{chunks, cpz};
+}
+
+// The split the tile grid starts from: about one wave of CTAs.
+int wave_split(int tiles_xy, int num_sms) { return std::max(1, (num_sms + tiles_xy - 1) / tiles_xy); }
+
+// Autotuned split of a pixel reduction: the first time a shape (n, M, D, which) is seen
+// outside stream capture, `launch(z)` runs for the wave split, half of it and twice it (one
+// untimed warm-up run first), timed with CUDA events on the stream, and the fastest split is
+// kept in the context.  Returns the split to use.
+template <class Launch>
+latentam_status tuned_split(latentam_ctx* ctx, int64_t n, int M, int D, int which, int z0, cudaStream_t st,
+                            Launch&& launch, int* z_out) {
+    *z_out = z0;
+    for (int i = 0; i < ctx->tune_used; ++i) {
+        const auto& t = ctx->tune[i];
+        if (t.n == n && t.M == M && t.D == D && t.which == which) {
+            *z_out = t.z;
+            return LATENTAM_OK;
+        }
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (!ctx->autotune || cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return LATENTAM_OK;
+    const int cand[3] = {z0, std::max(1, z0 / 2), 2 * z0};
+    cudaEvent_t ev[4];
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return cuda_error(cudaGetLastError(), "tuning events");
+    latentam_status s = launch(cand[0]);  // warm-up
+    float best = 1e30f;
+    for (int i = 0; i < 3 && s == LATENTAM_OK; ++i) {
+        cudaEventRecord(ev[i], st);
+        s = launch(cand[i]);
+        cudaEventRecord(ev[i + 1], st);
+        cudaEventSynchronize(ev[i + 1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+        if (s == LATENTAM_OK && ms < best) best = ms, *z_out = cand[i];
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    LAT_TRY(s);
+    auto& t = ctx->tune[ctx->tune_next];
+    t = latentam_ctx::TuneEntry{n, M, D, which, *z_out};
+    ctx->tune_next = (ctx->tune_next + 1) % 32;
+    if (ctx->tune_used < 32) ++ctx->tune_used;
+    return LATENTAM_OK;
 }
 
 }  // namespace
@@ -908,13 +953,10 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
                                               b.acc);
     LAT_CHECK_LAUNCH("tc_trust_region");
     constexpr int BNq = kPad;  // queries padded to 64 columns
-    int zV = 1, zK = 1;
-    tc::GemmGrid gV{0, 1}, gK{0, 1};
-    if (n > 0) {
-        gV = pixel_split(n, cdiv(M, kTileM) * cdiv(D, 256), ctx->num_sms, &zV);
-        gK = pixel_split(n, cdiv(M, kTileM), ctx->num_sms, &zK);
-    }
-    const size_t part_floats = std::max((size_t)zV * M * D, (size_t)zK * M * BNq);
+    const int tilesV = cdiv(M, kTileM) * cdiv(D, 256), tilesK = cdiv(M, kTileM);
+    const int zV0 = wave_split(tilesV, ctx->num_sms), zK0 = wave_split(tilesK, ctx->num_sms);
+    // partial sums for the largest split a tuner may try
+    const size_t part_floats = std::max((size_t)2 * zV0 * M * D, (size_t)2 * zK0 * M * BNq);
     b.part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * part_floats));
     if (!b.part) return LATENTAM_ERR_OUT_OF_MEMORY;
     if (n > 0) {
@@ -944,13 +986,22 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
         }
     }
     // G5: dV = A^T dFhat (+ trust region), both operands pixel-major (MN-major)
+    int zV = 0, zK = 0;
     if (a.dV) {
         if (n > 0) {
             CUtensorMap mA, mdF;
             LAT_TRY(bf16_map(&mA, b.A, M, n, M, 64));
             LAT_TRY(bf16_map(&mdF, b.dF, D, n, D, 64));
             PartParams pp{M, D, D, b.part};
-            LAT_TRY(launch_gemm<PartEpi<256>>(mA, mdF, dim3(cdiv(M, kTileM), cdiv(D, 256), zV), gV, pp, b.err, st));
+            auto g5 = [&](int z) -> latentam_status {
+                int zz;
+                const tc::GemmGrid g = pixel_split(n, z, &zz);
+                return launch_gemm<PartEpi<256>>(mA, mdF, dim3(cdiv(M, kTileM), cdiv(D, 256), zz), g, pp, b.err, st);
+            };
+            int z;
+            LAT_TRY(tuned_split(ctx, n, M, D, 5, zV0, st, g5, &z));
+            LAT_TRY(g5(z));
+            pixel_split(n, z, &zV);
         }
         tc_reduce_parts<<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, n > 0 ? zV : 0, M, D, D, 1.0f, b.coef, a.V,
                                                                   a.V0, a.dV);
@@ -963,7 +1014,15 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
             LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, 64));
             LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, 64));
             PartParams pp{M, BNq, BNq, b.part};
-            LAT_TRY(launch_gemm<PartEpi<BNq>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zK), gK, pp, b.err, st));
+            auto g6 = [&](int z) -> latentam_status {
+                int zz;
+                const tc::GemmGrid g = pixel_split(n, z, &zz);
+                return launch_gemm<PartEpi<BNq>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zz), g, pp, b.err, st);
+            };
+            int z;
+            LAT_TRY(tuned_split(ctx, n, M, D, 6, zK0, st, g6, &z));
+            LAT_TRY(g6(z));
+            pixel_split(n, z, &zK);
         }
         tc_reduce_parts<<<cdiv((int64_t)M * d, 32), 256, 0, st>>>(b.part, n > 0 ? zK : 0, M, BNq, d, a.c, nullptr,
                                                                   nullptr, nullptr, a.dK);

@@ -97,6 +97,13 @@ struct latentam_ctx {
     cudaStream_t cap_stream;
     int* step_dev;
     lat::GraphCache* graphs;
+    // autotuned split factors of the pixel reductions (see latentam_autotune_enable)
+    int autotune;
+    struct TuneEntry {
+        int64_t n;
+        int M, D, which, z;
+    } tune[32];
+    int tune_used, tune_next;
 };
 
 namespace lat {

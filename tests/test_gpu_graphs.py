@@ -84,3 +84,21 @@ def test_batch_graph_replays_match_plain_launches(api, prec):
         assert np.linalg.norm(b[k] - a[k]) / np.linalg.norm(a[k]) <= tol / 10, k
     assert np.linalg.norm(fb - fa) / np.linalg.norm(fa) <= tol / 10
     np.testing.assert_allclose(lb, la, rtol=tol)
+
+
+def test_autotuned_splits_change_only_summation_order(api):
+    from workloads import room_scene
+    s = room_scene(4, n=60_000, width=160, height=120, fx=131.25)
+    out = []
+    for tune in (False, True):
+        ctx = api.Context(0)
+        ctx.autotune(tune)
+        Q = torch.randn((s.camera.n_pixels, s.d), device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        K, V = (torch.as_tensor(x, device="cuda") for x in (s.K, s.V))
+        F = torch.as_tensor(s.F, device="cuda").to(torch.bfloat16)
+        mask = torch.as_tensor(s.mask, device="cuda")
+        res = [api.decode_loss_bwd(ctx, Q, K, V, V, F, mask, precision=api.BF16) for _ in range(2)]
+        out.append([t.cpu().numpy() for t in res[-1]])
+        ctx.close()
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6 * np.abs(a).max())
