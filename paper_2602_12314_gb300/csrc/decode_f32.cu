@@ -90,7 +90,9 @@ __global__ void trust_region_kernel(const float* __restrict__ V, const float* __
 
 // ---- rows kernel: S, softmax, Fhat, loss coefficients, dFhat ---------------------------
 // smem: sA[kRows][M] | sKt[d][kAtomChunk + 1] | sQ[kRows][d] | stats
-template <int DQ, bool TRAIN>
+// MODE 0: Fhat only (inference); 1: the whole row pass of the loss; 2: S and the softmax only
+// (A and its row statistics), for the tiled path.
+template <int DQ, int MODE>
 __global__ void __launch_bounds__(kThreads) dec_rows_fwd(const float* __restrict__ Q, int64_t n, const float* __restrict__ K,
                                                           const float* __restrict__ V, int M, int D, float c,
                                                           const void* __restrict__ F, latentam_dtype F_dtype,
@@ -162,13 +164,15 @@ __global__ void __launch_bounds__(kThreads) dec_rows_fwd(const float* __restrict
         for (int j = lane; j < M; j += 32) {
             const float v = a[j] * il;
             a[j] = v;
-            if (TRAIN && p < n) A_out[p * M + j] = v;
+            if (MODE >= 1 && p < n) A_out[p * M + j] = v;
         }
         if (lane == 0 && stats_out && p < n) {
             stats_out[2 * p] = m;
             stats_out[2 * p + 1] = l;
         }
     }
+    if (MODE == 2) return;
+    constexpr bool TRAIN = MODE == 1;
     __syncthreads();
     // Fhat = A V in column chunks; thread owns rows 4 warp + r, columns c0 + 4 lane + 128 g
     float pdot[4] = {0.f, 0.f, 0.f, 0.f}, pnh[4] = {0.f, 0.f, 0.f, 0.f}, pnf[4] = {0.f, 0.f, 0.f, 0.f},
@@ -445,16 +449,319 @@ __global__ void finalize_loss(const double* __restrict__ acc, int D, latentam_lo
     parts[4] = nv;
 }
 
+// ---- register-tiled FP32 GEMM (CUDA cores) --------------------------------------------------
+//
+// C (128 x 128 tile) = sum_k A(m, k) B(k, n) over one K split (blockIdx.z), 256 threads with an
+// 8 x 8 register tile each (rows ty*4 + {0..3} and 64 + ty*4 + {0..3}, likewise the columns),
+// operands staged through double-buffered shared memory 16 K-steps at a time.  A is read from a
+// matrix stored with k contiguous (A_KM) or m contiguous; B with k contiguous (B_KM) or n
+// contiguous.  The epilogue receives the 8 x 8 accumulator.
+
+constexpr int kGM = 128, kGN = 128, kGK = 16, kGPad = 4;
+
+// Row-major source matrix X (row stride ld); four consecutive elements of a row at a time.
+struct PlainSrc {
+    const float* X;
+    int64_t ld, rows, cols;
+    __device__ __forceinline__ float4 load4(int64_t r, int64_t c) const {
+        if (r >= rows || c >= cols) return make_float4(0.f, 0.f, 0.f, 0.f);
+        return *reinterpret_cast<const float4*>(X + r * ld + c);
+    }
+};
+
+// dL/dFhat (n x D) formed on load: a_p Fhat_p + b_p F_p with a_p = coef[4p], b_p = coef[4p+1].
+struct DFhatSrc {
+    const float* Fh;
+    const void* F;
+    latentam_dtype F_dtype;
+    const float* coef;
+    int64_t rows, cols;  // n, D
+    __device__ __forceinline__ float4 load4(int64_t r, int64_t c) const {
+        if (r >= rows || c >= cols) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const float a = coef[4 * r], b = coef[4 * r + 1];
+        const float4 h = *reinterpret_cast<const float4*>(Fh + r * cols + c);
+        const float4 f = load_target4(F, F_dtype, (size_t)((r * cols + c) / 4));
+        return make_float4(a * h.x + b * f.x, a * h.y + b * f.y, a * h.z + b * f.z, a * h.w + b * f.w);
+    }
+};
+
+template <bool A_KM, bool B_KM, class SrcA, class SrcB, class Epi>
+__global__ void __launch_bounds__(256, 2) sgemm_tile(SrcA sa, SrcB sb, int64_t m_ext, int64_t n_ext, int64_t k_ext,
+                                                     int64_t k_per_split, typename Epi::Params ep) {
+    __shared__ __align__(16) float sA[2][kGK][kGM + kGPad];
+    __shared__ __align__(16) float sB[2][kGK][kGN + kGPad];
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    const int64_t m0 = (int64_t)blockIdx.x * kGM, n0 = (int64_t)blockIdx.y * kGN;
+    const int64_t kb = (int64_t)blockIdx.z * k_per_split;
+    const int64_t ke = min(k_ext, kb + k_per_split);
+    float4 ra[2], rb[2];
+    // global -> registers for the K slice starting at k0
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int e = t + 256 * i;
+            if (A_KM) {
+                const int mm = e >> 2, kq = (e & 3) * 4;
+                ra[i] = (k0 + kq < ke) ? sa.load4(m0 + mm, k0 + kq) : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const int kk = e >> 5, mq = (e & 31) * 4;
+                ra[i] = (k0 + kk < ke) ? sa.load4(k0 + kk, m0 + mq) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (B_KM) {
+                const int nn = e >> 2, kq = (e & 3) * 4;
+                rb[i] = (k0 + kq < ke) ? sb.load4(n0 + nn, k0 + kq) : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const int kk = e >> 5, nq = (e & 31) * 4;
+                rb[i] = (k0 + kk < ke) ? sb.load4(k0 + kk, n0 + nq) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+    // registers -> shared buffer `buf`
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int e = t + 256 * i;
+            if (A_KM) {
+                const int mm = e >> 2, kq = (e & 3) * 4;
+                sA[buf][kq][mm] = ra[i].x;
+                sA[buf][kq + 1][mm] = ra[i].y;
+                sA[buf][kq + 2][mm] = ra[i].z;
+                sA[buf][kq + 3][mm] = ra[i].w;
+            } else {
+                *reinterpret_cast<float4*>(&sA[buf][e >> 5][(e & 31) * 4]) = ra[i];
+            }
+            if (B_KM) {
+                const int nn = e >> 2, kq = (e & 3) * 4;
+                sB[buf][kq][nn] = rb[i].x;
+                sB[buf][kq + 1][nn] = rb[i].y;
+                sB[buf][kq + 2][nn] = rb[i].z;
+                sB[buf][kq + 3][nn] = rb[i].w;
+            } else {
+                *reinterpret_cast<float4*>(&sB[buf][e >> 5][(e & 31) * 4]) = rb[i];
+            }
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    int buf = 0;
+    if (kb < ke) {
+        fetch(kb);
+        stash(0);
+    }
+    __syncthreads();
+    for (int64_t k0 = kb; k0 < ke; k0 += kGK) {
+        const bool more = k0 + kGK < ke;
+        if (more) fetch(k0 + kGK);
+#pragma unroll
+        for (int k = 0; k < kGK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&sA[buf][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sA[buf][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&sB[buf][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&sB[buf][k][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        if (more) stash(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+    Epi::store(ep, m0, n0, ty, tx, acc, m_ext, n_ext, (int)blockIdx.z);
+}
+
+__device__ __forceinline__ int64_t tile_row(int64_t m0, int ty, int i) { return m0 + (i < 4 ? ty * 4 + i : 60 + ty * 4 + i); }
+__device__ __forceinline__ int64_t tile_col(int64_t n0, int tx) { return n0 + tx * 4; }  // and + 64
+
+// Fhat tile: stored; with `stats`, the per-row partial sums <Fhat,F>, |Fhat|^2, |F|^2,
+// |Fhat - F|^2 over the tile's 128 columns go to stats[(p * tiles + column tile) * 4 ...]
+// (summed in a fixed order later: the result does not depend on the order the tiles run in).
+struct FhatTileEpi {
+    struct Params {
+        float* Fh;
+        int64_t D;
+        const void* F;
+        latentam_dtype F_dtype;
+        float* stats;
+    };
+    static __device__ __forceinline__ void store(const Params& p, int64_t m0, int64_t n0, int ty, int tx,
+                                                 float (&acc)[8][8], int64_t m_ext, int64_t n_ext, int) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t m = tile_row(m0, ty, i);
+            float s[4] = {0.f, 0.f, 0.f, 0.f};
+            if (m < m_ext) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t c = tile_col(n0, tx) + 64 * h;
+                    if (c >= n_ext) continue;
+                    const float4 v = make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+                    *reinterpret_cast<float4*>(p.Fh + m * p.D + c) = v;
+                    if (p.stats) {
+                        const float4 f = load_target4(p.F, p.F_dtype, (size_t)((m * p.D + c) / 4));
+                        const float hv[4] = {v.x, v.y, v.z, v.w}, fv[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            s[0] += hv[q] * fv[q];
+                            s[1] += hv[q] * hv[q];
+                            s[2] += fv[q] * fv[q];
+                            const float e = hv[q] - fv[q];
+                            s[3] += e * e;
+                        }
+                    }
+                }
+            }
+            if (p.stats) {
+                // the 16 threads of one tile row are 16 consecutive lanes
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+                if (tx == 0 && m < m_ext) {
+                    const int64_t tiles = (p.D + kGN - 1) / kGN;
+                    *reinterpret_cast<float4*>(p.stats + (m * tiles + n0 / kGN) * 4) = make_float4(s[0], s[1], s[2], s[3]);
+                }
+            }
+        }
+    }
+};
+
+// dS tile: dS = A (dA - <A, dA>_p) with <A, dA>_p = coef[4p + 2]; A and dS are n x M.
+struct DsTileEpi {
+    struct Params {
+        const float* A;
+        const float* coef;
+        float* dS;
+        int64_t M;
+    };
+    static __device__ __forceinline__ void store(const Params& p, int64_t m0, int64_t n0, int ty, int tx,
+                                                 float (&acc)[8][8], int64_t m_ext, int64_t n_ext, int) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t m = tile_row(m0, ty, i);
+            if (m >= m_ext) continue;
+            const float rd = p.coef[4 * m + 2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t c = tile_col(n0, tx) + 64 * h;
+                if (c >= n_ext) continue;
+                const float4 a = *reinterpret_cast<const float4*>(p.A + m * p.M + c);
+                *reinterpret_cast<float4*>(p.dS + m * p.M + c) =
+                    make_float4(a.x * (acc[i][4 * h] - rd), a.y * (acc[i][4 * h + 1] - rd), a.z * (acc[i][4 * h + 2] - rd),
+                                a.w * (acc[i][4 * h + 3] - rd));
+            }
+        }
+    }
+};
+
+// Plain scaled store C[m][n] = scale * acc into a row-major (ld) matrix, split z at offset
+// z * split_stride (the partial sums of a split-K product, or dQ).
+struct StoreTileEpi {
+    struct Params {
+        float* C;
+        int64_t ld, split_stride;
+        float scale;
+    };
+    static __device__ __forceinline__ void store(const Params& p, int64_t m0, int64_t n0, int ty, int tx,
+                                                 float (&acc)[8][8], int64_t m_ext, int64_t n_ext, int z) {
+        float* C = p.C + (int64_t)z * p.split_stride;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t m = tile_row(m0, ty, i);
+            if (m >= m_ext) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t c = tile_col(n0, tx) + 64 * h;
+                if (c >= n_ext) continue;
+                *reinterpret_cast<float4*>(C + m * p.ld + c) =
+                    make_float4(p.scale * acc[i][4 * h], p.scale * acc[i][4 * h + 1], p.scale * acc[i][4 * h + 2],
+                                p.scale * acc[i][4 * h + 3]);
+            }
+        }
+    }
+};
+
+// Per-pixel coefficients of dL/dFhat from the row sums (a_p, b_p, <A_p, dA_p>, cos_p into
+// coef) and the frame's loss sums (FP64, one atomic pair per warp).
+__global__ void __launch_bounds__(256) coef_rows(const float* __restrict__ stats, int64_t n, int D,
+                                                 const uint8_t* __restrict__ mask, latentam_loss_cfg cfg,
+                                                 double* __restrict__ acc, float* __restrict__ coef) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float lc = 0.f, le = 0.f;
+    if (p < n) {
+        const int tiles = (D + kGN - 1) / kGN;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < tiles; ++k) {  // column tiles in order
+            const float4 u = *reinterpret_cast<const float4*>(stats + ((int64_t)p * tiles + k) * 4);
+            s.x += u.x, s.y += u.y, s.z += u.z, s.w += u.w;
+        }
+        const float dot = s.x, nh2 = s.y, nf2 = s.z, e2 = s.w;
+        const bool valid = mask == nullptr || mask[p] != 0;
+        const float nv = (float)acc[3];
+        const float scale = nv > 0.f ? cfg.lambda_f / nv : 0.f;
+        const float den = sqrtf(nh2) * sqrtf(nf2);
+        const float cs = dot / fmaxf(den, 1e-8f);
+        float a = 0.f, b = 0.f;
+        if (valid) {
+            lc = 1.0f - cs;
+            le = e2;
+            const float l2c = 2.0f * cfg.lambda_2 / (float)D;
+            if (den > 1e-8f) {
+                a = scale * (cfg.lambda_cos * cs / nh2 + l2c);
+                b = scale * (-cfg.lambda_cos / den - l2c);
+            } else {
+                a = scale * l2c;
+                b = scale * (-cfg.lambda_cos / 1e-8f - l2c);
+            }
+        }
+        *reinterpret_cast<float4*>(coef + 4 * p) = make_float4(a, b, a * nh2 + b * dot, cs);
+    }
+    lc = warp_sum(lc);
+    le = warp_sum(le);
+    if ((threadIdx.x & 31) == 0 && (lc != 0.f || le != 0.f)) {
+        atomicAdd(&acc[0], (double)lc);
+        atomicAdd(&acc[1], (double)le);
+    }
+}
+
+// *z_out (nullable) receives the number of K splits launched.
+template <bool A_KM, bool B_KM, class SrcA, class SrcB, class Epi>
+latentam_status launch_sgemm(const SrcA& a, const SrcB& b, int64_t m_ext, int64_t n_ext, int64_t k_ext, int splits,
+                             const typename Epi::Params& ep, cudaStream_t st, int* z_out = nullptr) {
+    if (z_out) *z_out = 0;
+    if (m_ext <= 0 || n_ext <= 0 || k_ext <= 0) return LATENTAM_OK;
+    const int64_t kps = ((k_ext + splits - 1) / splits + kGK - 1) / kGK * kGK;
+    const int z = (int)std::max<int64_t>(1, (k_ext + kps - 1) / std::max<int64_t>(kps, 1));
+    if (z_out) *z_out = z;
+    dim3 grid((unsigned)((m_ext + kGM - 1) / kGM), (unsigned)((n_ext + kGN - 1) / kGN), (unsigned)z);
+    sgemm_tile<A_KM, B_KM, SrcA, SrcB, Epi><<<grid, 256, 0, st>>>(a, b, m_ext, n_ext, k_ext, kps, ep);
+    LAT_CHECK_LAUNCH("sgemm_tile");
+    return LATENTAM_OK;
+}
+
+// Number of K splits of a pixel reduction: about two CTAs per SM over the output tiles.
+int tile_splits(int num_sms, int64_t m_ext, int64_t n_ext, int64_t k_ext) {
+    const int64_t tiles = ((m_ext + kGM - 1) / kGM) * ((n_ext + kGN - 1) / kGN);
+    int64_t z = std::max<int64_t>(1, (2 * num_sms + tiles - 1) / tiles);
+    z = std::min<int64_t>(z, std::max<int64_t>(1, k_ext / 256));
+    return (int)z;
+}
+
 size_t rows_fwd_smem(int d, int M) { return sizeof(float) * ((size_t)kRows * M + (size_t)d * (kAtomChunk + 1) + (size_t)kRows * d); }
 size_t rows_bwd_smem(int M) { return sizeof(float) * ((size_t)kRows * M + (size_t)kAtomChunk * 33 + (size_t)kRows * 33); }
 
-template <int DQ, bool TRAIN>
+template <int DQ, int MODE>
 latentam_status launch_rows_fwd(const float* Q, int64_t n, const float* K, const float* V, int M, int D, float c,
                                 const void* F, latentam_dtype F_dtype, const uint8_t* mask,
                                 const latentam_loss_cfg& cfg, double* acc, float* A_out, float* Fh, float* row,
                                 float* stats, cudaStream_t st) {
     const size_t smem = rows_fwd_smem(DQ, M);
-    auto kern = dec_rows_fwd<DQ, TRAIN>;
+    auto kern = dec_rows_fwd<DQ, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "dec_rows_fwd smem attribute");
     const unsigned blocks = (unsigned)((n + kRows - 1) / kRows);
@@ -501,17 +808,23 @@ latentam_status atb(latentam_ctx* ctx, const float* X, int ldx, int nx, const fl
     return LATENTAM_OK;
 }
 
+// The FP32 form: S and the softmax in the row kernel, then register-tiled GEMMs:
+//   Fhat = A V (+ per-row loss sums)  ->  per-pixel coefficients a_p, b_p  ->
+//   dA = dFhat V^T (dFhat = a_p Fhat + b_p F formed on load) -> dS = A (dA - <A, dA>),
+//   dQ = c dS K,  dV = A^T dFhat (split over pixels),  dK = c dS^T Q (split over pixels).
 template <int DQ>
 latentam_status loss_bwd_t(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
-    const int64_t n = a.n;
+    const int64_t n = a.n, nn = std::max<int64_t>(n, 1);
     const int M = a.M, D = a.D;
     double* acc = static_cast<double*>(ws(ctx, WS_LOSS, sizeof(double) * 8));
-    float* A = static_cast<float*>(ws(ctx, WS_DEC_A, sizeof(float) * (size_t)std::max<int64_t>(n, 1) * M));
-    float* dF = static_cast<float*>(ws(ctx, WS_DEC_DF, sizeof(float) * (size_t)std::max<int64_t>(n, 1) * D));
-    float* dS = static_cast<float*>(ws(ctx, WS_DEC_DS, sizeof(float) * (size_t)std::max<int64_t>(n, 1) * M));
-    float* row = static_cast<float*>(ws(ctx, WS_DEC_ROW, sizeof(float) * 4 * (size_t)std::max<int64_t>(n, 1)));
-    float* coef = static_cast<float*>(ws(ctx, WS_DEC_AUX3, sizeof(float) * (size_t)M));
-    if (!acc || !A || !dF || !dS || !row || !coef) return LATENTAM_ERR_OUT_OF_MEMORY;
+    float* A = static_cast<float*>(ws(ctx, WS_DEC_A, sizeof(float) * (size_t)nn * M));
+    float* Fh = static_cast<float*>(ws(ctx, WS_DEC_DF, sizeof(float) * (size_t)nn * D));
+    float* dS = static_cast<float*>(ws(ctx, WS_DEC_DS, sizeof(float) * (size_t)nn * M));
+    float* coef = static_cast<float*>(ws(ctx, WS_DEC_ROW, sizeof(float) * 4 * (size_t)nn));
+    const int ctiles = (D + kGN - 1) / kGN;
+    float* stats = static_cast<float*>(ws(ctx, WS_DEC_AUX, sizeof(float) * 4 * (size_t)nn * ctiles));
+    float* trc = static_cast<float*>(ws(ctx, WS_DEC_AUX3, sizeof(float) * (size_t)M));
+    if (!acc || !A || !Fh || !dS || !coef || !stats || !trc) return LATENTAM_ERR_OUT_OF_MEMORY;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 8, st);
     if (e != cudaSuccess) return cuda_error(e, "memset loss");
     if (n > 0) {
@@ -520,16 +833,49 @@ latentam_status loss_bwd_t(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t 
         LAT_CHECK_LAUNCH("count_mask_kernel");
     }
     trust_region_kernel<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(a.V, a.V0, M, D, a.cfg.delta,
-                                                                 a.cfg.lambda_f * a.cfg.lambda_D, coef, acc);
+                                                                 a.cfg.lambda_f * a.cfg.lambda_D, trc, acc);
     LAT_CHECK_LAUNCH("trust_region_kernel");
+    const PlainSrc Asrc{A, M, n, M}, Vsrc{a.V, D, M, D}, dSsrc{dS, M, n, M};
+    const DFhatSrc dFsrc{Fh, a.F, a.F_dtype, coef, n, D};
     if (n > 0) {
-        LAT_TRY((launch_rows_fwd<DQ, true>(a.Q, n, a.K, a.V, M, D, a.c, a.F, a.F_dtype, a.mask, a.cfg, acc, A, dF, row,
-                                           nullptr, st)));
+        LAT_TRY((launch_rows_fwd<DQ, 2>(a.Q, n, a.K, a.V, M, D, a.c, nullptr, LATENTAM_DTYPE_F32, nullptr, a.cfg,
+                                        nullptr, A, nullptr, nullptr, nullptr, st)));
+        LAT_TRY((launch_sgemm<true, false, PlainSrc, PlainSrc, FhatTileEpi>(
+            Asrc, Vsrc, n, D, M, 1, FhatTileEpi::Params{Fh, D, a.F, a.F_dtype, stats}, st)));
+        coef_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(stats, n, D, a.mask, a.cfg, acc, coef);
+        LAT_CHECK_LAUNCH("coef_rows");
         if (a.dQ || a.dK)
-            LAT_TRY(launch_rows_bwd<DQ>(dF, A, row, a.K, a.V, n, M, D, a.c, dS, a.dQ, st));
+            LAT_TRY((launch_sgemm<true, true, DFhatSrc, PlainSrc, DsTileEpi>(dFsrc, Vsrc, n, M, D, 1,
+                                                                             DsTileEpi::Params{A, coef, dS, M}, st)));
+        if (a.dQ) {
+            const PlainSrc Ksrc{a.K, DQ, M, DQ};
+            LAT_TRY((launch_sgemm<true, false, PlainSrc, PlainSrc, StoreTileEpi>(
+                dSsrc, Ksrc, n, DQ, M, 1, StoreTileEpi::Params{a.dQ, DQ, 0, a.c}, st)));
+        }
     }
-    if (a.dV) LAT_TRY(atb(ctx, A, M, M, dF, D, D, n, 1.0f, coef, a.V, a.V0, a.dV, st));
-    if (a.dK) LAT_TRY(atb(ctx, dS, M, M, a.Q, DQ, DQ, n, a.c, nullptr, nullptr, nullptr, a.dK, st));
+    if (a.dV) {
+        const int z0 = n > 0 ? tile_splits(ctx->num_sms, M, D, n) : 1;
+        float* part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * (size_t)z0 * M * D));
+        if (!part) return LATENTAM_ERR_OUT_OF_MEMORY;
+        int z = 0;
+        LAT_TRY((launch_sgemm<false, false, PlainSrc, DFhatSrc, StoreTileEpi>(
+            Asrc, dFsrc, M, D, n, z0, StoreTileEpi::Params{part, D, (int64_t)M * D, 1.0f}, st, &z)));
+        reduce_splits<<<(unsigned)(((int64_t)M * D + 255) / 256), 256, 0, st>>>(part, z, M, D, 1.0f, trc, a.V, a.V0,
+                                                                                a.dV);
+        LAT_CHECK_LAUNCH("reduce_splits");
+    }
+    if (a.dK) {
+        const int z0 = n > 0 ? tile_splits(ctx->num_sms, M, DQ, n) : 1;
+        float* part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * (size_t)z0 * M * DQ));
+        if (!part) return LATENTAM_ERR_OUT_OF_MEMORY;
+        const PlainSrc Qsrc{a.Q, DQ, n, DQ};
+        int z = 0;
+        LAT_TRY((launch_sgemm<false, false, PlainSrc, PlainSrc, StoreTileEpi>(
+            dSsrc, Qsrc, M, DQ, n, z0, StoreTileEpi::Params{part, DQ, (int64_t)M * DQ, 1.0f}, st, &z)));
+        reduce_splits<<<(unsigned)(((int64_t)M * DQ + 255) / 256), 256, 0, st>>>(part, z, M, DQ, a.c, nullptr,
+                                                                                 nullptr, nullptr, a.dK);
+        LAT_CHECK_LAUNCH("reduce_splits");
+    }
     finalize_loss<<<1, 1, 0, st>>>(acc, D, a.cfg, a.loss_parts);
     LAT_CHECK_LAUNCH("finalize_loss");
     return LATENTAM_OK;
@@ -539,14 +885,15 @@ template <int DQ>
 latentam_status decode_fwd_t(latentam_ctx* ctx, const float* Q, int64_t n, const float* K, const float* V, int M,
                              int D, float c, float* F_hat, float* row_stats, cudaStream_t st) {
     if (n == 0) return LATENTAM_OK;
-    float* Fh = F_hat;
-    if (!Fh) {
-        Fh = static_cast<float*>(ws(ctx, WS_DEC_DF, sizeof(float) * (size_t)n * D));
-        if (!Fh) return LATENTAM_ERR_OUT_OF_MEMORY;
-    }
+    float* A = static_cast<float*>(ws(ctx, WS_DEC_A, sizeof(float) * (size_t)n * M));
+    if (!A) return LATENTAM_ERR_OUT_OF_MEMORY;
     latentam_loss_cfg cfg{};
-    return launch_rows_fwd<DQ, false>(Q, n, K, V, M, D, c, nullptr, LATENTAM_DTYPE_F32, nullptr, cfg, nullptr, nullptr,
-                                      Fh, nullptr, row_stats, st);
+    LAT_TRY((launch_rows_fwd<DQ, 2>(Q, n, K, V, M, D, c, nullptr, LATENTAM_DTYPE_F32, nullptr, cfg, nullptr, A,
+                                    nullptr, nullptr, row_stats, st)));
+    if (!F_hat) return LATENTAM_OK;
+    const PlainSrc Asrc{A, M, n, M}, Vsrc{V, D, M, D};
+    return launch_sgemm<true, false, PlainSrc, PlainSrc, FhatTileEpi>(
+        Asrc, Vsrc, n, D, M, 1, FhatTileEpi::Params{F_hat, D, nullptr, LATENTAM_DTYPE_F32, nullptr}, st);
 }
 
 // ---- allocation-free variant -------------------------------------------------------------
@@ -668,7 +1015,7 @@ latentam_status loss_bwd_noalloc_t(latentam_ctx* ctx, const DecodeArgs& a, cudaS
                                                                  a.cfg.lambda_f * a.cfg.lambda_D, coef, acc);
     LAT_CHECK_LAUNCH("trust_region_kernel");
     if (n > 0) {
-        LAT_TRY((launch_rows_fwd<DQ, true>(a.Q, n, a.K, a.V, M, D, a.c, a.F, a.F_dtype, a.mask, a.cfg, acc, A, dF, row,
+        LAT_TRY((launch_rows_fwd<DQ, 1>(a.Q, n, a.K, a.V, M, D, a.c, a.F, a.F_dtype, a.mask, a.cfg, acc, A, dF, row,
                                            nullptr, st)));
         if (a.dQ || a.dK)
             LAT_TRY(launch_rows_bwd<DQ>(dF, A, row, a.K, a.V, n, M, D, a.c, dS, a.dQ, st));
