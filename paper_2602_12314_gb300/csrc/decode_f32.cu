@@ -491,7 +491,9 @@ __global__ void __launch_bounds__(256, 2) sgemm_tile(SrcA sa, SrcB sb, int64_t m
     __shared__ __align__(16) float sA[2][kGK][kGM + kGPad];
     __shared__ __align__(16) float sB[2][kGK][kGN + kGPad];
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
-    const int64_t m0 = (int64_t)blockIdx.x * kGM, n0 = (int64_t)blockIdx.y * kGN;
+    // x: column tile, y: row tile (the column tiles of a row tile run together and share its
+    // A rows in L2)
+    const int64_t m0 = (int64_t)blockIdx.y * kGM, n0 = (int64_t)blockIdx.x * kGN;
     const int64_t kb = (int64_t)blockIdx.z * k_per_split;
     const int64_t ke = min(k_ext, kb + k_per_split);
     float4 ra[2], rb[2];
@@ -573,6 +575,94 @@ __global__ void __launch_bounds__(256, 2) sgemm_tile(SrcA sa, SrcB sb, int64_t m
         buf ^= 1;
     }
     Epi::store(ep, m0, n0, ty, tx, acc, m_ext, n_ext, (int)blockIdx.z);
+}
+
+// Narrow form for products with few columns (dQ = c dS K and dK = c dS^T Q, n <= 64): 128 x 32
+// tiles, 256 threads with 4 x 4 each; B is read n-contiguous.  C[m][n] = scale * acc is stored
+// at C + z * split_stride (row stride ld).
+template <bool A_KM>
+__global__ void __launch_bounds__(256) sgemm_narrow(PlainSrc sa, PlainSrc sb, int64_t m_ext, int64_t n_ext,
+                                                    int64_t k_ext, int64_t k_per_split, float* __restrict__ C,
+                                                    int64_t ld, int64_t split_stride, float scale) {
+    constexpr int TN = 32;
+    __shared__ __align__(16) float sA[2][kGK][kGM + kGPad];
+    __shared__ __align__(16) float sB[2][kGK][TN + kGPad];
+    const int t = threadIdx.x, ty = t >> 3, tx = t & 7;
+    const int64_t m0 = (int64_t)blockIdx.y * kGM, n0 = (int64_t)blockIdx.x * TN;
+    const int64_t kb = (int64_t)blockIdx.z * k_per_split;
+    const int64_t ke = min(k_ext, kb + k_per_split);
+    float4 ra[2], rb = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int e = t + 256 * i;
+            if (A_KM) {
+                const int mm = e >> 2, kq = (e & 3) * 4;
+                ra[i] = (k0 + kq < ke) ? sa.load4(m0 + mm, k0 + kq) : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const int kk = e >> 5, mq = (e & 31) * 4;
+                ra[i] = (k0 + kk < ke) ? sa.load4(k0 + kk, m0 + mq) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        if (t < kGK * TN / 4) {
+            const int kk = t >> 3, nq = (t & 7) * 4;
+            rb = (k0 + kk < ke) ? sb.load4(k0 + kk, n0 + nq) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int e = t + 256 * i;
+            if (A_KM) {
+                const int mm = e >> 2, kq = (e & 3) * 4;
+                sA[buf][kq][mm] = ra[i].x;
+                sA[buf][kq + 1][mm] = ra[i].y;
+                sA[buf][kq + 2][mm] = ra[i].z;
+                sA[buf][kq + 3][mm] = ra[i].w;
+            } else {
+                *reinterpret_cast<float4*>(&sA[buf][e >> 5][(e & 31) * 4]) = ra[i];
+            }
+        }
+        if (t < kGK * TN / 4) *reinterpret_cast<float4*>(&sB[buf][t >> 3][(t & 7) * 4]) = rb;
+    };
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    int buf = 0;
+    if (kb < ke) {
+        fetch(kb);
+        stash(0);
+    }
+    __syncthreads();
+    for (int64_t k0 = kb; k0 < ke; k0 += kGK) {
+        const bool more = k0 + kGK < ke;
+        if (more) fetch(k0 + kGK);
+#pragma unroll
+        for (int k = 0; k < kGK; ++k) {
+            const float4 a = *reinterpret_cast<const float4*>(&sA[buf][k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&sB[buf][k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        if (more) stash(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+    float* Cz = C + (int64_t)blockIdx.z * split_stride;
+    const int64_t c = n0 + tx * 4;
+    if (c >= n_ext) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t m = m0 + ty * 4 + i;
+        if (m < m_ext)
+            *reinterpret_cast<float4*>(Cz + m * ld + c) =
+                make_float4(scale * acc[i][0], scale * acc[i][1], scale * acc[i][2], scale * acc[i][3]);
+    }
 }
 
 __device__ __forceinline__ int64_t tile_row(int64_t m0, int ty, int i) { return m0 + (i < 4 ? ty * 4 + i : 60 + ty * 4 + i); }
@@ -738,9 +828,24 @@ latentam_status launch_sgemm(const SrcA& a, const SrcB& b, int64_t m_ext, int64_
     const int64_t kps = ((k_ext + splits - 1) / splits + kGK - 1) / kGK * kGK;
     const int z = (int)std::max<int64_t>(1, (k_ext + kps - 1) / std::max<int64_t>(kps, 1));
     if (z_out) *z_out = z;
-    dim3 grid((unsigned)((m_ext + kGM - 1) / kGM), (unsigned)((n_ext + kGN - 1) / kGN), (unsigned)z);
+    dim3 grid((unsigned)((n_ext + kGN - 1) / kGN), (unsigned)((m_ext + kGM - 1) / kGM), (unsigned)z);
     sgemm_tile<A_KM, B_KM, SrcA, SrcB, Epi><<<grid, 256, 0, st>>>(a, b, m_ext, n_ext, k_ext, kps, ep);
     LAT_CHECK_LAUNCH("sgemm_tile");
+    return LATENTAM_OK;
+}
+
+template <bool A_KM>
+latentam_status launch_narrow(const PlainSrc& a, const PlainSrc& b, int64_t m_ext, int64_t n_ext, int64_t k_ext,
+                              int splits, float* C, int64_t ld, int64_t split_stride, float scale, cudaStream_t st,
+                              int* z_out = nullptr) {
+    if (z_out) *z_out = 0;
+    if (m_ext <= 0 || n_ext <= 0 || k_ext <= 0) return LATENTAM_OK;
+    const int64_t kps = ((k_ext + splits - 1) / splits + kGK - 1) / kGK * kGK;
+    const int z = (int)std::max<int64_t>(1, (k_ext + kps - 1) / kps);
+    if (z_out) *z_out = z;
+    dim3 grid((unsigned)((n_ext + 31) / 32), (unsigned)((m_ext + kGM - 1) / kGM), (unsigned)z);
+    sgemm_narrow<A_KM><<<grid, 256, 0, st>>>(a, b, m_ext, n_ext, k_ext, kps, C, ld, split_stride, scale);
+    LAT_CHECK_LAUNCH("sgemm_narrow");
     return LATENTAM_OK;
 }
 
@@ -849,8 +954,7 @@ latentam_status loss_bwd_t(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t 
                                                                              DsTileEpi::Params{A, coef, dS, M}, st)));
         if (a.dQ) {
             const PlainSrc Ksrc{a.K, DQ, M, DQ};
-            LAT_TRY((launch_sgemm<true, false, PlainSrc, PlainSrc, StoreTileEpi>(
-                dSsrc, Ksrc, n, DQ, M, 1, StoreTileEpi::Params{a.dQ, DQ, 0, a.c}, st)));
+            LAT_TRY(launch_narrow<true>(dSsrc, Ksrc, n, DQ, M, 1, a.dQ, DQ, 0, a.c, st));
         }
     }
     if (a.dV) {
@@ -865,13 +969,16 @@ latentam_status loss_bwd_t(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t 
         LAT_CHECK_LAUNCH("reduce_splits");
     }
     if (a.dK) {
-        const int z0 = n > 0 ? tile_splits(ctx->num_sms, M, DQ, n) : 1;
+        // narrow tiles: (M / 128) x (d / 32) of them, so more pixel splits
+        const int64_t ntiles = ((M + kGM - 1) / kGM) * ((DQ + 31) / 32);
+        const int z0 = n > 0 ? (int)std::max<int64_t>(1, std::min<int64_t>((4 * ctx->num_sms + ntiles - 1) / ntiles,
+                                                                            std::max<int64_t>(1, n / 256)))
+                             : 1;
         float* part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * (size_t)z0 * M * DQ));
         if (!part) return LATENTAM_ERR_OUT_OF_MEMORY;
         const PlainSrc Qsrc{a.Q, DQ, n, DQ};
         int z = 0;
-        LAT_TRY((launch_sgemm<false, false, PlainSrc, PlainSrc, StoreTileEpi>(
-            dSsrc, Qsrc, M, DQ, n, z0, StoreTileEpi::Params{part, DQ, (int64_t)M * DQ, 1.0f}, st, &z)));
+        LAT_TRY(launch_narrow<false>(dSsrc, Qsrc, M, DQ, n, z0, part, DQ, (int64_t)M * DQ, 1.0f, st, &z));
         reduce_splits<<<(unsigned)(((int64_t)M * DQ + 255) / 256), 256, 0, st>>>(part, z, M, DQ, a.c, nullptr,
                                                                                  nullptr, nullptr, a.dK);
         LAT_CHECK_LAUNCH("reduce_splits");
