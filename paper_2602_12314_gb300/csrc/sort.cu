@@ -1,7 +1,10 @@
 // Tile binning and sorting of the splats (the depth-ordered lists that Eq. alpha_blending
 // walks, Sec. III-A):
-//   1. stable LSD radix sort of the Gaussians by binary32 depth key (ties keep index order)
-//   2. exclusive scan of tiles-touched in that order -> pair offsets and the pair count P
+//   0. compaction of the visible Gaussians (tiles touched > 0) in index order; the visible
+//      count V and the pair count P are read back together (the one host round trip)
+//   1. stable LSD radix sort of the V visible Gaussians by binary32 depth key (ties keep
+//      index order)
+//   2. exclusive scan of tiles-touched in that order -> pair offsets
 //   3. emission of one (tile, Gaussian) pair per covered tile, in depth order
 //   4. stable radix sort of the pairs on the ceil(log2(tiles)) tile bits only
 //   5. per-tile [start, end) ranges
@@ -177,12 +180,35 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter(const uint32_t* __re
 
 // ---- binning ---------------------------------------------------------------------------
 
-__global__ void depth_keys(int N, const float* __restrict__ depth, const int32_t* __restrict__ tiles,
-                           uint32_t* __restrict__ keys) {
+// flags[i] = (tiles[i] > 0); cnt[1] += sum of tiles (the pair count P).
+__global__ void __launch_bounds__(256) visible_flags(int N, const int32_t* __restrict__ tiles, uint32_t* __restrict__ flags,
+                                                     uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t red[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    // visible Gaussians have depth > z_near > 0, whose binary32 bits order like the values
-    keys[i] = tiles[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
+    const uint32_t tt = i < N ? (uint32_t)max(tiles[i], 0) : 0u;
+    if (i < N) flags[i] = tt > 0 ? 1u : 0u;
+    uint32_t s = tt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t b = 0;
+        for (int w = 0; w < 8; ++w) b += red[w];
+        if (b) atomicAdd(&cnt[1], b);
+    }
+}
+
+// The visible Gaussians in index order with their depth keys (visible Gaussians have
+// depth > z_near > 0, whose binary32 bits order like the values).
+__global__ void depth_keys(int N, const float* __restrict__ depth, const int32_t* __restrict__ tiles,
+                           const uint32_t* __restrict__ vis_off, uint32_t* __restrict__ keys,
+                           uint32_t* __restrict__ ids) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || tiles[i] <= 0) return;
+    const uint32_t o = vis_off[i];
+    keys[o] = __float_as_uint(depth[i]);
+    ids[o] = (uint32_t)i;
 }
 
 __global__ void gather_tiles(int N, const uint32_t* __restrict__ order, const int32_t* __restrict__ tiles,
@@ -294,29 +320,36 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
     if (!dk[0] || !dk[1] || !dv[0] || !dv[1] || !off || !cnt) return LATENTAM_ERR_OUT_OF_MEMORY;
     const int threads = 256;
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
-    // 1. Gaussians by depth key (index order kept among equal keys)
-    depth_keys<<<blocks, threads, 0, st>>>(N, proj.depth, proj.tiles_touched, dk[0]);
-    LAT_CHECK_LAUNCH("depth_keys");
-    int r = 0;
-    LAT_TRY(radix_sort_pairs(ctx, dk, dv, true, N, 32, &r, st));
-    const uint32_t* order = dv[r];
-    // 2. pair offsets in depth order
-    uint32_t* counts = dk[1 - r];
-    gather_tiles<<<blocks, threads, 0, st>>>(N, order, proj.tiles_touched, counts);
-    LAT_CHECK_LAUNCH("gather_tiles");
-    LAT_TRY(scan_exclusive_u32(ctx, counts, off, N, cnt, st));
-    uint32_t P32 = 0;
-    e = cudaMemcpyAsync(&P32, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_error(e, "read pair count");
+    // 0. visible Gaussians (flags -> offsets, count V into cnt[0]) and the pair count P (cnt[1])
+    e = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return cuda_error(e, "memset counters");
+    visible_flags<<<blocks, threads, 0, st>>>(N, proj.tiles_touched, dv[1], cnt);
+    LAT_CHECK_LAUNCH("visible_flags");
+    LAT_TRY(scan_exclusive_u32(ctx, dv[1], off, N, cnt, st));
+    uint32_t VP[2] = {0, 0};
+    e = cudaMemcpyAsync(VP, cnt, sizeof(VP), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_error(e, "read visible and pair counts");
     e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_error(e, "sync for pair count");
-    const int64_t P = (int64_t)P32;
+    if (e != cudaSuccess) return cuda_error(e, "sync for the counts");
+    const int64_t V = (int64_t)VP[0], P = (int64_t)VP[1];
     bins->num_pairs = P;
     if (P > bins->capacity) {
         set_error("pair buffer holds %lld pairs, %lld needed", (long long)bins->capacity, (long long)P);
         return LATENTAM_ERR_CAPACITY;
     }
-    if (P == 0) return LATENTAM_OK;
+    if (P == 0 || V == 0) return LATENTAM_OK;
+    // 1. visible Gaussians by depth key (index order kept among equal keys)
+    depth_keys<<<blocks, threads, 0, st>>>(N, proj.depth, proj.tiles_touched, off, dk[0], dv[0]);
+    LAT_CHECK_LAUNCH("depth_keys");
+    int r = 0;
+    LAT_TRY(radix_sort_pairs(ctx, dk, dv, false, V, 32, &r, st));
+    const uint32_t* order = dv[r];
+    // 2. pair offsets in depth order
+    const unsigned vblocks = (unsigned)((V + threads - 1) / threads);
+    uint32_t* counts = dk[1 - r];
+    gather_tiles<<<vblocks, threads, 0, st>>>((int)V, order, proj.tiles_touched, counts);
+    LAT_CHECK_LAUNCH("gather_tiles");
+    LAT_TRY(scan_exclusive_u32(ctx, counts, off, V, nullptr, st));
     // 3. emission in depth order; 4. stable sort on the tile bits.  The depth order stays in
     // its own slot (WS_SORT_V*), the key slots may be regrown: their contents are consumed.
     const size_t pbytes = sizeof(uint32_t) * (size_t)P;
@@ -326,8 +359,8 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
                        static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX2, pbytes))};
     if (!pk[0] || !pk[1] || !pv[0] || !pv[1]) return LATENTAM_ERR_OUT_OF_MEMORY;
     order = static_cast<const uint32_t*>(ctx->slot_ptr[r == 0 ? WS_SORT_V0 : WS_SORT_V1]);
-    emit_pairs<<<blocks, threads, 0, st>>>(N, order, off, reinterpret_cast<const int4*>(proj.rect), cam.tiles_x,
-                                           pk[0], pv[0]);
+    emit_pairs<<<vblocks, threads, 0, st>>>((int)V, order, off, reinterpret_cast<const int4*>(proj.rect), cam.tiles_x,
+                                            pk[0], pv[0]);
     LAT_CHECK_LAUNCH("emit_pairs");
     const int tile_bits = std::max(1, ceil_log2(num_tiles));
     LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, st));
