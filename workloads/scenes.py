@@ -57,6 +57,7 @@ class Scene:
     F: np.ndarray          # (H*W, D) target features, row = y*W + x
     mask: np.ndarray       # (H*W,) uint8, 1 = pixel in the loss set
     camera: Camera
+    labels: np.ndarray | None = None  # (H*W,) int32 region id per pixel (-1 = none), for masks
 
     @property
     def n(self) -> int:
@@ -82,8 +83,11 @@ class Scene:
         c2 = dataclasses.replace(cam, cx=cam.cx - x0, cy=cam.cy - y0, width=w, height=h)
         F = self.F.reshape(cam.height, cam.width, -1)[y0:y0 + h, x0:x0 + w].reshape(w * h, -1)
         m = self.mask.reshape(cam.height, cam.width)[y0:y0 + h, x0:x0 + w].reshape(-1)
+        lab = None
+        if self.labels is not None:
+            lab = np.ascontiguousarray(self.labels.reshape(cam.height, cam.width)[y0:y0 + h, x0:x0 + w].reshape(-1))
         return dataclasses.replace(self, name=name or f"{self.name}[crop {x0},{y0} {w}x{h}]",
-                                   camera=c2, F=np.ascontiguousarray(F), mask=np.ascontiguousarray(m))
+                                   camera=c2, F=np.ascontiguousarray(F), mask=np.ascontiguousarray(m), labels=lab)
 
 
 def _f32(a) -> np.ndarray:
@@ -153,9 +157,11 @@ def tiny_scene(seed: int = 0, n: int = 2000, d: int = 16, M: int = 64, D: int = 
             if rng.uniform() < mask_drop:
                 mask[ys, xs] = 0
     F = _normalise_rows(F.reshape(-1, D))
+    yy, xx = np.mgrid[0:height, 0:width]
+    labels = ((yy // 8) * bw + xx // 8).astype(np.int32).reshape(-1)
     return Scene(name=f"tiny(seed={seed},N={n},{width}x{height},d={d},M={M},D={D})",
                  means=means, quats=quats, scales=scales, opacities=opac, f=f, K=K, V=V, V0=V.copy(),
-                 F=_f32(F), mask=mask.reshape(-1), camera=cam)
+                 F=_f32(F), mask=mask.reshape(-1), camera=cam, labels=labels)
 
 
 # ----------------------------------------------------------------------------------------
@@ -281,7 +287,8 @@ def room_scene(seed: int = 0, n: int = 300_000, d: int = 32, M: int = 256, D: in
     F[mask == 0] = 0.0
     return Scene(name=f"room(seed={seed},N={n},{width}x{height},d={d},M={M},D={D})",
                  means=_f32(means), quats=_f32(quats), scales=_f32(scales), opacities=_f32(opac),
-                 f=_f32(f), K=K, V=V, V0=V.copy(), F=_f32(F), mask=mask, camera=cam)
+                 f=_f32(f), K=K, V=V, V0=V.copy(), F=_f32(F), mask=mask, camera=cam,
+                 labels=label.astype(np.int32))
 
 
 def room_views(seed: int = 0, n_views: int = 6, n: int = 300_000, d: int = 32, M: int = 256, D: int = 512,
@@ -315,7 +322,8 @@ def room_views(seed: int = 0, n_views: int = 6, n: int = 300_000, d: int = 32, M
         F = _normalise_rows(F)
         mask = (label >= 0).astype(np.uint8)
         F[mask == 0] = 0.0
-        views.append(dataclasses.replace(base, name=f"{base.name}[view {v}]", camera=cam, F=_f32(F), mask=mask))
+        views.append(dataclasses.replace(base, name=f"{base.name}[view {v}]", camera=cam, F=_f32(F), mask=mask,
+                                         labels=label.astype(np.int32)))
     return views
 
 
