@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define LATENTAM_TILE 16
-#define LATENTAM_ABI_VERSION 1
+#define LATENTAM_ABI_VERSION 2
 
 typedef int32_t latentam_status;
 #define LATENTAM_OK 0
@@ -312,6 +312,32 @@ LATENTAM_API latentam_status latentam_backward(latentam_ctx* ctx, int32_t n, con
                                   latentam_precision prec, double* loss_parts, float* dQ_scratch,
                                   float* df, float* dK, float* dV, latentam_stream stream);
 
+/* ---- mask pooling (SAM-based targets) ------------------------------------------------ */
+
+/* With SAM-based targets the decode's rows are the n valid masks instead of the pixels
+ * (Sec. III-B, the passage after Eq. render_query), and the target of a mask is pooled over
+ * its region.  Reading: the query of mask m is the mean of the rendered per-pixel queries over
+ * the mask, Qm_m = (1/|m|) sum_{p in m} Q_p.
+ *
+ * Masks are CSR lists on the device: mask m owns entries [mask_offsets[m], mask_offsets[m+1])
+ * of mask_pixels (pixel index y*W + x).  Offsets are clamped into [0, n_entries] and a
+ * decreasing pair gives an empty mask; a pixel index outside [0, npix) is skipped and not
+ * counted; masks may overlap and list a pixel several times; an empty mask pools to 0.
+ * Q, Qm, dQm and dQ are row-major float32, 16-byte aligned; d in {16, 32, 64}; S >= 0;
+ * 0 <= n_entries <= INT32_MAX.  All buffers are caller-owned device memory.  The result
+ * does not depend on scheduling (fixed chunking and summation order). */
+LATENTAM_API latentam_status latentam_pool_queries(latentam_ctx* ctx, const float* Q, int64_t npix, int32_t d,
+                                                   const int32_t* mask_offsets, const int32_t* mask_pixels,
+                                                   int64_t n_entries, int32_t S, float* Qm,
+                                                   latentam_stream stream);
+/* Backward of latentam_pool_queries: dQ (npix x d) is overwritten with
+ * dQ_p = sum over the masks m listing p of dQm_m / |m| (zero for pixels in no mask).  Where
+ * masks overlap the sum is taken with atomic adds (order-dependent in the last bits). */
+LATENTAM_API latentam_status latentam_pool_queries_bwd(latentam_ctx* ctx, const float* dQm, int32_t S, int32_t d,
+                                                       const int32_t* mask_offsets, const int32_t* mask_pixels,
+                                                       int64_t n_entries, int64_t npix, float* dQ,
+                                                       latentam_stream stream);
+
 /* ---- optimiser ----------------------------------------------------------------------- */
 
 /* One Adam update of `count` tensors in a single launch: params[i], grads[i], m[i], v[i]
@@ -324,13 +350,21 @@ LATENTAM_API latentam_status latentam_adam(latentam_ctx* ctx, int32_t count, flo
 
 /* ---- the step (Algorithm 1, optimisation stages) ------------------------------------- */
 
-/* One keyframe's state for latentam_step. */
+/* One keyframe's state for latentam_step.  With n_masks > 0 the step is mask-pooled (see
+ * latentam_pool_queries): the rendered queries are pooled per mask before the decode, F holds
+ * one target per mask (n_masks x D) and mask one loss-set flag per mask; the query gradient
+ * flows back to the pixels through the pooling's adjoint.  n_masks == 0 (the zero-initialised
+ * struct) is the per-pixel step. */
 typedef struct {
     latentam_gaussians gaussians;
     latentam_camera camera;
-    const void* F;          /* H*W x D target features */
+    const void* F;          /* H*W x D target features (n_masks x D when mask-pooled) */
     latentam_dtype F_dtype;
-    const uint8_t* mask;    /* H*W loss-set mask, NULL = all pixels */
+    const uint8_t* mask;    /* loss-set flags per pixel (per mask when mask-pooled), NULL = all */
+    const int32_t* mask_offsets;  /* device, n_masks + 1 CSR offsets (mask-pooled only) */
+    const int32_t* mask_pixels;   /* device, n_mask_entries pixel indices (mask-pooled only) */
+    int64_t n_mask_entries;
+    int32_t n_masks;        /* 0 = per-pixel targets */
 } latentam_frame;
 
 /* Learnable state: queries f (N x d) and dictionary K (M x d), V (M x D), the trust-region

@@ -56,8 +56,8 @@ def pool_bwd(dQm, offsets, pixels, npix: int) -> np.ndarray:
     dQ = np.zeros((npix, d))
     for m in range(S):
         e = mask_entries(offsets, pixels, npix, m)
-        for p in e:
-            dQ[p] += dQm[m] / e.size
+        if e.size:
+            np.add.at(dQ, e, dQm[m] / e.size)  # unbuffered: a repeated index adds once per entry
     return dQ
 
 

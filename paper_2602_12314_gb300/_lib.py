@@ -24,6 +24,8 @@ ERR_TIMEOUT = -6
 _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED_SHAPE", -3: "OUT_OF_MEMORY", -4: "CUDA", -5: "CAPACITY",
           -6: "TIMEOUT"}
 
+ABI_VERSION = 2
+
 PREC_FP32 = 0
 PREC_BF16 = 1
 PREC_FP8 = 2
@@ -72,7 +74,8 @@ class AdamCfg(ctypes.Structure):
 
 
 class Frame(ctypes.Structure):
-    _fields_ = [("gaussians", Gaussians), ("camera", Camera), ("F", P), ("F_dtype", I32), ("mask", P)]
+    _fields_ = [("gaussians", Gaussians), ("camera", Camera), ("F", P), ("F_dtype", I32), ("mask", P),
+                ("mask_offsets", P), ("mask_pixels", P), ("n_mask_entries", I64), ("n_masks", I32)]
 
 
 class Params(ctypes.Structure):
@@ -118,6 +121,8 @@ _SIGS = {
                                           P, P, P], I32),
     "latentam_backward": ([P, I32, ctypes.POINTER(Projected), ctypes.POINTER(Camera), ctypes.POINTER(Bins), P, P,
                            I32, P, P, P, I32, I32, P, I32, P, ctypes.POINTER(LossCfg), I32, P, P, P, P, P, P], I32),
+    "latentam_pool_queries": ([P, P, I64, I32, P, P, I64, I32, P, P], I32),
+    "latentam_pool_queries_bwd": ([P, P, I32, I32, P, P, I64, I64, P, P], I32),
     "latentam_adam": ([P, I32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                        ctypes.POINTER(I64), ctypes.POINTER(F32), ctypes.POINTER(AdamCfg), P], I32),
     "latentam_step": ([P, ctypes.POINTER(Frame), ctypes.POINTER(Params), ctypes.POINTER(LossCfg),
@@ -148,7 +153,7 @@ def load(build_if_missing: bool = False):
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = res
-            if lib.latentam_version() != 1:
+            if lib.latentam_version() != ABI_VERSION:
                 raise RuntimeError("liblatentam.so ABI version mismatch")
             _lib = lib
     return _lib

@@ -288,6 +288,36 @@ def decode_loss_bwd(ctx: Context, Q, K, V, V0, F, mask=None, cfg: LossConfig | N
     return parts, dQ, dK, dV
 
 
+def _mask_csr(offsets, pixels, device):
+    off = torch.as_tensor(offsets, dtype=torch.int32).to(device).contiguous()
+    pix = torch.as_tensor(pixels, dtype=torch.int32).to(device).contiguous()
+    return off, pix
+
+
+def pool_queries(ctx: Context, Q, offsets, pixels):
+    """Per-mask mean of the rows of Q (npix x d) over CSR mask lists (SAM-based targets,
+    Sec. III-B): returns Qm (S x d)."""
+    Q = Q.contiguous()
+    npix, d = Q.shape
+    off, pix = _mask_csr(offsets, pixels, Q.device)
+    S = off.numel() - 1
+    Qm = torch.empty((max(S, 0), d), dtype=torch.float32, device=Q.device)
+    L.check(_lib().latentam_pool_queries(ctx.handle, _ptr(Q), npix, d, _ptr(off), _ptr(pix), pix.numel(), S,
+                                         _ptr(Qm), _stream()))
+    return Qm
+
+
+def pool_queries_bwd(ctx: Context, dQm, offsets, pixels, npix: int):
+    """Adjoint of pool_queries: dQ (npix x d) with dQ_p = sum over masks m listing p of dQm_m / |m|."""
+    dQm = dQm.contiguous()
+    S, d = dQm.shape
+    off, pix = _mask_csr(offsets, pixels, dQm.device)
+    dQ = torch.empty((npix, d), dtype=torch.float32, device=dQm.device)
+    L.check(_lib().latentam_pool_queries_bwd(ctx.handle, _ptr(dQm), S, d, _ptr(off), _ptr(pix), pix.numel(),
+                                             int(npix), _ptr(dQ), _stream()))
+    return dQ
+
+
 def decode_fwd_paper(ctx: Context, Q, W, D, tau: float, precision: int = FP32, want_stats: bool = True):
     """The paper's cosine / temperature decode (Eq. dict_recon): Fhat = softmax(cos(Q W, D) / tau) D."""
     Q, W, D = Q.contiguous(), W.contiguous(), D.contiguous()
@@ -387,7 +417,9 @@ class LatentStep:
     latentam_step."""
 
     def __init__(self, ctx: Context, scene, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
-                 precision: int = FP32, target_dtype=torch.float32):
+                 precision: int = FP32, target_dtype=torch.float32, masks=None):
+        """`masks` (optional; offsets, pixels, per-mask targets F and flags valid, as
+        workloads.MaskSet): the mask-pooled step, one decoded row and target per mask."""
         dev = torch.device("cuda", ctx.device)
         self.ctx = ctx
         self.cfg = cfg or LossConfig()
@@ -397,8 +429,14 @@ class LatentStep:
         self.means, self.quats, self.scales, self.opacities = (t(scene.means), t(scene.quats), t(scene.scales),
                                                                t(scene.opacities))
         self.f, self.K, self.V, self.V0 = t(scene.f), t(scene.K), t(scene.V), t(scene.V0)
-        self.F = t(scene.F).to(target_dtype).contiguous()
-        self.mask = torch.as_tensor(scene.mask, dtype=torch.uint8, device=dev).contiguous()
+        self.mask_offsets = self.mask_pixels = None
+        if masks is None:
+            self.F = t(scene.F).to(target_dtype).contiguous()
+            self.mask = torch.as_tensor(scene.mask, dtype=torch.uint8, device=dev).contiguous()
+        else:
+            self.F = t(masks.F).to(target_dtype).contiguous()
+            self.mask = torch.as_tensor(masks.valid, dtype=torch.uint8, device=dev).contiguous()
+            self.mask_offsets, self.mask_pixels = _mask_csr(masks.offsets, masks.pixels, dev)
         self.moments = {k: torch.zeros_like(getattr(self, k)) for k in ("f", "K", "V")}
         self.moments.update({"v" + k: torch.zeros_like(getattr(self, k)) for k in ("f", "K", "V")})
         self.camera = camera_struct(scene.camera)
@@ -411,6 +449,10 @@ class LatentStep:
         fr.F = self.F.data_ptr()
         fr.F_dtype = _target_dtype(self.F)
         fr.mask = self.mask.data_ptr()
+        if self.mask_offsets is not None:
+            fr.mask_offsets, fr.mask_pixels = self.mask_offsets.data_ptr(), self.mask_pixels.data_ptr()
+            fr.n_mask_entries = self.mask_pixels.numel()
+            fr.n_masks = self.mask_offsets.numel() - 1
         return fr
 
     def params_struct(self) -> L.Params:

@@ -713,6 +713,58 @@ latentam_status latentam_backward(latentam_ctx* ctx, int32_t n, const latentam_p
     return latentam_render_bwd(ctx, n, proj, cam, bins, n_contrib, dQ_scratch, d, df, stream);
 }
 
+namespace {
+
+latentam_status check_masks(int32_t S, int64_t E, int64_t npix, int d, const int32_t* off, const int32_t* pix) {
+    LAT_TRY(check_d(d));
+    REQUIRE(S >= 0 && E >= 0 && npix >= 0, "negative mask count, entry count or pixel count");
+    REQUIRE(E <= INT32_MAX, "n_entries=%lld exceeds the int32 offsets", (long long)E);
+    REQUIRE(S == 0 || off, "null mask offsets");
+    REQUIRE(E == 0 || pix, "null mask pixels");
+    return LATENTAM_OK;
+}
+
+// The plan of a mask set in the context's WS_MASKS slot, followed by `extra` bytes.
+latentam_status mask_plan(latentam_ctx* ctx, const int32_t* off, const int32_t* pix, int64_t E, int32_t S,
+                          int64_t npix, int d, size_t extra, MaskPlan* p, char** extra_ptr) {
+    const size_t pb = (mask_plan_bytes(S, E, d) + 255) & ~(size_t)255;
+    char* base = static_cast<char*>(ws(ctx, WS_MASKS, pb + extra));
+    if (!base) return LATENTAM_ERR_OUT_OF_MEMORY;
+    mask_plan_carve(base, off, pix, E, S, npix, d, p);
+    if (extra_ptr) *extra_ptr = base + pb;
+    return LATENTAM_OK;
+}
+
+}  // namespace
+
+latentam_status latentam_pool_queries(latentam_ctx* ctx, const float* Q, int64_t npix, int32_t d,
+                                      const int32_t* mask_offsets, const int32_t* mask_pixels, int64_t n_entries,
+                                      int32_t S, float* Qm, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_masks(S, n_entries, npix, d, mask_offsets, mask_pixels));
+    REQUIRE((npix == 0 || Q) && (S == 0 || Qm), "null Q or Qm");
+    REQUIRE(aligned16(Q) && aligned16(Qm), "Q, Qm must be 16-byte aligned");
+    MaskPlan p;
+    LAT_TRY(mask_plan(ctx, mask_offsets, mask_pixels, n_entries, S, npix, d, 0, &p, nullptr));
+    cudaStream_t st = (cudaStream_t)stream;
+    LAT_TRY(launch_mask_plan(p, st));
+    return launch_pool_fwd(p, Q, d, Qm, st);
+}
+
+latentam_status latentam_pool_queries_bwd(latentam_ctx* ctx, const float* dQm, int32_t S, int32_t d,
+                                          const int32_t* mask_offsets, const int32_t* mask_pixels, int64_t n_entries,
+                                          int64_t npix, float* dQ, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    LAT_TRY(check_masks(S, n_entries, npix, d, mask_offsets, mask_pixels));
+    REQUIRE((S == 0 || dQm) && (npix == 0 || dQ), "null dQm or dQ");
+    REQUIRE(aligned16(dQm) && aligned16(dQ), "dQm, dQ must be 16-byte aligned");
+    MaskPlan p;
+    LAT_TRY(mask_plan(ctx, mask_offsets, mask_pixels, n_entries, S, npix, d, 0, &p, nullptr));
+    cudaStream_t st = (cudaStream_t)stream;
+    LAT_TRY(launch_mask_plan(p, st));
+    return launch_pool_bwd(p, dQm, d, dQ, st);
+}
+
 latentam_status latentam_adam(latentam_ctx* ctx, int32_t count, float* const* params, const float* const* grads,
                               float* const* m, float* const* v, const int64_t* sizes, const float* lrs,
                               const latentam_adam_cfg* cfg, latentam_stream stream) {
@@ -800,18 +852,38 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
     float* dV = reinterpret_cast<float*>(gb + g_dv);
     double* lp = reinterpret_cast<double*>(gb + g_lp);
     const CamParams cp = cam_params(cam);
-    // one iteration on stream `s`: render, decode + loss + backward, render backward, Adam
-    // (with the step read from step_dev when it is set: graph replays)
+    // mask-pooled targets: the plan of the mask set (once per call) and the pooled queries
+    const int32_t S = frame->n_masks;
+    const bool pooled = S > 0;
+    MaskPlan plan{};
+    float *Qm = nullptr, *dQm = nullptr;
+    if (pooled) {
+        LAT_TRY(check_masks(S, frame->n_mask_entries, npix, d, frame->mask_offsets, frame->mask_pixels));
+        const size_t qb = up(4 * (size_t)S * d);
+        char* xb = nullptr;
+        LAT_TRY(mask_plan(ctx, frame->mask_offsets, frame->mask_pixels, frame->n_mask_entries, S, npix, d, 2 * qb,
+                          &plan, &xb));
+        Qm = reinterpret_cast<float*>(xb);
+        dQm = reinterpret_cast<float*>(xb + qb);
+        LAT_TRY(launch_mask_plan(plan, st));
+    }
+    const float* Qdec = pooled ? Qm : Q;
+    const int64_t ndec = pooled ? (int64_t)S : npix;
+    // one iteration on stream `s`: render (and pool), decode + loss + backward, render backward
+    // (through the pooling's adjoint), Adam (with the step read from step_dev when it is set:
+    // graph replays)
     auto iteration = [&](cudaStream_t s, bool render, const int* step_dev) -> latentam_status {
         if (render) {
             StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, s);
             LAT_TRY(launch_render_fwd(cp, proj, bins, params->f, d, Q, T, nc, s));
+            if (pooled) LAT_TRY(launch_pool_fwd(plan, Q, d, Qm, s));
         }
-        LAT_TRY(latentam_decode_loss_bwd(ctx, Q, npix, d, params->K, params->V, params->V0, M, D, frame->F,
-                                         frame->F_dtype, frame->mask, cfg, prec, lp, learn_f ? dQ : nullptr, dK, dV,
-                                         s));
+        LAT_TRY(latentam_decode_loss_bwd(ctx, Qdec, ndec, d, params->K, params->V, params->V0, M, D, frame->F,
+                                         frame->F_dtype, frame->mask, cfg, prec, lp,
+                                         learn_f ? (pooled ? dQm : dQ) : nullptr, dK, dV, s));
         if (learn_f && N > 0) {
             StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, s);
+            if (pooled) LAT_TRY(launch_pool_bwd(plan, dQm, d, dQ, s));
             LAT_TRY(launch_render_bwd(cp, proj, bins, nc, dQ, d, df, N, s));
         }
         AdamTensor t[3];
@@ -829,10 +901,11 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
     if (graphable) {
         const void* ptrs[] = {params->f, params->K, params->V, params->V0, params->m_f, params->v_f, params->m_K,
                               params->v_K, params->m_V, params->v_V, frame->F, frame->mask, Q, T, nc, dQ, df, dK,
-                              dV, lp, proj.xy, proj.conic_opacity, bins.pair_ids, bins.tile_ranges, st};
+                              dV, lp, proj.xy, proj.conic_opacity, bins.pair_ids, bins.tile_ranges, st,
+                              frame->mask_offsets, frame->mask_pixels, Qm, dQm, plan.chunk_start};
         for (const void* p : ptrs) key.addp(p);
         const int64_t ints[] = {N, d, M, D, (int64_t)bins.num_pairs, (int64_t)frame->F_dtype, (int64_t)prec,
-                                (int64_t)ctx->ws_generation};
+                                (int64_t)ctx->ws_generation, (int64_t)S, frame->n_mask_entries};
         for (int64_t x : ints) key.add((uint64_t)x);
         key.add_camera(cam);
         for (float f : {cfg->lambda_f, cfg->lambda_cos, cfg->lambda_2, cfg->lambda_D, cfg->delta, cfg->logit_scale,

@@ -63,6 +63,7 @@ enum Slot : int {
     WS_STEP_IMG,
     WS_STEP_GRAD,
     WS_PAPER,      // keys, norms, Gram matrix, scaled queries and gradients of the W/D form
+    WS_MASKS,      // mask-pooling plan, pooled queries and their gradients
     WS_NUM_SLOTS
 };
 
@@ -223,6 +224,28 @@ latentam_status paper_prepare(latentam_ctx* ctx, const PaperArgs& a, const Paper
 // dQ, dW, dD (each nullable) from the free-key gradients dQ' (b.dQp), dK (b.dK), dV (b.dV)
 latentam_status paper_chain(latentam_ctx* ctx, const PaperArgs& a, const PaperBuffers& b, float* dQ, float* dW,
                             float* dD, cudaStream_t st);
+
+// Mask pooling (SAM-based targets): the plan of one mask set over an image of npix pixels.
+struct MaskPlan {
+    const int32_t* offsets;  // S + 1 CSR offsets (device)
+    const int32_t* pixels;   // n_entries pixel indices (device)
+    int64_t n_entries;
+    int32_t S;
+    int64_t npix;
+    int64_t max_chunks;      // capacity of part, in chunks
+    int32_t* chunk_start;    // S + 1: first chunk of each mask, [S] = number of chunks
+    int32_t* count;          // S: valid entries per mask
+    float* part;             // max_chunks x d chunk partial sums
+};
+int64_t mask_max_chunks(int32_t S, int64_t E);
+size_t mask_plan_bytes(int32_t S, int64_t E, int d);
+void mask_plan_carve(void* base, const int32_t* offsets, const int32_t* pixels, int64_t E, int32_t S, int64_t npix,
+                     int d, MaskPlan* p);
+latentam_status launch_mask_plan(const MaskPlan& p, cudaStream_t st);
+// Qm (S x d) = per-mask mean of the valid rows of Q (npix x d)
+latentam_status launch_pool_fwd(const MaskPlan& p, const float* Q, int d, float* Qm, cudaStream_t st);
+// dQ (npix x d) = 0, then += dQm_m / count_m over the valid entries of every mask
+latentam_status launch_pool_bwd(const MaskPlan& p, const float* dQm, int d, float* dQ, cudaStream_t st);
 
 struct AdamTensor {
     float* p;
