@@ -396,13 +396,20 @@ LATENTAM_API latentam_status latentam_step(latentam_ctx* ctx, const latentam_fra
 
 /* One keyframe of a batch: its Gaussians and camera, and the queries it renders.  Frames that
  * view the same map pass the same f (and the same Gaussians, N and moments): their query
- * gradients are summed before the single Adam update of f. */
+ * gradients are summed before the single Adam update of f.  The mask fields are those of
+ * latentam_frame (mask-pooled targets, see latentam_pool_queries); the batch is mask-pooled
+ * when any frame has n_masks > 0, and then every frame contributes its n_masks pooled rows
+ * (possibly none). */
 typedef struct {
     latentam_gaussians gaussians;
     latentam_camera camera;
     float* f;     /* N x d */
     float* m_f;   /* Adam moments of f */
     float* v_f;
+    const int32_t* mask_offsets;  /* device, n_masks + 1 CSR offsets (mask-pooled only) */
+    const int32_t* mask_pixels;   /* device, n_mask_entries pixel indices */
+    int64_t n_mask_entries;
+    int32_t n_masks;
 } latentam_batch_frame;
 
 /* The dictionary shared by every frame: keys K (M x d), values V (M x D), trust-region centre
@@ -421,7 +428,9 @@ typedef struct {
  * all stacked pixels in one call, back-propagates to every frame and takes one Adam step on
  * (each distinct f if learn_f, K, V).  The objective pools the loss-set pixels of all frames
  * (one |Omega|) and adds the trust-region term once.  F (sum_k H_k W_k x D, dtype F_dtype) and
- * mask (sum_k H_k W_k, NULL = all) hold the frames' targets concatenated in frame order.
+ * mask (sum_k H_k W_k, NULL = all) hold the frames' targets concatenated in frame order; in a
+ * mask-pooled batch they hold one row and one flag per mask (sum_k n_masks_k rows), the pooled
+ * queries of every frame are stacked in frame order and decoded in one call.
  * adam->step and loss_host behave as in latentam_step. */
 LATENTAM_API latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam_batch_frame* frames,
                                                  int32_t n_frames, const void* F, latentam_dtype F_dtype,

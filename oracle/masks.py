@@ -82,3 +82,33 @@ def iteration_masks(scene, masks, cfg=None, f=None, K=None, V=None, with_df=True
     if with_df:
         out["df"] = oracle.render_frame_bwd(proj, dQ, scene.camera, np.asarray(f).shape[0], Q.shape[1])
     return out
+
+
+def iteration_batch_masks(scenes, mask_sets, cfg=None) -> dict:
+    """One forward + backward over a batch of keyframes sharing the dictionary, mask-pooled:
+    every frame rendered untiled and pooled over its own masks, the pooled rows, targets and
+    flags stacked in frame order, one decode / loss / backward over the stack (one trust-region
+    term), the query gradients pooled back to each frame's pixels and rendered back; df summed
+    over the frames that render the same query array (grouped by the identity of f)."""
+    import oracle
+
+    cfg = cfg or oracle.LossConfig()
+    s0 = scenes[0]
+    projs = [oracle.project_scene(s) for s in scenes]
+    Qs = [oracle.render_frame(p, s.f, s.camera)[0] for p, s in zip(projs, scenes)]
+    Qm = np.concatenate([pool(Q, ms.offsets, ms.pixels) for Q, ms in zip(Qs, mask_sets)])
+    F = np.concatenate([ms.F for ms in mask_sets])
+    valid = np.concatenate([ms.valid for ms in mask_sets])
+    _, A, Fh = oracle.decode(Qm, s0.K, s0.V, cfg.c(Qm.shape[1]))
+    parts, _ = oracle.loss(Fh, F, valid, s0.V, s0.V0, cfg, Qm.shape[1])
+    dQm, dK, dV = oracle.backward(Qm, s0.K, s0.V, s0.V0, A, Fh, F, valid, cfg)
+    df = {}
+    row = 0
+    for p, s, ms in zip(projs, scenes, mask_sets):
+        S = ms.n_masks
+        dQ = pool_bwd(dQm[row:row + S], ms.offsets, ms.pixels, s.camera.n_pixels)
+        g = oracle.render_frame_bwd(p, dQ, s.camera, s.n, Qm.shape[1])
+        df[id(s.f)] = df.get(id(s.f), 0.0) + g
+        row += S
+    return dict(Qm=Qm, loss=parts, dK=dK, dV=dV, dQm=dQm, df=df)
+

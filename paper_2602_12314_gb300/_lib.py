@@ -84,7 +84,8 @@ class Params(ctypes.Structure):
 
 
 class BatchFrame(ctypes.Structure):
-    _fields_ = [("gaussians", Gaussians), ("camera", Camera), ("f", P), ("m_f", P), ("v_f", P)]
+    _fields_ = [("gaussians", Gaussians), ("camera", Camera), ("f", P), ("m_f", P), ("v_f", P),
+                ("mask_offsets", P), ("mask_pixels", P), ("n_mask_entries", I64), ("n_masks", I32)]
 
 
 class Dictionary(ctypes.Structure):

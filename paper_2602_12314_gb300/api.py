@@ -486,7 +486,9 @@ class LatentBatchStep:
     Scenes whose query arrays are the same object render one shared query tensor."""
 
     def __init__(self, ctx: Context, scenes, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
-                 precision: int = FP32, target_dtype=torch.float32):
+                 precision: int = FP32, target_dtype=torch.float32, masks=None):
+        """`masks` (optional): one mask set per scene (workloads.MaskSet layout), the
+        mask-pooled batch."""
         if not 1 <= len(scenes) <= L.MAX_BATCH:
             raise ValueError(f"a batch holds 1..{L.MAX_BATCH} keyframes")
         dev = torch.device("cuda", ctx.device)
@@ -512,8 +514,16 @@ class LatentBatchStep:
                 qs[qk] = (f, torch.zeros_like(f), torch.zeros_like(f))
             self.frames.append((geo[gk], qs[qk], camera_struct(sc.camera)))
         self.queries = [q[0] for q in qs.values()]
-        self.F = torch.cat([t(sc.F) for sc in scenes]).to(target_dtype).contiguous()
-        self.mask = torch.cat([torch.as_tensor(sc.mask, dtype=torch.uint8) for sc in scenes]).to(dev).contiguous()
+        self.csr = None
+        if masks is None:
+            self.F = torch.cat([t(sc.F) for sc in scenes]).to(target_dtype).contiguous()
+            self.mask = torch.cat([torch.as_tensor(sc.mask, dtype=torch.uint8) for sc in scenes]).to(dev).contiguous()
+        else:
+            if len(masks) != len(scenes):
+                raise ValueError("one mask set per scene")
+            self.F = torch.cat([t(m.F) for m in masks]).to(target_dtype).contiguous()
+            self.mask = torch.cat([torch.as_tensor(m.valid, dtype=torch.uint8) for m in masks]).to(dev).contiguous()
+            self.csr = [_mask_csr(m.offsets, m.pixels, dev) for m in masks]
 
     def step(self, iters: int = 1, learn_f: bool = True, want_loss: bool = True):
         fr = (L.BatchFrame * len(self.frames))()
@@ -521,6 +531,10 @@ class LatentBatchStep:
             fr[k].gaussians = _gaussians_struct(*g)
             fr[k].camera = cam
             fr[k].f, fr[k].m_f, fr[k].v_f = q[0].data_ptr(), q[1].data_ptr(), q[2].data_ptr()
+            if self.csr is not None:
+                off, pix = self.csr[k]
+                fr[k].mask_offsets, fr[k].mask_pixels = off.data_ptr(), pix.data_ptr()
+                fr[k].n_mask_entries, fr[k].n_masks = pix.numel(), off.numel() - 1
         dic = L.Dictionary(self.K.data_ptr(), self.V.data_ptr(), self.V0.data_ptr(), self.mK.data_ptr(),
                            self.vK.data_ptr(), self.mV.data_ptr(), self.vV.data_ptr(), self.d, self.M, self.D)
         cs = self.cfg.struct()
@@ -533,6 +547,106 @@ class LatentBatchStep:
         if out is None:
             return None
         return dict(cos=out[0], l2=out[1], tr=out[2], total=out[3], n_valid=out[4])
+
+
+@dataclasses.dataclass
+class Keyframe:
+    """One keyframe of a LatentMap on the device: its camera, its targets (per pixel, or per
+    mask with the CSR mask lists) and its loss-set flags."""
+    camera: L.Camera
+    F: torch.Tensor
+    mask: torch.Tensor
+    csr: tuple | None = None  # (offsets, pixels) int32 device tensors when mask-pooled
+
+    @property
+    def rows(self) -> int:
+        return self.F.shape[0]
+
+
+class LatentMap:
+    """The optimisation loop of Algorithm 1 over a stream of keyframes of one map (Sec. III-C).
+
+    The map's Gaussians and queries f and the dictionary (K, V) with their Adam moments stay on
+    the device.  add_keyframe(camera, targets) runs, for the new keyframe:
+      1. the trust-region centre V0 <- V (the dictionary at the start of the keyframe);
+      2. the training batch: the new keyframe plus B keyframes sampled from the history;
+      3. Stage I: R1 iterations updating f, K and V (the Gaussians' other attributes are fixed);
+      4. Stage II: R2 iterations updating K and V with f fixed;
+      5. the new keyframe joins the history.
+    Defaults R1 = 1, R2 = 5 (Sec. III-C).  Every iteration goes through latentam_step_batch."""
+
+    def __init__(self, ctx: Context, scene, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
+                 precision: int = FP32, target_dtype=torch.float32, B: int = 2, R1: int = 1, R2: int = 5,
+                 seed: int = 0):
+        from .history import KeyframeHistory
+
+        dev = torch.device("cuda", ctx.device)
+        self.ctx, self.dev = ctx, dev
+        self.cfg = cfg or LossConfig()
+        self.adam_cfg = adam_cfg or AdamConfig()
+        self.precision, self.target_dtype = int(precision), target_dtype
+        self.B, self.R1, self.R2 = int(B), int(R1), int(R2)
+        t = lambda a: _dev_f32(a, dev)  # noqa: E731
+        self.geometry = tuple(t(getattr(scene, a)) for a in ("means", "quats", "scales", "opacities"))
+        self.f = t(scene.f)
+        self.m_f, self.v_f = torch.zeros_like(self.f), torch.zeros_like(self.f)
+        self.K, self.V = t(scene.K), t(scene.V)
+        self.V0 = self.V.clone()
+        self.mK, self.vK = torch.zeros_like(self.K), torch.zeros_like(self.K)
+        self.mV, self.vV = torch.zeros_like(self.V), torch.zeros_like(self.V)
+        self.d, self.M, self.D = self.f.shape[1], self.V.shape[0], self.V.shape[1]
+        self.history = KeyframeHistory(seed)
+
+    def keyframe(self, camera, F, mask=None, masks=None) -> Keyframe:
+        """Device copy of a keyframe: per-pixel targets F (H*W x D) with loss-set mask, or a
+        mask set (offsets, pixels, per-mask targets F and flags valid)."""
+        dev = self.dev
+        if masks is not None:
+            return Keyframe(camera_struct(camera), _dev_f32(masks.F, dev).to(self.target_dtype).contiguous(),
+                            torch.as_tensor(masks.valid, dtype=torch.uint8).to(dev).contiguous(),
+                            _mask_csr(masks.offsets, masks.pixels, dev))
+        n = camera.width * camera.height
+        m = torch.ones(n, dtype=torch.uint8) if mask is None else torch.as_tensor(mask, dtype=torch.uint8)
+        return Keyframe(camera_struct(camera), _dev_f32(F, dev).to(self.target_dtype).contiguous(),
+                        m.to(dev).contiguous())
+
+    def _run(self, batch, iters: int, learn_f: bool):
+        if iters <= 0:
+            return None
+        pooled = batch[0].csr is not None
+        if any((k.csr is not None) != pooled for k in batch):
+            raise ValueError("keyframes of one map are either all mask-pooled or all per-pixel")
+        fr = (L.BatchFrame * len(batch))()
+        for i, kf in enumerate(batch):
+            fr[i].gaussians = _gaussians_struct(*self.geometry)
+            fr[i].camera = kf.camera
+            fr[i].f, fr[i].m_f, fr[i].v_f = self.f.data_ptr(), self.m_f.data_ptr(), self.v_f.data_ptr()
+            if pooled:
+                off, pix = kf.csr
+                fr[i].mask_offsets, fr[i].mask_pixels = off.data_ptr(), pix.data_ptr()
+                fr[i].n_mask_entries, fr[i].n_masks = pix.numel(), off.numel() - 1
+        F = torch.cat([k.F for k in batch]).contiguous()
+        mask = torch.cat([k.mask for k in batch]).contiguous()
+        dic = L.Dictionary(self.K.data_ptr(), self.V.data_ptr(), self.V0.data_ptr(), self.mK.data_ptr(),
+                           self.vK.data_ptr(), self.mV.data_ptr(), self.vV.data_ptr(), self.d, self.M, self.D)
+        cs, ac = self.cfg.struct(), self.adam_cfg.struct()
+        out = (ctypes.c_double * L.LOSS_PARTS)()
+        L.check(_lib().latentam_step_batch(self.ctx.handle, fr, len(batch), _ptr(F), _target_dtype(F), _ptr(mask),
+                                           ctypes.byref(dic), ctypes.byref(cs), ctypes.byref(ac), int(iters),
+                                           int(bool(learn_f)), self.precision, out, _stream()))
+        self.adam_cfg.step = int(ac.step)
+        return dict(cos=out[0], l2=out[1], tr=out[2], total=out[3], n_valid=out[4])
+
+    def add_keyframe(self, camera, F=None, mask=None, masks=None) -> dict:
+        """Algorithm 1's optimisation of one new keyframe; returns the loss of the last Stage I
+        and Stage II iterations and the batch size."""
+        kf = self.keyframe(camera, F, mask, masks)
+        self.V0.copy_(self.V)
+        batch = self.history.batch(kf, self.B)
+        l1 = self._run(batch, self.R1, True)
+        l2 = self._run(batch, self.R2, False)
+        self.history.add(kf)
+        return dict(stage1=l1, stage2=l2, batch=len(batch))
 
 
 def default_logit_scale(d: int) -> float:

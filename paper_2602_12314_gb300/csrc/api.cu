@@ -20,7 +20,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // Instantiated graphs of the step's iteration, keyed by every pointer, shape and scalar the
 // iteration bakes into its launches (and the workspace generation).
 struct GraphKey {
-    static constexpr int kMax = 320;
+    static constexpr int kMax = 1280;  // a batch of 32 frames with masks needs about 1100
     uint64_t v[kMax];
     int n = 0;
     bool overflow = false;  // a key that did not fit never matches (no graph)
@@ -1030,6 +1030,38 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
     const size_t i_q = 0, i_t = i_q + up(4 * (size_t)total_pix * d), i_n = i_t + up(4 * (size_t)total_pix),
                  i_dq = i_n + up(4 * (size_t)total_pix), i_end = i_dq + up(4 * (size_t)total_pix * d);
     char* ib = static_cast<char*>(ws(ctx, WS_STEP_IMG, i_end));
+    // mask-pooled batch: one plan per frame, the pooled rows of every frame stacked in order
+    bool pooled = false;
+    for (int k = 0; k < n_frames; ++k) pooled = pooled || frames[k].n_masks > 0;
+    MaskPlan plans[LATENTAM_MAX_BATCH];
+    int64_t row_off[LATENTAM_MAX_BATCH + 1];
+    row_off[0] = 0;
+    float *Qm = nullptr, *dQm = nullptr;
+    if (pooled) {
+        size_t pbytes[LATENTAM_MAX_BATCH], tot = 0;
+        for (int k = 0; k < n_frames; ++k) {
+            const latentam_batch_frame& fr = frames[k];
+            const int64_t np_k = (int64_t)fr.camera.width * fr.camera.height;
+            LAT_TRY(check_masks(fr.n_masks, fr.n_mask_entries, np_k, d, fr.mask_offsets, fr.mask_pixels));
+            pbytes[k] = up(mask_plan_bytes(fr.n_masks, fr.n_mask_entries, d));
+            tot += pbytes[k];
+            row_off[k + 1] = row_off[k] + fr.n_masks;
+        }
+        const size_t qb = up(4 * (size_t)row_off[n_frames] * d);
+        char* mb = static_cast<char*>(ws(ctx, WS_MASKS, tot + 2 * qb));
+        if (!mb) return LATENTAM_ERR_OUT_OF_MEMORY;
+        size_t o = 0;
+        for (int k = 0; k < n_frames; ++k) {
+            const latentam_batch_frame& fr = frames[k];
+            mask_plan_carve(mb + o, fr.mask_offsets, fr.mask_pixels, fr.n_mask_entries, fr.n_masks,
+                            (int64_t)fr.camera.width * fr.camera.height, d, &plans[k]);
+            o += pbytes[k];
+            LAT_TRY(launch_mask_plan(plans[k], st));
+        }
+        Qm = reinterpret_cast<float*>(mb + o);
+        dQm = reinterpret_cast<float*>(mb + o + qb);
+    }
+    const int64_t ndec = pooled ? row_off[n_frames] : total_pix;
     size_t g_end = 0;
     size_t g_df[LATENTAM_MAX_BATCH];
     for (int u = 0; u < n_groups; ++u) {
@@ -1055,15 +1087,19 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
             for (int k = 0; k < n_frames; ++k)
                 LAT_TRY(launch_render_fwd(fs[k].cam, fs[k].proj, fs[k].bins, frames[k].f, d, Q + fs[k].pix_off * d,
                                           T + fs[k].pix_off, nc + fs[k].pix_off, s));
+            for (int k = 0; pooled && k < n_frames; ++k)
+                LAT_TRY(launch_pool_fwd(plans[k], Q + fs[k].pix_off * d, d, Qm + row_off[k] * d, s));
         }
-        LAT_TRY(latentam_decode_loss_bwd(ctx, Q, total_pix, d, dict->K, dict->V, dict->V0, M, D, F, F_dtype, mask,
-                                         cfg, prec, lp, learn_f ? dQ : nullptr, dK, dV, s));
+        LAT_TRY(latentam_decode_loss_bwd(ctx, pooled ? Qm : Q, ndec, d, dict->K, dict->V, dict->V0, M, D, F, F_dtype,
+                                         mask, cfg, prec, lp, learn_f ? (pooled ? dQm : dQ) : nullptr, dK, dV, s));
         if (learn_f) {
             StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, s);
             for (int u = 0; u < n_groups; ++u) {
                 cudaError_t e = cudaMemsetAsync(groups[u].df, 0, sizeof(float) * (size_t)groups[u].n * d, s);
                 if (e != cudaSuccess) return cuda_error(e, "memset df");
             }
+            for (int k = 0; pooled && k < n_frames; ++k)
+                LAT_TRY(launch_pool_bwd(plans[k], dQm + row_off[k] * d, d, dQ + fs[k].pix_off * d, s));
             for (int k = 0; k < n_frames; ++k)
                 if (frames[k].gaussians.n > 0)
                     LAT_TRY(launch_render_bwd(fs[k].cam, fs[k].proj, fs[k].bins, nc + fs[k].pix_off,
@@ -1090,7 +1126,7 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
     const bool graphable = ctx->use_graphs && learn_f && !ctx->profiling && iters > 0;
     if (graphable) {
         const void* ptrs[] = {dict->K, dict->V, dict->V0, dict->m_K, dict->v_K, dict->m_V, dict->v_V, F, mask,
-                              Q, T, nc, dQ, dK, dV, lp, st};
+                              Q, T, nc, dQ, dK, dV, lp, st, Qm, dQm};
         for (const void* p : ptrs) key.addp(p);
         const int64_t ints[] = {n_frames, n_groups, d, M, D, (int64_t)F_dtype, (int64_t)prec,
                                 (int64_t)ctx->ws_generation};
@@ -1104,6 +1140,11 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
             key.add((uint64_t)fr.gaussians.n);
             key.add((uint64_t)fs[k].bins.num_pairs);
             key.add_camera(fr.camera);
+            key.addp(fr.mask_offsets);
+            key.addp(fr.mask_pixels);
+            key.addp(pooled ? plans[k].chunk_start : nullptr);
+            key.add((uint64_t)fr.n_mask_entries);
+            key.add((uint64_t)fr.n_masks);
         }
         for (int u = 0; u < n_groups; ++u) key.addp(groups[u].df);
         for (float f : {cfg->lambda_f, cfg->lambda_cos, cfg->lambda_2, cfg->lambda_D, cfg->delta, cfg->logit_scale,

@@ -200,3 +200,53 @@ def test_full_size_room_pooling_and_decode(api, ctx):
     dQ = api.pool_queries_bwd(ctx, dQm, ms.offsets, ms.pixels, s.camera.n_pixels).cpu().numpy()
     dQo = om.pool_bwd(dQm.cpu().numpy(), ms.offsets, ms.pixels, s.camera.n_pixels)
     np.testing.assert_allclose(dQ, dQo, rtol=1e-5, atol=1e-6 * np.abs(dQo).max())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_one_iteration_matches_oracle(api, ctx, prec):
+    from workloads import room_views
+    views = room_views(5, n_views=3, n=40_000, width=96, height=72, fx=78.75)
+    mss = [sam_masks(v, cell=(24, 18), overlap=(k == 1), drop=0.1, seed=k) for k, v in enumerate(views)]
+    p = api.FP32 if prec == "fp32" else api.BF16
+    tdt = torch.float32 if prec == "fp32" else torch.bfloat16
+    st = api.LatentBatchStep(ctx, views, precision=p, target_dtype=tdt, masks=mss)
+    loss = st.step(iters=1)
+    o = om.iteration_batch_masks(views, mss, oracle.LossConfig())
+    assert loss["n_valid"] == o["loss"]["n_valid"]
+    rel = 1e-4 if prec == "fp32" else 5e-3
+    for k in ("cos", "l2", "total"):
+        assert loss[k] == pytest.approx(o["loss"][k], rel=rel, abs=1e-9), k
+    if prec == "fp32":
+        _first_update_check(views[0].K, st.K.cpu().numpy().astype(np.float64), o["dK"])
+        _first_update_check(views[0].V, st.V.cpu().numpy().astype(np.float64), o["dV"])
+        _first_update_check(views[0].f, st.queries[0].cpu().numpy().astype(np.float64), o["df"][id(views[0].f)])
+
+
+def test_latent_map_runs_algorithm_1(api, ctx):
+    """Four keyframes of one room through LatentMap (B = 2, R1 = 1, R2 = 5): batch sizes grow
+    with the history, the first keyframe's Stage I loss is the oracle's, and Stage II leaves the
+    queries alone."""
+    from workloads import room_views
+    views = room_views(6, n_views=4, n=40_000, width=96, height=72, fx=78.75)
+    mss = [sam_masks(v, cell=(24, 18), seed=k) for k, v in enumerate(views)]
+    m = api.LatentMap(ctx, views[0], B=2)
+    o = om.iteration_masks(views[0], mss[0], oracle.LossConfig())
+    sizes = []
+    for k, (v, ms) in enumerate(zip(views, mss)):
+        r = m.add_keyframe(v.camera, masks=ms)
+        sizes.append(r["batch"])
+        assert np.isfinite(r["stage1"]["total"]) and np.isfinite(r["stage2"]["total"])
+        if k == 0:
+            assert r["stage1"]["total"] == pytest.approx(o["loss"]["total"], rel=1e-4)
+    assert sizes == [1, 2, 3, 3] and len(m.history) == 4
+    assert m.adam_cfg.step == 1 + 4 * (1 + 5)
+    # Stage II alone: the queries stay, the dictionary moves
+    m2 = api.LatentMap(ctx, views[0], B=1, R1=0, R2=3)
+    f0, V0 = m2.f.clone(), m2.V.clone()
+    m2.add_keyframe(views[0].camera, masks=mss[0])
+    assert torch.equal(m2.f, f0) and not torch.equal(m2.V, V0)
+    # the per-pixel form of the map
+    m3 = api.LatentMap(ctx, views[0], B=1)
+    for v in views[:2]:
+        r = m3.add_keyframe(v.camera, F=v.F, mask=v.mask)
+        assert np.isfinite(r["stage2"]["total"])

@@ -133,3 +133,21 @@ def test_mask_sets_partition_and_overlap():
     assert np.all(np.bincount(b.pixels, minlength=npix) == 2)
     norms = np.linalg.norm(b.F, axis=1)
     np.testing.assert_allclose(norms, 1.0, rtol=1e-6)
+
+
+def test_batch_of_pixel_masks_is_the_per_pixel_batch_and_one_frame_is_the_single_step():
+    from workloads import room_views
+    views = room_views(2, n_views=2, n=4000, width=24, height=18, fx=19.7)
+    cfg = oracle.LossConfig()
+    a = om.iteration_batch_masks(views, [pixel_masks(v) for v in views], cfg)
+    b = oracle.iteration_batch(views, cfg)
+    for k in ("cos", "l2", "tr", "total", "n_valid"):
+        assert a["loss"][k] == b["loss"][k], k
+    np.testing.assert_array_equal(a["dK"], b["dK"])
+    np.testing.assert_array_equal(a["dV"], b["dV"])
+    np.testing.assert_array_equal(a["df"][id(views[0].f)], b["df"][id(views[0].f)])
+    ms = sam_masks(views[0], cell=(6, 6), overlap=True, seed=1)
+    c = om.iteration_batch_masks(views[:1], [ms], cfg)
+    e = om.iteration_masks(views[0], ms, cfg)
+    assert c["loss"]["total"] == e["loss"]["total"]
+    np.testing.assert_array_equal(c["df"][id(views[0].f)], e["df"])
