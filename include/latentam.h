@@ -338,6 +338,35 @@ LATENTAM_API latentam_status latentam_pool_queries_bwd(latentam_ctx* ctx, const 
                                                        int64_t n_entries, int64_t npix, float* dQ,
                                                        latentam_stream stream);
 
+/* ---- dictionary initialisation from streaming data ------------------------------------ */
+
+/* Streaming K-means update of the dictionary atoms (Algorithm 1, Eq. stream_kmeans_init,
+ * Sec. III-C): D_t^(0) = StreamKMeans(F_t, D_{t-1}, K).
+ *   1. local K-means: the valid rows of F (n x D, row-major float32; valid: n flags, NULL = all)
+ *      are clustered into k_micro micro-clusters by iters_local Lloyd iterations started at the
+ *      rows init_idx (device, k_micro int32; distinct valid rows; an index outside [0, n)
+ *      starts its centre at the origin);
+ *   2. merge: the occupied slots of the dictionary (weights > 0) and the non-empty
+ *      micro-clusters (weight = row count) form weighted points; the empty slots, in slot
+ *      order, start at the micro-centres, heaviest first (ties: lower micro index);
+ *   3. re-cluster: iters_global weighted Lloyd iterations of the points against the occupied
+ *      slots; a slot becomes the weighted mean of its points and its weight their total weight
+ *      (a slot left without points keeps its centre with weight 0).
+ * Squared Euclidean distances in float32 (|c|^2 - 2 <x, c>), ties to the lower index; fixed
+ * iteration counts; deterministic summation order.  centres (K x D) and weights (K) are
+ * updated in place; slots keep their identity.  micro_centres (k_micro x D), micro_weights
+ * (k_micro) and micro_assign (n, -1 for invalid rows) receive the local clustering, and
+ * point_assign (K + k_micro) the slot of each merged point in the last global iteration (points
+ * in merge order: occupied slots, then non-empty micro-clusters; -1 past the last point), when
+ * not NULL.  Limits: 1 <= k_micro <= min(32, n) (n >= 1), 1 <= K <= 8192, D % 4 == 0 and
+ * D <= 1024, iteration counts >= 1; pointers 16-byte aligned; UNSUPPORTED_SHAPE otherwise. */
+LATENTAM_API latentam_status latentam_stream_kmeans(latentam_ctx* ctx, const float* F, int64_t n, int32_t D,
+                                                    const uint8_t* valid, const int32_t* init_idx, int32_t k_micro,
+                                                    int32_t iters_local, int32_t iters_global, float* centres,
+                                                    float* weights, int32_t K, float* micro_centres,
+                                                    float* micro_weights, int32_t* micro_assign,
+                                                    int32_t* point_assign, latentam_stream stream);
+
 /* ---- optimiser ----------------------------------------------------------------------- */
 
 /* One Adam update of `count` tensors in a single launch: params[i], grads[i], m[i], v[i]

@@ -36,11 +36,15 @@ import numpy as np
 
 
 def sq_dist(X, C) -> np.ndarray:
-    """||x_i - c_j||^2 for every row pair (the direct definition)."""
+    """||x_i - c_j||^2 for every row pair (the direct definition, a block of rows at a time)."""
     X = np.asarray(X, np.float64)
     C = np.asarray(C, np.float64)
-    diff = X[:, None, :] - C[None, :, :]
-    return (diff * diff).sum(axis=2)
+    out = np.empty((X.shape[0], C.shape[0]))
+    step = max(1, (1 << 22) // max(1, C.shape[0] * C.shape[1]))
+    for i in range(0, X.shape[0], step):
+        diff = X[i:i + step, None, :] - C[None, :, :]
+        out[i:i + step] = (diff * diff).sum(axis=2)
+    return out
 
 
 def assign(X, C, active=None):

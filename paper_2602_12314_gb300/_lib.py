@@ -124,6 +124,7 @@ _SIGS = {
                            I32, P, P, P, I32, I32, P, I32, P, ctypes.POINTER(LossCfg), I32, P, P, P, P, P, P], I32),
     "latentam_pool_queries": ([P, P, I64, I32, P, P, I64, I32, P, P], I32),
     "latentam_pool_queries_bwd": ([P, P, I32, I32, P, P, I64, I64, P, P], I32),
+    "latentam_stream_kmeans": ([P, P, I64, I32, P, P, I32, I32, I32, P, P, I32, P, P, P, P, P], I32),
     "latentam_adam": ([P, I32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                        ctypes.POINTER(I64), ctypes.POINTER(F32), ctypes.POINTER(AdamCfg), P], I32),
     "latentam_step": ([P, ctypes.POINTER(Frame), ctypes.POINTER(Params), ctypes.POINTER(LossCfg),

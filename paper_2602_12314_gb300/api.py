@@ -288,6 +288,30 @@ def decode_loss_bwd(ctx: Context, Q, K, V, V0, F, mask=None, cfg: LossConfig | N
     return parts, dQ, dK, dV
 
 
+def stream_kmeans(ctx: Context, F, centres, weights, init_idx, valid=None, iters_local: int = 10,
+                  iters_global: int = 10, want_micro: bool = False):
+    """Streaming K-means update of the dictionary (Algorithm 1, Eq. stream_kmeans_init): centres
+    (K x D) and weights (K) float32 device tensors are updated in place from the new embeddings
+    F (n x D); init_idx holds the k_micro initial rows of the local K-means.  Returns the
+    micro-clusters (centres, weights, row assignment) and the merged points' slots in the last
+    global iteration when want_micro."""
+    F = F.contiguous()
+    n, D = F.shape
+    K = centres.shape[0]
+    assert centres.is_contiguous() and weights.is_contiguous() and centres.dtype == torch.float32
+    idx = torch.as_tensor(init_idx, dtype=torch.int32).to(F.device).contiguous()
+    k = idx.numel()
+    v = valid.contiguous().to(torch.uint8) if valid is not None else None
+    mC = torch.empty((k, D), dtype=torch.float32, device=F.device) if want_micro else None
+    mW = torch.empty((k,), dtype=torch.float32, device=F.device) if want_micro else None
+    ma = torch.empty((n,), dtype=torch.int32, device=F.device) if want_micro else None
+    pa = torch.empty((K + k,), dtype=torch.int32, device=F.device) if want_micro else None
+    L.check(_lib().latentam_stream_kmeans(ctx.handle, _ptr(F), n, D, _ptr(v), _ptr(idx), k, int(iters_local),
+                                          int(iters_global), _ptr(centres), _ptr(weights), K, _ptr(mC), _ptr(mW),
+                                          _ptr(ma), _ptr(pa), _stream()))
+    return (mC, mW, ma, pa) if want_micro else None
+
+
 def _mask_csr(offsets, pixels, device):
     off = torch.as_tensor(offsets, dtype=torch.int32).to(device).contiguous()
     pix = torch.as_tensor(pixels, dtype=torch.int32).to(device).contiguous()

@@ -765,6 +765,25 @@ latentam_status latentam_pool_queries_bwd(latentam_ctx* ctx, const float* dQm, i
     return launch_pool_bwd(p, dQm, d, dQ, st);
 }
 
+latentam_status latentam_stream_kmeans(latentam_ctx* ctx, const float* F, int64_t n, int32_t D,
+                                       const uint8_t* valid, const int32_t* init_idx, int32_t k_micro,
+                                       int32_t iters_local, int32_t iters_global, float* centres, float* weights,
+                                       int32_t K, float* micro_centres, float* micro_weights, int32_t* micro_assign,
+                                       int32_t* point_assign, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    REQUIRE(F && init_idx && centres && weights, "null argument");
+    if (!(n >= 1 && k_micro >= 1 && k_micro <= 32 && k_micro <= n && K >= 1 && K <= 8192 && D >= 4 && D % 4 == 0 &&
+          D <= 1024)) {
+        set_error("stream_kmeans: unsupported shape n=%lld D=%d k_micro=%d K=%d", (long long)n, D, k_micro, K);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    REQUIRE(iters_local >= 1 && iters_global >= 1, "iteration counts must be >= 1");
+    REQUIRE(aligned16(F) && aligned16(centres) && aligned16(micro_centres), "F and centres must be 16-byte aligned");
+    KMeansArgs a{F, n, D, valid, init_idx, k_micro, iters_local, iters_global, centres, weights, K,
+                 micro_centres, micro_weights, micro_assign, point_assign};
+    return stream_kmeans(ctx, a, (cudaStream_t)stream);
+}
+
 latentam_status latentam_adam(latentam_ctx* ctx, int32_t count, float* const* params, const float* const* grads,
                               float* const* m, float* const* v, const int64_t* sizes, const float* lrs,
                               const latentam_adam_cfg* cfg, latentam_stream stream) {

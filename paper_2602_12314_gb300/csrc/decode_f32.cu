@@ -1151,6 +1151,13 @@ latentam_status decode_loss_bwd_f32_noalloc(latentam_ctx* ctx, const DecodeArgs&
 
 size_t decode_noalloc_scratch_bytes() { return kStaticScratchBytes; }
 
+latentam_status sgemm_abt(const float* A, int64_t m, const float* B, int64_t n, int64_t k, float* C, int64_t ldc,
+                          float scale, cudaStream_t st) {
+    const PlainSrc a{A, k, m, k}, b{B, k, n, k};
+    const StoreTileEpi::Params ep{C, ldc, 0, scale};
+    return launch_sgemm<true, true, PlainSrc, PlainSrc, StoreTileEpi>(a, b, m, n, k, 1, ep, st);
+}
+
 latentam_status decode_loss_bwd_f32(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
     switch (a.d) {
         case 16: return loss_bwd_t<16>(ctx, a, st);

@@ -64,6 +64,7 @@ enum Slot : int {
     WS_STEP_GRAD,
     WS_PAPER,      // keys, norms, Gram matrix, scaled queries and gradients of the W/D form
     WS_MASKS,      // mask-pooling plan, pooled queries and their gradients
+    WS_KMEANS,     // streaming K-means scratch
     WS_NUM_SLOTS
 };
 
@@ -224,6 +225,31 @@ latentam_status paper_prepare(latentam_ctx* ctx, const PaperArgs& a, const Paper
 // dQ, dW, dD (each nullable) from the free-key gradients dQ' (b.dQp), dK (b.dK), dV (b.dV)
 latentam_status paper_chain(latentam_ctx* ctx, const PaperArgs& a, const PaperBuffers& b, float* dQ, float* dW,
                             float* dD, cudaStream_t st);
+
+// C = scale A B^T on the FP32 tiled GEMM: A (m x k) and B (n x k) row-major with row stride k,
+// C row stride ldc.  k and ldc multiples of 4, pointers 16-byte aligned, C rows padded to a
+// multiple of 4 columns (the tile stores float4).
+latentam_status sgemm_abt(const float* A, int64_t m, const float* B, int64_t n, int64_t k, float* C, int64_t ldc,
+                          float scale, cudaStream_t st);
+
+// Streaming K-means update of the dictionary (see latentam_stream_kmeans).
+struct KMeansArgs {
+    const float* F;          // n x D embeddings of the new keyframe
+    int64_t n;
+    int D;
+    const uint8_t* valid;    // n flags, nullable
+    const int32_t* init_idx; // k initial rows of the micro-clusters (device)
+    int k;                   // micro-clusters, 1..32
+    int iters_local, iters_global;
+    float* centres;          // K x D, in/out
+    float* weights;          // K, in/out
+    int K;
+    float* micro_C;          // k x D out, nullable
+    float* micro_W;          // k out, nullable
+    int32_t* micro_assign;   // n out, nullable
+    int32_t* point_assign;   // K + k out, nullable
+};
+latentam_status stream_kmeans(latentam_ctx* ctx, const KMeansArgs& a, cudaStream_t st);
 
 // Mask pooling (SAM-based targets): the plan of one mask set over an image of npix pixels.
 struct MaskPlan {
