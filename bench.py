@@ -63,7 +63,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--batch", type=int, default=6, help="keyframes of the batched form (B + 1, B = 5 in Sec. IV-A)")
-    p.add_argument("--precision", choices=["both", "fp32", "bf16", "fp8", "bf16_batch", "fp32_batch"], default="both",
+    p.add_argument("--precision", choices=["both", "fp32", "bf16", "fp8", "bf16_batch", "fp32_batch", "fp32_masks",
+                                          "bf16_masks"], default="both",
                    help="both: the FP32 form is the headline value, the BF16 tensor-core form is reported beside it")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -242,10 +243,11 @@ def decode_flops(n, M, D, d):
     return 6.0 * n * M * D + 6.0 * n * M * d
 
 
-def _measure(args, world, rank, local, scene, prec, dist, views=None):
+def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None):
     """Time args.steps steps of one precision form; returns its numbers (rank 0 view).  With
     `views`, a step is one iteration of the batched step over all those keyframes and the
-    value counts keyframe-iterations per second."""
+    value counts keyframe-iterations per second.  With `masks`, the step is mask-pooled (one
+    decoded row and target per SAM-style mask)."""
     import numpy as np
     import torch
 
@@ -255,7 +257,7 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
     ctx = api.Context(local)
     target_dtype = torch.float32 if prec == api.FP32 else torch.bfloat16
     if views is None:
-        st = api.LatentStep(ctx, scene, precision=prec, target_dtype=target_dtype)
+        st = api.LatentStep(ctx, scene, precision=prec, target_dtype=target_dtype, masks=masks)
     else:
         st = api.LatentBatchStep(ctx, views, precision=prec, target_dtype=target_dtype)
     n_frames = 1 if views is None else len(views)
@@ -302,8 +304,14 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
         if views is None:
             host = {k: torch.as_tensor(np.ascontiguousarray(getattr(scene, k)), dtype=torch.float32).pin_memory()
                     for k in ("means", "quats", "scales", "opacities")}
-            host["F"] = torch.as_tensor(scene.F, dtype=torch.float32).to(target_dtype).pin_memory()
-            host["mask"] = torch.as_tensor(scene.mask, dtype=torch.uint8).pin_memory()
+            if masks is None:
+                host["F"] = torch.as_tensor(scene.F, dtype=torch.float32).to(target_dtype).pin_memory()
+                host["mask"] = torch.as_tensor(scene.mask, dtype=torch.uint8).pin_memory()
+            else:
+                host["F"] = torch.as_tensor(masks.F, dtype=torch.float32).to(target_dtype).pin_memory()
+                host["mask"] = torch.as_tensor(masks.valid, dtype=torch.uint8).pin_memory()
+                host["mask_offsets"] = torch.as_tensor(masks.offsets).pin_memory()
+                host["mask_pixels"] = torch.as_tensor(masks.pixels).pin_memory()
         else:  # the keyframes' targets (the map's geometry stays on the device)
             host = {"F": torch.cat([torch.as_tensor(v.F) for v in views]).to(target_dtype).pin_memory(),
                     "mask": torch.cat([torch.as_tensor(v.mask) for v in views]).pin_memory()}
@@ -328,6 +336,8 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
     # ---- roofline of the dominant stage (decode + loss + decode backward) -------------------
     peaks, peak_src = _peaks()
     n, M, D, d = scene.camera.n_pixels * n_frames, scene.M, scene.D, scene.d
+    if masks is not None:
+        n = masks.n_masks
     dec_ms, dec_cnt = prof["decode"]
     dec_avg_s = dec_ms / max(dec_cnt, 1) / 1e3
     flops = decode_flops(n, M, D, d)
@@ -359,6 +369,41 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None):
             "dtype": {api.FP32: "f32", api.BF16: "bf16", api.FP8: "bf16+e4m3"}[prec]}
 
 
+def _measure_kmeans(args, local, scene, masks):
+    """Device time of one streaming K-means dictionary update (5 micro-clusters, 10 + 10 Lloyd
+    iterations, K = M slots half occupied) from the keyframe's mask targets and from its
+    per-pixel targets (CUDA events, median of 5 calls after 2 warm-up calls)."""
+    import numpy as np
+    import torch
+
+    from paper_2602_12314_gb300 import api
+
+    ctx = api.Context(local)
+    rng = np.random.default_rng(args.seed)
+    out = {}
+    for name, F, valid in (("mask_targets", masks.F, masks.valid), ("per_pixel_targets", scene.F, scene.mask)):
+        Fd = torch.as_tensor(F, dtype=torch.float32, device="cuda")
+        vd = torch.as_tensor(valid, dtype=torch.uint8, device="cuda")
+        init = rng.choice(np.flatnonzero(valid), size=5, replace=False).astype(np.int32)
+        V0 = torch.as_tensor(scene.V, device="cuda")
+        w0 = torch.zeros(scene.M, device="cuda")
+        w0[: scene.M // 2] = 10.0
+        times = []
+        for it in range(7):
+            V, w = V0.clone(), w0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            api.stream_kmeans(ctx, Fd, V, w, init, valid=vd)
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= 2:
+                times.append(e0.elapsed_time(e1))
+        out[name] = {"rows": int(F.shape[0]), "ms": float(np.median(times))}
+    ctx.close()
+    out["K"], out["D"], out["k_micro"] = scene.M, scene.D, 5
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -370,16 +415,21 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     scene = _scene(args.seed + rank, args.crop)
-    forms = ["fp32", "bf16", "bf16_batch", "fp8"] if args.precision == "both" else [args.precision]
+    forms = (["fp32", "bf16", "bf16_batch", "fp8", "fp32_masks", "bf16_masks"] if args.precision == "both"
+             else [args.precision])
     res = {}
+    masks = None
     for f in forms:
         views = None
         if f.endswith("_batch"):
             from workloads import room_views
             views = room_views(args.seed + rank, n_views=args.batch)
+        if f.endswith("_masks") and masks is None:
+            from workloads import sam_masks
+            masks = sam_masks(scene, overlap=True, seed=args.seed + rank)
         prec = api.FP32 if f.startswith("fp32") else api.FP8 if f == "fp8" else api.BF16
         res[f] = _measure(args, world, rank, local, scene, prec, dist,
-                          views)
+                          views, masks if f.endswith("_masks") else None)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -416,6 +466,12 @@ def run_ours(args, world, rank, local):
         line["forms"]["bf16_batch"]["workload"] = (
             f"{args.batch} keyframes of the room (the new keyframe + {args.batch - 1} history keyframes) "
             "sharing the map and the dictionary, one latentam_step_batch iteration; value = keyframe-iterations/s")
+        for f in ("fp32_masks", "bf16_masks"):
+            line["forms"][f]["workload"] = (
+                f"the room keyframe with SAM-style mask targets ({masks.n_masks} masks: 80x60-pixel cells of "
+                "the surface regions plus the whole regions, overlapping), queries mask-pooled before the "
+                "decode; the roofline is the decode stage on the pooled rows, a small part of this step")
+        line["kmeans"] = _measure_kmeans(args, local, scene, masks)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

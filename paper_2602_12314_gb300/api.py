@@ -581,6 +581,7 @@ class Keyframe:
     F: torch.Tensor
     mask: torch.Tensor
     csr: tuple | None = None  # (offsets, pixels) int32 device tensors when mask-pooled
+    valid_rows: object = None  # host indices of the rows in the loss set (K-means starts)
 
     @property
     def rows(self) -> int:
@@ -592,6 +593,9 @@ class LatentMap:
 
     The map's Gaussians and queries f and the dictionary (K, V) with their Adam moments stay on
     the device.  add_keyframe(camera, targets) runs, for the new keyframe:
+      0. with kmeans: the streaming K-means update of the atoms V from the keyframe's targets
+         (latentam_stream_kmeans, k_micro micro-clusters started at rows drawn by the map's
+         seeded generator; the slots' weights live in `atom_weights`);
       1. the trust-region centre V0 <- V (the dictionary at the start of the keyframe);
       2. the training batch: the new keyframe plus B keyframes sampled from the history;
       3. Stage I: R1 iterations updating f, K and V (the Gaussians' other attributes are fixed);
@@ -601,7 +605,9 @@ class LatentMap:
 
     def __init__(self, ctx: Context, scene, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
                  precision: int = FP32, target_dtype=torch.float32, B: int = 2, R1: int = 1, R2: int = 5,
-                 seed: int = 0):
+                 seed: int = 0, kmeans: bool = False, k_micro: int = 5, kmeans_iters: int = 10):
+        import numpy as np
+
         from .history import KeyframeHistory
 
         dev = torch.device("cuda", ctx.device)
@@ -620,19 +626,34 @@ class LatentMap:
         self.mV, self.vV = torch.zeros_like(self.V), torch.zeros_like(self.V)
         self.d, self.M, self.D = self.f.shape[1], self.V.shape[0], self.V.shape[1]
         self.history = KeyframeHistory(seed)
+        self.kmeans, self.k_micro, self.kmeans_iters = bool(kmeans), int(k_micro), int(kmeans_iters)
+        self.atom_weights = torch.zeros(self.M, dtype=torch.float32, device=dev)  # every slot empty
+        self._rng = np.random.default_rng(seed + 1)
 
     def keyframe(self, camera, F, mask=None, masks=None) -> Keyframe:
         """Device copy of a keyframe: per-pixel targets F (H*W x D) with loss-set mask, or a
         mask set (offsets, pixels, per-mask targets F and flags valid)."""
+        import numpy as np
+
         dev = self.dev
         if masks is not None:
             return Keyframe(camera_struct(camera), _dev_f32(masks.F, dev).to(self.target_dtype).contiguous(),
                             torch.as_tensor(masks.valid, dtype=torch.uint8).to(dev).contiguous(),
-                            _mask_csr(masks.offsets, masks.pixels, dev))
+                            _mask_csr(masks.offsets, masks.pixels, dev), np.flatnonzero(np.asarray(masks.valid)))
         n = camera.width * camera.height
         m = torch.ones(n, dtype=torch.uint8) if mask is None else torch.as_tensor(mask, dtype=torch.uint8)
         return Keyframe(camera_struct(camera), _dev_f32(F, dev).to(self.target_dtype).contiguous(),
-                        m.to(dev).contiguous())
+                        m.to(dev).contiguous(), None, np.flatnonzero(m.numpy()))
+
+    def _update_atoms(self, kf: Keyframe):
+        rows = kf.valid_rows
+        if rows is None or len(rows) == 0:
+            return
+        k = min(self.k_micro, len(rows))
+        init = self._rng.choice(rows, size=k, replace=False).astype("int32")
+        F = kf.F if kf.F.dtype == torch.float32 else kf.F.float()
+        stream_kmeans(self.ctx, F, self.V, self.atom_weights, init, valid=kf.mask, iters_local=self.kmeans_iters,
+                      iters_global=self.kmeans_iters)
 
     def _run(self, batch, iters: int, learn_f: bool):
         if iters <= 0:
@@ -665,6 +686,8 @@ class LatentMap:
         """Algorithm 1's optimisation of one new keyframe; returns the loss of the last Stage I
         and Stage II iterations and the batch size."""
         kf = self.keyframe(camera, F, mask, masks)
+        if self.kmeans:
+            self._update_atoms(kf)
         self.V0.copy_(self.V)
         batch = self.history.batch(kf, self.B)
         l1 = self._run(batch, self.R1, True)

@@ -250,3 +250,27 @@ def test_latent_map_runs_algorithm_1(api, ctx):
     for v in views[:2]:
         r = m3.add_keyframe(v.camera, F=v.F, mask=v.mask)
         assert np.isfinite(r["stage2"]["total"])
+
+
+def test_latent_map_with_streaming_kmeans(api, ctx):
+    """LatentMap with the streaming K-means first step: the atoms' weights count every valid
+    mask seen, the first keyframe's update equals a direct latentam_stream_kmeans call from the
+    same start, and the optimisation runs on the updated atoms."""
+    from workloads import room_views
+    views = room_views(8, n_views=3, n=40_000, width=96, height=72, fx=78.75)
+    mss = [sam_masks(v, cell=(24, 18), seed=k) for k, v in enumerate(views)]
+    m = api.LatentMap(ctx, views[0], B=1, R1=0, R2=1, kmeans=True, seed=5)
+    # the same first update, directly
+    rng = np.random.default_rng(5 + 1)
+    rows = np.flatnonzero(mss[0].valid)
+    init = rng.choice(rows, size=5, replace=False).astype(np.int32)
+    V, w = _dev(views[0].V), torch.zeros(views[0].M, device="cuda")
+    api.stream_kmeans(ctx, _dev(mss[0].F), V, w, init, valid=_dev(mss[0].valid, torch.uint8))
+    m.R2 = 0
+    m.add_keyframe(views[0].camera, masks=mss[0])
+    assert torch.equal(m.V, V) and torch.equal(m.atom_weights, w)
+    m.R2 = 1
+    for v, ms in zip(views[1:], mss[1:]):
+        r = m.add_keyframe(v.camera, masks=ms)
+        assert np.isfinite(r["stage2"]["total"])
+    assert float(m.atom_weights.sum()) == sum(int(ms.valid.sum()) for ms in mss)
