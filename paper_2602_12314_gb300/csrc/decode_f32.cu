@@ -460,13 +460,20 @@ __global__ void finalize_loss(const double* __restrict__ acc, int D, latentam_lo
 constexpr int kGM = 128, kGN = 128, kGK = 16, kGPad = 4;
 
 // Row-major source matrix X (row stride ld); four consecutive elements of a row at a time.
+// The GEMM loads a K slice into registers (load_raw) before computing on the previous one and
+// turns it into operand values (finish) only when it stages them in shared memory, so the
+// loads' latency hides behind the compute.
 struct PlainSrc {
     const float* X;
     int64_t ld, rows, cols;
+    using Raw = float4;
     __device__ __forceinline__ float4 load4(int64_t r, int64_t c) const {
         if (r >= rows || c >= cols) return make_float4(0.f, 0.f, 0.f, 0.f);
         return *reinterpret_cast<const float4*>(X + r * ld + c);
     }
+    __device__ __forceinline__ Raw load_raw(int64_t r, int64_t c) const { return load4(r, c); }
+    static __device__ __forceinline__ Raw zero_raw() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ __forceinline__ float4 finish(const Raw& x) const { return x; }
 };
 
 // dL/dFhat (n x D) formed on load: a_p Fhat_p + b_p F_p with a_p = coef[4p], b_p = coef[4p+1].
@@ -476,12 +483,45 @@ struct DFhatSrc {
     latentam_dtype F_dtype;
     const float* coef;
     int64_t rows, cols;  // n, D
-    __device__ __forceinline__ float4 load4(int64_t r, int64_t c) const {
-        if (r >= rows || c >= cols) return make_float4(0.f, 0.f, 0.f, 0.f);
-        const float a = coef[4 * r], b = coef[4 * r + 1];
-        const float4 h = *reinterpret_cast<const float4*>(Fh + r * cols + c);
-        const float4 f = load_target4(F, F_dtype, (size_t)((r * cols + c) / 4));
-        return make_float4(a * h.x + b * f.x, a * h.y + b * f.y, a * h.z + b * f.z, a * h.w + b * f.w);
+    struct Raw {
+        float4 h;
+        uint4 f;  // four FP32 targets, or four BF16 targets in f.x, f.y
+        float a, b;
+    };
+    __device__ __forceinline__ Raw load_raw(int64_t r, int64_t c) const {
+        Raw x;
+        if (r >= rows || c >= cols) return zero_raw();
+        x.a = coef[4 * r];
+        x.b = coef[4 * r + 1];
+        x.h = *reinterpret_cast<const float4*>(Fh + r * cols + c);
+        const size_t i4 = (size_t)((r * cols + c) / 4);
+        if (F_dtype == LATENTAM_DTYPE_F32) {
+            x.f = reinterpret_cast<const uint4*>(F)[i4];
+        } else {
+            const uint2 u = reinterpret_cast<const uint2*>(F)[i4];
+            x.f = make_uint4(u.x, u.y, 0u, 0u);
+        }
+        return x;
+    }
+    static __device__ __forceinline__ Raw zero_raw() {
+        Raw x;
+        x.h = make_float4(0.f, 0.f, 0.f, 0.f);
+        x.f = make_uint4(0u, 0u, 0u, 0u);
+        x.a = x.b = 0.f;
+        return x;
+    }
+    __device__ __forceinline__ float4 finish(const Raw& x) const {
+        float4 f;
+        if (F_dtype == LATENTAM_DTYPE_F32) {
+            f = make_float4(__uint_as_float(x.f.x), __uint_as_float(x.f.y), __uint_as_float(x.f.z),
+                            __uint_as_float(x.f.w));
+        } else {
+            const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x.f.x));
+            const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x.f.y));
+            f = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+        return make_float4(x.a * x.h.x + x.b * f.x, x.a * x.h.y + x.b * f.y, x.a * x.h.z + x.b * f.z,
+                           x.a * x.h.w + x.b * f.w);
     }
 };
 
@@ -496,7 +536,8 @@ __global__ void __launch_bounds__(256, 2) sgemm_tile(SrcA sa, SrcB sb, int64_t m
     const int64_t m0 = (int64_t)blockIdx.y * kGM, n0 = (int64_t)blockIdx.x * kGN;
     const int64_t kb = (int64_t)blockIdx.z * k_per_split;
     const int64_t ke = min(k_ext, kb + k_per_split);
-    float4 ra[2], rb[2];
+    typename SrcA::Raw ra[2];
+    typename SrcB::Raw rb[2];
     // global -> registers for the K slice starting at k0
     auto fetch = [&](int64_t k0) {
 #pragma unroll
@@ -504,42 +545,43 @@ __global__ void __launch_bounds__(256, 2) sgemm_tile(SrcA sa, SrcB sb, int64_t m
             const int e = t + 256 * i;
             if (A_KM) {
                 const int mm = e >> 2, kq = (e & 3) * 4;
-                ra[i] = (k0 + kq < ke) ? sa.load4(m0 + mm, k0 + kq) : make_float4(0.f, 0.f, 0.f, 0.f);
+                ra[i] = (k0 + kq < ke) ? sa.load_raw(m0 + mm, k0 + kq) : SrcA::zero_raw();
             } else {
                 const int kk = e >> 5, mq = (e & 31) * 4;
-                ra[i] = (k0 + kk < ke) ? sa.load4(k0 + kk, m0 + mq) : make_float4(0.f, 0.f, 0.f, 0.f);
+                ra[i] = (k0 + kk < ke) ? sa.load_raw(k0 + kk, m0 + mq) : SrcA::zero_raw();
             }
             if (B_KM) {
                 const int nn = e >> 2, kq = (e & 3) * 4;
-                rb[i] = (k0 + kq < ke) ? sb.load4(n0 + nn, k0 + kq) : make_float4(0.f, 0.f, 0.f, 0.f);
+                rb[i] = (k0 + kq < ke) ? sb.load_raw(n0 + nn, k0 + kq) : SrcB::zero_raw();
             } else {
                 const int kk = e >> 5, nq = (e & 31) * 4;
-                rb[i] = (k0 + kk < ke) ? sb.load4(k0 + kk, n0 + nq) : make_float4(0.f, 0.f, 0.f, 0.f);
+                rb[i] = (k0 + kk < ke) ? sb.load_raw(k0 + kk, n0 + nq) : SrcB::zero_raw();
             }
         }
     };
-    // registers -> shared buffer `buf`
+    // registers -> operand values -> shared buffer `buf`
     auto stash = [&](int buf) {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int e = t + 256 * i;
+            const float4 va = sa.finish(ra[i]), vb = sb.finish(rb[i]);
             if (A_KM) {
                 const int mm = e >> 2, kq = (e & 3) * 4;
-                sA[buf][kq][mm] = ra[i].x;
-                sA[buf][kq + 1][mm] = ra[i].y;
-                sA[buf][kq + 2][mm] = ra[i].z;
-                sA[buf][kq + 3][mm] = ra[i].w;
+                sA[buf][kq][mm] = va.x;
+                sA[buf][kq + 1][mm] = va.y;
+                sA[buf][kq + 2][mm] = va.z;
+                sA[buf][kq + 3][mm] = va.w;
             } else {
-                *reinterpret_cast<float4*>(&sA[buf][e >> 5][(e & 31) * 4]) = ra[i];
+                *reinterpret_cast<float4*>(&sA[buf][e >> 5][(e & 31) * 4]) = va;
             }
             if (B_KM) {
                 const int nn = e >> 2, kq = (e & 3) * 4;
-                sB[buf][kq][nn] = rb[i].x;
-                sB[buf][kq + 1][nn] = rb[i].y;
-                sB[buf][kq + 2][nn] = rb[i].z;
-                sB[buf][kq + 3][nn] = rb[i].w;
+                sB[buf][kq][nn] = vb.x;
+                sB[buf][kq + 1][nn] = vb.y;
+                sB[buf][kq + 2][nn] = vb.z;
+                sB[buf][kq + 3][nn] = vb.w;
             } else {
-                *reinterpret_cast<float4*>(&sB[buf][e >> 5][(e & 31) * 4]) = rb[i];
+                *reinterpret_cast<float4*>(&sB[buf][e >> 5][(e & 31) * 4]) = vb;
             }
         }
     };
@@ -681,9 +723,23 @@ struct FhatTileEpi {
     };
     static __device__ __forceinline__ void store(const Params& p, int64_t m0, int64_t n0, int ty, int tx,
                                                  float (&acc)[8][8], int64_t m_ext, int64_t n_ext, int) {
+        // four rows at a time: their target loads are issued together, ahead of the stores
+        float4 fr[4][2];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int64_t m = tile_row(m0, ty, i);
+            if ((i & 3) == 0 && p.stats) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t mj = tile_row(m0, ty, i + j);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int64_t c = tile_col(n0, tx) + 64 * h;
+                        fr[j][h] = (mj < m_ext && c < n_ext) ? load_target4(p.F, p.F_dtype, (size_t)((mj * p.D + c) / 4))
+                                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
             float s[4] = {0.f, 0.f, 0.f, 0.f};
             if (m < m_ext) {
 #pragma unroll
@@ -693,7 +749,7 @@ struct FhatTileEpi {
                     const float4 v = make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
                     *reinterpret_cast<float4*>(p.Fh + m * p.D + c) = v;
                     if (p.stats) {
-                        const float4 f = load_target4(p.F, p.F_dtype, (size_t)((m * p.D + c) / 4));
+                        const float4 f = fr[i & 3][h];
                         const float hv[4] = {v.x, v.y, v.z, v.w}, fv[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
@@ -731,19 +787,37 @@ struct DsTileEpi {
     };
     static __device__ __forceinline__ void store(const Params& p, int64_t m0, int64_t n0, int ty, int tx,
                                                  float (&acc)[8][8], int64_t m_ext, int64_t n_ext, int) {
+        // four rows at a time: their attention and coefficient loads are issued together,
+        // ahead of the stores
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t m = tile_row(m0, ty, i);
-            if (m >= m_ext) continue;
-            const float rd = p.coef[4 * m + 2];
+        for (int g = 0; g < 2; ++g) {
+            float4 av[4][2];
+            float rd[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t c = tile_col(n0, tx) + 64 * h;
-                if (c >= n_ext) continue;
-                const float4 a = *reinterpret_cast<const float4*>(p.A + m * p.M + c);
-                *reinterpret_cast<float4*>(p.dS + m * p.M + c) =
-                    make_float4(a.x * (acc[i][4 * h] - rd), a.y * (acc[i][4 * h + 1] - rd), a.z * (acc[i][4 * h + 2] - rd),
-                                a.w * (acc[i][4 * h + 3] - rd));
+            for (int j = 0; j < 4; ++j) {
+                const int64_t m = tile_row(m0, ty, 4 * g + j);
+                rd[j] = m < m_ext ? p.coef[4 * m + 2] : 0.f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t c = tile_col(n0, tx) + 64 * h;
+                    av[j][h] = (m < m_ext && c < n_ext) ? *reinterpret_cast<const float4*>(p.A + m * p.M + c)
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = 4 * g + j;
+                const int64_t m = tile_row(m0, ty, i);
+                if (m >= m_ext) continue;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t c = tile_col(n0, tx) + 64 * h;
+                    if (c >= n_ext) continue;
+                    const float4 a = av[j][h];
+                    *reinterpret_cast<float4*>(p.dS + m * p.M + c) =
+                        make_float4(a.x * (acc[i][4 * h] - rd[j]), a.y * (acc[i][4 * h + 1] - rd[j]),
+                                    a.z * (acc[i][4 * h + 2] - rd[j]), a.w * (acc[i][4 * h + 3] - rd[j]));
+                }
             }
         }
     }
