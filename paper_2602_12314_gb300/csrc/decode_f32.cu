@@ -599,6 +599,7 @@ __global__ void __launch_bounds__(256, 2) sgemm_tile(SrcA sa, SrcB sb, int64_t m
     for (int64_t k0 = kb; k0 < ke; k0 += kGK) {
         const bool more = k0 + kGK < ke;
         if (more) fetch(k0 + kGK);
+        else Epi::prefetch(ep, m0, n0, m_ext, n_ext);
 #pragma unroll
         for (int k = 0; k < kGK; ++k) {
             const float4 a0 = *reinterpret_cast<const float4*>(&sA[buf][k][ty * 4]);
@@ -710,6 +711,20 @@ __global__ void __launch_bounds__(256) sgemm_narrow(PlainSrc sa, PlainSrc sb, in
 __device__ __forceinline__ int64_t tile_row(int64_t m0, int ty, int i) { return m0 + (i < 4 ? ty * 4 + i : 60 + ty * 4 + i); }
 __device__ __forceinline__ int64_t tile_col(int64_t n0, int tx) { return n0 + tx * 4; }  // and + 64
 
+// L2 prefetch of the 128 x 128 block of a row-major matrix (row stride ld elements of `esz`
+// bytes) at (m0, n0), clipped to rows x cols: one 128-byte line per thread and step.
+__device__ __forceinline__ void prefetch_tile_l2(const void* base, int64_t ld, int esz, int64_t m0, int64_t n0,
+                                                 int64_t rows, int64_t cols) {
+    const int lines_per_row = (kGN * esz + 127) / 128;
+    for (int l = threadIdx.x; l < kGM * lines_per_row; l += blockDim.x) {
+        const int64_t r = m0 + l / lines_per_row, c = n0 + (int64_t)(l % lines_per_row) * (128 / esz);
+        if (r < rows && c < cols) {
+            const char* ptr = static_cast<const char*>(base) + (r * ld + c) * esz;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+        }
+    }
+}
+
 // Fhat tile: stored; with `stats`, the per-row partial sums <Fhat,F>, |Fhat|^2, |F|^2,
 // |Fhat - F|^2 over the tile's 128 columns go to stats[(p * tiles + column tile) * 4 ...]
 // (summed in a fixed order later: the result does not depend on the order the tiles run in).
@@ -721,6 +736,12 @@ struct FhatTileEpi {
         latentam_dtype F_dtype;
         float* stats;
     };
+    // the targets the statistics read, while the last K slice computes
+    static __device__ __forceinline__ void prefetch(const Params& p, int64_t m0, int64_t n0, int64_t m_ext,
+                                                    int64_t n_ext) {
+        if (p.stats)
+            prefetch_tile_l2(p.F, p.D, p.F_dtype == LATENTAM_DTYPE_F32 ? 4 : 2, m0, n0, m_ext, n_ext);
+    }
     static __device__ __forceinline__ void store(const Params& p, int64_t m0, int64_t n0, int ty, int tx,
                                                  float (&acc)[8][8], int64_t m_ext, int64_t n_ext, int) {
         // four rows at a time: their target loads are issued together, ahead of the stores
@@ -785,6 +806,14 @@ struct DsTileEpi {
         float* dS;
         int64_t M;
     };
+    static __device__ __forceinline__ void prefetch(const Params& p, int64_t m0, int64_t n0, int64_t m_ext,
+                                                    int64_t n_ext) {
+        prefetch_tile_l2(p.A, p.M, 4, m0, n0, m_ext, n_ext);
+        if (threadIdx.x < kGM * 16 / 128) {
+            const int64_t r = m0 + threadIdx.x * 8;
+            if (r < m_ext) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.coef + 4 * r));
+        }
+    }
     static __device__ __forceinline__ void store(const Params& p, int64_t m0, int64_t n0, int ty, int tx,
                                                  float (&acc)[8][8], int64_t m_ext, int64_t n_ext, int) {
         // four rows at a time: their attention and coefficient loads are issued together,
@@ -831,6 +860,7 @@ struct StoreTileEpi {
         int64_t ld, split_stride;
         float scale;
     };
+    static __device__ __forceinline__ void prefetch(const Params&, int64_t, int64_t, int64_t, int64_t) {}
     static __device__ __forceinline__ void store(const Params& p, int64_t m0, int64_t n0, int ty, int tx,
                                                  float (&acc)[8][8], int64_t m_ext, int64_t n_ext, int z) {
         float* C = p.C + (int64_t)z * p.split_stride;
