@@ -39,10 +39,10 @@ WORKLOAD = ("room keyframe: 300k Gaussians (6x5x3 m room, 20 boxes), 640x480, d=
 SM_FP32_LANES = 128  # FP32 FMA lanes per SM
 
 # DRAM traffic (read + write bytes) of the decode stage per pixel, from one ncu capture of every
-# decode launch of a step (profiles/decode_bf16_tc_crop480x360.md: 1,305 MB over 172,800
+# decode launch of a step (profiles/decode_bf16_tc_crop480x360.md: 1,320 MB over 172,800
 # pixels), keyed by a hash of the kernel sources it was taken on: once they change, the figure
 # no longer describes the kernels and the roofline reports no traffic.
-_DECODE_TRAFFIC = {"bf16": ("5c06c4a7ff178e05", 1305.04e6 / 172800)}
+_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800)}
 _DECODE_SOURCES = ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh")
 
 
