@@ -367,6 +367,68 @@ LATENTAM_API latentam_status latentam_stream_kmeans(latentam_ctx* ctx, const flo
                                                     float* micro_weights, int32_t* micro_assign,
                                                     int32_t* point_assign, latentam_stream stream);
 
+/* ---- voxel-hashed global map and the active local map (Sec. III-E) ----------------------- */
+
+/* The global Gaussian map and its voxel hash, and the local map optimised around the camera.
+ * Every Gaussian of the global store owns the table slot of the voxel floor(p / voxel_size) it
+ * was inserted from (floor of the float32 quotient per axis); the slot of voxel (x, y, z) is
+ * (x 73856093 ^ y 19349663 ^ z 83492791) mod 2^table_log2 on 64-bit two's-complement integers
+ * (the spatial hash of Teschner et al.); the table stores no key, so two voxels with the same
+ * slot collide and the later one counts as occupied; at most one Gaussian per slot.  The store,
+ * the table and the local map live in device memory owned by the map. */
+typedef struct latentam_map latentam_map;
+
+/* The local map (device pointers owned by the map, valid until the next call that changes it):
+ * count rows of means (x3), quats (x4), scales (x3), opacities, queries f (x d) and the Adam
+ * moments of f (x d, zero for rows appended from the store), and gidx, each row's index in the
+ * global store (-1: not in the store). */
+typedef struct {
+    float *means, *quats, *scales, *opacities, *f, *m_f, *v_f;
+    int32_t* gidx;
+    int64_t count;
+} latentam_map_local;
+
+/* The global store (device pointers owned by the map): count rows in index order, and the slot
+ * table of table_size entries (-1 = empty). */
+typedef struct {
+    const float *means, *quats, *scales, *opacities, *f;
+    const int32_t* table;
+    int64_t count, table_size;
+} latentam_map_global;
+
+/* An empty map for queries of dimension d (1..256) with 2^table_log2 slots (4..30), voxel
+ * edge voxel_size (> 0; 0.01 m in the paper) and room for `capacity` Gaussians (grown on
+ * demand).  INVALID_ARG, OUT_OF_MEMORY. */
+LATENTAM_API latentam_status latentam_map_create(latentam_ctx* ctx, int32_t d, int32_t table_log2, float voxel_size,
+                                                 int64_t capacity, latentam_map** out);
+/* Synchronises the device and frees the map.  NULL is accepted. */
+LATENTAM_API latentam_status latentam_map_destroy(latentam_map* map);
+/* Insert-if-free of g->n new Gaussians (device SoA, queries f n x d) in input order: a
+ * Gaussian whose slot is empty takes the next index of the store and the slot, the others are
+ * not inserted (the same result as inserting one at a time).  out_index (device, n, nullable)
+ * receives each Gaussian's new index or -1; n_inserted (host, nullable) the count.
+ * Synchronises the stream.  At most 2^24 Gaussians per call; the store holds up to 2^31 - 1. */
+LATENTAM_API latentam_status latentam_map_insert(latentam_ctx* ctx, latentam_map* map, const latentam_gaussians* g,
+                                                 const float* f, int32_t* out_index, int64_t* n_inserted,
+                                                 latentam_stream stream);
+/* Appends g->n Gaussians created during local mapping to the local map (gidx -1, zero
+ * moments); the next synchronisation inserts them into the store if their slot is free. */
+LATENTAM_API latentam_status latentam_map_add_local(latentam_ctx* ctx, latentam_map* map,
+                                                    const latentam_gaussians* g, const float* f,
+                                                    latentam_stream stream);
+/* The two synchronisation steps around camera position centre (host, 3 floats) with the
+ * active radius: Local -> Global (local Gaussians from the store overwrite their entries, new
+ * ones are inserted if their slot is free), then Global -> Local (local Gaussians with
+ * (dx*dx + dy*dy) + dz*dz > radius*radius in float32 are dropped, the kept ones keep their order
+ * and moments, and the store's Gaussians inside the radius that are not local are appended in
+ * index order).  local_out (host, nullable) receives the new local map.  Synchronises. */
+LATENTAM_API latentam_status latentam_map_sync(latentam_ctx* ctx, latentam_map* map, const float* centre,
+                                               float radius, latentam_map_local* local_out,
+                                               latentam_stream stream);
+/* The current local map / global store (no device work). */
+LATENTAM_API latentam_status latentam_map_local_view(latentam_map* map, latentam_map_local* out);
+LATENTAM_API latentam_status latentam_map_global_view(latentam_map* map, latentam_map_global* out);
+
 /* ---- optimiser ----------------------------------------------------------------------- */
 
 /* One Adam update of `count` tensors in a single launch: params[i], grads[i], m[i], v[i]

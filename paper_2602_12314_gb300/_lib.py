@@ -88,6 +88,16 @@ class BatchFrame(ctypes.Structure):
                 ("mask_offsets", P), ("mask_pixels", P), ("n_mask_entries", I64), ("n_masks", I32)]
 
 
+class MapLocal(ctypes.Structure):
+    _fields_ = [("means", P), ("quats", P), ("scales", P), ("opacities", P), ("f", P), ("m_f", P), ("v_f", P),
+                ("gidx", P), ("count", I64)]
+
+
+class MapGlobal(ctypes.Structure):
+    _fields_ = [("means", P), ("quats", P), ("scales", P), ("opacities", P), ("f", P), ("table", P),
+                ("count", I64), ("table_size", I64)]
+
+
 class Dictionary(ctypes.Structure):
     _fields_ = [("K", P), ("V", P), ("V0", P), ("m_K", P), ("v_K", P), ("m_V", P), ("v_V", P), ("d", I32),
                 ("M", I32), ("D", I32)]
@@ -125,6 +135,13 @@ _SIGS = {
     "latentam_pool_queries": ([P, P, I64, I32, P, P, I64, I32, P, P], I32),
     "latentam_pool_queries_bwd": ([P, P, I32, I32, P, P, I64, I64, P, P], I32),
     "latentam_stream_kmeans": ([P, P, I64, I32, P, P, I32, I32, I32, P, P, I32, P, P, P, P, P], I32),
+    "latentam_map_create": ([P, I32, I32, F32, I64, ctypes.POINTER(P)], I32),
+    "latentam_map_destroy": ([P], I32),
+    "latentam_map_insert": ([P, P, ctypes.POINTER(Gaussians), P, P, ctypes.POINTER(I64), P], I32),
+    "latentam_map_add_local": ([P, P, ctypes.POINTER(Gaussians), P, P], I32),
+    "latentam_map_sync": ([P, P, ctypes.POINTER(F32), F32, ctypes.POINTER(MapLocal), P], I32),
+    "latentam_map_local_view": ([P, ctypes.POINTER(MapLocal)], I32),
+    "latentam_map_global_view": ([P, ctypes.POINTER(MapGlobal)], I32),
     "latentam_adam": ([P, I32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                        ctypes.POINTER(I64), ctypes.POINTER(F32), ctypes.POINTER(AdamCfg), P], I32),
     "latentam_step": ([P, ctypes.POINTER(Frame), ctypes.POINTER(Params), ctypes.POINTER(LossCfg),

@@ -696,5 +696,93 @@ class LatentMap:
         return dict(stage1=l1, stage2=l2, batch=len(batch))
 
 
+class _DeviceArray:
+    """A view of map-owned device memory for torch.as_tensor (no copy)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2}
+
+
+def _device_view(ptr, shape, typestr, dev):
+    if ptr is None or any(s == 0 for s in shape):
+        dt = torch.int32 if typestr == "<i4" else torch.float32
+        return torch.empty(shape, dtype=dt, device=dev)
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=dev)
+
+
+class VoxelMap:
+    """The voxel-hashed global Gaussian map and the active local map (Sec. III-E), held on the
+    device by latentam_map.  The tensors that local() and global_store() return are views of
+    the map's memory, valid until the next call that changes the map."""
+
+    def __init__(self, ctx: Context, d: int, table_log2: int = 24, voxel_size: float = 0.01, capacity: int = 1 << 20):
+        self.ctx, self.d = ctx, int(d)
+        self.dev = torch.device("cuda", ctx.device)
+        h = ctypes.c_void_p()
+        L.check(_lib().latentam_map_create(ctx.handle, self.d, int(table_log2), float(voxel_size), int(capacity),
+                                           ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            _lib().latentam_map_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _gaussians(self, means, quats, scales, opacities, f):
+        t = [_dev_f32(x, self.dev) for x in (means, quats, scales, opacities, f)]
+        return t, _gaussians_struct(*t[:4])
+
+    def insert(self, means, quats, scales, opacities, f):
+        """Insert-if-free in input order; returns (each row's new index or -1, count inserted)."""
+        t, g = self._gaussians(means, quats, scales, opacities, f)
+        out = torch.empty(g.n, dtype=torch.int32, device=self.dev)
+        n = ctypes.c_int64(0)
+        L.check(_lib().latentam_map_insert(self.ctx.handle, self.handle, ctypes.byref(g), _ptr(t[4]), _ptr(out),
+                                           ctypes.byref(n), _stream()))
+        return out, int(n.value)
+
+    def add_local(self, means, quats, scales, opacities, f):
+        t, g = self._gaussians(means, quats, scales, opacities, f)
+        L.check(_lib().latentam_map_add_local(self.ctx.handle, self.handle, ctypes.byref(g), _ptr(t[4]), _stream()))
+        torch.cuda.current_stream().synchronize()
+
+    def _local_dict(self, v: L.MapLocal) -> dict:
+        n, d = int(v.count), self.d
+        out = {k: _device_view(getattr(v, k), (n, w), "<f4", self.dev)
+               for k, w in (("means", 3), ("quats", 4), ("scales", 3), ("f", d), ("m_f", d), ("v_f", d))}
+        out["opacities"] = _device_view(v.opacities, (n,), "<f4", self.dev)
+        out["gidx"] = _device_view(v.gidx, (n,), "<i4", self.dev)
+        return out
+
+    def sync(self, centre, radius: float) -> dict:
+        """Local -> Global then Global -> Local around `centre`; returns the new local map."""
+        c = (ctypes.c_float * 3)(*[float(x) for x in centre])
+        v = L.MapLocal()
+        L.check(_lib().latentam_map_sync(self.ctx.handle, self.handle, c, float(radius), ctypes.byref(v), _stream()))
+        return self._local_dict(v)
+
+    def local(self) -> dict:
+        v = L.MapLocal()
+        L.check(_lib().latentam_map_local_view(self.handle, ctypes.byref(v)))
+        return self._local_dict(v)
+
+    def global_store(self) -> dict:
+        v = L.MapGlobal()
+        L.check(_lib().latentam_map_global_view(self.handle, ctypes.byref(v)))
+        n, d = int(v.count), self.d
+        out = {k: _device_view(getattr(v, k), (n, w), "<f4", self.dev)
+               for k, w in (("means", 3), ("quats", 4), ("scales", 3), ("f", d))}
+        out["opacities"] = _device_view(v.opacities, (n,), "<f4", self.dev)
+        out["table"] = _device_view(v.table, (int(v.table_size),), "<i4", self.dev)
+        return out
+
+
 def default_logit_scale(d: int) -> float:
     return 1.0 / math.sqrt(d)

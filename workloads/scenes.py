@@ -367,3 +367,52 @@ def random_scene(seed: int, n: int, d: int, M: int, D: int, width: int, height: 
     return Scene(name=f"random(seed={seed},N={n},{width}x{height},d={d},M={M},D={D})",
                  means=means, quats=quats, scales=scales, opacities=opac, f=f, K=K, V=V, V0=V.copy(),
                  F=_f32(F), mask=mask, camera=cam)
+
+
+# ----------------------------------------------------------------------------------------
+# Large map: a two-floor building
+# ----------------------------------------------------------------------------------------
+
+def building_gaussians(seed: int = 0, n: int = 2_000_000, d: int = 32, size=(20.0, 15.0, 6.0),
+                       rooms=(4, 3), floors: int = 2) -> dict:
+    """Gaussians of a 20 x 15 x 6 m building with two floors of 4 x 3 rooms: the floor and
+    ceiling slab of every floor and the interior and exterior wall planes (each wall between
+    rooms split by a 1 m door gap), sampled in proportion to surface area.  Per-axis log-normal
+    scales around 1.5 cm (sigma 0.3), random unit quaternions, opacity U(0.3, 0.99), queries
+    ~N(0, 1).  Returns the SoA arrays (float32) of the map."""
+    rng = np.random.default_rng(seed)
+    X, Y, Z = size
+    fh = Z / floors
+    quads = []  # (origin, edge u, edge v)
+    for k in range(floors + 1):
+        quads.append(((0.0, 0.0, k * fh), (X, 0.0, 0.0), (0.0, Y, 0.0)))
+    for k in range(floors):
+        z0 = k * fh
+        for i in range(rooms[0] + 1):
+            x = X * i / rooms[0]
+            for j in range(rooms[1]):
+                y0, y1 = Y * j / rooms[1], Y * (j + 1) / rooms[1]
+                gap = 0 < i < rooms[0]
+                mid = 0.5 * (y0 + y1)
+                segs = [(y0, mid - 0.5), (mid + 0.5, y1)] if gap else [(y0, y1)]
+                for a, b in segs:
+                    quads.append(((x, a, z0), (0.0, b - a, 0.0), (0.0, 0.0, fh)))
+        for j in range(rooms[1] + 1):
+            y = Y * j / rooms[1]
+            for i in range(rooms[0]):
+                x0, x1 = X * i / rooms[0], X * (i + 1) / rooms[0]
+                gap = 0 < j < rooms[1]
+                mid = 0.5 * (x0 + x1)
+                segs = [(x0, mid - 0.5), (mid + 0.5, x1)] if gap else [(x0, x1)]
+                for a, b in segs:
+                    quads.append(((a, y, z0), (b - a, 0.0, 0.0), (0.0, 0.0, fh)))
+    O = np.array([q[0] for q in quads])
+    U = np.array([q[1] for q in quads])
+    V = np.array([q[2] for q in quads])
+    area = np.linalg.norm(np.cross(U, V), axis=1)
+    which = rng.choice(len(quads), size=n, p=area / area.sum())
+    a, b = rng.uniform(size=n), rng.uniform(size=n)
+    means = O[which] + a[:, None] * U[which] + b[:, None] * V[which]
+    scales = np.exp(rng.normal(math.log(0.015), 0.3, size=(n, 3)))
+    return dict(means=_f32(means), quats=random_unit_quats(rng, n), scales=_f32(scales),
+                opacities=_f32(rng.uniform(0.3, 0.99, size=n)), f=_f32(rng.normal(size=(n, d))))
