@@ -601,11 +601,16 @@ class LatentMap:
       3. Stage I: R1 iterations updating f, K and V (the Gaussians' other attributes are fixed);
       4. Stage II: R2 iterations updating K and V with f fixed;
       5. the new keyframe joins the history.
-    Defaults R1 = 1, R2 = 5 (Sec. III-C).  Every iteration goes through latentam_step_batch."""
+    Defaults R1 = 1, R2 = 5 (Sec. III-C).  Every iteration goes through latentam_step_batch.
+    With a voxel_map (a VoxelMap holding the global Gaussian map, Sec. III-E), each keyframe
+    first synchronises the map around its camera centre with the active radius, and the map's
+    local Gaussians, queries and moments are optimised in place (the next synchronisation
+    writes them back); `scene` then supplies only the dictionary."""
 
     def __init__(self, ctx: Context, scene, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
                  precision: int = FP32, target_dtype=torch.float32, B: int = 2, R1: int = 1, R2: int = 5,
-                 seed: int = 0, kmeans: bool = False, k_micro: int = 5, kmeans_iters: int = 10):
+                 seed: int = 0, kmeans: bool = False, k_micro: int = 5, kmeans_iters: int = 10,
+                 voxel_map=None, radius: float = 5.0):
         import numpy as np
 
         from .history import KeyframeHistory
@@ -617,14 +622,18 @@ class LatentMap:
         self.precision, self.target_dtype = int(precision), target_dtype
         self.B, self.R1, self.R2 = int(B), int(R1), int(R2)
         t = lambda a: _dev_f32(a, dev)  # noqa: E731
-        self.geometry = tuple(t(getattr(scene, a)) for a in ("means", "quats", "scales", "opacities"))
-        self.f = t(scene.f)
-        self.m_f, self.v_f = torch.zeros_like(self.f), torch.zeros_like(self.f)
+        self.voxel_map, self.radius = voxel_map, float(radius)
+        if voxel_map is None:
+            self.geometry = tuple(t(getattr(scene, a)) for a in ("means", "quats", "scales", "opacities"))
+            self.f = t(scene.f)
+            self.m_f, self.v_f = torch.zeros_like(self.f), torch.zeros_like(self.f)
+        else:
+            self._use_local(voxel_map.local())
         self.K, self.V = t(scene.K), t(scene.V)
         self.V0 = self.V.clone()
         self.mK, self.vK = torch.zeros_like(self.K), torch.zeros_like(self.K)
         self.mV, self.vV = torch.zeros_like(self.V), torch.zeros_like(self.V)
-        self.d, self.M, self.D = self.f.shape[1], self.V.shape[0], self.V.shape[1]
+        self.d, self.M, self.D = scene.f.shape[1], self.V.shape[0], self.V.shape[1]
         self.history = KeyframeHistory(seed)
         self.kmeans, self.k_micro, self.kmeans_iters = bool(kmeans), int(k_micro), int(kmeans_iters)
         self.atom_weights = torch.zeros(self.M, dtype=torch.float32, device=dev)  # every slot empty
@@ -644,6 +653,16 @@ class LatentMap:
         m = torch.ones(n, dtype=torch.uint8) if mask is None else torch.as_tensor(mask, dtype=torch.uint8)
         return Keyframe(camera_struct(camera), _dev_f32(F, dev).to(self.target_dtype).contiguous(),
                         m.to(dev).contiguous(), None, np.flatnonzero(m.numpy()))
+
+    def _use_local(self, loc: dict):
+        self.geometry = (loc["means"], loc["quats"], loc["scales"], loc["opacities"])
+        self.f, self.m_f, self.v_f = loc["f"], loc["m_f"], loc["v_f"]
+
+    def _sync(self, camera):
+        R = torch.as_tensor(camera.R, dtype=torch.float64)
+        t = torch.as_tensor(camera.t, dtype=torch.float64)
+        centre = (-R.T @ t).tolist()  # the camera centre in world coordinates
+        self._use_local(self.voxel_map.sync(centre, self.radius))
 
     def _update_atoms(self, kf: Keyframe):
         rows = kf.valid_rows
@@ -686,6 +705,8 @@ class LatentMap:
         """Algorithm 1's optimisation of one new keyframe; returns the loss of the last Stage I
         and Stage II iterations and the batch size."""
         kf = self.keyframe(camera, F, mask, masks)
+        if self.voxel_map is not None:
+            self._sync(camera)
         if self.kmeans:
             self._update_atoms(kf)
         self.V0.copy_(self.V)

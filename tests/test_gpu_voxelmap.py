@@ -154,3 +154,32 @@ def test_building_active_set(api, ctx):
         np.testing.assert_array_equal(_np(loc["gidx"]), want.astype(np.int32))
         np.testing.assert_array_equal(_np(loc["f"]), _np(st["f"])[want])
     gm.close()
+
+
+def test_latent_map_optimises_the_active_local_map(api, ctx):
+    """LatentMap over a voxel map (Sec. III-E with Algorithm 1): each keyframe synchronises the
+    map around its camera, the local Gaussians' queries are optimised in place, and the next
+    synchronisation writes them back to the store; Gaussians never in an active set keep their
+    queries."""
+    from workloads import room_views, sam_masks
+    views = room_views(9, n_views=3, n=40_000, width=96, height=72, fx=78.75)
+    s = views[0]
+    vmap = api.VoxelMap(ctx, s.d, table_log2=20, voxel_size=0.01)
+    _, n = vmap.insert(s.means, s.quats, s.scales, s.opacities, s.f)
+    f0 = vmap.global_store()["f"].clone()
+    m = api.LatentMap(ctx, s, B=1, voxel_map=vmap, radius=4.0)
+    seen = set()
+    for v in views:
+        r = m.add_keyframe(v.camera, masks=sam_masks(v, cell=(24, 18)))
+        assert np.isfinite(r["stage1"]["total"]) and np.isfinite(r["stage2"]["total"])
+        loc = vmap.local()
+        centre = -v.camera.R.astype(np.float64).T @ v.camera.t.astype(np.float64)
+        want = np.flatnonzero(vm.in_radius(_np(vmap.global_store()["means"]), centre.astype(np.float32), 4.0))
+        np.testing.assert_array_equal(np.sort(_np(loc["gidx"])), want.astype(np.int32))
+        seen |= set(want.tolist())
+    vmap.sync([100.0, 100.0, 100.0], 0.1)  # write everything back, keep nothing local
+    f1 = _np(vmap.global_store()["f"])
+    changed = np.flatnonzero(np.abs(f1 - _np(f0)).max(axis=1) > 0)
+    # the rendered ones among the active Gaussians learned (the rest of the sphere is out of view)
+    assert len(changed) > 1000 and set(changed.tolist()) <= seen
+    vmap.close()
