@@ -429,6 +429,44 @@ LATENTAM_API latentam_status latentam_map_sync(latentam_ctx* ctx, latentam_map* 
 LATENTAM_API latentam_status latentam_map_local_view(latentam_map* map, latentam_map_local* out);
 LATENTAM_API latentam_status latentam_map_global_view(latentam_map* map, latentam_map_global* out);
 
+/* ---- the full Stage I objective: geometry, colour and depth (Eq. full_obj) ------------- */
+
+/* Weights of Eq. (full_obj) and Eq. (rgb_loss): lambda_rgb (1; the paper gives no value),
+ * lambda_I1 = 0.2, lambda_I2 = 0.8, lambda_d = 0.1 (Sec. IV-A); lambda_f is the feature
+ * loss's own weight (latentam_loss_cfg). */
+typedef struct {
+    float lambda_rgb, lambda_I1, lambda_I2, lambda_d;
+} latentam_image_cfg;
+
+/* Loss parts of latentam_backward_full (device doubles): [0..4] those of
+ * latentam_decode_loss_bwd ([3] = lambda_f L_f), [5] mean |I_hat - I| over pixels and channels,
+ * [6] 1 - mean SSIM (11 x 11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2,
+ * C2 = 0.03^2), [7] L_d = mean |Z_hat - Z| over pixels with an observed depth (Z > 0), [8] their
+ * count, [9] the total lambda_rgb (lambda_I1 [5] + lambda_I2 [6]) + lambda_d [7] + [3]. */
+#define LATENTAM_FULL_LOSS_PARTS 10
+
+/* The gradients of the full Stage I objective of one keyframe with respect to every attribute
+ * of every Gaussian and the dictionary: projection and binning, the render of the queries f,
+ * the colours (n x 3, view-independent) and the camera depth with the same blend (Eq.
+ * alpha_blending), the decode, the feature loss, L_rgb against `image` (H*W x 3 float32, row
+ * y*W + x) and L_d against `depth` (H*W float32, 0 = not observed), then the backward through
+ * the blend (queries, colours, depth channel, opacities, screen means, conics) and the EWA
+ * projection (means, quaternions, scales).  Gradients are written (not accumulated): d_means
+ * (n x 3), d_quats (n x 4; through the normalisation), d_scales (n x 3), d_opacities (n),
+ * d_colours (n x 3), df (n x d), dK, dV; every one of them is required.  loss_parts: device,
+ * LATENTAM_FULL_LOSS_PARTS doubles.  Synchronises once for the pair count. */
+LATENTAM_API latentam_status latentam_backward_full(latentam_ctx* ctx, const latentam_gaussians* g,
+                                                    const float* colours, const float* f, int32_t d,
+                                                    const latentam_camera* cam, const float* K, const float* V,
+                                                    const float* V0, int32_t M, int32_t D, const void* F,
+                                                    latentam_dtype F_dtype, const uint8_t* mask,
+                                                    const float* image, const float* depth,
+                                                    const latentam_loss_cfg* cfg, const latentam_image_cfg* icfg,
+                                                    latentam_precision prec, double* loss_parts, float* d_means,
+                                                    float* d_quats, float* d_scales, float* d_opacities,
+                                                    float* d_colours, float* df, float* dK, float* dV,
+                                                    latentam_stream stream);
+
 /* ---- optimiser ----------------------------------------------------------------------- */
 
 /* One Adam update of `count` tensors in a single launch: params[i], grads[i], m[i], v[i]

@@ -175,5 +175,5 @@ def gradients(scene, colours, image, depth, cfg, **lams) -> dict:
     total.backward()
     out = {k: params[k].grad.numpy().copy() for k in PARAMS}
     out["total"] = float(total.detach())
-    out.update({k: (float(v) if v.dim() == 0 else v.detach().numpy()) for k, v in parts.items()})
+    out.update({k: (float(v.detach()) if v.dim() == 0 else v.detach().numpy()) for k, v in parts.items()})
     return out

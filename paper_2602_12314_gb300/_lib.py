@@ -88,6 +88,13 @@ class BatchFrame(ctypes.Structure):
                 ("mask_offsets", P), ("mask_pixels", P), ("n_mask_entries", I64), ("n_masks", I32)]
 
 
+class ImageCfg(ctypes.Structure):
+    _fields_ = [("lambda_rgb", F32), ("lambda_I1", F32), ("lambda_I2", F32), ("lambda_d", F32)]
+
+
+FULL_LOSS_PARTS = 10
+
+
 class MapLocal(ctypes.Structure):
     _fields_ = [("means", P), ("quats", P), ("scales", P), ("opacities", P), ("f", P), ("m_f", P), ("v_f", P),
                 ("gidx", P), ("count", I64)]
@@ -135,6 +142,9 @@ _SIGS = {
     "latentam_pool_queries": ([P, P, I64, I32, P, P, I64, I32, P, P], I32),
     "latentam_pool_queries_bwd": ([P, P, I32, I32, P, P, I64, I64, P, P], I32),
     "latentam_stream_kmeans": ([P, P, I64, I32, P, P, I32, I32, I32, P, P, I32, P, P, P, P, P], I32),
+    "latentam_backward_full": ([P, ctypes.POINTER(Gaussians), P, P, I32, ctypes.POINTER(Camera), P, P, P, I32, I32,
+                                P, I32, P, P, P, ctypes.POINTER(LossCfg), ctypes.POINTER(ImageCfg), I32, P, P, P, P,
+                                P, P, P, P, P, P], I32),
     "latentam_map_create": ([P, I32, I32, F32, I64, ctypes.POINTER(P)], I32),
     "latentam_map_destroy": ([P], I32),
     "latentam_map_insert": ([P, P, ctypes.POINTER(Gaussians), P, P, ctypes.POINTER(I64), P], I32),

@@ -312,6 +312,87 @@ def stream_kmeans(ctx: Context, F, centres, weights, init_idx, valid=None, iters
     return (mC, mW, ma, pa) if want_micro else None
 
 
+@dataclasses.dataclass
+class ImageConfig:
+    """Weights of Eq. (full_obj) and Eq. (rgb_loss): lambda_rgb (no value in the paper: 1) and
+    lambda_I1 = 0.2, lambda_I2 = 0.8, lambda_d = 0.1 of Sec. IV-A."""
+    lambda_rgb: float = 1.0
+    lambda_I1: float = 0.2
+    lambda_I2: float = 0.8
+    lambda_d: float = 0.1
+
+    def struct(self) -> L.ImageCfg:
+        return L.ImageCfg(self.lambda_rgb, self.lambda_I1, self.lambda_I2, self.lambda_d)
+
+
+def backward_full(ctx: Context, means, quats, scales, opacities, colours, f, camera, K, V, V0, F, mask, image, depth,
+                  cfg: LossConfig | None = None, icfg: ImageConfig | None = None, precision: int = FP32) -> dict:
+    """Gradients of the full Stage I objective (Eq. full_obj) with respect to every Gaussian
+    attribute and the dictionary, and its loss parts (latentam_backward_full)."""
+    cfg, icfg = cfg or LossConfig(), icfg or ImageConfig()
+    dev = torch.device("cuda", ctx.device)
+    t = [_dev_f32(x, dev) for x in (means, quats, scales, opacities, colours, f, K, V, V0, image, depth)]
+    means, quats, scales, opacities, colours, f, K, V, V0, image, depth = t
+    F = F.contiguous() if isinstance(F, torch.Tensor) else _dev_f32(F, dev)
+    m = torch.as_tensor(mask, dtype=torch.uint8).to(dev).contiguous() if mask is not None else None
+    g = _gaussians_struct(means, quats, scales, opacities)
+    cam = camera_struct(camera)
+    out = {k: torch.empty_like(v) for k, v in (("means", means), ("quats", quats), ("scales", scales),
+                                               ("opacities", opacities), ("colours", colours), ("f", f), ("K", K),
+                                               ("V", V))}
+    parts = torch.empty(L.FULL_LOSS_PARTS, dtype=torch.float64, device=dev)
+    cs, ic = cfg.struct(), icfg.struct()
+    L.check(_lib().latentam_backward_full(
+        ctx.handle, ctypes.byref(g), _ptr(colours), _ptr(f), f.shape[1], ctypes.byref(cam), _ptr(K), _ptr(V), _ptr(V0),
+        V.shape[0], V.shape[1], _ptr(F), _target_dtype(F), _ptr(m), _ptr(image), _ptr(depth), ctypes.byref(cs),
+        ctypes.byref(ic), int(precision), _ptr(parts), _ptr(out["means"]), _ptr(out["quats"]), _ptr(out["scales"]),
+        _ptr(out["opacities"]), _ptr(out["colours"]), _ptr(out["f"]), _ptr(out["K"]), _ptr(out["V"]), _stream()))
+    out["parts"] = parts
+    return out
+
+
+class LatentStepFull:
+    """Stage I of Algorithm 1 with the whole objective of Eq. (full_obj): every iteration takes
+    the gradients of latentam_backward_full and one Adam update (latentam_adam) of the means,
+    quaternions, scales, opacities, colours, queries, keys and values.  The Gaussians' stored
+    values are optimised directly (linear scales and opacities; the renderer culls an opacity
+    below 1/255 and uses the scales only through the covariance)."""
+
+    GROUPS = ("means", "quats", "scales", "opacities", "colours", "f", "K", "V")
+    LR = dict(means=1e-4, quats=1e-3, scales=1e-4, opacities=1e-3, colours=2.5e-3, f=0.01, K=0.01, V=0.01)
+
+    def __init__(self, ctx: Context, scene, colours, image, depth, cfg: LossConfig | None = None,
+                 icfg: ImageConfig | None = None, adam_cfg: AdamConfig | None = None, lr: dict | None = None):
+        dev = torch.device("cuda", ctx.device)
+        self.ctx = ctx
+        self.cfg, self.icfg = cfg or LossConfig(), icfg or ImageConfig()
+        self.adam_cfg = adam_cfg or AdamConfig()
+        self.lr = dict(self.LR, **(lr or {}))
+        t = lambda a: _dev_f32(a, dev)  # noqa: E731
+        self.p = dict(means=t(scene.means), quats=t(scene.quats), scales=t(scene.scales),
+                      opacities=t(scene.opacities), colours=t(colours), f=t(scene.f), K=t(scene.K), V=t(scene.V))
+        self.m = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        self.v = {k: torch.zeros_like(v) for k, v in self.p.items()}
+        self.V0, self.F, self.mask = t(scene.V0), t(scene.F), torch.as_tensor(scene.mask, dtype=torch.uint8).to(dev)
+        self.image, self.depth, self.camera = t(image), t(depth), scene.camera
+
+    def step(self, iters: int = 1) -> dict:
+        """`iters` iterations; returns the loss parts of the last one (before its update)."""
+        parts = None
+        for _ in range(iters):
+            p = self.p
+            g = backward_full(self.ctx, p["means"], p["quats"], p["scales"], p["opacities"], p["colours"], p["f"],
+                              self.camera, p["K"], p["V"], self.V0, self.F, self.mask, self.image, self.depth, self.cfg,
+                              self.icfg)
+            parts = g["parts"]
+            adam(self.ctx, [p[k] for k in self.GROUPS], [g[k] for k in self.GROUPS], [self.m[k] for k in self.GROUPS],
+                 [self.v[k] for k in self.GROUPS], [self.lr[k] for k in self.GROUPS], self.adam_cfg)
+            self.adam_cfg.step += 1
+        out = parts.cpu().numpy()
+        return dict(cos=out[0], l2=out[1], tr=out[2], L_f=out[3], n_valid=out[4], l1=out[5], ssim=out[6], L_d=out[7],
+                    n_depth=out[8], total=out[9])
+
+
 def _mask_csr(offsets, pixels, device):
     off = torch.as_tensor(offsets, dtype=torch.int32).to(device).contiguous()
     pix = torch.as_tensor(pixels, dtype=torch.int32).to(device).contiguous()

@@ -799,6 +799,81 @@ latentam_status latentam_adam(latentam_ctx* ctx, int32_t count, float* const* pa
     return launch_adam(ctx, t, count, cfg->beta1, cfg->beta2, cfg->eps, cfg->step, (cudaStream_t)stream);
 }
 
+latentam_status latentam_backward_full(latentam_ctx* ctx, const latentam_gaussians* g, const float* colours,
+                                       const float* f, int32_t d, const latentam_camera* cam, const float* K,
+                                       const float* V, const float* V0, int32_t M, int32_t D, const void* F,
+                                       latentam_dtype F_dtype, const uint8_t* mask, const float* image,
+                                       const float* depth, const latentam_loss_cfg* cfg,
+                                       const latentam_image_cfg* icfg, latentam_precision prec, double* loss_parts,
+                                       float* d_means, float* d_quats, float* d_scales, float* d_opacities,
+                                       float* d_colours, float* df, float* dK, float* dV, latentam_stream stream) {
+    LAT_TRY(enter(ctx));
+    REQUIRE(g && cam && cfg && icfg && loss_parts, "null argument");
+    LAT_TRY(check_camera(cam));
+    LAT_TRY(check_d(d));
+    LAT_TRY(check_dict(M, D));
+    const int N = g->n;
+    REQUIRE(N >= 0, "negative Gaussian count");
+    REQUIRE(K && V && V0 && image && depth && F && dK && dV, "null dictionary, target or gradient");
+    if (N > 0)
+        REQUIRE(g->means && g->quats && g->scales && g->opacities && colours && f && d_means && d_quats &&
+                    d_scales && d_opacities && d_colours && df,
+                "null Gaussian attribute or gradient");
+    REQUIRE(aligned16(f) && aligned16(df), "f and df must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    const int64_t tiles = latentam_num_tiles(cam);
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // projection and bins in the step's buffers
+    const size_t o_xy = 0, o_co = o_xy + up(8 * (size_t)N), o_dp = o_co + up(16 * (size_t)N),
+                 o_rc = o_dp + up(4 * (size_t)N), o_tt = o_rc + up(16 * (size_t)N), o_tr = o_tt + up(4 * (size_t)N),
+                 o_end = o_tr + up(8 * (size_t)tiles);
+    char* pb = static_cast<char*>(ws(ctx, WS_STEP_PROJ, o_end));
+    if (!pb) return LATENTAM_ERR_OUT_OF_MEMORY;
+    latentam_projected proj{reinterpret_cast<float*>(pb + o_xy), reinterpret_cast<float*>(pb + o_co),
+                            reinterpret_cast<float*>(pb + o_dp), reinterpret_cast<int32_t*>(pb + o_rc),
+                            reinterpret_cast<int32_t*>(pb + o_tt)};
+    latentam_bins bins{};
+    bins.tile_ranges = reinterpret_cast<int32_t*>(pb + o_tr);
+    bins.pair_ids = static_cast<int32_t*>(ctx->slot_ptr[WS_STEP_PAIRS]);
+    bins.capacity = (int64_t)(ctx->slot_bytes[WS_STEP_PAIRS] / sizeof(int32_t));
+    const CamParams cp = cam_params(*cam);
+    LAT_TRY(launch_project(*g, cp, proj, st));
+    latentam_status s = bin_and_sort(ctx, N, proj, cp, &bins, st);
+    if (s == LATENTAM_ERR_CAPACITY) {
+        bins.pair_ids = static_cast<int32_t*>(ws(ctx, WS_STEP_PAIRS, sizeof(int32_t) * (size_t)bins.num_pairs));
+        if (!bins.pair_ids) return LATENTAM_ERR_OUT_OF_MEMORY;
+        bins.capacity = bins.num_pairs;
+        s = bin_and_sort(ctx, N, proj, cp, &bins, st);
+    }
+    LAT_TRY(s);
+    // images, their gradients and the screen-space gradients
+    const size_t nn = (size_t)std::max<int64_t>(npix, 1);
+    const size_t i_q = 0, i_c = i_q + up(4 * nn * d), i_z = i_c + up(12 * nn), i_t = i_z + up(4 * nn),
+                 i_n = i_t + up(4 * nn), i_dq = i_n + up(4 * nn), i_dc = i_dq + up(4 * nn * d),
+                 i_dz = i_dc + up(12 * nn), i_g = i_dz + up(4 * nn),
+                 i_end = i_g + up(32 * (size_t)std::max(N, 1));
+    char* ib = static_cast<char*>(ws(ctx, WS_FULL_IMG, i_end));
+    if (!ib) return LATENTAM_ERR_OUT_OF_MEMORY;
+    float* Q = reinterpret_cast<float*>(ib + i_q);
+    float* C = reinterpret_cast<float*>(ib + i_c);
+    float* Z = reinterpret_cast<float*>(ib + i_z);
+    float* T = reinterpret_cast<float*>(ib + i_t);
+    int32_t* nc = reinterpret_cast<int32_t*>(ib + i_n);
+    float* dQ = reinterpret_cast<float*>(ib + i_dq);
+    float* dC = reinterpret_cast<float*>(ib + i_dc);
+    float* dZ = reinterpret_cast<float*>(ib + i_dz);
+    float* dgeo = reinterpret_cast<float*>(ib + i_g);
+    LAT_TRY(launch_render_full(cp, proj, bins, f, d, colours, Q, C, Z, T, nc, st));
+    LAT_TRY(latentam_decode_loss_bwd(ctx, Q, npix, d, K, V, V0, M, D, F, F_dtype, mask, cfg, prec, loss_parts, dQ,
+                                     dK, dV, stream));
+    LAT_TRY(launch_image_loss(ctx, C, Z, image, depth, cam->width, cam->height, *icfg, loss_parts, dC, dZ, st));
+    if (N == 0) return LATENTAM_OK;
+    LAT_TRY(launch_render_bwd_full(cp, proj, bins, f, d, colours, nc, Q, C, Z, dQ, dC, dZ, df, d_colours, dgeo, N,
+                                   st));
+    return launch_project_bwd(*g, cp, dgeo, d_means, d_quats, d_scales, d_opacities, st);
+}
+
 latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, latentam_params* params,
                               const latentam_loss_cfg* cfg, latentam_adam_cfg* adam, int32_t iters, int32_t learn_f,
                               latentam_precision prec, double* loss_host, latentam_stream stream) {

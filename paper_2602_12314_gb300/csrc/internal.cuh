@@ -65,6 +65,8 @@ enum Slot : int {
     WS_PAPER,      // keys, norms, Gram matrix, scaled queries and gradients of the W/D form
     WS_MASKS,      // mask-pooling plan, pooled queries and their gradients
     WS_KMEANS,     // streaming K-means scratch
+    WS_FULL_IMG,   // images and gradients of the full Stage I backward
+    WS_FULL_AUX,   // SSIM maps and loss sums
     WS_NUM_SLOTS
 };
 
@@ -173,6 +175,23 @@ latentam_status launch_render_bwd(const CamParams& cam, const latentam_projected
                                   const latentam_bins& bins, const int32_t* n_contrib,
                                   const float* dQ, int d, float* df, int32_t n, cudaStream_t st,
                                   bool accumulate = false);
+// Queries, colours and depth blended together (Q, C n x 3, Z, T_final, n_contrib).
+latentam_status launch_render_full(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
+                                   const float* f, int d, const float* colours, float* Q, float* C, float* Z,
+                                   float* T_final, int32_t* n_contrib, cudaStream_t st);
+// df, dcol (n x 3) and dgeo (n x 8: d mean2d x, y, d conic a, b, c, d opacity, d depth, -), zeroed
+// first, from the image gradients dQ, dC, dZ and the rendered Q, C, Z.
+latentam_status launch_render_bwd_full(const CamParams& cam, const latentam_projected& proj,
+                                       const latentam_bins& bins, const float* f, int d, const float* colours,
+                                       const int32_t* n_contrib, const float* Q, const float* C, const float* Z,
+                                       const float* dQ, const float* dC, const float* dZ, float* df, float* dcol,
+                                       float* dgeo, int32_t n, cudaStream_t st);
+// L_rgb and L_d with their image gradients; parts[5..9] (parts[3] must hold lambda_f L_f).
+latentam_status launch_image_loss(latentam_ctx* ctx, const float* C, const float* Z, const float* image,
+                                  const float* depth_obs, int W, int H, const latentam_image_cfg& cfg,
+                                  double* parts, float* dC, float* dZ, cudaStream_t st);
+latentam_status launch_project_bwd(const latentam_gaussians& g, const CamParams& cam, const float* dgeo,
+                                   float* dmean, float* dquat, float* dscale, float* dopac, cudaStream_t st);
 // Per-frame buffer `idx` of at least `bytes` (grows like ws()).
 void* frame_ws(latentam_ctx* ctx, int idx, size_t bytes);
 

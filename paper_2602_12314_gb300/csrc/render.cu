@@ -193,6 +193,231 @@ __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, 
     }
 }
 
+// ---- the full Stage I render: queries, colours and depth blended together ---------------
+//
+// The colour c_i (view-independent) and the camera depth z_i of every Gaussian are blended with
+// the same weights as its query (Eq. alpha_blending; the depth image uses the same blend).  The
+// backward adds the gradients of the blend weights: with G = dL/dX the pixel's gradient over all
+// blended channels X, and x_i the channels of contribution i,
+//   dL/dalpha_i = T_i <G, x_i> - (<G, X> - P_i) / (1 - alpha_i),  P_i = sum_{k <= i} w_k <G, x_k>,
+// so one running scalar per pixel replaces the back-to-front pass.  alpha = min(0.99, o e^power)
+// passes dL/dalpha to o (e^power) and to power (alpha) unless it is clamped, and power to the
+// screen mean and the conic.
+
+constexpr int kBatchFull = 128;  // Gaussians staged per round (f rows, colour + depth, geometry)
+
+template <int DQ>
+__global__ void __launch_bounds__(kTilePixels) render_fwd_full_kernel(
+    CamParams cam, const int2* __restrict__ ranges, const int32_t* __restrict__ pair_ids,
+    const float2* __restrict__ xy, const float4* __restrict__ conic_opac, const float4* __restrict__ f,
+    const float* __restrict__ colours, const float* __restrict__ depth, float4* __restrict__ Q,
+    float* __restrict__ C, float* __restrict__ Z, float* __restrict__ T_final, int32_t* __restrict__ n_contrib) {
+    constexpr int DV = DQ / 4;
+    __shared__ float2 s_xy[kBatchFull];
+    __shared__ float4 s_co[kBatchFull];
+    __shared__ float4 s_cz[kBatchFull];
+    __shared__ float4 s_f[kBatchFull][DV];
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int t = threadIdx.x;
+    const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
+    const bool inside = px < cam.W && py < cam.H;
+    const float fpx = (float)px, fpy = (float)py;
+    const int2 range = ranges[tile];
+    float4 acc[DV];
+#pragma unroll
+    for (int k = 0; k < DV; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acz = make_float4(0.f, 0.f, 0.f, 0.f);
+    float T = 1.0f;
+    int count = 0;
+    bool done = !inside;
+    for (int start = range.x; start < range.y; start += kBatchFull) {
+        if (__syncthreads_count(done) == kTilePixels) break;
+        const int k = start + t;
+        if (t < kBatchFull && k < range.y) {
+            const int g = pair_ids[k];
+            s_xy[t] = xy[g];
+            s_co[t] = stage_splat(conic_opac[g]);
+            s_cz[t] = make_float4(colours[3 * g], colours[3 * g + 1], colours[3 * g + 2], depth[g]);
+#pragma unroll
+            for (int c = 0; c < DV; ++c) s_f[t][c] = f[(size_t)g * DV + c];
+        }
+        __syncthreads();
+        const int cnt = min(kBatchFull, range.y - start);
+        for (int j = 0; j < cnt && !done; ++j) {
+            const float alpha = splat_alpha(s_xy[j], s_co[j], fpx, fpy);
+            if (alpha < kAlphaMin) continue;
+            const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+            if (test_T < kTMin) {
+                done = true;
+                break;
+            }
+            const float w = __fmul_rn(alpha, T);
+#pragma unroll
+            for (int c = 0; c < DV; ++c) {
+                const float4 v = s_f[j][c];
+                acc[c].x += w * v.x;
+                acc[c].y += w * v.y;
+                acc[c].z += w * v.z;
+                acc[c].w += w * v.w;
+            }
+            const float4 v = s_cz[j];
+            acz.x += w * v.x;
+            acz.y += w * v.y;
+            acz.z += w * v.z;
+            acz.w += w * v.w;
+            T = test_T;
+            ++count;
+        }
+    }
+    if (inside) {
+        const size_t p = (size_t)py * cam.W + px;
+#pragma unroll
+        for (int c = 0; c < DV; ++c) Q[p * DV + c] = acc[c];
+        C[3 * p] = acz.x;
+        C[3 * p + 1] = acz.y;
+        C[3 * p + 2] = acz.z;
+        Z[p] = acz.w;
+        T_final[p] = T;
+        n_contrib[p] = count;
+    }
+}
+
+// Per-Gaussian gradients: df (N x DQ), dcol (N x 3) and dgeo (N x 8: d mean2d x, y, d conic
+// a, b, c, d opacity, d depth channel, unused), accumulated with one atomic per warp and channel.
+template <int DQ>
+__global__ void __launch_bounds__(kTilePixels) render_bwd_full_kernel(
+    CamParams cam, const int2* __restrict__ ranges, const int32_t* __restrict__ pair_ids,
+    const float2* __restrict__ xy, const float4* __restrict__ conic_opac, const float4* __restrict__ f,
+    const float* __restrict__ colours, const float* __restrict__ depth, const int32_t* __restrict__ n_contrib,
+    const float4* __restrict__ Qf, const float* __restrict__ Cf, const float* __restrict__ Zf,
+    const float4* __restrict__ dQ, const float* __restrict__ dC, const float* __restrict__ dZ,
+    float* __restrict__ df, float* __restrict__ dcol, float* __restrict__ dgeo) {
+    constexpr int DV = DQ / 4;
+    constexpr int NG = DQ / 32 > 0 ? DQ / 32 : 1;
+    __shared__ float2 s_xy[kBatchFull];
+    __shared__ float4 s_co[kBatchFull];
+    __shared__ float4 s_cz[kBatchFull];
+    __shared__ float4 s_f[kBatchFull][DV];
+    __shared__ int s_id[kBatchFull];
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int t = threadIdx.x, lane = t & 31;
+    const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
+    const bool inside = px < cam.W && py < cam.H;
+    const float fpx = (float)px, fpy = (float)py;
+    const int2 range = ranges[tile];
+    float g[DQ];
+    float4 gcz = make_float4(0.f, 0.f, 0.f, 0.f);  // dL/dC (3), dL/dZ
+    float GX = 0.f;
+    int remaining = 0;
+    if (inside) {
+        const size_t p = (size_t)py * cam.W + px;
+#pragma unroll
+        for (int c = 0; c < DV; ++c) {
+            const float4 v = dQ[p * DV + c], q = Qf[p * DV + c];
+            g[4 * c] = v.x;
+            g[4 * c + 1] = v.y;
+            g[4 * c + 2] = v.z;
+            g[4 * c + 3] = v.w;
+            GX += v.x * q.x + v.y * q.y + v.z * q.z + v.w * q.w;
+        }
+        gcz = make_float4(dC[3 * p], dC[3 * p + 1], dC[3 * p + 2], dZ[p]);
+        GX += gcz.x * Cf[3 * p] + gcz.y * Cf[3 * p + 1] + gcz.z * Cf[3 * p + 2] + gcz.w * Zf[p];
+        remaining = n_contrib[p];
+    } else {
+#pragma unroll
+        for (int c = 0; c < DQ; ++c) g[c] = 0.f;
+    }
+    float T = 1.0f, P = 0.0f;
+    bool done = remaining == 0;
+    for (int start = range.x; start < range.y; start += kBatchFull) {
+        if (__syncthreads_count(done) == kTilePixels) break;
+        const int k = start + t;
+        if (t < kBatchFull && k < range.y) {
+            const int gid = pair_ids[k];
+            s_xy[t] = xy[gid];
+            s_co[t] = stage_splat(conic_opac[gid]);
+            s_cz[t] = make_float4(colours[3 * gid], colours[3 * gid + 1], colours[3 * gid + 2], depth[gid]);
+#pragma unroll
+            for (int c = 0; c < DV; ++c) s_f[t][c] = f[(size_t)gid * DV + c];
+            s_id[t] = gid;
+        }
+        __syncthreads();
+        const int cnt = min(kBatchFull, range.y - start);
+        for (int j = 0; j < cnt; ++j) {
+            float w = 0.0f;
+            float geo[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (!done) {
+                const float2 m = s_xy[j];
+                const float4 q = s_co[j];
+                const float dx = __fsub_rn(m.x, fpx), dy = __fsub_rn(m.y, fpy);
+                const float power =
+                    __fmaf_rn(dx, __fmaf_rn(q.x, dx, __fmul_rn(q.y, dy)), __fmul_rn(__fmul_rn(q.z, dy), dy));
+                if (power <= 0.0f) {
+                    const float raw = __fmul_rn(q.w, __expf(power));
+                    const float alpha = fminf(kAlphaMax, raw);
+                    if (alpha >= kAlphaMin) {
+                        const float Tb = T;
+                        w = __fmul_rn(alpha, T);
+                        T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+                        if (--remaining == 0) done = true;
+                        // <G, x_j>
+                        float gx = gcz.x * s_cz[j].x + gcz.y * s_cz[j].y + gcz.z * s_cz[j].z + gcz.w * s_cz[j].w;
+#pragma unroll
+                        for (int c = 0; c < DV; ++c) {
+                            const float4 v = s_f[j][c];
+                            gx += g[4 * c] * v.x + g[4 * c + 1] * v.y + g[4 * c + 2] * v.z + g[4 * c + 3] * v.w;
+                        }
+                        P += w * gx;
+                        const float dalpha = Tb * gx - (GX - P) / (1.0f - alpha);
+                        geo[0] = w * gcz.x;
+                        geo[1] = w * gcz.y;
+                        geo[2] = w * gcz.z;
+                        geo[3] = w * gcz.w;
+                        if (raw <= kAlphaMax) {
+                            const float dpow = dalpha * raw;
+                            const float a = -2.0f * q.x, b = -q.y, cc = -2.0f * q.z;
+                            geo[4] = dpow * (-a * dx - b * dy);  // d mean2d x
+                            geo[5] = dpow * (-b * dx - cc * dy);
+                            geo[6] = dpow * (-0.5f * dx * dx);    // d conic a, b, c
+                            geo[7] = dpow * (-dx * dy);
+                            geo[8] = dpow * (-0.5f * dy * dy);
+                            geo[9] = dalpha * (raw / q.w);         // d opacity
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, w != 0.0f)) {
+                const int gid = s_id[j];
+#pragma unroll
+                for (int grp = 0; grp < NG; ++grp) {
+                    float v[32];
+                    if (DQ >= 32) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) v[c] = w * g[grp * 32 + c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) v[c] = c < DQ ? w * g[c] : 0.0f;
+                    }
+                    const float s = warp_reduce_scatter32(v, lane);
+                    if (lane < (DQ < 32 ? DQ : 32)) atomicAdd(&df[(size_t)gid * DQ + grp * 32 + lane], s);
+                }
+                float v[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) v[c] = c < 10 ? geo[c] : 0.0f;
+                const float s = warp_reduce_scatter32(v, lane);
+                if (lane < 3) atomicAdd(&dcol[(size_t)gid * 3 + lane], s);
+                else if (lane < 10) {
+                    // lanes 3..9: depth channel, mean2d x, y, conic a, b, c, opacity
+                    const int slot = lane == 3 ? 6 : lane - 4;
+                    atomicAdd(&dgeo[(size_t)gid * 8 + slot], s);
+                }
+            }
+        }
+    }
+}
+
 template <int DQ>
 latentam_status render_fwd_t(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
                              const float* f, float* Q, float* T_final, int32_t* n_contrib, cudaStream_t st) {
@@ -232,6 +457,54 @@ latentam_status launch_render_fwd(const CamParams& cam, const latentam_projected
         case 64: return render_fwd_t<64>(cam, proj, bins, f, Q, T_final, n_contrib, st);
         default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
     }
+}
+
+latentam_status launch_render_full(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
+                                   const float* f, int d, const float* colours, float* Q, float* C, float* Z,
+                                   float* T_final, int32_t* n_contrib, cudaStream_t st) {
+    const int tiles = cam.tiles_x * cam.tiles_y;
+    auto args = [&](auto kernel) {
+        kernel<<<tiles, kTilePixels, 0, st>>>(cam, reinterpret_cast<const int2*>(bins.tile_ranges), bins.pair_ids,
+                                              reinterpret_cast<const float2*>(proj.xy),
+                                              reinterpret_cast<const float4*>(proj.conic_opacity),
+                                              reinterpret_cast<const float4*>(f), colours, proj.depth,
+                                              reinterpret_cast<float4*>(Q), C, Z, T_final, n_contrib);
+    };
+    switch (d) {
+        case 16: args(render_fwd_full_kernel<16>); break;
+        case 32: args(render_fwd_full_kernel<32>); break;
+        case 64: args(render_fwd_full_kernel<64>); break;
+        default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    LAT_CHECK_LAUNCH("render_fwd_full_kernel");
+    return LATENTAM_OK;
+}
+
+latentam_status launch_render_bwd_full(const CamParams& cam, const latentam_projected& proj,
+                                       const latentam_bins& bins, const float* f, int d, const float* colours,
+                                       const int32_t* n_contrib, const float* Q, const float* C, const float* Z,
+                                       const float* dQ, const float* dC, const float* dZ, float* df, float* dcol,
+                                       float* dgeo, int32_t n, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(df, 0, sizeof(float) * (size_t)n * d, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dcol, 0, sizeof(float) * (size_t)n * 3, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dgeo, 0, sizeof(float) * (size_t)n * 8, st);
+    if (e != cudaSuccess) return cuda_error(e, "memset full gradients");
+    const int tiles = cam.tiles_x * cam.tiles_y;
+    auto args = [&](auto kernel) {
+        kernel<<<tiles, kTilePixels, 0, st>>>(
+            cam, reinterpret_cast<const int2*>(bins.tile_ranges), bins.pair_ids, reinterpret_cast<const float2*>(proj.xy),
+            reinterpret_cast<const float4*>(proj.conic_opacity), reinterpret_cast<const float4*>(f), colours, proj.depth,
+            n_contrib, reinterpret_cast<const float4*>(Q), C, Z, reinterpret_cast<const float4*>(dQ), dC, dZ, df, dcol,
+            dgeo);
+    };
+    switch (d) {
+        case 16: args(render_bwd_full_kernel<16>); break;
+        case 32: args(render_bwd_full_kernel<32>); break;
+        case 64: args(render_bwd_full_kernel<64>); break;
+        default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+    LAT_CHECK_LAUNCH("render_bwd_full_kernel");
+    return LATENTAM_OK;
 }
 
 latentam_status launch_render_bwd(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
