@@ -398,9 +398,12 @@ typedef struct {
 
 /* An empty map for queries of dimension d (1..256) with 2^table_log2 slots (4..30), voxel
  * edge voxel_size (> 0; 0.01 m in the paper) and room for `capacity` Gaussians (grown on
- * demand).  INVALID_ARG, OUT_OF_MEMORY. */
+ * demand).  host_store != 0 keeps the store's rows in pinned host memory, which the kernels
+ * read and write in place through unified addressing (the slot table and the local map stay
+ * in device memory); the global_view pointers are then host pointers.  INVALID_ARG,
+ * OUT_OF_MEMORY. */
 LATENTAM_API latentam_status latentam_map_create(latentam_ctx* ctx, int32_t d, int32_t table_log2, float voxel_size,
-                                                 int64_t capacity, latentam_map** out);
+                                                 int64_t capacity, int32_t host_store, latentam_map** out);
 /* Synchronises the device and frees the map.  NULL is accepted. */
 LATENTAM_API latentam_status latentam_map_destroy(latentam_map* map);
 /* Insert-if-free of g->n new Gaussians (device SoA, queries f n x d) in input order: a

@@ -145,7 +145,7 @@ _SIGS = {
     "latentam_backward_full": ([P, ctypes.POINTER(Gaussians), P, P, I32, ctypes.POINTER(Camera), P, P, P, I32, I32,
                                 P, I32, P, P, P, ctypes.POINTER(LossCfg), ctypes.POINTER(ImageCfg), I32, P, P, P, P,
                                 P, P, P, P, P, P], I32),
-    "latentam_map_create": ([P, I32, I32, F32, I64, ctypes.POINTER(P)], I32),
+    "latentam_map_create": ([P, I32, I32, F32, I64, I32, ctypes.POINTER(P)], I32),
     "latentam_map_destroy": ([P], I32),
     "latentam_map_insert": ([P, P, ctypes.POINTER(Gaussians), P, P, ctypes.POINTER(I64), P], I32),
     "latentam_map_add_local": ([P, P, ctypes.POINTER(Gaussians), P, P], I32),

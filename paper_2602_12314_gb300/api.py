@@ -813,17 +813,35 @@ def _device_view(ptr, shape, typestr, dev):
     return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=dev)
 
 
+def _host_view(ptr, shape, typestr):
+    """A view of pinned host memory owned by the library (no copy)."""
+    import numpy as np
+
+    count = 1
+    for s_ in shape:
+        count *= s_
+    if ptr is None or count == 0:
+        return torch.empty(shape, dtype=torch.float32)
+    ct = ctypes.c_float if typestr == "<f4" else ctypes.c_int32
+    arr = np.ctypeslib.as_array((ct * count).from_address(int(ptr))).reshape(shape)
+    return torch.from_numpy(arr)
+
+
 class VoxelMap:
     """The voxel-hashed global Gaussian map and the active local map (Sec. III-E), held on the
     device by latentam_map.  The tensors that local() and global_store() return are views of
     the map's memory, valid until the next call that changes the map."""
 
-    def __init__(self, ctx: Context, d: int, table_log2: int = 24, voxel_size: float = 0.01, capacity: int = 1 << 20):
+    def __init__(self, ctx: Context, d: int, table_log2: int = 24, voxel_size: float = 0.01, capacity: int = 1 << 20,
+                 host_store: bool = False):
+        """host_store: the global store's rows in pinned host memory (the slot table and the
+        local map stay on the device); global_store() then returns host tensors."""
         self.ctx, self.d = ctx, int(d)
         self.dev = torch.device("cuda", ctx.device)
+        self.host_store = bool(host_store)
         h = ctypes.c_void_p()
         L.check(_lib().latentam_map_create(ctx.handle, self.d, int(table_log2), float(voxel_size), int(capacity),
-                                           ctypes.byref(h)))
+                                           int(self.host_store), ctypes.byref(h)))
         self.handle = h
 
     def close(self):
@@ -878,10 +896,11 @@ class VoxelMap:
     def global_store(self) -> dict:
         v = L.MapGlobal()
         L.check(_lib().latentam_map_global_view(self.handle, ctypes.byref(v)))
+        torch.cuda.current_stream().synchronize()
         n, d = int(v.count), self.d
-        out = {k: _device_view(getattr(v, k), (n, w), "<f4", self.dev)
-               for k, w in (("means", 3), ("quats", 4), ("scales", 3), ("f", d))}
-        out["opacities"] = _device_view(v.opacities, (n,), "<f4", self.dev)
+        view = _host_view if self.host_store else (lambda p, shape, ts: _device_view(p, shape, ts, self.dev))
+        out = {k: view(getattr(v, k), (n, w), "<f4") for k, w in (("means", 3), ("quats", 4), ("scales", 3), ("f", d))}
+        out["opacities"] = view(v.opacities, (n,), "<f4")
         out["table"] = _device_view(v.table, (int(v.table_size),), "<i4", self.dev)
         return out
 

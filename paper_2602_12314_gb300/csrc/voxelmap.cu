@@ -31,6 +31,7 @@ constexpr int64_t kScanChunk = 1ll << 24;  // the largest exclusive scan one cal
 struct Rows {  // SoA rows of Gaussians (any may be null where not used)
     float *means, *quats, *scales, *opac, *f, *m_f, *v_f;
     int32_t* gidx;
+    bool host;  // pinned host memory (read and written by the kernels through unified addressing)
 };
 
 }  // namespace
@@ -41,6 +42,7 @@ struct latentam_map {
     int table_log2;
     float voxel_size;
     int64_t capacity, count;  // global store (count mirrored on the host)
+    bool host_store;          // the store's rows in pinned host memory
     int32_t* table;           // 2^table_log2 slots, -1 = empty
     int32_t* claim;           // per-slot claims of one insertion, INT_MAX when idle
     int32_t* epoch_mark;      // per global row: the last synchronisation that found it local
@@ -62,14 +64,21 @@ namespace {
 void free_rows(Rows& r) {
     for (void* p : {(void*)r.means, (void*)r.quats, (void*)r.scales, (void*)r.opac, (void*)r.f, (void*)r.m_f,
                     (void*)r.v_f, (void*)r.gidx})
-        if (p) cudaFree(p);
+        if (p) {
+            if (r.host) cudaFreeHost(p);
+            else cudaFree(p);
+        }
     r = Rows{};
 }
 
 // Rows of `cap` Gaussians (moments and gidx only when `local`); the first `keep` rows of `old`
 // are copied over and `old` is freed.
-latentam_status alloc_rows(Rows& r, int64_t cap, int d, bool local, Rows* old, int64_t keep) {
+latentam_status alloc_rows(Rows& r, int64_t cap, int d, bool local, Rows* old, int64_t keep, bool host = false) {
     Rows n{};
+    n.host = host;
+    auto alloc = [&](void** p, size_t bytes) {
+        return host ? cudaHostAlloc(p, bytes, cudaHostAllocMapped) : cudaMalloc(p, bytes);
+    };
     const size_t c = (size_t)std::max<int64_t>(cap, 1);
     struct Field {
         float** dst;
@@ -81,13 +90,13 @@ latentam_status alloc_rows(Rows& r, int64_t cap, int d, bool local, Rows* old, i
                   {&n.v_f, old ? old->v_f : nullptr, local ? d : 0}};
     for (auto& fl : fields) {
         if (fl.w == 0) continue;
-        if (cudaMalloc(fl.dst, sizeof(float) * c * fl.w) != cudaSuccess) {
+        if (alloc(reinterpret_cast<void**>(fl.dst), sizeof(float) * c * fl.w) != cudaSuccess) {
             cudaGetLastError();
             free_rows(n);
             set_error("voxel map: out of device memory for %lld rows", (long long)cap);
             return LATENTAM_ERR_OUT_OF_MEMORY;
         }
-        if (fl.src && keep > 0) cudaMemcpy(*fl.dst, fl.src, sizeof(float) * (size_t)keep * fl.w, cudaMemcpyDeviceToDevice);
+        if (fl.src && keep > 0) cudaMemcpy(*fl.dst, fl.src, sizeof(float) * (size_t)keep * fl.w, cudaMemcpyDefault);
     }
     if (local) {
         if (cudaMalloc(&n.gidx, sizeof(int32_t) * c) != cudaSuccess) {
@@ -113,7 +122,7 @@ latentam_status grow_global(latentam_map* m, int64_t need) {
     const int64_t cap = std::min<int64_t>(INT32_MAX, std::max<int64_t>(need, 2 * m->capacity));
     cudaDeviceSynchronize();
     Rows old = m->g;
-    LAT_TRY(alloc_rows(m->g, cap, m->d, false, &old, m->count));
+    LAT_TRY(alloc_rows(m->g, cap, m->d, false, &old, m->count, m->host_store));
     int32_t* mark = nullptr;
     if (cudaMalloc(&mark, sizeof(int32_t) * (size_t)cap) != cudaSuccess) {
         cudaGetLastError();
@@ -356,7 +365,7 @@ latentam_status enter_map(latentam_ctx* ctx, latentam_map* m) {
 extern "C" {
 
 latentam_status latentam_map_create(latentam_ctx* ctx, int32_t d, int32_t table_log2, float voxel_size,
-                                    int64_t capacity, latentam_map** out) {
+                                    int64_t capacity, int32_t host_store, latentam_map** out) {
     if (!ctx || !out) {
         set_error("null context or output");
         return LATENTAM_ERR_INVALID_ARG;
@@ -375,6 +384,7 @@ latentam_status latentam_map_create(latentam_ctx* ctx, int32_t d, int32_t table_
     m->d = d;
     m->table_log2 = table_log2;
     m->voxel_size = voxel_size;
+    m->host_store = host_store != 0;
     m->epoch = 0;
     const size_t T = (size_t)1 << table_log2;
     bool ok = cudaMalloc(&m->table, sizeof(int32_t) * T) == cudaSuccess &&

@@ -70,13 +70,14 @@ def test_insert_matches_oracle_with_collisions(api, ctx):
     gm.close()
 
 
-def test_sync_sequence_matches_oracle(api, ctx):
+@pytest.mark.parametrize("host_store", [False, True])
+def test_sync_sequence_matches_oracle(api, ctx, host_store):
     """Insert 5,000 Gaussians in a 10 m box, then walk the camera: after each synchronisation
     the local map and the store equal the oracle's; between them the local queries change (what
     an optimiser would do), new local Gaussians appear, and the moments travel with their rows."""
     rng = np.random.default_rng(1)
     d = 16
-    gm = api.VoxelMap(ctx, d, table_log2=16, voxel_size=0.05, capacity=1000)
+    gm = api.VoxelMap(ctx, d, table_log2=16, voxel_size=0.05, capacity=1000, host_store=host_store)
     om = vm.GlobalMap(d, 16, 0.05)
     g0 = _gauss(rng, rng.uniform(-5, 5, size=(5000, 3)), d)
     gm.insert(*_args(g0))
@@ -126,12 +127,14 @@ def test_empty_map_and_zero_radius(api, ctx):
     gm.close()
 
 
-def test_building_active_set(api, ctx):
-    """The two-floor building (2M Gaussians, 1 cm voxels, 2^24 slots): the local map around a
-    camera with the 5 m active radius is exactly the brute-force radius filter of the store,
-    in index order, each row a copy of its store entry."""
+@pytest.mark.parametrize("host_store", [False, True])
+def test_building_active_set(api, ctx, host_store):
+    """The two-floor building (2M Gaussians, 1 cm voxels, 2^24 slots), with the store in HBM or
+    in pinned host memory: the local map around a camera with the 5 m active radius is exactly
+    the brute-force radius filter of the store, in index order, each row a copy of its store
+    entry."""
     g = building_gaussians(0)
-    gm = api.VoxelMap(ctx, 32, table_log2=24, voxel_size=0.01, capacity=1 << 21)
+    gm = api.VoxelMap(ctx, 32, table_log2=24, voxel_size=0.01, capacity=1 << 21, host_store=host_store)
     idx, n = gm.insert(*_args(g))
     idx = _np(idx)
     # into an empty table the winners are the first Gaussian of every occupied slot, in input
