@@ -64,7 +64,7 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--batch", type=int, default=6, help="keyframes of the batched form (B + 1, B = 5 in Sec. IV-A)")
     p.add_argument("--precision", choices=["both", "fp32", "bf16", "fp8", "bf16_batch", "fp32_batch", "fp32_masks",
-                                          "bf16_masks"], default="both",
+                                          "bf16_masks", "fp32_full"], default="both",
                    help="both: the FP32 form is the headline value, the BF16 tensor-core form is reported beside it")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -243,7 +243,7 @@ def decode_flops(n, M, D, d):
     return 6.0 * n * M * D + 6.0 * n * M * d
 
 
-def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None):
+def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None, full=None):
     """Time args.steps steps of one precision form; returns its numbers (rank 0 view).  With
     `views`, a step is one iteration of the batched step over all those keyframes and the
     value counts keyframe-iterations per second.  With `masks`, the step is mask-pooled (one
@@ -256,7 +256,9 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
 
     ctx = api.Context(local)
     target_dtype = torch.float32 if prec == api.FP32 else torch.bfloat16
-    if views is None:
+    if full is not None:  # the whole Stage I objective: geometry, colour and depth too
+        st = api.LatentStepFull(ctx, scene, *full)
+    elif views is None:
         st = api.LatentStep(ctx, scene, precision=prec, target_dtype=target_dtype, masks=masks)
     else:
         st = api.LatentBatchStep(ctx, views, precision=prec, target_dtype=target_dtype)
@@ -300,7 +302,32 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
 
     # ---- end to end through the public API, host buffers ----------------------------------
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and full is not None:
+        host = {k: torch.as_tensor(np.ascontiguousarray(getattr(scene, k)), dtype=torch.float32).pin_memory()
+                for k in ("means", "quats", "scales", "opacities")}
+        host["colours"] = torch.as_tensor(full[0]).pin_memory()
+        tgt = {"F": torch.as_tensor(scene.F, dtype=torch.float32).pin_memory(),
+               "mask": torch.as_tensor(scene.mask, dtype=torch.uint8).pin_memory(),
+               "image": torch.as_tensor(full[1]).pin_memory(), "depth": torch.as_tensor(full[2]).pin_memory()}
+        h2d = sum(t.numel() * t.element_size() for t in list(host.values()) + list(tgt.values()))
+        d2h = 8 * L.FULL_LOSS_PARTS
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            for k, t in host.items():
+                st.p[k].copy_(t, non_blocking=True)
+            for k, t in tgt.items():
+                getattr(st, k).copy_(t, non_blocking=True)
+            st.step(1)  # reads the loss parts back (synchronises)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ems = max_over_ranks(e0.elapsed_time(e1))
+        e2e = {"value": job_throughput(world, n_frames, args.steps, ems), "unit": "iters/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    elif not args.no_e2e:
         if views is None:
             host = {k: torch.as_tensor(np.ascontiguousarray(getattr(scene, k)), dtype=torch.float32).pin_memory()
                     for k in ("means", "quats", "scales", "opacities")}
@@ -338,6 +365,11 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
     n, M, D, d = scene.camera.n_pixels * n_frames, scene.M, scene.D, scene.d
     if masks is not None:
         n = masks.n_masks
+    if full is not None:
+        ctx.close()
+        return {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": int(launches), "e2e": e2e,
+                "keyframes_per_step": n_frames, "roofline": None, "clocks": clk,
+                "stages_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()}, "dtype": "f32"}
     dec_ms, dec_cnt = prof["decode"]
     dec_avg_s = dec_ms / max(dec_cnt, 1) / 1e3
     flops = decode_flops(n, M, D, d)
@@ -415,8 +447,8 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     scene = _scene(args.seed + rank, args.crop)
-    forms = (["fp32", "bf16", "bf16_batch", "fp8", "fp32_masks", "bf16_masks"] if args.precision == "both"
-             else [args.precision])
+    forms = (["fp32", "bf16", "bf16_batch", "fp8", "fp32_masks", "bf16_masks", "fp32_full"]
+             if args.precision == "both" else [args.precision])
     res = {}
     masks = None
     for f in forms:
@@ -427,9 +459,13 @@ def run_ours(args, world, rank, local):
         if f.endswith("_masks") and masks is None:
             from workloads import sam_masks
             masks = sam_masks(scene, overlap=True, seed=args.seed + rank)
+        full = None
+        if f.endswith("_full"):
+            from workloads import room_rgbd
+            full = room_rgbd(args.seed + rank, scene)
         prec = api.FP32 if f.startswith("fp32") else api.FP8 if f == "fp8" else api.BF16
         res[f] = _measure(args, world, rank, local, scene, prec, dist,
-                          views, masks if f.endswith("_masks") else None)
+                          views, masks if f.endswith("_masks") else None, full)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -466,6 +502,11 @@ def run_ours(args, world, rank, local):
         line["forms"]["bf16_batch"]["workload"] = (
             f"{args.batch} keyframes of the room (the new keyframe + {args.batch - 1} history keyframes) "
             "sharing the map and the dictionary, one latentam_step_batch iteration; value = keyframe-iterations/s")
+        line["forms"]["fp32_full"]["workload"] = (
+            "the room keyframe with the whole Stage I objective (Eq. full_obj): queries, colours and depth "
+            "rendered together, feature loss, L1 + SSIM against a ray-cast RGB image, depth L1, gradients of "
+            "every Gaussian attribute and the dictionary, one Adam update of all eight groups (plain launches, "
+            "one host synchronisation per iteration for the pair count)")
         for f in ("fp32_masks", "bf16_masks"):
             line["forms"][f]["workload"] = (
                 f"the room keyframe with SAM-style mask targets ({masks.n_masks} masks: 80x60-pixel cells of "

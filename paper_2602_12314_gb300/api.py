@@ -376,18 +376,22 @@ class LatentStepFull:
         self.V0, self.F, self.mask = t(scene.V0), t(scene.F), torch.as_tensor(scene.mask, dtype=torch.uint8).to(dev)
         self.image, self.depth, self.camera = t(image), t(depth), scene.camera
 
-    def step(self, iters: int = 1) -> dict:
-        """`iters` iterations; returns the loss parts of the last one (before its update)."""
+    def step(self, iters: int = 1, learn_f: bool = True, want_loss: bool = True):
+        """`iters` iterations; returns the loss parts of the last one (before its update), or
+        None when not want_loss.  learn_f = False (Stage II) updates only the dictionary."""
         parts = None
+        groups = self.GROUPS if learn_f else ("K", "V")
         for _ in range(iters):
             p = self.p
             g = backward_full(self.ctx, p["means"], p["quats"], p["scales"], p["opacities"], p["colours"], p["f"],
                               self.camera, p["K"], p["V"], self.V0, self.F, self.mask, self.image, self.depth, self.cfg,
                               self.icfg)
             parts = g["parts"]
-            adam(self.ctx, [p[k] for k in self.GROUPS], [g[k] for k in self.GROUPS], [self.m[k] for k in self.GROUPS],
-                 [self.v[k] for k in self.GROUPS], [self.lr[k] for k in self.GROUPS], self.adam_cfg)
+            adam(self.ctx, [p[k] for k in groups], [g[k] for k in groups], [self.m[k] for k in groups],
+                 [self.v[k] for k in groups], [self.lr[k] for k in groups], self.adam_cfg)
             self.adam_cfg.step += 1
+        if not want_loss or parts is None:
+            return None
         out = parts.cpu().numpy()
         return dict(cos=out[0], l2=out[1], tr=out[2], L_f=out[3], n_valid=out[4], l1=out[5], ssim=out[6], L_d=out[7],
                     n_depth=out[8], total=out[9])

@@ -838,13 +838,20 @@ latentam_status latentam_backward_full(latentam_ctx* ctx, const latentam_gaussia
     bins.pair_ids = static_cast<int32_t*>(ctx->slot_ptr[WS_STEP_PAIRS]);
     bins.capacity = (int64_t)(ctx->slot_bytes[WS_STEP_PAIRS] / sizeof(int32_t));
     const CamParams cp = cam_params(*cam);
-    LAT_TRY(launch_project(*g, cp, proj, st));
-    latentam_status s = bin_and_sort(ctx, N, proj, cp, &bins, st);
-    if (s == LATENTAM_ERR_CAPACITY) {
-        bins.pair_ids = static_cast<int32_t*>(ws(ctx, WS_STEP_PAIRS, sizeof(int32_t) * (size_t)bins.num_pairs));
-        if (!bins.pair_ids) return LATENTAM_ERR_OUT_OF_MEMORY;
-        bins.capacity = bins.num_pairs;
+    {
+        StageTimer tm(ctx, LATENTAM_STAGE_PROJECT, st);
+        LAT_TRY(launch_project(*g, cp, proj, st));
+    }
+    latentam_status s;
+    {
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
         s = bin_and_sort(ctx, N, proj, cp, &bins, st);
+        if (s == LATENTAM_ERR_CAPACITY) {
+            bins.pair_ids = static_cast<int32_t*>(ws(ctx, WS_STEP_PAIRS, sizeof(int32_t) * (size_t)bins.num_pairs));
+            if (!bins.pair_ids) return LATENTAM_ERR_OUT_OF_MEMORY;
+            bins.capacity = bins.num_pairs;
+            s = bin_and_sort(ctx, N, proj, cp, &bins, st);
+        }
     }
     LAT_TRY(s);
     // images, their gradients and the screen-space gradients
@@ -864,9 +871,14 @@ latentam_status latentam_backward_full(latentam_ctx* ctx, const latentam_gaussia
     float* dC = reinterpret_cast<float*>(ib + i_dc);
     float* dZ = reinterpret_cast<float*>(ib + i_dz);
     float* dgeo = reinterpret_cast<float*>(ib + i_g);
-    LAT_TRY(launch_render_full(cp, proj, bins, f, d, colours, Q, C, Z, T, nc, st));
+    {
+        StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, st);
+        LAT_TRY(launch_render_full(cp, proj, bins, f, d, colours, Q, C, Z, T, nc, st));
+    }
     LAT_TRY(latentam_decode_loss_bwd(ctx, Q, npix, d, K, V, V0, M, D, F, F_dtype, mask, cfg, prec, loss_parts, dQ,
                                      dK, dV, stream));
+    // the image losses and the geometry backward count as the render backward stage
+    StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, st);
     LAT_TRY(launch_image_loss(ctx, C, Z, image, depth, cam->width, cam->height, *icfg, loss_parts, dC, dZ, st));
     if (N == 0) return LATENTAM_OK;
     LAT_TRY(launch_render_bwd_full(cp, proj, bins, f, d, colours, nc, Q, C, Z, dQ, dC, dZ, df, d_colours, dgeo, N,

@@ -203,6 +203,11 @@ def _room_faces(rng, size, n_boxes):
 
 def _raycast_labels(cam: Camera, size, boxes, n_boxes):
     """Segment id of the first analytic surface hit by each pixel's ray (-1 if none)."""
+    return _raycast(cam, size, boxes, n_boxes)[0]
+
+
+def _raycast(cam: Camera, size, boxes, n_boxes):
+    """Segment id and camera depth (0 if none) of the first surface hit by each pixel's ray."""
     H, W = cam.height, cam.width
     ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
     dirc = np.stack([(xs - cam.cx) / cam.fx, (ys - cam.cy) / cam.fy, np.ones_like(xs)], -1).reshape(-1, 3)
@@ -238,7 +243,9 @@ def _raycast_labels(cam: Camera, size, boxes, n_boxes):
             upd = ok & (tmin < best_t)
             best_t[upd] = tmin[upd]
             label[upd] = b
-    return label
+    # the ray direction has camera-space z = 1, so the hit parameter is the camera depth
+    depth = np.where(np.isfinite(best_t), best_t, 0.0)
+    return label, depth
 
 
 def room_scene(seed: int = 0, n: int = 300_000, d: int = 32, M: int = 256, D: int = 512,
@@ -289,6 +296,22 @@ def room_scene(seed: int = 0, n: int = 300_000, d: int = 32, M: int = 256, D: in
                  means=_f32(means), quats=_f32(quats), scales=_f32(scales), opacities=_f32(opac),
                  f=_f32(f), K=K, V=V, V0=V.copy(), F=_f32(F), mask=mask, camera=cam,
                  labels=label.astype(np.int32))
+
+
+def room_rgbd(seed: int, scene: Scene, n_boxes: int = 20, size=(6.0, 5.0, 3.0), noise: float = 0.02):
+    """Observed RGB-D of a room keyframe (the photometric and depth targets of the full Stage I
+    objective): every surface segment a random colour, plus N(0, noise^2) per channel, clipped
+    to [0, 1]; the ray-cast camera depth (0 where no surface is hit).  Also random initial
+    Gaussian colours U(0, 1).  `seed` must be the seed the room was drawn with."""
+    rng0 = np.random.default_rng(seed)
+    _, boxes = _room_faces(rng0, size, n_boxes)
+    label, depth = _raycast(scene.camera, size, boxes, n_boxes)
+    rng = np.random.default_rng(seed + 3000)
+    seg = rng.uniform(0.0, 1.0, size=(n_boxes + 12, 3))
+    image = np.clip(seg[np.maximum(label, 0)] + rng.normal(0.0, noise, size=(label.shape[0], 3)), 0.0, 1.0)
+    image[label < 0] = 0.0
+    colours = rng.uniform(0.0, 1.0, size=(scene.n, 3))
+    return _f32(colours), _f32(image), _f32(depth)
 
 
 def room_views(seed: int = 0, n_views: int = 6, n: int = 300_000, d: int = 32, M: int = 256, D: int = 512,
