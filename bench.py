@@ -39,18 +39,19 @@ WORKLOAD = ("room keyframe: 300k Gaussians (6x5x3 m room, 20 boxes), 640x480, d=
 SM_FP32_LANES = 128  # FP32 FMA lanes per SM
 
 # DRAM traffic (read + write bytes) of the decode stage per pixel, from one ncu capture of every
-# decode launch of a step (profiles/decode_bf16_tc_crop480x360.md: 1,320 MB over 172,800
-# pixels), keyed by a hash of the kernel sources it was taken on: once they change, the figure
-# no longer describes the kernels and the roofline reports no traffic.
-_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800)}
-_DECODE_SOURCES = ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh")
+# decode launch of a step on the 480x360 crop (profiles/decode_bf16_tc_crop480x360.md: 1,320 MB
+# over 172,800 pixels; profiles/decode_fp32_crop480x360.md: 3,369 MB), keyed by a hash of the
+# kernel sources it was taken on: once they change, the figure no longer describes the kernels
+# and the roofline reports no traffic.
+_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800), "fp32": ("16daa1049514a475", 3368.56e6 / 172800)}
+_DECODE_SOURCES = {"bf16": ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh"), "fp32": ("decode_f32.cu",)}
 
 
-def _decode_sources_hash():
+def _decode_sources_hash(form="bf16"):
     import hashlib
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2602_12314_gb300", "csrc")
     h = hashlib.sha256()
-    for f in _DECODE_SOURCES:
+    for f in _DECODE_SOURCES[form]:
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -377,15 +378,21 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
     if prec == api.FP32:
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = props.multi_processor_count * SM_FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "decode stage (dec_rows_fwd + dec_rows_bwd + atb_splitk)",
+        key, per_pixel = _DECODE_TRAFFIC["fp32"]
+        traffic = per_pixel * n if key == _decode_sources_hash("fp32") and masks is None else None
+        roof = {"bound": "alu", "kernel": "decode stage (dec_rows_fwd, sgemm_tile x3, coef_rows, sgemm_narrow x2, "
+                                          "reduce_splits x2)",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x {SM_FP32_LANES} lanes x 2 x "
                                f"{sm_mhz:.0f} MHz (max SM clock)",
-                "traffic": None, "algorithmic_per_launch": flops}
+                "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of every decode launch of one "
+                                  "step on the 480x360 crop, scaled by pixel count" if traffic else None,
+                "algorithmic_per_launch": flops}
     else:
         peak = float(peaks["bf16_tflops_sustained"])
         key, per_pixel = _DECODE_TRAFFIC["bf16"]
-        traffic = per_pixel * n if key == _decode_sources_hash() and prec == api.BF16 else None
+        traffic = per_pixel * n if key == _decode_sources_hash("bf16") and prec == api.BF16 and masks is None else None
         roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 GEMM kernels + their epilogues)",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"bf16 sustained, {peak_src}" + (
