@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define LATENTAM_TILE 16
-#define LATENTAM_ABI_VERSION 2
+#define LATENTAM_ABI_VERSION 3
 
 typedef int32_t latentam_status;
 #define LATENTAM_OK 0
@@ -500,7 +500,11 @@ typedef struct {
 } latentam_frame;
 
 /* Learnable state: queries f (N x d) and dictionary K (M x d), V (M x D), the trust-region
- * centre V0 (M x D), and the Adam moments of each (same shapes). */
+ * centre V0 (M x D), and the Adam moments of each (same shapes).  tau > 0 selects the paper's
+ * own parameterisation (Sec. III-B, the decode of latentam_decode_loss_bwd_paper with
+ * temperature tau): K then holds the projection W (d x D, moments likewise) and V the atoms
+ * D (M x D); tau = 0 (the zero-initialised struct) is the free-key decode with logit scale
+ * cfg->logit_scale. */
 typedef struct {
     float* f;
     float* K;
@@ -508,6 +512,7 @@ typedef struct {
     const float* V0;
     float *m_f, *v_f, *m_K, *v_K, *m_V, *v_V;
     int32_t d, M, D;
+    float tau;
 } latentam_params;
 
 /* `iters` iterations of: render (Q from f) -> decode + loss -> backward -> Adam on
@@ -545,13 +550,15 @@ typedef struct {
 } latentam_batch_frame;
 
 /* The dictionary shared by every frame: keys K (M x d), values V (M x D), trust-region centre
- * V0 (M x D) and the Adam moments of K and V. */
+ * V0 (M x D) and the Adam moments of K and V; tau as in latentam_params (K = W, d x D, when
+ * tau > 0). */
 typedef struct {
     float* K;
     float* V;
     const float* V0;
     float *m_K, *v_K, *m_V, *v_V;
     int32_t d, M, D;
+    float tau;
 } latentam_dictionary;
 
 /* `iters` iterations over a batch of n_frames (1..LATENTAM_MAX_BATCH) keyframes that share the

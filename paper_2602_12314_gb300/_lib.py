@@ -24,7 +24,7 @@ ERR_TIMEOUT = -6
 _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED_SHAPE", -3: "OUT_OF_MEMORY", -4: "CUDA", -5: "CAPACITY",
           -6: "TIMEOUT"}
 
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 PREC_FP32 = 0
 PREC_BF16 = 1
@@ -80,7 +80,7 @@ class Frame(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("f", P), ("K", P), ("V", P), ("V0", P), ("m_f", P), ("v_f", P), ("m_K", P), ("v_K", P),
-                ("m_V", P), ("v_V", P), ("d", I32), ("M", I32), ("D", I32)]
+                ("m_V", P), ("v_V", P), ("d", I32), ("M", I32), ("D", I32), ("tau", F32)]
 
 
 class BatchFrame(ctypes.Structure):
@@ -107,7 +107,7 @@ class MapGlobal(ctypes.Structure):
 
 class Dictionary(ctypes.Structure):
     _fields_ = [("K", P), ("V", P), ("V0", P), ("m_K", P), ("v_K", P), ("m_V", P), ("v_V", P), ("d", I32),
-                ("M", I32), ("D", I32)]
+                ("M", I32), ("D", I32), ("tau", F32)]
 
 
 MAX_BATCH = 32

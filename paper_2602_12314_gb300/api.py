@@ -526,9 +526,11 @@ class LatentStep:
     latentam_step."""
 
     def __init__(self, ctx: Context, scene, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
-                 precision: int = FP32, target_dtype=torch.float32, masks=None):
+                 precision: int = FP32, target_dtype=torch.float32, masks=None, tau: float = 0.0, W=None):
         """`masks` (optional; offsets, pixels, per-mask targets F and flags valid, as
-        workloads.MaskSet): the mask-pooled step, one decoded row and target per mask."""
+        workloads.MaskSet): the mask-pooled step, one decoded row and target per mask.
+        tau > 0: the paper's cosine / temperature decode, with the projection W (d x D,
+        required) held in K and the atoms D in V."""
         dev = torch.device("cuda", ctx.device)
         self.ctx = ctx
         self.cfg = cfg or LossConfig()
@@ -538,6 +540,11 @@ class LatentStep:
         self.means, self.quats, self.scales, self.opacities = (t(scene.means), t(scene.quats), t(scene.scales),
                                                                t(scene.opacities))
         self.f, self.K, self.V, self.V0 = t(scene.f), t(scene.K), t(scene.V), t(scene.V0)
+        self.tau = float(tau)
+        if self.tau > 0:
+            if W is None:
+                raise ValueError("the paper's form needs the projection W (d x D)")
+            self.K = t(W)
         self.mask_offsets = self.mask_pixels = None
         if masks is None:
             self.F = t(scene.F).to(target_dtype).contiguous()
@@ -571,6 +578,7 @@ class LatentStep:
         p.m_f, p.v_f, p.m_K, p.v_K, p.m_V, p.v_V = (m["f"].data_ptr(), m["vf"].data_ptr(), m["K"].data_ptr(),
                                                     m["vK"].data_ptr(), m["V"].data_ptr(), m["vV"].data_ptr())
         p.d, p.M, p.D = self.d, self.M, self.D
+        p.tau = self.tau
         return p
 
     def step(self, iters: int = 1, learn_f: bool = True, want_loss: bool = True):
@@ -595,9 +603,9 @@ class LatentBatchStep:
     Scenes whose query arrays are the same object render one shared query tensor."""
 
     def __init__(self, ctx: Context, scenes, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
-                 precision: int = FP32, target_dtype=torch.float32, masks=None):
+                 precision: int = FP32, target_dtype=torch.float32, masks=None, tau: float = 0.0, W=None):
         """`masks` (optional): one mask set per scene (workloads.MaskSet layout), the
-        mask-pooled batch."""
+        mask-pooled batch.  tau > 0 and W: the paper's decode, as in LatentStep."""
         if not 1 <= len(scenes) <= L.MAX_BATCH:
             raise ValueError(f"a batch holds 1..{L.MAX_BATCH} keyframes")
         dev = torch.device("cuda", ctx.device)
@@ -608,6 +616,11 @@ class LatentBatchStep:
         t = lambda a: _dev_f32(a, dev)  # noqa: E731
         s0 = scenes[0]
         self.K, self.V, self.V0 = t(s0.K), t(s0.V), t(s0.V0)
+        self.tau = float(tau)
+        if self.tau > 0:
+            if W is None:
+                raise ValueError("the paper's form needs the projection W (d x D)")
+            self.K = t(W)
         self.mK, self.vK = torch.zeros_like(self.K), torch.zeros_like(self.K)
         self.mV, self.vV = torch.zeros_like(self.V), torch.zeros_like(self.V)
         self.d, self.M, self.D = s0.f.shape[1], self.V.shape[0], self.V.shape[1]
@@ -645,7 +658,7 @@ class LatentBatchStep:
                 fr[k].mask_offsets, fr[k].mask_pixels = off.data_ptr(), pix.data_ptr()
                 fr[k].n_mask_entries, fr[k].n_masks = pix.numel(), off.numel() - 1
         dic = L.Dictionary(self.K.data_ptr(), self.V.data_ptr(), self.V0.data_ptr(), self.mK.data_ptr(),
-                           self.vK.data_ptr(), self.mV.data_ptr(), self.vV.data_ptr(), self.d, self.M, self.D)
+                           self.vK.data_ptr(), self.mV.data_ptr(), self.vV.data_ptr(), self.d, self.M, self.D, self.tau)
         cs = self.cfg.struct()
         ac = self.adam_cfg.struct()
         out = (ctypes.c_double * L.LOSS_PARTS)() if want_loss else None
@@ -695,7 +708,7 @@ class LatentMap:
     def __init__(self, ctx: Context, scene, cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
                  precision: int = FP32, target_dtype=torch.float32, B: int = 2, R1: int = 1, R2: int = 5,
                  seed: int = 0, kmeans: bool = False, k_micro: int = 5, kmeans_iters: int = 10,
-                 voxel_map=None, radius: float = 5.0):
+                 voxel_map=None, radius: float = 5.0, tau: float = 0.0, W=None):
         import numpy as np
 
         from .history import KeyframeHistory
@@ -715,6 +728,11 @@ class LatentMap:
         else:
             self._use_local(voxel_map.local())
         self.K, self.V = t(scene.K), t(scene.V)
+        self.tau = float(tau)
+        if self.tau > 0:  # the paper's decode: K holds the projection W, V the atoms D
+            if W is None:
+                raise ValueError("the paper's form needs the projection W (d x D)")
+            self.K = t(W)
         self.V0 = self.V.clone()
         self.mK, self.vK = torch.zeros_like(self.K), torch.zeros_like(self.K)
         self.mV, self.vV = torch.zeros_like(self.V), torch.zeros_like(self.V)
@@ -777,7 +795,7 @@ class LatentMap:
         F = torch.cat([k.F for k in batch]).contiguous()
         mask = torch.cat([k.mask for k in batch]).contiguous()
         dic = L.Dictionary(self.K.data_ptr(), self.V.data_ptr(), self.V0.data_ptr(), self.mK.data_ptr(),
-                           self.vK.data_ptr(), self.mV.data_ptr(), self.vV.data_ptr(), self.d, self.M, self.D)
+                           self.vK.data_ptr(), self.mV.data_ptr(), self.vV.data_ptr(), self.d, self.M, self.D, self.tau)
         cs, ac = self.cfg.struct(), self.adam_cfg.struct()
         out = (ctypes.c_double * L.LOSS_PARTS)()
         L.check(_lib().latentam_step_batch(self.ctx.handle, fr, len(batch), _ptr(F), _target_dtype(F), _ptr(mask),

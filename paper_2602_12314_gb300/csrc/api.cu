@@ -901,6 +901,10 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
             "null parameter or moment");
     cudaStream_t st = (cudaStream_t)stream;
     const int d = params->d, M = params->M, D = params->D;
+    const float tau = params->tau;
+    REQUIRE(tau >= 0.f && isfinite(tau), "tau=%g must be 0 (free keys) or positive", (double)tau);
+    const bool paper = tau > 0.f;
+    const int64_t ksize = paper ? (int64_t)d * D : (int64_t)M * d;  // K holds W (d x D) in the paper form
     const int N = g.n;
     const latentam_camera& cam = frame->camera;
     const int64_t npix = (int64_t)cam.width * cam.height;
@@ -945,7 +949,7 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
     const size_t i_q = 0, i_t = i_q + up(4 * (size_t)npix * d), i_n = i_t + up(4 * (size_t)npix),
                  i_dq = i_n + up(4 * (size_t)npix), i_end = i_dq + up(4 * (size_t)npix * d);
     char* ib = static_cast<char*>(ws(ctx, WS_STEP_IMG, i_end));
-    const size_t g_df = 0, g_dk = g_df + up(4 * (size_t)N * d), g_dv = g_dk + up(4 * (size_t)M * d),
+    const size_t g_df = 0, g_dk = g_df + up(4 * (size_t)N * d), g_dv = g_dk + up(4 * (size_t)ksize),
                  g_lp = g_dv + up(4 * (size_t)M * D), g_end = g_lp + up(8 * LATENTAM_LOSS_PARTS);
     char* gb = static_cast<char*>(ws(ctx, WS_STEP_GRAD, g_end));
     if (!ib || !gb) return LATENTAM_ERR_OUT_OF_MEMORY;
@@ -984,9 +988,14 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
             LAT_TRY(launch_render_fwd(cp, proj, bins, params->f, d, Q, T, nc, s));
             if (pooled) LAT_TRY(launch_pool_fwd(plan, Q, d, Qm, s));
         }
-        LAT_TRY(latentam_decode_loss_bwd(ctx, Qdec, ndec, d, params->K, params->V, params->V0, M, D, frame->F,
-                                         frame->F_dtype, frame->mask, cfg, prec, lp,
-                                         learn_f ? (pooled ? dQm : dQ) : nullptr, dK, dV, s));
+        float* dQd = learn_f ? (pooled ? dQm : dQ) : nullptr;
+        if (paper)
+            LAT_TRY(latentam_decode_loss_bwd_paper(ctx, Qdec, ndec, d, params->K, params->V, params->V0, M, D, tau,
+                                                   frame->F, frame->F_dtype, frame->mask, cfg, prec, lp, dQd, dK, dV,
+                                                   s));
+        else
+            LAT_TRY(latentam_decode_loss_bwd(ctx, Qdec, ndec, d, params->K, params->V, params->V0, M, D, frame->F,
+                                             frame->F_dtype, frame->mask, cfg, prec, lp, dQd, dK, dV, s));
         if (learn_f && N > 0) {
             StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, s);
             if (pooled) LAT_TRY(launch_pool_bwd(plan, dQm, d, dQ, s));
@@ -995,7 +1004,7 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
         AdamTensor t[3];
         int cnt = 0;
         if (learn_f) t[cnt++] = AdamTensor{params->f, df, params->m_f, params->v_f, (int64_t)N * d, adam->lr_f};
-        t[cnt++] = AdamTensor{params->K, dK, params->m_K, params->v_K, (int64_t)M * d, adam->lr_dict};
+        t[cnt++] = AdamTensor{params->K, dK, params->m_K, params->v_K, ksize, adam->lr_dict};
         t[cnt++] = AdamTensor{params->V, dV, params->m_V, params->v_V, (int64_t)M * D, adam->lr_dict};
         StageTimer tm(ctx, LATENTAM_STAGE_ADAM, s);
         if (step_dev) LAT_TRY(launch_step_advance(const_cast<int*>(step_dev), s));
@@ -1015,7 +1024,7 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
         for (int64_t x : ints) key.add((uint64_t)x);
         key.add_camera(cam);
         for (float f : {cfg->lambda_f, cfg->lambda_cos, cfg->lambda_2, cfg->lambda_D, cfg->delta, cfg->logit_scale,
-                        adam->lr_f, adam->lr_dict, adam->beta1, adam->beta2, adam->eps})
+                        adam->lr_f, adam->lr_dict, adam->beta1, adam->beta2, adam->eps, tau})
             key.addf(f);
     }
     LAT_TRY(run_iterations(ctx, graphable, key, iters, learn_f != 0, adam, st, iteration));
@@ -1064,6 +1073,10 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
     REQUIRE(F && (F_dtype == LATENTAM_DTYPE_F32 || F_dtype == LATENTAM_DTYPE_BF16), "bad targets");
     cudaStream_t st = (cudaStream_t)stream;
     const int d = dict->d, M = dict->M, D = dict->D;
+    const float tau = dict->tau;
+    REQUIRE(tau >= 0.f && isfinite(tau), "tau=%g must be 0 (free keys) or positive", (double)tau);
+    const bool paper = tau > 0.f;
+    const int64_t ksize = paper ? (int64_t)d * D : (int64_t)M * d;  // K holds W (d x D) in the paper form
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
 
     // distinct query arrays (frames of one map share them)
@@ -1174,7 +1187,7 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
         g_df[u] = g_end;
         g_end += up(4 * (size_t)groups[u].n * d);
     }
-    const size_t g_dk = g_end, g_dv = g_dk + up(4 * (size_t)M * d), g_lp = g_dv + up(4 * (size_t)M * D);
+    const size_t g_dk = g_end, g_dv = g_dk + up(4 * (size_t)ksize), g_lp = g_dv + up(4 * (size_t)M * D);
     g_end = g_lp + up(8 * LATENTAM_LOSS_PARTS);
     char* gb = static_cast<char*>(ws(ctx, WS_STEP_GRAD, g_end));
     if (!ib || !gb) return LATENTAM_ERR_OUT_OF_MEMORY;
@@ -1196,8 +1209,13 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
             for (int k = 0; pooled && k < n_frames; ++k)
                 LAT_TRY(launch_pool_fwd(plans[k], Q + fs[k].pix_off * d, d, Qm + row_off[k] * d, s));
         }
-        LAT_TRY(latentam_decode_loss_bwd(ctx, pooled ? Qm : Q, ndec, d, dict->K, dict->V, dict->V0, M, D, F, F_dtype,
-                                         mask, cfg, prec, lp, learn_f ? (pooled ? dQm : dQ) : nullptr, dK, dV, s));
+        float* dQd = learn_f ? (pooled ? dQm : dQ) : nullptr;
+        if (paper)
+            LAT_TRY(latentam_decode_loss_bwd_paper(ctx, pooled ? Qm : Q, ndec, d, dict->K, dict->V, dict->V0, M, D, tau,
+                                                   F, F_dtype, mask, cfg, prec, lp, dQd, dK, dV, s));
+        else
+            LAT_TRY(latentam_decode_loss_bwd(ctx, pooled ? Qm : Q, ndec, d, dict->K, dict->V, dict->V0, M, D, F,
+                                             F_dtype, mask, cfg, prec, lp, dQd, dK, dV, s));
         if (learn_f) {
             StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, s);
             for (int u = 0; u < n_groups; ++u) {
@@ -1216,7 +1234,7 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
         if (step_dev) LAT_TRY(launch_step_advance(const_cast<int*>(step_dev), s));
         AdamTensor t[8];
         int cnt = 0;
-        t[cnt++] = AdamTensor{dict->K, dK, dict->m_K, dict->v_K, (int64_t)M * d, adam->lr_dict};
+        t[cnt++] = AdamTensor{dict->K, dK, dict->m_K, dict->v_K, ksize, adam->lr_dict};
         t[cnt++] = AdamTensor{dict->V, dV, dict->m_V, dict->v_V, (int64_t)M * D, adam->lr_dict};
         for (int u = 0; learn_f && u < n_groups; ++u) {
             if (cnt == 8) {
@@ -1236,6 +1254,7 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
         for (const void* p : ptrs) key.addp(p);
         const int64_t ints[] = {n_frames, n_groups, d, M, D, (int64_t)F_dtype, (int64_t)prec,
                                 (int64_t)ctx->ws_generation};
+        key.addf(tau);
         for (int64_t x : ints) key.add((uint64_t)x);
         for (int k = 0; k < n_frames; ++k) {
             const latentam_batch_frame& fr = frames[k];

@@ -40,7 +40,7 @@ def test_binding_covers_the_header():
 def test_version_and_tiles_without_gpu(lib):
     from paper_2602_12314_gb300 import _lib
     L = _lib.load()
-    assert L.latentam_version() == 2
+    assert L.latentam_version() == 3
     cam = _lib.Camera()
     cam.width, cam.height = 640, 480
     assert L.latentam_num_tiles(ctypes.byref(cam)) == 40 * 30

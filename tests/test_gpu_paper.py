@@ -119,3 +119,65 @@ def test_paper_stage2_and_errors(api, ctx):
     with pytest.raises(L.LatentamError) as e:
         api.decode_fwd_paper(ctx, _dev(Q), _dev(W), _dev(D), 0.0)
     assert e.value.status == L.ERR_INVALID_ARG
+
+
+def _first_update_check(x0, got, g, lr=0.01):
+    x = np.asarray(x0, np.float64).copy()
+    m, v = np.zeros_like(x), np.zeros_like(x)
+    oracle.adam(x.reshape(-1), g.reshape(-1), m.reshape(-1), v.reshape(-1), 1, lr)
+    well = (np.abs(g) > 1e-2 * np.abs(g).max()) & (np.abs(g) > 1e-5)
+    np.testing.assert_allclose(got[well], x[well], rtol=0, atol=1e-4 * lr + 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_paper_step_one_iteration_matches_oracle(api, ctx, prec):
+    """latentam_step in the paper's form (tau > 0, K holding W, V the atoms D): the loss of the
+    first iteration and the first Adam update of f, W and D against the oracle."""
+    from workloads import tiny_scene
+    s = tiny_scene(0)
+    rng = np.random.default_rng(7)
+    W = (rng.normal(size=(s.d, s.D)) / np.sqrt(s.d)).astype(np.float32)
+    tau = 0.1
+    p = api.FP32 if prec == "fp32" else api.BF16
+    st = api.LatentStep(ctx, s, precision=p, target_dtype=torch.float32 if prec == "fp32" else torch.bfloat16,
+                        tau=tau, W=W)
+    loss = st.step(iters=1)
+    cfg = oracle.LossConfig()
+    proj = oracle.project_scene(s)
+    Q = oracle.render_frame(proj, s.f, s.camera)[0]
+    Fo = paper.decode_paper(Q, W, s.V, tau)[3]
+    po = paper.loss_paper(Fo, s.F, s.mask, s.V, s.V0, cfg)
+    rel = 1e-4 if prec == "fp32" else 5e-3
+    assert loss["total"] == pytest.approx(po["total"], rel=rel)
+    if prec == "fp32":
+        dQ, dW, dD = paper.backward_paper(Q, W, s.V, s.V0, s.F, s.mask, cfg, tau)
+        df = oracle.render_frame_bwd(proj, dQ, s.camera, s.n, s.d)
+        _first_update_check(s.f, st.f.cpu().numpy().astype(np.float64), df)
+        _first_update_check(W, st.K.cpu().numpy().astype(np.float64), dW)
+        _first_update_check(s.V, st.V.cpu().numpy().astype(np.float64), dD)
+    # a few more iterations stay finite and Stage II leaves f alone
+    f1 = st.f.clone()
+    assert np.isfinite(st.step(iters=3, learn_f=False)["total"])
+    assert torch.equal(st.f, f1)
+
+
+def test_paper_batch_and_map(api, ctx):
+    """The batched step and LatentMap (with the streaming K-means of the atoms) in the paper's
+    form: the batch's first loss against the oracle, the map's iterations finite."""
+    from workloads import room_views, sam_masks
+    views = room_views(4, n_views=3, n=40_000, width=96, height=72, fx=78.75)
+    rng = np.random.default_rng(8)
+    s0 = views[0]
+    W = (rng.normal(size=(s0.d, s0.D)) / np.sqrt(s0.d)).astype(np.float32)
+    st = api.LatentBatchStep(ctx, views, precision=api.FP32, tau=0.1, W=W)
+    loss = st.step(iters=1)
+    cfg = oracle.LossConfig()
+    Q = np.concatenate([oracle.render_frame(oracle.project_scene(v), v.f, v.camera)[0] for v in views])
+    F = np.concatenate([v.F for v in views])
+    mask = np.concatenate([v.mask for v in views])
+    po = paper.loss_paper(paper.decode_paper(Q, W, s0.V, 0.1)[3], F, mask, s0.V, s0.V0, cfg)
+    assert loss["total"] == pytest.approx(po["total"], rel=1e-4)
+    m = api.LatentMap(ctx, s0, B=1, kmeans=True, tau=0.1, W=W)
+    for v in views:
+        r = m.add_keyframe(v.camera, masks=sam_masks(v, cell=(24, 18)))
+        assert np.isfinite(r["stage1"]["total"]) and np.isfinite(r["stage2"]["total"])
