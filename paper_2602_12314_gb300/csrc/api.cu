@@ -48,7 +48,7 @@ struct GraphKey {
     }
 };
 struct GraphCache {
-    static constexpr int kSlots = 4;
+    static constexpr int kSlots = 16;  // a batch of keyframes bins each of its frames
     GraphKey key[kSlots];
     cudaGraphExec_t exec[kSlots] = {};
     int64_t launches[kSlots] = {};
@@ -75,6 +75,55 @@ struct GraphCache {
 };
 
 int64_t launch_count_now() { return g_launches.load(std::memory_order_relaxed); }
+void launch_count_add(int64_t k);
+
+latentam_status cached_launch(latentam_ctx* ctx, const uint64_t* words, int n, cudaStream_t st,
+                              const std::function<latentam_status(cudaStream_t)>& fn) {
+    if (!ctx->use_graphs || ctx->profiling || !ctx->sort_graphs) return fn(st);
+    GraphKey key;
+    for (int i = 0; i < n; ++i) key.add(words[i]);
+    if (key.overflow) return fn(st);
+    GraphCache& gc = *ctx->sort_graphs;
+    int slot = GraphCache::find(gc.key, gc.used, key);
+    if (slot < 0) {
+        if (GraphCache::find(gc.failed, gc.failed_used, key) >= 0) return fn(st);
+        if (GraphCache::find(gc.warm, gc.warm_used, key) < 0) {
+            GraphCache::put(gc.warm, gc.warm_used, gc.warm_next, key);
+            return fn(st);
+        }
+        // second sighting: capture, instantiate, then replay below
+        cudaGraph_t graph = nullptr;
+        const int64_t l0 = launch_count_now();
+        cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+        latentam_status cs = e == cudaSuccess ? fn(ctx->cap_stream) : LATENTAM_ERR_CUDA;
+        cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->cap_stream, &graph) : e;
+        const int64_t captured = launch_count_now() - l0;
+        launch_count_add(-captured);  // nothing ran yet
+        cudaGraphExec_t exec = nullptr;
+        if (cs == LATENTAM_OK && e2 == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+            slot = gc.next;
+            if (gc.exec[slot]) {
+                cudaStreamSynchronize(st);
+                cudaGraphExecDestroy(gc.exec[slot]);
+            }
+            gc.exec[slot] = exec;
+            gc.key[slot] = key;
+            gc.launches[slot] = captured;
+            gc.next = (gc.next + 1) % GraphCache::kSlots;
+            if (gc.used < GraphCache::kSlots) ++gc.used;
+        } else {
+            (void)cudaGetLastError();
+            GraphCache::put(gc.failed, gc.failed_used, gc.failed_next, key);
+            if (graph) cudaGraphDestroy(graph);
+            return fn(st);
+        }
+        if (graph) cudaGraphDestroy(graph);
+    }
+    cudaError_t e = cudaGraphLaunch(gc.exec[slot], st);
+    if (e != cudaSuccess) return cuda_error(e, "graph launch");
+    launch_count_add(gc.launches[slot]);
+    return LATENTAM_OK;
+}
 void launch_count_add(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
@@ -380,10 +429,11 @@ latentam_status latentam_ctx_create(int32_t device, latentam_ctx** out) {
     c->use_graphs = 1;
     c->autotune = 1;
     c->graphs = new (std::nothrow) GraphCache();
+    c->sort_graphs = new (std::nothrow) GraphCache();
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->step_dev, sizeof(int));
-    if (e != cudaSuccess || !c->graphs) {
+    if (e != cudaSuccess || !c->graphs || !c->sort_graphs) {
         latentam_ctx_destroy(c);
         if (e != cudaSuccess) return cuda_error(e, "context stream / counter");
         set_error("host allocation failed");
@@ -408,6 +458,10 @@ latentam_status latentam_ctx_destroy(latentam_ctx* ctx) {
         ctx->graphs->clear();
         delete ctx->graphs;
     }
+    if (ctx->sort_graphs) {
+        ctx->sort_graphs->clear();
+        delete ctx->sort_graphs;
+    }
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->step_dev) cudaFree(ctx->step_dev);
     delete ctx;
@@ -421,6 +475,7 @@ latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t enable) {
     if (!enable) {
         cudaError_t e = cudaDeviceSynchronize();
         ctx->graphs->clear();
+        ctx->sort_graphs->clear();
         if (e != cudaSuccess) return cuda_error(e, "synchronise before dropping graphs");
     }
     return LATENTAM_OK;

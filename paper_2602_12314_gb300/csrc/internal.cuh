@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <functional>
 #include <stdint.h>
 
 #include "latentam.h"
@@ -101,6 +103,7 @@ struct latentam_ctx {
     cudaStream_t cap_stream;
     int* step_dev;
     lat::GraphCache* graphs;
+    lat::GraphCache* sort_graphs;  // the binning after its host read (see cached_launch)
     // autotuned split factors of the pixel reductions (see latentam_autotune_enable)
     int autotune;
     struct TuneEntry {
@@ -192,6 +195,12 @@ latentam_status launch_image_loss(latentam_ctx* ctx, const float* C, const float
                                   double* parts, float* dC, float* dZ, cudaStream_t st);
 latentam_status launch_project_bwd(const latentam_gaussians& g, const CamParams& cam, const float* dgeo,
                                    float* dmean, float* dquat, float* dscale, float* dopac, cudaStream_t st);
+// Runs fn(stream) eagerly the first time a key is seen, captures it into a CUDA graph (on
+// the context's capture stream) the second time and replays the graph on `st` from then on,
+// while graphs are enabled and stage timing is off.  The key must name every pointer, size and
+// workspace generation the launches depend on.
+latentam_status cached_launch(latentam_ctx* ctx, const uint64_t* key, int n, cudaStream_t st,
+                              const std::function<latentam_status(cudaStream_t)>& fn);
 // Per-frame buffer `idx` of at least `bytes` (grows like ws()).
 void* frame_ws(latentam_ctx* ctx, int idx, size_t bytes);
 

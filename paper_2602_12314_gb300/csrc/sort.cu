@@ -338,38 +338,48 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
         return LATENTAM_ERR_CAPACITY;
     }
     if (P == 0 || V == 0) return LATENTAM_OK;
-    // 1. visible Gaussians by depth key (index order kept among equal keys)
-    depth_keys<<<blocks, threads, 0, st>>>(N, proj.depth, proj.tiles_touched, off, dk[0], dv[0]);
-    LAT_CHECK_LAUNCH("depth_keys");
-    int r = 0;
-    LAT_TRY(radix_sort_pairs(ctx, dk, dv, false, V, 32, &r, st));
-    const uint32_t* order = dv[r];
-    // 2. pair offsets in depth order
-    const unsigned vblocks = (unsigned)((V + threads - 1) / threads);
-    uint32_t* counts = dk[1 - r];
-    gather_tiles<<<vblocks, threads, 0, st>>>((int)V, order, proj.tiles_touched, counts);
-    LAT_CHECK_LAUNCH("gather_tiles");
-    LAT_TRY(scan_exclusive_u32(ctx, counts, off, V, nullptr, st));
-    // 3. emission in depth order; 4. stable sort on the tile bits.  The depth order stays in
-    // its own slot (WS_SORT_V*), the key slots may be regrown: their contents are consumed.
+    // Steps 1-5 depend on the host only through V and P: the same frame binned again (the
+    // iterations of one keyframe, each call of Stage I and II) replays one captured graph.
     const size_t pbytes = sizeof(uint32_t) * (size_t)P;
-    uint32_t* pk[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_K0, std::max(pbytes, nbytes))),
-                       static_cast<uint32_t*>(ws(ctx, WS_SORT_K1, std::max(pbytes, nbytes)))};
-    uint32_t* pv[2] = {static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX, pbytes)),
-                       static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX2, pbytes))};
-    if (!pk[0] || !pk[1] || !pv[0] || !pv[1]) return LATENTAM_ERR_OUT_OF_MEMORY;
-    order = static_cast<const uint32_t*>(ctx->slot_ptr[r == 0 ? WS_SORT_V0 : WS_SORT_V1]);
-    emit_pairs<<<vblocks, threads, 0, st>>>((int)V, order, off, reinterpret_cast<const int4*>(proj.rect), cam.tiles_x,
-                                            pk[0], pv[0]);
-    LAT_CHECK_LAUNCH("emit_pairs");
     const int tile_bits = std::max(1, ceil_log2(num_tiles));
-    LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, st));
-    e = cudaMemcpyAsync(bins->pair_ids, pv[r], pbytes, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return cuda_error(e, "copy pair ids");
-    // 5. ranges
-    tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(pk[r], P, reinterpret_cast<int2*>(bins->tile_ranges));
-    LAT_CHECK_LAUNCH("tile_ranges");
-    return LATENTAM_OK;
+    auto rest = [&, V, P](cudaStream_t s) -> latentam_status {
+        // 1. visible Gaussians by depth key (index order kept among equal keys)
+        depth_keys<<<blocks, threads, 0, s>>>(N, proj.depth, proj.tiles_touched, off, dk[0], dv[0]);
+        LAT_CHECK_LAUNCH("depth_keys");
+        int r = 0;
+        LAT_TRY(radix_sort_pairs(ctx, dk, dv, false, V, 32, &r, s));
+        const uint32_t* order = dv[r];
+        // 2. pair offsets in depth order
+        const unsigned vblocks = (unsigned)((V + threads - 1) / threads);
+        uint32_t* counts = dk[1 - r];
+        gather_tiles<<<vblocks, threads, 0, s>>>((int)V, order, proj.tiles_touched, counts);
+        LAT_CHECK_LAUNCH("gather_tiles");
+        LAT_TRY(scan_exclusive_u32(ctx, counts, off, V, nullptr, s));
+        // 3. emission in depth order; 4. stable sort on the tile bits.  The depth order stays
+        // in its own slot (WS_SORT_V*), the key slots may be regrown: their contents are consumed.
+        uint32_t* pk[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_K0, std::max(pbytes, nbytes))),
+                           static_cast<uint32_t*>(ws(ctx, WS_SORT_K1, std::max(pbytes, nbytes)))};
+        uint32_t* pv[2] = {static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX, pbytes)),
+                           static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX2, pbytes))};
+        if (!pk[0] || !pk[1] || !pv[0] || !pv[1]) return LATENTAM_ERR_OUT_OF_MEMORY;
+        order = static_cast<const uint32_t*>(ctx->slot_ptr[r == 0 ? WS_SORT_V0 : WS_SORT_V1]);
+        emit_pairs<<<vblocks, threads, 0, s>>>((int)V, order, off, reinterpret_cast<const int4*>(proj.rect),
+                                               cam.tiles_x, pk[0], pv[0]);
+        LAT_CHECK_LAUNCH("emit_pairs");
+        LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, s));
+        cudaError_t e2 = cudaMemcpyAsync(bins->pair_ids, pv[r], pbytes, cudaMemcpyDeviceToDevice, s);
+        if (e2 != cudaSuccess) return cuda_error(e2, "copy pair ids");
+        // 5. ranges
+        tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(pk[r], P, reinterpret_cast<int2*>(bins->tile_ranges));
+        LAT_CHECK_LAUNCH("tile_ranges");
+        return LATENTAM_OK;
+    };
+    const uint64_t key[] = {(uint64_t)N, (uint64_t)V, (uint64_t)P, (uint64_t)num_tiles, (uint64_t)cam.tiles_x,
+                            reinterpret_cast<uint64_t>(proj.depth), reinterpret_cast<uint64_t>(proj.tiles_touched),
+                            reinterpret_cast<uint64_t>(proj.rect), reinterpret_cast<uint64_t>(bins->pair_ids),
+                            reinterpret_cast<uint64_t>(bins->tile_ranges), reinterpret_cast<uint64_t>(st),
+                            ctx->ws_generation};
+    return cached_launch(ctx, key, (int)(sizeof(key) / sizeof(key[0])), st, rest);
 }
 
 }  // namespace lat
