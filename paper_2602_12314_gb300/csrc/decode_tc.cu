@@ -661,11 +661,13 @@ latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 gri
         return LATENTAM_ERR_INVALID_ARG;
     }
     auto kern = tc::tc_gemm_kernel<Epi>;
-    static bool attr_set = false;  // per instantiation; setting it twice is harmless
-    if (!attr_set) {
+    static unsigned long long attr_set = 0;  // per instantiation and device; setting it twice is harmless
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(attr_set & (1ull << (dev & 63)))) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "tc_gemm smem attribute");
-        attr_set = true;
+        attr_set |= 1ull << (dev & 63);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -703,11 +705,13 @@ latentam_status launch_persist(latentam_ctx* ctx, const CUtensorMap& a, const CU
         return LATENTAM_ERR_INVALID_ARG;
     }
     auto kern = tc::tc_persist_kernel<Epi>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static unsigned long long attr_set = 0;  // per instantiation and device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(attr_set & (1ull << (dev & 63)))) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "tc_persist smem attribute");
-        attr_set = true;
+        attr_set |= 1ull << (dev & 63);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(tc::persist_threads(Epi::EPI_WG), 1, 1);

@@ -321,15 +321,17 @@ latentam_status launch_image_loss(latentam_ctx* ctx, const float* C, const float
                                   const float* depth_obs, int W, int H, const latentam_image_cfg& cfg,
                                   double* parts, float* dC, float* dZ, cudaStream_t st) {
     const int64_t n = (int64_t)W * H;
-    static bool win_set = false;
-    if (!win_set) {
+    static unsigned long long win_set = 0;  // the window lives in each device's constant memory
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(win_set & (1ull << (dev & 63)))) {
         float w[kWin];
         double s = 0.0;
         for (int k = 0; k < kWin; ++k) s += exp(-(double)((k - kHalf) * (k - kHalf)) / (2.0 * 1.5 * 1.5));
         for (int k = 0; k < kWin; ++k) w[k] = (float)(exp(-(double)((k - kHalf) * (k - kHalf)) / (2.0 * 1.5 * 1.5)) / s);
         cudaError_t e = cudaMemcpyToSymbol(c_win, w, sizeof(w));
         if (e != cudaSuccess) return cuda_error(e, "SSIM window");
-        win_set = true;
+        win_set |= 1ull << (dev & 63);
     }
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
