@@ -70,6 +70,8 @@ def _args():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", choices=["room", "tiny", "precision", "batch8", "building"], default="room",
+                   help="room (the headline run); the others print their own line")
     p.add_argument("--crop", type=int, nargs=2, metavar=("W", "H"), default=None,
                    help="profiling only: the central W x H crop of the keyframe (all Gaussians kept)")
     return p.parse_args()
@@ -392,6 +394,8 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
     # ---- roofline of the dominant stage (decode + loss + decode backward) -------------------
     peaks, peak_src = _peaks()
     n, M, D, d = scene.camera.n_pixels * n_frames, scene.M, scene.D, scene.d
+    if views is not None:
+        n = sum(v.camera.n_pixels for v in views)
     if masks is not None:
         n = masks.n_masks
     if full is not None:
@@ -553,11 +557,97 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def _building_keyframe(args, ctx):
+    """The large-map workload: the 2M-Gaussian two-floor building in a voxel-hashed map with a
+    host-resident store (5 cm voxels), the active set within 5 m of a 1296 x 968 camera gathered
+    on the GPU, synthetic per-pixel targets (64 segment embeddings, one per 32 x 32 block, plus
+    N(0, 0.02^2), l2-normalised), d = 32, M = 1024, D = 768.  Returns the keyframe as a scene and
+    the gather time."""
+    import time as _t
+
+    import numpy as np
+    import torch
+
+    from paper_2602_12314_gb300 import api
+    from workloads import Scene, building_gaussians
+    from workloads.scenes import _look_camera
+
+    g = building_gaussians(args.seed)
+    vmap = api.VoxelMap(ctx, 32, table_log2=24, voxel_size=0.05, capacity=1 << 21, host_store=True)
+    vmap.insert(*[g[k] for k in ("means", "quats", "scales", "opacities", "f")])
+    cam = _look_camera((7.5, 7.5, 1.5), (1.0, 0.0, 0.0), (0, 0, -1), 1000.0, 1000.0, 648.0, 484.0, 1296, 968)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    loc = vmap.sync([7.5, 7.5, 1.5], 5.0)
+    gather_ms = (_t.perf_counter() - t0) * 1e3
+    H, W, D, M = 968, 1296, 768, 1024
+    gen = torch.Generator(device="cuda").manual_seed(args.seed)
+    emb = torch.randn((64, D), generator=gen, device="cuda")
+    yy, xx = torch.meshgrid(torch.arange(H, device="cuda"), torch.arange(W, device="cuda"), indexing="ij")
+    lab = ((yy // 32) * ((W + 31) // 32) + xx // 32) % 64
+    F = emb[lab.reshape(-1)] + 0.02 * torch.randn((H * W, D), generator=gen, device="cuda")
+    F = F / F.norm(dim=1, keepdim=True)
+    rng = np.random.default_rng(args.seed)
+    K = (rng.normal(size=(M, 32)) / np.sqrt(32)).astype(np.float32)
+    V = (rng.normal(size=(M, D)) / np.sqrt(32)).astype(np.float32)
+    scene = Scene(name="building keyframe", means=loc["means"], quats=loc["quats"], scales=loc["scales"],
+                  opacities=loc["opacities"], f=loc["f"], K=K, V=V, V0=V.copy(), F=F,
+                  mask=torch.ones(H * W, dtype=torch.uint8, device="cuda"), camera=cam)
+    return scene, gather_ms, vmap
+
+
+def run_workloads(args, world, rank, local):
+    """The other workloads of the step (their numbers are reported beside the headline run):
+    tiny, precision (500k Gaussians, M = 512, D = 1024), batch8 (eight keyframes of uneven
+    resolution with their own maps, M = 512, D = 768) and building (the large map)."""
+    import torch
+
+    from paper_2602_12314_gb300 import api
+    from workloads import keyframe_batch, precision_scene, tiny_scene
+
+    torch.cuda.set_device(local)
+    args.no_e2e = True
+    res, extra = {}, {}
+    views = None
+    if args.workload == "tiny":
+        scene, forms = tiny_scene(args.seed), ("fp32", "bf16")
+        desc = "tiny keyframe: 2,000 Gaussians, 64x48, d=16, M=64, D=512"
+    elif args.workload == "precision":
+        scene, forms = precision_scene(args.seed), ("fp32", "bf16", "fp8")
+        desc = "room keyframe at larger dims: 500k Gaussians, 640x480, d=32, M=512, D=1024"
+    elif args.workload == "batch8":
+        sizes = ((320, 240), (640, 480), (640, 480), (640, 480), (848, 480), (848, 480), (1200, 680), (1200, 680))
+        ns = (100_000, 150_000, 250_000, 300_000, 400_000, 500_000, 700_000, 1_000_000)
+        views = keyframe_batch(args.seed, sizes=sizes, ns=ns, d=32, M=512, D=768)
+        scene, forms = views[0], ("bf16_batch", "fp32_batch")
+        desc = ("eight keyframes of uneven resolution (320x240, 640x480 x3, 848x480 x2, 1200x680 x2; 3,444,480 pixels), "
+                "each with its own room and 100k-1M Gaussians, one shared dictionary d=32, M=512, D=768")
+    else:
+        ctx = api.Context(local)
+        scene, gather_ms, vmap = _building_keyframe(args, ctx)
+        extra = {"gather_ms": gather_ms, "local_gaussians": int(scene.means.shape[0]), "map_gaussians_inserted": None}
+        forms = ("bf16",)
+        desc = ("large map: 2M-Gaussian two-floor building in a voxel-hashed map (5 cm voxels, host-resident store), "
+                "the active set within 5 m gathered on the GPU, one 1296x968 keyframe, d=32, M=1024, D=768, "
+                "10 iterations per keyframe")
+        args.steps = 10
+    for f in forms:
+        prec = api.FP32 if f.startswith("fp32") else api.FP8 if f == "fp8" else api.BF16
+        res[f] = _measure(args, world, rank, local, scene, prec, None, views if f.endswith("_batch") else None)
+    line = {"workload": args.workload, "description": desc, "steps": args.steps,
+            "forms": {f: {k: r[k] for k in ("value", "ms_per_step", "dtype", "roofline", "clocks",
+                                            "stages_ms_per_step", "keyframes_per_step")} for f, r in res.items()}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     world, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload != "room":
+        run_workloads(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 
