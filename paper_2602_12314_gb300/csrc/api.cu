@@ -162,6 +162,15 @@ void* ws(latentam_ctx* ctx, Slot s, size_t bytes) {
         set_error("workspace allocation of %zu bytes failed: %s", nb, cudaGetErrorString(e));
         return nullptr;
     }
+    if (s == WS_COUNTERS) {
+        // the counters carry an error word across calls: it starts clear
+        e = cudaMemset(p, 0, nb);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            cuda_error(e, "clear the counters");
+            return nullptr;
+        }
+    }
     ctx->slot_ptr[s] = p;
     ctx->slot_bytes[s] = nb;
     return p;

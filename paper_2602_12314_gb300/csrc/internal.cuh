@@ -162,11 +162,12 @@ latentam_status launch_project(const latentam_gaussians& g, const CamParams& cam
 // Exclusive scan of n uint32 values; *total_dev (device, nullable) receives the sum.
 latentam_status scan_exclusive_u32(latentam_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
                                    uint32_t* total_dev, cudaStream_t st);
-// Stable LSD radix sort of n (key, value) pairs on key bits [0, bits).  keys[0]/vals[0]
-// hold the input (vals_iota: value = index, vals[0] is then only scratch); keys[1]/vals[1]
-// are scratch.  *result receives the index of the buffer pair holding the sorted output.
+// Stable LSD radix sort of n (key, value) pairs on key bits [0, bits), bits <= 32, n < 2^30.
+// keys[0]/vals[0] hold the input (vals_iota: value = index, vals[0] is then only scratch);
+// keys[1]/vals[1] are scratch.  *result receives the index of the buffer pair holding the
+// sorted output.  *err (device) is set if a bounded cross-block wait gave up.
 latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uint32_t* const vals[2], bool vals_iota,
-                                 int64_t n, int bits, int* result, cudaStream_t st);
+                                 int64_t n, int bits, int* result, uint32_t* err, cudaStream_t st);
 latentam_status bin_and_sort(latentam_ctx* ctx, int32_t n, const latentam_projected& proj,
                              const CamParams& cam, latentam_bins* bins, cudaStream_t st);
 

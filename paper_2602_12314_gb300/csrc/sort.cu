@@ -9,7 +9,9 @@
 //   4. stable radix sort of the pairs on the ceil(log2(tiles)) tile bits only
 //   5. per-tile [start, end) ranges
 // Sorting depth first and then only the few tile bits replaces a 64-bit (tile|depth)
-// sort of all pairs: 4 passes over N Gaussians plus 1-2 passes over P pairs.
+// sort of all pairs: 4 passes over N Gaussians plus 1-2 passes over P pairs.  Each radix pass
+// is one launch (decoupled look-back across blocks), after one launch that counts the digits
+// of every pass.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -106,38 +108,87 @@ constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 2048; warp w owns items [256 w, 256 w + 256)
 constexpr int kRadix = 256;
 
-__global__ void __launch_bounds__(kRsThreads) radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                                                         uint32_t mask, uint32_t* __restrict__ hist, int nblocks) {
-    __shared__ uint32_t h[kRadix];
-    const int t = threadIdx.x;
-    h[t] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRsTile;
-#pragma unroll
-    for (int k = 0; k < kRsItems; ++k) {
-        const int64_t i = base + k * kRsThreads + t;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
-    }
-    __syncthreads();
-    hist[(int64_t)t * nblocks + blockIdx.x] = h[t];
+// Look-back words of the one-sweep passes: per (block, digit) the block's own count of the
+// digit, flagged as an aggregate, later replaced by the inclusive count of every block up to
+// and including it.  Counts stay below 2^30.
+constexpr uint32_t kLbAggregate = 1u << 30;
+constexpr uint32_t kLbInclusive = 2u << 30;
+constexpr uint32_t kLbValue = kLbAggregate - 1u;
+constexpr int kLbSpinLimit = 1 << 20;
+
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kRsThreads) radix_scatter(const uint32_t* __restrict__ keys_in,
-                                                            const uint32_t* __restrict__ vals_in,
-                                                            uint32_t* __restrict__ keys_out,
-                                                            uint32_t* __restrict__ vals_out, int64_t n, int shift,
-                                                            uint32_t mask, const uint32_t* __restrict__ hist_scanned,
-                                                            int nblocks) {
+// Digit mask of LSD pass p over key bits [0, bits): 8-bit digits, the last one narrower.
+__host__ __device__ __forceinline__ uint32_t pass_mask(int bits, int p) {
+    const int pb = min(8, max(bits - 8 * p, 1));
+    return (1u << pb) - 1u;
+}
+
+// Digit counts over all n keys for every pass at once (counts[p * 256 + digit]).  One read of
+// the keys; the counts do not depend on the order the earlier passes leave behind.
+__global__ void __launch_bounds__(kRsThreads) radix_digit_counts(const uint32_t* __restrict__ keys, int64_t n,
+                                                                 int passes, int bits,
+                                                                 uint32_t* __restrict__ counts) {
+    __shared__ uint32_t h[4][kRadix];
+    const int t = threadIdx.x, lane = t & 31;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) h[p][t] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * kRsThreads;
+    for (int64_t base = (int64_t)blockIdx.x * kRsThreads + (t & ~31); base < n; base += stride) {
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+        const uint32_t k = valid ? keys[i] : 0u;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t dig = valid ? ((k >> (8 * p)) & pass_mask(bits, p)) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[p][dig], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p)
+        if (h[p][t]) atomicAdd(&counts[p * kRadix + t], h[p][t]);
+}
+
+// One stable LSD pass in a single launch.  Each block takes the next 2048-key tile in input
+// order (a ticket, so that every tile before it belongs to a block already running), ranks
+// its keys by digit in input order (warp w owns keys [256 w, 256 w + 256) of the tile), posts
+// its per-digit counts, and adds the counts of the earlier tiles by walking back over their
+// posted words until it meets an inclusive one (decoupled look-back).  The waits are bounded:
+// a walk that gives up raises *err and uses what it summed (every position stays below n).
+__global__ void __launch_bounds__(kRsThreads) radix_onesweep(const uint32_t* __restrict__ keys_in,
+                                                             const uint32_t* __restrict__ vals_in,
+                                                             uint32_t* __restrict__ keys_out,
+                                                             uint32_t* __restrict__ vals_out, int64_t n, int shift,
+                                                             uint32_t mask, const uint32_t* __restrict__ counts,
+                                                             uint32_t* status, uint32_t* ticket, uint32_t* err) {
     __shared__ uint32_t s_off[kRadix];
     __shared__ uint32_t s_cnt[kRsThreads / 32][kRadix];
+    __shared__ uint32_t s_wsum[kRsThreads / 32];
+    __shared__ uint32_t s_tile;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    s_off[t] = hist_scanned[(int64_t)t * nblocks + blockIdx.x];
+    if (t == 0) s_tile = atomicAdd(ticket, 1u);
 #pragma unroll
     for (int w = 0; w < kRsThreads / 32; ++w) s_cnt[w][t] = 0;
+    // first output position of digit t: exclusive scan of the digit counts
+    const uint32_t c_all = counts[t];
+    const uint32_t c_incl = warp_incl_scan(c_all, lane);
+    if (lane == 31) s_wsum[warp] = c_incl;
     __syncthreads();
+    uint32_t digit_start = c_incl - c_all;
+    for (int w = 0; w < warp; ++w) digit_start += s_wsum[w];
+    const int64_t tile = s_tile;
+
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t kk[kRsItems], vv[kRsItems], dd[kRsItems], rr[kRsItems];
-    const int64_t base = (int64_t)blockIdx.x * kRsTile + warp * (32 * kRsItems);
+    const int64_t base = tile * kRsTile + warp * (32 * kRsItems);
 #pragma unroll
     for (int it = 0; it < kRsItems; ++it) {
         const int64_t i = base + it * 32 + lane;
@@ -157,15 +208,37 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter(const uint32_t* __re
         rr[it] = before + rank;
     }
     __syncthreads();
-    {
-        uint32_t run = 0;
+    uint32_t own = 0;  // keys of digit t in this tile; s_cnt becomes the per-warp exclusive prefix
 #pragma unroll
-        for (int w = 0; w < kRsThreads / 32; ++w) {
-            const uint32_t c = s_cnt[w][t];
-            s_cnt[w][t] = run;
-            run += c;
-        }
+    for (int w = 0; w < kRsThreads / 32; ++w) {
+        const uint32_t c = s_cnt[w][t];
+        s_cnt[w][t] = own;
+        own += c;
     }
+    uint32_t* word = status + tile * kRadix + t;
+    st_relaxed_gpu(word, (tile == 0 ? kLbInclusive : kLbAggregate) | own);
+    uint32_t earlier = 0;  // keys of digit t in the tiles before this one
+    if (tile > 0) {
+        bool ok = true;
+        for (int64_t j = tile - 1; j >= 0 && ok; --j) {
+            const uint32_t* w = status + j * kRadix + t;
+            uint32_t v = ld_relaxed_gpu(w);
+            for (int spins = 0; (v & ~kLbValue) == 0; ++spins) {
+                if (spins >= kLbSpinLimit) {
+                    ok = false;
+                    break;
+                }
+                if (spins >= 32) __nanosleep(64);
+                v = ld_relaxed_gpu(w);
+            }
+            if (!ok) break;
+            earlier += v & kLbValue;
+            if (v & kLbInclusive) break;
+        }
+        if (!ok) atomicExch(err, 1u);
+        st_relaxed_gpu(word, kLbInclusive | (earlier + own));
+    }
+    s_off[t] = digit_start + earlier;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kRsItems; ++it) {
@@ -233,9 +306,11 @@ __global__ void emit_pairs(int N, const uint32_t* __restrict__ order, const uint
         }
 }
 
-__global__ void tile_ranges(const uint32_t* __restrict__ keys, int64_t P, int2* __restrict__ ranges) {
+// A sort whose look-back gave up (*err) leaves every tile empty (the ranges were cleared).
+__global__ void tile_ranges(const uint32_t* __restrict__ keys, int64_t P, const uint32_t* __restrict__ err,
+                            int2* __restrict__ ranges) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
+    if (i >= P || *err) return;
     const uint32_t t = keys[i];
     if (i == 0 || keys[i - 1] != t) ranges[t].x = (int)i;
     if (i == P - 1 || keys[i + 1] != t) ranges[t].y = (int)(i + 1);
@@ -277,26 +352,34 @@ latentam_status scan_exclusive_u32(latentam_ctx* ctx, const uint32_t* in, uint32
 }
 
 latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uint32_t* const vals[2], bool vals_iota,
-                                 int64_t n, int bits, int* result, cudaStream_t st) {
+                                 int64_t n, int bits, int* result, uint32_t* err, cudaStream_t st) {
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
     *result = passes % 2;
     if (n <= 0) return LATENTAM_OK;
+    if (passes > 4 || n > (int64_t)kLbValue) {
+        set_error("radix sort of %lld keys on %d bits is not supported", (long long)n, bits);
+        return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
     const int64_t nb = (n + kRsTile - 1) / kRsTile;
-    const int64_t hist_n = nb * kRadix;
-    uint32_t* hist = static_cast<uint32_t*>(ws(ctx, WS_SORT_HIST, sizeof(uint32_t) * (size_t)hist_n));
-    if (!hist) return LATENTAM_ERR_OUT_OF_MEMORY;
+    // [digit counts: passes x 256 | tickets: 256 | look-back words: passes x nb x 256], zeroed
+    const size_t words = (size_t)(passes + 1) * kRadix + (size_t)passes * (size_t)nb * kRadix;
+    uint32_t* buf = static_cast<uint32_t*>(ws(ctx, WS_SORT_HIST, sizeof(uint32_t) * words));
+    if (!buf) return LATENTAM_ERR_OUT_OF_MEMORY;
+    cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(uint32_t) * words, st);
+    if (e != cudaSuccess) return cuda_error(e, "clear radix sort counters");
+    uint32_t* counts = buf;
+    uint32_t* tickets = buf + (size_t)passes * kRadix;
+    uint32_t* status = tickets + kRadix;
+    const unsigned cblocks = (unsigned)std::min<int64_t>(nb, 2 * (int64_t)ctx->num_sms);
+    radix_digit_counts<<<cblocks, kRsThreads, 0, st>>>(keys[0], n, passes, bits, counts);
+    LAT_CHECK_LAUNCH("radix_digit_counts");
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        const int pb = std::min(8, std::max(bits - shift, 1));
-        const uint32_t mask = (1u << pb) - 1u;
         const int src = p % 2, dst = 1 - src;
         const uint32_t* vin = (p == 0 && vals_iota) ? nullptr : vals[src];
-        radix_hist<<<(unsigned)nb, kRsThreads, 0, st>>>(keys[src], n, shift, mask, hist, (int)nb);
-        LAT_CHECK_LAUNCH("radix_hist");
-        LAT_TRY(scan_exclusive_u32(ctx, hist, hist, hist_n, nullptr, st));
-        radix_scatter<<<(unsigned)nb, kRsThreads, 0, st>>>(keys[src], vin, keys[dst], vals[dst], n, shift, mask, hist,
-                                                          (int)nb);
-        LAT_CHECK_LAUNCH("radix_scatter");
+        radix_onesweep<<<(unsigned)nb, kRsThreads, 0, st>>>(keys[src], vin, keys[dst], vals[dst], n, 8 * p,
+                                                            pass_mask(bits, p), counts + p * kRadix,
+                                                            status + (size_t)p * (size_t)nb * kRadix, tickets + p, err);
+        LAT_CHECK_LAUNCH("radix_onesweep");
     }
     return LATENTAM_OK;
 }
@@ -321,16 +404,24 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
     const int threads = 256;
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
     // 0. visible Gaussians (flags -> offsets, count V into cnt[0]) and the pair count P (cnt[1])
+    // cnt[2]: raised by a sort pass whose look-back gave up; it outlives the call and is
+    // reported (and cleared) by the next binning's host read
     e = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), st);
     if (e != cudaSuccess) return cuda_error(e, "memset counters");
     visible_flags<<<blocks, threads, 0, st>>>(N, proj.tiles_touched, dv[1], cnt);
     LAT_CHECK_LAUNCH("visible_flags");
     LAT_TRY(scan_exclusive_u32(ctx, dv[1], off, N, cnt, st));
-    uint32_t VP[2] = {0, 0};
+    uint32_t VP[3] = {0, 0, 0};
     e = cudaMemcpyAsync(VP, cnt, sizeof(VP), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_error(e, "read visible and pair counts");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_error(e, "sync for the counts");
+    if (VP[2]) {
+        e = cudaMemsetAsync(cnt + 2, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_error(e, "clear the sort error word");
+        set_error("a radix sort look-back wait gave up in an earlier binning (its tiles were left empty)");
+        return LATENTAM_ERR_TIMEOUT;
+    }
     const int64_t V = (int64_t)VP[0], P = (int64_t)VP[1];
     bins->num_pairs = P;
     if (P > bins->capacity) {
@@ -347,7 +438,7 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
         depth_keys<<<blocks, threads, 0, s>>>(N, proj.depth, proj.tiles_touched, off, dk[0], dv[0]);
         LAT_CHECK_LAUNCH("depth_keys");
         int r = 0;
-        LAT_TRY(radix_sort_pairs(ctx, dk, dv, false, V, 32, &r, s));
+        LAT_TRY(radix_sort_pairs(ctx, dk, dv, false, V, 32, &r, cnt + 2, s));
         const uint32_t* order = dv[r];
         // 2. pair offsets in depth order
         const unsigned vblocks = (unsigned)((V + threads - 1) / threads);
@@ -366,11 +457,12 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
         emit_pairs<<<vblocks, threads, 0, s>>>((int)V, order, off, reinterpret_cast<const int4*>(proj.rect),
                                                cam.tiles_x, pk[0], pv[0]);
         LAT_CHECK_LAUNCH("emit_pairs");
-        LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, s));
+        LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, cnt + 2, s));
         cudaError_t e2 = cudaMemcpyAsync(bins->pair_ids, pv[r], pbytes, cudaMemcpyDeviceToDevice, s);
         if (e2 != cudaSuccess) return cuda_error(e2, "copy pair ids");
         // 5. ranges
-        tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(pk[r], P, reinterpret_cast<int2*>(bins->tile_ranges));
+        tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(pk[r], P, cnt + 2,
+                                                             reinterpret_cast<int2*>(bins->tile_ranges));
         LAT_CHECK_LAUNCH("tile_ranges");
         return LATENTAM_OK;
     };

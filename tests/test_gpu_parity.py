@@ -6,6 +6,8 @@ ambiguous (a candidate within a relative 5e-5 of alpha = 1/255 or within 1e-3 of
 T = 1e-4 stop, where a float32 evaluation may legitimately decide the other way) are
 compared only for validity; they must stay rare.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -347,6 +349,52 @@ def test_max_dictionary_shape(api, ctx):
 @pytest.fixture(scope="module")
 def room():
     return room_scene(0)
+
+
+def _filtered_lists(off, ids, amb):
+    """Tile index and Gaussian of every list entry whose Gaussian is not rect-ambiguous."""
+    tile = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    keep = ~np.isin(ids, amb)
+    return tile[keep], ids[keep]
+
+
+def test_full_size_bins_match_oracle(api, ctx, room):
+    """640x480, 300k Gaussians (1200 tiles, about 117k pairs: dozens of 2048-key blocks in
+    every pass of the sort, each finding its offsets by look-back): every tile's list equals the
+    oracle's (depth, index) order, bit for bit, apart from the Gaussians whose tile rect is
+    ambiguous."""
+    s = room
+    proj, bins = _gpu_front(api, ctx, s)
+    o = oracle.project_scene(s)
+    off, ids = oracle.tile_lists(o, s.camera)
+    amb = np.nonzero(o["rect_ambiguous"])[0]
+    pairs = bins.pair_ids[:bins.num_pairs].cpu().numpy().astype(np.int64)
+    ranges = bins.tile_ranges.cpu().numpy().astype(np.int64)
+    assert bins.num_pairs > 50_000
+    # ranges tile the pair list in order (empty tiles are (0, 0))
+    nonempty = ranges[:, 1] > ranges[:, 0]
+    r = ranges[nonempty]
+    assert r[0, 0] == 0 and r[-1, 1] == bins.num_pairs and np.all(r[1:, 0] == r[:-1, 1])
+    goff = np.zeros(len(ranges) + 1, np.int64)
+    goff[1:] = np.cumsum(ranges[:, 1] - ranges[:, 0])
+    gt, gg = _filtered_lists(goff, pairs, amb)
+    wt, wg = _filtered_lists(off, ids.astype(np.int64), amb)
+    np.testing.assert_array_equal(gt, wt)
+    np.testing.assert_array_equal(gg, wg)
+    # binning the same frame into the same buffers again: a plain run, then the captured and
+    # the replayed graph of the launches after the count read; the lists do not change
+    from paper_2602_12314_gb300 import _lib as L
+    want_pairs, want_ranges = bins.pair_ids.clone(), bins.tile_ranges.clone()
+    cam = api.camera_struct(s.camera)
+    for _ in range(3):
+        bins.pair_ids.fill_(-1)
+        bins.tile_ranges.fill_(-1)
+        bs, ps = bins.struct(), proj.struct()
+        L.check(L.load().latentam_sort(ctx.handle, proj.n, ctypes.byref(ps), ctypes.byref(cam), ctypes.byref(bs),
+                                       api._stream()))
+        assert int(bs.num_pairs) == bins.num_pairs
+        assert torch.equal(bins.pair_ids[:bins.num_pairs], want_pairs[:bins.num_pairs])
+        assert torch.equal(bins.tile_ranges, want_ranges)
 
 
 def test_full_size_sampled_pixels(api, ctx, room):
