@@ -176,6 +176,17 @@ void* ws(latentam_ctx* ctx, Slot s, size_t bytes) {
     return p;
 }
 
+// cp with the launch order of its tiles (computed from the frame's bins into the order slot at
+// `offset` tiles); the per-tile kernels then start the longest tile lists first.
+latentam_status ordered(latentam_ctx* ctx, CamParams* cp, const latentam_bins& bins, size_t offset, size_t total,
+                        cudaStream_t st) {
+    int32_t* order = static_cast<int32_t*>(ws(ctx, WS_TILE_ORDER, sizeof(int32_t) * total));
+    if (!order) return LATENTAM_ERR_OUT_OF_MEMORY;
+    LAT_TRY(launch_tile_order(*cp, bins, order + offset, st));
+    cp->tile_order = order + offset;
+    return LATENTAM_OK;
+}
+
 void* frame_ws(latentam_ctx* ctx, int idx, size_t bytes) {
     if (bytes == 0) bytes = 256;
     if (ctx->frame_bytes[idx] >= bytes) return ctx->frame_ptr[idx];
@@ -553,7 +564,10 @@ latentam_status latentam_render_fwd(latentam_ctx* ctx, int32_t n, const latentam
     REQUIRE(Q && T_final && n_contrib, "null output");
     REQUIRE(aligned16(f) && aligned16(Q), "f and Q must be 16-byte aligned");
     StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, (cudaStream_t)stream);
-    return launch_render_fwd(cam_params(*cam), *proj, *bins, f, d, Q, T_final, n_contrib, (cudaStream_t)stream);
+    CamParams cp = cam_params(*cam);
+    const size_t tiles = (size_t)cp.tiles_x * cp.tiles_y;
+    LAT_TRY(ordered(ctx, &cp, *bins, 0, tiles, (cudaStream_t)stream));
+    return launch_render_fwd(cp, *proj, *bins, f, d, Q, T_final, n_contrib, (cudaStream_t)stream);
 }
 
 latentam_status latentam_render_bwd(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
@@ -568,7 +582,10 @@ latentam_status latentam_render_bwd(latentam_ctx* ctx, int32_t n, const latentam
     REQUIRE(aligned16(dQ), "dQ must be 16-byte aligned");
     if (n == 0) return LATENTAM_OK;
     StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, (cudaStream_t)stream);
-    return launch_render_bwd(cam_params(*cam), *proj, *bins, n_contrib, dQ, d, df, n, (cudaStream_t)stream);
+    CamParams cp = cam_params(*cam);
+    const size_t tiles = (size_t)cp.tiles_x * cp.tiles_y;
+    LAT_TRY(ordered(ctx, &cp, *bins, 0, tiles, (cudaStream_t)stream));
+    return launch_render_bwd(cp, *proj, *bins, n_contrib, dQ, d, df, n, (cudaStream_t)stream);
 }
 
 latentam_status latentam_decode_fwd(latentam_ctx* ctx, const float* Q, int64_t n, int32_t d, const float* K,
@@ -901,7 +918,7 @@ latentam_status latentam_backward_full(latentam_ctx* ctx, const latentam_gaussia
     bins.tile_ranges = reinterpret_cast<int32_t*>(pb + o_tr);
     bins.pair_ids = static_cast<int32_t*>(ctx->slot_ptr[WS_STEP_PAIRS]);
     bins.capacity = (int64_t)(ctx->slot_bytes[WS_STEP_PAIRS] / sizeof(int32_t));
-    const CamParams cp = cam_params(*cam);
+    CamParams cp = cam_params(*cam);
     {
         StageTimer tm(ctx, LATENTAM_STAGE_PROJECT, st);
         LAT_TRY(launch_project(*g, cp, proj, st));
@@ -916,6 +933,7 @@ latentam_status latentam_backward_full(latentam_ctx* ctx, const latentam_gaussia
             bins.capacity = bins.num_pairs;
             s = bin_and_sort(ctx, N, proj, cp, &bins, st);
         }
+        if (s == LATENTAM_OK) s = ordered(ctx, &cp, bins, 0, (size_t)tiles, st);
     }
     LAT_TRY(s);
     // images, their gradients and the screen-space gradients
@@ -1025,7 +1043,11 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
     float* dK = reinterpret_cast<float*>(gb + g_dk);
     float* dV = reinterpret_cast<float*>(gb + g_dv);
     double* lp = reinterpret_cast<double*>(gb + g_lp);
-    const CamParams cp = cam_params(cam);
+    CamParams cp = cam_params(cam);
+    {
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+        LAT_TRY(ordered(ctx, &cp, bins, 0, (size_t)cp.tiles_x * cp.tiles_y, st));
+    }
     // mask-pooled targets: the plan of the mask set (once per call) and the pooled queries
     const int32_t S = frame->n_masks;
     const bool pooled = S > 0;
@@ -1207,6 +1229,17 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
             s = bin_and_sort(ctx, N, fs[k].proj, fs[k].cam, &bins, st);
         }
         LAT_TRY(s);
+    }
+    {
+        // every frame's tile launch order, side by side in the order slot
+        size_t total_tiles = 0;
+        for (int k = 0; k < n_frames; ++k) total_tiles += (size_t)fs[k].cam.tiles_x * fs[k].cam.tiles_y;
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+        size_t off = 0;
+        for (int k = 0; k < n_frames; ++k) {
+            LAT_TRY(ordered(ctx, &fs[k].cam, fs[k].bins, off, total_tiles, st));
+            off += (size_t)fs[k].cam.tiles_x * fs[k].cam.tiles_y;
+        }
     }
 
     // stacked images, per-group query gradients, dictionary gradients

@@ -23,6 +23,8 @@ struct CamParams {
     float t[3];
     float fx, fy, cx, cy, z_near;
     int W, H, tiles_x, tiles_y;
+    // launch order of the per-tile kernels (block b renders tile tile_order[b]); null: b itself
+    const int32_t* tile_order;
 };
 
 inline CamParams cam_params(const latentam_camera& c) {
@@ -38,6 +40,7 @@ inline CamParams cam_params(const latentam_camera& c) {
     p.H = c.height;
     p.tiles_x = (c.width + kTile - 1) / kTile;
     p.tiles_y = (c.height + kTile - 1) / kTile;
+    p.tile_order = nullptr;
     return p;
 }
 
@@ -69,6 +72,7 @@ enum Slot : int {
     WS_KMEANS,     // streaming K-means scratch
     WS_FULL_IMG,   // images and gradients of the full Stage I backward
     WS_FULL_AUX,   // SSIM maps and loss sums
+    WS_TILE_ORDER, // launch order of the per-tile render kernels (per frame)
     WS_NUM_SLOTS
 };
 
@@ -171,6 +175,9 @@ latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uin
 latentam_status bin_and_sort(latentam_ctx* ctx, int32_t n, const latentam_projected& proj,
                              const CamParams& cam, latentam_bins* bins, cudaStream_t st);
 
+// The tiles of a binned frame in decreasing order of list length (power-of-two classes), into
+// order[tiles]: the per-tile kernels start the longest tiles first.
+latentam_status launch_tile_order(const CamParams& cam, const latentam_bins& bins, int32_t* order, cudaStream_t st);
 latentam_status launch_render_fwd(const CamParams& cam, const latentam_projected& proj,
                                   const latentam_bins& bins, const float* f, int d, float* Q,
                                   float* T_final, int32_t* n_contrib, cudaStream_t st);

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, 
     __shared__ float2 s_xy[kBatch];
     __shared__ float4 s_co[kBatch];
     __shared__ float4 s_f[kBatch][DV];
-    const int tile = blockIdx.x;
+    const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int t = threadIdx.x;
     const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
@@ -112,6 +112,25 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
     return v[0];
 }
 
+// Backward of the query blend, df_i = sum_p w_ip dQ_p, as one small GEMM per tile and batch:
+// the weights w_ip of a batch of kBwdBatch Gaussians are first recomputed front to back by the
+// pixel threads (the forward's arithmetic, so the same contributions are taken: a pixel stops
+// after its n_contrib-th one) into a shared-memory matrix W (pixels x Gaussians); then
+// thread (q, j) sums W[p][j] dQ_p over the 64 pixels p of quarter q with the tile's dQ rows
+// broadcast from shared memory, the four quarters are added in a fixed order, and each
+// non-zero (Gaussian, channel) sum goes to df with one atomic per tile.  Pixel rows that are
+// zero for the whole batch (finished or untouched pixels) are skipped block-uniformly.
+constexpr int kBwdBatch = 64;
+constexpr int kBwdQuarters = kTilePixels / kBwdBatch;  // 4
+constexpr int kWStride = kBwdBatch + 1;                // padded W row (conflict-free stores)
+
+template <int DQ>
+constexpr size_t render_bwd_smem() {
+    // W (its space reused by the per-quarter partial sums), dQ rows, staged splats, row flags
+    return sizeof(float) * (size_t)kTilePixels * kWStride + sizeof(float) * (size_t)kTilePixels * DQ +
+           (sizeof(float2) + sizeof(float4) + sizeof(int)) * kBwdBatch + sizeof(int) * kTilePixels;
+}
+
 template <int DQ>
 __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, const int2* __restrict__ ranges,
                                                                  const int32_t* __restrict__ pair_ids,
@@ -120,76 +139,99 @@ __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, 
                                                                  const int32_t* __restrict__ n_contrib,
                                                                  const float4* __restrict__ dQ, float* __restrict__ df) {
     constexpr int DV = DQ / 4;
-    constexpr int NG = DQ / 32 > 0 ? DQ / 32 : 1;  // 32-channel groups
-    __shared__ float2 s_xy[kBatch];
-    __shared__ float4 s_co[kBatch];
-    __shared__ int s_id[kBatch];
-    const int tile = blockIdx.x;
+    static_assert((size_t)kBwdQuarters * DQ * kWStride <= (size_t)kTilePixels * kWStride,
+                  "the partial sums must fit in the space of W");
+    extern __shared__ float4 smem_f4[];
+    float* s_w = reinterpret_cast<float*>(smem_f4);                // [pixel][kWStride]
+    float* s_part = s_w;                                           // [quarter][channel][kWStride]
+    float4* s_dq = reinterpret_cast<float4*>(s_w + (size_t)kTilePixels * kWStride);  // [pixel][DV]
+    float4* s_co = s_dq + (size_t)kTilePixels * DV;
+    float2* s_xy = reinterpret_cast<float2*>(s_co + kBwdBatch);
+    int* s_id = reinterpret_cast<int*>(s_xy + kBwdBatch);
+    int* s_row = s_id + kBwdBatch;  // pixel row of W non-zero in this batch
+    static_assert((kTilePixels * kWStride) % 4 == 0, "dQ rows must stay 16-byte aligned");
+
+    const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-    const int t = threadIdx.x, lane = t & 31;
+    const int t = threadIdx.x;
     const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
     const bool inside = px < cam.W && py < cam.H;
     const float fpx = (float)px, fpy = (float)py;
     const int2 range = ranges[tile];
-    float g[DQ];
     int remaining = 0;
     if (inside) {
         const size_t p = (size_t)py * cam.W + px;
 #pragma unroll
-        for (int c = 0; c < DV; ++c) {
-            const float4 v = dQ[p * DV + c];
-            g[4 * c] = v.x;
-            g[4 * c + 1] = v.y;
-            g[4 * c + 2] = v.z;
-            g[4 * c + 3] = v.w;
-        }
+        for (int c = 0; c < DV; ++c) s_dq[t * DV + c] = dQ[p * DV + c];
         remaining = n_contrib[p];
     } else {
 #pragma unroll
-        for (int c = 0; c < DQ; ++c) g[c] = 0.f;
+        for (int c = 0; c < DV; ++c) s_dq[t * DV + c] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    const int q = t / kBwdBatch, jj = t % kBwdBatch;  // GEMM role: quarter and Gaussian column
     float T = 1.0f;
     bool done = remaining == 0;
-    for (int start = range.x; start < range.y; start += kBatch) {
+    for (int start = range.x; start < range.y; start += kBwdBatch) {
         if (__syncthreads_count(done) == kTilePixels) break;
-        const int k = start + t;
-        if (k < range.y) {
-            const int gid = pair_ids[k];
+        const int cnt = min(kBwdBatch, range.y - start);
+        if (t < cnt) {
+            const int gid = pair_ids[start + t];
             s_xy[t] = xy[gid];
             s_co[t] = stage_splat(conic_opac[gid]);
             s_id[t] = gid;
         }
         __syncthreads();
-        const int cnt = min(kBatch, range.y - start);
+        // 1. this pixel's weights for the batch (identical arithmetic to the forward pass)
+        int any = 0;
+        float* wrow = s_w + (size_t)t * kWStride;
         for (int j = 0; j < cnt; ++j) {
-            // identical arithmetic to the forward pass, so the same contributions are taken
             float w = 0.0f;
             if (!done) {
                 const float alpha = splat_alpha(s_xy[j], s_co[j], fpx, fpy);
                 if (alpha >= kAlphaMin) {
                     w = __fmul_rn(alpha, T);
                     T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+                    any = 1;
                     if (--remaining == 0) done = true;
                 }
             }
-            if (__any_sync(0xffffffffu, w != 0.0f)) {
-                const int gid = s_id[j];
+            wrow[j] = w;
+        }
+        s_row[t] = any;
+        __syncthreads();
+        // 2. thread (q, jj): sum over the quarter's pixels of W[p][jj] dQ_p
+        float acc[DQ];
 #pragma unroll
-                for (int grp = 0; grp < NG; ++grp) {
-                    float v[32];
-                    if (DQ >= 32) {
+        for (int c = 0; c < DQ; ++c) acc[c] = 0.f;
+        if (jj < cnt) {
+            for (int i = 0; i < kBwdBatch; ++i) {
+                const int p = q * kBwdBatch + i;
+                if (!s_row[p]) continue;  // the same p for every thread of the warp
+                const float w = s_w[(size_t)p * kWStride + jj];
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) v[c] = w * g[grp * 32 + c];
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 32; ++c) v[c] = c < DQ ? w * g[c] : 0.0f;
-                    }
-                    // lane l now holds channel l summed over the warp (channels >= DQ are zero)
-                    const float s = warp_reduce_scatter32(v, lane);
-                    if (lane < (DQ < 32 ? DQ : 32)) atomicAdd(&df[(size_t)gid * DQ + grp * 32 + lane], s);
+                for (int c = 0; c < DV; ++c) {
+                    const float4 g = s_dq[p * DV + c];
+                    acc[4 * c] = __fmaf_rn(w, g.x, acc[4 * c]);
+                    acc[4 * c + 1] = __fmaf_rn(w, g.y, acc[4 * c + 1]);
+                    acc[4 * c + 2] = __fmaf_rn(w, g.z, acc[4 * c + 2]);
+                    acc[4 * c + 3] = __fmaf_rn(w, g.w, acc[4 * c + 3]);
                 }
             }
         }
+        __syncthreads();  // W is read; its space takes the partial sums
+#pragma unroll
+        for (int c = 0; c < DQ; ++c) s_part[((size_t)q * DQ + c) * kWStride + jj] = acc[c];
+        __syncthreads();
+        // 3. quarters added in order; one atomic per non-zero (Gaussian, channel) of the tile
+        for (int o = t; o < kBwdBatch * DQ; o += kTilePixels) {
+            const int j = o / DQ, c = o % DQ;
+            if (j >= cnt) break;
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < kBwdQuarters; ++k) s += s_part[((size_t)k * DQ + c) * kWStride + j];
+            if (s != 0.0f) atomicAdd(&df[(size_t)s_id[j] * DQ + c], s);
+        }
+        // the next batch's staging and W writes come after the barrier at the loop head
     }
 }
 
@@ -217,7 +259,7 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_full_kernel(
     __shared__ float4 s_co[kBatchFull];
     __shared__ float4 s_cz[kBatchFull];
     __shared__ float4 s_f[kBatchFull][DV];
-    const int tile = blockIdx.x;
+    const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int t = threadIdx.x;
     const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
@@ -300,7 +342,7 @@ __global__ void __launch_bounds__(kTilePixels) render_bwd_full_kernel(
     __shared__ float4 s_cz[kBatchFull];
     __shared__ float4 s_f[kBatchFull][DV];
     __shared__ int s_id[kBatchFull];
-    const int tile = blockIdx.x;
+    const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int t = threadIdx.x, lane = t & 31;
     const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
@@ -439,14 +481,58 @@ latentam_status render_bwd_t(const CamParams& cam, const latentam_projected& pro
         if (e != cudaSuccess) return cuda_error(e, "memset df");
     }
     const int tiles = cam.tiles_x * cam.tiles_y;
-    render_bwd_kernel<DQ><<<tiles, kTilePixels, 0, st>>>(
+    constexpr size_t smem = render_bwd_smem<DQ>();
+    static_assert(smem <= 227 * 1024, "render backward tile does not fit in shared memory");
+    auto kern = render_bwd_kernel<DQ>;
+    static unsigned long long attr_set = 0;  // per instantiation and device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(attr_set & (1ull << (dev & 63)))) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "render backward smem attribute");
+        attr_set |= 1ull << (dev & 63);
+    }
+    kern<<<tiles, kTilePixels, smem, st>>>(
         cam, reinterpret_cast<const int2*>(bins.tile_ranges), bins.pair_ids, reinterpret_cast<const float2*>(proj.xy),
         reinterpret_cast<const float4*>(proj.conic_opacity), n_contrib, reinterpret_cast<const float4*>(dQ), df);
     LAT_CHECK_LAUNCH("render_bwd_kernel");
     return LATENTAM_OK;
 }
 
+// Longest tiles first: class b holds the tiles whose list length has its highest set bit at b
+// (empty tiles last); within a class the order is that of the atomics (it only schedules).
+__global__ void __launch_bounds__(1024) tile_order_kernel(const int2* __restrict__ ranges, int tiles,
+                                                          int32_t* __restrict__ order) {
+    __shared__ int s_cnt[33], s_pos[33];
+    const int t = threadIdx.x;
+    if (t < 33) s_cnt[t] = 0;
+    __syncthreads();
+    auto cls = [&](int i) {
+        const int2 r = ranges[i];
+        const int len = r.y - r.x;
+        return len > 0 ? 32 - __clz(len) : 0;  // 1..31, 0 for an empty tile
+    };
+    for (int i = t; i < tiles; i += blockDim.x) atomicAdd(&s_cnt[cls(i)], 1);
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int c = 32; c >= 0; --c) {
+            s_pos[c] = run;
+            run += s_cnt[c];
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < tiles; i += blockDim.x) order[atomicAdd(&s_pos[cls(i)], 1)] = i;
+}
+
 }  // namespace
+
+latentam_status launch_tile_order(const CamParams& cam, const latentam_bins& bins, int32_t* order, cudaStream_t st) {
+    const int tiles = cam.tiles_x * cam.tiles_y;
+    tile_order_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const int2*>(bins.tile_ranges), tiles, order);
+    LAT_CHECK_LAUNCH("tile_order_kernel");
+    return LATENTAM_OK;
+}
 
 latentam_status launch_render_fwd(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
                                   const float* f, int d, float* Q, float* T_final, int32_t* n_contrib,
