@@ -1,17 +1,14 @@
 // Tile binning and sorting of the splats (the depth-ordered lists that Eq. alpha_blending
 // walks, Sec. III-A):
-//   0. compaction of the visible Gaussians (tiles touched > 0) in index order; the visible
-//      count V and the pair count P are read back together (the one host round trip)
-//   1. stable LSD radix sort of the V visible Gaussians by binary32 depth key (ties keep
-//      index order)
-//   2. exclusive scan of tiles-touched in that order -> pair offsets
-//   3. emission of one (tile, Gaussian) pair per covered tile, in depth order
-//   4. stable radix sort of the pairs on the ceil(log2(tiles)) tile bits only
-//   5. per-tile [start, end) ranges
-// Sorting depth first and then only the few tile bits replaces a 64-bit (tile|depth)
-// sort of all pairs: 4 passes over N Gaussians plus 1-2 passes over P pairs.  Each radix pass
-// is one launch (decoupled look-back across blocks), after one launch that counts the digits
-// of every pass.
+//   0. exclusive scan of tiles-touched -> pair offsets and the pair count P (the one host
+//      round trip)
+//   1. emission of one (tile, Gaussian) pair per covered tile, Gaussians in index order
+//   2. stable radix sort of the pairs on the ceil(log2(tiles)) tile bits only
+//   3. per-tile [start, end) ranges
+//   4. each tile's list sorted by (binary32 depth key, index) in shared memory
+// Sorting each short list on its own replaces a global depth sort of the visible Gaussians;
+// each radix pass is one launch (decoupled look-back across blocks) after one launch that
+// counts the digits of every pass.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -253,57 +250,120 @@ __global__ void __launch_bounds__(kRsThreads) radix_onesweep(const uint32_t* __r
 
 // ---- binning ---------------------------------------------------------------------------
 
-// flags[i] = (tiles[i] > 0); cnt[1] += sum of tiles (the pair count P).
-__global__ void __launch_bounds__(256) visible_flags(int N, const int32_t* __restrict__ tiles, uint32_t* __restrict__ flags,
-                                                     uint32_t* __restrict__ cnt) {
-    __shared__ uint32_t red[8];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t tt = i < N ? (uint32_t)max(tiles[i], 0) : 0u;
-    if (i < N) flags[i] = tt > 0 ? 1u : 0u;
-    uint32_t s = tt;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t b = 0;
-        for (int w = 0; w < 8; ++w) b += red[w];
-        if (b) atomicAdd(&cnt[1], b);
-    }
-}
-
-// The visible Gaussians in index order with their depth keys (visible Gaussians have
-// depth > z_near > 0, whose binary32 bits order like the values).
-__global__ void depth_keys(int N, const float* __restrict__ depth, const int32_t* __restrict__ tiles,
-                           const uint32_t* __restrict__ vis_off, uint32_t* __restrict__ keys,
-                           uint32_t* __restrict__ ids) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || tiles[i] <= 0) return;
-    const uint32_t o = vis_off[i];
-    keys[o] = __float_as_uint(depth[i]);
-    ids[o] = (uint32_t)i;
-}
-
-__global__ void gather_tiles(int N, const uint32_t* __restrict__ order, const int32_t* __restrict__ tiles,
-                             uint32_t* __restrict__ out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) out[k] = (uint32_t)tiles[order[k]];
-}
-
-__global__ void emit_pairs(int N, const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
-                           const int4* __restrict__ rect, int tiles_x, uint32_t* __restrict__ pair_tile,
+// One (tile, Gaussian) pair per covered tile, Gaussians in index order, at the exclusive scan
+// of tiles_touched; writes beyond the P pairs counted are dropped.
+__global__ void emit_pairs(int N, const int32_t* __restrict__ tiles, const uint32_t* __restrict__ offsets,
+                           const int4* __restrict__ rect, int tiles_x, int64_t P, uint32_t* __restrict__ pair_tile,
                            uint32_t* __restrict__ pair_gauss) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    const uint32_t g = order[k];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
     const int4 r = rect[g];
-    uint32_t o = offsets[k];
-    for (int ty = r.y; ty < r.w; ++ty)
-        for (int tx = r.x; tx < r.z; ++tx) {
+    const int n = max(0, min(tiles[g], (r.z - r.x) * (r.w - r.y)));
+    int64_t o = offsets[g];
+    int k = 0;
+    for (int ty = r.y; ty < r.w && k < n; ++ty)
+        for (int tx = r.x; tx < r.z && k < n; ++tx, ++k, ++o) {
+            if (o >= P) return;
             pair_tile[o] = (uint32_t)(ty * tiles_x + tx);
-            pair_gauss[o] = g;
-            ++o;
+            pair_gauss[o] = (uint32_t)g;
         }
+}
+
+// Per-tile depth order.  The tile lists arrive in Gaussian index order (the stable tile sort of
+// the index-ordered pairs); each is sorted on the 64-bit key (binary32 depth bits, index), i.e.
+// by depth with ties in index order (visible depths are > z_near > 0, so their bits order like
+// the values).  Lists of up to kTsCap keys are sorted in shared memory by a bitonic network;
+// longer ones are cut into kTsCap runs sorted the same way and merged pairwise through the
+// scratch buffers (two arrays of P keys, each tile using its own segment).
+constexpr int kTsThreads = 256;
+constexpr int kTsCap = 4096;
+
+__device__ __forceinline__ uint64_t depth_index_key(const float* __restrict__ depth, uint32_t g) {
+    return ((uint64_t)__float_as_uint(depth[g]) << 32) | g;
+}
+
+// Bitonic sort of s[0, n2) (n2 a power of two) by the whole block, ascending.
+__device__ void block_bitonic(uint64_t* s, int n2) {
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint64_t a = s[i], b = s[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        s[i] = b;
+                        s[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Number of elements taken from a (length na) among the first `diag` outputs of the merge of
+// a and b (length nb): the merge-path split, ties taken from a first.
+__device__ __forceinline__ int merge_split(const uint64_t* a, int na, const uint64_t* b, int nb, int diag) {
+    int lo = max(0, diag - nb), hi = min(diag, na);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= b[diag - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kTsThreads) tile_depth_sort(const int2* __restrict__ ranges,
+                                                              const float* __restrict__ depth,
+                                                              int32_t* __restrict__ ids, uint64_t* __restrict__ buf0,
+                                                              uint64_t* __restrict__ buf1, const uint32_t* err) {
+    __shared__ uint64_t s[kTsCap];
+    if (*err) return;
+    const int2 r = ranges[blockIdx.x];
+    const int L = r.y - r.x;
+    if (L <= 1) return;
+    int32_t* list = ids + r.x;
+    if (L <= kTsCap) {
+        int n2 = 1;
+        while (n2 < L) n2 <<= 1;
+        for (int i = threadIdx.x; i < n2; i += blockDim.x)
+            s[i] = i < L ? depth_index_key(depth, (uint32_t)list[i]) : ~0ull;
+        __syncthreads();
+        block_bitonic(s, n2);
+        for (int i = threadIdx.x; i < L; i += blockDim.x) list[i] = (int32_t)(uint32_t)s[i];
+        return;
+    }
+    // long list: sorted runs of kTsCap keys, then pairwise merges
+    uint64_t* src = buf0 + r.x;
+    uint64_t* dst = buf1 + r.x;
+    for (int c0 = 0; c0 < L; c0 += kTsCap) {
+        const int n = min(kTsCap, L - c0);
+        for (int i = threadIdx.x; i < kTsCap; i += blockDim.x)
+            s[i] = i < n ? depth_index_key(depth, (uint32_t)list[c0 + i]) : ~0ull;
+        __syncthreads();
+        block_bitonic(s, kTsCap);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) src[c0 + i] = s[i];
+        __syncthreads();
+    }
+    for (int width = kTsCap; width < L; width <<= 1) {
+        for (int m0 = 0; m0 < L; m0 += 2 * width) {
+            const int na = min(width, L - m0), nb = max(0, min(width, L - m0 - width));
+            const uint64_t* a = src + m0;
+            const uint64_t* b = a + na;
+            const int total = na + nb;
+            const int per = (total + blockDim.x - 1) / blockDim.x;
+            const int d0 = min(total, (int)threadIdx.x * per), d1 = min(total, d0 + per);
+            int ia = merge_split(a, na, b, nb, d0), ib = d0 - ia;
+            for (int o = d0; o < d1; ++o) {
+                const bool take_a = ib >= nb || (ia < na && a[ia] <= b[ib]);
+                dst[m0 + o] = take_a ? a[ia++] : b[ib++];
+            }
+        }
+        __syncthreads();
+        uint64_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) list[i] = (int32_t)(uint32_t)src[i];
 }
 
 // A sort whose look-back gave up (*err) leaves every tile empty (the ranges were cleared).
@@ -393,80 +453,67 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
         bins->num_pairs = 0;
         return LATENTAM_OK;
     }
-    const size_t nbytes = sizeof(uint32_t) * (size_t)N;
-    uint32_t* dk[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_K0, nbytes)),
-                       static_cast<uint32_t*>(ws(ctx, WS_SORT_K1, nbytes))};
-    uint32_t* dv[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_V0, nbytes)),
-                       static_cast<uint32_t*>(ws(ctx, WS_SORT_V1, nbytes))};
     uint32_t* off = static_cast<uint32_t*>(ws(ctx, WS_OFFSETS, sizeof(uint32_t) * ((size_t)N + 1)));
     uint32_t* cnt = static_cast<uint32_t*>(ws(ctx, WS_COUNTERS, 64));
-    if (!dk[0] || !dk[1] || !dv[0] || !dv[1] || !off || !cnt) return LATENTAM_ERR_OUT_OF_MEMORY;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((N + threads - 1) / threads);
-    // 0. visible Gaussians (flags -> offsets, count V into cnt[0]) and the pair count P (cnt[1])
-    // cnt[2]: raised by a sort pass whose look-back gave up; it outlives the call and is
-    // reported (and cleared) by the next binning's host read
+    if (!off || !cnt) return LATENTAM_ERR_OUT_OF_MEMORY;
+    // 0. pair offsets (exclusive scan of tiles_touched) and the pair count P into cnt[1].
+    //    cnt[2]: raised by a sort pass whose look-back gave up; it outlives the call and is
+    //    reported (and cleared) by the next binning's host read
     e = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), st);
     if (e != cudaSuccess) return cuda_error(e, "memset counters");
-    visible_flags<<<blocks, threads, 0, st>>>(N, proj.tiles_touched, dv[1], cnt);
-    LAT_CHECK_LAUNCH("visible_flags");
-    LAT_TRY(scan_exclusive_u32(ctx, dv[1], off, N, cnt, st));
+    LAT_TRY(scan_exclusive_u32(ctx, reinterpret_cast<const uint32_t*>(proj.tiles_touched), off, N, cnt + 1, st));
     uint32_t VP[3] = {0, 0, 0};
     e = cudaMemcpyAsync(VP, cnt, sizeof(VP), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_error(e, "read visible and pair counts");
+    if (e != cudaSuccess) return cuda_error(e, "read the pair count");
     e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_error(e, "sync for the counts");
+    if (e != cudaSuccess) return cuda_error(e, "sync for the pair count");
     if (VP[2]) {
         e = cudaMemsetAsync(cnt + 2, 0, sizeof(uint32_t), st);
         if (e != cudaSuccess) return cuda_error(e, "clear the sort error word");
         set_error("a radix sort look-back wait gave up in an earlier binning (its tiles were left empty)");
         return LATENTAM_ERR_TIMEOUT;
     }
-    const int64_t V = (int64_t)VP[0], P = (int64_t)VP[1];
+    const int64_t P = (int64_t)VP[1];
     bins->num_pairs = P;
     if (P > bins->capacity) {
         set_error("pair buffer holds %lld pairs, %lld needed", (long long)bins->capacity, (long long)P);
         return LATENTAM_ERR_CAPACITY;
     }
-    if (P == 0 || V == 0) return LATENTAM_OK;
-    // Steps 1-5 depend on the host only through V and P: the same frame binned again (the
-    // iterations of one keyframe, each call of Stage I and II) replays one captured graph.
+    if (P == 0) return LATENTAM_OK;
+    // Steps 1-4 depend on the host only through P: the same frame binned again (the iterations
+    // of one keyframe, each call of Stage I and II) replays one captured graph.
     const size_t pbytes = sizeof(uint32_t) * (size_t)P;
     const int tile_bits = std::max(1, ceil_log2(num_tiles));
-    auto rest = [&, V, P](cudaStream_t s) -> latentam_status {
-        // 1. visible Gaussians by depth key (index order kept among equal keys)
-        depth_keys<<<blocks, threads, 0, s>>>(N, proj.depth, proj.tiles_touched, off, dk[0], dv[0]);
-        LAT_CHECK_LAUNCH("depth_keys");
-        int r = 0;
-        LAT_TRY(radix_sort_pairs(ctx, dk, dv, false, V, 32, &r, cnt + 2, s));
-        const uint32_t* order = dv[r];
-        // 2. pair offsets in depth order
-        const unsigned vblocks = (unsigned)((V + threads - 1) / threads);
-        uint32_t* counts = dk[1 - r];
-        gather_tiles<<<vblocks, threads, 0, s>>>((int)V, order, proj.tiles_touched, counts);
-        LAT_CHECK_LAUNCH("gather_tiles");
-        LAT_TRY(scan_exclusive_u32(ctx, counts, off, V, nullptr, s));
-        // 3. emission in depth order; 4. stable sort on the tile bits.  The depth order stays
-        // in its own slot (WS_SORT_V*), the key slots may be regrown: their contents are consumed.
-        uint32_t* pk[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_K0, std::max(pbytes, nbytes))),
-                           static_cast<uint32_t*>(ws(ctx, WS_SORT_K1, std::max(pbytes, nbytes)))};
-        uint32_t* pv[2] = {static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX, pbytes)),
-                           static_cast<uint32_t*>(ws(ctx, WS_DEC_AUX2, pbytes))};
-        if (!pk[0] || !pk[1] || !pv[0] || !pv[1]) return LATENTAM_ERR_OUT_OF_MEMORY;
-        order = static_cast<const uint32_t*>(ctx->slot_ptr[r == 0 ? WS_SORT_V0 : WS_SORT_V1]);
-        emit_pairs<<<vblocks, threads, 0, s>>>((int)V, order, off, reinterpret_cast<const int4*>(proj.rect),
-                                               cam.tiles_x, pk[0], pv[0]);
+    const int passes = (tile_bits + 7) / 8;
+    uint32_t* pk[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_K0, pbytes)),
+                       static_cast<uint32_t*>(ws(ctx, WS_SORT_K1, pbytes))};
+    uint32_t* scratch = static_cast<uint32_t*>(ws(ctx, WS_SORT_V0, pbytes));
+    uint64_t* lng = static_cast<uint64_t*>(ws(ctx, WS_SORT_V1, 2 * sizeof(uint64_t) * (size_t)P));
+    if (!pk[0] || !pk[1] || !scratch || !lng) return LATENTAM_ERR_OUT_OF_MEMORY;
+    // the tile sort's result lands in buffer passes % 2: make that the caller's pair list
+    uint32_t* ids = reinterpret_cast<uint32_t*>(bins->pair_ids);
+    uint32_t* pv[2] = {passes % 2 == 0 ? ids : scratch, passes % 2 == 0 ? scratch : ids};
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((N + threads - 1) / threads);
+    auto rest = [&, P](cudaStream_t s) -> latentam_status {
+        // 1. pairs in Gaussian index order
+        emit_pairs<<<blocks, threads, 0, s>>>(N, proj.tiles_touched, off, reinterpret_cast<const int4*>(proj.rect),
+                                              cam.tiles_x, P, pk[0], pv[0]);
         LAT_CHECK_LAUNCH("emit_pairs");
+        // 2. stable sort on the tile bits (index order kept within a tile)
+        int r = 0;
         LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, cnt + 2, s));
-        cudaError_t e2 = cudaMemcpyAsync(bins->pair_ids, pv[r], pbytes, cudaMemcpyDeviceToDevice, s);
-        if (e2 != cudaSuccess) return cuda_error(e2, "copy pair ids");
-        // 5. ranges
+        // 3. ranges
         tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(pk[r], P, cnt + 2,
-                                                             reinterpret_cast<int2*>(bins->tile_ranges));
+                                                                 reinterpret_cast<int2*>(bins->tile_ranges));
         LAT_CHECK_LAUNCH("tile_ranges");
+        // 4. depth order within each tile
+        tile_depth_sort<<<(unsigned)num_tiles, kTsThreads, 0, s>>>(reinterpret_cast<const int2*>(bins->tile_ranges),
+                                                                   proj.depth, bins->pair_ids, lng, lng + P, cnt + 2);
+        LAT_CHECK_LAUNCH("tile_depth_sort");
         return LATENTAM_OK;
     };
-    const uint64_t key[] = {(uint64_t)N, (uint64_t)V, (uint64_t)P, (uint64_t)num_tiles, (uint64_t)cam.tiles_x,
+    const uint64_t key[] = {(uint64_t)N, (uint64_t)P, (uint64_t)num_tiles, (uint64_t)cam.tiles_x,
                             reinterpret_cast<uint64_t>(proj.depth), reinterpret_cast<uint64_t>(proj.tiles_touched),
                             reinterpret_cast<uint64_t>(proj.rect), reinterpret_cast<uint64_t>(bins->pair_ids),
                             reinterpret_cast<uint64_t>(bins->tile_ranges), reinterpret_cast<uint64_t>(st),

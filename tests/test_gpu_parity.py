@@ -56,6 +56,13 @@ def _gpu_front(api, ctx, s):
     return proj, bins
 
 
+def _filtered_lists(off, ids, amb):
+    """Tile index and Gaussian of every list entry whose Gaussian is not rect-ambiguous."""
+    tile = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    keep = ~np.isin(ids, amb)
+    return tile[keep], ids[keep]
+
+
 def _rel_rows(a, b, floor):
     num = np.linalg.norm(a - b, axis=1)
     den = np.maximum(np.linalg.norm(b, axis=1), floor)
@@ -100,6 +107,26 @@ def test_sort_matches_oracle_tile_lists(api, ctx, name):
         assert got == want, f"tile {t}"
     if not amb:
         assert bins.num_pairs == len(ids)
+
+
+@pytest.mark.parametrize("w,n", [(16, 12000), (32, 20000)])
+def test_sort_long_tile_lists(api, ctx, w, n):
+    """Tile lists longer than the 4096 keys a tile sorts in shared memory (12000 in one tile;
+    about 13.6k and 14.8k in two): sorted runs merged pairwise, bit-exact against the oracle."""
+    s = random_scene(21, n=n, d=16, M=16, D=128, width=w, height=16, log_scale=-2.0)
+    proj, bins = _gpu_front(api, ctx, s)
+    o = oracle.project_scene(s)
+    off, ids = oracle.tile_lists(o, s.camera)
+    assert np.diff(off).max() > 4096
+    amb = np.nonzero(o["rect_ambiguous"])[0]
+    ranges = bins.tile_ranges.cpu().numpy().astype(np.int64)
+    goff = np.zeros(len(ranges) + 1, np.int64)
+    goff[1:] = np.cumsum(ranges[:, 1] - ranges[:, 0])
+    pairs = bins.pair_ids[:bins.num_pairs].cpu().numpy().astype(np.int64)
+    gt, gg = _filtered_lists(goff, pairs, amb)
+    wt, wg = _filtered_lists(off, ids.astype(np.int64), amb)
+    np.testing.assert_array_equal(gt, wt)
+    np.testing.assert_array_equal(gg, wg)
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -349,13 +376,6 @@ def test_max_dictionary_shape(api, ctx):
 @pytest.fixture(scope="module")
 def room():
     return room_scene(0)
-
-
-def _filtered_lists(off, ids, amb):
-    """Tile index and Gaussian of every list entry whose Gaussian is not rect-ambiguous."""
-    tile = np.repeat(np.arange(len(off) - 1), np.diff(off))
-    keep = ~np.isin(ids, amb)
-    return tile[keep], ids[keep]
 
 
 def test_full_size_bins_match_oracle(api, ctx, room):
