@@ -48,7 +48,8 @@ struct GraphKey {
     }
 };
 struct GraphCache {
-    static constexpr int kSlots = 16;  // a batch of keyframes bins each of its frames
+    // a batch of up to LATENTAM_MAX_BATCH keyframes bins each frame in two captured phases
+    static constexpr int kSlots = 2 * LATENTAM_MAX_BATCH + 8;
     GraphKey key[kSlots];
     cudaGraphExec_t exec[kSlots] = {};
     int64_t launches[kSlots] = {};
@@ -453,6 +454,7 @@ latentam_status latentam_ctx_create(int32_t device, latentam_ctx** out) {
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->step_dev, sizeof(int));
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&c->host_counts), 16, cudaHostAllocDefault);
     if (e != cudaSuccess || !c->graphs || !c->sort_graphs) {
         latentam_ctx_destroy(c);
         if (e != cudaSuccess) return cuda_error(e, "context stream / counter");
@@ -484,6 +486,7 @@ latentam_status latentam_ctx_destroy(latentam_ctx* ctx) {
     }
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->step_dev) cudaFree(ctx->step_dev);
+    if (ctx->host_counts) cudaFreeHost(ctx->host_counts);
     delete ctx;
     if (e != cudaSuccess) return cuda_error(e, "synchronise before destroy");
     return LATENTAM_OK;

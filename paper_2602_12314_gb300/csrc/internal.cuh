@@ -107,7 +107,8 @@ struct latentam_ctx {
     cudaStream_t cap_stream;
     int* step_dev;
     lat::GraphCache* graphs;
-    lat::GraphCache* sort_graphs;  // the binning after its host read (see cached_launch)
+    lat::GraphCache* sort_graphs;  // the binning before and after its host read (see cached_launch)
+    uint32_t* host_counts;         // pinned: the binning's counts read back by the host
     // autotuned split factors of the pixel reductions (see latentam_autotune_enable)
     int autotune;
     struct TuneEntry {
