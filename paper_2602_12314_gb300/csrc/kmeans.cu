@@ -358,11 +358,10 @@ latentam_status stream_kmeans(latentam_ctx* ctx, const KMeansArgs& a, cudaStream
         o += up(bytes);
         return p;
     };
+    // the buffers whose sizes do not depend on n first: their addresses (and the global
+    // phase's captured graph) then stay the same from one keyframe to the next
     float* mC = a.micro_C ? a.micro_C : reinterpret_cast<float*>(take(4 * (size_t)k * D));
     float* mW = a.micro_W ? a.micro_W : reinterpret_cast<float*>(take(4 * (size_t)k));
-    int32_t* asg = a.micro_assign ? a.micro_assign : reinterpret_cast<int32_t*>(take(4 * (size_t)std::max<int64_t>(n, 1)));
-    float* part = reinterpret_cast<float*>(take(4 * (size_t)nb * k * D));
-    float* pcnt = reinterpret_cast<float*>(take(4 * (size_t)nb * k));
     MergeBufs mb;
     mb.n_points = reinterpret_cast<int32_t*>(take(4));
     mb.pt_src = reinterpret_cast<int32_t*>(take(4 * KP));
@@ -373,52 +372,76 @@ latentam_status stream_kmeans(latentam_ctx* ctx, const KMeansArgs& a, cudaStream
     float* nrm = reinterpret_cast<float*>(take(4 * (size_t)K));
     float* Pm = reinterpret_cast<float*>(take(4 * KP * D));
     float* G = reinterpret_cast<float*>(take(4 * KP * ldg));
+    int32_t* asg = a.micro_assign ? a.micro_assign : reinterpret_cast<int32_t*>(take(4 * (size_t)std::max<int64_t>(n, 1)));
+    float* part = reinterpret_cast<float*>(take(4 * (size_t)nb * k * D));
+    float* pcnt = reinterpret_cast<float*>(take(4 * (size_t)nb * k));
 
-    // local phase
+    // Both phases are chains of small dependent launches with no host round trip: each replays
+    // a captured CUDA graph once the same shapes and buffers recur (the global phase's shapes
+    // are the dictionary's, the same for every keyframe; the local phase's depend on the
+    // number of targets).
     const size_t sm_assign = 4 * ((size_t)k * D + k);
     const int G_rows = kAccumThreads / (D / 4);
     const size_t sm_accum = 4 * (size_t)G_rows * k * D;
-    cudaFuncSetAttribute(local_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_assign);
-    cudaFuncSetAttribute(local_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_accum);
-    local_init<<<k, 256, 0, st>>>(a.F, n, D, a.init_idx, mC);
-    LAT_CHECK_LAUNCH("kmeans local_init");
     const int ga = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 4 * (int64_t)ctx->num_sms));
-    for (int it = 0; it < a.iters_local; ++it) {
-        if (n > 0) {
-            local_assign<<<ga, 256, sm_assign, st>>>(a.F, n, D, a.valid, mC, k, asg);
-            LAT_CHECK_LAUNCH("kmeans local_assign");
-            local_accum<<<nb, kAccumThreads, sm_accum, st>>>(a.F, n, D, asg, k, R, part, pcnt);
-            LAT_CHECK_LAUNCH("kmeans local_accum");
-        } else {
-            cudaError_t e = cudaMemsetAsync(pcnt, 0, 4 * (size_t)nb * k, st);
-            if (e != cudaSuccess) return cuda_error(e, "clear kmeans counts");
-            e = cudaMemsetAsync(part, 0, 4 * (size_t)nb * k * D, st);
-            if (e != cudaSuccess) return cuda_error(e, "clear kmeans sums");
+    auto local = [&](cudaStream_t s) -> latentam_status {
+        cudaFuncSetAttribute(local_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_assign);
+        cudaFuncSetAttribute(local_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_accum);
+        local_init<<<k, 256, 0, s>>>(a.F, n, D, a.init_idx, mC);
+        LAT_CHECK_LAUNCH("kmeans local_init");
+        for (int it = 0; it < a.iters_local; ++it) {
+            if (n > 0) {
+                local_assign<<<ga, 256, sm_assign, s>>>(a.F, n, D, a.valid, mC, k, asg);
+                LAT_CHECK_LAUNCH("kmeans local_assign");
+                local_accum<<<nb, kAccumThreads, sm_accum, s>>>(a.F, n, D, asg, k, R, part, pcnt);
+                LAT_CHECK_LAUNCH("kmeans local_accum");
+            } else {
+                cudaError_t e = cudaMemsetAsync(pcnt, 0, 4 * (size_t)nb * k, s);
+                if (e != cudaSuccess) return cuda_error(e, "clear kmeans counts");
+                e = cudaMemsetAsync(part, 0, 4 * (size_t)nb * k * D, s);
+                if (e != cudaSuccess) return cuda_error(e, "clear kmeans sums");
+            }
+            local_finish<<<(unsigned)(((int64_t)k * D + 255) / 256), 256, 0, s>>>(part, pcnt, nb, k, D, mC, mW);
+            LAT_CHECK_LAUNCH("kmeans local_finish");
         }
-        local_finish<<<(unsigned)(((int64_t)k * D + 255) / 256), 256, 0, st>>>(part, pcnt, nb, k, D, mC, mW);
-        LAT_CHECK_LAUNCH("kmeans local_finish");
-    }
-
-    // global phase
-    cudaError_t e = cudaMemsetAsync(Pm, 0, 4 * KP * D, st);
-    if (e != cudaSuccess) return cuda_error(e, "clear kmeans points");
-    e = cudaMemsetAsync(pa, 0xff, 4 * KP, st);  // -1 past the last point
-    if (e != cudaSuccess) return cuda_error(e, "clear kmeans point assignment");
-    global_merge<<<1, 1024, 0, st>>>(a.weights, K, mW, k, mb);
-    LAT_CHECK_LAUNCH("kmeans global_merge");
-    global_points<<<(unsigned)KP, 256, 0, st>>>(a.centres, mC, D, mb, Pm);
-    LAT_CHECK_LAUNCH("kmeans global_points");
-    global_fill<<<K, 256, 0, st>>>(mC, D, mb, a.centres);
-    LAT_CHECK_LAUNCH("kmeans global_fill");
-    for (int it = 0; it < a.iters_global; ++it) {
-        centre_norms<<<(K + 7) / 8, 256, 0, st>>>(a.centres, K, D, nrm);
-        LAT_CHECK_LAUNCH("kmeans centre_norms");
-        LAT_TRY(sgemm_abt(Pm, (int64_t)KP, a.centres, K, D, G, (int64_t)ldg, 1.0f, st));
-        global_assign<<<(unsigned)((KP + 7) / 8), 256, 0, st>>>(G, (int64_t)ldg, nrm, K, mb, pa);
-        LAT_CHECK_LAUNCH("kmeans global_assign");
-        global_update<<<K, 256, 0, st>>>(Pm, D, mb, pa, a.centres, a.weights);
-        LAT_CHECK_LAUNCH("kmeans global_update");
-    }
+        return LATENTAM_OK;
+    };
+    auto global = [&](cudaStream_t s) -> latentam_status {
+        cudaError_t e = cudaMemsetAsync(Pm, 0, 4 * KP * D, s);
+        if (e != cudaSuccess) return cuda_error(e, "clear kmeans points");
+        e = cudaMemsetAsync(pa, 0xff, 4 * KP, s);  // -1 past the last point
+        if (e != cudaSuccess) return cuda_error(e, "clear kmeans point assignment");
+        global_merge<<<1, 1024, 0, s>>>(a.weights, K, mW, k, mb);
+        LAT_CHECK_LAUNCH("kmeans global_merge");
+        global_points<<<(unsigned)KP, 256, 0, s>>>(a.centres, mC, D, mb, Pm);
+        LAT_CHECK_LAUNCH("kmeans global_points");
+        global_fill<<<K, 256, 0, s>>>(mC, D, mb, a.centres);
+        LAT_CHECK_LAUNCH("kmeans global_fill");
+        for (int it = 0; it < a.iters_global; ++it) {
+            centre_norms<<<(K + 7) / 8, 256, 0, s>>>(a.centres, K, D, nrm);
+            LAT_CHECK_LAUNCH("kmeans centre_norms");
+            LAT_TRY(sgemm_abt(Pm, (int64_t)KP, a.centres, K, D, G, (int64_t)ldg, 1.0f, s));
+            global_assign<<<(unsigned)((KP + 7) / 8), 256, 0, s>>>(G, (int64_t)ldg, nrm, K, mb, pa);
+            LAT_CHECK_LAUNCH("kmeans global_assign");
+            global_update<<<K, 256, 0, s>>>(Pm, D, mb, pa, a.centres, a.weights);
+            LAT_CHECK_LAUNCH("kmeans global_update");
+        }
+        return LATENTAM_OK;
+    };
+    const uint64_t lkey[] = {0x6b6d2d6c6f63616cull /* tag: local phase */, (uint64_t)n, (uint64_t)D, (uint64_t)k,
+                             (uint64_t)a.iters_local, reinterpret_cast<uint64_t>(a.F),
+                             reinterpret_cast<uint64_t>(a.valid), reinterpret_cast<uint64_t>(a.init_idx),
+                             reinterpret_cast<uint64_t>(mC), reinterpret_cast<uint64_t>(mW),
+                             reinterpret_cast<uint64_t>(asg), reinterpret_cast<uint64_t>(base),
+                             reinterpret_cast<uint64_t>(st), ctx->ws_generation};
+    LAT_TRY(cached_launch(ctx, lkey, (int)(sizeof(lkey) / sizeof(lkey[0])), st, local));
+    const uint64_t gkey[] = {0x6b6d2d676c6f6262ull /* tag: global phase */, (uint64_t)D, (uint64_t)k, (uint64_t)K,
+                             (uint64_t)a.iters_global, reinterpret_cast<uint64_t>(a.centres),
+                             reinterpret_cast<uint64_t>(a.weights), reinterpret_cast<uint64_t>(mC),
+                             reinterpret_cast<uint64_t>(mW), reinterpret_cast<uint64_t>(pa),
+                             reinterpret_cast<uint64_t>(Pm), reinterpret_cast<uint64_t>(G),
+                             reinterpret_cast<uint64_t>(base), reinterpret_cast<uint64_t>(st), ctx->ws_generation};
+    LAT_TRY(cached_launch(ctx, gkey, (int)(sizeof(gkey) / sizeof(gkey[0])), st, global));
     return LATENTAM_OK;
 }
 
