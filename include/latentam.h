@@ -202,11 +202,13 @@ LATENTAM_API latentam_status latentam_project(latentam_ctx* ctx, const latentam_
                                  const latentam_camera* cam, const latentam_projected* out,
                                  latentam_stream stream);
 
-/* Bin and sort: order visible Gaussians by depth key (stable radix sort, so ties keep
- * index order), emit one pair per covered tile, stable radix sort of the pairs by tile,
- * then per-tile ranges.  SYNCHRONISES `stream` once to read the pair count P into
- * bins->num_pairs; if P > bins->capacity returns LATENTAM_ERR_CAPACITY and writes no
- * pairs (retry with a larger buffer). */
+/* Bin and sort: emit one (tile, Gaussian) pair per covered tile in Gaussian index order,
+ * stable radix sort of the pairs by tile, per-tile ranges, then each tile's list sorted by
+ * (binary32 depth key, index): the front-to-back order, ties in index order.
+ * SYNCHRONISES `stream` once to read the pair count P into bins->num_pairs; if
+ * P > bins->capacity returns LATENTAM_ERR_CAPACITY and writes no pairs (retry with a larger
+ * buffer).  Returns LATENTAM_ERR_TIMEOUT if a bounded wait of an EARLIER call's sort gave up
+ * (that call's tiles were left empty). */
 LATENTAM_API latentam_status latentam_sort(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
                               const latentam_camera* cam, latentam_bins* bins,
                               latentam_stream stream);
@@ -220,9 +222,10 @@ LATENTAM_API latentam_status latentam_render_fwd(latentam_ctx* ctx, int32_t n, c
                                     int32_t* n_contrib, latentam_stream stream);
 
 /* Gradient of the blend with respect to the queries: df_i = sum_p w_ip dQ_p with the
- * blend weights w_ip = alpha_ip T_ip recomputed front to back (no division), reduced
- * over each warp before one atomic add per warp and channel.  n_contrib is the output
- * of latentam_render_fwd for the same inputs.  df is N x d (overwritten). */
+ * blend weights w_ip = alpha_ip T_ip recomputed front to back (no division) into shared
+ * memory per tile and batch, summed over the tile's pixels, one atomic add per Gaussian,
+ * channel and tile.  n_contrib is the output of latentam_render_fwd for the same inputs.
+ * df is N x d (overwritten). */
 LATENTAM_API latentam_status latentam_render_bwd(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
                                     const latentam_camera* cam, const latentam_bins* bins,
                                     const int32_t* n_contrib, const float* dQ, int32_t d,
