@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_add(uint32_t* __restrict__ 
 // ---- radix sort ---------------------------------------------------------------------
 
 constexpr int kRsThreads = 256;
-constexpr int kRsItems = 8;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 2048; warp w owns items [256 w, 256 w + 256)
+constexpr int kRsItems = 4;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 1024; warp w owns items [128 w, 128 w + 128)
 constexpr int kRadix = 256;
 
 // Look-back words of the one-sweep passes: per (block, digit) the block's own count of the
@@ -154,9 +154,9 @@ __global__ void __launch_bounds__(kRsThreads) radix_digit_counts(const uint32_t*
         if (h[p][t]) atomicAdd(&counts[p * kRadix + t], h[p][t]);
 }
 
-// One stable LSD pass in a single launch.  Each block takes the next 2048-key tile in input
+// One stable LSD pass in a single launch.  Each block takes the next 1024-key tile in input
 // order (a ticket, so that every tile before it belongs to a block already running), ranks
-// its keys by digit in input order (warp w owns keys [256 w, 256 w + 256) of the tile), posts
+// its keys by digit in input order (warp w owns keys [128 w, 128 w + 128) of the tile), posts
 // its per-digit counts, and adds the counts of the earlier tiles by walking back over their
 // posted words until it meets an inclusive one (decoupled look-back).  The waits are bounded:
 // a walk that gives up raises *err and uses what it summed (every position stays below n).

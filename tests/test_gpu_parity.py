@@ -379,7 +379,7 @@ def room():
 
 
 def test_full_size_bins_match_oracle(api, ctx, room):
-    """640x480, 300k Gaussians (1200 tiles, about 117k pairs: dozens of 2048-key blocks in
+    """640x480, 300k Gaussians (1200 tiles, about 117k pairs: over a hundred 1024-key blocks in
     every pass of the sort, each finding its offsets by look-back): every tile's list equals the
     oracle's (depth, index) order, bit for bit, apart from the Gaussians whose tile rect is
     ambiguous."""
