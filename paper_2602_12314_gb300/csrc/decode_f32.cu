@@ -961,6 +961,89 @@ int tile_splits(int num_sms, int64_t m_ext, int64_t n_ext, int64_t k_ext) {
     return (int)z;
 }
 
+// S = c Q K^T and its row softmax for d = 32 queries and M = 32 MU <= 256 atoms (the attention
+// weights A and the row statistics (max, sum) only): a persistent CTA stages K^T once, then
+// takes 64-row tiles; warp w owns rows 8 w .. 8 w + 7 and lane l the atoms l + 32 u, so each row's
+// max and sum are warp reductions and every K value read from shared memory feeds 8 rows.
+// The arithmetic of every row is dec_rows_fwd's, in the same order (S accumulated over k in
+// order and scaled by c, the per-lane sums over u in order, then the same warp reduction), so
+// A and the statistics are the same numbers.
+constexpr int kAttnRows = 64;
+template <int MU>
+__global__ void __launch_bounds__(256, 2) attn_rows_d32(const float* __restrict__ Q, int64_t n,
+                                                         const float* __restrict__ K, float c,
+                                                         float* __restrict__ A_out, float* __restrict__ stats_out) {
+    constexpr int DQ = 32, M = 32 * MU;
+    __shared__ __align__(16) float sKt[DQ][M];              // K transposed: atom j at column j
+    __shared__ __align__(16) float sQt[DQ][kAttnRows + 4];  // the tile's queries transposed
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int e = t; e < M * DQ; e += 256) {  // consecutive threads: consecutive atoms (no bank conflict)
+        const int k = e / M, j = e % M;
+        sKt[k][j] = K[j * DQ + k];
+    }
+    const int64_t tiles = (n + kAttnRows - 1) / kAttnRows;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t row0 = tile * kAttnRows;
+        __syncthreads();  // K staged / the previous tile's queries read
+        for (int e = t; e < kAttnRows * DQ / 4; e += 256) {
+            const int r = e / (DQ / 4), k4 = (e % (DQ / 4)) * 4;
+            const float4 q = (row0 + r < n) ? *reinterpret_cast<const float4*>(Q + (row0 + r) * DQ + k4)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            sQt[k4][r] = q.x;
+            sQt[k4 + 1][r] = q.y;
+            sQt[k4 + 2][r] = q.z;
+            sQt[k4 + 3][r] = q.w;
+        }
+        __syncthreads();
+        float s[8][MU];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int u = 0; u < MU; ++u) s[r][u] = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < DQ; ++k) {
+            const float4 q0 = *reinterpret_cast<const float4*>(&sQt[k][warp * 8]);
+            const float4 q1 = *reinterpret_cast<const float4*>(&sQt[k][warp * 8 + 4]);
+            const float q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+            float kv[MU];
+#pragma unroll
+            for (int u = 0; u < MU; ++u) kv[u] = sKt[k][lane + 32 * u];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int u = 0; u < MU; ++u) s[r][u] += q[r] * kv[u];
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int64_t p = row0 + warp * 8 + r;
+            float a[MU];
+            float m = -INFINITY;
+#pragma unroll
+            for (int u = 0; u < MU; ++u) {
+                a[u] = c * s[r][u];
+                m = fmaxf(m, a[u]);
+            }
+            m = warp_max(m);
+            float l = 0.f;
+#pragma unroll
+            for (int u = 0; u < MU; ++u) {
+                a[u] = __expf(a[u] - m);
+                l += a[u];
+            }
+            l = warp_sum(l);
+            const float il = 1.0f / l;
+            if (p < n) {
+#pragma unroll
+                for (int u = 0; u < MU; ++u) A_out[p * M + lane + 32 * u] = a[u] * il;
+                if (lane == 0 && stats_out) {
+                    stats_out[2 * p] = m;
+                    stats_out[2 * p + 1] = l;
+                }
+            }
+        }
+    }
+}
+
 size_t rows_fwd_smem(int d, int M) { return sizeof(float) * ((size_t)kRows * M + (size_t)d * (kAtomChunk + 1) + (size_t)kRows * d); }
 size_t rows_bwd_smem(int M) { return sizeof(float) * ((size_t)kRows * M + (size_t)kAtomChunk * 33 + (size_t)kRows * 33); }
 
@@ -969,6 +1052,20 @@ latentam_status launch_rows_fwd(const float* Q, int64_t n, const float* K, const
                                 const void* F, latentam_dtype F_dtype, const uint8_t* mask,
                                 const latentam_loss_cfg& cfg, double* acc, float* A_out, float* Fh, float* row,
                                 float* stats, cudaStream_t st) {
+    if constexpr (DQ == 32 && MODE == 2) {
+        if (M == 64 || M == 128 || M == 256) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const unsigned blocks =
+                (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + kAttnRows - 1) / kAttnRows, 2 * (int64_t)sms));
+            if (M == 64) attn_rows_d32<2><<<blocks, 256, 0, st>>>(Q, n, K, c, A_out, stats);
+            else if (M == 128) attn_rows_d32<4><<<blocks, 256, 0, st>>>(Q, n, K, c, A_out, stats);
+            else attn_rows_d32<8><<<blocks, 256, 0, st>>>(Q, n, K, c, A_out, stats);
+            LAT_CHECK_LAUNCH("attn_rows_d32");
+            return LATENTAM_OK;
+        }
+    }
     const size_t smem = rows_fwd_smem(DQ, M);
     auto kern = dec_rows_fwd<DQ, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -989,31 +1086,6 @@ latentam_status launch_rows_bwd(const float* dFh, const float* A, const float* r
     const unsigned blocks = (unsigned)((n + kRows - 1) / kRows);
     kern<<<blocks, kThreads, smem, st>>>(dFh, A, row, K, V, n, M, D, c, dS, dQ);
     LAT_CHECK_LAUNCH("dec_rows_bwd");
-    return LATENTAM_OK;
-}
-
-// C (nx x ny) = scale * X^T Y (+ trust-region term), split over pixels.
-latentam_status atb(latentam_ctx* ctx, const float* X, int ldx, int nx, const float* Y, int ldy, int ny, int64_t n,
-                    float scale, const float* coef, const float* V, const float* V0, float* out, cudaStream_t st) {
-    const int vec = ny >= 128 ? 4 : 1;
-    const int ct = 32 * vec;
-    const int bx = (nx + 63) / 64, by = (ny + ct - 1) / ct;
-    const int target = 2 * ctx->num_sms;
-    int64_t splits = std::max<int64_t>(1, (target + bx * by - 1) / (bx * by));
-    splits = std::min<int64_t>(splits, std::max<int64_t>(1, (n + 255) / 256));
-    const int64_t rps = std::max<int64_t>(32, ((n + splits - 1) / splits + 31) / 32 * 32);
-    splits = std::max<int64_t>(1, (n + rps - 1) / rps);
-    float* part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * (size_t)splits * nx * ny));
-    if (!part) return LATENTAM_ERR_OUT_OF_MEMORY;
-    dim3 grid((unsigned)bx, (unsigned)by, (unsigned)splits);
-    if (vec == 4)
-        atb_splitk<4><<<grid, kThreads, 0, st>>>(X, ldx, nx, Y, ldy, ny, n, rps, part);
-    else
-        atb_splitk<1><<<grid, kThreads, 0, st>>>(X, ldx, nx, Y, ldy, ny, n, rps, part);
-    LAT_CHECK_LAUNCH("atb_splitk");
-    const int64_t total = (int64_t)nx * ny;
-    reduce_splits<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, (int)splits, nx, ny, scale, coef, V, V0, out);
-    LAT_CHECK_LAUNCH("reduce_splits");
     return LATENTAM_OK;
 }
 
@@ -1123,7 +1195,7 @@ struct NoallocPlan {
     int64_t splitsV, rpsV, splitsK, rpsK;
 };
 
-// Same split rule as atb(): about two CTAs per SM, at least 256 pixels per split.
+// Split of a pixel reduction over atb_splitk: about two CTAs per SM, at least 256 pixels per split.
 void plan_split(int num_sms, int nx, int ny, int64_t n, int64_t* splits_out, int64_t* rps_out) {
     const int vec = ny >= 128 ? 4 : 1;
     const int ct = 32 * vec;
