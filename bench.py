@@ -43,7 +43,7 @@ SM_FP32_LANES = 128  # FP32 FMA lanes per SM
 # over 172,800 pixels; profiles/decode_fp32_crop480x360.md: 3,369 MB), keyed by a hash of the
 # kernel sources it was taken on: once they change, the figure no longer describes the kernels
 # and the roofline reports no traffic.
-_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800), "fp32": ("16daa1049514a475", 3368.56e6 / 172800)}
+_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800), "fp32": ("c39470a9bf516ec3", 3359.13e6 / 172800)}
 _DECODE_SOURCES = {"bf16": ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh"), "fp32": ("decode_f32.cu",)}
 
 
@@ -412,7 +412,7 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
         peak = props.multi_processor_count * SM_FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
         key, per_pixel = _DECODE_TRAFFIC["fp32"]
         traffic = per_pixel * n if key == _decode_sources_hash("fp32") and masks is None else None
-        roof = {"bound": "alu", "kernel": "decode stage (dec_rows_fwd, sgemm_tile x3, coef_rows, sgemm_narrow x2, "
+        roof = {"bound": "alu", "kernel": "decode stage (attn_rows_d32, sgemm_tile x3, coef_rows, sgemm_narrow x2, "
                                           "reduce_splits x2)",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x {SM_FP32_LANES} lanes x 2 x "
