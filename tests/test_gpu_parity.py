@@ -190,6 +190,36 @@ def test_decode_fwd_matches_oracle(api, ctx, name):
     np.testing.assert_allclose(st[:, 1], np.exp(S - S.max(1, keepdims=True)).sum(1), rtol=1e-5)
 
 
+@pytest.mark.parametrize("M", [64, 128, 256])
+def test_decode_d32_attention_kernel_shapes(api, ctx, M):
+    """d = 32 with M = 64, 128, 256 atoms (the persistent attention-weight kernel's three
+    instantiations) on a ragged pixel count (not a multiple of its 64-row tiles): Fhat and the
+    row statistics against the oracle, and the training path's gradients."""
+    rng = np.random.default_rng(M)
+    n, d, D = 1000 + M // 2 + 3, 32, 128
+    Q = rng.normal(size=(n, d)).astype(np.float32)
+    K = (rng.normal(size=(M, d)) / np.sqrt(d)).astype(np.float32)
+    V = rng.normal(size=(M, D)).astype(np.float32)
+    c = 1.0 / np.sqrt(d)
+    Fh, stats = api.decode_fwd(ctx, _dev(Q), _dev(K), _dev(V), c, api.FP32)
+    S, A, Fo = oracle.decode(Q, K, V, c)
+    assert _rel_rows(Fh.cpu().numpy().astype(np.float64), Fo, floor=1e-6).max() <= REL_Q
+    st = stats.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(st[:, 0], S.max(1), rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(st[:, 1], np.exp(S - S.max(1, keepdims=True)).sum(1), rtol=1e-5)
+    F = rng.normal(size=(n, D)).astype(np.float32)
+    mask = (rng.uniform(size=n) > 0.1).astype(np.uint8)
+    V0 = (V + 0.05 * rng.normal(size=V.shape)).astype(np.float32)
+    cfg = oracle.LossConfig()
+    out = oracle.decode(Q, K, V, cfg.c(d))
+    dQo, dKo, dVo = oracle.backward(Q, K, V, V0, out[1], out[2], F, mask, cfg)
+    _, dQ, dK, dV = api.decode_loss_bwd(ctx, _dev(Q), _dev(K), _dev(V), _dev(V0), _dev(F), _dev(mask, torch.uint8),
+                                        api.LossConfig(), api.FP32)
+    for g, go in ((dQ, dQo), (dK, dKo), (dV, dVo)):
+        g = g.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(g - go) / np.linalg.norm(go) <= REL_G
+
+
 @pytest.mark.parametrize("name", list(SCENES))
 def test_decode_loss_bwd_matches_oracle(api, ctx, name):
     s = SCENES[name]
