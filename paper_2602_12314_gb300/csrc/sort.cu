@@ -478,14 +478,14 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
     LAT_TRY(cached_launch(ctx, pre_key, (int)(sizeof(pre_key) / sizeof(pre_key[0])), st, pre));
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_error(e, "sync for the pair count");
-    const uint32_t VP[3] = {host[0], host[1], host[2]};
-    if (VP[2]) {
+    const uint32_t pairs = host[1], sort_error = host[2];
+    if (sort_error) {
         e = cudaMemsetAsync(cnt + 2, 0, sizeof(uint32_t), st);
         if (e != cudaSuccess) return cuda_error(e, "clear the sort error word");
         set_error("a radix sort look-back wait gave up in an earlier binning (its tiles were left empty)");
         return LATENTAM_ERR_TIMEOUT;
     }
-    const int64_t P = (int64_t)VP[1];
+    const int64_t P = (int64_t)pairs;
     bins->num_pairs = P;
     if (P > bins->capacity) {
         set_error("pair buffer holds %lld pairs, %lld needed", (long long)bins->capacity, (long long)P);
