@@ -13,8 +13,11 @@
  *    contiguous, 16-byte aligned (float4 access); the library never frees it.  Pointer
  *    members of the structs below follow the same rule.  Host pointers are marked "host".
  *  - The library owns only the context: a growable device workspace (sort buffers,
- *    decode intermediates, loss accumulators).  A context belongs to one device and must
- *    not be used by two host threads at once.
+ *    decode intermediates, loss accumulators, the tile launch order of the render calls).
+ *    A context belongs to one device and must not be used by two host threads at once; its
+ *    calls share the workspace, so calls that overlap on the GPU (enqueued on different
+ *    streams without an ordering event) race on it: enqueue a context's calls on one stream
+ *    or order the streams.
  *  - All work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream)
  *    and returns without waiting, except where a call says it synchronises.
  *  - Gradients are OVERWRITTEN, never accumulated; callers zero nothing.
