@@ -419,21 +419,33 @@ __global__ void __launch_bounds__(kThreads) atb_splitk(const float* __restrict__
     }
 }
 
-// out[j][k] = scale * sum_s part[s][j][k] (+ coef[j] (V - V0)[j][k] when coef != NULL)
-__global__ void reduce_splits(const float* __restrict__ part, int splits, int nx, int ny, float scale,
-                              const float* __restrict__ coef, const float* __restrict__ V,
-                              const float* __restrict__ V0, float* __restrict__ out) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// out[j][k] = scale * sum_s part[s][j][k] (+ coef[j] (V - V0)[j][k] when coef != NULL).  A CTA
+// owns 32 consecutive outputs (lane = output); warp w adds the splits w, w + 8, ... in order and
+// the eight warp sums are added in warp order, so the result does not depend on scheduling and
+// no thread walks more than splits / 8 dependent loads.
+__global__ void __launch_bounds__(256) reduce_splits(const float* __restrict__ part, int splits, int nx, int ny,
+                                                     float scale, const float* __restrict__ coef,
+                                                     const float* __restrict__ V, const float* __restrict__ V0,
+                                                     float* __restrict__ out) {
+    __shared__ float s_w[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t total = (int64_t)nx * ny;
-    if (e >= total) return;
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int k = 0; k < splits; ++k) s += part[(size_t)k * total + e];
-    s *= scale;
+    if (e < total)
+        for (int k = warp; k < splits; k += 8) s += part[(size_t)k * total + e];
+    s_w[warp][lane] = s;
+    __syncthreads();
+    if (warp != 0 || e >= total) return;
+    float r = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) r += s_w[w][lane];
+    r *= scale;
     if (coef) {
         const int j = (int)(e / ny);
-        s += coef[j] * (V[e] - V0[e]);
+        r += coef[j] * (V[e] - V0[e]);
     }
-    out[e] = s;
+    out[e] = r;
 }
 
 __global__ void finalize_loss(const double* __restrict__ acc, int D, latentam_loss_cfg cfg, double* __restrict__ parts) {
@@ -1140,8 +1152,8 @@ latentam_status loss_bwd_t(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t 
         int z = 0;
         LAT_TRY((launch_sgemm<false, false, PlainSrc, DFhatSrc, StoreTileEpi>(
             Asrc, dFsrc, M, D, n, z0, StoreTileEpi::Params{part, D, (int64_t)M * D, 1.0f}, st, &z)));
-        reduce_splits<<<(unsigned)(((int64_t)M * D + 255) / 256), 256, 0, st>>>(part, z, M, D, 1.0f, trc, a.V, a.V0,
-                                                                                a.dV);
+        reduce_splits<<<(unsigned)(((int64_t)M * D + 31) / 32), 256, 0, st>>>(part, z, M, D, 1.0f, trc, a.V, a.V0,
+                                                                               a.dV);
         LAT_CHECK_LAUNCH("reduce_splits");
     }
     if (a.dK) {
@@ -1155,8 +1167,8 @@ latentam_status loss_bwd_t(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t 
         const PlainSrc Qsrc{a.Q, DQ, n, DQ};
         int z = 0;
         LAT_TRY(launch_narrow<false>(dSsrc, Qsrc, M, DQ, n, z0, part, DQ, (int64_t)M * DQ, 1.0f, st, &z));
-        reduce_splits<<<(unsigned)(((int64_t)M * DQ + 255) / 256), 256, 0, st>>>(part, z, M, DQ, a.c, nullptr,
-                                                                                 nullptr, nullptr, a.dK);
+        reduce_splits<<<(unsigned)(((int64_t)M * DQ + 31) / 32), 256, 0, st>>>(part, z, M, DQ, a.c, nullptr,
+                                                                                nullptr, nullptr, a.dK);
         LAT_CHECK_LAUNCH("reduce_splits");
     }
     finalize_loss<<<1, 1, 0, st>>>(acc, D, a.cfg, a.loss_parts);
@@ -1262,7 +1274,7 @@ latentam_status atb_noalloc(const float* X, int ldx, int nx, const float* Y, int
         atb_splitk<1><<<grid, kThreads, 0, st>>>(X, ldx, nx, Y, ldy, ny, n, rps, part);
     LAT_CHECK_LAUNCH("atb_splitk");
     const int64_t total = (int64_t)nx * ny;
-    reduce_splits<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, (int)splits, nx, ny, scale, coef, V, V0, out);
+    reduce_splits<<<(unsigned)((total + 31) / 32), 256, 0, st>>>(part, (int)splits, nx, ny, scale, coef, V, V0, out);
     LAT_CHECK_LAUNCH("reduce_splits");
     return LATENTAM_OK;
 }
