@@ -43,7 +43,7 @@ SM_FP32_LANES = 128  # FP32 FMA lanes per SM
 # over 172,800 pixels; profiles/decode_fp32_crop480x360.md: 3,369 MB), keyed by a hash of the
 # kernel sources it was taken on: once they change, the figure no longer describes the kernels
 # and the roofline reports no traffic.
-_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800), "fp32": ("c39470a9bf516ec3", 3359.13e6 / 172800)}
+_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800), "fp32": ("7b418b1e0197fc9c", 3359.37e6 / 172800)}
 _DECODE_SOURCES = {"bf16": ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh"), "fp32": ("decode_f32.cu",)}
 
 
