@@ -180,6 +180,32 @@ def test_tile_lists_sorted_by_depth_key_then_index():
         assert sorted(seg.tolist()) == member.tolist()
 
 
+def test_tile_lists_break_depth_ties_by_index():
+    """Many Gaussians on three depths (equal binary32 keys), rects over different tiles,
+    some invisible: each tile's list is its visible members by (binary32 depth, index), the
+    tie rule every renderer here shares (brute force over the synthetic projection)."""
+    s = tiny_scene(0)
+    tiles_x = (s.camera.width + 15) // 16
+    tiles_y = (s.camera.height + 15) // 16
+    rng = np.random.default_rng(7)
+    N = 300
+    depth = rng.choice([1.5, 2.5, 2.5 + 1e-9], size=N)  # the last two share a binary32 key
+    x0 = rng.integers(0, tiles_x, size=N)
+    y0 = rng.integers(0, tiles_y, size=N)
+    x1 = np.minimum(tiles_x, x0 + rng.integers(1, 3, size=N))
+    y1 = np.minimum(tiles_y, y0 + rng.integers(1, 3, size=N))
+    proj = dict(depth=depth.astype(np.float64), visible=(rng.uniform(size=N) > 0.1).astype(np.int32),
+                rect=np.ascontiguousarray(np.stack([x0, y0, x1, y1], 1).astype(np.int32)))
+    off, ids = oracle.tile_lists(proj, s.camera)
+    key = depth.astype(np.float32)
+    assert len(np.unique(key)) == 2
+    for t in range(tiles_x * tiles_y):
+        tx, ty = t % tiles_x, t // tiles_x
+        member = [g for g in range(N) if proj["visible"][g] and x0[g] <= tx < x1[g] and y0[g] <= ty < y1[g]]
+        want = sorted(member, key=lambda g: (key[g], g))
+        assert ids[off[t]:off[t + 1]].tolist() == want, t
+
+
 def test_blend_weights_sum_to_one_minus_transmittance_and_linearity():
     s = tiny_scene(1)
     proj = oracle.project_scene(s)
