@@ -72,6 +72,7 @@ typedef int32_t latentam_status;
 #define LATENTAM_ERR_CUDA (-4)              /* a CUDA runtime call or launch failed */
 #define LATENTAM_ERR_CAPACITY (-5)          /* caller buffer too small; required size reported */
 #define LATENTAM_ERR_TIMEOUT (-6)           /* a bounded device-side wait gave up */
+#define LATENTAM_ERR_NOT_FINITE (-7)        /* a step's loss or a gradient fed to Adam was not finite */
 
 typedef int32_t latentam_precision;
 #define LATENTAM_PREC_FP32 0 /* decode on FP32 CUDA cores, FP32 throughout */
@@ -189,6 +190,15 @@ LATENTAM_API latentam_status latentam_profile_read(latentam_ctx* ctx, double* ms
  * as plain launches.  Disabling drops the instantiated graphs (synchronises the device). */
 LATENTAM_API latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t enable);
 
+/* Test hook for the failure paths of the bounded device waits (no GPU fault is involved).
+ * which = 0: the next binning's radix sort makes the look-back of one 1024-key block poll a
+ * word that nothing writes, with a short limit (4096 polls), so that the wait gives up: that
+ * binning leaves its tiles empty and the NEXT binning returns LATENTAM_ERR_TIMEOUT.
+ * which = 1: raises the flag a tensor-core kernel's bounded wait raises when it gives up, so
+ * that the next synchronising call (binning, or a step reading its loss) reports it.
+ * INVALID_ARG for other values. */
+LATENTAM_API latentam_status latentam_test_wait_timeout(latentam_ctx* ctx, int32_t which);
+
 /* Autotuning of the tensor-core decode (on by default): the first time a context meets a shape
  * (pixel count, M, D) outside stream capture, the pixel-split factors of the two reductions
  * over pixels (dV and dK) are chosen by timing three candidates (the one-wave split, half and
@@ -211,7 +221,8 @@ LATENTAM_API latentam_status latentam_project(latentam_ctx* ctx, const latentam_
  * SYNCHRONISES `stream` once to read the pair count P into bins->num_pairs; if
  * P > bins->capacity returns LATENTAM_ERR_CAPACITY and writes no pairs (retry with a larger
  * buffer).  Returns LATENTAM_ERR_TIMEOUT if a bounded wait of an EARLIER call's sort gave up
- * (that call's tiles were left empty). */
+ * (that call's tiles were left empty), or if a bounded wait of a tensor-core decode kernel
+ * gave up since the last report (that call's loss was NaN); the flag is cleared when reported. */
 LATENTAM_API latentam_status latentam_sort(latentam_ctx* ctx, int32_t n, const latentam_projected* proj,
                               const latentam_camera* cam, latentam_bins* bins,
                               latentam_stream stream);
@@ -287,17 +298,21 @@ LATENTAM_API latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, c
  * start-up by another runtime's allocator, or a caller that cannot accept the device-wide
  * synchronisation that cudaMalloc/cudaFree may imply.  It calls no allocation routine.
  * Its scratch (attention, dFhat, dS, per-pixel coefficients, split-K partial sums, loss
- * accumulators) lives in one static 16 MiB device array inside the library, held by every
- * device that loads the library until the process exits.  A call whose scratch would not fit
- * (about 4 n (2M + D) bytes plus, per split, 4 M (D + d) bytes) returns
- * LATENTAM_ERR_UNSUPPORTED_SHAPE with the required size in latentam_last_error(); for
- * example n <= 2048 rows fit at M = 256, D = 512, d = 32, which covers mask-pooled targets.
- * The first call on a device looks up the array's device address with that device current;
- * make that first call before any stream capture.  All calls share the one array, which
- * keeps the last call's contents (the loss accumulators are cleared at the start of each
- * call): calls that overlap on the GPU (other streams or other host threads) race on it
- * and must be serialised by the caller.  Arguments, layouts and the other errors are those
- * of latentam_decode_loss_bwd. */
+ * accumulators) lives in one static 16 MiB device array inside the library.  Creating a
+ * context loads the library's device code on that device, which commits the array there, and
+ * resolves its device address (latentam_ctx_create, with the device current); the array then
+ * stays committed until the process exits, and the call itself neither allocates nor
+ * resolves anything.  The address belongs to the CUDA context it was resolved in: after a
+ * cudaDeviceReset create a new latentam context.  A call whose scratch would not fit returns
+ * LATENTAM_ERR_UNSUPPORTED_SHAPE with the required size in latentam_last_error().  The
+ * scratch is 4 n (2M + D) bytes (attention, dFhat, dS) + 16 n (coefficients) + 4 M (D + d) s
+ * bytes of split partial sums, where the split count s grows with the SM count up to
+ * min(2 SMs / tiles, n / 256); for example n <= 2048 rows fit at M = 256, D = 512, d = 32 on
+ * any SM count, which covers mask-pooled targets.  All calls share the one array, which keeps
+ * the last call's contents (the loss accumulators are cleared at the start of each call):
+ * calls that overlap on the GPU (other streams or other host threads) race on it and must
+ * be serialised by the caller.  Arguments, layouts and the other errors are those of
+ * latentam_decode_loss_bwd. */
 LATENTAM_API latentam_status latentam_decode_loss_bwd_noalloc(latentam_ctx* ctx, const float* Q, int64_t n,
                                                               int32_t d, const float* K, const float* V,
                                                               const float* V0, int32_t M, int32_t D, const void* F,
@@ -527,7 +542,11 @@ typedef struct {
  * adam->step is the step number of the first update; it is incremented per iteration in
  * the caller's struct.  loss_host (host, nullable, LATENTAM_LOSS_PARTS doubles) receives
  * the loss of the LAST iteration (evaluated before its update); passing it synchronises
- * the stream at the end.  Also synchronises once for the pair count (latentam_sort). */
+ * the stream at the end and then reports the context's device flags: LATENTAM_ERR_TIMEOUT
+ * if a bounded wait of a tensor-core decode kernel gave up since they were last reported
+ * (that loss is NaN), LATENTAM_ERR_NOT_FINITE if the loss or any gradient entry fed to Adam
+ * was not finite (the update has been applied: parameters may then hold non-finite values).
+ * Also synchronises once for the pair count (latentam_sort). */
 LATENTAM_API latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame,
                               latentam_params* params, const latentam_loss_cfg* cfg,
                               latentam_adam_cfg* adam, int32_t iters, int32_t learn_f,

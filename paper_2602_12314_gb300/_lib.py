@@ -21,8 +21,9 @@ ERR_OUT_OF_MEMORY = -3
 ERR_CUDA = -4
 ERR_CAPACITY = -5
 ERR_TIMEOUT = -6
+ERR_NOT_FINITE = -7
 _NAMES = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED_SHAPE", -3: "OUT_OF_MEMORY", -4: "CUDA", -5: "CAPACITY",
-          -6: "TIMEOUT"}
+          -6: "TIMEOUT", -7: "NOT_FINITE"}
 
 ABI_VERSION = 3
 
@@ -122,6 +123,7 @@ _SIGS = {
     "latentam_profile_enable": ([P, I32], I32),
     "latentam_graphs_enable": ([P, I32], I32),
     "latentam_autotune_enable": ([P, I32], I32),
+    "latentam_test_wait_timeout": ([P, I32], I32),
     "latentam_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I32], I32),
     "latentam_project": ([P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Projected), P], I32),
     "latentam_sort": ([P, I32, ctypes.POINTER(Projected), ctypes.POINTER(Camera), ctypes.POINTER(Bins), P], I32),

@@ -116,6 +116,11 @@ class Context:
         """Capture and replay the step's iterations as CUDA graphs (on by default)."""
         L.check(_lib().latentam_graphs_enable(self.handle, int(bool(enable))))
 
+    def test_wait_timeout(self, which: int):
+        """Arms a bounded device wait to give up (latentam_test_wait_timeout): 0 = the radix
+        look-back of the next binning, 1 = the tensor-core kernels' wait flag."""
+        L.check(_lib().latentam_test_wait_timeout(self.handle, int(which)))
+
     def autotune(self, enable: bool = True):
         """Time candidate split factors of the pixel reductions on first use of a shape (on by default)."""
         L.check(_lib().latentam_autotune_enable(self.handle, int(bool(enable))))

@@ -18,6 +18,7 @@ struct AdamBatch {
     int count;
     float beta1, beta2, eps, inv_bc1, inv_bc2;  // inverse bias corrections 1 / (1 - beta^step)
     const int* step_dev;                        // when set: the step is read here (graph replays)
+    int* nonfinite;                             // raised (sticky) when a gradient entry is not finite
 };
 
 __device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, const AdamBatch& b,
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamBatch b) {
     const bool vec = ((reinterpret_cast<uintptr_t>(T.p) | reinterpret_cast<uintptr_t>(T.g) |
                        reinterpret_cast<uintptr_t>(T.m) | reinterpret_cast<uintptr_t>(T.v)) & 15u) == 0;
     int64_t done = 0;
+    bool bad = false;
     if (vec) {
         const int64_t n4 = T.n / 4;
         float4* p4 = reinterpret_cast<float4*>(T.p);
@@ -56,6 +58,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamBatch b) {
         for (int64_t i = tid; i < n4; i += stride) {
             float4 p = p4[i], m = m4[i], v = v4[i];
             const float4 g = g4[i];
+            bad |= !(isfinite(g.x) && isfinite(g.y) && isfinite(g.z) && isfinite(g.w));
             adam_one(p.x, g.x, m.x, v.x, T.lr, b, inv_bc1, inv_bc2);
             adam_one(p.y, g.y, m.y, v.y, T.lr, b, inv_bc1, inv_bc2);
             adam_one(p.z, g.z, m.z, v.z, T.lr, b, inv_bc1, inv_bc2);
@@ -68,11 +71,13 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamBatch b) {
     }
     for (int64_t i = done + tid; i < T.n; i += stride) {
         float p = T.p[i], m = T.m[i], v = T.v[i];
+        bad |= !isfinite(T.g[i]);
         adam_one(p, T.g[i], m, v, T.lr, b, inv_bc1, inv_bc2);
         T.p[i] = p;
         T.m[i] = m;
         T.v[i] = v;
     }
+    if (bad && b.nonfinite) atomicExch(b.nonfinite, 1);
 }
 
 // The Adam step counter of graph replays: advanced by one on the device before each update.
@@ -112,6 +117,7 @@ latentam_status launch_adam(latentam_ctx* ctx, const AdamTensor* t, int count, f
     b.inv_bc1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
     b.inv_bc2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
     b.step_dev = step_dev;
+    b.nonfinite = ctx->dev_flags ? ctx->dev_flags + 1 : nullptr;
     // blocks in proportion to the tensor sizes (at least one each), about 4 waves in total
     int64_t total = 0;
     for (int k = 0; k < count; ++k) {

@@ -1,6 +1,8 @@
 // C ABI of include/latentam.h: argument validation, the context and its workspace, and the
 // composition of the kernels into the calls of the latent-feature optimisation step.
 #include <math.h>
+
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -271,6 +273,33 @@ latentam_status enter(latentam_ctx* ctx) {
     return LATENTAM_OK;
 }
 
+// The loss parts of a step into loss_host (synchronises `st`), then the context's sticky
+// device flags: a tensor-core wait that gave up -> TIMEOUT; a non-finite loss or a non-finite
+// gradient fed to Adam -> NOT_FINITE.  Reported flags are cleared.
+latentam_status read_loss(latentam_ctx* ctx, const double* lp, double* loss_host, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(loss_host, lp, sizeof(double) * LATENTAM_LOSS_PARTS, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_error(e, "copy loss");
+    int* flags = reinterpret_cast<int*>(ctx->host_counts) + 4;
+    e = cudaMemcpyAsync(flags, ctx->dev_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_error(e, "copy device flags");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "synchronise step");
+    const bool timeout = flags[0] != 0, grad_bad = flags[1] != 0;
+    if (timeout || grad_bad) {
+        e = cudaMemsetAsync(ctx->dev_flags, 0, 2 * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_error(e, "clear device flags");
+    }
+    if (timeout) {
+        set_error("a bounded wait of a tensor-core decode kernel gave up (the loss is NaN)");
+        return LATENTAM_ERR_TIMEOUT;
+    }
+    if (grad_bad || !std::isfinite(loss_host[3])) {
+        set_error("non-finite %s (loss %g)", grad_bad ? "gradient met the Adam update" : "loss", loss_host[3]);
+        return LATENTAM_ERR_NOT_FINITE;
+    }
+    return LATENTAM_OK;
+}
+
 latentam_status check_camera(const latentam_camera* cam) {
     if (!cam) {
         set_error("null camera");
@@ -454,12 +483,21 @@ latentam_status latentam_ctx_create(int32_t device, latentam_ctx** out) {
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->step_dev, sizeof(int));
-    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&c->host_counts), 16, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&c->host_counts), 32, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&c->dev_flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->dev_flags, 0, 4 * sizeof(int));
     if (e != cudaSuccess || !c->graphs || !c->sort_graphs) {
         latentam_ctx_destroy(c);
         if (e != cudaSuccess) return cuda_error(e, "context stream / counter");
         set_error("host allocation failed");
         return LATENTAM_ERR_OUT_OF_MEMORY;
+    }
+    // the allocation-free decode's static scratch: its address, resolved once per context with
+    // the device current (this also loads the module that holds it)
+    const latentam_status ss = decode_noalloc_setup(c);
+    if (ss != LATENTAM_OK) {
+        latentam_ctx_destroy(c);
+        return ss;
     }
     *out = c;
     return LATENTAM_OK;
@@ -487,6 +525,7 @@ latentam_status latentam_ctx_destroy(latentam_ctx* ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->step_dev) cudaFree(ctx->step_dev);
     if (ctx->host_counts) cudaFreeHost(ctx->host_counts);
+    if (ctx->dev_flags) cudaFree(ctx->dev_flags);
     delete ctx;
     if (e != cudaSuccess) return cuda_error(e, "synchronise before destroy");
     return LATENTAM_OK;
@@ -502,6 +541,23 @@ latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t enable) {
         if (e != cudaSuccess) return cuda_error(e, "synchronise before dropping graphs");
     }
     return LATENTAM_OK;
+}
+
+latentam_status latentam_test_wait_timeout(latentam_ctx* ctx, int32_t which) {
+    LAT_TRY(enter(ctx));
+    if (which == 0) {
+        ctx->test_stall_sort = 1;
+        return LATENTAM_OK;
+    }
+    if (which == 1) {
+        // what a tensor-core kernel's bounded wait leaves behind when it gives up
+        const int one = 1;
+        cudaError_t e = cudaMemcpy(ctx->dev_flags, &one, sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_error(e, "raise the tensor-core wait flag");
+        return LATENTAM_OK;
+    }
+    set_error("unknown wait %d (0: radix look-back of the next binning, 1: tensor-core flag)", which);
+    return LATENTAM_ERR_INVALID_ARG;
 }
 
 latentam_status latentam_autotune_enable(latentam_ctx* ctx, int32_t enable) {
@@ -1117,12 +1173,7 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
             key.addf(f);
     }
     LAT_TRY(run_iterations(ctx, graphable, key, iters, learn_f != 0, adam, st, iteration));
-    if (loss_host) {
-        cudaError_t e = cudaMemcpyAsync(loss_host, lp, sizeof(double) * LATENTAM_LOSS_PARTS, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_error(e, "copy loss");
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_error(e, "synchronise step");
-    }
+    if (loss_host) LAT_TRY(read_loss(ctx, lp, loss_host, st));
     return LATENTAM_OK;
 }
 
@@ -1377,11 +1428,6 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
             key.addf(f);
     }
     LAT_TRY(run_iterations(ctx, graphable, key, iters, learn_f != 0, adam, st, iteration));
-    if (loss_host) {
-        cudaError_t e = cudaMemcpyAsync(loss_host, lp, sizeof(double) * LATENTAM_LOSS_PARTS, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_error(e, "copy loss");
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_error(e, "synchronise step");
-    }
+    if (loss_host) LAT_TRY(read_loss(ctx, lp, loss_host, st));
     return LATENTAM_OK;
 }

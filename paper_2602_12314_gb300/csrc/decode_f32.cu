@@ -1192,15 +1192,12 @@ latentam_status decode_fwd_t(latentam_ctx* ctx, const float* Q, int64_t n, const
 }
 
 // ---- allocation-free variant -------------------------------------------------------------
-// Scratch of decode_loss_bwd_f32_noalloc: one file-scope device array, resident on every
-// device that loads the library until process exit.  Host code only ever sees a host-side
-// stand-in for the symbol; the device address comes from cudaGetSymbolAddress.
+// Scratch of decode_loss_bwd_f32_noalloc: one file-scope device array.  Host code only ever
+// sees a host-side stand-in for the symbol; the device address comes from cudaGetSymbolAddress,
+// called by decode_noalloc_setup when a context is created (that device current), which also
+// loads this module and so commits the array on the device before the first call.
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
 
 struct NoallocPlan {
     size_t acc, A, dF, dS, row, coef, partV, partK, total;
@@ -1245,23 +1242,6 @@ NoallocPlan plan_noalloc(int num_sms, int64_t n, int M, int D, int d) {
     return p;
 }
 
-// Device address of the static scratch; looked up once per device (that device current).
-latentam_status noalloc_scratch(int device, unsigned char** out) {
-    if (device < 0 || device >= kMaxDevices) {
-        set_error("device %d outside the %d devices the static scratch table covers", device, kMaxDevices);
-        return LATENTAM_ERR_INVALID_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static decode scratch)");
-        g_noalloc_ptr[device] = ptr;
-    }
-    *out = static_cast<unsigned char*>(g_noalloc_ptr[device]);
-    return LATENTAM_OK;
-}
-
 latentam_status atb_noalloc(const float* X, int ldx, int nx, const float* Y, int ldy, int ny, int64_t n, float scale,
                             const float* coef, const float* V, const float* V0, float* out, float* part,
                             int64_t splits, int64_t rps, cudaStream_t st) {
@@ -1290,8 +1270,11 @@ latentam_status loss_bwd_noalloc_t(latentam_ctx* ctx, const DecodeArgs& a, cudaS
                   p.total, (long long)n, M, D, DQ, kStaticScratchBytes);
         return LATENTAM_ERR_UNSUPPORTED_SHAPE;
     }
-    unsigned char* base = nullptr;
-    LAT_TRY(noalloc_scratch(ctx->device, &base));
+    unsigned char* base = static_cast<unsigned char*>(ctx->noalloc_scratch);
+    if (!base) {
+        set_error("the context holds no address of the static decode scratch");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
     double* acc = reinterpret_cast<double*>(base + p.acc);
     float* A = reinterpret_cast<float*>(base + p.A);
     float* dF = reinterpret_cast<float*>(base + p.dF);
@@ -1337,7 +1320,13 @@ latentam_status decode_loss_bwd_f32_noalloc(latentam_ctx* ctx, const DecodeArgs&
     }
 }
 
-size_t decode_noalloc_scratch_bytes() { return kStaticScratchBytes; }
+latentam_status decode_noalloc_setup(latentam_ctx* ctx) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static decode scratch)");
+    ctx->noalloc_scratch = ptr;
+    return LATENTAM_OK;
+}
 
 latentam_status sgemm_abt(const float* A, int64_t m, const float* B, int64_t n, int64_t k, float* C, int64_t ldc,
                           float scale, cudaStream_t st) {

@@ -106,7 +106,9 @@ __global__ void fp8_values(const float* __restrict__ V, int M, int D, uint8_t* _
 }
 
 // Accumulators: [0] sum (1 - cos) over valid pixels, [1] sum of squared errors, [2] trust
-// region, [3] |Omega|; int at acc + 8: device error flag of the tensor-core kernels.
+// region, [3] |Omega|.  The tensor-core kernels raise the context's sticky device flag when a
+// bounded wait gives up; the loss of that call is then NaN and the next synchronising call
+// (binning, or a step that reads its loss back) returns LATENTAM_ERR_TIMEOUT.
 __global__ void tc_count_mask(const uint8_t* __restrict__ mask, int64_t n, double* __restrict__ acc) {
     __shared__ int s[8];
     int c = 0;
@@ -784,7 +786,7 @@ latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool trai
     b->dF = train ? reinterpret_cast<bf16*>(rows + up(e2 * nn * M)) : nullptr;
     b->dS = train ? reinterpret_cast<bf16*>(rows + up(e2 * nn * M) + up(e2 * nn * D)) : nullptr;
     b->acc = acc;
-    b->err = reinterpret_cast<int*>(acc + 8);
+    b->err = ctx->dev_flags;  // sticky: reported by the next synchronising call
     b->part = nullptr;
     b->Aq = fp8 ? reinterpret_cast<uint8_t*>(ops + off[5]) : nullptr;
     b->Vtq = fp8 ? reinterpret_cast<uint8_t*>(ops + off[6]) : nullptr;

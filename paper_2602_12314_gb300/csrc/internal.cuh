@@ -116,6 +116,13 @@ struct latentam_ctx {
         int M, D, which, z;
     } tune[32];
     int tune_used, tune_next;
+    // device address of the allocation-free decode's static scratch (resolved at creation)
+    void* noalloc_scratch;
+    // sticky device flags, cleared when a synchronising call reports them:
+    // [0] a bounded wait of a tensor-core kernel gave up, [1] a non-finite gradient met Adam
+    int* dev_flags;
+    // test hook (latentam_test_wait_timeout): the next binning's look-back stalls once
+    int test_stall_sort;
 };
 
 namespace lat {
@@ -240,7 +247,9 @@ latentam_status decode_loss_bwd_f32(latentam_ctx* ctx, const DecodeArgs& a, cuda
 latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st, bool fp8 = false);
 // FP32 decode + loss + backward with all scratch in a static device array (no allocation).
 latentam_status decode_loss_bwd_f32_noalloc(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st);
-size_t decode_noalloc_scratch_bytes();
+// Resolves the device address of that array into ctx->noalloc_scratch (the context's device
+// current); called once when the context is created.
+latentam_status decode_noalloc_setup(latentam_ctx* ctx);
 latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K,
                                 const float* V, int M, int D, float c, float* F_hat, float* row_stats,
                                 cudaStream_t st, bool fp8 = false);

@@ -112,6 +112,7 @@ constexpr uint32_t kLbAggregate = 1u << 30;
 constexpr uint32_t kLbInclusive = 2u << 30;
 constexpr uint32_t kLbValue = kLbAggregate - 1u;
 constexpr int kLbSpinLimit = 1 << 20;
+constexpr int kTestSpinLimit = 1 << 12;  // the short limit of an armed test stall
 
 __device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t* p) {
     uint32_t v;
@@ -158,14 +159,18 @@ __global__ void __launch_bounds__(kRsThreads) radix_digit_counts(const uint32_t*
 // order (a ticket, so that every tile before it belongs to a block already running), ranks
 // its keys by digit in input order (warp w owns keys [128 w, 128 w + 128) of the tile), posts
 // its per-digit counts, and adds the counts of the earlier tiles by walking back over their
-// posted words until it meets an inclusive one (decoupled look-back).  The waits are bounded:
-// a walk that gives up raises *err and uses what it summed (every position stays below n).
+// posted words until it meets an inclusive one (decoupled look-back).  The waits are bounded
+// (spin_limit polls): a walk that gives up raises *err and uses what it summed (every position
+// stays below n).  stall_tile >= 0 (a test of that path) makes that tile's first look-back poll
+// stall_word, a zero word that nothing writes, so that its wait runs out.
 __global__ void __launch_bounds__(kRsThreads) radix_onesweep(const uint32_t* __restrict__ keys_in,
                                                              const uint32_t* __restrict__ vals_in,
                                                              uint32_t* __restrict__ keys_out,
                                                              uint32_t* __restrict__ vals_out, int64_t n, int shift,
                                                              uint32_t mask, const uint32_t* __restrict__ counts,
-                                                             uint32_t* status, uint32_t* ticket, uint32_t* err) {
+                                                             uint32_t* status, uint32_t* ticket, uint32_t* err,
+                                                             int spin_limit, int64_t stall_tile,
+                                                             const uint32_t* stall_word) {
     __shared__ uint32_t s_off[kRadix];
     __shared__ uint32_t s_cnt[kRsThreads / 32][kRadix];
     __shared__ uint32_t s_wsum[kRsThreads / 32];
@@ -218,10 +223,10 @@ __global__ void __launch_bounds__(kRsThreads) radix_onesweep(const uint32_t* __r
     if (tile > 0) {
         bool ok = true;
         for (int64_t j = tile - 1; j >= 0 && ok; --j) {
-            const uint32_t* w = status + j * kRadix + t;
+            const uint32_t* w = (tile == stall_tile && j == tile - 1) ? stall_word : status + j * kRadix + t;
             uint32_t v = ld_relaxed_gpu(w);
             for (int spins = 0; (v & ~kLbValue) == 0; ++spins) {
-                if (spins >= kLbSpinLimit) {
+                if (spins >= spin_limit) {
                     ok = false;
                     break;
                 }
@@ -421,7 +426,8 @@ latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uin
         return LATENTAM_ERR_UNSUPPORTED_SHAPE;
     }
     const int64_t nb = (n + kRsTile - 1) / kRsTile;
-    // [digit counts: passes x 256 | tickets: 256 | look-back words: passes x nb x 256], zeroed
+    // [digit counts: passes x 256 | tickets: 256 | look-back words: passes x nb x 256], zeroed;
+    // tickets[255] is never written (the word an armed test stall polls)
     const size_t words = (size_t)(passes + 1) * kRadix + (size_t)passes * (size_t)nb * kRadix;
     uint32_t* buf = static_cast<uint32_t*>(ws(ctx, WS_SORT_HIST, sizeof(uint32_t) * words));
     if (!buf) return LATENTAM_ERR_OUT_OF_MEMORY;
@@ -433,12 +439,16 @@ latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uin
     const unsigned cblocks = (unsigned)std::min<int64_t>(nb, 2 * (int64_t)ctx->num_sms);
     radix_digit_counts<<<cblocks, kRsThreads, 0, st>>>(keys[0], n, passes, bits, counts);
     LAT_CHECK_LAUNCH("radix_digit_counts");
+    // an armed test stall applies to the last tile of the first pass (once)
+    const bool stall = ctx->test_stall_sort && nb > 1;
+    if (stall) ctx->test_stall_sort = 0;
     for (int p = 0; p < passes; ++p) {
         const int src = p % 2, dst = 1 - src;
         const uint32_t* vin = (p == 0 && vals_iota) ? nullptr : vals[src];
-        radix_onesweep<<<(unsigned)nb, kRsThreads, 0, st>>>(keys[src], vin, keys[dst], vals[dst], n, 8 * p,
-                                                            pass_mask(bits, p), counts + p * kRadix,
-                                                            status + (size_t)p * (size_t)nb * kRadix, tickets + p, err);
+        radix_onesweep<<<(unsigned)nb, kRsThreads, 0, st>>>(
+            keys[src], vin, keys[dst], vals[dst], n, 8 * p, pass_mask(bits, p), counts + p * kRadix,
+            status + (size_t)p * (size_t)nb * kRadix, tickets + p, err, stall ? kTestSpinLimit : kLbSpinLimit,
+            (stall && p == 0) ? nb - 1 : -1, tickets + (kRadix - 1));
         LAT_CHECK_LAUNCH("radix_onesweep");
     }
     return LATENTAM_OK;
@@ -468,6 +478,8 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
         if (e2 != cudaSuccess) return cuda_error(e2, "clear ranges and counters");
         LAT_TRY(scan_exclusive_u32(ctx, reinterpret_cast<const uint32_t*>(proj.tiles_touched), off, N, cnt + 1, s));
         e2 = cudaMemcpyAsync(host, cnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e2 == cudaSuccess)  // and the tensor-core kernels' sticky wait flag
+            e2 = cudaMemcpyAsync(host + 3, ctx->dev_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e2 != cudaSuccess) return cuda_error(e2, "read the pair count");
         return LATENTAM_OK;
     };
@@ -478,11 +490,17 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
     LAT_TRY(cached_launch(ctx, pre_key, (int)(sizeof(pre_key) / sizeof(pre_key[0])), st, pre));
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_error(e, "sync for the pair count");
-    const uint32_t pairs = host[1], sort_error = host[2];
+    const uint32_t pairs = host[1], sort_error = host[2], tc_error = host[3];
     if (sort_error) {
         e = cudaMemsetAsync(cnt + 2, 0, sizeof(uint32_t), st);
         if (e != cudaSuccess) return cuda_error(e, "clear the sort error word");
         set_error("a radix sort look-back wait gave up in an earlier binning (its tiles were left empty)");
+        return LATENTAM_ERR_TIMEOUT;
+    }
+    if (tc_error) {
+        e = cudaMemsetAsync(ctx->dev_flags, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_error(e, "clear the tensor-core wait flag");
+        set_error("a bounded wait of a tensor-core decode kernel gave up in an earlier call (its loss was NaN)");
         return LATENTAM_ERR_TIMEOUT;
     }
     const int64_t P = (int64_t)pairs;
@@ -530,7 +548,7 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
                             reinterpret_cast<uint64_t>(proj.depth), reinterpret_cast<uint64_t>(proj.tiles_touched),
                             reinterpret_cast<uint64_t>(proj.rect), reinterpret_cast<uint64_t>(bins->pair_ids),
                             reinterpret_cast<uint64_t>(bins->tile_ranges), reinterpret_cast<uint64_t>(st),
-                            ctx->ws_generation};
+                            ctx->ws_generation, (uint64_t)ctx->test_stall_sort};
     return cached_launch(ctx, key, (int)(sizeof(key) / sizeof(key[0])), st, rest);
 }
 
