@@ -12,8 +12,11 @@ end; seeded synthetic data standing in for the paper's RGB-D + CLIP/SAM keyframe
 
   python bench.py [--gpus N --steps K --warmup W] [--precision both|fp32|bf16] [--impl reference]
 
-By default both precision forms run: the plain FP32 form (CUDA-core decode) gives the
-headline value, and the BF16 form (tcgen05 tensor-core decode) is reported under "forms".
+By default every precision form runs: the FP32 form gives the headline value (its decode on the
+tcgen05 tensor cores with each FP32 operand split into a BF16 hi and lo term, three MMAs per
+product, FP32 accumulation), and the FP32 form on the FMA pipes, the BF16, BF16-batched and FP8
+tensor-core forms, the mask-pooled forms and the full Stage I objective are reported under
+"forms".
 
 Under torchrun (N > 1) every rank optimises its own keyframe (replicas, weak scaling); the
 timed region is bracketed by a barrier and a device synchronisation and the slowest rank's
@@ -39,12 +42,18 @@ WORKLOAD = ("room keyframe: 300k Gaussians (6x5x3 m room, 20 boxes), 640x480, d=
 SM_FP32_LANES = 128  # FP32 FMA lanes per SM
 
 # DRAM traffic (read + write bytes) of the decode stage per pixel, from one ncu capture of every
-# decode launch of a step on the 480x360 crop (profiles/decode_bf16_tc_crop480x360.md: 1,320 MB
-# over 172,800 pixels; profiles/decode_fp32_crop480x360.md: 3,369 MB), keyed by a hash of the
-# kernel sources it was taken on: once they change, the figure no longer describes the kernels
-# and the roofline reports no traffic.
-_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800), "fp32": ("7b418b1e0197fc9c", 3359.37e6 / 172800)}
-_DECODE_SOURCES = {"bf16": ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh"), "fp32": ("decode_f32.cu",)}
+# decode launch of a step on the 480x360 crop (172,800 pixels), keyed by a hash of the kernel
+# sources it was taken on: once they change, the figure no longer describes the kernels and the
+# roofline reports no traffic.
+_DECODE_TRAFFIC = {"bf16": ("29bfffdc30d3e8d1", 1320.12e6 / 172800), "fp32_fma": ("7b418b1e0197fc9c", 3359.37e6 / 172800),
+                   "fp32": ("", 0.0)}
+_DECODE_SOURCES = {"bf16": ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh"), "fp32_fma": ("decode_f32.cu",),
+                   "fp32": ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh")}
+# bytes each splat kernel must move per unit (render forward: per pair 24 B of conic, mean and
+# opacity + 4d B of query staged once per tile, per pixel 4d B of Q + 8 B of T and count; render
+# backward: per pixel 4d B of dQ, per pair 24 B, per Gaussian 4d B of df)
+SPLAT_FWD_BYTES = lambda P, n, N, d: P * (24 + 4 * d) + n * (4 * d + 8)  # noqa: E731
+SPLAT_BWD_BYTES = lambda P, n, N, d: n * 4 * d + P * 24 + N * 4 * d  # noqa: E731
 
 
 def _decode_sources_hash(form="bf16"):
@@ -64,8 +73,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--batch", type=int, default=6, help="keyframes of the batched form (B + 1, B = 5 in Sec. IV-A)")
-    p.add_argument("--precision", choices=["both", "fp32", "bf16", "fp8", "bf16_batch", "fp32_batch", "fp32_masks",
-                                          "bf16_masks", "fp32_full"], default="both",
+    p.add_argument("--precision", choices=["both", "fp32", "fp32_fma", "bf16", "fp8", "bf16_batch", "fp32_batch",
+                                          "fp32_masks", "bf16_masks", "fp32_full"], default="both",
                    help="both: the FP32 form is the headline value, the BF16 tensor-core form is reported beside it")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -191,7 +200,10 @@ def _config(args, scene, world, precision):
             "n_pixels": scene.camera.n_pixels, "gaussians": scene.n, "d": scene.d, "M": scene.M, "D": scene.D,
             "l2": "inputs larger than L2 (target features %.0f MB FP32 / %.0f MB BF16 per step)"
                   % (scene.F.nbytes / 1e6, scene.F.nbytes / 2e6),
-            "parallelism": f"replicas x{world}"}
+            "parallelism": f"replicas x{world}",
+            "fp32_form": "decode contractions on tcgen05: each FP32 operand split into BF16 hi + lo, three MMAs per "
+                         "product (hi hi + hi lo + lo hi), FP32 accumulation; softmax and loss in FP32 (held to the "
+                         "FP32 parity bars: 1e-4 on features, 1e-3 on gradients)"}
 
 
 def _oracle_iteration(scene, cfg):
@@ -207,35 +219,36 @@ def _oracle_iteration(scene, cfg):
     return out
 
 
+def _cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
 def run_reference(args, world, rank):
-    """The oracle (plain FP64 C, OpenMP) as it stands, timed on this machine's host cores on a
-    bounded sample of the workload: the 160x120 central crop of the keyframe (all 300k
-    Gaussians), iterations/s extrapolated to the full 640x480 frame by pixel count."""
+    """The oracle (plain FP64 C, OpenMP over independent outputs) as it stands, timed on this
+    machine's host cores: every step is one whole oracle iteration (render, decode, loss,
+    backward, Adam) of the full 640x480 room keyframe with its 300k Gaussians.  Under torchrun
+    only rank 0 runs it."""
     if rank != 0:
         return
     import oracle
     s = _scene(args.seed, args.crop)
-    full = s.camera.n_pixels
-    crop = s.crop((s.camera.width - 160) // 2, (s.camera.height - 120) // 2, 160, 120)
-    frac = crop.camera.n_pixels / full
     cfg = oracle.LossConfig()
     oracle.build()
     for _ in range(max(args.warmup, 0)):
-        _oracle_iteration(crop, cfg)
+        _oracle_iteration(s, cfg)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _oracle_iteration(crop, cfg)
+        _oracle_iteration(s, cfg)
     dt = time.perf_counter() - t0
-    value = args.steps / dt * frac
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = (f"{args.steps} oracle iterations on the 160x120 central crop (all 300k Gaussians); "
-              f"iters/s scaled by the pixel fraction {frac:.4f} to the 640x480 frame")
+    value = args.steps / dt
+    sample = (f"{args.steps} whole oracle iterations (fwd, bwd, Adam) of the {s.camera.width}x{s.camera.height} "
+              f"keyframe with all {s.n} Gaussians, {dt:.1f} s on {_cores()} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(args, s, world, args.precision),
-        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": _cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -299,7 +312,7 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
     from paper_2602_12314_gb300 import api
 
     ctx = api.Context(local)
-    target_dtype = torch.float32 if prec == api.FP32 else torch.bfloat16
+    target_dtype = torch.float32 if prec in (api.FP32, api.FP32_FMA) else torch.bfloat16
     if full is not None:  # the whole Stage I objective: geometry, colour and depth too
         st = api.LatentStepFull(ctx, scene, *full)
     elif views is None:
@@ -389,6 +402,9 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
                                    barrier, max_over_ranks, world, n_frames)
         e2e = {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "pipelined": True}
+    ctx_pairs = None
+    if full is None:
+        ctx_pairs = _pair_counts(ctx, views if views is not None else [scene])
     ctx.close()
 
     # ---- roofline of the dominant stage (decode + loss + decode backward) -------------------
@@ -399,45 +415,78 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
     if masks is not None:
         n = masks.n_masks
     if full is not None:
-        ctx.close()
         return {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": int(launches), "e2e": e2e,
-                "keyframes_per_step": n_frames, "roofline": None, "clocks": clk,
+                "keyframes_per_step": n_frames, "roofline": None, "splat_roofline": None, "clocks": clk,
                 "stages_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()}, "dtype": "f32"}
     dec_ms, dec_cnt = prof["decode"]
     dec_avg_s = dec_ms / max(dec_cnt, 1) / 1e3
     flops = decode_flops(n, M, D, d)
     props = torch.cuda.get_device_properties(local)
-    if prec == api.FP32:
+    split = prec == api.FP32 and M <= 1024 and D <= 1024
+    form = "fp32" if split else "fp32_fma" if prec in (api.FP32, api.FP32_FMA) else "bf16"
+    key, per_pixel = _DECODE_TRAFFIC[form]
+    traffic = per_pixel * n if key and key == _decode_sources_hash(form) and masks is None and \
+        prec != api.FP8 else None
+    src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of every decode launch of one step on the 480x360 "
+           "crop, scaled by pixel count") if traffic else None
+    if form == "fp32_fma":
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = props.multi_processor_count * SM_FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-        key, per_pixel = _DECODE_TRAFFIC["fp32"]
-        traffic = per_pixel * n if key == _decode_sources_hash("fp32") and masks is None else None
-        roof = {"bound": "alu", "kernel": "decode stage (attn_rows_d32, sgemm_tile x3, coef_rows, sgemm_narrow x2, "
-                                          "reduce_splits x2)",
+        roof = {"bound": "alu", "kernel": "decode stage on the FMA pipes (attention rows, tiled FP32 GEMMs)",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x {SM_FP32_LANES} lanes x 2 x "
-                               f"{sm_mhz:.0f} MHz (max SM clock)",
-                "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of every decode launch of one "
-                                  "step on the 480x360 crop, scaled by pixel count" if traffic else None,
-                "algorithmic_per_launch": flops}
+                               f"{sm_mhz:.0f} MHz (max SM clock)"}
+    elif form == "fp32":
+        peak = float(peaks["bf16_tflops_sustained"]) / 3.0
+        roof = {"bound": "tensor", "kernel": "decode stage: six tcgen05 GEMM kernels, operands split into BF16 hi/lo "
+                                             "planes, three MMAs per FP32 product",
+                "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"bf16 sustained ({peak_src}) / 3: each FP32 product is three BF16 MMAs",
+                "executed_bf16_tflops": 3.0 * flops / dec_avg_s / 1e12}
     else:
         peak = float(peaks["bf16_tflops_sustained"])
-        key, per_pixel = _DECODE_TRAFFIC["bf16"]
-        traffic = per_pixel * n if key == _decode_sources_hash("bf16") and prec == api.BF16 and masks is None else None
         roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 GEMM kernels + their epilogues)",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"bf16 sustained, {peak_src}" + (
-                    " (five of the six contractions are BF16; the value contraction runs on E4M3)"
-                    if prec == api.FP8 else ""), "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of every decode launch of one "
-                                  "step on the 480x360 crop, scaled by pixel count" if traffic else None,
-                "algorithmic_per_launch": flops}
+                "peak_source": f"bf16 sustained ({peak_src})" + (
+                    "; the FP8 form is quoted against this BF16 peak: five of its six contractions are BF16 and no "
+                    "FP8 peak was measured on this pool" if prec == api.FP8 else "")}
+    roof.update({"traffic": traffic, "traffic_source": src, "algorithmic_per_launch": flops})
     roof["frac"] = roof["achieved"] / roof["peak"]
     return {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": int(launches), "e2e": e2e,
-            "keyframes_per_step": n_frames,
-            "roofline": roof, "clocks": clk, "stages_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
-            "dtype": {api.FP32: "f32", api.BF16: "bf16", api.FP8: "bf16+e4m3"}[prec]}
+            "keyframes_per_step": n_frames, "roofline": roof,
+            "splat_roofline": _splat_roofline(ctx_pairs, prof, prof_steps, peaks, peak_src, d),
+            "clocks": clk, "stages_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
+            "dtype": {api.FP32: "f32", api.FP32_FMA: "f32", api.BF16: "bf16", api.FP8: "bf16+e4m3"}[prec]}
+
+
+def _pair_counts(ctx, scenes):
+    """(pairs P, pixels n, Gaussians N) of each keyframe: one binning through the C ABI."""
+    from paper_2602_12314_gb300 import api
+    out = []
+    for s in scenes:
+        proj = api.project(ctx, s.means, s.quats, s.scales, s.opacities, s.camera)
+        bins = api.sort(ctx, proj, s.camera)
+        out.append((int(bins.num_pairs), s.camera.n_pixels, int(s.means.shape[0])))
+    return out
+
+
+def _splat_roofline(pairs, prof, prof_steps, peaks, peak_src, d):
+    """Render forward and backward against the HBM roofline: the algorithmic bytes of the
+    keyframes of one step (SPLAT_FWD_BYTES / SPLAT_BWD_BYTES) over each stage's device time per
+    step (CUDA-event stage timers)."""
+    if not pairs:
+        return None
+    out = {}
+    for stage, fn in (("render_fwd", SPLAT_FWD_BYTES), ("render_bwd", SPLAT_BWD_BYTES)):
+        ms = prof[stage][0] / prof_steps
+        if ms <= 0:
+            continue
+        b = sum(fn(P, n, N, d) for P, n, N in pairs)
+        a = b / (ms / 1e3) / 1e9
+        out[stage] = {"bound": "hbm", "achieved": a, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                      "frac": a / float(peaks["hbm_gbs"]), "algorithmic_bytes_per_step": b, "ms_per_step": ms,
+                      "peak_source": f"hbm copy ({peak_src})", "pairs": [p[0] for p in pairs]}
+    return out
 
 
 def _measure_kmeans(args, local, scene, masks):
@@ -475,6 +524,12 @@ def _measure_kmeans(args, local, scene, masks):
     return out
 
 
+def _prec_of(api, form):
+    if form.startswith("fp32_fma"):
+        return api.FP32_FMA
+    return api.FP32 if form.startswith("fp32") else api.FP8 if form == "fp8" else api.BF16
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -486,7 +541,7 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     scene = _scene(args.seed + rank, args.crop)
-    forms = (["fp32", "bf16", "bf16_batch", "fp8", "fp32_masks", "bf16_masks", "fp32_full"]
+    forms = (["fp32", "fp32_fma", "bf16", "bf16_batch", "fp8", "fp32_masks", "bf16_masks", "fp32_full"]
              if args.precision == "both" else [args.precision])
     res = {}
     masks = None
@@ -502,7 +557,7 @@ def run_ours(args, world, rank, local):
         if f.endswith("_full"):
             from workloads import room_rgbd
             full = room_rgbd(args.seed + rank, scene)
-        prec = api.FP32 if f.startswith("fp32") else api.FP8 if f == "fp8" else api.BF16
+        prec = _prec_of(api, f)
         res[f] = _measure(args, world, rank, local, scene, prec, dist,
                           views, masks if f.endswith("_masks") else None, full)
     if rank != 0:
@@ -515,29 +570,31 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        crop = scene.crop((scene.camera.width - 160) // 2, (scene.camera.height - 120) // 2, 160, 120)
-        frac = crop.camera.n_pixels / n
-        t0 = time.perf_counter()
-        _oracle_iteration(crop, oracle.LossConfig())
-        dt = time.perf_counter() - t0
-        cpu = {"value": frac / dt, "unit": "iters/s", "cores": int(os.environ.get("OMP_NUM_THREADS",
-                                                                                   os.cpu_count() or 1)),
-               "kind": "oracle",
-               "sample": "one FP64 oracle iteration (fwd, bwd, Adam) on the 160x120 central crop with all 300k "
-                         f"Gaussians, {dt:.2f} s; scaled by the pixel fraction {frac:.4f} to the full frame"}
+        times = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            _oracle_iteration(scene, oracle.LossConfig())
+            times.append(time.perf_counter() - t0)
+        cpu = {"value": 1.0 / min(times), "unit": "iters/s", "cores": _cores(), "kind": "oracle",
+               "sample": f"whole FP64 oracle iterations (fwd, bwd, Adam) of the {scene.camera.width}x"
+                         f"{scene.camera.height} keyframe with all {scene.n} Gaussians: best of 3 "
+                         f"({', '.join(f'{t:.2f}' for t in times)} s)"}
     line = {
         "metric": METRIC, "value": head["value"], "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic",
         "config": _config(args, scene, world, args.precision),
-        "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"], "cpu_baseline": cpu,
+        "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"],
+        "splat_roofline": head["splat_roofline"], "cpu_baseline": cpu,
         "clocks": head["clocks"], "stages_ms_per_step": head["stages_ms_per_step"],
     }
     if len(forms) > 1:
         line["forms"] = {f: {k: res[f][k] for k in ("value", "ms_per_step", "dtype", "e2e", "roofline",
-                                                    "gpu_launches", "clocks", "stages_ms_per_step",
-                                                    "keyframes_per_step")}
+                                                    "splat_roofline", "gpu_launches", "clocks",
+                                                    "stages_ms_per_step", "keyframes_per_step")}
                          for f in forms}
+        line["forms"]["fp32_fma"]["workload"] = (
+            "the room keyframe, FP32 form with every decode contraction on the FMA pipes (CUDA cores)")
         line["forms"]["bf16_batch"]["workload"] = (
             f"{args.batch} keyframes of the room (the new keyframe + {args.batch - 1} history keyframes) "
             "sharing the map and the dictionary, one latentam_step_batch iteration; value = keyframe-iterations/s")
@@ -632,10 +689,10 @@ def run_workloads(args, world, rank, local):
                 "10 iterations per keyframe")
         args.steps = 10
     for f in forms:
-        prec = api.FP32 if f.startswith("fp32") else api.FP8 if f == "fp8" else api.BF16
+        prec = _prec_of(api, f)
         res[f] = _measure(args, world, rank, local, scene, prec, None, views if f.endswith("_batch") else None)
     line = {"workload": args.workload, "description": desc, "steps": args.steps,
-            "forms": {f: {k: r[k] for k in ("value", "ms_per_step", "dtype", "roofline", "clocks",
+            "forms": {f: {k: r[k] for k in ("value", "ms_per_step", "dtype", "roofline", "splat_roofline", "clocks",
                                             "stages_ms_per_step", "keyframes_per_step")} for f, r in res.items()}}
     line.update(extra)
     print(json.dumps(line), flush=True)

@@ -75,7 +75,13 @@ typedef int32_t latentam_status;
 #define LATENTAM_ERR_NOT_FINITE (-7)        /* a step's loss or a gradient fed to Adam was not finite */
 
 typedef int32_t latentam_precision;
-#define LATENTAM_PREC_FP32 0 /* decode on FP32 CUDA cores, FP32 throughout */
+#define LATENTAM_PREC_FP32 0 /* FP32 form: where M <= 1024 and D <= 1024, the decode contractions on
+                                tcgen05 tensor cores with every FP32 operand split into two BF16 terms
+                                x = hi + lo (hi = bf16(x), lo = bf16(x - hi): x within 2^-16 |x|) and
+                                every product taken as three MMAs a_hi b_hi + a_hi b_lo + a_lo b_hi
+                                with FP32 accumulation (the dropped a_lo b_lo is below 2^-16 |a b|);
+                                softmax, loss and the a_p/b_p coefficients in FP32, frame sums in
+                                FP64; larger dictionaries run the LATENTAM_PREC_FP32_FMA kernels */
 #define LATENTAM_PREC_BF16 1 /* decode contractions on tcgen05 tensor cores: BF16 operands, FP32 accumulation;
                                  M <= 1024 and D <= 1024 (else LATENTAM_ERR_UNSUPPORTED_SHAPE) */
 #define LATENTAM_PREC_FP8 2  /* the BF16 form with the value contraction Fhat = A V on E4M3 operands
@@ -83,6 +89,7 @@ typedef int32_t latentam_precision;
                                 softmax denominator: the row maximum of A is 1 / l_p), V scaled per
                                 feature by 448 / max_j |V_jc|, FP32 accumulation, scales undone in
                                 the epilogue; same shape limits as BF16 */
+#define LATENTAM_PREC_FP32_FMA 3 /* every decode contraction in FP32 on the FMA pipes (CUDA cores) */
 
 typedef int32_t latentam_dtype;
 #define LATENTAM_DTYPE_F32 0

@@ -30,6 +30,7 @@ ABI_VERSION = 3
 PREC_FP32 = 0
 PREC_BF16 = 1
 PREC_FP8 = 2
+PREC_FP32_FMA = 3
 DTYPE_F32 = 0
 DTYPE_BF16 = 1
 LOSS_PARTS = 5

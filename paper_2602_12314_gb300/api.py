@@ -17,6 +17,7 @@ from . import _lib as L
 FP32 = L.PREC_FP32
 BF16 = L.PREC_BF16
 FP8 = L.PREC_FP8
+FP32_FMA = L.PREC_FP32_FMA
 
 
 def _lib():

@@ -300,6 +300,35 @@ latentam_status read_loss(latentam_ctx* ctx, const double* lp, double* loss_host
     return LATENTAM_OK;
 }
 
+// The precision forms of the decode.  FP32: the split tensor-core form (every FP32 operand a hi /
+// lo pair of BF16 terms, three MMAs per product, FP32 accumulation) where its shapes allow
+// (M, D <= 1024), else the FMA-pipe kernels; FP32_FMA: the FMA-pipe kernels at every shape.
+bool known_prec(latentam_precision p) {
+    return p == LATENTAM_PREC_FP32 || p == LATENTAM_PREC_BF16 || p == LATENTAM_PREC_FP8 || p == LATENTAM_PREC_FP32_FMA;
+}
+
+latentam_status run_decode_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, latentam_precision prec, cudaStream_t st) {
+    if (prec == LATENTAM_PREC_FP32 && decode_split_supported(a.d, a.M, a.D)) return decode_loss_bwd_split(ctx, a, st);
+    if (prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_FP32_FMA) return decode_loss_bwd_f32(ctx, a, st);
+    if (prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8)
+        return decode_loss_bwd_bf16(ctx, a, st, prec == LATENTAM_PREC_FP8);
+    set_error("unknown precision %d", prec);
+    return LATENTAM_ERR_INVALID_ARG;
+}
+
+latentam_status run_decode_fwd(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V,
+                               int M, int D, float c, latentam_precision prec, float* F_hat, float* row_stats,
+                               cudaStream_t st) {
+    if (prec == LATENTAM_PREC_FP32 && decode_split_supported(d, M, D))
+        return decode_fwd_split(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, st);
+    if (prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_FP32_FMA)
+        return decode_fwd_f32(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, st);
+    if (prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8)
+        return decode_fwd_bf16(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, st, prec == LATENTAM_PREC_FP8);
+    set_error("unknown precision %d", prec);
+    return LATENTAM_ERR_INVALID_ARG;
+}
+
 latentam_status check_camera(const latentam_camera* cam) {
     if (!cam) {
         set_error("null camera");
@@ -657,13 +686,7 @@ latentam_status latentam_decode_fwd(latentam_ctx* ctx, const float* Q, int64_t n
     REQUIRE(aligned16(Q) && aligned16(V) && aligned16(F_hat), "Q, V, F_hat must be 16-byte aligned");
     const float c = logit_scale_ > 0.f ? logit_scale_ : 1.0f / sqrtf((float)d);
     StageTimer tm(ctx, LATENTAM_STAGE_DECODE, (cudaStream_t)stream);
-    if (prec == LATENTAM_PREC_FP32)
-        return decode_fwd_f32(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, (cudaStream_t)stream);
-    if (prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8)
-        return decode_fwd_bf16(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, (cudaStream_t)stream,
-                               prec == LATENTAM_PREC_FP8);
-    set_error("unknown precision %d", prec);
-    return LATENTAM_ERR_INVALID_ARG;
+    return run_decode_fwd(ctx, Q, n, d, K, V, M, D, c, prec, F_hat, row_stats, (cudaStream_t)stream);
 }
 
 latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const float* Q, int64_t n, int32_t d, const float* K,
@@ -698,11 +721,7 @@ latentam_status latentam_decode_loss_bwd(latentam_ctx* ctx, const float* Q, int6
     a.dK = dK;
     a.dV = dV;
     StageTimer tm(ctx, LATENTAM_STAGE_DECODE, (cudaStream_t)stream);
-    if (prec == LATENTAM_PREC_FP32) return decode_loss_bwd_f32(ctx, a, (cudaStream_t)stream);
-    if (prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8)
-        return decode_loss_bwd_bf16(ctx, a, (cudaStream_t)stream, prec == LATENTAM_PREC_FP8);
-    set_error("unknown precision %d", prec);
-    return LATENTAM_ERR_INVALID_ARG;
+    return run_decode_loss_bwd(ctx, a, prec, (cudaStream_t)stream);
 }
 
 namespace {
@@ -745,17 +764,14 @@ latentam_status latentam_decode_fwd_paper(latentam_ctx* ctx, const float* Q, int
     LAT_TRY(enter(ctx));
     LAT_TRY(check_paper(n, ds, Q, W, D, M, df, tau));
     REQUIRE(aligned16(F_hat), "F_hat must be 16-byte aligned");
-    REQUIRE(prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8,
-            "unknown precision %d", prec);
+    REQUIRE(known_prec(prec), "unknown precision %d", prec);
     lat::PaperBuffers b;
     LAT_TRY(paper_buffers(ctx, n, ds, M, df, &b));
     const lat::PaperArgs a{Q, n, ds, W, D, M, df};
     cudaStream_t st = (cudaStream_t)stream;
     StageTimer tm(ctx, LATENTAM_STAGE_DECODE, st);
     LAT_TRY(lat::paper_prepare(ctx, a, b, st));
-    if (prec == LATENTAM_PREC_FP32) return decode_fwd_f32(ctx, b.Qp, n, ds, b.K, D, M, df, 1.0f / tau, F_hat, row_stats, st);
-    return decode_fwd_bf16(ctx, b.Qp, n, ds, b.K, D, M, df, 1.0f / tau, F_hat, row_stats, st,
-                           prec == LATENTAM_PREC_FP8);
+    return run_decode_fwd(ctx, b.Qp, n, ds, b.K, D, M, df, 1.0f / tau, prec, F_hat, row_stats, st);
 }
 
 latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, const float* Q, int64_t n, int32_t ds,
@@ -770,8 +786,7 @@ latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, const float* Q
     REQUIRE(F_dtype == LATENTAM_DTYPE_F32 || F_dtype == LATENTAM_DTYPE_BF16, "unknown target dtype %d", F_dtype);
     REQUIRE(aligned16(D0) && aligned16(F) && aligned16(dQ) && aligned16(dW) && aligned16(dD),
             "D0, F, dQ, dW, dD must be 16-byte aligned");
-    REQUIRE(prec == LATENTAM_PREC_FP32 || prec == LATENTAM_PREC_BF16 || prec == LATENTAM_PREC_FP8,
-            "unknown precision %d", prec);
+    REQUIRE(known_prec(prec), "unknown precision %d", prec);
     lat::PaperBuffers b;
     LAT_TRY(paper_buffers(ctx, n, ds, M, df, &b));
     const lat::PaperArgs pa{Q, n, ds, W, D, M, df};
@@ -796,10 +811,7 @@ latentam_status latentam_decode_loss_bwd_paper(latentam_ctx* ctx, const float* Q
     a.dQ = (dQ || dW) ? b.dQp : nullptr;  // dW needs dQ' for the query-norm term
     a.dK = b.dK;
     a.dV = b.dV;
-    if (prec == LATENTAM_PREC_FP32)
-        LAT_TRY(decode_loss_bwd_f32(ctx, a, st));
-    else
-        LAT_TRY(decode_loss_bwd_bf16(ctx, a, st, prec == LATENTAM_PREC_FP8));
+    LAT_TRY(run_decode_loss_bwd(ctx, a, prec, st));
     return lat::paper_chain(ctx, pa, b, dQ, dW, dD, st);
 }
 

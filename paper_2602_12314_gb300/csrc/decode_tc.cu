@@ -31,35 +31,50 @@ constexpr int kPad = 64;  // query / key rows padded to one 64-wide K chunk
 // ---- operand preparation ----------------------------------------------------------------
 
 // Qb[p][0..63] = bf16(Q[p][0..d)) zero-padded; thread t writes 8 columns (16 bytes) of row t / 8,
-// so a warp reads and writes contiguous memory.
+// so a warp reads and writes contiguous memory.  SPLIT: Qb holds two planes [2][n][64], the hi
+// terms bf16(q) and the lo terms bf16(q - hi).
+template <bool SPLIT>
 __global__ void prep_queries(const float* __restrict__ Q, int64_t n, int d, bf16* __restrict__ Qb) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * (kPad / 8)) return;
     const int64_t p = t / (kPad / 8);
     const int c = (int)(t % (kPad / 8)) * 8;
-    uint4 out = make_uint4(0u, 0u, 0u, 0u);
+    uint4 hi = make_uint4(0u, 0u, 0u, 0u), lo = hi;
     if (c < d) {  // d is a multiple of 8 and Q rows are 16-byte aligned
         const float4 a = *reinterpret_cast<const float4*>(Q + p * d + c);
         const float4 b = *reinterpret_cast<const float4*>(Q + p * d + c + 4);
-        out = make_uint4(tc::pack_bf16x2(a.x, a.y), tc::pack_bf16x2(a.z, a.w), tc::pack_bf16x2(b.x, b.y),
-                         tc::pack_bf16x2(b.z, b.w));
+        tc::pack_split_bf16x2(a.x, a.y, hi.x, lo.x);
+        tc::pack_split_bf16x2(a.z, a.w, hi.y, lo.y);
+        tc::pack_split_bf16x2(b.x, b.y, hi.z, lo.z);
+        tc::pack_split_bf16x2(b.z, b.w, hi.w, lo.w);
     }
-    reinterpret_cast<uint4*>(Qb + p * kPad)[t % (kPad / 8)] = out;
+    reinterpret_cast<uint4*>(Qb + p * kPad)[t % (kPad / 8)] = hi;
+    if (SPLIT) reinterpret_cast<uint4*>(Qb + n * kPad + p * kPad)[t % (kPad / 8)] = lo;
 }
 
-// Kb[j][0..63] (zero-padded) and Vb[j][c]: BF16 copies of the dictionary.
+// Kb[j][0..63] (zero-padded) and Vb[j][c]: BF16 copies of the dictionary (SPLIT: hi planes
+// followed by lo planes, Kb [2][M][64], Vb [2][M][D]).
+template <bool SPLIT>
 __global__ void prep_dict(const float* __restrict__ K, const float* __restrict__ V, int M, int d, int D,
                           bf16* __restrict__ Kb, bf16* __restrict__ Vb) {
-    const int64_t total = (int64_t)M * D + (int64_t)M * kPad;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        if (e < (int64_t)M * D) {
-            Vb[e] = __float2bfloat16_rn(V[e]);
+    const int64_t nv = (int64_t)M * D, nk = (int64_t)M * kPad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv + nk; e += (int64_t)gridDim.x * blockDim.x) {
+        float v;
+        bf16* dst;
+        int64_t plane;
+        if (e < nv) {
+            v = V[e];
+            dst = Vb + e;
+            plane = nv;
         } else {
-            const int64_t f = e - (int64_t)M * D;
+            const int64_t f = e - nv;
             const int j = (int)(f / kPad), k = (int)(f % kPad);
-            const float v = k < d ? K[(int64_t)j * d + k] : 0.f;
-            Kb[f] = __float2bfloat16_rn(v);
+            v = k < d ? K[(int64_t)j * d + k] : 0.f;
+            dst = Kb + f;
+            plane = nk;
         }
+        *dst = __float2bfloat16_rn(v);
+        if (SPLIT) dst[plane] = __float2bfloat16_rn(tc::split_lo(v));
     }
 }
 
@@ -235,9 +250,14 @@ struct SoftmaxParams {
 
 // One CTA holds the logits of 256 atoms; when M > 256 the CTAs of a row block form a cluster
 // and combine their (row max, partial denominator) pairs before normalising.
+// SPLIT_: the FP32 form (queries, keys and A as hi / lo BF16 planes, three MMAs per product):
+// 16-wide K chunks over the d query columns, three ring stages.
+template <bool SPLIT_ = false>
 struct SoftmaxEpi {
-    // persistent: one K chunk (the padded queries) per tile
-    static constexpr int BN = 256, BK = 64, ELEM = 2, STAGES = 1, BOX_B = 256, EPI_WG = 4, E_BOXES = 0, O_BOXES = 4;
+    // plain: one K chunk (the padded queries) per tile
+    static constexpr bool SPLIT = SPLIT_;
+    static constexpr int BN = 256, BK = SPLIT_ ? 16 : 64, ELEM = 2, STAGES = SPLIT_ ? 3 : 1, BOX_B = 256;
+    static constexpr int EPI_WG = 4, E_BOXES = 0, O_BOXES = 4;
     static constexpr int XROUNDS = 1;
     static constexpr bool A_MN = false, B_MN = false;
     using Params = SoftmaxParams;
@@ -277,6 +297,7 @@ struct SoftmaxEpi {
             sum = l;
         }
         const float il = 1.0f / sum;
+        ec.wait_out();
         for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
@@ -315,10 +336,15 @@ struct FhatParams {
 // (FP32 targets) each thread reads its own row from global memory, one chunk ahead.
 // Q8: the contraction runs on E4M3 operands (attention rows scaled per pixel, values per
 // feature, both K-major) and the accumulator is rescaled before any use.
-template <bool ETILE, bool Q8 = false>
+// SPLIT_ (the FP32 form, FP32 or BF16 targets read per thread): A and V as hi / lo BF16 planes,
+// three MMAs per product, dFhat staged as hi / lo planes; 32-byte K chunks so that three ring
+// stages fit beside the output's two planes.
+template <bool ETILE, bool Q8 = false, bool SPLIT_ = false>
 struct FhatEpi {
+    static_assert(!SPLIT_ || (!ETILE && !Q8), "the split form reads FP32 targets per thread");
+    static constexpr bool SPLIT = SPLIT_;
     // persistent, 64-byte K chunks (three ring stages fit beside two epilogue buffers)
-    static constexpr int ELEM = Q8 ? 1 : 2, BK = 64 / ELEM;
+    static constexpr int ELEM = Q8 ? 1 : 2, BK = SPLIT_ ? 16 : 64 / ELEM;
     static constexpr int BN = 256, STAGES = 3, BOX_B = 256, EPI_WG = ETILE ? 4 : 2, XROUNDS = 1;
     static constexpr int E_BOXES = ETILE ? BN / 64 : 0, O_BOXES = BN / 64;  // dFhat staged over the target
     // B = V (atoms x features, features contiguous: MN-major) or, for E4M3, V^T (K-major)
@@ -377,6 +403,7 @@ struct FhatEpi {
         const bool valid = pix < p.n;
         const float isp = row_scale_inv(p, pix, valid);
         if (p.Fout) {  // inference form, launched without a cluster
+            ec.wait_out();
             float h[32];
             for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
                 fhat32(p, ec, c0, isp, h);
@@ -448,6 +475,7 @@ struct FhatEpi {
             }
         }
         // dFhat overwrites the target chunk it was formed from (same thread, same bytes)
+        ec.wait_out();
         sweep(p, ec, frow, ncols, isp, [&](int c0, const float(&h)[32], const float(&f)[32]) {
             float v[32];
 #pragma unroll
@@ -468,10 +496,13 @@ struct DsParams {
 };
 
 // One CTA holds 256 atoms of its rows (M > 256: several CTAs along y, nothing to trade: the
-// row term <A, dA> comes from G2).
+// row term <A, dA> comes from G2).  SPLIT_: the FP32 form (hi / lo planes in and out).
+template <bool SPLIT_ = false>
 struct DsEpi {
+    static constexpr bool SPLIT = SPLIT_;
     // the attention rows of the tile come through shared memory
-    static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 0, MIN_SMEM = 0, MIN_BLOCKS = 2;
+    static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 0, MIN_SMEM = 0;
+    static constexpr int MIN_BLOCKS = SPLIT_ ? 1 : 2;
     static constexpr int E_BOXES = BN / 64, O_BOXES = BN / 64;  // dS staged over the attention rows
     static constexpr bool A_MN = false, B_MN = false;
     using Params = DsParams;
@@ -501,8 +532,9 @@ struct DqParams {
     float* dQ;
 };
 
-template <int BN_>
+template <int BN_, bool SPLIT_ = false>
 struct DqEpi {
+    static constexpr bool SPLIT = SPLIT_;
     static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, O_BOXES = 0, XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
@@ -539,9 +571,11 @@ struct PartParams {
     float* part;
 };
 
-template <int BN_>
+template <int BN_, bool SPLIT_ = false>
 struct PartEpi {
-    static constexpr int BN = BN_, STAGES = BN_ <= 64 ? 6 : 4, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, O_BOXES = 0;
+    static constexpr bool SPLIT = SPLIT_;
+    static constexpr int BN = BN_, STAGES = (BN_ <= 64 ? 6 : 4) / (SPLIT_ ? 2 : 1), BOX_B = BN_, EPI_WG = 1;
+    static constexpr int E_BOXES = 0, O_BOXES = 0;
     static constexpr int XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
@@ -623,6 +657,42 @@ latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_
         return LATENTAM_ERR_CUDA;
     }
     return LATENTAM_OK;
+}
+
+// Tensor map of a split operand: two row-major BF16 planes [2][rows][ld] (hi, then lo) as a 3D
+// tensor with the plane as z, boxes of box_inner (64 / 32 / 16: 128 / 64 / 32-byte swizzle) x
+// box_rows x 1 plane; out-of-range elements read as zero.
+latentam_status split_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows,
+                          int box_inner) {
+    EncodeTiledFn enc;
+    LAT_TRY(encoder(&enc));
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || (ld * 2) % 16 || (rows * ld * 2) % 16) {
+        set_error("split tensor-core operand not 16-byte aligned");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(rows * ld * 2)};
+    const cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapSwizzle sw = box_inner == 16   ? CU_TENSOR_MAP_SWIZZLE_32B
+                                  : box_inner == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                    : CU_TENSOR_MAP_SWIZZLE_128B;
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for a split %lld x %lld operand", (int)r, (long long)rows,
+                  (long long)inner);
+        return LATENTAM_ERR_CUDA;
+    }
+    return LATENTAM_OK;
+}
+
+// The map of an operand of the plain (BF16) or the split (FP32) form.
+latentam_status op_map(bool split, CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld,
+                       int box_rows, int box_inner = tc::kChunkK) {
+    return split ? split_map(m, base, inner, rows, ld, box_rows, box_inner)
+                 : bf16_map(m, base, inner, rows, ld, box_rows, box_inner);
 }
 
 // Launch one tile grid of Epi (emap: epilogue operand, omap: staged output); cluster_y > 1
@@ -758,10 +828,12 @@ struct TcBuffers {
     float *stats, *inv_t;
 };
 
-latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool train, bool fp8, TcBuffers* b) {
+// split: Qb, Kb, Vb, A, dF and dS each hold a hi and a lo plane.
+latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool train, bool fp8, TcBuffers* b,
+                           bool split = false) {
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const int64_t nn = std::max<int64_t>(n, 1);
-    const size_t e2 = sizeof(bf16);
+    const size_t e2 = sizeof(bf16) * (split ? 2 : 1);  // bytes per element over all planes
     size_t o = 0, off[9];
     off[0] = o, o += up(e2 * nn * kPad);                      // Qb
     off[1] = o, o += up(e2 * (size_t)M * kPad);               // Kb
@@ -869,26 +941,30 @@ latentam_status check_tc_shape(int M, int D) {
     return LATENTAM_OK;
 }
 
-// Operand preparation + G1 (softmax).
+// Operand preparation + G1 (softmax).  SPLIT: the FP32 form (hi / lo planes, 16-wide K chunks
+// over the d query columns).
+template <bool SPLIT>
 latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V, int M,
                            int D, float c, const TcBuffers& b, float* stats, cudaStream_t st) {
-    prep_dict<<<std::min(4 * ctx->num_sms, cdiv((int64_t)M * (D + kPad), 256)), 256, 0, st>>>(K, V, M, d, D, b.Kb,
-                                                                                                b.Vb);
+    prep_dict<SPLIT><<<std::min(4 * ctx->num_sms, cdiv((int64_t)M * (D + kPad), 256)), 256, 0, st>>>(K, V, M, d, D,
+                                                                                                      b.Kb, b.Vb);
     LAT_CHECK_LAUNCH("prep_dict");
-    prep_queries<<<cdiv(n * (kPad / 8), 256), 256, 0, st>>>(Q, n, d, b.Qb);
+    prep_queries<SPLIT><<<cdiv(n * (kPad / 8), 256), 256, 0, st>>>(Q, n, d, b.Qb);
     LAT_CHECK_LAUNCH("prep_queries");
     if (b.Vtq) {
         fp8_values<<<cdiv(D, 128), 128, 0, st>>>(V, M, D, b.Vtq, b.inv_t);
         LAT_CHECK_LAUNCH("fp8_values");
     }
+    using Epi = SoftmaxEpi<SPLIT>;
     CUtensorMap mQ, mK;
-    LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, kTileM));
-    LAT_TRY(bf16_map(&mK, b.Kb, kPad, M, kPad, 256));
+    LAT_TRY(op_map(SPLIT, &mQ, b.Qb, kPad, n, kPad, kTileM, Epi::BK));
+    LAT_TRY(op_map(SPLIT, &mK, b.Kb, kPad, M, kPad, 256, Epi::BK));
     CUtensorMap mA;  // the attention rows leave through the TMA
-    LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM));
+    LAT_TRY(op_map(SPLIT, &mA, b.A, M, n, M, kTileM));
     SoftmaxParams sp{n, M, c, b.A, stats};
     const int cy = cdiv(M, 256);
-    return launch_persist<SoftmaxEpi>(ctx, mQ, mK, cdiv(n, kTileM), 1, cy, true, sp, b.err, st, nullptr, &mA);
+    const int kc = SPLIT ? d / Epi::BK : 1;  // plain: the padded queries are one 64-wide chunk
+    return launch_persist<Epi>(ctx, mQ, mK, cdiv(n, kTileM), kc, cy, true, sp, b.err, st, nullptr, &mA);
 }
 
 // G2: Fhat = A V (A in 32-wide K chunks, 64-byte swizzle), B = V read MN-major in 64 x 32
@@ -896,25 +972,27 @@ latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, 
 latentam_status tc_fhat8(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp,
                          cudaStream_t st);
 
+template <bool SPLIT>
 latentam_status tc_fhat(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M, int D, const FhatParams& fp,
                         cudaStream_t st) {
-    if (b.Aq) return tc_fhat8(ctx, b, n, M, D, fp, st);
-    constexpr int BK = FhatEpi<true>::BK;
+    if (!SPLIT && b.Aq) return tc_fhat8(ctx, b, n, M, D, fp, st);
+    using EpiF = FhatEpi<false, false, SPLIT>;  // targets read per thread (FP32 or BF16)
+    constexpr int BK = EpiF::BK;
     CUtensorMap mA, mV;
-    LAT_TRY(bf16_map(&mA, b.A, M, n, M, kTileM, BK));
-    LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, BK));
+    LAT_TRY(op_map(SPLIT, &mA, b.A, M, n, M, kTileM, BK));
+    LAT_TRY(op_map(SPLIT, &mV, b.Vb, D, M, D, BK));
     const int cy = cdiv(D, 256), tiles = cdiv(n, kTileM), kc = cdiv(M, BK);
     if (fp.Fout)  // no row terms: independent column tiles
-        return launch_persist<FhatEpi<false>>(ctx, mA, mV, tiles, kc, cy, false, fp, b.err, st);
+        return launch_persist<EpiF>(ctx, mA, mV, tiles, kc, cy, false, fp, b.err, st);
     CUtensorMap mdF;  // dFhat leaves through the TMA
-    LAT_TRY(bf16_map(&mdF, fp.dF, D, n, D, kTileM));
-    if (fp.F_dtype == LATENTAM_DTYPE_BF16) {
+    LAT_TRY(op_map(SPLIT, &mdF, fp.dF, D, n, D, kTileM));
+    if (!SPLIT && fp.F_dtype == LATENTAM_DTYPE_BF16) {
         // BF16 targets: the tile's target rows are TMA-loaded into shared memory for the epilogue
         CUtensorMap mF;
         LAT_TRY(bf16_map(&mF, fp.F, D, n, D, kTileM));
         return launch_persist<FhatEpi<true>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, &mF, &mdF);
     }
-    return launch_persist<FhatEpi<false>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, nullptr, &mdF);
+    return launch_persist<EpiF>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, nullptr, &mdF);
 }
 
 // G2 on E4M3 operands: the attention rows scaled per pixel (from the softmax row statistics)
@@ -941,14 +1019,15 @@ latentam_status tc_fhat8(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M
     return launch_persist<FhatEpi<false, true>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, nullptr, &mdF);
 }
 
-}  // namespace
-
-latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st, bool fp8) {
+// The six contractions of the decode, its loss and its backward.  SPLIT: the FP32 form, every
+// operand a hi / lo pair of BF16 planes and every product three MMAs (see tc::mma_step).
+template <bool SPLIT>
+latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st, bool fp8) {
     const int64_t n = a.n;
     const int M = a.M, D = a.D, d = a.d;
     LAT_TRY(check_tc_shape(M, D));
     TcBuffers b;
-    LAT_TRY(tc_buffers(ctx, n, M, D, true, fp8, &b));
+    LAT_TRY(tc_buffers(ctx, n, M, D, true, fp8, &b, SPLIT));
     cudaError_t e = cudaMemsetAsync(b.acc, 0, 256, st);
     if (e != cudaSuccess) return cuda_error(e, "memset accumulators");
     if (n > 0) {
@@ -965,30 +1044,32 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
     const size_t part_floats = std::max((size_t)2 * zV0 * M * D, (size_t)2 * zK0 * M * BNq);
     b.part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * part_floats));
     if (!b.part) return LATENTAM_ERR_OUT_OF_MEMORY;
+    const int which = SPLIT ? 16 : 0;  // autotuner key offset of the split form
     if (n > 0) {
         // G1: S = Q K^T -> softmax
-        LAT_TRY(tc_forward(ctx, a.Q, n, d, a.K, a.V, M, D, a.c, b, b.stats, st));
+        LAT_TRY(tc_forward<SPLIT>(ctx, a.Q, n, d, a.K, a.V, M, D, a.c, b, b.stats, st));
         // G2: Fhat = A V -> loss terms -> dFhat
         FhatParams fp{n, D, a.F, a.F_dtype, a.mask, a.cfg, b.acc, b.dF, b.row, nullptr, nullptr, nullptr};
-        LAT_TRY(tc_fhat(ctx, b, n, M, D, fp, st));
+        LAT_TRY(tc_fhat<SPLIT>(ctx, b, n, M, D, fp, st));
         // G3: dA = dFhat V^T -> dS
         CUtensorMap mdF, mV, mdS, mK;
-        LAT_TRY(bf16_map(&mdF, b.dF, D, n, D, kTileM));
-        LAT_TRY(bf16_map(&mV, b.Vb, D, M, D, 256));
+        LAT_TRY(op_map(SPLIT, &mdF, b.dF, D, n, D, kTileM));
+        LAT_TRY(op_map(SPLIT, &mV, b.Vb, D, M, D, 256));
         DsParams dp{n, M, b.A, b.row, b.dS};
         const dim3 grow(cdiv(n, kTileM), 1, 1);
         const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
         CUtensorMap mAe, mdSo;  // attention rows for the epilogue, dS out through the TMA
-        LAT_TRY(bf16_map(&mAe, b.A, M, n, M, kTileM));
-        LAT_TRY(bf16_map(&mdSo, b.dS, M, n, M, kTileM));
-        LAT_TRY(launch_gemm<DsEpi>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st, &mAe, &mdSo));
+        LAT_TRY(op_map(SPLIT, &mAe, b.A, M, n, M, kTileM));
+        LAT_TRY(op_map(SPLIT, &mdSo, b.dS, M, n, M, kTileM));
+        LAT_TRY((launch_gemm<DsEpi<SPLIT>>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st,
+                                           &mAe, &mdSo)));
         // G4: dQ = c dS K, B = K padded read MN-major (queries x atoms)
         if (a.dQ) {
-            LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, kTileM));
-            LAT_TRY(bf16_map(&mK, b.Kb, kPad, M, kPad, 64));
+            LAT_TRY(op_map(SPLIT, &mdS, b.dS, M, n, M, kTileM));
+            LAT_TRY(op_map(SPLIT, &mK, b.Kb, kPad, M, kPad, 64));
             DqParams qp{n, d, a.c, a.dQ};
             const tc::GemmGrid g4{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
-            LAT_TRY(launch_gemm<DqEpi<BNq>>(mdS, mK, grow, g4, qp, b.err, st));
+            LAT_TRY((launch_gemm<DqEpi<BNq, SPLIT>>(mdS, mK, grow, g4, qp, b.err, st)));
         }
     }
     // G5: dV = A^T dFhat (+ trust region), both operands pixel-major (MN-major)
@@ -996,16 +1077,17 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
     if (a.dV) {
         if (n > 0) {
             CUtensorMap mA, mdF;
-            LAT_TRY(bf16_map(&mA, b.A, M, n, M, 64));
-            LAT_TRY(bf16_map(&mdF, b.dF, D, n, D, 64));
+            LAT_TRY(op_map(SPLIT, &mA, b.A, M, n, M, 64));
+            LAT_TRY(op_map(SPLIT, &mdF, b.dF, D, n, D, 64));
             PartParams pp{M, D, D, b.part};
             auto g5 = [&](int z) -> latentam_status {
                 int zz;
                 const tc::GemmGrid g = pixel_split(n, z, &zz);
-                return launch_gemm<PartEpi<256>>(mA, mdF, dim3(cdiv(M, kTileM), cdiv(D, 256), zz), g, pp, b.err, st);
+                return launch_gemm<PartEpi<256, SPLIT>>(mA, mdF, dim3(cdiv(M, kTileM), cdiv(D, 256), zz), g, pp, b.err,
+                                                        st);
             };
             int z;
-            LAT_TRY(tuned_split(ctx, n, M, D, 5, zV0, st, g5, &z));
+            LAT_TRY(tuned_split(ctx, n, M, D, 5 + which, zV0, st, g5, &z));
             LAT_TRY(g5(z));
             pixel_split(n, z, &zV);
         }
@@ -1017,16 +1099,16 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
     if (a.dK) {
         if (n > 0) {
             CUtensorMap mdS, mQ;
-            LAT_TRY(bf16_map(&mdS, b.dS, M, n, M, 64));
-            LAT_TRY(bf16_map(&mQ, b.Qb, kPad, n, kPad, 64));
+            LAT_TRY(op_map(SPLIT, &mdS, b.dS, M, n, M, 64));
+            LAT_TRY(op_map(SPLIT, &mQ, b.Qb, kPad, n, kPad, 64));
             PartParams pp{M, BNq, BNq, b.part};
             auto g6 = [&](int z) -> latentam_status {
                 int zz;
                 const tc::GemmGrid g = pixel_split(n, z, &zz);
-                return launch_gemm<PartEpi<BNq>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zz), g, pp, b.err, st);
+                return launch_gemm<PartEpi<BNq, SPLIT>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zz), g, pp, b.err, st);
             };
             int z;
-            LAT_TRY(tuned_split(ctx, n, M, D, 6, zK0, st, g6, &z));
+            LAT_TRY(tuned_split(ctx, n, M, D, 6 + which, zK0, st, g6, &z));
             LAT_TRY(g6(z));
             pixel_split(n, z, &zK);
         }
@@ -1039,16 +1121,17 @@ latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cud
     return LATENTAM_OK;
 }
 
-latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V,
-                                int M, int D, float c, float* F_hat, float* row_stats, cudaStream_t st, bool fp8) {
+template <bool SPLIT>
+latentam_status tc_fwd(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V, int M,
+                       int D, float c, float* F_hat, float* row_stats, cudaStream_t st, bool fp8) {
     LAT_TRY(check_tc_shape(M, D));
     if (n == 0) return LATENTAM_OK;
     TcBuffers b;
-    LAT_TRY(tc_buffers(ctx, n, M, D, false, fp8, &b));
+    LAT_TRY(tc_buffers(ctx, n, M, D, false, fp8, &b, SPLIT));
     cudaError_t e = cudaMemsetAsync(b.acc, 0, 256, st);
     if (e != cudaSuccess) return cuda_error(e, "memset accumulators");
     float* stats = fp8 ? b.stats : row_stats;
-    LAT_TRY(tc_forward(ctx, Q, n, d, K, V, M, D, c, b, stats, st));
+    LAT_TRY(tc_forward<SPLIT>(ctx, Q, n, d, K, V, M, D, c, b, stats, st));
     if (fp8 && row_stats) {
         e = cudaMemcpyAsync(row_stats, b.stats, sizeof(float) * 2 * n, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_error(e, "copy row statistics");
@@ -1056,9 +1139,33 @@ latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, in
     if (F_hat) {
         FhatParams fp{n, D, nullptr, LATENTAM_DTYPE_F32, nullptr, latentam_loss_cfg{}, b.acc, nullptr, b.row, F_hat,
                       nullptr, nullptr};
-        LAT_TRY(tc_fhat(ctx, b, n, M, D, fp, st));
+        LAT_TRY(tc_fhat<SPLIT>(ctx, b, n, M, D, fp, st));
     }
     return LATENTAM_OK;
+}
+
+}  // namespace
+
+latentam_status decode_loss_bwd_bf16(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st, bool fp8) {
+    return tc_loss_bwd<false>(ctx, a, st, fp8);
+}
+
+latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V,
+                                int M, int D, float c, float* F_hat, float* row_stats, cudaStream_t st, bool fp8) {
+    return tc_fwd<false>(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, st, fp8);
+}
+
+bool decode_split_supported(int d, int M, int D) {
+    return (d == 16 || d == 32 || d == 64) && M <= kMaxCols && D <= kMaxCols;
+}
+
+latentam_status decode_loss_bwd_split(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st) {
+    return tc_loss_bwd<true>(ctx, a, st, false);
+}
+
+latentam_status decode_fwd_split(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K, const float* V,
+                                 int M, int D, float c, float* F_hat, float* row_stats, cudaStream_t st) {
+    return tc_fwd<true>(ctx, Q, n, d, K, V, M, D, c, F_hat, row_stats, st, false);
 }
 
 }  // namespace lat

@@ -253,6 +253,13 @@ latentam_status decode_noalloc_setup(latentam_ctx* ctx);
 latentam_status decode_fwd_bf16(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K,
                                 const float* V, int M, int D, float c, float* F_hat, float* row_stats,
                                 cudaStream_t st, bool fp8 = false);
+// The FP32 form on the tensor cores: every FP32 operand as a hi / lo pair of BF16 terms and every
+// product as three MMAs (hi hi + hi lo + lo hi), FP32 accumulation; supported for M, D <= 1024.
+bool decode_split_supported(int d, int M, int D);
+latentam_status decode_loss_bwd_split(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t st);
+latentam_status decode_fwd_split(latentam_ctx* ctx, const float* Q, int64_t n, int d, const float* K,
+                                 const float* V, int M, int D, float c, float* F_hat, float* row_stats,
+                                 cudaStream_t st);
 
 // The paper's W / D / tau form of the decode, computed through the free-key decode.
 struct PaperArgs {

@@ -117,6 +117,39 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// 3D TMA tile load (x inner, y row, z plane) completing on `bar`: one plane of a split operand
+// stored as [2][rows][inner] (hi plane z = 0, lo plane z = 1).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// 2D (z < 0) or 3D tile load: the plain operands use 2D maps, the split ones 3D maps.
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    if (z < 0)
+        tma_load_2d(dst, map, bar, x, y);
+    else
+        tma_load_3d(dst, map, bar, x, y, z);
+}
+
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
+// 3D TMA tile store from shared memory (bulk-group completion) into plane z.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
 // Prefetch the 2D TMA tile at (x, y) into L2 (no shared memory, no completion).
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
     asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
@@ -201,6 +234,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// Shared-memory descriptor of a K-major tile written by TMA with 32-byte swizzle: rows of 16
+// BF16 (32 B), 8-row atoms 256 B apart.  `saddr` is the 256-aligned tile base.
+__device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+}
+
 // Shared-memory descriptor of a K-major tile written by TMA with 64-byte swizzle: rows of 32
 // BF16 (64 B), 8-row atoms 512 B apart.  `saddr` is the (512-aligned tile base + k * 32 B)
 // shared address.
@@ -239,6 +279,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Split of an FP32 value into two BF16 terms: hi = bf16(x), lo = bf16(x - hi) (x - hi is exact
+// in FP32), so hi + lo equals x within 2^-16 |x|.  A product a b is then taken as
+// a_hi b_hi + a_hi b_lo + a_lo b_hi (the dropped a_lo b_lo is below 2^-16 |a b|).
+__device__ __forceinline__ float split_lo(float x) {
+    return x - __bfloat162float(__float2bfloat16_rn(x));
+}
+// The hi and lo terms of (x0, x1), each packed as two BF16.
+__device__ __forceinline__ void pack_split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+    hi = pack_bf16x2(x0, x1);
+    lo = pack_bf16x2(split_lo(x0), split_lo(x1));
 }
 
 }  // namespace tc

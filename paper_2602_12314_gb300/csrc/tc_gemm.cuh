@@ -32,12 +32,21 @@ __host__ __device__ constexpr uint32_t tmem_cols_for(int n) {
     return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
 }
 
+// Planes per operand: 2 for the split form (every FP32 operand held as a BF16 hi and lo term,
+// stored [2][rows][inner]), 1 otherwise.
+template <class Epi>
+__host__ __device__ constexpr int planes() {
+    return Epi::SPLIT ? 2 : 1;
+}
+
 // Shared memory at the start of the tile: the operand pipeline, reused once the MMAs are done
-// for the epilogue operand (E_BOXES boxes of 64 x 128 BF16) and the staged output (O_BOXES).
+// for the epilogue operand (E_BOXES boxes of 64 x 128 BF16 per plane) and the staged output
+// (O_BOXES per plane).
 template <class Epi>
 __host__ __device__ constexpr uint32_t tile_region_bytes() {
-    const uint32_t pipe = (uint32_t)Epi::STAGES * (kTileABytes + (uint32_t)Epi::BN * 128);
-    const uint32_t boxes = (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * kTileABytes;
+    const uint32_t pipe = (uint32_t)Epi::STAGES * planes<Epi>() * (kTileABytes + (uint32_t)Epi::BN * 128);
+    const uint32_t boxes =
+        (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * planes<Epi>() * kTileABytes;
     return pipe > boxes ? pipe : boxes;
 }
 
@@ -101,7 +110,9 @@ struct GemmGrid {
 };
 
 // Epi must provide: static constexpr int BN, STAGES, BOX_B (rows per TMA box of a K-major B,
-// divides BN, <= 256); static constexpr bool A_MN, B_MN (operand stored MN-major: the tile is
+// divides BN, <= 256); static constexpr bool SPLIT (every operand, epilogue operand and staged
+// output held as a BF16 hi and lo plane, 3D tensor maps with the plane as z, and each product
+// taken as three MMAs); static constexpr bool A_MN, B_MN (operand stored MN-major: the tile is
 // loaded as 64 (MN) x 64 (K) boxes of a row-major K x MN matrix, x = MN, y = K); struct
 // Params; static constexpr int EPI_WG (1 or 2 epilogue warpgroups: warpgroup g owns the
 // 32-column chunks c with c % EPI_WG == g of every row); static constexpr int E_BOXES (number
@@ -129,6 +140,19 @@ struct EpiCtx {
     uint32_t xphase = 0;   // phase parity of xbar for this tile
     int ngroups = 1;       // epilogue warpgroups
     int leader = 64;       // first epilogue thread
+    uint32_t eplane = 0;   // split form: bytes from the hi to the lo plane of the epilogue operand
+    uint32_t oplane = 0;   // split form: bytes from the hi to the lo plane of the staged output
+    uint64_t* ofree = nullptr;  // split persistent form: completes when the staging buffers are free
+    uint32_t ofree_phase = 0;
+
+    // Split persistent form: wait until the previous tile's staged output has been read by its
+    // TMA stores (call before the first put32; a no-op elsewhere).  Bounded.
+    __device__ __forceinline__ bool wait_out() const {
+        if (!ofree) return true;
+        const bool ok = mbar_wait(ofree, ofree_phase, abort);
+        if (!ok) *abort = 1;
+        return ok;
+    }
 
     // Give this row's kXchgVals partials to every other CTA of the cluster and wait for theirs
     // (read back with xval).  Warpgroup 0 stages the CTA's partials in shared memory; one thread
@@ -164,23 +188,38 @@ struct EpiCtx {
 
     // Wait for box b of the epilogue operand (bounded; false if it gave up).
     __device__ __forceinline__ bool wait_box(int b) const { return mbar_wait(&ebar[b], ephase, abort); }
-    // Stage 32 values of this thread's row as BF16 at column c0 (a multiple of 32) of the output.
+    // Stage 32 values of this thread's row as BF16 at column c0 (a multiple of 32) of the output
+    // (split form: the hi terms in the hi plane, the lo terms in the lo plane).
     __device__ __forceinline__ void put32(int c0, const float (&v)[32]) const {
         uint8_t* base = otile + (c0 >> 6) * (kTileM * 128) + row * 128;
         const int j0 = (c0 & 63) >> 3;
+        if (oplane) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) pack_split_bf16x2(v[8 * q + 2 * k], v[8 * q + 2 * k + 1], h[k], l[k]);
+                const int off = ((j0 + q) ^ (row & 7)) << 4;
+                *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4*>(base + oplane + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             *reinterpret_cast<uint4*>(base + (((j0 + q) ^ (row & 7)) << 4)) =
                 make_uint4(pack_bf16x2(v[8 * q], v[8 * q + 1]), pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
                            pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
     }
-    // 32 BF16 values of this thread's row from column c0 (a multiple of 32) of the operand.
+    // 32 values of this thread's row from column c0 (a multiple of 32) of the operand (split
+    // form: hi + lo).
     __device__ __forceinline__ void row32(int c0, float (&v)[32]) const {
         const uint8_t* base = etile + (c0 >> 6) * (kTileM * 128) + row * 128;
         const int j0 = (c0 & 63) >> 3;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint4 u = *reinterpret_cast<const uint4*>(base + (((j0 + q) ^ (row & 7)) << 4));
+            const int off = ((j0 + q) ^ (row & 7)) << 4;
+            const uint4 u = *reinterpret_cast<const uint4*>(base + off);
             const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
@@ -188,9 +227,38 @@ struct EpiCtx {
                 v[8 * q + 2 * h] = f.x;
                 v[8 * q + 2 * h + 1] = f.y;
             }
+            if (eplane) {
+                const uint4 ul = *reinterpret_cast<const uint4*>(base + eplane + off);
+                const uint32_t wl[4] = {ul.x, ul.y, ul.z, ul.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wl[h]));
+                    v[8 * q + 2 * h] += f.x;
+                    v[8 * q + 2 * h + 1] += f.y;
+                }
+            }
         }
     }
 };
+
+// One MMA step of the product: A x B (plain) or, split, A_hi B_hi + A_hi B_lo + A_lo B_hi.
+template <bool SPLIT>
+__device__ __forceinline__ void mma_step(uint32_t d, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi, uint64_t b_lo,
+                                         uint32_t idesc, uint32_t acc) {
+    mma_bf16(d, a_hi, b_hi, idesc, acc);
+    if (SPLIT) {
+        mma_bf16(d, a_hi, b_lo, idesc, 1u);
+        mma_bf16(d, a_lo, b_hi, idesc, 1u);
+    }
+}
+
+// 2D (plain, z < 0) or 3D (split plane z) tile store.
+__device__ __forceinline__ void tma_store(const CUtensorMap* map, const void* src, int x, int y, int z) {
+    if (z < 0)
+        tma_store_2d(map, src, x, y);
+    else
+        tma_store_3d(map, src, x, y, z);
+}
 
 template <class Epi>
 __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
@@ -203,8 +271,10 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     constexpr int BOX_B = Epi::BOX_B;
     constexpr int NSUB = BN <= 256 ? 1 : 2;      // MMA instructions per K step (N <= 256 each)
     constexpr int SUBN = BN / NSUB;
-    constexpr uint32_t B_BYTES = (uint32_t)BN * 128;
-    constexpr uint32_t STAGE_BYTES = kTileABytes + B_BYTES;
+    constexpr bool SPLIT = Epi::SPLIT;
+    constexpr int PL = planes<Epi>();
+    constexpr uint32_t B_BYTES = (uint32_t)BN * 128;  // per plane
+    constexpr uint32_t STAGE_BYTES = PL * (kTileABytes + B_BYTES);  // [A planes][B planes]
     constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
     constexpr bool A_MN = Epi::A_MN, B_MN = Epi::B_MN;
     constexpr uint32_t IDESC = idesc_bf16(kTileM, SUBN, A_MN, B_MN);
@@ -213,7 +283,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     static_assert(!B_MN || SUBN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
     constexpr int E_BOXES = Epi::E_BOXES;
     constexpr uint32_t TILE_REGION = tile_region_bytes<Epi>();
-    static_assert(E_BOXES <= 8 && Epi::O_BOXES <= 8, "at most 8 boxes of epilogue operand / output");
+    static_assert(E_BOXES * PL <= 8 && Epi::O_BOXES * PL <= 8, "at most 8 boxes of epilogue operand / output");
     static_assert(Epi::XROUNDS == 0, "row exchanges run in the persistent form");
 
     extern __shared__ uint8_t smem_raw[];
@@ -263,23 +333,29 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                     *abort_flag = 1;
                     break;
                 }
-                uint8_t* sa = smem + s * STAGE_BYTES;
-                uint8_t* sb = sa + kTileABytes;
                 const int kx = (k_begin + i) * kChunkK;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
-                if (A_MN) {
 #pragma unroll
-                    for (int b = 0; b < kTileM / 64; ++b) tma_load_2d(sa + b * kMnBoxBytes, &tmA, &full[s], m0 + 64 * b, kx);
-                } else {
-                    tma_load_2d(sa, &tmA, &full[s], kx, m0);
-                }
-                if (B_MN) {
+                for (int z = 0; z < PL; ++z) {
+                    const int zz = SPLIT ? z : -1;
+                    uint8_t* sa = smem + s * STAGE_BYTES + z * kTileABytes;
+                    uint8_t* sb = smem + s * STAGE_BYTES + PL * kTileABytes + z * B_BYTES;
+                    if (A_MN) {
 #pragma unroll
-                    for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * kMnBoxBytes, &tmB, &full[s], n0 + 64 * b, kx);
-                } else {
+                        for (int b = 0; b < kTileM / 64; ++b)
+                            tma_load(sa + b * kMnBoxBytes, &tmA, &full[s], m0 + 64 * b, kx, zz);
+                    } else {
+                        tma_load(sa, &tmA, &full[s], kx, m0, zz);
+                    }
+                    if (B_MN) {
 #pragma unroll
-                    for (int b = 0; b < BN / BOX_B; ++b)
-                        tma_load_2d(sb + b * BOX_B * 128, &tmB, &full[s], kx, n0 + b * BOX_B);
+                        for (int b = 0; b < BN / 64; ++b)
+                            tma_load(sb + b * kMnBoxBytes, &tmB, &full[s], n0 + 64 * b, kx, zz);
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < BN / BOX_B; ++b)
+                            tma_load(sb + b * BOX_B * 128, &tmB, &full[s], kx, n0 + b * BOX_B, zz);
+                    }
                 }
                 ++issued;
             }
@@ -293,8 +369,10 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 if (mbar_wait(accum, 0, abort_flag) && !*abort_flag) {
                     prefetch_tmap(&tmE);
                     for (int b = 0; b < E_BOXES; ++b) {
-                        mbar_expect_tx(&ebar[b], kTileM * 128);
-                        tma_load_2d(smem + b * (kTileM * 128), &tmE, &ebar[b], n0 + 64 * b, m0);
+                        mbar_expect_tx(&ebar[b], PL * kTileM * 128);
+                        for (int z = 0; z < PL; ++z)
+                            tma_load(smem + (z * E_BOXES + b) * (kTileM * 128), &tmE, &ebar[b], n0 + 64 * b, m0,
+                                     SPLIT ? z : -1);
                     }
                     for (int b = 0; b < E_BOXES; ++b) (void)mbar_wait(&ebar[b], 0, nullptr);
                 } else {
@@ -314,17 +392,22 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                const uint32_t sb = sa + kTileABytes;
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);  // A hi (then A lo)
+                const uint32_t sb = sa + PL * kTileABytes;             // B hi (then B lo)
+                auto adesc = [&](uint32_t base, int kk) {
+                    return A_MN ? mn128_desc(base + kk * 16 * 128) : sw128_desc(base + kk * 32);
+                };
+                auto bdesc = [&](uint32_t base, int j, int kk) {
+                    return B_MN ? mn128_desc(base + (uint32_t)(j * (SUBN / 64)) * kMnBoxBytes + kk * 16 * 128)
+                                : sw128_desc(base + (uint32_t)(j * SUBN * 128) + kk * 32);
+                };
 #pragma unroll
                 for (int kk = 0; kk < kChunkK / 16; ++kk) {
-                    const uint64_t da = A_MN ? mn128_desc(sa + kk * 16 * 128) : sw128_desc(sa + kk * 32);
+                    const uint64_t da = adesc(sa, kk), dal = adesc(sa + kTileABytes, kk);
 #pragma unroll
-                    for (int j = 0; j < NSUB; ++j) {
-                        const uint64_t db = B_MN ? mn128_desc(sb + (uint32_t)(j * (SUBN / 64)) * kMnBoxBytes + kk * 16 * 128)
-                                                 : sw128_desc(sb + (uint32_t)(j * SUBN * 128) + kk * 32);
-                        mma_bf16(tmem_base + (uint32_t)(j * SUBN), da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
-                    }
+                    for (int j = 0; j < NSUB; ++j)
+                        mma_step<SPLIT>(tmem_base + (uint32_t)(j * SUBN), da, dal, bdesc(sb, j, kk),
+                                        bdesc(sb + B_BYTES, j, kk), IDESC, (i > 0 || kk > 0) ? 1u : 0u);
                 }
                 mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
             }
@@ -346,6 +429,10 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
         epi_sync(128 * Epi::EPI_WG);
         EpiCtx ec{tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch,
                   E_BOXES > 0 ? smem : nullptr, smem, ebar, abort_flag, 0, 1, nullptr, nullptr};
+        if (SPLIT) {
+            ec.eplane = (uint32_t)E_BOXES * kTileM * 128;
+            ec.oplane = (uint32_t)Epi::O_BOXES * kTileABytes;
+        }
         int out_boxes = 0;
         if (*decision) out_boxes = Epi::run(ep, ec);
         if (Epi::O_BOXES > 0) {
@@ -355,7 +442,8 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
             epi_sync(128 * Epi::EPI_WG);
             if (threadIdx.x == 64 && out_boxes > 0 && !*abort_flag) {
                 for (int b = 0; b < out_boxes && b < Epi::O_BOXES; ++b)
-                    tma_store_2d(&tmO, smem + b * kTileABytes, n0 + 64 * b, m0);
+                    for (int z = 0; z < PL; ++z)
+                        tma_store(&tmO, smem + (z * Epi::O_BOXES + b) * kTileABytes, n0 + 64 * b, m0, SPLIT ? z : -1);
                 bulk_commit();
                 bulk_wait_read();  // shared memory stays valid until the copies have read it
             }
@@ -408,10 +496,11 @@ __host__ __device__ constexpr uint32_t persist_box_bytes() {  // one box buffer
     return (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * kTileABytes;
 }
 
-// One ring stage: A (128 x BK) and B (BN x BK) elements of Epi::ELEM bytes (2: BF16, 1: E4M3).
+// One ring stage: A (128 x BK) and B (BN x BK) elements of Epi::ELEM bytes (2: BF16, 1: E4M3),
+// each in both planes in the split form ([A hi][A lo][B hi][B lo]).
 template <class Epi>
 __host__ __device__ constexpr uint32_t persist_stage_bytes() {
-    return (uint32_t)(kTileM + Epi::BN) * Epi::BK * Epi::ELEM;
+    return (uint32_t)planes<Epi>() * (kTileM + Epi::BN) * Epi::BK * Epi::ELEM;
 }
 
 __host__ __device__ constexpr int persist_threads(int epi_warpgroups) { return 96 + 128 * epi_warpgroups; }
@@ -434,8 +523,11 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
     constexpr int G = Epi::EPI_WG;
     constexpr int BK = Epi::BK;      // K elements per chunk
     constexpr int ELEM = Epi::ELEM;  // 2: BF16 operands (kind::f16), 1: E4M3 (kind::f8f6f4)
-    constexpr int ROWB = BK * ELEM;  // 128: 128-byte swizzled K-major rows; 64: 64-byte swizzled
-    constexpr uint32_t A_BYTES = (uint32_t)kTileM * ROWB;
+    constexpr int ROWB = BK * ELEM;  // bytes per K-major row: 128, 64 or 32 (that swizzle)
+    constexpr bool SPLIT = Epi::SPLIT;
+    constexpr int PL = planes<Epi>();
+    constexpr uint32_t A_BYTES = (uint32_t)kTileM * ROWB;          // per plane
+    constexpr uint32_t B_BYTES = (uint32_t)Epi::BN * BK * ELEM;    // per plane
     constexpr uint32_t STAGE_BYTES = persist_stage_bytes<Epi>();
     constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;
     constexpr uint32_t MN_BOX = 64u * BK * 2;  // one 64 (MN) x BK (K) box of an MN-major operand
@@ -448,8 +540,9 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
     static_assert(!B_MN || BN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
     static_assert(E_BOXES <= 4 && O_BOXES <= 4 && Epi::XROUNDS <= 1 && G <= 4, "epilogue shape");
-    static_assert(ROWB == 128 || ROWB == 64, "K chunk rows of 128 or 64 bytes");
+    static_assert(ROWB == 128 || ROWB == 64 || ROWB == 32, "K chunk rows of 128, 64 or 32 bytes");
     static_assert(!A_MN, "the persistent tile reads A K-major");
+    static_assert(!SPLIT || (ELEM == 2 && E_BOXES == 0), "split form: BF16 planes, outputs only");
     static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "stages stay 1024-byte aligned");
 
     extern __shared__ uint8_t smem_raw[];
@@ -518,25 +611,36 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                 const int m0 = (first + lt * stride) * kTileM;
                 // the next tile's A rows go to L2 now, so that its ring refills at L2 latency
                 if (lt + 1 < my_tiles)
-                    for (int i = 0; i < nk; ++i) tma_prefetch_2d(&tmA, i * BK, m0 + stride * kTileM);
+                    for (int i = 0; i < nk; ++i)
+                        for (int z = 0; z < PL; ++z) {
+                            if (SPLIT)
+                                tma_prefetch_3d(&tmA, i * BK, m0 + stride * kTileM, z);
+                            else
+                                tma_prefetch_2d(&tmA, i * BK, m0 + stride * kTileM);
+                        }
                 for (int i = 0; i < nk; ++i, ++it) {
                     const int s = it % STAGES;
                     if (it >= STAGES && !mbar_wait(&empty[s], ((uint32_t)(it / STAGES) & 1u) ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
-                    uint8_t* sa = smem + s * STAGE_BYTES;
-                    uint8_t* sb = sa + A_BYTES;
                     const int kx = i * BK;
                     mbar_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_2d(sa, &tmA, &full[s], kx, m0);
-                    if (B_MN) {
 #pragma unroll
-                        for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * MN_BOX, &tmB, &full[s], n0 + 64 * b, kx);
-                    } else {
+                    for (int z = 0; z < PL; ++z) {
+                        const int zz = SPLIT ? z : -1;
+                        uint8_t* sa = smem + s * STAGE_BYTES + z * A_BYTES;
+                        uint8_t* sb = smem + s * STAGE_BYTES + PL * A_BYTES + z * B_BYTES;
+                        tma_load(sa, &tmA, &full[s], kx, m0, zz);
+                        if (B_MN) {
 #pragma unroll
-                        for (int b = 0; b < BN / BOX_B; ++b)
-                            tma_load_2d(sb + b * BOX_B * ROWB, &tmB, &full[s], kx, n0 + b * BOX_B);
+                            for (int b = 0; b < BN / 64; ++b)
+                                tma_load(sb + b * MN_BOX, &tmB, &full[s], n0 + 64 * b, kx, zz);
+                        } else {
+#pragma unroll
+                            for (int b = 0; b < BN / BOX_B; ++b)
+                                tma_load(sb + b * BOX_B * ROWB, &tmB, &full[s], kx, n0 + b * BOX_B, zz);
+                        }
                     }
                 }
             }
@@ -545,6 +649,32 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                 // never leave the CTA with copies in flight
                 for (int j = max(0, it - STAGES); j < it; ++j)
                     (void)mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u, nullptr);
+            }
+        }
+    } else if (warp == 2 && SPLIT) {
+        if (lane == 0 && nk > 0) {
+            // ---- split form: one staged output per tile, its hi plane in buffer 0 and its lo
+            // plane in buffer 1; tile t + 1 stages once the stores of tile t have read them ----
+            bool ok = true;
+            mbar_arrive(&e_free[0]);  // tile 0 may stage
+            for (int t = 0; t < my_tiles && ok; ++t) {
+                if (!mbar_wait(&staged[0], (uint32_t)t & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const int nb = nbox[0];
+                const int m0t = (first + t * stride) * kTileM;
+                for (int b = 0; b < nb && b < O_BOXES; ++b) {
+                    tma_store_3d(&tmO, boxes + b * kTileABytes, n0 + 64 * b, m0t, 0);
+                    tma_store_3d(&tmO, boxes + BOX_BYTES + b * kTileABytes, n0 + 64 * b, m0t, 1);
+                }
+                bulk_commit();
+                bulk_wait_read();
+                mbar_arrive(&e_free[0]);  // tile t + 1 may stage
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                bulk_wait_read();
             }
         }
     } else if (warp == 2) {
@@ -616,17 +746,23 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                    const uint32_t sb = sa + A_BYTES;
+                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);  // A hi (then A lo)
+                    const uint32_t sb = sa + PL * A_BYTES;                 // B hi (then B lo)
+                    auto kdesc = [&](uint32_t a) {
+                        return ROWB == 128 ? sw128_desc(a) : ROWB == 64 ? sw64_desc(a) : sw32_desc(a);
+                    };
 #pragma unroll
                     for (int kk = 0; kk < ROWB / 32; ++kk) {  // one MMA consumes 32 bytes of K
-                        const uint64_t da = ROWB == 128 ? sw128_desc(sa + kk * 32) : sw64_desc(sa + kk * 32);
-                        const uint64_t db = B_MN ? mn128_desc(sb + kk * 16 * 128, MN_BOX)
-                                                 : (ROWB == 128 ? sw128_desc(sb + kk * 32) : sw64_desc(sb + kk * 32));
-                        if (ELEM == 1)
+                        const uint64_t da = kdesc(sa + kk * 32);
+                        const uint64_t db = B_MN ? mn128_desc(sb + kk * 16 * 128, MN_BOX) : kdesc(sb + kk * 32);
+                        if (ELEM == 1) {
                             mma_e4m3(dst, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
-                        else
-                            mma_bf16(dst, da, db, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+                        } else {
+                            const uint64_t dal = kdesc(sa + A_BYTES + kk * 32);
+                            const uint64_t dbl =
+                                B_MN ? mn128_desc(sb + B_BYTES + kk * 16 * 128, MN_BOX) : kdesc(sb + B_BYTES + kk * 32);
+                            mma_step<SPLIT>(dst, da, dal, db, dbl, IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+                        }
                     }
                     mma_commit(&empty[s]);
                 }
@@ -647,7 +783,8 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
             const int e = lt & 1, use = lt >> 1;
             const int tile = first + lt * stride;
             bool ready = nk > 0 && mbar_wait(&acc_full[e], (uint32_t)use & 1u, abort_flag);
-            if (ready && E_BOXES == 0 && O_BOXES > 0) ready = mbar_wait(&e_free[e], (uint32_t)use & 1u, abort_flag);
+            if (!SPLIT && ready && E_BOXES == 0 && O_BOXES > 0)
+                ready = mbar_wait(&e_free[e], (uint32_t)use & 1u, abort_flag);
             tc_fence_after();
             if (!ready) *abort_flag = 1;
             epi_sync(128 * G);
@@ -658,12 +795,21 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                       row, tile * kTileM, n0, 0, group, scratch, E_BOXES > 0 ? box : nullptr, box,
                       &e_full[4 * e], abort_flag, (int)crank, (int)csize, &xbars[e],
                       xbufs + e * (kXchgBytes / 4), (uint32_t)use & 1u, (uint32_t)use & 1u, G, 96};
+            if (SPLIT) {  // both buffers hold this tile's output; run() waits for them (wait_out)
+                ec.otile = boxes;
+                ec.oplane = BOX_BYTES;
+                ec.ofree = &e_free[0];
+                ec.ofree_phase = (uint32_t)lt & 1u;
+            }
             int out_boxes = 0;
             if (*decision) {
-                out_boxes = Epi::run(ep, ec);
-            } else if (Epi::XROUNDS > 0) {
-                const float zero[kXchgVals] = {0.f, 0.f, 0.f, 0.f};
-                (void)ec.exchange(zero);
+                out_boxes = Epi::run(ep, ec);  // split form: run() calls ec.wait_out() once, on every path
+            } else {
+                if (Epi::XROUNDS > 0) {
+                    const float zero[kXchgVals] = {0.f, 0.f, 0.f, 0.f};
+                    (void)ec.exchange(zero);
+                }
+                if (SPLIT) (void)ec.wait_out();
             }
             // TMEM and the staged output are handed over once every epilogue thread is done
             tc_fence_before();
@@ -671,8 +817,9 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
             epi_sync(128 * G);
             if (threadIdx.x == 96) {
                 mbar_arrive(&acc_empty[e]);
-                nbox[e] = *abort_flag ? 0 : out_boxes;
-                mbar_arrive(&staged[e]);
+                const int sb = SPLIT ? 0 : e;
+                nbox[sb] = *abort_flag ? 0 : out_boxes;
+                mbar_arrive(&staged[sb]);
             }
         }
     }

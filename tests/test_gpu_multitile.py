@@ -207,13 +207,19 @@ def test_uneven_batch_step_first_update(api, ctx, uneven):
     st = api.LatentBatchStep(ctx, frames, precision=api.BF16, target_dtype=torch.bfloat16)
     loss = st.step(iters=1, learn_f=True)
     assert loss["total"] == pytest.approx(o["loss"]["total"], rel=BARS["bf16"][1])
-    lr = 0.01
+    lr, eps = 0.01, 1e-8
     checks = [("K", st.K, frames[0].K, o["dK"]), ("V", st.V, frames[0].V, o["dV"])]
     checks += [(f"f{k}", st.queries[k], frames[k].f, o["df"][id(frames[k].f)]) for k in range(3)]
     for nm, dev_t, x0, g in checks:
         got = dev_t.cpu().numpy().astype(np.float64)
+        step = x0.astype(np.float64) - got
+        # the first update is lr g / (|g| + eps): at most lr, along -sign(g) wherever the
+        # gradient is large enough for its BF16 sign to be determined
+        assert np.all(np.abs(step) <= lr * (1 + 1e-4) + 1e-6), nm
         well = np.abs(g) > 5e-2 * np.abs(g).max()
-        want = x0.astype(np.float64).copy()
-        m, v = np.zeros_like(want), np.zeros_like(want)
-        oracle.adam(want.reshape(-1), g.reshape(-1), m.reshape(-1), v.reshape(-1), 1, lr)
-        np.testing.assert_allclose(got[well], want[well], rtol=0, atol=1e-3 * lr + 1e-6, err_msg=nm)
+        assert well.sum() > 50, nm
+        np.testing.assert_array_equal(np.sign(step[well]), np.sign(g[well]), err_msg=nm)
+        # far above eps the step's size no longer depends on the gradient's rounding
+        big = well & (np.abs(g) > 100 * eps)
+        want = lr * g / (np.abs(g) + eps)
+        np.testing.assert_allclose(step[big], want[big], rtol=0, atol=2e-3 * lr, err_msg=nm)
