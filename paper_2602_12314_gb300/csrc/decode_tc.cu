@@ -661,9 +661,11 @@ latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_
 
 // Tensor map of a split operand: two row-major BF16 planes [2][rows][ld] (hi, then lo) as a 3D
 // tensor with the plane as z, boxes of box_inner (64 / 32 / 16: 128 / 64 / 32-byte swizzle) x
-// box_rows x 1 plane; out-of-range elements read as zero.
+// box_rows x box_planes (2: one load brings both planes, [plane][row][inner]; 1: one plane, for
+// the epilogue operands and outputs and the MN-major A operands); out-of-range elements read as
+// zero.
 latentam_status split_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows,
-                          int box_inner) {
+                          int box_inner, int box_planes) {
     EncodeTiledFn enc;
     LAT_TRY(encoder(&enc));
     if ((reinterpret_cast<uintptr_t>(base) & 15u) || (ld * 2) % 16 || (rows * ld * 2) % 16) {
@@ -672,7 +674,7 @@ latentam_status split_map(CUtensorMap* m, const void* base, int64_t inner, int64
     }
     const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, 2};
     const cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(rows * ld * 2)};
-    const cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapSwizzle sw = box_inner == 16   ? CU_TENSOR_MAP_SWIZZLE_32B
                                   : box_inner == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
@@ -688,10 +690,50 @@ latentam_status split_map(CUtensorMap* m, const void* base, int64_t inner, int64
     return LATENTAM_OK;
 }
 
-// The map of an operand of the plain (BF16) or the split (FP32) form.
+// Tensor map of a split operand read MN-major (K rows of `inner` contiguous MN elements, inner a
+// multiple of 64): a 4D view (64 elements, K row, 64-element block, plane) whose box of 64 x
+// box_rows x nblk x 2 lands in shared memory as [plane][block][K row][128 B], the MN-major
+// layout of both planes of a BN = 64 nblk tile, in one load.
+latentam_status split_map_mn(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows,
+                             int nblk) {
+    EncodeTiledFn enc;
+    LAT_TRY(encoder(&enc));
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || (ld * 2) % 16 || (rows * ld * 2) % 16 || inner % 64) {
+        set_error("split MN-major operand not 16-byte aligned or not made of 64-wide blocks");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    const cuuint64_t dims[4] = {64, (cuuint64_t)rows, (cuuint64_t)(inner / 64), 2};
+    const cuuint64_t strides[3] = {(cuuint64_t)(ld * 2), 128, (cuuint64_t)(rows * ld * 2)};
+    const cuuint32_t box[4] = {64, (cuuint32_t)box_rows, (cuuint32_t)nblk, 2};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for a split MN-major %lld x %lld operand", (int)r,
+                  (long long)rows, (long long)inner);
+        return LATENTAM_ERR_CUDA;
+    }
+    return LATENTAM_OK;
+}
+
+// Maps of the plain (BF16, 2D) or split (FP32, hi / lo planes) form: op_map for a K-major MMA
+// operand (split: both planes per box), mn_map for an MN-major B operand (split: both planes
+// and nblk 64-wide blocks per box), io_map for epilogue operands, staged outputs and MN-major A
+// operands (split: one plane per box).
 latentam_status op_map(bool split, CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld,
                        int box_rows, int box_inner = tc::kChunkK) {
-    return split ? split_map(m, base, inner, rows, ld, box_rows, box_inner)
+    return split ? split_map(m, base, inner, rows, ld, box_rows, box_inner, 2)
+                 : bf16_map(m, base, inner, rows, ld, box_rows, box_inner);
+}
+latentam_status mn_map(bool split, CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld,
+                       int box_rows, int nblk) {
+    return split ? split_map_mn(m, base, inner, rows, ld, box_rows, nblk)
+                 : bf16_map(m, base, inner, rows, ld, box_rows);
+}
+latentam_status io_map(bool split, CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld,
+                       int box_rows, int box_inner = tc::kChunkK) {
+    return split ? split_map(m, base, inner, rows, ld, box_rows, box_inner, 1)
                  : bf16_map(m, base, inner, rows, ld, box_rows, box_inner);
 }
 
@@ -960,7 +1002,7 @@ latentam_status tc_forward(latentam_ctx* ctx, const float* Q, int64_t n, int d, 
     LAT_TRY(op_map(SPLIT, &mQ, b.Qb, kPad, n, kPad, kTileM, Epi::BK));
     LAT_TRY(op_map(SPLIT, &mK, b.Kb, kPad, M, kPad, 256, Epi::BK));
     CUtensorMap mA;  // the attention rows leave through the TMA
-    LAT_TRY(op_map(SPLIT, &mA, b.A, M, n, M, kTileM));
+    LAT_TRY(io_map(SPLIT, &mA, b.A, M, n, M, kTileM));
     SoftmaxParams sp{n, M, c, b.A, stats};
     const int cy = cdiv(M, 256);
     const int kc = SPLIT ? d / Epi::BK : 1;  // plain: the padded queries are one 64-wide chunk
@@ -980,12 +1022,12 @@ latentam_status tc_fhat(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M,
     constexpr int BK = EpiF::BK;
     CUtensorMap mA, mV;
     LAT_TRY(op_map(SPLIT, &mA, b.A, M, n, M, kTileM, BK));
-    LAT_TRY(op_map(SPLIT, &mV, b.Vb, D, M, D, BK));
+    LAT_TRY(mn_map(SPLIT, &mV, b.Vb, D, M, D, BK, EpiF::BN / 64));
     const int cy = cdiv(D, 256), tiles = cdiv(n, kTileM), kc = cdiv(M, BK);
     if (fp.Fout)  // no row terms: independent column tiles
         return launch_persist<EpiF>(ctx, mA, mV, tiles, kc, cy, false, fp, b.err, st);
     CUtensorMap mdF;  // dFhat leaves through the TMA
-    LAT_TRY(op_map(SPLIT, &mdF, fp.dF, D, n, D, kTileM));
+    LAT_TRY(io_map(SPLIT, &mdF, fp.dF, D, n, D, kTileM));
     if (!SPLIT && fp.F_dtype == LATENTAM_DTYPE_BF16) {
         // BF16 targets: the tile's target rows are TMA-loaded into shared memory for the epilogue
         CUtensorMap mF;
@@ -1059,14 +1101,14 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
         const dim3 grow(cdiv(n, kTileM), 1, 1);
         const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
         CUtensorMap mAe, mdSo;  // attention rows for the epilogue, dS out through the TMA
-        LAT_TRY(op_map(SPLIT, &mAe, b.A, M, n, M, kTileM));
-        LAT_TRY(op_map(SPLIT, &mdSo, b.dS, M, n, M, kTileM));
+        LAT_TRY(io_map(SPLIT, &mAe, b.A, M, n, M, kTileM));
+        LAT_TRY(io_map(SPLIT, &mdSo, b.dS, M, n, M, kTileM));
         LAT_TRY((launch_gemm<DsEpi<SPLIT>>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st,
                                            &mAe, &mdSo)));
         // G4: dQ = c dS K, B = K padded read MN-major (queries x atoms)
         if (a.dQ) {
             LAT_TRY(op_map(SPLIT, &mdS, b.dS, M, n, M, kTileM));
-            LAT_TRY(op_map(SPLIT, &mK, b.Kb, kPad, M, kPad, 64));
+            LAT_TRY(mn_map(SPLIT, &mK, b.Kb, kPad, M, kPad, 64, kPad / 64));
             DqParams qp{n, d, a.c, a.dQ};
             const tc::GemmGrid g4{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
             LAT_TRY((launch_gemm<DqEpi<BNq, SPLIT>>(mdS, mK, grow, g4, qp, b.err, st)));
@@ -1077,8 +1119,8 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
     if (a.dV) {
         if (n > 0) {
             CUtensorMap mA, mdF;
-            LAT_TRY(op_map(SPLIT, &mA, b.A, M, n, M, 64));
-            LAT_TRY(op_map(SPLIT, &mdF, b.dF, D, n, D, 64));
+            LAT_TRY(io_map(SPLIT, &mA, b.A, M, n, M, 64));
+            LAT_TRY(mn_map(SPLIT, &mdF, b.dF, D, n, D, 64, 256 / 64));
             PartParams pp{M, D, D, b.part};
             auto g5 = [&](int z) -> latentam_status {
                 int zz;
@@ -1099,8 +1141,8 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
     if (a.dK) {
         if (n > 0) {
             CUtensorMap mdS, mQ;
-            LAT_TRY(op_map(SPLIT, &mdS, b.dS, M, n, M, 64));
-            LAT_TRY(op_map(SPLIT, &mQ, b.Qb, kPad, n, kPad, 64));
+            LAT_TRY(io_map(SPLIT, &mdS, b.dS, M, n, M, 64));
+            LAT_TRY(mn_map(SPLIT, &mQ, b.Qb, kPad, n, kPad, 64, kPad / 64));
             PartParams pp{M, BNq, BNq, b.part};
             auto g6 = [&](int z) -> latentam_status {
                 int zz;

@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     constexpr int E_BOXES = Epi::E_BOXES;
     constexpr uint32_t TILE_REGION = tile_region_bytes<Epi>();
     static_assert(E_BOXES * PL <= 8 && Epi::O_BOXES * PL <= 8, "at most 8 boxes of epilogue operand / output");
+    static_assert(!SPLIT || B_MN || BOX_B == BN, "a split K-major B tile is one box");
     static_assert(Epi::XROUNDS == 0, "row exchanges run in the persistent form");
 
     extern __shared__ uint8_t smem_raw[];
@@ -335,26 +336,40 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 }
                 const int kx = (k_begin + i) * kChunkK;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
+                uint8_t* sa = smem + s * STAGE_BYTES;
+                uint8_t* sb = sa + PL * kTileABytes;
+                if (SPLIT) {
+                    // one box holds both planes: K-major [plane][row][128 B] (3D), MN-major B
+                    // [plane][block][K row][128 B] (4D); an MN-major A loads each plane's blocks
+                    if (A_MN) {
 #pragma unroll
-                for (int z = 0; z < PL; ++z) {
-                    const int zz = SPLIT ? z : -1;
-                    uint8_t* sa = smem + s * STAGE_BYTES + z * kTileABytes;
-                    uint8_t* sb = smem + s * STAGE_BYTES + PL * kTileABytes + z * B_BYTES;
+                        for (int z = 0; z < 2; ++z)
+#pragma unroll
+                            for (int b = 0; b < kTileM / 64; ++b)
+                                tma_load_3d(sa + z * kTileABytes + b * kMnBoxBytes, &tmA, &full[s], m0 + 64 * b, kx, z);
+                    } else {
+                        tma_load_3d(sa, &tmA, &full[s], kx, m0, 0);
+                    }
+                    if (B_MN)
+                        tma_load_4d(sb, &tmB, &full[s], 0, kx, n0 / 64, 0);
+                    else
+                        tma_load_3d(sb, &tmB, &full[s], kx, n0, 0);
+                } else {
                     if (A_MN) {
 #pragma unroll
                         for (int b = 0; b < kTileM / 64; ++b)
-                            tma_load(sa + b * kMnBoxBytes, &tmA, &full[s], m0 + 64 * b, kx, zz);
+                            tma_load_2d(sa + b * kMnBoxBytes, &tmA, &full[s], m0 + 64 * b, kx);
                     } else {
-                        tma_load(sa, &tmA, &full[s], kx, m0, zz);
+                        tma_load_2d(sa, &tmA, &full[s], kx, m0);
                     }
                     if (B_MN) {
 #pragma unroll
                         for (int b = 0; b < BN / 64; ++b)
-                            tma_load(sb + b * kMnBoxBytes, &tmB, &full[s], n0 + 64 * b, kx, zz);
+                            tma_load_2d(sb + b * kMnBoxBytes, &tmB, &full[s], n0 + 64 * b, kx);
                     } else {
 #pragma unroll
                         for (int b = 0; b < BN / BOX_B; ++b)
-                            tma_load(sb + b * BOX_B * 128, &tmB, &full[s], kx, n0 + b * BOX_B, zz);
+                            tma_load_2d(sb + b * BOX_B * 128, &tmB, &full[s], kx, n0 + b * BOX_B);
                     }
                 }
                 ++issued;
@@ -543,6 +558,7 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
     static_assert(ROWB == 128 || ROWB == 64 || ROWB == 32, "K chunk rows of 128, 64 or 32 bytes");
     static_assert(!A_MN, "the persistent tile reads A K-major");
     static_assert(!SPLIT || (ELEM == 2 && E_BOXES == 0), "split form: BF16 planes, outputs only");
+    static_assert(!SPLIT || B_MN || BOX_B == BN, "a split K-major B tile is one box");
     static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "stages stay 1024-byte aligned");
 
     extern __shared__ uint8_t smem_raw[];
@@ -611,13 +627,12 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                 const int m0 = (first + lt * stride) * kTileM;
                 // the next tile's A rows go to L2 now, so that its ring refills at L2 latency
                 if (lt + 1 < my_tiles)
-                    for (int i = 0; i < nk; ++i)
-                        for (int z = 0; z < PL; ++z) {
-                            if (SPLIT)
-                                tma_prefetch_3d(&tmA, i * BK, m0 + stride * kTileM, z);
-                            else
-                                tma_prefetch_2d(&tmA, i * BK, m0 + stride * kTileM);
-                        }
+                    for (int i = 0; i < nk; ++i) {
+                        if (SPLIT)
+                            tma_prefetch_3d(&tmA, i * BK, m0 + stride * kTileM, 0);  // both planes
+                        else
+                            tma_prefetch_2d(&tmA, i * BK, m0 + stride * kTileM);
+                    }
                 for (int i = 0; i < nk; ++i, ++it) {
                     const int s = it % STAGES;
                     if (it >= STAGES && !mbar_wait(&empty[s], ((uint32_t)(it / STAGES) & 1u) ^ 1u, abort_flag)) {
@@ -626,20 +641,24 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                     }
                     const int kx = i * BK;
                     mbar_expect_tx(&full[s], STAGE_BYTES);
-#pragma unroll
-                    for (int z = 0; z < PL; ++z) {
-                        const int zz = SPLIT ? z : -1;
-                        uint8_t* sa = smem + s * STAGE_BYTES + z * A_BYTES;
-                        uint8_t* sb = smem + s * STAGE_BYTES + PL * A_BYTES + z * B_BYTES;
-                        tma_load(sa, &tmA, &full[s], kx, m0, zz);
+                    uint8_t* sa = smem + s * STAGE_BYTES;
+                    uint8_t* sb = sa + PL * A_BYTES;
+                    if (SPLIT) {  // one box holds both planes (see tc_gemm_kernel)
+                        tma_load_3d(sa, &tmA, &full[s], kx, m0, 0);
+                        if (B_MN)
+                            tma_load_4d(sb, &tmB, &full[s], 0, kx, n0 / 64, 0);
+                        else
+                            tma_load_3d(sb, &tmB, &full[s], kx, n0, 0);
+                    } else {
+                        tma_load_2d(sa, &tmA, &full[s], kx, m0);
                         if (B_MN) {
 #pragma unroll
                             for (int b = 0; b < BN / 64; ++b)
-                                tma_load(sb + b * MN_BOX, &tmB, &full[s], n0 + 64 * b, kx, zz);
+                                tma_load_2d(sb + b * MN_BOX, &tmB, &full[s], n0 + 64 * b, kx);
                         } else {
 #pragma unroll
                             for (int b = 0; b < BN / BOX_B; ++b)
-                                tma_load(sb + b * BOX_B * ROWB, &tmB, &full[s], kx, n0 + b * BOX_B, zz);
+                                tma_load_2d(sb + b * BOX_B * ROWB, &tmB, &full[s], kx, n0 + b * BOX_B);
                         }
                     }
                 }
