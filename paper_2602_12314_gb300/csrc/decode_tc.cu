@@ -255,7 +255,7 @@ struct SoftmaxParams {
 template <bool SPLIT_ = false>
 struct SoftmaxEpi {
     // plain: one K chunk (the padded queries) per tile
-    static constexpr bool SPLIT = SPLIT_;
+    static constexpr bool SPLIT = SPLIT_, INPLACE = false;
     static constexpr int BN = 256, BK = SPLIT_ ? 16 : 64, ELEM = 2, STAGES = SPLIT_ ? 3 : 1, BOX_B = 256;
     static constexpr int EPI_WG = 4, E_BOXES = 0, O_BOXES = 4;
     static constexpr int XROUNDS = 1;
@@ -336,17 +336,20 @@ struct FhatParams {
 // (FP32 targets) each thread reads its own row from global memory, one chunk ahead.
 // Q8: the contraction runs on E4M3 operands (attention rows scaled per pixel, values per
 // feature, both K-major) and the accumulator is rescaled before any use.
-// SPLIT_ (the FP32 form, FP32 or BF16 targets read per thread): A and V as hi / lo BF16 planes,
-// three MMAs per product, dFhat staged as hi / lo planes; 32-byte K chunks so that three ring
-// stages fit beside the output's two planes.
+// SPLIT_ (the FP32 form): A and V as hi / lo BF16 planes, three MMAs per product, dFhat out as
+// hi / lo planes, 32-byte K chunks so that three ring stages fit beside the staged tile.  With
+// ETILE (FP32 targets) the tile's target rows come by TMA as eight 32-column FP32 chunks filling
+// both box buffers and dFhat is written over them (INPLACE); without, the targets (FP32 or BF16)
+// are read per thread and dFhat is staged as two planes across the buffers.
 template <bool ETILE, bool Q8 = false, bool SPLIT_ = false>
 struct FhatEpi {
-    static_assert(!SPLIT_ || (!ETILE && !Q8), "the split form reads FP32 targets per thread");
-    static constexpr bool SPLIT = SPLIT_;
+    static_assert(!SPLIT_ || !Q8, "the split form has no E4M3 operands");
+    static constexpr bool SPLIT = SPLIT_, INPLACE = SPLIT_ && ETILE;
     // persistent, 64-byte K chunks (three ring stages fit beside two epilogue buffers)
     static constexpr int ELEM = Q8 ? 1 : 2, BK = SPLIT_ ? 16 : 64 / ELEM;
     static constexpr int BN = 256, STAGES = 3, BOX_B = 256, EPI_WG = ETILE ? 4 : 2, XROUNDS = 1;
-    static constexpr int E_BOXES = ETILE ? BN / 64 : 0, O_BOXES = BN / 64;  // dFhat staged over the target
+    // dFhat staged over the target
+    static constexpr int E_BOXES = INPLACE ? 8 : ETILE ? BN / 64 : 0, O_BOXES = BN / 64;
     // B = V (atoms x features, features contiguous: MN-major) or, for E4M3, V^T (K-major)
     static constexpr bool A_MN = false, B_MN = !Q8;
     using Params = FhatParams;
@@ -379,7 +382,10 @@ struct FhatEpi {
         float h[32], f[32];
         if constexpr (ETILE) {
             for (int c0 = 32 * ec.g; c0 < ncols; c0 += step) {
-                ec.row32(c0, f);
+                if (INPLACE)
+                    ec.row32f(c0, f);
+                else
+                    ec.row32(c0, f);
                 fhat32(p, ec, c0, isp, h);
                 body(c0, h, f);
             }
@@ -474,13 +480,19 @@ struct FhatEpi {
                 atomicAdd(&p.acc[1], (double)le);
             }
         }
-        // dFhat overwrites the target chunk it was formed from (same thread, same bytes)
+        // dFhat overwrites the target chunk it was formed from (plain: same thread, same bytes;
+        // in place: the chunk's two planes replace its FP32 rows once its warpgroup read them)
         ec.wait_out();
         sweep(p, ec, frow, ncols, isp, [&](int c0, const float(&h)[32], const float(&f)[32]) {
             float v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = a * h[i] + b * f[i];
-            ec.put32(c0, v);
+            if (INPLACE) {
+                ec.group_sync();
+                ec.put32s(c0, v);
+            } else {
+                ec.put32(c0, v);
+            }
         });
         return (ncols + 63) / 64;
     }
@@ -653,6 +665,30 @@ latentam_status bf16_map(CUtensorMap* m, const void* base, int64_t inner, int64_
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld operand", (int)r, (long long)rows,
+                  (long long)inner);
+        return LATENTAM_ERR_CUDA;
+    }
+    return LATENTAM_OK;
+}
+
+// Tensor map of a row-major FP32 matrix read in boxes of 32 columns (128 bytes, 128-byte
+// swizzle) x box_rows.
+latentam_status f32_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int box_rows) {
+    EncodeTiledFn enc;
+    LAT_TRY(encoder(&enc));
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || (inner * 4) % 16) {
+        set_error("FP32 tensor-core epilogue operand not 16-byte aligned");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(inner * 4)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld FP32 operand", (int)r, (long long)rows,
                   (long long)inner);
         return LATENTAM_ERR_CUDA;
     }
@@ -1027,6 +1063,13 @@ latentam_status tc_fhat(latentam_ctx* ctx, const TcBuffers& b, int64_t n, int M,
     if (fp.Fout)  // no row terms: independent column tiles
         return launch_persist<EpiF>(ctx, mA, mV, tiles, kc, cy, false, fp, b.err, st);
     CUtensorMap mdF;  // dFhat leaves through the TMA
+    if (SPLIT && fp.F_dtype == LATENTAM_DTYPE_F32) {
+        // FP32 targets by TMA, 32 columns at a time; dFhat written over them as 32-column planes
+        CUtensorMap mF;
+        LAT_TRY(f32_map(&mF, fp.F, D, n, kTileM));
+        LAT_TRY(io_map(true, &mdF, fp.dF, D, n, D, kTileM, 32));
+        return launch_persist<FhatEpi<true, false, true>>(ctx, mA, mV, tiles, kc, cy, true, fp, b.err, st, &mF, &mdF);
+    }
     LAT_TRY(io_map(SPLIT, &mdF, fp.dF, D, n, D, kTileM));
     if (!SPLIT && fp.F_dtype == LATENTAM_DTYPE_BF16) {
         // BF16 targets: the tile's target rows are TMA-loaded into shared memory for the epilogue

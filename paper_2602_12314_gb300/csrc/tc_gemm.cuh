@@ -145,6 +145,42 @@ struct EpiCtx {
     uint64_t* ofree = nullptr;  // split persistent form: completes when the staging buffers are free
     uint32_t ofree_phase = 0;
 
+    // In-place split form (Epi::INPLACE): the tile's FP32 epilogue operand sits in the box
+    // buffers as 32-column chunks (128 rows x 128 B, 128-byte swizzle, chunk c at c x 16 KB), and
+    // the output of chunk c replaces it as two 32-column BF16 boxes (hi at the chunk's first
+    // 8 KB, lo at its second, 64-byte swizzle).
+    // 32 FP32 values of this thread's row from chunk c0 / 32 of the epilogue operand.
+    __device__ __forceinline__ void row32f(int c0, float (&v)[32]) const {
+        const uint8_t* base = etile + (c0 >> 5) * 16384 + row * 128;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 u = *reinterpret_cast<const float4*>(base + ((q ^ (row & 7)) << 4));
+            v[4 * q] = u.x;
+            v[4 * q + 1] = u.y;
+            v[4 * q + 2] = u.z;
+            v[4 * q + 3] = u.w;
+        }
+    }
+    // The hi and lo terms of 32 values of this thread's row into chunk c0 / 32 (every thread that
+    // reads the chunk must have read it first: the caller synchronises its warpgroup).
+    __device__ __forceinline__ void put32s(int c0, const float (&v)[32]) const {
+        uint8_t* base = otile + (c0 >> 5) * 16384 + row * 64;
+        const int sw = (row >> 1) & 3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pack_split_bf16x2(v[8 * q + 2 * k], v[8 * q + 2 * k + 1], h[k], l[k]);
+            const int off = (q ^ sw) << 4;
+            *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(base + 8192 + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    }
+    // Barrier of this thread's epilogue warpgroup only (named barriers 2 + g).
+    __device__ __forceinline__ void group_sync() const {
+        asm volatile("bar.sync %0, 128;" ::"r"(2 + g) : "memory");
+    }
+
     // Split persistent form: wait until the previous tile's staged output has been read by its
     // TMA stores (call before the first put32; a no-op elsewhere).  Bounded.
     __device__ __forceinline__ bool wait_out() const {
@@ -508,7 +544,9 @@ struct PersistGrid {
 
 template <class Epi>
 __host__ __device__ constexpr uint32_t persist_box_bytes() {  // one box buffer
-    return (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * kTileABytes;
+    // in place (split): the eight 16 KB operand chunks of one tile fill both buffers
+    return Epi::INPLACE ? 4 * kTileABytes
+                        : (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * kTileABytes;
 }
 
 // One ring stage: A (128 x BK) and B (BN x BK) elements of Epi::ELEM bytes (2: BF16, 1: E4M3),
@@ -554,10 +592,12 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
     static_assert(ELEM == 2 || (ELEM == 1 && !B_MN), "E4M3 operands are read K-major");
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
     static_assert(!B_MN || BN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
-    static_assert(E_BOXES <= 4 && O_BOXES <= 4 && Epi::XROUNDS <= 1 && G <= 4, "epilogue shape");
+    constexpr bool INPLACE = Epi::INPLACE;  // split: FP32 operand chunks in, output over them
+    static_assert((E_BOXES <= 4 || INPLACE) && O_BOXES <= 4 && Epi::XROUNDS <= 1 && G <= 4, "epilogue shape");
     static_assert(ROWB == 128 || ROWB == 64 || ROWB == 32, "K chunk rows of 128, 64 or 32 bytes");
     static_assert(!A_MN, "the persistent tile reads A K-major");
-    static_assert(!SPLIT || (ELEM == 2 && E_BOXES == 0), "split form: BF16 planes, outputs only");
+    static_assert(!SPLIT || (ELEM == 2 && (E_BOXES == 0 || INPLACE)), "split form: BF16 planes");
+    static_assert(!INPLACE || (SPLIT && E_BOXES == 8 && 2 * BOX_BYTES == 8 * 16384), "in-place chunks fill both buffers");
     static_assert(!SPLIT || B_MN || BOX_B == BN, "a split K-major B tile is one box");
     static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "stages stay 1024-byte aligned");
 
@@ -598,7 +638,7 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
         for (int e = 0; e < 2; ++e) {
             mbar_init(&acc_full[e], 1);
             mbar_init(&acc_empty[e], 1);
-            for (int b = 0; b < E_BOXES; ++b) mbar_init(&e_full[4 * e + b], 1);
+            for (int b = 0; b < (INPLACE ? 4 : E_BOXES); ++b) mbar_init(&e_full[4 * e + b], 1);
             mbar_init(&e_free[e], 1);
             mbar_init(&staged[e], 1);
             if (csize > 1) mbar_init(&xbars[e], 1);  // this CTA's expect-tx arrival
@@ -668,6 +708,44 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                 // never leave the CTA with copies in flight
                 for (int j = max(0, it - STAGES); j < it; ++j)
                     (void)mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u, nullptr);
+            }
+        }
+    } else if (warp == 2 && INPLACE) {
+        if (lane == 0 && nk > 0) {
+            // ---- in-place split form: the FP32 operand chunks of tile t are loaded once the
+            // stores of tile t - 1 (written over its chunks) have read them ----
+            bool ok = true;
+            int loaded = -1;
+            auto store_tile = [&](int t) -> bool {
+                if (!mbar_wait(&staged[0], (uint32_t)t & 1u, abort_flag)) return false;
+                const int nb = nbox[0];
+                const int m0t = (first + t * stride) * kTileM;
+                for (int c = 0; c < 2 * nb && c < 8; ++c) {
+                    tma_store_3d(&tmO, boxes + c * 16384, n0 + 32 * c, m0t, 0);
+                    tma_store_3d(&tmO, boxes + c * 16384 + 8192, n0 + 32 * c, m0t, 1);
+                }
+                bulk_commit();
+                bulk_wait_read();
+                return true;
+            };
+            for (int t = 0; t < my_tiles && ok; ++t) {
+                if (t >= 1 && !store_tile(t - 1)) {
+                    ok = false;
+                    break;
+                }
+                const int m0t = (first + t * stride) * kTileM;
+                for (int c = 0; c < 8; ++c) {
+                    mbar_expect_tx(&e_full[c], 16384);
+                    tma_load_2d(boxes + c * 16384, &tmE, &e_full[c], n0 + 32 * c, m0t);
+                }
+                loaded = t;
+            }
+            if (ok && my_tiles > 0) ok = store_tile(my_tiles - 1);
+            if (!ok) {
+                *abort_flag = 1;
+                if (loaded >= 0)  // never leave the CTA with copies in flight
+                    for (int c = 0; c < 8; ++c) (void)mbar_wait(&e_full[c], (uint32_t)loaded & 1u, nullptr);
+                bulk_wait_read();
             }
         }
     } else if (warp == 2 && SPLIT) {
@@ -814,7 +892,12 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                       row, tile * kTileM, n0, 0, group, scratch, E_BOXES > 0 ? box : nullptr, box,
                       &e_full[4 * e], abort_flag, (int)crank, (int)csize, &xbars[e],
                       xbufs + e * (kXchgBytes / 4), (uint32_t)use & 1u, (uint32_t)use & 1u, G, 96};
-            if (SPLIT) {  // both buffers hold this tile's output; run() waits for them (wait_out)
+            if (INPLACE) {  // the operand chunks of this tile, the output written over them
+                ec.etile = boxes;
+                ec.otile = boxes;
+                ec.ebar = e_full;
+                ec.ephase = (uint32_t)lt & 1u;
+            } else if (SPLIT) {  // both buffers hold this tile's output; run() waits for them (wait_out)
                 ec.otile = boxes;
                 ec.oplane = BOX_BYTES;
                 ec.ofree = &e_free[0];
@@ -828,7 +911,7 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                     const float zero[kXchgVals] = {0.f, 0.f, 0.f, 0.f};
                     (void)ec.exchange(zero);
                 }
-                if (SPLIT) (void)ec.wait_out();
+                if (SPLIT && !INPLACE) (void)ec.wait_out();
             }
             // TMEM and the staged output are handed over once every epilogue thread is done
             tc_fence_before();
