@@ -136,8 +136,12 @@ def test_singleton_masks_reproduce_the_per_pixel_step(api, ctx):
     la = [a.step(iters=2)["total"] for _ in range(2)]
     lb = [b.step(iters=2)["total"] for _ in range(2)]
     np.testing.assert_allclose(lb, la, rtol=1e-6)
+    # the two paths reduce over pixels in different orders (different row counts and splits);
+    # Adam's per-coordinate normalisation turns those last-bit gradient differences into steps
+    # that differ by up to lr x (relative difference) where a gradient is near zero, so the
+    # parameters after four updates are compared to 1e-4 lr
     for k in ("f", "K", "V"):
-        np.testing.assert_allclose(getattr(b, k).cpu().numpy(), getattr(a, k).cpu().numpy(), rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(getattr(b, k).cpu().numpy(), getattr(a, k).cpu().numpy(), rtol=1e-5, atol=1e-6)
 
 
 def test_step_bf16_and_stage2(api, ctx):
