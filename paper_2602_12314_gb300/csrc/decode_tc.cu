@@ -255,8 +255,7 @@ struct SoftmaxParams {
 template <bool SPLIT_ = false>
 struct SoftmaxEpi {
     // plain: one K chunk (the padded queries) per tile
-    static constexpr bool SPLIT = SPLIT_;
-    static constexpr int INPLACE = 0;
+    static constexpr bool SPLIT = SPLIT_, INPLACE = false;
     static constexpr int BN = 256, BK = SPLIT_ ? 16 : 64, ELEM = 2, STAGES = SPLIT_ ? 3 : 1, BOX_B = 256;
     static constexpr int EPI_WG = 4, E_BOXES = 0, O_BOXES = 4;
     static constexpr int XROUNDS = 1;
@@ -345,8 +344,7 @@ struct FhatParams {
 template <bool ETILE, bool Q8 = false, bool SPLIT_ = false>
 struct FhatEpi {
     static_assert(!SPLIT_ || !Q8, "the split form has no E4M3 operands");
-    static constexpr bool SPLIT = SPLIT_;
-    static constexpr int INPLACE = SPLIT_ && ETILE ? 1 : 0;
+    static constexpr bool SPLIT = SPLIT_, INPLACE = SPLIT_ && ETILE;
     // persistent, 64-byte K chunks (three ring stages fit beside two epilogue buffers)
     static constexpr int ELEM = Q8 ? 1 : 2, BK = SPLIT_ ? 16 : 64 / ELEM;
     static constexpr int BN = 256, STAGES = 3, BOX_B = 256, EPI_WG = ETILE ? 4 : 2, XROUNDS = 1;
@@ -536,21 +534,6 @@ struct DsEpi {
         }
         return (ncols + 63) / 64;
     }
-};
-
-// G3 in the split form, persistent: one CTA per SM walks 128-row tiles with two TMEM
-// accumulators (the MMAs of the next tile run during this tile's epilogue); the attention rows'
-// hi / lo planes arrive by TMA in the two box buffers and dS's planes are written over them,
-// each thread over its own row.
-struct DsSplitEpi {
-    static constexpr bool SPLIT = true;
-    static constexpr int INPLACE = 2;
-    static constexpr int BN = 256, BK = 16, ELEM = 2, STAGES = 3, BOX_B = 256, EPI_WG = DsEpi<true>::EPI_WG;
-    static constexpr int XROUNDS = 0;
-    static constexpr int E_BOXES = BN / 64, O_BOXES = BN / 64;
-    static constexpr bool A_MN = false, B_MN = false;
-    using Params = DsParams;
-    static __device__ int run(const Params& p, const tc::EpiCtx& ec) { return DsEpi<true>::run(p, ec); }
 };
 
 // G4: dQ = c dS K (the first d of the 64 padded query columns).
@@ -1163,17 +1146,8 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
         CUtensorMap mAe, mdSo;  // attention rows for the epilogue, dS out through the TMA
         LAT_TRY(io_map(SPLIT, &mAe, b.A, M, n, M, kTileM));
         LAT_TRY(io_map(SPLIT, &mdSo, b.dS, M, n, M, kTileM));
-        if (SPLIT) {
-            // persistent, 16-wide K chunks (32-byte swizzle) beside the staged attention rows
-            CUtensorMap mdF3, mV3;
-            LAT_TRY(op_map(true, &mdF3, b.dF, D, n, D, kTileM, DsSplitEpi::BK));
-            LAT_TRY(op_map(true, &mV3, b.Vb, D, M, D, 256, DsSplitEpi::BK));
-            LAT_TRY(launch_persist<DsSplitEpi>(ctx, mdF3, mV3, cdiv(n, kTileM), cdiv(D, DsSplitEpi::BK),
-                                               cdiv(M, 256), false, dp, b.err, st, &mAe, &mdSo));
-        } else {
-            LAT_TRY((launch_gemm<DsEpi<SPLIT>>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st,
-                                               &mAe, &mdSo)));
-        }
+        LAT_TRY((launch_gemm<DsEpi<SPLIT>>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st,
+                                           &mAe, &mdSo)));
         // G4: dQ = c dS K, B = K padded read MN-major (queries x atoms)
         if (a.dQ) {
             LAT_TRY(op_map(SPLIT, &mdS, b.dS, M, n, M, kTileM));

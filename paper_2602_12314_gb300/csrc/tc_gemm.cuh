@@ -592,17 +592,12 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
     static_assert(ELEM == 2 || (ELEM == 1 && !B_MN), "E4M3 operands are read K-major");
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
     static_assert(!B_MN || BN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
-    // split, in place: 1 = eight 32-column FP32 operand chunks in, the output's two planes
-    // written over each chunk; 2 = the operand's hi / lo planes in (buffer 0 / 1), the output's
-    // planes over them, row by row
-    constexpr int INPLACE = Epi::INPLACE;
-    static_assert((E_BOXES <= 4 || INPLACE == 1) && O_BOXES <= 4 && Epi::XROUNDS <= 1 && G <= 4, "epilogue shape");
+    constexpr bool INPLACE = Epi::INPLACE;  // split: FP32 operand chunks in, output over them
+    static_assert((E_BOXES <= 4 || INPLACE) && O_BOXES <= 4 && Epi::XROUNDS <= 1 && G <= 4, "epilogue shape");
     static_assert(ROWB == 128 || ROWB == 64 || ROWB == 32, "K chunk rows of 128, 64 or 32 bytes");
     static_assert(!A_MN, "the persistent tile reads A K-major");
     static_assert(!SPLIT || (ELEM == 2 && (E_BOXES == 0 || INPLACE)), "split form: BF16 planes");
-    static_assert(INPLACE != 1 || (SPLIT && E_BOXES == 8 && 2 * BOX_BYTES == 8 * 16384), "in-place chunks fill both buffers");
-    static_assert(INPLACE != 2 || (SPLIT && E_BOXES == 4 && O_BOXES == 4 && BOX_BYTES == 4 * kTileABytes),
-                  "in-place planes fill one buffer each");
+    static_assert(!INPLACE || (SPLIT && E_BOXES == 8 && 2 * BOX_BYTES == 8 * 16384), "in-place chunks fill both buffers");
     static_assert(!SPLIT || B_MN || BOX_B == BN, "a split K-major B tile is one box");
     static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "stages stay 1024-byte aligned");
 
@@ -717,25 +712,17 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
         }
     } else if (warp == 2 && INPLACE) {
         if (lane == 0 && nk > 0) {
-            // ---- in-place split form: the operand of tile t is loaded once the stores of tile
-            // t - 1 (written over its operand) have read the buffers ----
-            constexpr int NBAR = INPLACE == 1 ? 8 : 4;
+            // ---- in-place split form: the FP32 operand chunks of tile t are loaded once the
+            // stores of tile t - 1 (written over its chunks) have read them ----
             bool ok = true;
             int loaded = -1;
             auto store_tile = [&](int t) -> bool {
                 if (!mbar_wait(&staged[0], (uint32_t)t & 1u, abort_flag)) return false;
                 const int nb = nbox[0];
                 const int m0t = (first + t * stride) * kTileM;
-                if (INPLACE == 1) {
-                    for (int c = 0; c < 2 * nb && c < 8; ++c) {
-                        tma_store_3d(&tmO, boxes + c * 16384, n0 + 32 * c, m0t, 0);
-                        tma_store_3d(&tmO, boxes + c * 16384 + 8192, n0 + 32 * c, m0t, 1);
-                    }
-                } else {
-                    for (int b = 0; b < nb && b < 4; ++b) {
-                        tma_store_3d(&tmO, boxes + b * kTileABytes, n0 + 64 * b, m0t, 0);
-                        tma_store_3d(&tmO, boxes + BOX_BYTES + b * kTileABytes, n0 + 64 * b, m0t, 1);
-                    }
+                for (int c = 0; c < 2 * nb && c < 8; ++c) {
+                    tma_store_3d(&tmO, boxes + c * 16384, n0 + 32 * c, m0t, 0);
+                    tma_store_3d(&tmO, boxes + c * 16384 + 8192, n0 + 32 * c, m0t, 1);
                 }
                 bulk_commit();
                 bulk_wait_read();
@@ -747,17 +734,9 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                     break;
                 }
                 const int m0t = (first + t * stride) * kTileM;
-                if (INPLACE == 1) {
-                    for (int c = 0; c < 8; ++c) {
-                        mbar_expect_tx(&e_full[c], 16384);
-                        tma_load_2d(boxes + c * 16384, &tmE, &e_full[c], n0 + 32 * c, m0t);
-                    }
-                } else {
-                    for (int b = 0; b < 4; ++b) {
-                        mbar_expect_tx(&e_full[b], 2 * kTileABytes);
-                        tma_load_3d(boxes + b * kTileABytes, &tmE, &e_full[b], n0 + 64 * b, m0t, 0);
-                        tma_load_3d(boxes + BOX_BYTES + b * kTileABytes, &tmE, &e_full[b], n0 + 64 * b, m0t, 1);
-                    }
+                for (int c = 0; c < 8; ++c) {
+                    mbar_expect_tx(&e_full[c], 16384);
+                    tma_load_2d(boxes + c * 16384, &tmE, &e_full[c], n0 + 32 * c, m0t);
                 }
                 loaded = t;
             }
@@ -765,7 +744,7 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
             if (!ok) {
                 *abort_flag = 1;
                 if (loaded >= 0)  // never leave the CTA with copies in flight
-                    for (int c = 0; c < NBAR; ++c) (void)mbar_wait(&e_full[c], (uint32_t)loaded & 1u, nullptr);
+                    for (int c = 0; c < 8; ++c) (void)mbar_wait(&e_full[c], (uint32_t)loaded & 1u, nullptr);
                 bulk_wait_read();
             }
         }
@@ -913,12 +892,11 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
                       row, tile * kTileM, n0, 0, group, scratch, E_BOXES > 0 ? box : nullptr, box,
                       &e_full[4 * e], abort_flag, (int)crank, (int)csize, &xbars[e],
                       xbufs + e * (kXchgBytes / 4), (uint32_t)use & 1u, (uint32_t)use & 1u, G, 96};
-            if (INPLACE) {  // the operand of this tile, the output written over it
+            if (INPLACE) {  // the operand chunks of this tile, the output written over them
                 ec.etile = boxes;
                 ec.otile = boxes;
                 ec.ebar = e_full;
                 ec.ephase = (uint32_t)lt & 1u;
-                if (INPLACE == 2) ec.eplane = ec.oplane = BOX_BYTES;
             } else if (SPLIT) {  // both buffers hold this tile's output; run() waits for them (wait_out)
                 ec.otile = boxes;
                 ec.oplane = BOX_BYTES;
