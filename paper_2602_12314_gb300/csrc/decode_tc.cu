@@ -512,6 +512,7 @@ struct DsParams {
 template <bool SPLIT_ = false>
 struct DsEpi {
     static constexpr bool SPLIT = SPLIT_;
+    static constexpr int MSUB = 1, BKC = 64;
     // the attention rows of the tile come through shared memory
     static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 0, MIN_SMEM = 0;
     static constexpr int MIN_BLOCKS = SPLIT_ ? 1 : 2;
@@ -547,6 +548,7 @@ struct DqParams {
 template <int BN_, bool SPLIT_ = false>
 struct DqEpi {
     static constexpr bool SPLIT = SPLIT_;
+    static constexpr int MSUB = 1, BKC = 64;
     static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, O_BOXES = 0, XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
@@ -583,18 +585,27 @@ struct PartParams {
     float* part;
 };
 
-template <int BN_, bool SPLIT_ = false>
+// MSUB_ = 2: one CTA covers 256 rows (two accumulators) so that each B stage (the pixel block
+// of the wide operand) is read once for both; with 32-wide pixel stages in the split form.
+template <int BN_, bool SPLIT_ = false, int MSUB_ = 1>
 struct PartEpi {
     static constexpr bool SPLIT = SPLIT_;
-    static constexpr int BN = BN_, STAGES = (BN_ <= 64 ? 6 : 4) / (SPLIT_ ? 2 : 1), BOX_B = BN_, EPI_WG = 1;
+    static constexpr int MSUB = MSUB_, BKC = MSUB_ == 2 && SPLIT_ ? 32 : 64;
+    static constexpr int BN = BN_, BOX_B = BN_, EPI_WG = 1;
+    static constexpr int STAGES = MSUB_ == 2 ? 3 : (BN_ <= 64 ? 6 : 4) / (SPLIT_ ? 2 : 1);
     static constexpr int E_BOXES = 0, O_BOXES = 0;
     static constexpr int XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
     using Params = PartParams;
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
-        const uint32_t taddr = ec.taddr;
-        const int row = ec.row, m0 = ec.m0, n0 = ec.n0, z = ec.z;
+#pragma unroll
+        for (int ms = 0; ms < MSUB; ++ms) sub(p, ec, ms);
+        return 0;
+    }
+    static __device__ void sub(const Params& p, const tc::EpiCtx& ec, int ms) {
+        const uint32_t taddr = ec.taddr + (uint32_t)(ms * BN);
+        const int row = ec.row, m0 = ec.m0 + ms * tc::kTileM, n0 = ec.n0, z = ec.z;
         const int j = m0 + row;
         float v[32];
 #pragma unroll
@@ -613,7 +624,6 @@ struct PartEpi {
                 }
             }
         }
-        return 0;
     }
 };
 
@@ -945,10 +955,10 @@ latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool trai
     return LATENTAM_OK;
 }
 
-// Split of the pixel reduction (K) of G5/G6 into about z parts of at least four 64-pixel
-// chunks; *z_out receives the number of parts.
-tc::GemmGrid pixel_split(int64_t n, int z, int* z_out) {
-    const int chunks = (int)((n + tc::kChunkK - 1) / tc::kChunkK);
+// Split of the pixel reduction (K) of G5/G6 into about z parts of at least four chunks of
+// `chunk` pixels; *z_out receives the number of parts.
+tc::GemmGrid pixel_split(int64_t n, int z, int* z_out, int chunk = tc::kChunkK) {
+    const int chunks = (int)((n + chunk - 1) / chunk);
     z = std::max(1, std::min(z, std::max(1, chunks / 4)));
     const int cpz = (chunks + z - 1) / z;
     *z_out = (chunks + cpz - 1) / cpz;
@@ -1123,7 +1133,8 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
                                               b.acc);
     LAT_CHECK_LAUNCH("tc_trust_region");
     constexpr int BNq = kPad;  // queries padded to 64 columns
-    const int tilesV = cdiv(M, kTileM) * cdiv(D, 256), tilesK = cdiv(M, kTileM);
+    using EpiV = PartEpi<256, SPLIT, 2>;  // dV: 256 atoms per CTA, each dFhat block read once for both halves
+    const int tilesV = cdiv(M, 2 * kTileM) * cdiv(D, 256), tilesK = cdiv(M, kTileM);
     const int zV0 = wave_split(tilesV, ctx->num_sms), zK0 = wave_split(tilesK, ctx->num_sms);
     // partial sums for the largest split a tuner may try
     const size_t part_floats = std::max((size_t)2 * zV0 * M * D, (size_t)2 * zK0 * M * BNq);
@@ -1162,19 +1173,18 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
     if (a.dV) {
         if (n > 0) {
             CUtensorMap mA, mdF;
-            LAT_TRY(io_map(SPLIT, &mA, b.A, M, n, M, 64));
-            LAT_TRY(mn_map(SPLIT, &mdF, b.dF, D, n, D, 64, 256 / 64));
+            LAT_TRY(io_map(SPLIT, &mA, b.A, M, n, M, EpiV::BKC));
+            LAT_TRY(mn_map(SPLIT, &mdF, b.dF, D, n, D, EpiV::BKC, 256 / 64));
             PartParams pp{M, D, D, b.part};
             auto g5 = [&](int z) -> latentam_status {
                 int zz;
-                const tc::GemmGrid g = pixel_split(n, z, &zz);
-                return launch_gemm<PartEpi<256, SPLIT>>(mA, mdF, dim3(cdiv(M, kTileM), cdiv(D, 256), zz), g, pp, b.err,
-                                                        st);
+                const tc::GemmGrid g = pixel_split(n, z, &zz, EpiV::BKC);
+                return launch_gemm<EpiV>(mA, mdF, dim3(cdiv(M, 2 * kTileM), cdiv(D, 256), zz), g, pp, b.err, st);
             };
             int z;
             LAT_TRY(tuned_split(ctx, n, M, D, 5 + which, zV0, st, g5, &z));
             LAT_TRY(g5(z));
-            pixel_split(n, z, &zV);
+            pixel_split(n, z, &zV, EpiV::BKC);
         }
         tc_reduce_parts<<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, n > 0 ? zV : 0, M, D, D, 1.0f, b.coef, a.V,
                                                                   a.V0, a.dV);

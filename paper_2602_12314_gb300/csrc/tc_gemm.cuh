@@ -44,7 +44,8 @@ __host__ __device__ constexpr int planes() {
 // (O_BOXES per plane).
 template <class Epi>
 __host__ __device__ constexpr uint32_t tile_region_bytes() {
-    const uint32_t pipe = (uint32_t)Epi::STAGES * planes<Epi>() * (kTileABytes + (uint32_t)Epi::BN * 128);
+    const uint32_t pipe = (uint32_t)Epi::STAGES * planes<Epi>() *
+                          ((uint32_t)Epi::MSUB * kTileM + (uint32_t)Epi::BN) * Epi::BKC * 2;
     const uint32_t boxes =
         (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * planes<Epi>() * kTileABytes;
     return pipe > boxes ? pipe : boxes;
@@ -110,7 +111,10 @@ struct GemmGrid {
 };
 
 // Epi must provide: static constexpr int BN, STAGES, BOX_B (rows per TMA box of a K-major B,
-// divides BN, <= 256); static constexpr bool SPLIT (every operand, epilogue operand and staged
+// divides BN, <= 256); static constexpr int MSUB (one-tile kernel: 128-row sub-tiles of A per CTA
+// sharing each B stage, 1 or 2 (MN-major A), each its own TMEM accumulator of BN columns) and
+// BKC (one-tile kernel: K elements per ring stage, 64, or 32 when both operands are MN-major);
+// static constexpr bool SPLIT (every operand, epilogue operand and staged
 // output held as a BF16 hi and lo plane, 3D tensor maps with the plane as z, and each product
 // taken as three MMAs); static constexpr bool A_MN, B_MN (operand stored MN-major: the tile is
 // loaded as 64 (MN) x 64 (K) boxes of a row-major K x MN matrix, x = MN, y = K); struct
@@ -309,11 +313,17 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     constexpr int SUBN = BN / NSUB;
     constexpr bool SPLIT = Epi::SPLIT;
     constexpr int PL = planes<Epi>();
-    constexpr uint32_t B_BYTES = (uint32_t)BN * 128;  // per plane
-    constexpr uint32_t STAGE_BYTES = PL * (kTileABytes + B_BYTES);  // [A planes][B planes]
-    constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
+    constexpr int MSUB = Epi::MSUB;  // 128-row sub-tiles of A sharing every B stage
+    constexpr int BKC = Epi::BKC;    // K elements per ring stage
+    constexpr uint32_t A_BYTES = (uint32_t)MSUB * kTileM * BKC * 2;  // per plane
+    constexpr uint32_t B_BYTES = (uint32_t)BN * BKC * 2;             // per plane
+    constexpr uint32_t MNBOX = 64u * BKC * 2;  // one 64 (MN) x BKC (K) box of an MN-major operand
+    constexpr uint32_t STAGE_BYTES = PL * (A_BYTES + B_BYTES);  // [A planes][B planes]
+    constexpr uint32_t TMEM_COLS = tmem_cols_for(MSUB * BN);
     constexpr bool A_MN = Epi::A_MN, B_MN = Epi::B_MN;
     constexpr uint32_t IDESC = idesc_bf16(kTileM, SUBN, A_MN, B_MN);
+    static_assert(BKC == kChunkK || (A_MN && B_MN && BKC == 32), "32-wide K stages read both operands MN-major");
+    static_assert(MSUB == 1 || (A_MN && MSUB == 2 && MSUB * BN <= 512), "two A sub-tiles: MN-major, <= 512 columns");
     static_assert(BN % 16 == 0 && SUBN % 16 == 0 && SUBN <= 256, "MMA N must be a multiple of 16, <= 256");
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
     static_assert(!B_MN || SUBN % 64 == 0, "an MN-major B tile is made of 64-wide boxes");
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     float* scratch = reinterpret_cast<float*>(smem + TILE_REGION + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kTileM;
+    const int m0 = blockIdx.x * MSUB * kTileM;
     const int n0 = blockIdx.y * BN;
     const int k_begin = blockIdx.z * g.chunks_per_z;
     const int k_end = min(g.k_chunks, k_begin + g.chunks_per_z);
@@ -370,10 +380,10 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                     *abort_flag = 1;
                     break;
                 }
-                const int kx = (k_begin + i) * kChunkK;
+                const int kx = (k_begin + i) * BKC;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
                 uint8_t* sa = smem + s * STAGE_BYTES;
-                uint8_t* sb = sa + PL * kTileABytes;
+                uint8_t* sb = sa + PL * A_BYTES;
                 if (SPLIT) {
                     // one box holds both planes: K-major [plane][row][128 B] (3D), MN-major B
                     // [plane][block][K row][128 B] (4D); an MN-major A loads each plane's blocks
@@ -381,8 +391,8 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
 #pragma unroll
                         for (int z = 0; z < 2; ++z)
 #pragma unroll
-                            for (int b = 0; b < kTileM / 64; ++b)
-                                tma_load_3d(sa + z * kTileABytes + b * kMnBoxBytes, &tmA, &full[s], m0 + 64 * b, kx, z);
+                            for (int b = 0; b < MSUB * kTileM / 64; ++b)
+                                tma_load_3d(sa + z * A_BYTES + b * MNBOX, &tmA, &full[s], m0 + 64 * b, kx, z);
                     } else {
                         tma_load_3d(sa, &tmA, &full[s], kx, m0, 0);
                     }
@@ -393,15 +403,15 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 } else {
                     if (A_MN) {
 #pragma unroll
-                        for (int b = 0; b < kTileM / 64; ++b)
-                            tma_load_2d(sa + b * kMnBoxBytes, &tmA, &full[s], m0 + 64 * b, kx);
+                        for (int b = 0; b < MSUB * kTileM / 64; ++b)
+                            tma_load_2d(sa + b * MNBOX, &tmA, &full[s], m0 + 64 * b, kx);
                     } else {
                         tma_load_2d(sa, &tmA, &full[s], kx, m0);
                     }
                     if (B_MN) {
 #pragma unroll
                         for (int b = 0; b < BN / 64; ++b)
-                            tma_load_2d(sb + b * kMnBoxBytes, &tmB, &full[s], n0 + 64 * b, kx);
+                            tma_load_2d(sb + b * MNBOX, &tmB, &full[s], n0 + 64 * b, kx);
                     } else {
 #pragma unroll
                         for (int b = 0; b < BN / BOX_B; ++b)
@@ -444,21 +454,25 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 }
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);  // A hi (then A lo)
-                const uint32_t sb = sa + PL * kTileABytes;             // B hi (then B lo)
-                auto adesc = [&](uint32_t base, int kk) {
-                    return A_MN ? mn128_desc(base + kk * 16 * 128) : sw128_desc(base + kk * 32);
+                const uint32_t sb = sa + PL * A_BYTES;                 // B hi (then B lo)
+                auto adesc = [&](uint32_t base, int ms, int kk) {
+                    return A_MN ? mn128_desc(base + (uint32_t)(ms * 2) * MNBOX + kk * 16 * 128, MNBOX)
+                                : sw128_desc(base + kk * 32);
                 };
                 auto bdesc = [&](uint32_t base, int j, int kk) {
-                    return B_MN ? mn128_desc(base + (uint32_t)(j * (SUBN / 64)) * kMnBoxBytes + kk * 16 * 128)
+                    return B_MN ? mn128_desc(base + (uint32_t)(j * (SUBN / 64)) * MNBOX + kk * 16 * 128, MNBOX)
                                 : sw128_desc(base + (uint32_t)(j * SUBN * 128) + kk * 32);
                 };
 #pragma unroll
-                for (int kk = 0; kk < kChunkK / 16; ++kk) {
-                    const uint64_t da = adesc(sa, kk), dal = adesc(sa + kTileABytes, kk);
+                for (int kk = 0; kk < BKC / 16; ++kk) {
 #pragma unroll
-                    for (int j = 0; j < NSUB; ++j)
-                        mma_step<SPLIT>(tmem_base + (uint32_t)(j * SUBN), da, dal, bdesc(sb, j, kk),
-                                        bdesc(sb + B_BYTES, j, kk), IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+                    for (int ms = 0; ms < MSUB; ++ms) {
+                        const uint64_t da = adesc(sa, ms, kk), dal = adesc(sa + A_BYTES, ms, kk);
+#pragma unroll
+                        for (int j = 0; j < NSUB; ++j)
+                            mma_step<SPLIT>(tmem_base + (uint32_t)(ms * BN + j * SUBN), da, dal, bdesc(sb, j, kk),
+                                            bdesc(sb + B_BYTES, j, kk), IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+                    }
                 }
                 mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
             }
