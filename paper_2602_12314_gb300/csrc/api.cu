@@ -1296,17 +1296,13 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
         }
         LAT_TRY(s);
     }
-    {
-        // every frame's tile launch order, side by side in the order slot
-        size_t total_tiles = 0;
-        for (int k = 0; k < n_frames; ++k) total_tiles += (size_t)fs[k].cam.tiles_x * fs[k].cam.tiles_y;
-        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
-        size_t off = 0;
-        for (int k = 0; k < n_frames; ++k) {
-            LAT_TRY(ordered(ctx, &fs[k].cam, fs[k].bins, off, total_tiles, st));
-            off += (size_t)fs[k].cam.tiles_x * fs[k].cam.tiles_y;
-        }
-    }
+    // one work list over the tiles of every frame, longest lists first, and the two work tickets
+    // of the persistent render launches
+    int total_tiles = 0;
+    for (int k = 0; k < n_frames; ++k) total_tiles += fs[k].cam.tiles_x * fs[k].cam.tiles_y;
+    int32_t* work = static_cast<int32_t*>(ws(ctx, WS_TILE_ORDER, sizeof(int32_t) * ((size_t)total_tiles + 64)));
+    if (!work) return LATENTAM_ERR_OUT_OF_MEMORY;
+    int* tickets = work + ((total_tiles + 31) / 32) * 32;  // [0] forward, [1] backward
 
     // stacked images, per-group query gradients, dictionary gradients
     const size_t i_q = 0, i_t = i_q + up(4 * (size_t)total_pix * d), i_n = i_t + up(4 * (size_t)total_pix),
@@ -1362,13 +1358,34 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
     float* dK = reinterpret_cast<float*>(gb + g_dk);
     float* dV = reinterpret_cast<float*>(gb + g_dv);
     double* lp = reinterpret_cast<double*>(gb + g_lp);
+    BatchJobs jobs{};
+    jobs.n = n_frames;
+    for (int k = 0; k < n_frames; ++k) {
+        const CamParams& cp = fs[k].cam;
+        jobs.fr[k] = TileJob{0,
+                             cp.tiles_x,
+                             cp.W,
+                             cp.H,
+                             reinterpret_cast<const int2*>(fs[k].bins.tile_ranges),
+                             fs[k].bins.pair_ids,
+                             reinterpret_cast<const float2*>(fs[k].proj.xy),
+                             reinterpret_cast<const float4*>(fs[k].proj.conic_opacity),
+                             reinterpret_cast<const float4*>(frames[k].f),
+                             reinterpret_cast<float4*>(Q + fs[k].pix_off * d),
+                             T + fs[k].pix_off,
+                             nc + fs[k].pix_off,
+                             reinterpret_cast<const float4*>(dQ + fs[k].pix_off * d),
+                             groups[fs[k].group].df};
+    }
+    {
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+        LAT_TRY(launch_batch_order(jobs, work, st));
+    }
 
     auto iteration = [&](cudaStream_t s, bool render, const int* step_dev) -> latentam_status {
         if (render) {
             StageTimer tm(ctx, LATENTAM_STAGE_RENDER_FWD, s);
-            for (int k = 0; k < n_frames; ++k)
-                LAT_TRY(launch_render_fwd(fs[k].cam, fs[k].proj, fs[k].bins, frames[k].f, d, Q + fs[k].pix_off * d,
-                                          T + fs[k].pix_off, nc + fs[k].pix_off, s));
+            LAT_TRY(launch_render_fwd_batch(jobs, d, work, total_tiles, tickets, s));
             for (int k = 0; pooled && k < n_frames; ++k)
                 LAT_TRY(launch_pool_fwd(plans[k], Q + fs[k].pix_off * d, d, Qm + row_off[k] * d, s));
         }
@@ -1387,11 +1404,7 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
             }
             for (int k = 0; pooled && k < n_frames; ++k)
                 LAT_TRY(launch_pool_bwd(plans[k], dQm + row_off[k] * d, d, dQ + fs[k].pix_off * d, s));
-            for (int k = 0; k < n_frames; ++k)
-                if (frames[k].gaussians.n > 0)
-                    LAT_TRY(launch_render_bwd(fs[k].cam, fs[k].proj, fs[k].bins, nc + fs[k].pix_off,
-                                              dQ + fs[k].pix_off * d, d, groups[fs[k].group].df, frames[k].gaussians.n,
-                                              s, /*accumulate=*/true));
+            LAT_TRY(launch_render_bwd_batch(jobs, d, work, total_tiles, tickets + 1, s));
         }
         StageTimer tm(ctx, LATENTAM_STAGE_ADAM, s);
         if (step_dev) LAT_TRY(launch_step_advance(const_cast<int*>(step_dev), s));

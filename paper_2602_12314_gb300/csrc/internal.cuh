@@ -194,6 +194,35 @@ latentam_status launch_render_bwd(const CamParams& cam, const latentam_projected
                                   const latentam_bins& bins, const int32_t* n_contrib,
                                   const float* dQ, int d, float* df, int32_t n, cudaStream_t st,
                                   bool accumulate = false);
+// One tile of one frame: its list range, the frame's buffers and image size.
+struct TileJob {
+    int tile, tiles_x, W, H;
+    const int2* ranges;
+    const int32_t* pair_ids;
+    const float2* xy;
+    const float4* conic_opac;
+    const float4* f;
+    float4* Q;
+    float* T_final;
+    int32_t* n_contrib;
+    const float4* dQ;
+    float* df;
+};
+
+// The frames of a batch (one launch renders the tiles of all of them).
+struct BatchJobs {
+    TileJob fr[LATENTAM_MAX_BATCH];  // tile unused
+    int n;
+};
+
+// Longest tiles first over every frame of jobs (entries (frame << 20) | tile, Σ tiles of all frames).
+latentam_status launch_batch_order(const BatchJobs& jobs, int32_t* order, cudaStream_t st);
+// Persistent render forward / backward over the `total` entries of order (atomic work ticket
+// *counter, reset by the launch); the backward adds into each frame's df.
+latentam_status launch_render_fwd_batch(const BatchJobs& jobs, int d, const int32_t* order, int total, int* counter,
+                                        cudaStream_t st);
+latentam_status launch_render_bwd_batch(const BatchJobs& jobs, int d, const int32_t* order, int total, int* counter,
+                                        cudaStream_t st);
 // Queries, colours and depth blended together (Q, C n x 3, Z, T_final, n_contrib).
 latentam_status launch_render_full(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
                                    const float* f, int d, const float* colours, float* Q, float* C, float* Z,

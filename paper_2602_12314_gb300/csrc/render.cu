@@ -6,6 +6,8 @@
 // shared memory in batches of 256 (mean, exponent coefficients/opacity, query as
 // float4 rows), so every query row is read from L2/HBM once per tile and broadcast to the
 // 256 pixels.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace lat {
@@ -30,24 +32,23 @@ __device__ __forceinline__ float splat_alpha(float2 m, float4 q, float px, float
 }
 
 template <int DQ>
-__global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, const int2* __restrict__ ranges,
-                                                                 const int32_t* __restrict__ pair_ids,
-                                                                 const float2* __restrict__ xy,
-                                                                 const float4* __restrict__ conic_opac,
-                                                                 const float4* __restrict__ f, float4* __restrict__ Q,
-                                                                 float* __restrict__ T_final,
-                                                                 int32_t* __restrict__ n_contrib) {
+struct FwdSmem {
+    float2 xy[kBatch];
+    float4 co[kBatch];
+    float4 f[kBatch][DQ / 4];
+};
+
+// Front-to-back blend of one tile (256 threads, one pixel each).
+template <int DQ>
+__device__ __forceinline__ void render_fwd_tile(const TileJob& job, FwdSmem<DQ>& sm) {
     constexpr int DV = DQ / 4;
-    __shared__ float2 s_xy[kBatch];
-    __shared__ float4 s_co[kBatch];
-    __shared__ float4 s_f[kBatch][DV];
-    const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int tile = job.tile;
+    const int tx = tile % job.tiles_x, ty = tile / job.tiles_x;
     const int t = threadIdx.x;
     const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
-    const bool inside = px < cam.W && py < cam.H;
+    const bool inside = px < job.W && py < job.H;
     const float fpx = (float)px, fpy = (float)py;
-    const int2 range = ranges[tile];
+    const int2 range = job.ranges[tile];
     float4 acc[DV];
 #pragma unroll
     for (int k = 0; k < DV; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -58,16 +59,16 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, 
         if (__syncthreads_count(done) == kTilePixels) break;
         const int k = start + t;
         if (k < range.y) {
-            const int g = pair_ids[k];
-            s_xy[t] = xy[g];
-            s_co[t] = stage_splat(conic_opac[g]);
+            const int g = job.pair_ids[k];
+            sm.xy[t] = job.xy[g];
+            sm.co[t] = stage_splat(job.conic_opac[g]);
 #pragma unroll
-            for (int c = 0; c < DV; ++c) s_f[t][c] = f[(size_t)g * DV + c];
+            for (int c = 0; c < DV; ++c) sm.f[t][c] = job.f[(size_t)g * DV + c];
         }
         __syncthreads();
         const int cnt = min(kBatch, range.y - start);
         for (int j = 0; j < cnt && !done; ++j) {
-            const float alpha = splat_alpha(s_xy[j], s_co[j], fpx, fpy);
+            const float alpha = splat_alpha(sm.xy[j], sm.co[j], fpx, fpy);
             if (alpha < kAlphaMin) continue;
             const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
             if (test_T < kTMin) {
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, 
             const float w = __fmul_rn(alpha, T);
 #pragma unroll
             for (int c = 0; c < DV; ++c) {
-                const float4 v = s_f[j][c];
+                const float4 v = sm.f[j][c];
                 acc[c].x += w * v.x;
                 acc[c].y += w * v.y;
                 acc[c].z += w * v.z;
@@ -88,11 +89,51 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, 
         }
     }
     if (inside) {
-        const size_t p = (size_t)py * cam.W + px;
+        const size_t p = (size_t)py * job.W + px;
 #pragma unroll
-        for (int c = 0; c < DV; ++c) Q[p * DV + c] = acc[c];
-        T_final[p] = T;
-        n_contrib[p] = count;
+        for (int c = 0; c < DV; ++c) job.Q[p * DV + c] = acc[c];
+        job.T_final[p] = T;
+        job.n_contrib[p] = count;
+    }
+}
+
+template <int DQ>
+__global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, const int2* __restrict__ ranges,
+                                                                 const int32_t* __restrict__ pair_ids,
+                                                                 const float2* __restrict__ xy,
+                                                                 const float4* __restrict__ conic_opac,
+                                                                 const float4* __restrict__ f, float4* __restrict__ Q,
+                                                                 float* __restrict__ T_final,
+                                                                 int32_t* __restrict__ n_contrib) {
+    __shared__ FwdSmem<DQ> sm;
+    const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
+    const TileJob job{tile, cam.tiles_x, cam.W, cam.H, ranges, pair_ids, xy, conic_opac, f, Q, T_final, n_contrib,
+                      nullptr, nullptr};
+    render_fwd_tile<DQ>(job, sm);
+}
+
+// Next (frame, tile) of a batch from the global work list (frame in the top 12 bits), taken in
+// list order by an atomic ticket; -1 when the list is exhausted.  Every thread returns the same
+// item; the two barriers also keep the previous item's shared memory until every thread is done.
+__device__ __forceinline__ int next_item(int* counter, const int32_t* order, int total) {
+    __shared__ int s_item;
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    return it < total ? order[it] : -1;
+}
+
+// Persistent render forward over every tile of every frame of a batch, longest lists first.
+template <int DQ>
+__global__ void __launch_bounds__(kTilePixels) render_fwd_batch_kernel(const __grid_constant__ BatchJobs jobs,
+                                                                       const int32_t* __restrict__ order, int total,
+                                                                       int* __restrict__ counter) {
+    __shared__ FwdSmem<DQ> sm;
+    for (int item = next_item(counter, order, total); item >= 0; item = next_item(counter, order, total)) {
+        TileJob job = jobs.fr[item >> 20];
+        job.tile = item & 0xFFFFF;
+        render_fwd_tile<DQ>(job, sm);
     }
 }
 
@@ -131,17 +172,12 @@ constexpr size_t render_bwd_smem() {
            (sizeof(float2) + sizeof(float4) + sizeof(int)) * kBwdBatch + sizeof(int) * kTilePixels;
 }
 
+// Backward of one tile (256 threads); smem_f4 is the dynamic shared memory of render_bwd_smem.
 template <int DQ>
-__global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, const int2* __restrict__ ranges,
-                                                                 const int32_t* __restrict__ pair_ids,
-                                                                 const float2* __restrict__ xy,
-                                                                 const float4* __restrict__ conic_opac,
-                                                                 const int32_t* __restrict__ n_contrib,
-                                                                 const float4* __restrict__ dQ, float* __restrict__ df) {
+__device__ __forceinline__ void render_bwd_tile(const TileJob& job, float4* smem_f4) {
     constexpr int DV = DQ / 4;
     static_assert((size_t)kBwdQuarters * DQ * kWStride <= (size_t)kTilePixels * kWStride,
                   "the partial sums must fit in the space of W");
-    extern __shared__ float4 smem_f4[];
     float* s_w = reinterpret_cast<float*>(smem_f4);                // [pixel][kWStride]
     float* s_part = s_w;                                           // [quarter][channel][kWStride]
     float4* s_dq = reinterpret_cast<float4*>(s_w + (size_t)kTilePixels * kWStride);  // [pixel][DV]
@@ -151,19 +187,24 @@ __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, 
     int* s_row = s_id + kBwdBatch;  // pixel row of W non-zero in this batch
     static_assert((kTilePixels * kWStride) % 4 == 0, "dQ rows must stay 16-byte aligned");
 
-    const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int tile = job.tile;
+    const int tx = tile % job.tiles_x, ty = tile / job.tiles_x;
     const int t = threadIdx.x;
     const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
-    const bool inside = px < cam.W && py < cam.H;
+    const bool inside = px < job.W && py < job.H;
     const float fpx = (float)px, fpy = (float)py;
-    const int2 range = ranges[tile];
+    const int2 range = job.ranges[tile];
+    const int32_t* __restrict__ pair_ids = job.pair_ids;
+    const float2* __restrict__ xy = job.xy;
+    const float4* __restrict__ conic_opac = job.conic_opac;
+    const float4* __restrict__ dQ = job.dQ;
+    float* __restrict__ df = job.df;
     int remaining = 0;
     if (inside) {
-        const size_t p = (size_t)py * cam.W + px;
+        const size_t p = (size_t)py * job.W + px;
 #pragma unroll
         for (int c = 0; c < DV; ++c) s_dq[t * DV + c] = dQ[p * DV + c];
-        remaining = n_contrib[p];
+        remaining = job.n_contrib[p];
     } else {
 #pragma unroll
         for (int c = 0; c < DV; ++c) s_dq[t * DV + c] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -232,6 +273,34 @@ __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, 
             if (s != 0.0f) atomicAdd(&df[(size_t)s_id[j] * DQ + c], s);
         }
         // the next batch's staging and W writes come after the barrier at the loop head
+    }
+}
+
+template <int DQ>
+__global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(CamParams cam, const int2* __restrict__ ranges,
+                                                                 const int32_t* __restrict__ pair_ids,
+                                                                 const float2* __restrict__ xy,
+                                                                 const float4* __restrict__ conic_opac,
+                                                                 const int32_t* __restrict__ n_contrib,
+                                                                 const float4* __restrict__ dQ, float* __restrict__ df) {
+    extern __shared__ float4 smem_f4[];
+    const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
+    const TileJob job{tile, cam.tiles_x, cam.W, cam.H, ranges, pair_ids, xy, conic_opac, nullptr, nullptr, nullptr,
+                      const_cast<int32_t*>(n_contrib), dQ, df};
+    render_bwd_tile<DQ>(job, smem_f4);
+}
+
+// Persistent render backward over every tile of every frame of a batch, longest lists first
+// (frames that share their queries add into the same df).
+template <int DQ>
+__global__ void __launch_bounds__(kTilePixels) render_bwd_batch_kernel(const __grid_constant__ BatchJobs jobs,
+                                                                       const int32_t* __restrict__ order, int total,
+                                                                       int* __restrict__ counter) {
+    extern __shared__ float4 smem_f4[];
+    for (int item = next_item(counter, order, total); item >= 0; item = next_item(counter, order, total)) {
+        TileJob job = jobs.fr[item >> 20];
+        job.tile = item & 0xFFFFF;
+        render_bwd_tile<DQ>(job, smem_f4);
     }
 }
 
@@ -525,7 +594,115 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const int2* __restrict
     for (int i = t; i < tiles; i += blockDim.x) order[atomicAdd(&s_pos[cls(i)], 1)] = i;
 }
 
+// Longest tiles first over every frame of a batch (the same length classes as
+// tile_order_kernel); entries are (frame << 20) | tile.
+__global__ void __launch_bounds__(1024) batch_order_kernel(const __grid_constant__ BatchJobs jobs,
+                                                           int32_t* __restrict__ order) {
+    __shared__ int s_cnt[33], s_pos[33];
+    const int t = threadIdx.x;
+    if (t < 33) s_cnt[t] = 0;
+    __syncthreads();
+    auto cls = [&](const TileJob& fr, int i) {
+        const int2 r = fr.ranges[i];
+        const int len = r.y - r.x;
+        return len > 0 ? 32 - __clz(len) : 0;
+    };
+    for (int k = 0; k < jobs.n; ++k) {
+        const TileJob& fr = jobs.fr[k];
+        const int tiles = fr.tiles_x * ((fr.H + kTile - 1) / kTile);
+        for (int i = t; i < tiles; i += blockDim.x) atomicAdd(&s_cnt[cls(fr, i)], 1);
+    }
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int c = 32; c >= 0; --c) {
+            s_pos[c] = run;
+            run += s_cnt[c];
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < jobs.n; ++k) {
+        const TileJob& fr = jobs.fr[k];
+        const int tiles = fr.tiles_x * ((fr.H + kTile - 1) / kTile);
+        for (int i = t; i < tiles; i += blockDim.x) order[atomicAdd(&s_pos[cls(fr, i)], 1)] = (k << 20) | i;
+    }
+}
+
+// CTAs of a persistent batch kernel: as many as can be resident at once, at most `total`.
+template <class Kernel>
+int persistent_grid(Kernel kern, size_t smem, int total) {
+    static int per_sm[64] = {0};
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+    int& b = per_sm[dev & 63];
+    if (b == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kTilePixels, smem) != cudaSuccess || b < 1) b = 1;
+        (void)cudaGetLastError();
+    }
+    return std::max(1, std::min(total, b * sms));
+}
+
+template <int DQ>
+latentam_status render_fwd_batch_t(const BatchJobs& jobs, const int32_t* order, int total, int* counter,
+                                   cudaStream_t st) {
+    auto kern = render_fwd_batch_kernel<DQ>;
+    kern<<<persistent_grid(kern, 0, total), kTilePixels, 0, st>>>(jobs, order, total, counter);
+    LAT_CHECK_LAUNCH("render_fwd_batch_kernel");
+    return LATENTAM_OK;
+}
+
+template <int DQ>
+latentam_status render_bwd_batch_t(const BatchJobs& jobs, const int32_t* order, int total, int* counter,
+                                   cudaStream_t st) {
+    constexpr size_t smem = render_bwd_smem<DQ>();
+    auto kern = render_bwd_batch_kernel<DQ>;
+    static unsigned long long attr_set = 0;  // per instantiation and device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(attr_set & (1ull << (dev & 63)))) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "batched render backward smem attribute");
+        attr_set |= 1ull << (dev & 63);
+    }
+    kern<<<persistent_grid(kern, smem, total), kTilePixels, smem, st>>>(jobs, order, total, counter);
+    LAT_CHECK_LAUNCH("render_bwd_batch_kernel");
+    return LATENTAM_OK;
+}
+
 }  // namespace
+
+latentam_status launch_batch_order(const BatchJobs& jobs, int32_t* order, cudaStream_t st) {
+    batch_order_kernel<<<1, 1024, 0, st>>>(jobs, order);
+    LAT_CHECK_LAUNCH("batch_order_kernel");
+    return LATENTAM_OK;
+}
+
+latentam_status launch_render_fwd_batch(const BatchJobs& jobs, int d, const int32_t* order, int total, int* counter,
+                                        cudaStream_t st) {
+    if (total <= 0) return LATENTAM_OK;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_error(e, "reset the render work ticket");
+    switch (d) {
+        case 16: return render_fwd_batch_t<16>(jobs, order, total, counter, st);
+        case 32: return render_fwd_batch_t<32>(jobs, order, total, counter, st);
+        case 64: return render_fwd_batch_t<64>(jobs, order, total, counter, st);
+        default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+}
+
+latentam_status launch_render_bwd_batch(const BatchJobs& jobs, int d, const int32_t* order, int total, int* counter,
+                                        cudaStream_t st) {
+    if (total <= 0) return LATENTAM_OK;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_error(e, "reset the render work ticket");
+    switch (d) {
+        case 16: return render_bwd_batch_t<16>(jobs, order, total, counter, st);
+        case 32: return render_bwd_batch_t<32>(jobs, order, total, counter, st);
+        case 64: return render_bwd_batch_t<64>(jobs, order, total, counter, st);
+        default: set_error("query dimension d=%d not in {16, 32, 64}", d); return LATENTAM_ERR_UNSUPPORTED_SHAPE;
+    }
+}
 
 latentam_status launch_tile_order(const CamParams& cam, const latentam_bins& bins, int32_t* order, cudaStream_t st) {
     const int tiles = cam.tiles_x * cam.tiles_y;
