@@ -6,6 +6,8 @@
 // shared memory in batches of 256 (mean, exponent coefficients/opacity, query as
 // float4 rows), so every query row is read from L2/HBM once per tile and broadcast to the
 // 256 pixels.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "internal.cuh"
@@ -19,6 +21,15 @@ constexpr int kBatch = kTilePixels;  // 256 Gaussians staged per round
 // (a, b, c).
 __device__ __forceinline__ float4 stage_splat(float4 co) {
     return make_float4(__fmul_rn(-0.5f, co.x), -co.y, __fmul_rn(-0.5f, co.z), co.w);
+}
+
+// The hi and lo BF16 terms of (x0, x1), packed: hi = bf16(x), lo = bf16(x - hi).
+__device__ __forceinline__ void tc_split(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // alpha of a splat at a pixel centre, or -1 when the exponent is positive.  Every rounding
@@ -153,124 +164,174 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
     return v[0];
 }
 
-// Backward of the query blend, df_i = sum_p w_ip dQ_p, as one small GEMM per tile and batch:
-// the weights w_ip of a batch of kBwdBatch Gaussians are first recomputed front to back by the
-// pixel threads (the forward's arithmetic, so the same contributions are taken: a pixel stops
-// after its n_contrib-th one) into a shared-memory matrix W (pixels x Gaussians); then
-// thread (q, j) sums W[p][j] dQ_p over the 64 pixels p of quarter q with the tile's dQ rows
-// broadcast from shared memory, the four quarters are added in a fixed order, and each
-// non-zero (Gaussian, channel) sum goes to df with one atomic per tile.  Pixel rows that are
-// zero for the whole batch (finished or untouched pixels) are skipped block-uniformly.
+// Backward of the query blend, df_i = sum_p w_ip dQ_p, as one small GEMM per tile and batch on
+// the tensor cores: the weights w_ip of a batch of kBwdBatch Gaussians are first recomputed front
+// to back by the pixel threads (the forward's arithmetic, so the same contributions are taken: a
+// pixel stops after its n_contrib-th one) into a shared-memory matrix W^T (Gaussians x pixels),
+// each weight as two BF16 terms w = hi + lo (hi = bf16(w), lo = bf16(w - hi)); the tile's dQ
+// rows are held the same way.  Then warp (m, h) takes Gaussians 16m..16m+15 and channel half h
+// and sums over the tile's 256 pixels with mma.sync m16n8k16 (BF16 in, FP32 accumulate) as
+// W_hi dQ_hi + W_hi dQ_lo + W_lo dQ_hi (each product within 2^-16 of the FP32 one), and each
+// non-zero (Gaussian, channel) sum goes to df with one atomic per tile.  A per-tile contraction
+// of 64 x 256 x d does not amortise TMEM allocation and completion waits; the warp-level MMA
+// runs in the registers of the warps that computed the weights.
 constexpr int kBwdBatch = 64;
-constexpr int kBwdQuarters = kTilePixels / kBwdBatch;  // 4
-constexpr int kWStride = kBwdBatch + 1;                // padded W row (conflict-free stores)
+constexpr int kWtStride = kTilePixels + 8;  // bf16 per W^T row (528 B: ldmatrix rows on distinct banks)
+
+template <int DQ>
+constexpr int dq_stride() {
+    return DQ + 8;  // bf16 per dQ row (16 B of padding: ldmatrix rows on distinct banks)
+}
 
 template <int DQ>
 constexpr size_t render_bwd_smem() {
-    // W (its space reused by the per-quarter partial sums), dQ rows, staged splats, row flags
-    return sizeof(float) * (size_t)kTilePixels * kWStride + sizeof(float) * (size_t)kTilePixels * DQ +
-           (sizeof(float2) + sizeof(float4) + sizeof(int)) * kBwdBatch + sizeof(int) * kTilePixels;
+    // W^T hi / lo, dQ hi / lo, staged splats
+    return 2 * sizeof(__nv_bfloat16) * (size_t)kBwdBatch * kWtStride +
+           2 * sizeof(__nv_bfloat16) * (size_t)kTilePixels * dq_stride<DQ>() +
+           (sizeof(float4) + sizeof(float2) + sizeof(int)) * kBwdBatch;
 }
 
-// Backward of one tile (256 threads); smem_f4 is the dynamic shared memory of render_bwd_smem.
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t addr, uint32_t (&r)[2]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+// c += a b, m16n8k16, BF16 operands, FP32 accumulators
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Backward of one tile (256 threads); smem is the dynamic shared memory of render_bwd_smem.
 template <int DQ>
-__device__ __forceinline__ void render_bwd_tile(const TileJob& job, float4* smem_f4) {
+__device__ __forceinline__ void render_bwd_tile(const TileJob& job, float4* smem) {
     constexpr int DV = DQ / 4;
-    static_assert((size_t)kBwdQuarters * DQ * kWStride <= (size_t)kTilePixels * kWStride,
-                  "the partial sums must fit in the space of W");
-    float* s_w = reinterpret_cast<float*>(smem_f4);                // [pixel][kWStride]
-    float* s_part = s_w;                                           // [quarter][channel][kWStride]
-    float4* s_dq = reinterpret_cast<float4*>(s_w + (size_t)kTilePixels * kWStride);  // [pixel][DV]
-    float4* s_co = s_dq + (size_t)kTilePixels * DV;
+    constexpr int DQS = dq_stride<DQ>();
+    constexpr int NT = DQ / 16;  // n-tiles of 8 channels per warp (a warp covers DQ / 2 channels)
+    using bf16 = __nv_bfloat16;
+    bf16* wt_hi = reinterpret_cast<bf16*>(smem);      // [Gaussian][pixel]
+    bf16* wt_lo = wt_hi + (size_t)kBwdBatch * kWtStride;
+    bf16* dq_hi = wt_lo + (size_t)kBwdBatch * kWtStride;  // [pixel][channel]
+    bf16* dq_lo = dq_hi + (size_t)kTilePixels * DQS;
+    float4* s_co = reinterpret_cast<float4*>(dq_lo + (size_t)kTilePixels * DQS);
     float2* s_xy = reinterpret_cast<float2*>(s_co + kBwdBatch);
     int* s_id = reinterpret_cast<int*>(s_xy + kBwdBatch);
-    int* s_row = s_id + kBwdBatch;  // pixel row of W non-zero in this batch
-    static_assert((kTilePixels * kWStride) % 4 == 0, "dQ rows must stay 16-byte aligned");
+    static_assert(((size_t)kBwdBatch * kWtStride * 2 * 2 + (size_t)kTilePixels * DQS * 2 * 2) % 16 == 0,
+                  "staged splats stay 16-byte aligned");
 
     const int tile = job.tile;
     const int tx = tile % job.tiles_x, ty = tile / job.tiles_x;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
     const bool inside = px < job.W && py < job.H;
     const float fpx = (float)px, fpy = (float)py;
     const int2 range = job.ranges[tile];
-    const int32_t* __restrict__ pair_ids = job.pair_ids;
-    const float2* __restrict__ xy = job.xy;
-    const float4* __restrict__ conic_opac = job.conic_opac;
-    const float4* __restrict__ dQ = job.dQ;
-    float* __restrict__ df = job.df;
     int remaining = 0;
-    if (inside) {
-        const size_t p = (size_t)py * job.W + px;
+    {
+        // this pixel's dQ row as hi / lo terms
+        float4 g[DV];
+        if (inside) {
+            const size_t p = (size_t)py * job.W + px;
 #pragma unroll
-        for (int c = 0; c < DV; ++c) s_dq[t * DV + c] = dQ[p * DV + c];
-        remaining = job.n_contrib[p];
-    } else {
+            for (int c = 0; c < DV; ++c) g[c] = job.dQ[p * DV + c];
+            remaining = job.n_contrib[p];
+        } else {
 #pragma unroll
-        for (int c = 0; c < DV; ++c) s_dq[t * DV + c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < DV; ++c) g[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int c = 0; c < DV; c += 2) {
+            uint32_t h[4], l[4];
+            const float4 a = g[c], b = c + 1 < DV ? g[c + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            tc_split(a.x, a.y, h[0], l[0]);
+            tc_split(a.z, a.w, h[1], l[1]);
+            tc_split(b.x, b.y, h[2], l[2]);
+            tc_split(b.z, b.w, h[3], l[3]);
+            if (c + 1 < DV) {
+                *reinterpret_cast<uint4*>(dq_hi + (size_t)t * DQS + 4 * c) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4*>(dq_lo + (size_t)t * DQS + 4 * c) = make_uint4(l[0], l[1], l[2], l[3]);
+            } else {
+                *reinterpret_cast<uint2*>(dq_hi + (size_t)t * DQS + 4 * c) = make_uint2(h[0], h[1]);
+                *reinterpret_cast<uint2*>(dq_lo + (size_t)t * DQS + 4 * c) = make_uint2(l[0], l[1]);
+            }
+        }
     }
-    const int q = t / kBwdBatch, jj = t % kBwdBatch;  // GEMM role: quarter and Gaussian column
+    const int mt = warp & 3, nh = warp >> 2;  // GEMM role: Gaussian rows 16 mt.., channel half nh
     float T = 1.0f;
     bool done = remaining == 0;
     for (int start = range.x; start < range.y; start += kBwdBatch) {
         if (__syncthreads_count(done) == kTilePixels) break;
         const int cnt = min(kBwdBatch, range.y - start);
         if (t < cnt) {
-            const int gid = pair_ids[start + t];
-            s_xy[t] = xy[gid];
-            s_co[t] = stage_splat(conic_opac[gid]);
+            const int gid = job.pair_ids[start + t];
+            s_xy[t] = job.xy[gid];
+            s_co[t] = stage_splat(job.conic_opac[gid]);
             s_id[t] = gid;
         }
         __syncthreads();
-        // 1. this pixel's weights for the batch (identical arithmetic to the forward pass)
-        int any = 0;
-        float* wrow = s_w + (size_t)t * kWStride;
-        for (int j = 0; j < cnt; ++j) {
+        // 1. this pixel's weights for the batch (identical arithmetic to the forward pass); the
+        //    columns of the Gaussians past the batch are zero
+        for (int j = 0; j < kBwdBatch; ++j) {
             float w = 0.0f;
-            if (!done) {
+            if (j < cnt && !done) {
                 const float alpha = splat_alpha(s_xy[j], s_co[j], fpx, fpy);
                 if (alpha >= kAlphaMin) {
                     w = __fmul_rn(alpha, T);
                     T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                    any = 1;
                     if (--remaining == 0) done = true;
                 }
             }
-            wrow[j] = w;
+            const __nv_bfloat16 wh = __float2bfloat16_rn(w);
+            wt_hi[(size_t)j * kWtStride + t] = wh;
+            wt_lo[(size_t)j * kWtStride + t] = __float2bfloat16_rn(w - __bfloat162float(wh));
         }
-        s_row[t] = any;
         __syncthreads();
-        // 2. thread (q, jj): sum over the quarter's pixels of W[p][jj] dQ_p
-        float acc[DQ];
+        // 2. warp (mt, nh): df rows 16 mt.. (Gaussians) x channels nh DQ/2.. over the 256 pixels
+        if (16 * mt < cnt) {
+            float acc[NT][4];
 #pragma unroll
-        for (int c = 0; c < DQ; ++c) acc[c] = 0.f;
-        if (jj < cnt) {
-            for (int i = 0; i < kBwdBatch; ++i) {
-                const int p = q * kBwdBatch + i;
-                if (!s_row[p]) continue;  // the same p for every thread of the warp
-                const float w = s_w[(size_t)p * kWStride + jj];
+            for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+            const int ar = 16 * mt + (lane & 15), ac = (lane >> 4) * 8;  // A fragment row / column
+            const int br = lane & 15;                                     // B fragment row (pixel)
+#pragma unroll 4
+            for (int kt = 0; kt < kTilePixels / 16; ++kt) {
+                uint32_t ah[4], al[4];
+                ldsm_x4(smem_addr(wt_hi + (size_t)ar * kWtStride + 16 * kt + ac), ah);
+                ldsm_x4(smem_addr(wt_lo + (size_t)ar * kWtStride + 16 * kt + ac), al);
 #pragma unroll
-                for (int c = 0; c < DV; ++c) {
-                    const float4 g = s_dq[p * DV + c];
-                    acc[4 * c] = __fmaf_rn(w, g.x, acc[4 * c]);
-                    acc[4 * c + 1] = __fmaf_rn(w, g.y, acc[4 * c + 1]);
-                    acc[4 * c + 2] = __fmaf_rn(w, g.z, acc[4 * c + 2]);
-                    acc[4 * c + 3] = __fmaf_rn(w, g.w, acc[4 * c + 3]);
+                for (int n = 0; n < NT; ++n) {
+                    const int col = nh * (DQ / 2) + 8 * n;
+                    uint32_t bh[2], bl[2];
+                    ldsm_x2_trans(smem_addr(dq_hi + (size_t)(16 * kt + br) * DQS + col), bh);
+                    ldsm_x2_trans(smem_addr(dq_lo + (size_t)(16 * kt + br) * DQS + col), bl);
+                    mma_bf16_16816(acc[n], ah, bh);
+                    mma_bf16_16816(acc[n], ah, bl);
+                    mma_bf16_16816(acc[n], al, bh);
                 }
             }
-        }
-        __syncthreads();  // W is read; its space takes the partial sums
+            // 3. one atomic per non-zero (Gaussian, channel) of the tile
+            const int g0 = 16 * mt + (lane >> 2);
 #pragma unroll
-        for (int c = 0; c < DQ; ++c) s_part[((size_t)q * DQ + c) * kWStride + jj] = acc[c];
-        __syncthreads();
-        // 3. quarters added in order; one atomic per non-zero (Gaussian, channel) of the tile
-        for (int o = t; o < kBwdBatch * DQ; o += kTilePixels) {
-            const int j = o / DQ, c = o % DQ;
-            if (j >= cnt) break;
-            float s = 0.f;
+            for (int n = 0; n < NT; ++n) {
+                const int c = nh * (DQ / 2) + 8 * n + 2 * (lane & 3);
 #pragma unroll
-            for (int k = 0; k < kBwdQuarters; ++k) s += s_part[((size_t)k * DQ + c) * kWStride + j];
-            if (s != 0.0f) atomicAdd(&df[(size_t)s_id[j] * DQ + c], s);
+                for (int h = 0; h < 2; ++h) {
+                    const int g = g0 + 8 * h;
+                    if (g >= cnt) continue;
+                    float* dst = job.df + (size_t)s_id[g] * DQ + c;
+                    if (acc[n][2 * h] != 0.0f) atomicAdd(dst, acc[n][2 * h]);
+                    if (acc[n][2 * h + 1] != 0.0f) atomicAdd(dst + 1, acc[n][2 * h + 1]);
+                }
+            }
         }
         // the next batch's staging and W writes come after the barrier at the loop head
     }
