@@ -15,9 +15,7 @@
 namespace lat {
 namespace {
 
-// bf16 per row of a weight matrix W^T (Gaussians x the tile's pixels) staged for the tensor
-// cores: 528 B, so that the eight rows an ldmatrix reads fall on distinct banks
-constexpr int kWtStride = kTilePixels + 8;
+constexpr int kBatch = kTilePixels;  // 256 Gaussians staged per round
 
 // Staged form of one splat: exponent coefficients q = (-a/2, -b, -c/2, opacity) of the conic
 // (a, b, c).
@@ -34,32 +32,6 @@ __device__ __forceinline__ void tc_split(float x0, float x1, uint32_t& hi, uint3
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Warp-level tensor-core helpers of the per-tile contractions (ldmatrix, mma.sync BF16).
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr));
-}
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t (&r)[4]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr));
-}
-__device__ __forceinline__ void ldsm_x2_trans(uint32_t addr, uint32_t (&r)[2]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
-}
-// c += a b, m16n8k16, BF16 operands, FP32 accumulators
-__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
 // alpha of a splat at a pixel centre, or -1 when the exponent is positive.  Every rounding
 // is explicit (fused multiply-adds written out), so the forward and backward kernels take
 // bit-identical decisions for the same inputs.
@@ -70,138 +42,67 @@ __device__ __forceinline__ float splat_alpha(float2 m, float4 q, float px, float
     return fminf(kAlphaMax, __fmul_rn(q.w, __expf(power)));
 }
 
-// Front-to-back blend of one tile (256 threads, one pixel each) in rounds of kFwdBatch Gaussians:
-// the pixel threads take each Gaussian's weight w_ip = alpha_ip T_ip in order (skipping alpha <
-// 1/255, stopping before the contribution that would take T below 1e-4) into a shared-memory
-// matrix W^T (Gaussians x pixels) as BF16 hi + lo terms, and the round's queries are staged the
-// same way; then warp w adds W f for its 32 pixels with mma.sync m16n8k16 (three products, FP32
-// accumulators held across the rounds).
-constexpr int kFwdBatch = 64;
-
 template <int DQ>
-constexpr size_t render_fwd_smem() {
-    return 2 * sizeof(__nv_bfloat16) * (size_t)kFwdBatch * kWtStride +
-           2 * sizeof(__nv_bfloat16) * (size_t)kFwdBatch * (DQ + 8) + (sizeof(float4) + sizeof(float2)) * kFwdBatch;
-}
+struct FwdSmem {
+    float2 xy[kBatch];
+    float4 co[kBatch];
+    float4 f[kBatch][DQ / 4];
+};
 
+// Front-to-back blend of one tile (256 threads, one pixel each).
 template <int DQ>
-__device__ __forceinline__ void render_fwd_tile(const TileJob& job, float4* smem) {
+__device__ __forceinline__ void render_fwd_tile(const TileJob& job, FwdSmem<DQ>& sm) {
     constexpr int DV = DQ / 4;
-    constexpr int FS = DQ + 8;   // bf16 per staged query row
-    constexpr int NT = DQ / 8;   // n-tiles of 8 channels
-    using bf16 = __nv_bfloat16;
-    bf16* wt_hi = reinterpret_cast<bf16*>(smem);  // [Gaussian][pixel]
-    bf16* wt_lo = wt_hi + (size_t)kFwdBatch * kWtStride;
-    bf16* f_hi = wt_lo + (size_t)kFwdBatch * kWtStride;  // [Gaussian][channel]
-    bf16* f_lo = f_hi + (size_t)kFwdBatch * FS;
-    float4* s_co = reinterpret_cast<float4*>(f_lo + (size_t)kFwdBatch * FS);
-    float2* s_xy = reinterpret_cast<float2*>(s_co + kFwdBatch);
-    static_assert(((size_t)kFwdBatch * kWtStride * 4 + (size_t)kFwdBatch * FS * 4) % 16 == 0, "aligned staging");
-
     const int tile = job.tile;
     const int tx = tile % job.tiles_x, ty = tile / job.tiles_x;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x;
     const int px = tx * kTile + (t % kTile), py = ty * kTile + (t / kTile);
     const bool inside = px < job.W && py < job.H;
     const float fpx = (float)px, fpy = (float)py;
     const int2 range = job.ranges[tile];
-    float acc[2][NT][4];
+    float4 acc[DV];
 #pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int n = 0; n < NT; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
+    for (int k = 0; k < DV; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     float T = 1.0f;
     int count = 0;
     bool done = !inside;
-    for (int start = range.x; start < range.y; start += kFwdBatch) {
+    for (int start = range.x; start < range.y; start += kBatch) {
         if (__syncthreads_count(done) == kTilePixels) break;
-        const int cnt = min(kFwdBatch, range.y - start);
-        if (t < kFwdBatch) {
-            // the round's splats and query rows (rows past the round are zero: 0 x stale is not 0)
-            float4 v[DV];
-            if (t < cnt) {
-                const int g = job.pair_ids[start + t];
-                s_xy[t] = job.xy[g];
-                s_co[t] = stage_splat(job.conic_opac[g]);
+        const int k = start + t;
+        if (k < range.y) {
+            const int g = job.pair_ids[k];
+            sm.xy[t] = job.xy[g];
+            sm.co[t] = stage_splat(job.conic_opac[g]);
 #pragma unroll
-                for (int c = 0; c < DV; ++c) v[c] = job.f[(size_t)g * DV + c];
-            } else {
-#pragma unroll
-                for (int c = 0; c < DV; ++c) v[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < DV; ++c) sm.f[t][c] = job.f[(size_t)g * DV + c];
+        }
+        __syncthreads();
+        const int cnt = min(kBatch, range.y - start);
+        for (int j = 0; j < cnt && !done; ++j) {
+            const float alpha = splat_alpha(sm.xy[j], sm.co[j], fpx, fpy);
+            if (alpha < kAlphaMin) continue;
+            const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+            if (test_T < kTMin) {
+                done = true;
+                break;
             }
+            const float w = __fmul_rn(alpha, T);
 #pragma unroll
             for (int c = 0; c < DV; ++c) {
-                uint32_t h0, l0, h1, l1;
-                tc_split(v[c].x, v[c].y, h0, l0);
-                tc_split(v[c].z, v[c].w, h1, l1);
-                *reinterpret_cast<uint2*>(f_hi + (size_t)t * FS + 4 * c) = make_uint2(h0, h1);
-                *reinterpret_cast<uint2*>(f_lo + (size_t)t * FS + 4 * c) = make_uint2(l0, l1);
+                const float4 v = sm.f[j][c];
+                acc[c].x += w * v.x;
+                acc[c].y += w * v.y;
+                acc[c].z += w * v.z;
+                acc[c].w += w * v.w;
             }
-        }
-        __syncthreads();
-        // 1. this pixel's weights for the round, front to back
-        for (int j = 0; j < kFwdBatch; ++j) {
-            float w = 0.0f;
-            if (j < cnt && !done) {
-                const float alpha = splat_alpha(s_xy[j], s_co[j], fpx, fpy);
-                if (alpha >= kAlphaMin) {
-                    const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                    if (test_T < kTMin) {
-                        done = true;
-                    } else {
-                        w = __fmul_rn(alpha, T);
-                        T = test_T;
-                        ++count;
-                    }
-                }
-            }
-            const bf16 wh = __float2bfloat16_rn(w);
-            wt_hi[(size_t)j * kWtStride + t] = wh;
-            wt_lo[(size_t)j * kWtStride + t] = __float2bfloat16_rn(w - __bfloat162float(wh));
-        }
-        __syncthreads();
-        // 2. warp w: Q rows of pixels 32 w .. 32 w + 31 += W f
-#pragma unroll
-        for (int kt = 0; kt < kFwdBatch / 16; ++kt) {
-            if (16 * kt >= cnt) break;  // block-uniform
-            const int ar = 16 * kt + (lane & 7) + ((lane >> 4) << 3);  // stored W^T row (Gaussian)
-            uint32_t ah[2][4], al[2][4];
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const int ac = 32 * warp + 16 * m + ((lane >> 3) & 1) * 8;  // stored column (pixel)
-                ldsm_x4_trans(smem_addr(wt_hi + (size_t)ar * kWtStride + ac), ah[m]);
-                ldsm_x4_trans(smem_addr(wt_lo + (size_t)ar * kWtStride + ac), al[m]);
-            }
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                uint32_t bh[2], bl[2];
-                ldsm_x2_trans(smem_addr(f_hi + (size_t)(16 * kt + (lane & 15)) * FS + 8 * n), bh);
-                ldsm_x2_trans(smem_addr(f_lo + (size_t)(16 * kt + (lane & 15)) * FS + 8 * n), bl);
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    mma_bf16_16816(acc[m][n], ah[m], bh);
-                    mma_bf16_16816(acc[m][n], ah[m], bl);
-                    mma_bf16_16816(acc[m][n], al[m], bh);
-                }
-            }
+            T = test_T;
+            ++count;
         }
     }
-    // this thread's accumulators: pixels 32 w + 16 m + lane / 4 (+ 8), channels 8 n + 2 (lane % 4)
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int p = 32 * warp + 16 * m + (lane >> 2) + 8 * h;
-            const int qx = tx * kTile + (p % kTile), qy = ty * kTile + (p / kTile);
-            if (qx >= job.W || qy >= job.H) continue;
-            float* row = reinterpret_cast<float*>(job.Q) + ((size_t)qy * job.W + qx) * DQ;
-#pragma unroll
-            for (int n = 0; n < NT; ++n)
-                *reinterpret_cast<float2*>(row + 8 * n + 2 * (lane & 3)) =
-                    make_float2(acc[m][n][2 * h], acc[m][n][2 * h + 1]);
-        }
     if (inside) {
         const size_t p = (size_t)py * job.W + px;
+#pragma unroll
+        for (int c = 0; c < DV; ++c) job.Q[p * DV + c] = acc[c];
         job.T_final[p] = T;
         job.n_contrib[p] = count;
     }
@@ -215,11 +116,11 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(CamParams cam, 
                                                                  const float4* __restrict__ f, float4* __restrict__ Q,
                                                                  float* __restrict__ T_final,
                                                                  int32_t* __restrict__ n_contrib) {
-    extern __shared__ float4 smem_f4[];
+    __shared__ FwdSmem<DQ> sm;
     const int tile = cam.tile_order ? cam.tile_order[blockIdx.x] : (int)blockIdx.x;
     const TileJob job{tile, cam.tiles_x, cam.W, cam.H, ranges, pair_ids, xy, conic_opac, f, Q, T_final, n_contrib,
                       nullptr, nullptr};
-    render_fwd_tile<DQ>(job, smem_f4);
+    render_fwd_tile<DQ>(job, sm);
 }
 
 // Next (frame, tile) of a batch from the global work list (frame in the top 12 bits), taken in
@@ -239,11 +140,11 @@ template <int DQ>
 __global__ void __launch_bounds__(kTilePixels) render_fwd_batch_kernel(const __grid_constant__ BatchJobs jobs,
                                                                        const int32_t* __restrict__ order, int total,
                                                                        int* __restrict__ counter) {
-    extern __shared__ float4 smem_f4[];
+    __shared__ FwdSmem<DQ> sm;
     for (int item = next_item(counter, order, total); item >= 0; item = next_item(counter, order, total)) {
         TileJob job = jobs.fr[item >> 20];
         job.tile = item & 0xFFFFF;
-        render_fwd_tile<DQ>(job, smem_f4);
+        render_fwd_tile<DQ>(job, sm);
     }
 }
 
@@ -275,6 +176,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
 // of 64 x 256 x d does not amortise TMEM allocation and completion waits; the warp-level MMA
 // runs in the registers of the warps that computed the weights.
 constexpr int kBwdBatch = 64;
+constexpr int kWtStride = kTilePixels + 8;  // bf16 per W^T row (528 B: ldmatrix rows on distinct banks)
 
 template <int DQ>
 constexpr int dq_stride() {
@@ -287,6 +189,26 @@ constexpr size_t render_bwd_smem() {
     return 2 * sizeof(__nv_bfloat16) * (size_t)kBwdBatch * kWtStride +
            2 * sizeof(__nv_bfloat16) * (size_t)kTilePixels * dq_stride<DQ>() +
            (sizeof(float4) + sizeof(float2) + sizeof(int)) * kBwdBatch;
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t addr, uint32_t (&r)[2]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+// c += a b, m16n8k16, BF16 operands, FP32 accumulators
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
 // Backward of one tile (256 threads); smem is the dynamic shared memory of render_bwd_smem.
@@ -672,17 +594,7 @@ template <int DQ>
 latentam_status render_fwd_t(const CamParams& cam, const latentam_projected& proj, const latentam_bins& bins,
                              const float* f, float* Q, float* T_final, int32_t* n_contrib, cudaStream_t st) {
     const int tiles = cam.tiles_x * cam.tiles_y;
-    constexpr size_t smem = render_fwd_smem<DQ>();
-    auto kern = render_fwd_kernel<DQ>;
-    static unsigned long long attr_set = 0;  // per instantiation and device
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (!(attr_set & (1ull << (dev & 63)))) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_error(e, "render forward smem attribute");
-        attr_set |= 1ull << (dev & 63);
-    }
-    kern<<<tiles, kTilePixels, smem, st>>>(
+    render_fwd_kernel<DQ><<<tiles, kTilePixels, 0, st>>>(
         cam, reinterpret_cast<const int2*>(bins.tile_ranges), bins.pair_ids, reinterpret_cast<const float2*>(proj.xy),
         reinterpret_cast<const float4*>(proj.conic_opacity), reinterpret_cast<const float4*>(f),
         reinterpret_cast<float4*>(Q), T_final, n_contrib);
@@ -795,17 +707,8 @@ int persistent_grid(Kernel kern, size_t smem, int total) {
 template <int DQ>
 latentam_status render_fwd_batch_t(const BatchJobs& jobs, const int32_t* order, int total, int* counter,
                                    cudaStream_t st) {
-    constexpr size_t smem = render_fwd_smem<DQ>();
     auto kern = render_fwd_batch_kernel<DQ>;
-    static unsigned long long attr_set = 0;  // per instantiation and device
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (!(attr_set & (1ull << (dev & 63)))) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_error(e, "batched render forward smem attribute");
-        attr_set |= 1ull << (dev & 63);
-    }
-    kern<<<persistent_grid(kern, smem, total), kTilePixels, smem, st>>>(jobs, order, total, counter);
+    kern<<<persistent_grid(kern, 0, total), kTilePixels, 0, st>>>(jobs, order, total, counter);
     LAT_CHECK_LAUNCH("render_fwd_batch_kernel");
     return LATENTAM_OK;
 }
