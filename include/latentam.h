@@ -35,8 +35,9 @@
  *    alpha < 1/255 skipped, blending stops before a contribution that would take the
  *    transmittance below 1e-4; pixel centres at integer coordinates; 16x16 tiles; a
  *    Gaussian's tile rectangle is the axis-aligned box of its alpha >= 1/255 ellipse.
- *  - front-to-back order: the camera depth of the mean, evaluated in double precision as
- *    ((R20 x + R21 y) + R22 z) + t2 and rounded to binary32, ascending; ties by index.
+ *  - front-to-back order: the camera depth of the mean, evaluated in binary32 with every
+ *    operation rounded as ((R20 x + R21 y) + R22 z) + t2 (no fused multiply-add), ascending;
+ *    ties by index; the near-plane test compares that key with z_near.
  *  - Gaussians with depth <= z_near or opacity < 1/255 are culled; an uncovered pixel
  *    renders Q_p = 0.
  *  - decode with free keys K (M x d) and values V (M x D), logit scale c (1/sqrt(d) by

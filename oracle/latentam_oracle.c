@@ -17,9 +17,10 @@
  *     (or a positive exponent) is skipped; blending stops before a contribution that
  *     would take the transmittance below 1e-4; near plane z = 0.2 (camera field).
  *  R2 pixel centres sit at integer coordinates (x, y).
- *  R3 front-to-back order: camera-space depth (evaluated in double precision, products
- *     and sums in the order written in orc_project) rounded to binary32 is the sort key;
- *     equal keys are ordered by Gaussian index.  The order is thereby an exact function
+ *  R3 front-to-back order: the camera-space depth of the mean evaluated in binary32, every
+ *     product and sum rounded to binary32 in the order ((R20 x + R21 y) + R22 z) + t2, is
+ *     the sort key, and the near-plane test compares it with the binary32 z_near; equal keys
+ *     are ordered by Gaussian index.  The order is thereby an exact function
  *     of the inputs, identical for every implementation that evaluates the key the same way.
  *  R4 an uncovered pixel renders Q_p = 0 (no background query).
  *  R5 decode with free keys K (M x d) and values V (M x D): S = c Q K^T, row softmax
@@ -55,7 +56,18 @@ static const double AMB_TOL_T = 1e-3;
 /* Same idea for the tile rectangle edges (pixels). */
 static const double RECT_TOL_PX = 1e-3;
 
-/* Sort key of reading R3. */
+/* Sort key of reading R3: the camera depth of the mean in binary32, every operation rounded
+ * to binary32 in the order ((R20 x + R21 y) + R22 z) + t2 (this file is compiled without FMA
+ * contraction).  The camera and the means are binary32 values held in doubles. */
+static float depth_key32(const double* W, const double* p, double t2) {
+    const float a = (float)W[6] * (float)p[0];
+    const float b = (float)W[7] * (float)p[1];
+    const float c = (float)W[8] * (float)p[2];
+    const float ab = a + b;
+    const float abc = ab + c;
+    return abc + (float)t2;
+}
+/* The key as the lists use it: binary32 (depth[] from orc_project already holds binary32 values). */
 static double depth_key(double z) { return (double)(float)z; }
 
 /* ------------------------------------------------------------------------------------ */
@@ -101,13 +113,14 @@ void orc_project(int64_t N, const double* means, const double* quats, const doub
         double y = W[3] * p[0] + W[4] * p[1] + W[5] * p[2] + cam->t[1];
         double z = W[6] * p[0] + W[7] * p[1] + W[8] * p[2] + cam->t[2];
         double o = opacities[i];
-        depth[i] = z;
+        const float zk = depth_key32(W, p, cam->t[2]);
+        depth[i] = (double)zk;
         visible[i] = 0;
         rect_ambiguous[i] = 0;
         for (int k = 0; k < 4; ++k) rect[4 * i + k] = 0;
         for (int k = 0; k < 3; ++k) cov2d[3 * i + k] = conic[3 * i + k] = 0.0;
         xy[2 * i] = xy[2 * i + 1] = extent[2 * i] = extent[2 * i + 1] = 0.0;
-        if (!(z > cam->z_near) || o < ALPHA_MIN) continue;
+        if (!(zk > (float)cam->z_near) || o < ALPHA_MIN) continue;
 
         /* Rotation of the primitive from its unit quaternion q = (w, x, y, z). */
         const double* q = quats + 4 * i;

@@ -31,18 +31,17 @@ __global__ void __launch_bounds__(256) project_kernel(int N, const float* __rest
     if (i >= N) return;
     const float px = means[3 * i], py = means[3 * i + 1], pz = means[3 * i + 2];
     const float o = opac[i];
-    // Depth sort key: evaluated in double with every rounding explicit, then rounded to
-    // binary32, so the front-to-back order is an exact function of the inputs.
-    const double zd = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)cam.R[6], (double)px),
-                                                    __dmul_rn((double)cam.R[7], (double)py)),
-                                          __dmul_rn((double)cam.R[8], (double)pz)),
-                                (double)cam.t[2]);
-    const float z = (float)zd;
+    // Depth sort key: evaluated in binary32 with every rounding explicit (no contraction into
+    // fused multiply-adds), so the front-to-back order is an exact function of the inputs.
+    const float z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cam.R[6], px), __fmul_rn(cam.R[7], py)),
+                                        __fmul_rn(cam.R[8], pz)),
+                              cam.t[2]);
     depth_out[i] = z;
     int4 rect = make_int4(0, 0, 0, 0);
     float2 xy = make_float2(0.f, 0.f);
     float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool vis = (zd > (double)cam.z_near) && !((double)o < 1.0 / 255.0);
+    // o < 1/255 for a binary32 o is o < bf(1/255), the nearest binary32 (above 1/255)
+    bool vis = (z > cam.z_near) && !(o < kAlphaMin);
     if (vis) {
         const float x = cam.R[0] * px + cam.R[1] * py + cam.R[2] * pz + cam.t[0];
         const float y = cam.R[3] * px + cam.R[4] * py + cam.R[5] * pz + cam.t[1];
