@@ -505,6 +505,12 @@ struct DsParams {
     const bf16* A;
     const float* row;
     bf16* dS;  // n x M
+    // G4 fused as the trailing product dQ = c dS K (K padded to 64 columns), or dQ == NULL;
+    // dq_add: the CTAs along y (two at most) add their partial rows into a zeroed dQ
+    float* dQ;
+    int d;
+    float c;
+    int dq_add;
 };
 
 // One CTA holds 256 atoms of its rows (M > 256: several CTAs along y, nothing to trade: the
@@ -518,7 +524,29 @@ struct DsEpi {
     static constexpr int MIN_BLOCKS = SPLIT_ ? 1 : 2;
     static constexpr int E_BOXES = BN / 64, O_BOXES = BN / 64;  // dS staged over the attention rows
     static constexpr bool A_MN = false, B_MN = false;
+    static constexpr int XPROD = 64;  // dQ = c dS K on the staged dS tile
     using Params = DsParams;
+    static __device__ bool x_active(const Params& p) { return p.dQ != nullptr; }
+    // dQ rows of this tile from TMEM columns 0 .. d - 1 (the padded columns hold zeros)
+    static __device__ void run_x(const Params& p, const tc::EpiCtx& ec) {
+        const int64_t pix = (int64_t)ec.m0 + ec.row;
+        float v[32];
+        for (int c0 = 32 * ec.g; c0 < p.d; c0 += 32 * EPI_WG) {
+            tc::tmem_ld32(ec.taddr + c0, v);
+            if (pix >= p.n) continue;
+            float4* d4 = reinterpret_cast<float4*>(p.dQ + pix * p.d + c0);
+            const int nq = min(32, p.d - c0) / 4;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q >= nq) break;
+                const float4 u = make_float4(p.c * v[4 * q], p.c * v[4 * q + 1], p.c * v[4 * q + 2], p.c * v[4 * q + 3]);
+                if (p.dq_add)
+                    atomicAdd(d4 + q, u);  // two addends onto zero: the same sum in either order
+                else
+                    d4[q] = u;
+            }
+        }
+    }
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const int64_t pix = (int64_t)ec.m0 + ec.row;
         const bool valid = pix < p.n;
@@ -552,6 +580,7 @@ struct DqEpi {
     static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, O_BOXES = 0, XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
+    static constexpr int XPROD = 0;
     using Params = DqParams;
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
@@ -597,6 +626,7 @@ struct PartEpi {
     static constexpr int XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
+    static constexpr int XPROD = 0;
     using Params = PartParams;
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
 #pragma unroll
@@ -813,7 +843,7 @@ latentam_status u8_map(CUtensorMap* m, const void* base, int64_t inner, int64_t 
 template <class Epi>
 latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 grid, tc::GemmGrid g,
                             const typename Epi::Params& p, int* err, cudaStream_t st, const CUtensorMap* emap = nullptr,
-                            const CUtensorMap* omap = nullptr, int cluster_y = 1) {
+                            const CUtensorMap* omap = nullptr, int cluster_y = 1, const CUtensorMap* xmap = nullptr) {
     constexpr size_t smem = tc::gemm_smem_bytes<Epi>();
     static_assert(smem <= 227 * 1024, "tile does not fit in shared memory");
     if (cluster_y > tc::kMaxCluster || (int)grid.y % cluster_y != 0 || (cluster_y > 1 && Epi::XROUNDS == 0)) {
@@ -843,7 +873,8 @@ latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 gri
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, omap ? *omap : a, g, p, err);
+    cudaError_t e =
+        cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, omap ? *omap : a, xmap ? *xmap : a, g, p, err);
     if (e != cudaSuccess) return cuda_error(e, "tc_gemm_kernel launch");
     LAT_CHECK_LAUNCH("tc_gemm_kernel");
     return LATENTAM_OK;
@@ -968,17 +999,19 @@ tc::GemmGrid pixel_split(int64_t n, int z, int* z_out, int chunk = tc::kChunkK) 
 // The split the tile grid starts from: about one wave of CTAs.
 int wave_split(int tiles_xy, int num_sms) { return std::max(1, (num_sms + tiles_xy - 1) / tiles_xy); }
 
-// Autotuned split of a pixel reduction: the first time a shape (n, M, D, which) is seen
-// outside stream capture, `launch(z)` runs for the wave split, half of it and twice it (one
-// untimed warm-up run first), timed with CUDA events on the stream, and the fastest split is
-// kept in the context.  Returns the split to use.
+// Autotuned launch shape of a pixel reduction: the first time a shape (n, M, D, which) is seen
+// outside stream capture, `launch(shape, z)` runs for every tile shape 0 .. nshapes - 1 with its
+// wave split z0[shape], half of it and twice it (one untimed warm-up run first), timed with CUDA
+// events on the stream, and the fastest (tile shape, split) is kept in the context.
 template <class Launch>
-latentam_status tuned_split(latentam_ctx* ctx, int64_t n, int M, int D, int which, int z0, cudaStream_t st,
-                            Launch&& launch, int* z_out) {
-    *z_out = z0;
+latentam_status tuned_shape(latentam_ctx* ctx, int64_t n, int M, int D, int which, int nshapes, const int* z0,
+                            cudaStream_t st, Launch&& launch, int* shape_out, int* z_out) {
+    *shape_out = 0;
+    *z_out = z0[0];
     for (int i = 0; i < ctx->tune_used; ++i) {
         const auto& t = ctx->tune[i];
         if (t.n == n && t.M == M && t.D == D && t.which == which) {
+            *shape_out = t.shape;
             *z_out = t.z;
             return LATENTAM_OK;
         }
@@ -986,25 +1019,27 @@ latentam_status tuned_split(latentam_ctx* ctx, int64_t n, int M, int D, int whic
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (!ctx->autotune || cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
         return LATENTAM_OK;
-    const int cand[3] = {z0, std::max(1, z0 / 2), 2 * z0};
-    cudaEvent_t ev[4];
+    cudaEvent_t ev[2];
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return cuda_error(cudaGetLastError(), "tuning events");
-    latentam_status s = launch(cand[0]);  // warm-up
+    latentam_status s = launch(0, z0[0]);  // warm-up
     float best = 1e30f;
-    for (int i = 0; i < 3 && s == LATENTAM_OK; ++i) {
-        cudaEventRecord(ev[i], st);
-        s = launch(cand[i]);
-        cudaEventRecord(ev[i + 1], st);
-        cudaEventSynchronize(ev[i + 1]);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
-        if (s == LATENTAM_OK && ms < best) best = ms, *z_out = cand[i];
+    for (int sh = 0; sh < nshapes && s == LATENTAM_OK; ++sh) {
+        const int cand[3] = {z0[sh], std::max(1, z0[sh] / 2), 2 * z0[sh]};
+        for (int i = 0; i < 3 && s == LATENTAM_OK; ++i) {
+            cudaEventRecord(ev[0], st);
+            s = launch(sh, cand[i]);
+            cudaEventRecord(ev[1], st);
+            cudaEventSynchronize(ev[1]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (s == LATENTAM_OK && ms < best) best = ms, *shape_out = sh, *z_out = cand[i];
+        }
     }
     for (auto& e : ev) cudaEventDestroy(e);
     LAT_TRY(s);
     auto& t = ctx->tune[ctx->tune_next];
-    t = latentam_ctx::TuneEntry{n, M, D, which, *z_out};
+    t = latentam_ctx::TuneEntry{n, M, D, which, *shape_out, *z_out, best};
     ctx->tune_next = (ctx->tune_next + 1) % 32;
     if (ctx->tune_used < 32) ++ctx->tune_used;
     return LATENTAM_OK;
@@ -1133,11 +1168,17 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
                                               b.acc);
     LAT_CHECK_LAUNCH("tc_trust_region");
     constexpr int BNq = kPad;  // queries padded to 64 columns
-    using EpiV = PartEpi<256, SPLIT, 2>;  // dV: 256 atoms per CTA, each dFhat block read once for both halves
-    const int tilesV = cdiv(M, 2 * kTileM) * cdiv(D, 256), tilesK = cdiv(M, kTileM);
-    const int zV0 = wave_split(tilesV, ctx->num_sms), zK0 = wave_split(tilesK, ctx->num_sms);
+    // dV tile shapes: 0 = 256 atoms per CTA (two accumulators: each dFhat block read once for
+    // both halves), 1 = 128 atoms per CTA (twice the CTAs, each dFhat block read twice)
+    using EpiV = PartEpi<256, SPLIT, 2>;
+    using EpiV1 = PartEpi<256, SPLIT, 1>;
+    const int tilesV[2] = {cdiv(M, 2 * kTileM) * cdiv(D, 256), cdiv(M, kTileM) * cdiv(D, 256)};
+    const int tilesK = cdiv(M, kTileM);
+    const int zV0[2] = {wave_split(tilesV[0], ctx->num_sms), wave_split(tilesV[1], ctx->num_sms)};
+    const int zK0 = wave_split(tilesK, ctx->num_sms);
     // partial sums for the largest split a tuner may try
-    const size_t part_floats = std::max((size_t)2 * zV0 * M * D, (size_t)2 * zK0 * M * BNq);
+    const size_t part_floats = std::max({(size_t)2 * zV0[0] * M * D, (size_t)2 * zV0[1] * M * D,
+                                         (size_t)2 * zK0 * M * BNq});
     b.part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * part_floats));
     if (!b.part) return LATENTAM_ERR_OUT_OF_MEMORY;
     const int which = SPLIT ? 16 : 0;  // autotuner key offset of the split form
@@ -1151,18 +1192,25 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
         CUtensorMap mdF, mV, mdS, mK;
         LAT_TRY(op_map(SPLIT, &mdF, b.dF, D, n, D, kTileM));
         LAT_TRY(op_map(SPLIT, &mV, b.Vb, D, M, D, 256));
-        DsParams dp{n, M, b.A, b.row, b.dS};
+        // G4 (dQ = c dS K, B = K padded, read MN-major) runs as G3's trailing product on the
+        // staged dS tile when a row's atoms span at most two CTAs, else as its own GEMM
+        const int ty = cdiv(M, 256);
+        const bool dq_fused = a.dQ != nullptr && ty <= 2;
+        if (a.dQ) LAT_TRY(mn_map(SPLIT, &mK, b.Kb, kPad, M, kPad, 64, kPad / 64));
+        if (dq_fused && ty > 1) {
+            e = cudaMemsetAsync(a.dQ, 0, sizeof(float) * (size_t)n * d, st);
+            if (e != cudaSuccess) return cuda_error(e, "memset dQ");
+        }
+        DsParams dp{n, M, b.A, b.row, b.dS, dq_fused ? a.dQ : nullptr, d, a.c, ty > 1 ? 1 : 0};
         const dim3 grow(cdiv(n, kTileM), 1, 1);
         const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
         CUtensorMap mAe, mdSo;  // attention rows for the epilogue, dS out through the TMA
         LAT_TRY(io_map(SPLIT, &mAe, b.A, M, n, M, kTileM));
         LAT_TRY(io_map(SPLIT, &mdSo, b.dS, M, n, M, kTileM));
-        LAT_TRY((launch_gemm<DsEpi<SPLIT>>(mdF, mV, dim3(cdiv(n, kTileM), cdiv(M, 256), 1), g3, dp, b.err, st,
-                                           &mAe, &mdSo)));
-        // G4: dQ = c dS K, B = K padded read MN-major (queries x atoms)
-        if (a.dQ) {
+        LAT_TRY((launch_gemm<DsEpi<SPLIT>>(mdF, mV, dim3(cdiv(n, kTileM), ty, 1), g3, dp, b.err, st, &mAe, &mdSo, 1,
+                                           dq_fused ? &mK : nullptr)));
+        if (a.dQ && !dq_fused) {
             LAT_TRY(op_map(SPLIT, &mdS, b.dS, M, n, M, kTileM));
-            LAT_TRY(mn_map(SPLIT, &mK, b.Kb, kPad, M, kPad, 64, kPad / 64));
             DqParams qp{n, d, a.c, a.dQ};
             const tc::GemmGrid g4{cdiv(M, tc::kChunkK), cdiv(M, tc::kChunkK)};
             LAT_TRY((launch_gemm<DqEpi<BNq, SPLIT>>(mdS, mK, grow, g4, qp, b.err, st)));
@@ -1172,19 +1220,26 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
     int zV = 0, zK = 0;
     if (a.dV) {
         if (n > 0) {
-            CUtensorMap mA, mdF;
-            LAT_TRY(io_map(SPLIT, &mA, b.A, M, n, M, EpiV::BKC));
-            LAT_TRY(mn_map(SPLIT, &mdF, b.dF, D, n, D, EpiV::BKC, 256 / 64));
+            CUtensorMap mA[2], mdF[2];  // per tile shape (pixel block of a ring stage: BKC)
+            LAT_TRY(io_map(SPLIT, &mA[0], b.A, M, n, M, EpiV::BKC));
+            LAT_TRY(mn_map(SPLIT, &mdF[0], b.dF, D, n, D, EpiV::BKC, 256 / 64));
+            LAT_TRY(io_map(SPLIT, &mA[1], b.A, M, n, M, EpiV1::BKC));
+            LAT_TRY(mn_map(SPLIT, &mdF[1], b.dF, D, n, D, EpiV1::BKC, 256 / 64));
             PartParams pp{M, D, D, b.part};
-            auto g5 = [&](int z) -> latentam_status {
+            auto g5 = [&](int shape, int z) -> latentam_status {
                 int zz;
-                const tc::GemmGrid g = pixel_split(n, z, &zz, EpiV::BKC);
-                return launch_gemm<EpiV>(mA, mdF, dim3(cdiv(M, 2 * kTileM), cdiv(D, 256), zz), g, pp, b.err, st);
+                if (shape == 0) {
+                    const tc::GemmGrid g = pixel_split(n, z, &zz, EpiV::BKC);
+                    return launch_gemm<EpiV>(mA[0], mdF[0], dim3(cdiv(M, 2 * kTileM), cdiv(D, 256), zz), g, pp, b.err,
+                                             st);
+                }
+                const tc::GemmGrid g = pixel_split(n, z, &zz, EpiV1::BKC);
+                return launch_gemm<EpiV1>(mA[1], mdF[1], dim3(cdiv(M, kTileM), cdiv(D, 256), zz), g, pp, b.err, st);
             };
-            int z;
-            LAT_TRY(tuned_split(ctx, n, M, D, 5 + which, zV0, st, g5, &z));
-            LAT_TRY(g5(z));
-            pixel_split(n, z, &zV, EpiV::BKC);
+            int shape, z;
+            LAT_TRY(tuned_shape(ctx, n, M, D, 5 + which, 2, zV0, st, g5, &shape, &z));
+            LAT_TRY(g5(shape, z));
+            pixel_split(n, z, &zV, shape == 0 ? EpiV::BKC : EpiV1::BKC);
         }
         tc_reduce_parts<<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, n > 0 ? zV : 0, M, D, D, 1.0f, b.coef, a.V,
                                                                   a.V0, a.dV);
@@ -1197,14 +1252,14 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
             LAT_TRY(io_map(SPLIT, &mdS, b.dS, M, n, M, 64));
             LAT_TRY(mn_map(SPLIT, &mQ, b.Qb, kPad, n, kPad, 64, kPad / 64));
             PartParams pp{M, BNq, BNq, b.part};
-            auto g6 = [&](int z) -> latentam_status {
+            auto g6 = [&](int, int z) -> latentam_status {
                 int zz;
                 const tc::GemmGrid g = pixel_split(n, z, &zz);
                 return launch_gemm<PartEpi<BNq, SPLIT>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zz), g, pp, b.err, st);
             };
-            int z;
-            LAT_TRY(tuned_split(ctx, n, M, D, 6 + which, zK0, st, g6, &z));
-            LAT_TRY(g6(z));
+            int shape, z;
+            LAT_TRY(tuned_shape(ctx, n, M, D, 6 + which, 1, &zK0, st, g6, &shape, &z));
+            LAT_TRY(g6(0, z));
             pixel_split(n, z, &zK);
         }
         tc_reduce_parts<<<cdiv((int64_t)M * d, 32), 256, 0, st>>>(b.part, n > 0 ? zK : 0, M, BNq, d, a.c, nullptr,

@@ -39,15 +39,23 @@ __host__ __device__ constexpr int planes() {
     return Epi::SPLIT ? 2 : 1;
 }
 
+// One-tile kernel with a trailing product (Epi::XPROD > 0): the B operand of that product,
+// BN (K) x XPROD (N) BF16 per plane, stored MN-major as BN / 64 boxes of 64 x 64.
+template <class Epi>
+__host__ __device__ constexpr uint32_t xprod_bytes() {
+    return Epi::XPROD > 0 ? (uint32_t)(Epi::BN / 64) * planes<Epi>() * 64u * 64u * 2u : 0u;
+}
+
 // Shared memory at the start of the tile: the operand pipeline, reused once the MMAs are done
 // for the epilogue operand (E_BOXES boxes of 64 x 128 BF16 per plane) and the staged output
-// (O_BOXES per plane).
+// (O_BOXES per plane), then the trailing product's B operand.
 template <class Epi>
 __host__ __device__ constexpr uint32_t tile_region_bytes() {
     const uint32_t pipe = (uint32_t)Epi::STAGES * planes<Epi>() *
                           ((uint32_t)Epi::MSUB * kTileM + (uint32_t)Epi::BN) * Epi::BKC * 2;
     const uint32_t boxes =
-        (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * planes<Epi>() * kTileABytes;
+        (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * planes<Epi>() * kTileABytes +
+        xprod_bytes<Epi>();
     return pipe > boxes ? pipe : boxes;
 }
 
@@ -127,7 +135,12 @@ struct GemmGrid {
 // EpiCtx::put32 (CTA-uniform; stored to tmO at (n0 + 64 b, m0) by TMA); static constexpr int
 // O_BOXES (boxes the epilogue may stage, 0 for none); static constexpr int XROUNDS (0 or 1: run() calls EpiCtx::exchange exactly
 // that many times, whatever the CTA's rows hold), MIN_SMEM (bytes of shared memory to request
-// at least) and MIN_BLOCKS (CTAs per SM the register allocation must allow).
+// at least) and MIN_BLOCKS (CTAs per SM the register allocation must allow).  One-tile kernel
+// only: static constexpr int XPROD (0, or the N = 64 of a trailing product: once the output
+// tile is staged, its 128 x BN BF16 values, K-major as staged, are multiplied on the tensor
+// cores by a BN x 64 operand tmX (MN-major, rows n0 .. n0 + BN) into TMEM columns 0 .. 63,
+// after which static __device__ void run_x(const Params&, const EpiCtx&) reads them; static
+// __device__ bool x_active(const Params&) says, CTA-uniformly, whether this launch takes it).
 struct EpiCtx {
     uint32_t taddr;        // TMEM address of this thread's row, column 0
     int row, m0, n0, z;    // tile row owned by this thread, tile origin, K split
@@ -303,8 +316,8 @@ __device__ __forceinline__ void tma_store(const CUtensorMap* map, const void* sr
 template <class Epi>
 __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmO, GemmGrid g,
-                   typename Epi::Params ep,
+                   const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmO,
+                   const __grid_constant__ CUtensorMap tmX, GemmGrid g, typename Epi::Params ep,
                    int* __restrict__ err) {
     constexpr int BN = Epi::BN;
     constexpr int STAGES = Epi::STAGES;
@@ -332,6 +345,14 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     static_assert(E_BOXES * PL <= 8 && Epi::O_BOXES * PL <= 8, "at most 8 boxes of epilogue operand / output");
     static_assert(!SPLIT || B_MN || BOX_B == BN, "a split K-major B tile is one box");
     static_assert(Epi::XROUNDS == 0, "row exchanges run in the persistent form");
+    // trailing product: staged output (K-major, 64 columns per box) x tmX (MN-major 64 x 64 boxes)
+    constexpr int XN = Epi::XPROD;
+    constexpr uint32_t X_BOX = 64u * 64u * 2u;  // one 64 (N) x 64 (K) box per plane
+    constexpr uint32_t X_OFF = (uint32_t)(E_BOXES > Epi::O_BOXES ? E_BOXES : Epi::O_BOXES) * PL * kTileABytes;
+    static_assert(XN == 0 || (XN == 64 && MSUB == 1 && !A_MN && Epi::O_BOXES * 64 == BN && BN <= 256 &&
+                              X_OFF + xprod_bytes<Epi>() <= TILE_REGION),
+                  "a trailing product multiplies the whole staged tile by a 64-column operand");
+    constexpr uint32_t XDESC = idesc_bf16(kTileM, XN > 0 ? XN : 64, false, true);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -342,7 +363,13 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* decision = abort_flag + 1;
     uint64_t* ebar = reinterpret_cast<uint64_t*>(tmem_slot + 4);  // 8-byte aligned, 8 barriers
+    uint64_t* x_loaded = ebar + 8;  // trailing product: its B operand arrived
+    uint64_t* x_staged = ebar + 9;  //   the staged output is complete
+    uint64_t* x_done = ebar + 10;   //   its MMAs have completed
     float* scratch = reinterpret_cast<float*>(smem + TILE_REGION + 256);
+    static_assert(STAGES * 16 + 8 + 16 + 11 * 8 <= 256, "barriers fit their 256 bytes");
+    bool x_on = false;
+    if constexpr (XN > 0) x_on = Epi::x_active(ep);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * MSUB * kTileM;
@@ -358,6 +385,11 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
         }
         mbar_init(accum, 1);
         for (int b = 0; b < E_BOXES; ++b) mbar_init(&ebar[b], 1);
+        if (XN > 0) {
+            mbar_init(x_loaded, 1);
+            mbar_init(x_staged, 1);
+            mbar_init(x_done, 1);
+        }
         *abort_flag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmA);
@@ -435,7 +467,19 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                             tma_load(smem + (z * E_BOXES + b) * (kTileM * 128), &tmE, &ebar[b], n0 + 64 * b, m0,
                                      SPLIT ? z : -1);
                     }
+                    if (XN > 0 && x_on) {
+                        // the trailing product's B rows n0 .. n0 + BN (both planes per box when split)
+                        mbar_expect_tx(x_loaded, xprod_bytes<Epi>());
+                        for (int c = 0; c < BN / 64; ++c) {
+                            uint8_t* dst = smem + X_OFF + c * PL * X_BOX;
+                            if (SPLIT)
+                                tma_load_4d(dst, &tmX, x_loaded, 0, n0 + 64 * c, 0, 0);
+                            else
+                                tma_load_2d(dst, &tmX, x_loaded, 0, n0 + 64 * c);
+                        }
+                    }
                     for (int b = 0; b < E_BOXES; ++b) (void)mbar_wait(&ebar[b], 0, nullptr);
+                    if (XN > 0 && x_on) (void)mbar_wait(x_loaded, 0, nullptr);
                 } else {
                     *abort_flag = 1;
                 }
@@ -478,6 +522,28 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
             }
             if (!ok) *abort_flag = 1;
             mma_commit(accum);  // accumulator complete (or the pipeline was abandoned)
+            if (XN > 0 && x_on) {
+                // trailing product into columns 0 .. XN - 1, once the epilogue has read them
+                // (x_staged) and the staged tile and the B operand are in shared memory
+                const bool go = ok && mbar_wait(x_loaded, 0, abort_flag) && mbar_wait(x_staged, 0, abort_flag) &&
+                                !*abort_flag;
+                if (go) {
+                    tc_fence_after();
+                    const uint32_t so = smem_u32(smem);         // staged output, hi plane (then lo)
+                    const uint32_t sx = smem_u32(smem + X_OFF);  // B boxes [c][plane]
+                    constexpr uint32_t OPL = (uint32_t)Epi::O_BOXES * kTileABytes;
+#pragma unroll
+                    for (int c = 0; c < BN / 64; ++c)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t oa = so + (uint32_t)c * kTileABytes + kk * 32;
+                            const uint32_t ob = sx + (uint32_t)c * PL * X_BOX + kk * 16 * 128;
+                            mma_step<SPLIT>(tmem_base, sw128_desc(oa), sw128_desc(oa + OPL), mn128_desc(ob, X_BOX),
+                                            mn128_desc(ob + X_BOX, X_BOX), XDESC, (c > 0 || kk > 0) ? 1u : 0u);
+                        }
+                }
+                mma_commit(x_done);  // at once when nothing was issued
+            }
         }
     } else {
         // ---- epilogue warps ----
@@ -504,13 +570,29 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
             // the staged output tile goes out through the TMA once every epilogue thread wrote
             // its part (coalesced and asynchronous, instead of one row per thread)
             fence_proxy_async();
+            if (XN > 0) tc_fence_before();  // this thread's TMEM reads precede the trailing product
             epi_sync(128 * Epi::EPI_WG);
-            if (threadIdx.x == 64 && out_boxes > 0 && !*abort_flag) {
-                for (int b = 0; b < out_boxes && b < Epi::O_BOXES; ++b)
-                    for (int z = 0; z < PL; ++z)
-                        tma_store(&tmO, smem + (z * Epi::O_BOXES + b) * kTileABytes, n0 + 64 * b, m0, SPLIT ? z : -1);
-                bulk_commit();
-                bulk_wait_read();  // shared memory stays valid until the copies have read it
+            if (threadIdx.x == 64) {
+                if (XN > 0 && x_on) mbar_arrive(x_staged);  // the tile is staged (or abandoned)
+                if (out_boxes > 0 && !*abort_flag) {
+                    for (int b = 0; b < out_boxes && b < Epi::O_BOXES; ++b)
+                        for (int z = 0; z < PL; ++z)
+                            tma_store(&tmO, smem + (z * Epi::O_BOXES + b) * kTileABytes, n0 + 64 * b, m0,
+                                      SPLIT ? z : -1);
+                    bulk_commit();
+                    bulk_wait_read();  // shared memory stays valid until the copies have read it
+                }
+            }
+        }
+        if constexpr (XN > 0) {
+            if (x_on) {
+                if (!mbar_wait(x_done, 0, abort_flag)) *abort_flag = 1;
+                // one CTA-uniform decision again: run_x's TMEM loads are warp-collective
+                epi_sync(128 * Epi::EPI_WG);
+                if (threadIdx.x == 64) *decision = (*decision && out_boxes > 0 && !*abort_flag) ? 1 : 0;
+                epi_sync(128 * Epi::EPI_WG);
+                tc_fence_after();
+                if (*decision) Epi::run_x(ep, ec);
             }
         }
         tc_fence_before();
