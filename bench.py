@@ -405,6 +405,7 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
     ctx_pairs = None
     if full is None:
         ctx_pairs = _pair_counts(ctx, views if views is not None else [scene])
+    tuned = _tune_summary(ctx.autotune_choices())
     ctx.close()
 
     # ---- roofline of the dominant stage (decode + loss + decode backward) -------------------
@@ -417,7 +418,8 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
     if full is not None:
         return {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": int(launches), "e2e": e2e,
                 "keyframes_per_step": n_frames, "roofline": None, "splat_roofline": None, "clocks": clk,
-                "stages_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()}, "dtype": "f32"}
+                "stages_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()}, "dtype": "f32",
+                "autotune": tuned}
     dec_ms, dec_cnt = prof["decode"]
     dec_avg_s = dec_ms / max(dec_cnt, 1) / 1e3
     flops = decode_flops(n, M, D, d)
@@ -456,7 +458,21 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
             "keyframes_per_step": n_frames, "roofline": roof,
             "splat_roofline": _splat_roofline(ctx_pairs, prof, prof_steps, peaks, peak_src, d),
             "clocks": clk, "stages_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
-            "dtype": {api.FP32: "f32", api.FP32_FMA: "f32", api.BF16: "bf16", api.FP8: "bf16+e4m3"}[prec]}
+            "dtype": {api.FP32: "f32", api.FP32_FMA: "f32", api.BF16: "bf16", api.FP8: "bf16+e4m3"}[prec],
+            "autotune": tuned}
+
+
+def _tune_summary(choices):
+    """The autotuner's choices for the pixel reductions of the decode backward, readable."""
+    names = {5: "dV = A^T dFhat", 6: "dK = c dS^T Q"}
+    tiles = {5: ("256 atoms x 256 features per CTA", "128 atoms x 256 features per CTA"), 6: ("128 atoms x 64",)}
+    out = []
+    for c in choices:
+        r = c["reduction"] % 16
+        out.append({"reduction": names.get(r, str(r)), "form": "fp32 split" if c["reduction"] >= 16 else "bf16",
+                    "pixels": c["n"], "M": c["M"], "D": c["D"], "tile": tiles.get(r, ("?",) * 2)[c["tile"]],
+                    "pixel_split": c["split"], "ms": round(c["ms"], 4)})
+    return out
 
 
 def _pair_counts(ctx, scenes):
@@ -587,11 +603,12 @@ def run_ours(args, world, rank, local):
         "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"],
         "splat_roofline": head["splat_roofline"], "cpu_baseline": cpu,
         "clocks": head["clocks"], "stages_ms_per_step": head["stages_ms_per_step"],
+        "autotune": head.get("autotune"),
     }
     if len(forms) > 1:
         line["forms"] = {f: {k: res[f][k] for k in ("value", "ms_per_step", "dtype", "e2e", "roofline",
                                                     "splat_roofline", "gpu_launches", "clocks",
-                                                    "stages_ms_per_step", "keyframes_per_step")}
+                                                    "stages_ms_per_step", "keyframes_per_step", "autotune")}
                          for f in forms}
         line["forms"]["fp32_fma"]["workload"] = (
             "the room keyframe, FP32 form with every decode contraction on the FMA pipes (CUDA cores)")

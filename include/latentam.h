@@ -208,12 +208,31 @@ LATENTAM_API latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t e
 LATENTAM_API latentam_status latentam_test_wait_timeout(latentam_ctx* ctx, int32_t which);
 
 /* Autotuning of the tensor-core decode (on by default): the first time a context meets a shape
- * (pixel count, M, D) outside stream capture, the pixel-split factors of the two reductions
- * over pixels (dV and dK) are chosen by timing three candidates (the one-wave split, half and
- * twice it) with CUDA events on the caller's stream (this synchronises that stream once); the
- * fastest is kept for the context's lifetime (32 shapes).  Results differ between splits only
- * by FP32 summation order.  Disabling clears the choices and uses the one-wave split. */
+ * (pixel count, M, D) outside stream capture, the launch shape of each of the two reductions
+ * over pixels (dV = A^T dFhat and dK = c dS^T Q) is chosen by timing its candidates with CUDA
+ * events on the caller's stream (this synchronises that stream once): for dV the CTA tile
+ * (256 atoms x 256 features, the pixel block read once for both 128-atom halves, or 128 x 256
+ * on twice the CTAs), for both the pixel split (the one-wave split of that tile, half and twice
+ * it).  The fastest is kept for the context's lifetime (32 shapes).  Results differ between
+ * candidates only by FP32 summation order.  Disabling clears the choices and uses the first
+ * tile shape with its one-wave split. */
 LATENTAM_API latentam_status latentam_autotune_enable(latentam_ctx* ctx, int32_t enable);
+
+/* One choice of the autotuner. */
+typedef struct latentam_tune_choice {
+    int64_t n;          /* pixels of the decode */
+    int32_t M, D;       /* dictionary atoms and feature width */
+    int32_t reduction;  /* 5: dV, 6: dK; plus 16 in the FP32 (split-BF16) form */
+    int32_t tile;       /* dV: 0 = 256 x 256 per CTA, 1 = 128 x 256; dK: 0 (128 x 64) */
+    int32_t split;      /* pixel split: CTAs along the pixel axis per output tile */
+    float ms;           /* measured time of the chosen candidate */
+} latentam_tune_choice;
+
+/* The choices the context holds: *count receives their number; when out is not NULL and
+ * 0 <= i < *count, *out receives choice i (oldest first while fewer than 32 are held).
+ * INVALID_ARG when out is not NULL and i is out of range. */
+LATENTAM_API latentam_status latentam_autotune_query(latentam_ctx* ctx, int32_t i, latentam_tune_choice* out,
+                                                     int32_t* count);
 
 /* ---- splatting (Sec. III-A, Eq. alpha_blending; Sec. III-B, Eq. render_query) ------- */
 

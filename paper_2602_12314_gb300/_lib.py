@@ -112,6 +112,11 @@ class Dictionary(ctypes.Structure):
                 ("M", I32), ("D", I32), ("tau", F32)]
 
 
+class TuneChoice(ctypes.Structure):
+    _fields_ = [("n", I64), ("M", I32), ("D", I32), ("reduction", I32), ("tile", I32), ("split", I32),
+                ("ms", F32)]
+
+
 MAX_BATCH = 32
 
 _SIGS = {
@@ -124,6 +129,7 @@ _SIGS = {
     "latentam_profile_enable": ([P, I32], I32),
     "latentam_graphs_enable": ([P, I32], I32),
     "latentam_autotune_enable": ([P, I32], I32),
+    "latentam_autotune_query": ([P, I32, ctypes.POINTER(TuneChoice), ctypes.POINTER(I32)], I32),
     "latentam_test_wait_timeout": ([P, I32], I32),
     "latentam_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I32], I32),
     "latentam_project": ([P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Projected), P], I32),

@@ -123,8 +123,22 @@ class Context:
         L.check(_lib().latentam_test_wait_timeout(self.handle, int(which)))
 
     def autotune(self, enable: bool = True):
-        """Time candidate split factors of the pixel reductions on first use of a shape (on by default)."""
+        """Time candidate tile shapes and split factors of the pixel reductions on first use of a
+        shape (on by default)."""
         L.check(_lib().latentam_autotune_enable(self.handle, int(bool(enable))))
+
+    def autotune_choices(self) -> list:
+        """The autotuner's choices (latentam_autotune_query), as dicts."""
+        lib = _lib()
+        count = L.I32(0)
+        L.check(lib.latentam_autotune_query(self.handle, 0, None, ctypes.byref(count)))
+        out = []
+        for i in range(count.value):
+            c = L.TuneChoice()
+            L.check(lib.latentam_autotune_query(self.handle, i, ctypes.byref(c), ctypes.byref(count)))
+            out.append({"n": c.n, "M": c.M, "D": c.D, "reduction": c.reduction, "tile": c.tile, "split": c.split,
+                        "ms": c.ms})
+        return out
 
     def profile(self, enable: bool = True):
         """Turn the per-stage CUDA-event timers on or off."""

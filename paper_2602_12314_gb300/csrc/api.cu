@@ -596,6 +596,23 @@ latentam_status latentam_autotune_enable(latentam_ctx* ctx, int32_t enable) {
     return LATENTAM_OK;
 }
 
+latentam_status latentam_autotune_query(latentam_ctx* ctx, int32_t i, latentam_tune_choice* out, int32_t* count) {
+    LAT_TRY(enter(ctx));
+    if (!count) {
+        set_error("count must not be NULL");
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    *count = ctx->tune_used;
+    if (!out) return LATENTAM_OK;
+    if (i < 0 || i >= ctx->tune_used) {
+        set_error("autotuner choice %d out of range (%d held)", i, ctx->tune_used);
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    const auto& t = ctx->tune[i];
+    *out = latentam_tune_choice{t.n, t.M, t.D, t.which, t.shape, t.z, t.ms};
+    return LATENTAM_OK;
+}
+
 latentam_status latentam_profile_enable(latentam_ctx* ctx, int32_t enable) {
     LAT_TRY(enter(ctx));
     ctx->profiling = enable != 0;

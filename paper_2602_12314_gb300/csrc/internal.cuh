@@ -113,7 +113,8 @@ struct latentam_ctx {
     int autotune;
     struct TuneEntry {
         int64_t n;
-        int M, D, which, z;
+        int M, D, which, shape, z;
+        float ms;  // the chosen candidate's measured time
     } tune[32];
     int tune_used, tune_next;
     // device address of the allocation-free decode's static scratch (resolved at creation)

@@ -99,6 +99,15 @@ def test_autotuned_splits_change_only_summation_order(api):
         mask = torch.as_tensor(s.mask, device="cuda")
         res = [api.decode_loss_bwd(ctx, Q, K, V, V, F, mask, precision=api.BF16) for _ in range(2)]
         out.append([t.cpu().numpy() for t in res[-1]])
+        choices = ctx.autotune_choices()
+        if tune:  # one choice per reduction over pixels: dV (tile shape and split) and dK (split)
+            assert sorted(c["reduction"] for c in choices) == [5, 6]
+            for c in choices:
+                assert (c["n"], c["M"], c["D"]) == (s.camera.n_pixels, s.M, s.D)
+                assert c["tile"] in ((0, 1) if c["reduction"] == 5 else (0,))
+                assert c["split"] >= 1 and c["ms"] > 0
+        else:
+            assert choices == []
         ctx.close()
     for a, b in zip(out[0], out[1]):
         np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6 * np.abs(a).max())
