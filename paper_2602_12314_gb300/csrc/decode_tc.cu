@@ -268,24 +268,32 @@ struct SoftmaxEpi {
         float* scr = ec.scratch;
         const int64_t pix = (int64_t)m0 + row;
         const bool valid = pix < p.n;
-        float v[32];
         float mx = -INFINITY;
         for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
+            float v[32];
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) mx = fmaxf(mx, v[i]);
         }
         mx = tc::group_max<EPI_WG>(mx, scr, 0, g, row);
         float cm = p.c * mx;  // c > 0
+        // the exponentials are taken once and written back over S in TMEM (this thread's lane
+        // and chunks only), then scaled by the row's normaliser on the way out
         float sum = 0.f;
         for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
+            float v[32];
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) sum += __expf(p.c * v[i] - cm);
+            for (int i = 0; i < 32; ++i) {
+                v[i] = __expf(p.c * v[i] - cm);
+                sum += v[i];
+            }
+            tc::tmem_st32(taddr + c0, v);
         }
         sum = tc::group_sum<EPI_WG>(sum, scr, 1, g, row);
         const float mine[tc::kXchgVals] = {cm, sum, 0.f, 0.f};
         ec.exchange(mine);
+        float rescale = 1.f;  // exp(cm - global max) when the row spans a cluster
         if (ec.csize > 1) {
             float gm = cm;
             for (int q = 0; q < ec.csize; ++q)
@@ -293,15 +301,17 @@ struct SoftmaxEpi {
             float l = 0.f;
             for (int q = 0; q < ec.csize; ++q)
                 l += q == ec.crank ? sum * __expf(cm - gm) : ec.xval(q, 1) * __expf(ec.xval(q, 0) - gm);
+            rescale = __expf(cm - gm);
             cm = gm;
             sum = l;
         }
-        const float il = 1.0f / sum;
+        const float il = rescale / sum;
         ec.wait_out();
         for (int c0 = 32 * g; c0 < ncols; c0 += 32 * EPI_WG) {
+            float v[32];
             tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = __expf(p.c * v[i] - cm) * il;
+            for (int i = 0; i < 32; ++i) v[i] *= il;
             ec.put32(c0, v);
         }
         if (valid && p.stats && g == 0 && ec.crank == 0) {
