@@ -213,7 +213,8 @@ LATENTAM_API latentam_status latentam_test_wait_timeout(latentam_ctx* ctx, int32
  * events on the caller's stream (this synchronises that stream once): for dV the CTA tile
  * (256 atoms x 256 features, the pixel block read once for both 128-atom halves, or 128 x 256
  * on twice the CTAs), for both the pixel split (the one-wave split of that tile, half and twice
- * it).  The fastest is kept for the context's lifetime (32 shapes).  Results differ between
+ * it); each candidate is timed together with the reduction of its partial sums.  The fastest
+ * is kept for the context's lifetime (32 shapes).  Results differ between
  * candidates only by FP32 summation order.  Disabling clears the choices and uses the first
  * tile shape with its one-wave split. */
 LATENTAM_API latentam_status latentam_autotune_enable(latentam_ctx* ctx, int32_t enable);

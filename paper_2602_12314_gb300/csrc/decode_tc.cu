@@ -528,10 +528,13 @@ struct DsParams {
 template <bool SPLIT_ = false>
 struct DsEpi {
     static constexpr bool SPLIT = SPLIT_;
-    static constexpr int MSUB = 1, BKC = 64;
+    // split form: 32-wide K stages and the epilogue in two passes over the column halves, so
+    // that the tile fits in half the shared memory and two CTAs share an SM (one CTA's epilogue
+    // runs during the other's main loop), as in the plain form
+    static constexpr int MSUB = 1, BKC = SPLIT_ ? 32 : 64, EPASS = SPLIT_ ? 2 : 1;
     // the attention rows of the tile come through shared memory
     static constexpr int BN = 256, STAGES = 2, BOX_B = 256, EPI_WG = 2, XROUNDS = 0, MIN_SMEM = 0;
-    static constexpr int MIN_BLOCKS = SPLIT_ ? 1 : 2;
+    static constexpr int MIN_BLOCKS = 2;
     static constexpr int E_BOXES = BN / 64, O_BOXES = BN / 64;  // dS staged over the attention rows
     static constexpr bool A_MN = false, B_MN = false;
     static constexpr int XPROD = 64;  // dQ = c dS K on the staged dS tile
@@ -557,21 +560,22 @@ struct DsEpi {
             }
         }
     }
+    // the columns [col0, col0 + BN / EPASS) of the tile (one epilogue pass)
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const int64_t pix = (int64_t)ec.m0 + ec.row;
         const bool valid = pix < p.n;
         const float rd = valid ? p.row[4 * pix + 2] : 0.f;
-        for (int b = 0; b < E_BOXES; ++b) (void)ec.wait_box(b);
-        const int ncols = min(BN, p.M - ec.n0);
+        for (int b = 0; b < E_BOXES / EPASS; ++b) (void)ec.wait_box(b);
+        const int cend = min(min(BN, p.M - ec.n0), ec.col0 + BN / EPASS);
         float dA[32], a[32];
-        for (int c0 = 32 * ec.g; c0 < ncols; c0 += 32 * EPI_WG) {
+        for (int c0 = ec.col0 + 32 * ec.g; c0 < cend; c0 += 32 * EPI_WG) {
             ec.row32(c0, a);
             tc::tmem_ld32(ec.taddr + c0, dA);
 #pragma unroll
             for (int i = 0; i < 32; ++i) dA[i] = a[i] * (dA[i] - rd);
             ec.put32(c0, dA);
         }
-        return (ncols + 63) / 64;
+        return cend > ec.col0 ? (cend - ec.col0 + 63) / 64 : 0;
     }
 };
 
@@ -590,7 +594,7 @@ struct DqEpi {
     static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, O_BOXES = 0, XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
-    static constexpr int XPROD = 0;
+    static constexpr int XPROD = 0, EPASS = 1;
     using Params = DqParams;
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
@@ -636,7 +640,7 @@ struct PartEpi {
     static constexpr int XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
-    static constexpr int XPROD = 0;
+    static constexpr int XPROD = 0, EPASS = 1;
     using Params = PartParams;
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
 #pragma unroll
@@ -1200,8 +1204,9 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
         LAT_TRY(tc_fhat<SPLIT>(ctx, b, n, M, D, fp, st));
         // G3: dA = dFhat V^T -> dS
         CUtensorMap mdF, mV, mdS, mK;
-        LAT_TRY(op_map(SPLIT, &mdF, b.dF, D, n, D, kTileM));
-        LAT_TRY(op_map(SPLIT, &mV, b.Vb, D, M, D, 256));
+        constexpr int BK3 = DsEpi<SPLIT>::BKC;  // K (feature) elements per ring stage
+        LAT_TRY(op_map(SPLIT, &mdF, b.dF, D, n, D, kTileM, BK3));
+        LAT_TRY(op_map(SPLIT, &mV, b.Vb, D, M, D, 256, BK3));
         // G4 (dQ = c dS K, B = K padded, read MN-major) runs as G3's trailing product on the
         // staged dS tile when a row's atoms span at most two CTAs, else as its own GEMM
         const int ty = cdiv(M, 256);
@@ -1213,7 +1218,7 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
         }
         DsParams dp{n, M, b.A, b.row, b.dS, dq_fused ? a.dQ : nullptr, d, a.c, ty > 1 ? 1 : 0};
         const dim3 grow(cdiv(n, kTileM), 1, 1);
-        const tc::GemmGrid g3{cdiv(D, tc::kChunkK), cdiv(D, tc::kChunkK)};
+        const tc::GemmGrid g3{cdiv(D, BK3), cdiv(D, BK3)};
         CUtensorMap mAe, mdSo;  // attention rows for the epilogue, dS out through the TMA
         LAT_TRY(io_map(SPLIT, &mAe, b.A, M, n, M, kTileM));
         LAT_TRY(io_map(SPLIT, &mdSo, b.dS, M, n, M, kTileM));
@@ -1226,9 +1231,21 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
             LAT_TRY((launch_gemm<DqEpi<BNq, SPLIT>>(mdS, mK, grow, g4, qp, b.err, st)));
         }
     }
-    // G5: dV = A^T dFhat (+ trust region), both operands pixel-major (MN-major)
-    int zV = 0, zK = 0;
+    // G5: dV = A^T dFhat (+ trust region), both operands pixel-major (MN-major); each candidate
+    // the tuner times includes the reduction of its partials (more splits, more partials to sum)
+    auto reduce_dV = [&](int z) -> latentam_status {
+        tc_reduce_parts<<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, z, M, D, D, 1.0f, b.coef, a.V, a.V0, a.dV);
+        LAT_CHECK_LAUNCH("tc_reduce_parts");
+        return LATENTAM_OK;
+    };
+    auto reduce_dK = [&](int z) -> latentam_status {
+        tc_reduce_parts<<<cdiv((int64_t)M * d, 32), 256, 0, st>>>(b.part, z, M, BNq, d, a.c, nullptr, nullptr, nullptr,
+                                                                  a.dK);
+        LAT_CHECK_LAUNCH("tc_reduce_parts");
+        return LATENTAM_OK;
+    };
     if (a.dV) {
+        if (n == 0) LAT_TRY(reduce_dV(0));  // the trust-region term alone
         if (n > 0) {
             CUtensorMap mA[2], mdF[2];  // per tile shape (pixel block of a ring stage: BKC)
             LAT_TRY(io_map(SPLIT, &mA[0], b.A, M, n, M, EpiV::BKC));
@@ -1240,23 +1257,23 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
                 int zz;
                 if (shape == 0) {
                     const tc::GemmGrid g = pixel_split(n, z, &zz, EpiV::BKC);
-                    return launch_gemm<EpiV>(mA[0], mdF[0], dim3(cdiv(M, 2 * kTileM), cdiv(D, 256), zz), g, pp, b.err,
-                                             st);
+                    LAT_TRY(launch_gemm<EpiV>(mA[0], mdF[0], dim3(cdiv(M, 2 * kTileM), cdiv(D, 256), zz), g, pp,
+                                              b.err, st));
+                } else {
+                    const tc::GemmGrid g = pixel_split(n, z, &zz, EpiV1::BKC);
+                    LAT_TRY(launch_gemm<EpiV1>(mA[1], mdF[1], dim3(cdiv(M, kTileM), cdiv(D, 256), zz), g, pp, b.err,
+                                               st));
                 }
-                const tc::GemmGrid g = pixel_split(n, z, &zz, EpiV1::BKC);
-                return launch_gemm<EpiV1>(mA[1], mdF[1], dim3(cdiv(M, kTileM), cdiv(D, 256), zz), g, pp, b.err, st);
+                return reduce_dV(zz);
             };
             int shape, z;
             LAT_TRY(tuned_shape(ctx, n, M, D, 5 + which, 2, zV0, st, g5, &shape, &z));
             LAT_TRY(g5(shape, z));
-            pixel_split(n, z, &zV, shape == 0 ? EpiV::BKC : EpiV1::BKC);
         }
-        tc_reduce_parts<<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, n > 0 ? zV : 0, M, D, D, 1.0f, b.coef, a.V,
-                                                                  a.V0, a.dV);
-        LAT_CHECK_LAUNCH("tc_reduce_parts");
     }
     // G6: dK = c dS^T Q
     if (a.dK) {
+        if (n == 0) LAT_TRY(reduce_dK(0));  // zero
         if (n > 0) {
             CUtensorMap mdS, mQ;
             LAT_TRY(io_map(SPLIT, &mdS, b.dS, M, n, M, 64));
@@ -1265,16 +1282,13 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
             auto g6 = [&](int, int z) -> latentam_status {
                 int zz;
                 const tc::GemmGrid g = pixel_split(n, z, &zz);
-                return launch_gemm<PartEpi<BNq, SPLIT>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zz), g, pp, b.err, st);
+                LAT_TRY((launch_gemm<PartEpi<BNq, SPLIT>>(mdS, mQ, dim3(cdiv(M, kTileM), 1, zz), g, pp, b.err, st)));
+                return reduce_dK(zz);
             };
             int shape, z;
             LAT_TRY(tuned_shape(ctx, n, M, D, 6 + which, 1, &zK0, st, g6, &shape, &z));
             LAT_TRY(g6(0, z));
-            pixel_split(n, z, &zK);
         }
-        tc_reduce_parts<<<cdiv((int64_t)M * d, 32), 256, 0, st>>>(b.part, n > 0 ? zK : 0, M, BNq, d, a.c, nullptr,
-                                                                  nullptr, nullptr, a.dK);
-        LAT_CHECK_LAUNCH("tc_reduce_parts");
     }
     tc_finalize<<<1, 1, 0, st>>>(b.acc, b.err, D, a.cfg, a.loss_parts);
     LAT_CHECK_LAUNCH("tc_finalize");

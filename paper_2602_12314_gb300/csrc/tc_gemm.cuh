@@ -41,21 +41,23 @@ __host__ __device__ constexpr int planes() {
 
 // One-tile kernel with a trailing product (Epi::XPROD > 0): the B operand of that product,
 // BN (K) x XPROD (N) BF16 per plane, stored MN-major as BN / 64 boxes of 64 x 64.
+// (One epilogue pass's share of it when the epilogue runs in Epi::EPASS passes.)
 template <class Epi>
 __host__ __device__ constexpr uint32_t xprod_bytes() {
-    return Epi::XPROD > 0 ? (uint32_t)(Epi::BN / 64) * planes<Epi>() * 64u * 64u * 2u : 0u;
+    return Epi::XPROD > 0 ? (uint32_t)(Epi::BN / 64 / Epi::EPASS) * planes<Epi>() * 64u * 64u * 2u : 0u;
 }
 
 // Shared memory at the start of the tile: the operand pipeline, reused once the MMAs are done
 // for the epilogue operand (E_BOXES boxes of 64 x 128 BF16 per plane) and the staged output
-// (O_BOXES per plane), then the trailing product's B operand.
+// (O_BOXES per plane), then the trailing product's B operand; with Epi::EPASS passes over
+// column slices of the tile, one pass's share of each at a time.
 template <class Epi>
 __host__ __device__ constexpr uint32_t tile_region_bytes() {
     const uint32_t pipe = (uint32_t)Epi::STAGES * planes<Epi>() *
                           ((uint32_t)Epi::MSUB * kTileM + (uint32_t)Epi::BN) * Epi::BKC * 2;
-    const uint32_t boxes =
-        (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) * planes<Epi>() * kTileABytes +
-        xprod_bytes<Epi>();
+    const uint32_t boxes = (uint32_t)(Epi::E_BOXES > Epi::O_BOXES ? Epi::E_BOXES : Epi::O_BOXES) / Epi::EPASS *
+                               planes<Epi>() * kTileABytes +
+                           xprod_bytes<Epi>();
     return pipe > boxes ? pipe : boxes;
 }
 
@@ -140,7 +142,11 @@ struct GemmGrid {
 // tile is staged, its 128 x BN BF16 values, K-major as staged, are multiplied on the tensor
 // cores by a BN x 64 operand tmX (MN-major, rows n0 .. n0 + BN) into TMEM columns 0 .. 63,
 // after which static __device__ void run_x(const Params&, const EpiCtx&) reads them; static
-// __device__ bool x_active(const Params&) says, CTA-uniformly, whether this launch takes it).
+// __device__ bool x_active(const Params&) says, CTA-uniformly, whether this launch takes it);
+// static constexpr int EPASS (1, or 2: the epilogue runs in two passes over the two column
+// halves of the tile, each with its half of the epilogue-operand boxes, of the staged output
+// and of the trailing product's K, in half the shared memory; run() then covers the columns
+// [EpiCtx::col0, col0 + BN / EPASS) and is called once per pass).
 struct EpiCtx {
     uint32_t taddr;        // TMEM address of this thread's row, column 0
     int row, m0, n0, z;    // tile row owned by this thread, tile origin, K split
@@ -157,6 +163,7 @@ struct EpiCtx {
     uint32_t xphase = 0;   // phase parity of xbar for this tile
     int ngroups = 1;       // epilogue warpgroups
     int leader = 64;       // first epilogue thread
+    int col0 = 0;          // one-tile kernel, epilogue pass: first tile column of the pass's boxes
     uint32_t eplane = 0;   // split form: bytes from the hi to the lo plane of the epilogue operand
     uint32_t oplane = 0;   // split form: bytes from the hi to the lo plane of the staged output
     uint64_t* ofree = nullptr;  // split persistent form: completes when the staging buffers are free
@@ -244,7 +251,7 @@ struct EpiCtx {
     // Stage 32 values of this thread's row as BF16 at column c0 (a multiple of 32) of the output
     // (split form: the hi terms in the hi plane, the lo terms in the lo plane).
     __device__ __forceinline__ void put32(int c0, const float (&v)[32]) const {
-        uint8_t* base = otile + (c0 >> 6) * (kTileM * 128) + row * 128;
+        uint8_t* base = otile + ((c0 - col0) >> 6) * (kTileM * 128) + row * 128;
         const int j0 = (c0 & 63) >> 3;
         if (oplane) {
 #pragma unroll
@@ -267,7 +274,7 @@ struct EpiCtx {
     // 32 values of this thread's row from column c0 (a multiple of 32) of the operand (split
     // form: hi + lo).
     __device__ __forceinline__ void row32(int c0, float (&v)[32]) const {
-        const uint8_t* base = etile + (c0 >> 6) * (kTileM * 128) + row * 128;
+        const uint8_t* base = etile + ((c0 - col0) >> 6) * (kTileM * 128) + row * 128;
         const int j0 = (c0 & 63) >> 3;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -335,7 +342,10 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     constexpr uint32_t TMEM_COLS = tmem_cols_for(MSUB * BN);
     constexpr bool A_MN = Epi::A_MN, B_MN = Epi::B_MN;
     constexpr uint32_t IDESC = idesc_bf16(kTileM, SUBN, A_MN, B_MN);
-    static_assert(BKC == kChunkK || (A_MN && B_MN && BKC == 32), "32-wide K stages read both operands MN-major");
+    static_assert(BKC == kChunkK || BKC == 32, "64- or 32-wide K stages");
+    static_assert(BKC == kChunkK || (A_MN && B_MN) || (!A_MN && !B_MN && MSUB == 1 && BN <= 256),
+                  "32-wide K stages: both operands MN-major, or both K-major (64-byte rows)");
+    constexpr uint32_t KROW = (uint32_t)BKC * 2;  // bytes per row of a K-major operand stage
     static_assert(MSUB == 1 || (A_MN && MSUB == 2 && MSUB * BN <= 512), "two A sub-tiles: MN-major, <= 512 columns");
     static_assert(BN % 16 == 0 && SUBN % 16 == 0 && SUBN <= 256, "MMA N must be a multiple of 16, <= 256");
     static_assert(BN % BOX_B == 0 && BOX_B <= 256 && (BOX_B * 128) % 1024 == 0, "bad B box");
@@ -345,10 +355,17 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     static_assert(E_BOXES * PL <= 8 && Epi::O_BOXES * PL <= 8, "at most 8 boxes of epilogue operand / output");
     static_assert(!SPLIT || B_MN || BOX_B == BN, "a split K-major B tile is one box");
     static_assert(Epi::XROUNDS == 0, "row exchanges run in the persistent form");
+    // epilogue passes over column slices of the tile: EB operand boxes, OB output boxes and XC
+    // trailing-product K chunks (64 atoms each) per pass
+    constexpr int EPASS = Epi::EPASS;
+    constexpr int EB = E_BOXES / EPASS, OB = Epi::O_BOXES / EPASS;
+    static_assert(EPASS == 1 || (EPASS == 2 && E_BOXES % 2 == 0 && Epi::O_BOXES % 2 == 0 && MSUB == 1),
+                  "one or two epilogue passes");
     // trailing product: staged output (K-major, 64 columns per box) x tmX (MN-major 64 x 64 boxes)
     constexpr int XN = Epi::XPROD;
+    constexpr int XC = BN / 64 / EPASS;
     constexpr uint32_t X_BOX = 64u * 64u * 2u;  // one 64 (N) x 64 (K) box per plane
-    constexpr uint32_t X_OFF = (uint32_t)(E_BOXES > Epi::O_BOXES ? E_BOXES : Epi::O_BOXES) * PL * kTileABytes;
+    constexpr uint32_t X_OFF = (uint32_t)(EB > OB ? EB : OB) * PL * kTileABytes;
     static_assert(XN == 0 || (XN == 64 && MSUB == 1 && !A_MN && Epi::O_BOXES * 64 == BN && BN <= 256 &&
                               X_OFF + xprod_bytes<Epi>() <= TILE_REGION),
                   "a trailing product multiplies the whole staged tile by a 64-column operand");
@@ -366,8 +383,9 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     uint64_t* x_loaded = ebar + 8;  // trailing product: its B operand arrived
     uint64_t* x_staged = ebar + 9;  //   the staged output is complete
     uint64_t* x_done = ebar + 10;   //   its MMAs have completed
+    uint64_t* p_free = ebar + 11;   // epilogue pass: its staged output has been read by its stores
     float* scratch = reinterpret_cast<float*>(smem + TILE_REGION + 256);
-    static_assert(STAGES * 16 + 8 + 16 + 11 * 8 <= 256, "barriers fit their 256 bytes");
+    static_assert(STAGES * 16 + 8 + 16 + 12 * 8 <= 256, "barriers fit their 256 bytes");
     bool x_on = false;
     if constexpr (XN > 0) x_on = Epi::x_active(ep);
 
@@ -390,6 +408,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
             mbar_init(x_staged, 1);
             mbar_init(x_done, 1);
         }
+        if (EPASS > 1) mbar_init(p_free, 1);
         *abort_flag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmA);
@@ -461,25 +480,33 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 // epilogue operand rows of this tile
                 if (mbar_wait(accum, 0, abort_flag) && !*abort_flag) {
                     prefetch_tmap(&tmE);
-                    for (int b = 0; b < E_BOXES; ++b) {
-                        mbar_expect_tx(&ebar[b], PL * kTileM * 128);
-                        for (int z = 0; z < PL; ++z)
-                            tma_load(smem + (z * E_BOXES + b) * (kTileM * 128), &tmE, &ebar[b], n0 + 64 * b, m0,
-                                     SPLIT ? z : -1);
-                    }
-                    if (XN > 0 && x_on) {
-                        // the trailing product's B rows n0 .. n0 + BN (both planes per box when split)
-                        mbar_expect_tx(x_loaded, xprod_bytes<Epi>());
-                        for (int c = 0; c < BN / 64; ++c) {
-                            uint8_t* dst = smem + X_OFF + c * PL * X_BOX;
-                            if (SPLIT)
-                                tma_load_4d(dst, &tmX, x_loaded, 0, n0 + 64 * c, 0, 0);
-                            else
-                                tma_load_2d(dst, &tmX, x_loaded, 0, n0 + 64 * c);
+                    for (int h = 0; h < EPASS; ++h) {
+                        // pass h reuses pass h - 1's buffers once its stores and products read them
+                        if (h > 0 && (!mbar_wait(p_free, (uint32_t)(h - 1) & 1u, abort_flag) ||
+                                      (XN > 0 && x_on && !mbar_wait(x_done, (uint32_t)(h - 1) & 1u, abort_flag)))) {
+                            *abort_flag = 1;
+                            break;
                         }
+                        for (int b = 0; b < EB; ++b) {
+                            mbar_expect_tx(&ebar[b], PL * kTileM * 128);
+                            for (int z = 0; z < PL; ++z)
+                                tma_load(smem + (z * EB + b) * (kTileM * 128), &tmE, &ebar[b], n0 + 64 * (h * EB + b),
+                                         m0, SPLIT ? z : -1);
+                        }
+                        if (XN > 0 && x_on) {
+                            // the trailing product's B rows of the pass (both planes per box when split)
+                            mbar_expect_tx(x_loaded, xprod_bytes<Epi>());
+                            for (int c = 0; c < XC; ++c) {
+                                uint8_t* dst = smem + X_OFF + c * PL * X_BOX;
+                                if (SPLIT)
+                                    tma_load_4d(dst, &tmX, x_loaded, 0, n0 + 64 * (h * XC + c), 0, 0);
+                                else
+                                    tma_load_2d(dst, &tmX, x_loaded, 0, n0 + 64 * (h * XC + c));
+                            }
+                        }
+                        for (int b = 0; b < EB; ++b) (void)mbar_wait(&ebar[b], (uint32_t)h & 1u, nullptr);
+                        if (XN > 0 && x_on) (void)mbar_wait(x_loaded, (uint32_t)h & 1u, nullptr);
                     }
-                    for (int b = 0; b < E_BOXES; ++b) (void)mbar_wait(&ebar[b], 0, nullptr);
-                    if (XN > 0 && x_on) (void)mbar_wait(x_loaded, 0, nullptr);
                 } else {
                     *abort_flag = 1;
                 }
@@ -499,13 +526,14 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);  // A hi (then A lo)
                 const uint32_t sb = sa + PL * A_BYTES;                 // B hi (then B lo)
+                auto kdesc = [&](uint32_t a) { return KROW == 128 ? sw128_desc(a) : sw64_desc(a); };
                 auto adesc = [&](uint32_t base, int ms, int kk) {
                     return A_MN ? mn128_desc(base + (uint32_t)(ms * 2) * MNBOX + kk * 16 * 128, MNBOX)
-                                : sw128_desc(base + kk * 32);
+                                : kdesc(base + kk * 32);
                 };
                 auto bdesc = [&](uint32_t base, int j, int kk) {
                     return B_MN ? mn128_desc(base + (uint32_t)(j * (SUBN / 64)) * MNBOX + kk * 16 * 128, MNBOX)
-                                : sw128_desc(base + (uint32_t)(j * SUBN * 128) + kk * 32);
+                                : kdesc(base + (uint32_t)j * SUBN * KROW + kk * 32);
                 };
 #pragma unroll
                 for (int kk = 0; kk < BKC / 16; ++kk) {
@@ -524,25 +552,30 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
             mma_commit(accum);  // accumulator complete (or the pipeline was abandoned)
             if (XN > 0 && x_on) {
                 // trailing product into columns 0 .. XN - 1, once the epilogue has read them
-                // (x_staged) and the staged tile and the B operand are in shared memory
-                const bool go = ok && mbar_wait(x_loaded, 0, abort_flag) && mbar_wait(x_staged, 0, abort_flag) &&
-                                !*abort_flag;
-                if (go) {
-                    tc_fence_after();
-                    const uint32_t so = smem_u32(smem);         // staged output, hi plane (then lo)
-                    const uint32_t sx = smem_u32(smem + X_OFF);  // B boxes [c][plane]
-                    constexpr uint32_t OPL = (uint32_t)Epi::O_BOXES * kTileABytes;
+                // (x_staged) and the pass's staged slice and B operand are in shared memory;
+                // each pass adds its K (atoms) slice into the same accumulator
+                for (int h = 0; h < EPASS; ++h) {
+                    const uint32_t ph = (uint32_t)h & 1u;
+                    const bool go = ok && mbar_wait(x_loaded, ph, abort_flag) && mbar_wait(x_staged, ph, abort_flag) &&
+                                    !*abort_flag;
+                    if (go) {
+                        tc_fence_after();
+                        const uint32_t so = smem_u32(smem);         // staged output, hi plane (then lo)
+                        const uint32_t sx = smem_u32(smem + X_OFF);  // B boxes [c][plane]
+                        constexpr uint32_t OPL = (uint32_t)OB * kTileABytes;
 #pragma unroll
-                    for (int c = 0; c < BN / 64; ++c)
+                        for (int c = 0; c < XC; ++c)
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint32_t oa = so + (uint32_t)c * kTileABytes + kk * 32;
-                            const uint32_t ob = sx + (uint32_t)c * PL * X_BOX + kk * 16 * 128;
-                            mma_step<SPLIT>(tmem_base, sw128_desc(oa), sw128_desc(oa + OPL), mn128_desc(ob, X_BOX),
-                                            mn128_desc(ob + X_BOX, X_BOX), XDESC, (c > 0 || kk > 0) ? 1u : 0u);
-                        }
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint32_t oa = so + (uint32_t)c * kTileABytes + kk * 32;
+                                const uint32_t ob = sx + (uint32_t)c * PL * X_BOX + kk * 16 * 128;
+                                mma_step<SPLIT>(tmem_base, sw128_desc(oa), sw128_desc(oa + OPL), mn128_desc(ob, X_BOX),
+                                                mn128_desc(ob + X_BOX, X_BOX), XDESC,
+                                                (h > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                            }
+                    }
+                    mma_commit(x_done);  // at once when nothing was issued
                 }
-                mma_commit(x_done);  // at once when nothing was issued
             }
         }
     } else {
@@ -561,35 +594,42 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
         EpiCtx ec{tmem_base + ((uint32_t)(quarter * 32) << 16), row, m0, n0, (int)blockIdx.z, group, scratch,
                   E_BOXES > 0 ? smem : nullptr, smem, ebar, abort_flag, 0, 1, nullptr, nullptr};
         if (SPLIT) {
-            ec.eplane = (uint32_t)E_BOXES * kTileM * 128;
-            ec.oplane = (uint32_t)Epi::O_BOXES * kTileABytes;
+            ec.eplane = (uint32_t)EB * kTileM * 128;
+            ec.oplane = (uint32_t)OB * kTileABytes;
         }
-        int out_boxes = 0;
-        if (*decision) out_boxes = Epi::run(ep, ec);
-        if (Epi::O_BOXES > 0) {
-            // the staged output tile goes out through the TMA once every epilogue thread wrote
-            // its part (coalesced and asynchronous, instead of one row per thread)
-            fence_proxy_async();
-            if (XN > 0) tc_fence_before();  // this thread's TMEM reads precede the trailing product
-            epi_sync(128 * Epi::EPI_WG);
-            if (threadIdx.x == 64) {
-                if (XN > 0 && x_on) mbar_arrive(x_staged);  // the tile is staged (or abandoned)
-                if (out_boxes > 0 && !*abort_flag) {
-                    for (int b = 0; b < out_boxes && b < Epi::O_BOXES; ++b)
-                        for (int z = 0; z < PL; ++z)
-                            tma_store(&tmO, smem + (z * Epi::O_BOXES + b) * kTileABytes, n0 + 64 * b, m0,
-                                      SPLIT ? z : -1);
-                    bulk_commit();
-                    bulk_wait_read();  // shared memory stays valid until the copies have read it
+        int any_boxes = 0;
+        for (int h = 0; h < EPASS; ++h) {
+            ec.col0 = h * (BN / EPASS);
+            ec.ephase = (uint32_t)h & 1u;
+            int out_boxes = 0;
+            if (*decision) out_boxes = Epi::run(ep, ec);
+            any_boxes |= out_boxes;
+            if (Epi::O_BOXES > 0) {
+                // the staged output slice goes out through the TMA once every epilogue thread
+                // wrote its part (coalesced and asynchronous, instead of one row per thread)
+                fence_proxy_async();
+                if (XN > 0) tc_fence_before();  // this thread's TMEM reads precede the trailing product
+                epi_sync(128 * Epi::EPI_WG);
+                if (threadIdx.x == 64) {
+                    if (XN > 0 && x_on) mbar_arrive(x_staged);  // the slice is staged (or abandoned)
+                    if (out_boxes > 0 && !*abort_flag) {
+                        for (int b = 0; b < out_boxes && b < OB; ++b)
+                            for (int z = 0; z < PL; ++z)
+                                tma_store(&tmO, smem + (z * OB + b) * kTileABytes, n0 + ec.col0 + 64 * b, m0,
+                                          SPLIT ? z : -1);
+                        bulk_commit();
+                        bulk_wait_read();  // shared memory stays valid until the copies have read it
+                    }
+                    if (EPASS > 1) mbar_arrive(p_free);  // the next pass may refill the buffers
                 }
             }
         }
         if constexpr (XN > 0) {
             if (x_on) {
-                if (!mbar_wait(x_done, 0, abort_flag)) *abort_flag = 1;
+                if (!mbar_wait(x_done, (uint32_t)(EPASS - 1) & 1u, abort_flag)) *abort_flag = 1;
                 // one CTA-uniform decision again: run_x's TMEM loads are warp-collective
                 epi_sync(128 * Epi::EPI_WG);
-                if (threadIdx.x == 64) *decision = (*decision && out_boxes > 0 && !*abort_flag) ? 1 : 0;
+                if (threadIdx.x == 64) *decision = (*decision && any_boxes > 0 && !*abort_flag) ? 1 : 0;
                 epi_sync(128 * Epi::EPI_WG);
                 tc_fence_after();
                 if (*decision) Epi::run_x(ep, ec);
