@@ -1062,6 +1062,8 @@ __global__ void __launch_bounds__(persist_threads(Epi::EPI_WG), 1)
         }
     }
     __syncthreads();
+    // no CTA leaves while a peer may still read or write its shared memory (the row exchange)
+    if (csize > 1) cluster_sync_all();
     if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
     if (warp == 1) {
         tc_fence_after();
