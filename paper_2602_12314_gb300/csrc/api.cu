@@ -512,7 +512,8 @@ latentam_status latentam_ctx_create(int32_t device, latentam_ctx** out) {
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->step_dev, sizeof(int));
-    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&c->host_counts), 32, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&c->host_counts),
+                                                  sizeof(uint32_t) * (8 + 4 * LATENTAM_MAX_BATCH), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&c->dev_flags, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->dev_flags, 0, 4 * sizeof(int));
     if (e != cudaSuccess || !c->graphs || !c->sort_graphs) {
@@ -1276,7 +1277,18 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
         total_pix += (int64_t)fr.camera.width * fr.camera.height;
     }
 
-    // projection and binning of every frame (once; the geometry is fixed during the step)
+    // projection and binning of every frame (once; the geometry is fixed during the step): the
+    // pair counts of all frames, one host synchronisation, then each frame's pairs, sort and
+    // ranges (binning slot k per frame, its scan offsets at offs + off_at[k])
+    size_t off_at[LATENTAM_MAX_BATCH + 1];
+    off_at[0] = 0;
+    bool any_gauss = false;
+    for (int k = 0; k < n_frames; ++k) {
+        off_at[k + 1] = off_at[k] + (((size_t)frames[k].gaussians.n + 1 + 63) & ~(size_t)63);
+        any_gauss = any_gauss || frames[k].gaussians.n > 0;
+    }
+    uint32_t* offs = static_cast<uint32_t*>(ws(ctx, WS_OFFSETS, sizeof(uint32_t) * off_at[n_frames]));
+    if (!offs) return LATENTAM_ERR_OUT_OF_MEMORY;
     for (int k = 0; k < n_frames; ++k) {
         const latentam_batch_frame& fr = frames[k];
         const int N = fr.gaussians.n;
@@ -1299,17 +1311,24 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
             StageTimer tm(ctx, LATENTAM_STAGE_PROJECT, st);
             LAT_TRY(launch_project(fr.gaussians, fs[k].cam, fs[k].proj, st));
         }
-        latentam_status s;
-        {
-            StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
-            s = bin_and_sort(ctx, N, fs[k].proj, fs[k].cam, &bins, st);
-        }
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+        LAT_TRY(bin_count(ctx, N, fs[k].proj, fs[k].cam, &bins, offs + off_at[k], k, st));
+    }
+    if (any_gauss) {
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_error(e, "sync for the pair counts");
+    }
+    for (int k = 0; k < n_frames; ++k) {
+        const int N = frames[k].gaussians.n;
+        latentam_bins& bins = fs[k].bins;
+        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
+        latentam_status s = bin_finish(ctx, N, fs[k].proj, fs[k].cam, &bins, offs + off_at[k], k, st);
         if (s == LATENTAM_ERR_CAPACITY) {
             bins.pair_ids = static_cast<int32_t*>(frame_ws(ctx, 2 * k + 1, sizeof(int32_t) * (size_t)bins.num_pairs));
             if (!bins.pair_ids) return LATENTAM_ERR_OUT_OF_MEMORY;
             bins.capacity = bins.num_pairs;
-            StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
-            s = bin_and_sort(ctx, N, fs[k].proj, fs[k].cam, &bins, st);
+            s = bin_finish(ctx, N, fs[k].proj, fs[k].cam, &bins, offs + off_at[k], k, st);
         }
         LAT_TRY(s);
     }

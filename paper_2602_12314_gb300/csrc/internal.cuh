@@ -108,7 +108,8 @@ struct latentam_ctx {
     int* step_dev;
     lat::GraphCache* graphs;
     lat::GraphCache* sort_graphs;  // the binning before and after its host read (see cached_launch)
-    uint32_t* host_counts;         // pinned: the binning's counts read back by the host
+    uint32_t* host_counts;         // pinned: [4..5] the device flags read with a step's loss, [8 + 4 k ..] the
+                                   // counts of binning slot k read back by the host
     // autotuned split factors of the pixel reductions (see latentam_autotune_enable)
     int autotune;
     struct TuneEntry {
@@ -183,6 +184,15 @@ latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uin
                                  int64_t n, int bits, int* result, uint32_t* err, cudaStream_t st);
 latentam_status bin_and_sort(latentam_ctx* ctx, int32_t n, const latentam_projected& proj,
                              const CamParams& cam, latentam_bins* bins, cudaStream_t st);
+// The two halves of bin_and_sort, for several keyframes binned with one host synchronisation:
+// bin_count enqueues the pair count of binning slot `slot` (0 .. LATENTAM_MAX_BATCH - 1) into
+// its pinned host words, the offsets into off[n + 1]; once the stream has been synchronised,
+// bin_finish reads them and enqueues the pairs, their sort and the ranges (LATENTAM_ERR_CAPACITY
+// when bins->capacity is short: bin_finish may then be called again with a larger buffer).
+latentam_status bin_count(latentam_ctx* ctx, int32_t n, const latentam_projected& proj, const CamParams& cam,
+                          latentam_bins* bins, uint32_t* off, int slot, cudaStream_t st);
+latentam_status bin_finish(latentam_ctx* ctx, int32_t n, const latentam_projected& proj, const CamParams& cam,
+                           latentam_bins* bins, const uint32_t* off, int slot, cudaStream_t st);
 
 // The tiles of a binned frame in decreasing order of list length (power-of-two classes), into
 // order[tiles]: the per-tile kernels start the longest tiles first.

@@ -454,24 +454,37 @@ latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uin
     return LATENTAM_OK;
 }
 
-latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projected& proj,
-                             const CamParams& cam, latentam_bins* bins, cudaStream_t st) {
+// Counters of binning slot k (a keyframe of a batch; a single binning uses slot 0): on the
+// device 4 words at cnt + 16 k ([1] the pair count P, [2] the sort error word), read back into
+// 4 pinned host words at host_counts + 8 + 4 k with the tensor-core wait flag.
+namespace {
+latentam_status bin_slot(latentam_ctx* ctx, int slot, uint32_t** cnt, uint32_t** host) {
+    if (slot < 0 || slot >= LATENTAM_MAX_BATCH) {
+        set_error("binning slot %d outside 0..%d", slot, LATENTAM_MAX_BATCH - 1);
+        return LATENTAM_ERR_INVALID_ARG;
+    }
+    uint32_t* c = static_cast<uint32_t*>(ws(ctx, WS_COUNTERS, 64 * LATENTAM_MAX_BATCH));
+    if (!c) return LATENTAM_ERR_OUT_OF_MEMORY;
+    *cnt = c + 16 * slot;
+    *host = ctx->host_counts + 8 + 4 * slot;
+    return LATENTAM_OK;
+}
+}  // namespace
+
+latentam_status bin_count(latentam_ctx* ctx, int32_t N, const latentam_projected& proj, const CamParams& cam,
+                          latentam_bins* bins, uint32_t* off, int slot, cudaStream_t st) {
     const int64_t num_tiles = (int64_t)cam.tiles_x * cam.tiles_y;
-    cudaError_t e;
     if (N == 0) {
-        e = cudaMemsetAsync(bins->tile_ranges, 0, sizeof(int2) * (size_t)num_tiles, st);
+        cudaError_t e = cudaMemsetAsync(bins->tile_ranges, 0, sizeof(int2) * (size_t)num_tiles, st);
         if (e != cudaSuccess) return cuda_error(e, "memset tile_ranges");
-        bins->num_pairs = 0;
         return LATENTAM_OK;
     }
-    uint32_t* off = static_cast<uint32_t*>(ws(ctx, WS_OFFSETS, sizeof(uint32_t) * ((size_t)N + 1)));
-    uint32_t* cnt = static_cast<uint32_t*>(ws(ctx, WS_COUNTERS, 64));
-    if (!off || !cnt) return LATENTAM_ERR_OUT_OF_MEMORY;
-    // 0. cleared ranges, pair offsets (exclusive scan of tiles_touched) and the pair count P
-    //    into cnt[1], read back with cnt[2]: raised by a sort pass whose look-back gave up; it
-    //    outlives the call and is reported (and cleared) by the next binning's host read.  The
-    //    same frame size and buffers replay one captured graph.
-    uint32_t* host = ctx->host_counts;
+    uint32_t *cnt, *host;
+    LAT_TRY(bin_slot(ctx, slot, &cnt, &host));
+    // cleared ranges, pair offsets (exclusive scan of tiles_touched) and the pair count P into
+    // cnt[1], read back with cnt[2]: raised by a sort pass whose look-back gave up; it outlives
+    // the call and is reported (and cleared) by the slot's next binning.  The same frame size
+    // and buffers replay one captured graph.
     auto pre = [&](cudaStream_t s) -> latentam_status {
         cudaError_t e2 = cudaMemsetAsync(bins->tile_ranges, 0, sizeof(int2) * (size_t)num_tiles, s);
         if (e2 == cudaSuccess) e2 = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s);
@@ -486,10 +499,20 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
     const uint64_t pre_key[] = {0x62696e302d707265ull /* tag: counting phase */, (uint64_t)N, (uint64_t)num_tiles,
                                 reinterpret_cast<uint64_t>(proj.tiles_touched),
                                 reinterpret_cast<uint64_t>(bins->tile_ranges), reinterpret_cast<uint64_t>(host),
-                                reinterpret_cast<uint64_t>(st), ctx->ws_generation};
-    LAT_TRY(cached_launch(ctx, pre_key, (int)(sizeof(pre_key) / sizeof(pre_key[0])), st, pre));
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_error(e, "sync for the pair count");
+                                reinterpret_cast<uint64_t>(off), reinterpret_cast<uint64_t>(st), ctx->ws_generation};
+    return cached_launch(ctx, pre_key, (int)(sizeof(pre_key) / sizeof(pre_key[0])), st, pre);
+}
+
+latentam_status bin_finish(latentam_ctx* ctx, int32_t N, const latentam_projected& proj, const CamParams& cam,
+                           latentam_bins* bins, const uint32_t* off, int slot, cudaStream_t st) {
+    const int64_t num_tiles = (int64_t)cam.tiles_x * cam.tiles_y;
+    cudaError_t e;
+    if (N == 0) {
+        bins->num_pairs = 0;
+        return LATENTAM_OK;
+    }
+    uint32_t *cnt, *host;
+    LAT_TRY(bin_slot(ctx, slot, &cnt, &host));
     const uint32_t pairs = host[1], sort_error = host[2], tc_error = host[3];
     if (sort_error) {
         e = cudaMemsetAsync(cnt + 2, 0, sizeof(uint32_t), st);
@@ -498,6 +521,7 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
         return LATENTAM_ERR_TIMEOUT;
     }
     if (tc_error) {
+        host[3] = 0;  // reported once, by this slot
         e = cudaMemsetAsync(ctx->dev_flags, 0, sizeof(int), st);
         if (e != cudaSuccess) return cuda_error(e, "clear the tensor-core wait flag");
         set_error("a bounded wait of a tensor-core decode kernel gave up in an earlier call (its loss was NaN)");
@@ -547,9 +571,25 @@ latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projec
                             (uint64_t)num_tiles, (uint64_t)cam.tiles_x,
                             reinterpret_cast<uint64_t>(proj.depth), reinterpret_cast<uint64_t>(proj.tiles_touched),
                             reinterpret_cast<uint64_t>(proj.rect), reinterpret_cast<uint64_t>(bins->pair_ids),
-                            reinterpret_cast<uint64_t>(bins->tile_ranges), reinterpret_cast<uint64_t>(st),
-                            ctx->ws_generation, (uint64_t)ctx->test_stall_sort};
+                            reinterpret_cast<uint64_t>(bins->tile_ranges), reinterpret_cast<uint64_t>(off),
+                            reinterpret_cast<uint64_t>(cnt), reinterpret_cast<uint64_t>(st), ctx->ws_generation,
+                            (uint64_t)ctx->test_stall_sort};
     return cached_launch(ctx, key, (int)(sizeof(key) / sizeof(key[0])), st, rest);
+}
+
+latentam_status bin_and_sort(latentam_ctx* ctx, int32_t N, const latentam_projected& proj,
+                             const CamParams& cam, latentam_bins* bins, cudaStream_t st) {
+    uint32_t* off = nullptr;
+    if (N > 0) {
+        off = static_cast<uint32_t*>(ws(ctx, WS_OFFSETS, sizeof(uint32_t) * ((size_t)N + 1)));
+        if (!off) return LATENTAM_ERR_OUT_OF_MEMORY;
+    }
+    LAT_TRY(bin_count(ctx, N, proj, cam, bins, off, 0, st));
+    if (N > 0) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_error(e, "sync for the pair count");
+    }
+    return bin_finish(ctx, N, proj, cam, bins, off, 0, st);
 }
 
 }  // namespace lat
