@@ -542,8 +542,12 @@ latentam_status latentam_ctx_destroy(latentam_ctx* ctx) {
         if (ctx->slot_ptr[s]) cudaFree(ctx->slot_ptr[s]);
     for (int s = 0; s < LATENTAM_NUM_STAGES; ++s)
         for (int i = 0; i < ctx->prof[s].created; ++i) cudaEventDestroy(ctx->prof[s].ev[i]);
-    for (int i = 0; i < 2 * LATENTAM_MAX_BATCH; ++i)
+    for (int i = 0; i < 8 * LATENTAM_MAX_BATCH; ++i)
         if (ctx->frame_ptr[i]) cudaFree(ctx->frame_ptr[i]);
+    if (ctx->bin_streams_ready) {
+        for (cudaStream_t b : ctx->bin_streams) cudaStreamDestroy(b);
+        for (cudaEvent_t v : ctx->bin_events) cudaEventDestroy(v);
+    }
     if (ctx->graphs) {
         ctx->graphs->clear();
         delete ctx->graphs;
@@ -1226,6 +1230,17 @@ struct QueryGroup {
 
 }  // namespace
 
+// The side streams and events of concurrent batch binning (created once per context).
+latentam_status bin_streams(latentam_ctx* ctx) {
+    if (ctx->bin_streams_ready) return LATENTAM_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&ctx->bin_streams[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->bin_events[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_error(e, "binning streams");
+    ctx->bin_streams_ready = 1;
+    return LATENTAM_OK;
+}
+
 extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam_batch_frame* frames,
                                                int32_t n_frames, const void* F, latentam_dtype F_dtype,
                                                const uint8_t* mask, latentam_dictionary* dict,
@@ -1307,30 +1322,59 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
         bins.tile_ranges = reinterpret_cast<int32_t*>(pb + o_tr);
         bins.pair_ids = static_cast<int32_t*>(ctx->frame_ptr[2 * k + 1]);
         bins.capacity = (int64_t)(ctx->frame_bytes[2 * k + 1] / sizeof(int32_t));
-        {
-            StageTimer tm(ctx, LATENTAM_STAGE_PROJECT, st);
-            LAT_TRY(launch_project(fr.gaussians, fs[k].cam, fs[k].proj, st));
-        }
-        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
-        LAT_TRY(bin_count(ctx, N, fs[k].proj, fs[k].cam, &bins, offs + off_at[k], k, st));
     }
-    if (any_gauss) {
+    {
+        // the keyframes are projected and binned at the same time, keyframe k on side stream
+        // k % 8 (each binning slot has its own scratch), between a fork from and a join back into
+        // the step's stream (timed as the sort stage: the projection of a batch is part of it)
         StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_error(e, "sync for the pair counts");
-    }
-    for (int k = 0; k < n_frames; ++k) {
-        const int N = frames[k].gaussians.n;
-        latentam_bins& bins = fs[k].bins;
-        StageTimer tm(ctx, LATENTAM_STAGE_SORT, st);
-        latentam_status s = bin_finish(ctx, N, fs[k].proj, fs[k].cam, &bins, offs + off_at[k], k, st);
-        if (s == LATENTAM_ERR_CAPACITY) {
-            bins.pair_ids = static_cast<int32_t*>(frame_ws(ctx, 2 * k + 1, sizeof(int32_t) * (size_t)bins.num_pairs));
-            if (!bins.pair_ids) return LATENTAM_ERR_OUT_OF_MEMORY;
-            bins.capacity = bins.num_pairs;
-            s = bin_finish(ctx, N, fs[k].proj, fs[k].cam, &bins, offs + off_at[k], k, st);
+        const int nside = n_frames > 1 ? std::min(n_frames, 8) : 0;
+        if (nside > 0) {
+            LAT_TRY(bin_streams(ctx));
+            cudaError_t e = cudaEventRecord(ctx->bin_events[0], st);
+            for (int i = 0; i < nside && e == cudaSuccess; ++i)
+                e = cudaStreamWaitEvent(ctx->bin_streams[i], ctx->bin_events[0], 0);
+            if (e != cudaSuccess) return cuda_error(e, "fork the binning streams");
         }
+        auto sk = [&](int k) { return nside > 0 ? ctx->bin_streams[k % nside] : st; };
+        // every wait below that returns early still joins the side streams into the step's stream
+        auto join = [&]() -> latentam_status {
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < nside && e == cudaSuccess; ++i) {
+                e = cudaEventRecord(ctx->bin_events[1 + i], ctx->bin_streams[i]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->bin_events[1 + i], 0);
+            }
+            return e == cudaSuccess ? LATENTAM_OK : cuda_error(e, "join the binning streams");
+        };
+        latentam_status s = LATENTAM_OK;
+        for (int k = 0; k < n_frames && s == LATENTAM_OK; ++k) {
+            s = launch_project(frames[k].gaussians, fs[k].cam, fs[k].proj, sk(k));
+            if (s == LATENTAM_OK)
+                s = bin_count(ctx, frames[k].gaussians.n, fs[k].proj, fs[k].cam, &fs[k].bins, offs + off_at[k], k,
+                              sk(k));
+        }
+        if (s == LATENTAM_OK && any_gauss) {
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < std::max(nside, 1) && e == cudaSuccess; ++i) e = cudaStreamSynchronize(sk(i));
+            if (e != cudaSuccess) s = cuda_error(e, "sync for the pair counts");
+        }
+        for (int k = 0; k < n_frames && s == LATENTAM_OK; ++k) {
+            const int N = frames[k].gaussians.n;
+            latentam_bins& bins = fs[k].bins;
+            s = bin_finish(ctx, N, fs[k].proj, fs[k].cam, &bins, offs + off_at[k], k, sk(k));
+            if (s == LATENTAM_ERR_CAPACITY) {
+                bins.pair_ids =
+                    static_cast<int32_t*>(frame_ws(ctx, 2 * k + 1, sizeof(int32_t) * (size_t)bins.num_pairs));
+                if (!bins.pair_ids) s = LATENTAM_ERR_OUT_OF_MEMORY;
+                if (s != LATENTAM_ERR_OUT_OF_MEMORY) {
+                    bins.capacity = bins.num_pairs;
+                    s = bin_finish(ctx, N, fs[k].proj, fs[k].cam, &bins, offs + off_at[k], k, sk(k));
+                }
+            }
+        }
+        const latentam_status sj = join();
         LAT_TRY(s);
+        LAT_TRY(sj);
     }
     // one work list over the tiles of every frame, longest lists first, and the two work tickets
     // of the persistent render launches

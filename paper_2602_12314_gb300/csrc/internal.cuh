@@ -98,9 +98,15 @@ struct latentam_ctx {
     size_t slot_bytes[lat::WS_NUM_SLOTS];
     int profiling;
     lat::StageProfile prof[LATENTAM_NUM_STAGES];
-    // per-frame buffers of the batched step: [2k] projection + tile ranges, [2k+1] pairs
-    void* frame_ptr[2 * LATENTAM_MAX_BATCH];
-    size_t frame_bytes[2 * LATENTAM_MAX_BATCH];
+    // per-frame buffers of the batched step: [2k] projection + tile ranges, [2k+1] pairs,
+    // [2 LATENTAM_MAX_BATCH + 6k + j] the scratch of binning slot k (j: scan sums, sort keys 0 / 1,
+    // sort values, long-list merge buffers, radix counters)
+    void* frame_ptr[8 * LATENTAM_MAX_BATCH];
+    size_t frame_bytes[8 * LATENTAM_MAX_BATCH];
+    // streams on which the keyframes of a batch are binned concurrently, created on first use
+    cudaStream_t bin_streams[8];
+    cudaEvent_t bin_events[9];  // [0] fork, [1 + i] join of stream i
+    int bin_streams_ready;
     // CUDA graphs of the step's iteration (see latentam_graphs_enable)
     int use_graphs;
     uint64_t ws_generation;  // bumped whenever a workspace buffer moves
@@ -173,15 +179,24 @@ void count_launch();
 latentam_status launch_project(const latentam_gaussians& g, const CamParams& cam,
                                const latentam_projected& out, cudaStream_t st);
 
-// Exclusive scan of n uint32 values; *total_dev (device, nullable) receives the sum.
+// Exclusive scan of n uint32 values; *total_dev (device, nullable) receives the sum.  sums: the
+// block-sum scratch (scan_scratch_words(n) words), the context's workspace when null.
 latentam_status scan_exclusive_u32(latentam_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
-                                   uint32_t* total_dev, cudaStream_t st);
+                                   uint32_t* total_dev, cudaStream_t st,
+                                   uint32_t* sums = nullptr);
 // Stable LSD radix sort of n (key, value) pairs on key bits [0, bits), bits <= 32, n < 2^30.
 // keys[0]/vals[0] hold the input (vals_iota: value = index, vals[0] is then only scratch);
 // keys[1]/vals[1] are scratch.  *result receives the index of the buffer pair holding the
-// sorted output.  *err (device) is set if a bounded cross-block wait gave up.
+// sorted output.  *err (device) is set if a bounded cross-block wait gave up.  counters: the
+// digit-count, ticket and look-back scratch (radix_scratch_words(n, bits) words), the context's
+// workspace when null.
 latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uint32_t* const vals[2], bool vals_iota,
-                                 int64_t n, int bits, int* result, uint32_t* err, cudaStream_t st);
+                                 int64_t n, int bits, int* result, uint32_t* err, cudaStream_t st,
+                                 uint32_t* counters = nullptr);
+// 32-bit words of the scratch of scan_exclusive_u32 over n items and of radix_sort_pairs over n
+// keys of `bits` bits (the buffers the optional `sums` / `counters` arguments must hold).
+size_t scan_scratch_words(int64_t n);
+size_t radix_scratch_words(int64_t n, int bits);
 latentam_status bin_and_sort(latentam_ctx* ctx, int32_t n, const latentam_projected& proj,
                              const CamParams& cam, latentam_bins* bins, cudaStream_t st);
 // The two halves of bin_and_sort, for several keyframes binned with one host synchronisation:

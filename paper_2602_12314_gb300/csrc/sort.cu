@@ -389,8 +389,10 @@ int ceil_log2(int64_t v) {
 
 }  // namespace
 
+size_t scan_scratch_words(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile + 1); }
+
 latentam_status scan_exclusive_u32(latentam_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
-                                   uint32_t* total_dev, cudaStream_t st) {
+                                   uint32_t* total_dev, cudaStream_t st, uint32_t* sums) {
     if (n <= 0) {
         if (total_dev) {
             cudaError_t e = cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), st);
@@ -403,7 +405,7 @@ latentam_status scan_exclusive_u32(latentam_ctx* ctx, const uint32_t* in, uint32
         set_error("scan of %lld items exceeds the supported %lld", (long long)n, (long long)kScanTile * kScanTile);
         return LATENTAM_ERR_UNSUPPORTED_SHAPE;
     }
-    uint32_t* sums = static_cast<uint32_t*>(ws(ctx, WS_SCAN_SUMS, sizeof(uint32_t) * (size_t)(nb + 1)));
+    if (!sums) sums = static_cast<uint32_t*>(ws(ctx, WS_SCAN_SUMS, sizeof(uint32_t) * (size_t)(nb + 1)));
     if (!sums) return LATENTAM_ERR_OUT_OF_MEMORY;
     scan_tiles<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, sums, n);
     LAT_CHECK_LAUNCH("scan_tiles");
@@ -416,8 +418,15 @@ latentam_status scan_exclusive_u32(latentam_ctx* ctx, const uint32_t* in, uint32
     return LATENTAM_OK;
 }
 
+size_t radix_scratch_words(int64_t n, int bits) {
+    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    const int64_t nb = (n + kRsTile - 1) / kRsTile;
+    return (size_t)(passes + 1) * kRadix + (size_t)passes * (size_t)nb * kRadix;
+}
+
 latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uint32_t* const vals[2], bool vals_iota,
-                                 int64_t n, int bits, int* result, uint32_t* err, cudaStream_t st) {
+                                 int64_t n, int bits, int* result, uint32_t* err, cudaStream_t st,
+                                 uint32_t* counters) {
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
     *result = passes % 2;
     if (n <= 0) return LATENTAM_OK;
@@ -428,8 +437,8 @@ latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uin
     const int64_t nb = (n + kRsTile - 1) / kRsTile;
     // [digit counts: passes x 256 | tickets: 256 | look-back words: passes x nb x 256], zeroed;
     // tickets[255] is never written (the word an armed test stall polls)
-    const size_t words = (size_t)(passes + 1) * kRadix + (size_t)passes * (size_t)nb * kRadix;
-    uint32_t* buf = static_cast<uint32_t*>(ws(ctx, WS_SORT_HIST, sizeof(uint32_t) * words));
+    const size_t words = radix_scratch_words(n, bits);
+    uint32_t* buf = counters ? counters : static_cast<uint32_t*>(ws(ctx, WS_SORT_HIST, sizeof(uint32_t) * words));
     if (!buf) return LATENTAM_ERR_OUT_OF_MEMORY;
     cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(uint32_t) * words, st);
     if (e != cudaSuccess) return cuda_error(e, "clear radix sort counters");
@@ -458,6 +467,15 @@ latentam_status radix_sort_pairs(latentam_ctx* ctx, uint32_t* const keys[2], uin
 // device 4 words at cnt + 16 k ([1] the pair count P, [2] the sort error word), read back into
 // 4 pinned host words at host_counts + 8 + 4 k with the tensor-core wait flag.
 namespace {
+// Scratch buffer j of binning slot k (j: 0 scan sums, 1-2 sort keys, 3 sort values, 4 long-list
+// merge buffers, 5 radix counters): slot 0 uses the context's workspace slots, the others their
+// own buffers, so that the keyframes of a batch can be binned at the same time.
+void* bin_scratch(latentam_ctx* ctx, int slot, int j, size_t bytes) {
+    static const Slot shared[6] = {WS_SCAN_SUMS, WS_SORT_K0, WS_SORT_K1, WS_SORT_V0, WS_SORT_V1, WS_SORT_HIST};
+    if (slot == 0) return ws(ctx, shared[j], bytes);
+    return frame_ws(ctx, 2 * LATENTAM_MAX_BATCH + 6 * slot + j, bytes);
+}
+
 latentam_status bin_slot(latentam_ctx* ctx, int slot, uint32_t** cnt, uint32_t** host) {
     if (slot < 0 || slot >= LATENTAM_MAX_BATCH) {
         set_error("binning slot %d outside 0..%d", slot, LATENTAM_MAX_BATCH - 1);
@@ -485,11 +503,14 @@ latentam_status bin_count(latentam_ctx* ctx, int32_t N, const latentam_projected
     // cnt[1], read back with cnt[2]: raised by a sort pass whose look-back gave up; it outlives
     // the call and is reported (and cleared) by the slot's next binning.  The same frame size
     // and buffers replay one captured graph.
+    uint32_t* sums = static_cast<uint32_t*>(bin_scratch(ctx, slot, 0, sizeof(uint32_t) * scan_scratch_words(N)));
+    if (!sums) return LATENTAM_ERR_OUT_OF_MEMORY;
     auto pre = [&](cudaStream_t s) -> latentam_status {
         cudaError_t e2 = cudaMemsetAsync(bins->tile_ranges, 0, sizeof(int2) * (size_t)num_tiles, s);
         if (e2 == cudaSuccess) e2 = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s);
         if (e2 != cudaSuccess) return cuda_error(e2, "clear ranges and counters");
-        LAT_TRY(scan_exclusive_u32(ctx, reinterpret_cast<const uint32_t*>(proj.tiles_touched), off, N, cnt + 1, s));
+        LAT_TRY(scan_exclusive_u32(ctx, reinterpret_cast<const uint32_t*>(proj.tiles_touched), off, N, cnt + 1, s,
+                                   sums));
         e2 = cudaMemcpyAsync(host, cnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e2 == cudaSuccess)  // and the tensor-core kernels' sticky wait flag
             e2 = cudaMemcpyAsync(host + 3, ctx->dev_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
@@ -499,7 +520,8 @@ latentam_status bin_count(latentam_ctx* ctx, int32_t N, const latentam_projected
     const uint64_t pre_key[] = {0x62696e302d707265ull /* tag: counting phase */, (uint64_t)N, (uint64_t)num_tiles,
                                 reinterpret_cast<uint64_t>(proj.tiles_touched),
                                 reinterpret_cast<uint64_t>(bins->tile_ranges), reinterpret_cast<uint64_t>(host),
-                                reinterpret_cast<uint64_t>(off), reinterpret_cast<uint64_t>(st), ctx->ws_generation};
+                                reinterpret_cast<uint64_t>(off), reinterpret_cast<uint64_t>(sums),
+                                reinterpret_cast<uint64_t>(st), ctx->ws_generation};
     return cached_launch(ctx, pre_key, (int)(sizeof(pre_key) / sizeof(pre_key[0])), st, pre);
 }
 
@@ -539,11 +561,13 @@ latentam_status bin_finish(latentam_ctx* ctx, int32_t N, const latentam_projecte
     const size_t pbytes = sizeof(uint32_t) * (size_t)P;
     const int tile_bits = std::max(1, ceil_log2(num_tiles));
     const int passes = (tile_bits + 7) / 8;
-    uint32_t* pk[2] = {static_cast<uint32_t*>(ws(ctx, WS_SORT_K0, pbytes)),
-                       static_cast<uint32_t*>(ws(ctx, WS_SORT_K1, pbytes))};
-    uint32_t* scratch = static_cast<uint32_t*>(ws(ctx, WS_SORT_V0, pbytes));
-    uint64_t* lng = static_cast<uint64_t*>(ws(ctx, WS_SORT_V1, 2 * sizeof(uint64_t) * (size_t)P));
-    if (!pk[0] || !pk[1] || !scratch || !lng) return LATENTAM_ERR_OUT_OF_MEMORY;
+    uint32_t* pk[2] = {static_cast<uint32_t*>(bin_scratch(ctx, slot, 1, pbytes)),
+                       static_cast<uint32_t*>(bin_scratch(ctx, slot, 2, pbytes))};
+    uint32_t* scratch = static_cast<uint32_t*>(bin_scratch(ctx, slot, 3, pbytes));
+    uint64_t* lng = static_cast<uint64_t*>(bin_scratch(ctx, slot, 4, 2 * sizeof(uint64_t) * (size_t)P));
+    uint32_t* rcnt =
+        static_cast<uint32_t*>(bin_scratch(ctx, slot, 5, sizeof(uint32_t) * radix_scratch_words(P, tile_bits)));
+    if (!pk[0] || !pk[1] || !scratch || !lng || !rcnt) return LATENTAM_ERR_OUT_OF_MEMORY;
     // the tile sort's result lands in buffer passes % 2: make that the caller's pair list
     uint32_t* ids = reinterpret_cast<uint32_t*>(bins->pair_ids);
     uint32_t* pv[2] = {passes % 2 == 0 ? ids : scratch, passes % 2 == 0 ? scratch : ids};
@@ -556,7 +580,7 @@ latentam_status bin_finish(latentam_ctx* ctx, int32_t N, const latentam_projecte
         LAT_CHECK_LAUNCH("emit_pairs");
         // 2. stable sort on the tile bits (index order kept within a tile)
         int r = 0;
-        LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, cnt + 2, s));
+        LAT_TRY(radix_sort_pairs(ctx, pk, pv, false, P, tile_bits, &r, cnt + 2, s, rcnt));
         // 3. ranges
         tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(pk[r], P, cnt + 2,
                                                                  reinterpret_cast<int2*>(bins->tile_ranges));
@@ -572,7 +596,8 @@ latentam_status bin_finish(latentam_ctx* ctx, int32_t N, const latentam_projecte
                             reinterpret_cast<uint64_t>(proj.depth), reinterpret_cast<uint64_t>(proj.tiles_touched),
                             reinterpret_cast<uint64_t>(proj.rect), reinterpret_cast<uint64_t>(bins->pair_ids),
                             reinterpret_cast<uint64_t>(bins->tile_ranges), reinterpret_cast<uint64_t>(off),
-                            reinterpret_cast<uint64_t>(cnt), reinterpret_cast<uint64_t>(st), ctx->ws_generation,
+                            reinterpret_cast<uint64_t>(cnt), reinterpret_cast<uint64_t>(rcnt),
+                            reinterpret_cast<uint64_t>(lng), reinterpret_cast<uint64_t>(st), ctx->ws_generation,
                             (uint64_t)ctx->test_stall_sort};
     return cached_launch(ctx, key, (int)(sizeof(key) / sizeof(key[0])), st, rest);
 }
