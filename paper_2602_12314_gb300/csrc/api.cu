@@ -547,6 +547,7 @@ latentam_status latentam_ctx_destroy(latentam_ctx* ctx) {
     if (ctx->bin_streams_ready) {
         for (cudaStream_t b : ctx->bin_streams) cudaStreamDestroy(b);
         for (cudaEvent_t v : ctx->bin_events) cudaEventDestroy(v);
+        for (cudaEvent_t v : ctx->iter_events) cudaEventDestroy(v);
     }
     if (ctx->graphs) {
         ctx->graphs->clear();
@@ -1061,6 +1062,41 @@ latentam_status latentam_backward_full(latentam_ctx* ctx, const latentam_gaussia
     return launch_project_bwd(*g, cp, dgeo, d_means, d_quats, d_scales, d_opacities, st);
 }
 
+// The side streams and events of concurrent batch binning and of the render backward branch of
+// an iteration (created once per context).
+latentam_status bin_streams(latentam_ctx* ctx) {
+    if (ctx->bin_streams_ready) return LATENTAM_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&ctx->bin_streams[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->bin_events[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ctx->iter_events[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_error(e, "binning streams");
+    ctx->bin_streams_ready = 1;
+    return LATENTAM_OK;
+}
+
+// The render backward of an iteration as a branch of its own: `body` runs on a side stream that
+// waits for everything enqueued on `s` so far (the decode up to its final dQ); join() makes `s`
+// wait for the branch.  Inside a stream capture the branch becomes parallel graph nodes, so the
+// render backward overlaps the decode's pixel reductions of dV and dK.
+latentam_status fork_branch(latentam_ctx* ctx, cudaStream_t s,
+                            const std::function<latentam_status(cudaStream_t)>& body) {
+    LAT_TRY(bin_streams(ctx));
+    cudaStream_t side = ctx->bin_streams[0];
+    cudaError_t e = cudaEventRecord(ctx->iter_events[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ctx->iter_events[0], 0);
+    if (e != cudaSuccess) return cuda_error(e, "fork the render backward");
+    const latentam_status r = body(side);
+    e = cudaEventRecord(ctx->iter_events[1], side);
+    if (e != cudaSuccess) return cuda_error(e, "end the render backward branch");
+    return r;
+}
+latentam_status join_branch(latentam_ctx* ctx, cudaStream_t s) {
+    cudaError_t e = cudaStreamWaitEvent(s, ctx->iter_events[1], 0);
+    return e == cudaSuccess ? LATENTAM_OK : cuda_error(e, "join the render backward");
+}
+
 latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, latentam_params* params,
                               const latentam_loss_cfg* cfg, latentam_adam_cfg* adam, int32_t iters, int32_t learn_f,
                               latentam_precision prec, double* loss_host, latentam_stream stream) {
@@ -1168,18 +1204,31 @@ latentam_status latentam_step(latentam_ctx* ctx, const latentam_frame* frame, la
             if (pooled) LAT_TRY(launch_pool_fwd(plan, Q, d, Qm, s));
         }
         float* dQd = learn_f ? (pooled ? dQm : dQ) : nullptr;
+        auto render_bwd = [&](cudaStream_t b) -> latentam_status {
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, b);
+            if (pooled) LAT_TRY(launch_pool_bwd(plan, dQm, d, dQ, b));
+            return launch_render_bwd(cp, proj, bins, nc, dQ, d, df, N, b);
+        };
+        // the render backward needs only dQ: it branches off once the decode has made it final
+        const std::function<latentam_status(cudaStream_t)> fork = [&](cudaStream_t ds) {
+            return fork_branch(ctx, ds, render_bwd);
+        };
+        // (not under the stage timers: each stage is then timed on its own)
+        const bool branch = learn_f && N > 0 && !paper && !ctx->profiling;
+        ctx->after_dq = branch ? &fork : nullptr;
+        ctx->after_dq_called = 0;
+        latentam_status sd;
         if (paper)
-            LAT_TRY(latentam_decode_loss_bwd_paper(ctx, Qdec, ndec, d, params->K, params->V, params->V0, M, D, tau,
-                                                   frame->F, frame->F_dtype, frame->mask, cfg, prec, lp, dQd, dK, dV,
-                                                   s));
+            sd = latentam_decode_loss_bwd_paper(ctx, Qdec, ndec, d, params->K, params->V, params->V0, M, D, tau,
+                                                frame->F, frame->F_dtype, frame->mask, cfg, prec, lp, dQd, dK, dV, s);
         else
-            LAT_TRY(latentam_decode_loss_bwd(ctx, Qdec, ndec, d, params->K, params->V, params->V0, M, D, frame->F,
-                                             frame->F_dtype, frame->mask, cfg, prec, lp, dQd, dK, dV, s));
-        if (learn_f && N > 0) {
-            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, s);
-            if (pooled) LAT_TRY(launch_pool_bwd(plan, dQm, d, dQ, s));
-            LAT_TRY(launch_render_bwd(cp, proj, bins, nc, dQ, d, df, N, s));
-        }
+            sd = latentam_decode_loss_bwd(ctx, Qdec, ndec, d, params->K, params->V, params->V0, M, D, frame->F,
+                                          frame->F_dtype, frame->mask, cfg, prec, lp, dQd, dK, dV, s);
+        ctx->after_dq = nullptr;
+        const bool joined = ctx->after_dq_called != 0;
+        if (joined) LAT_TRY(join_branch(ctx, s));  // joined even when the decode failed after the fork
+        LAT_TRY(sd);
+        if (learn_f && N > 0 && !joined) LAT_TRY(render_bwd(s));
         AdamTensor t[3];
         int cnt = 0;
         if (learn_f) t[cnt++] = AdamTensor{params->f, df, params->m_f, params->v_f, (int64_t)N * d, adam->lr_f};
@@ -1229,17 +1278,6 @@ struct QueryGroup {
 };
 
 }  // namespace
-
-// The side streams and events of concurrent batch binning (created once per context).
-latentam_status bin_streams(latentam_ctx* ctx) {
-    if (ctx->bin_streams_ready) return LATENTAM_OK;
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&ctx->bin_streams[i], cudaStreamNonBlocking);
-    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->bin_events[i], cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_error(e, "binning streams");
-    ctx->bin_streams_ready = 1;
-    return LATENTAM_OK;
-}
 
 extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam_batch_frame* frames,
                                                int32_t n_frames, const void* F, latentam_dtype F_dtype,
@@ -1470,22 +1508,34 @@ extern "C" latentam_status latentam_step_batch(latentam_ctx* ctx, const latentam
                 LAT_TRY(launch_pool_fwd(plans[k], Q + fs[k].pix_off * d, d, Qm + row_off[k] * d, s));
         }
         float* dQd = learn_f ? (pooled ? dQm : dQ) : nullptr;
-        if (paper)
-            LAT_TRY(latentam_decode_loss_bwd_paper(ctx, pooled ? Qm : Q, ndec, d, dict->K, dict->V, dict->V0, M, D, tau,
-                                                   F, F_dtype, mask, cfg, prec, lp, dQd, dK, dV, s));
-        else
-            LAT_TRY(latentam_decode_loss_bwd(ctx, pooled ? Qm : Q, ndec, d, dict->K, dict->V, dict->V0, M, D, F,
-                                             F_dtype, mask, cfg, prec, lp, dQd, dK, dV, s));
-        if (learn_f) {
-            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, s);
+        auto render_bwd = [&](cudaStream_t b) -> latentam_status {
+            StageTimer tm(ctx, LATENTAM_STAGE_RENDER_BWD, b);
             for (int u = 0; u < n_groups; ++u) {
-                cudaError_t e = cudaMemsetAsync(groups[u].df, 0, sizeof(float) * (size_t)groups[u].n * d, s);
+                cudaError_t e = cudaMemsetAsync(groups[u].df, 0, sizeof(float) * (size_t)groups[u].n * d, b);
                 if (e != cudaSuccess) return cuda_error(e, "memset df");
             }
             for (int k = 0; pooled && k < n_frames; ++k)
-                LAT_TRY(launch_pool_bwd(plans[k], dQm + row_off[k] * d, d, dQ + fs[k].pix_off * d, s));
-            LAT_TRY(launch_render_bwd_batch(jobs, d, work, total_tiles, tickets + 1, s));
-        }
+                LAT_TRY(launch_pool_bwd(plans[k], dQm + row_off[k] * d, d, dQ + fs[k].pix_off * d, b));
+            return launch_render_bwd_batch(jobs, d, work, total_tiles, tickets + 1, b);
+        };
+        // the render backward needs only dQ: it branches off once the decode has made it final
+        const std::function<latentam_status(cudaStream_t)> fork = [&](cudaStream_t ds) {
+            return fork_branch(ctx, ds, render_bwd);
+        };
+        ctx->after_dq = learn_f && !paper && !ctx->profiling ? &fork : nullptr;  // (see latentam_step)
+        ctx->after_dq_called = 0;
+        latentam_status sd;
+        if (paper)
+            sd = latentam_decode_loss_bwd_paper(ctx, pooled ? Qm : Q, ndec, d, dict->K, dict->V, dict->V0, M, D, tau,
+                                                F, F_dtype, mask, cfg, prec, lp, dQd, dK, dV, s);
+        else
+            sd = latentam_decode_loss_bwd(ctx, pooled ? Qm : Q, ndec, d, dict->K, dict->V, dict->V0, M, D, F,
+                                          F_dtype, mask, cfg, prec, lp, dQd, dK, dV, s);
+        ctx->after_dq = nullptr;
+        const bool joined = ctx->after_dq_called != 0;
+        if (joined) LAT_TRY(join_branch(ctx, s));  // joined even when the decode failed after the fork
+        LAT_TRY(sd);
+        if (learn_f && !joined) LAT_TRY(render_bwd(s));
         StageTimer tm(ctx, LATENTAM_STAGE_ADAM, s);
         if (step_dev) LAT_TRY(launch_step_advance(const_cast<int*>(step_dev), s));
         AdamTensor t[8];

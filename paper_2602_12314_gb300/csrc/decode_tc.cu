@@ -1231,6 +1231,11 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
             LAT_TRY((launch_gemm<DqEpi<BNq, SPLIT>>(mdS, mK, grow, g4, qp, b.err, st)));
         }
     }
+    // dQ is final: work of the caller's that needs only dQ may branch off here
+    if (ctx->after_dq && a.dQ) {
+        LAT_TRY((*ctx->after_dq)(st));
+        ctx->after_dq_called = 1;
+    }
     // G5: dV = A^T dFhat (+ trust region), both operands pixel-major (MN-major); each candidate
     // the tuner times includes the reduction of its partials (more splits, more partials to sum)
     auto reduce_dV = [&](int z) -> latentam_status {

@@ -106,7 +106,13 @@ struct latentam_ctx {
     // streams on which the keyframes of a batch are binned concurrently, created on first use
     cudaStream_t bin_streams[8];
     cudaEvent_t bin_events[9];  // [0] fork, [1 + i] join of stream i
+    cudaEvent_t iter_events[2];  // fork and join of the render backward branch of an iteration
     int bin_streams_ready;
+    // set by a step around its decode: called by the tensor-core decode on its stream once dQ is
+    // final, before the pixel reductions of dV and dK (the step forks its render backward there);
+    // after_dq_called reports whether it ran
+    const std::function<latentam_status(cudaStream_t)>* after_dq;
+    int after_dq_called;
     // CUDA graphs of the step's iteration (see latentam_graphs_enable)
     int use_graphs;
     uint64_t ws_generation;  // bumped whenever a workspace buffer moves
