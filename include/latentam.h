@@ -19,7 +19,11 @@
  *    streams without an ordering event) race on it: enqueue a context's calls on one stream
  *    or order the streams.
  *  - All work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream)
- *    and returns without waiting, except where a call says it synchronises.
+ *    and returns without waiting, except where a call says it synchronises.  The steps run
+ *    some of it on the context's own side streams (the keyframes of a batch binned at once;
+ *    the render backward of an iteration beside the decode's pixel reductions), each branch
+ *    forked from `stream` after the work enqueued on it before the call and joined back into
+ *    it before the call returns: ordered for the caller as if all of it ran on `stream`.
  *  - Gradients are OVERWRITTEN, never accumulated; callers zero nothing.
  *  - Shapes outside the supported set return LATENTAM_ERR_UNSUPPORTED_SHAPE; there is no
  *    slow or CPU fallback.  On any error nothing is guaranteed about the outputs.

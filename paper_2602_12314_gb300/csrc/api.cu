@@ -1066,18 +1066,30 @@ latentam_status latentam_backward_full(latentam_ctx* ctx, const latentam_gaussia
 // an iteration (created once per context).
 latentam_status bin_streams(latentam_ctx* ctx) {
     if (ctx->bin_streams_ready) return LATENTAM_OK;
+    cudaStream_t sides[8] = {};
+    cudaEvent_t bev[9] = {}, iev[2] = {};
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&ctx->bin_streams[i], cudaStreamNonBlocking);
-    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->bin_events[i], cudaEventDisableTiming);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
-        e = cudaEventCreateWithFlags(&ctx->iter_events[i], cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_error(e, "binning streams");
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&sides[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&bev[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&iev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {  // release what was created
+        for (cudaStream_t x : sides)
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t x : bev)
+            if (x) cudaEventDestroy(x);
+        for (cudaEvent_t x : iev)
+            if (x) cudaEventDestroy(x);
+        return cuda_error(e, "side streams");
+    }
+    for (int i = 0; i < 8; ++i) ctx->bin_streams[i] = sides[i];
+    for (int i = 0; i < 9; ++i) ctx->bin_events[i] = bev[i];
+    for (int i = 0; i < 2; ++i) ctx->iter_events[i] = iev[i];
     ctx->bin_streams_ready = 1;
     return LATENTAM_OK;
 }
 
 // The render backward of an iteration as a branch of its own: `body` runs on a side stream that
-// waits for everything enqueued on `s` so far (the decode up to its final dQ); join() makes `s`
+// waits for everything enqueued on `s` so far (the decode up to its final dQ); join_branch makes `s`
 // wait for the branch.  Inside a stream capture the branch becomes parallel graph nodes, so the
 // render backward overlaps the decode's pixel reductions of dV and dK.
 latentam_status fork_branch(latentam_ctx* ctx, cudaStream_t s,
