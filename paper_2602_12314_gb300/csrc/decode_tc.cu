@@ -163,29 +163,45 @@ __global__ void tc_trust_region(const float* __restrict__ V, const float* __rest
 }
 
 // out[j][k] = scale * sum_z part[z][j][k] (+ coef[j] (V - V0)[j][k]) for k < ncols (of ld columns).
-// A block owns 32 consecutive outputs (one per lane); its 8 warps take every 8th split, so the
-// reads of each split are contiguous and many splits are summed in parallel.
-__global__ void __launch_bounds__(256) tc_reduce_parts(const float* __restrict__ part, int splits, int rows, int ld,
-                                                       int ncols, float scale, const float* __restrict__ coef,
-                                                       const float* __restrict__ V, const float* __restrict__ V0,
-                                                       float* __restrict__ out) {
-    __shared__ float acc[8][32];
+// A block owns 32 consecutive outputs (one per lane); its W warps take every W-th split, so the
+// reads of each split are contiguous and many splits are summed in parallel (W = 32 for the
+// thousands of per-tile partials of the fused dK).
+// Eight loads of a warp's splits are in flight before their (in-order) additions.  T: the sum
+// goes to out[k][j] instead (partials stored transposed).
+template <int W, bool T = false>
+__global__ void __launch_bounds__(32 * W, W >= 32 ? 2 : 8)
+    tc_reduce_parts(const float* __restrict__ part, int splits, int rows, int ld, int ncols, float scale,
+                    const float* __restrict__ coef, const float* __restrict__ V, const float* __restrict__ V0,
+                    float* __restrict__ out) {
+    __shared__ float acc[W][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * 32 + lane;
     const bool live = e < (int64_t)rows * ncols;
     const int j = live ? (int)(e / ncols) : 0, k = live ? (int)(e % ncols) : 0;
     float s = 0.f;
-    if (live)
-        for (int z = w; z < splits; z += 8) s += part[((int64_t)z * rows + j) * ld + k];
+    if (live) {
+        const int64_t step = (int64_t)W * rows * ld;  // W splits
+        const float* p = part + (int64_t)j * ld + k + (int64_t)w * rows * ld;
+        int z = w;
+        for (; W >= 32 && z + 7 * W < splits; z += 8 * W) {  // (fewer registers for W = 8: more blocks)
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u, p += step) v[u] = __ldg(p);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+#pragma unroll 4
+        for (; z < splits; z += W, p += step) s += __ldg(p);
+    }
     acc[w][lane] = s;
     __syncthreads();
     if (w == 0 && live) {
         float t = 0.f;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) t += acc[q][lane];
+        for (int q = 0; q < W; ++q) t += acc[q][lane];
         t *= scale;
         if (coef) t += coef[j] * (V[e] - V0[e]);
-        out[e] = t;
+        out[T ? (int64_t)k * rows + j : e] = t;
     }
 }
 
@@ -521,6 +537,10 @@ struct DsParams {
     int d;
     float c;
     int dq_add;
+    // G6 fused as a second trailing product (needs dQ fused): dKpart[tile][j][atom], j < d, = the
+    // tile's share of dS^T Q (unscaled, transposed so that a warp's stores are contiguous), and
+    // dS is not stored; or dKpart == NULL
+    float* dKpart;
 };
 
 // One CTA holds 256 atoms of its rows (M > 256: several CTAs along y, nothing to trade: the
@@ -538,12 +558,66 @@ struct DsEpi {
     static constexpr int E_BOXES = BN / 64, O_BOXES = BN / 64;  // dS staged over the attention rows
     static constexpr bool A_MN = false, B_MN = false;
     static constexpr int XPROD = 64;  // dQ = c dS K on the staged dS tile
+    static constexpr int XPROD2 = 1;  // dK partial = dS^T Q on the same staged tile
+    // its Q tile preloaded into 16 KB of its own (the BF16 form: two CTAs per SM still fit; the
+    // split form's 32 KB do not, and it waits for the dQ product's operand space)
+    static constexpr int X2PRE = SPLIT_ ? 0 : 1;
     using Params = DsParams;
     static __device__ bool x_active(const Params& p) { return p.dQ != nullptr; }
-    // dQ rows of this tile from TMEM columns 0 .. d - 1 (the padded columns hold zeros)
+    static __device__ bool x2_active(const Params& p) { return p.dKpart != nullptr; }
+    // this tile's dK partial: atoms n0 + 128 G + row from TMEM columns 64 + 64 G .. + d - 1, one
+    // 128-byte row of atoms per warp and column
+    static __device__ void run_k(const Params& p, const tc::EpiCtx& ec, int tile) {
+        float v[32];
+        for (int G = ec.g; G < BN / 128; G += EPI_WG) {
+            const int atom = ec.n0 + 128 * G + ec.row;
+            for (int c0 = 0; c0 < p.d; c0 += 32) {
+                tc::tmem_ld32(ec.taddr + 64u + 64u * (uint32_t)G + (uint32_t)c0, v);
+                if (atom >= p.M) continue;
+                float* dst = p.dKpart + ((int64_t)tile * p.d + c0) * p.M + atom;
+                const int nc = min(32, p.d - c0);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    if (c >= nc) break;
+                    dst[(int64_t)c * p.M] = v[c];
+                }
+            }
+        }
+    }
+    // dQ rows of this tile from TMEM columns 0 .. d - 1 (the padded columns hold zeros); with free
+    // shared memory, each warp's 32 rows x 32 columns go through it (4 KB, 16-byte chunks
+    // swizzled by row) so that every store covers four whole 128-byte rows
     static __device__ void run_x(const Params& p, const tc::EpiCtx& ec) {
         const int64_t pix = (int64_t)ec.m0 + ec.row;
         float v[32];
+        if (ec.xstage) {
+            const int lane = ec.row & 31, quarter = ec.row >> 5;
+            const int64_t pix0 = (int64_t)ec.m0 + 32 * quarter;  // the warp's first row
+            for (int c0 = 32 * ec.g; c0 < p.d; c0 += 32 * EPI_WG) {
+                tc::tmem_ld32(ec.taddr + c0, v);
+                uint8_t* stage = ec.xstage + (ec.g * 4 + quarter) * 4096;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    *reinterpret_cast<float4*>(stage + lane * 128 + ((q ^ (lane & 7)) << 4)) =
+                        make_float4(p.c * v[4 * q], p.c * v[4 * q + 1], p.c * v[4 * q + 2], p.c * v[4 * q + 3]);
+                __syncwarp();
+                const int nq = min(32, p.d - c0) / 4, cq = lane & 7;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = 4 * i + (lane >> 3);
+                    const float4 u = *reinterpret_cast<const float4*>(stage + r * 128 + ((cq ^ (r & 7)) << 4));
+                    if (pix0 + r < p.n && cq < nq) {
+                        float4* d4 = reinterpret_cast<float4*>(p.dQ + (pix0 + r) * p.d + c0) + cq;
+                        if (p.dq_add)
+                            atomicAdd(d4, u);  // two addends onto zero: the same sum in either order
+                        else
+                            *d4 = u;
+                    }
+                }
+                __syncwarp();  // (the next column block reuses the warp's staging rows)
+            }
+            return;
+        }
         for (int c0 = 32 * ec.g; c0 < p.d; c0 += 32 * EPI_WG) {
             tc::tmem_ld32(ec.taddr + c0, v);
             if (pix >= p.n) continue;
@@ -572,7 +646,7 @@ struct DsEpi {
             ec.row32(c0, a);
             tc::tmem_ld32(ec.taddr + c0, dA);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) dA[i] = a[i] * (dA[i] - rd);
+            for (int i = 0; i < 32; ++i) dA[i] = valid ? a[i] * (dA[i] - rd) : 0.f;  // (the dK product sums rows)
             ec.put32(c0, dA);
         }
         return cend > ec.col0 ? (cend - ec.col0 + 63) / 64 : 0;
@@ -594,7 +668,7 @@ struct DqEpi {
     static constexpr int BN = BN_, STAGES = 2, BOX_B = BN_, EPI_WG = 1, E_BOXES = 0, O_BOXES = 0, XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = false, B_MN = true;  // B = K padded (atoms x 64), queries contiguous
-    static constexpr int XPROD = 0, EPASS = 1;
+    static constexpr int XPROD = 0, XPROD2 = 0, X2PRE = 0, EPASS = 1;
     using Params = DqParams;
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
         const uint32_t taddr = ec.taddr;
@@ -640,7 +714,7 @@ struct PartEpi {
     static constexpr int XROUNDS = 0;
     static constexpr int MIN_SMEM = 0, MIN_BLOCKS = 1;
     static constexpr bool A_MN = true, B_MN = true;  // both pixel-major: K = pixels runs along rows
-    static constexpr int XPROD = 0, EPASS = 1;
+    static constexpr int XPROD = 0, XPROD2 = 0, X2PRE = 0, EPASS = 1;
     using Params = PartParams;
     static __device__ int run(const Params& p, const tc::EpiCtx& ec) {
 #pragma unroll
@@ -857,7 +931,8 @@ latentam_status u8_map(CUtensorMap* m, const void* base, int64_t inner, int64_t 
 template <class Epi>
 latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 grid, tc::GemmGrid g,
                             const typename Epi::Params& p, int* err, cudaStream_t st, const CUtensorMap* emap = nullptr,
-                            const CUtensorMap* omap = nullptr, int cluster_y = 1, const CUtensorMap* xmap = nullptr) {
+                            const CUtensorMap* omap = nullptr, int cluster_y = 1, const CUtensorMap* xmap = nullptr,
+                            const CUtensorMap* xmap2 = nullptr) {
     constexpr size_t smem = tc::gemm_smem_bytes<Epi>();
     static_assert(smem <= 227 * 1024, "tile does not fit in shared memory");
     if (cluster_y > tc::kMaxCluster || (int)grid.y % cluster_y != 0 || (cluster_y > 1 && Epi::XROUNDS == 0)) {
@@ -888,7 +963,8 @@ latentam_status launch_gemm(const CUtensorMap& a, const CUtensorMap& b, dim3 gri
         cfg.numAttrs = 1;
     }
     cudaError_t e =
-        cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, omap ? *omap : a, xmap ? *xmap : a, g, p, err);
+        cudaLaunchKernelEx(&cfg, kern, a, b, emap ? *emap : a, omap ? *omap : a, xmap ? *xmap : a, xmap2 ? *xmap2 : a, g,
+                           p, err);
     if (e != cudaSuccess) return cuda_error(e, "tc_gemm_kernel launch");
     LAT_CHECK_LAUNCH("tc_gemm_kernel");
     return LATENTAM_OK;
@@ -978,7 +1054,9 @@ latentam_status tc_buffers(latentam_ctx* ctx, int64_t n, int M, int D, bool trai
     off[7] = o, o += fp8 ? up(sizeof(float) * 2 * nn) : 0;    // stats
     off[8] = o, o += fp8 ? up(sizeof(float) * (size_t)D) : 0; // inv_t
     char* ops = static_cast<char*>(ws(ctx, WS_DEC_AUX3, o));
-    const size_t rows_bytes = up(e2 * nn * M) + (train ? up(e2 * nn * D) + up(e2 * nn * M) : 0);
+    // dS, or (dK fused into G3) the per-tile dK partials: 128-pixel tiles x M x (d <= 64) FP32
+    const size_t ds_bytes = std::max(up(e2 * nn * M), up(sizeof(float) * (size_t)((nn + 127) / 128) * M * kPad));
+    const size_t rows_bytes = up(e2 * nn * M) + (train ? up(e2 * nn * D) + ds_bytes : 0);
     char* rows = static_cast<char*>(ws(ctx, WS_DEC_A, rows_bytes));
     double* acc = static_cast<double*>(ws(ctx, WS_LOSS, 256));
     if (!ops || !rows || !acc) return LATENTAM_ERR_OUT_OF_MEMORY;
@@ -1196,6 +1274,7 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
     b.part = static_cast<float*>(ws(ctx, WS_DEC_PART, sizeof(float) * part_floats));
     if (!b.part) return LATENTAM_ERR_OUT_OF_MEMORY;
     const int which = SPLIT ? 16 : 0;  // autotuner key offset of the split form
+    bool dk_fused = false;
     if (n > 0) {
         // G1: S = Q K^T -> softmax
         LAT_TRY(tc_forward<SPLIT>(ctx, a.Q, n, d, a.K, a.V, M, D, a.c, b, b.stats, st));
@@ -1211,19 +1290,25 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
         // staged dS tile when a row's atoms span at most two CTAs, else as its own GEMM
         const int ty = cdiv(M, 256);
         const bool dq_fused = a.dQ != nullptr && ty <= 2;
+        // G6 (dK partials = dS^T Q per tile, Q read MN-major as the tile's 128 x 64 block) runs as
+        // its second trailing product when G4 is fused: dS then never leaves the chip
+        dk_fused = dq_fused && a.dK != nullptr;
         if (a.dQ) LAT_TRY(mn_map(SPLIT, &mK, b.Kb, kPad, M, kPad, 64, kPad / 64));
+        CUtensorMap mQt;
+        if (dk_fused) LAT_TRY(op_map(SPLIT, &mQt, b.Qb, kPad, n, kPad, kTileM));
         if (dq_fused && ty > 1) {
             e = cudaMemsetAsync(a.dQ, 0, sizeof(float) * (size_t)n * d, st);
             if (e != cudaSuccess) return cuda_error(e, "memset dQ");
         }
-        DsParams dp{n, M, b.A, b.row, b.dS, dq_fused ? a.dQ : nullptr, d, a.c, ty > 1 ? 1 : 0};
+        DsParams dp{n,   M, b.A, b.row, b.dS, dq_fused ? a.dQ : nullptr, d, a.c, ty > 1 ? 1 : 0,
+                    dk_fused ? reinterpret_cast<float*>(b.dS) : nullptr};
         const dim3 grow(cdiv(n, kTileM), 1, 1);
         const tc::GemmGrid g3{cdiv(D, BK3), cdiv(D, BK3)};
         CUtensorMap mAe, mdSo;  // attention rows for the epilogue, dS out through the TMA
         LAT_TRY(io_map(SPLIT, &mAe, b.A, M, n, M, kTileM));
         LAT_TRY(io_map(SPLIT, &mdSo, b.dS, M, n, M, kTileM));
         LAT_TRY((launch_gemm<DsEpi<SPLIT>>(mdF, mV, dim3(cdiv(n, kTileM), ty, 1), g3, dp, b.err, st, &mAe, &mdSo, 1,
-                                           dq_fused ? &mK : nullptr)));
+                                           dq_fused ? &mK : nullptr, dk_fused ? &mQt : nullptr)));
         if (a.dQ && !dq_fused) {
             LAT_TRY(op_map(SPLIT, &mdS, b.dS, M, n, M, kTileM));
             DqParams qp{n, d, a.c, a.dQ};
@@ -1239,13 +1324,14 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
     // G5: dV = A^T dFhat (+ trust region), both operands pixel-major (MN-major); each candidate
     // the tuner times includes the reduction of its partials (more splits, more partials to sum)
     auto reduce_dV = [&](int z) -> latentam_status {
-        tc_reduce_parts<<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, z, M, D, D, 1.0f, b.coef, a.V, a.V0, a.dV);
+        tc_reduce_parts<8><<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, z, M, D, D, 1.0f, b.coef, a.V, a.V0,
+                                                                     a.dV);
         LAT_CHECK_LAUNCH("tc_reduce_parts");
         return LATENTAM_OK;
     };
     auto reduce_dK = [&](int z) -> latentam_status {
-        tc_reduce_parts<<<cdiv((int64_t)M * d, 32), 256, 0, st>>>(b.part, z, M, BNq, d, a.c, nullptr, nullptr, nullptr,
-                                                                  a.dK);
+        tc_reduce_parts<8><<<cdiv((int64_t)M * d, 32), 256, 0, st>>>(b.part, z, M, BNq, d, a.c, nullptr, nullptr,
+                                                                     nullptr, a.dK);
         LAT_CHECK_LAUNCH("tc_reduce_parts");
         return LATENTAM_OK;
     };
@@ -1277,7 +1363,12 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
         }
     }
     // G6: dK = c dS^T Q
-    if (a.dK) {
+    if (a.dK && dk_fused) {
+        // the per-tile partials G3 left in the dS buffer, summed in tile order
+        tc_reduce_parts<32, true><<<cdiv((int64_t)M * d, 32), 1024, 0, st>>>(
+            reinterpret_cast<const float*>(b.dS), (int)cdiv(n, kTileM), d, M, M, a.c, nullptr, nullptr, nullptr, a.dK);
+        LAT_CHECK_LAUNCH("tc_reduce_parts");
+    } else if (a.dK) {
         if (n == 0) LAT_TRY(reduce_dK(0));  // zero
         if (n > 0) {
             CUtensorMap mdS, mQ;

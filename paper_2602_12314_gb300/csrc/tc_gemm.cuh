@@ -61,8 +61,20 @@ __host__ __device__ constexpr uint32_t tile_region_bytes() {
     return pipe > boxes ? pipe : boxes;
 }
 
+// A second trailing product whose B tile (128 pixels x 64, per plane) has a region of its own,
+// loaded when the CTA starts (Epi::X2PRE), instead of taking the first product's operand space
+// once that product has completed.
+template <class Epi>
+__host__ __device__ constexpr uint32_t x2_pre_bytes() {
+    return Epi::XPROD2 > 0 && Epi::X2PRE ? (uint32_t)planes<Epi>() * kTileM * 128 : 0u;
+}
+
+// Compact layout (with a preloaded second product): no row-reduction scratch, and the 256 bytes
+// of barriers in the alignment slack in front of the tile when it has room for them, else right
+// behind the regions; either way within the regions + 1024 bytes.
 template <class Epi>
 __host__ __device__ constexpr size_t gemm_smem_bytes() {
+    if (x2_pre_bytes<Epi>() > 0) return (size_t)tile_region_bytes<Epi>() + x2_pre_bytes<Epi>() + 1024;
     const size_t need = (size_t)tile_region_bytes<Epi>() + 1024 /* alignment */ + 256 /* barriers */ +
                         kScratchBytes;
     // MIN_SMEM caps the CTAs resident on one SM (so that their TMEM allocations never wait)
@@ -146,7 +158,17 @@ struct GemmGrid {
 // static constexpr int EPASS (1, or 2: the epilogue runs in two passes over the two column
 // halves of the tile, each with its half of the epilogue-operand boxes, of the staged output
 // and of the trailing product's K, in half the shared memory; run() then covers the columns
-// [EpiCtx::col0, col0 + BN / EPASS) and is called once per pass).
+// [EpiCtx::col0, col0 + BN / EPASS) and is called once per pass); static constexpr int XPROD2
+// (0, or 1 with XPROD: a second trailing product of the staged output, transposed: its 128-column
+// groups (MN-major, M = the output's columns) times tmX2's 128 x 64 tile at (0, m0) (MN-major,
+// K = the tile's rows), group G into TMEM columns 64 + 64 G once the first product of the pass has
+// freed the shared memory its operand is loaded into (or with X2PRE, below, at once); static
+// __device__ bool x2_active(const
+// Params&) says whether this launch takes it, and then the staged output is not stored; static
+// __device__ void run_k(const Params&, const EpiCtx&, int tile) reads it at the end; with
+// static constexpr int X2PRE = 1 that tile has 16 KB (per plane) of shared memory of its own, is
+// loaded when the CTA starts, and run_x finds the first product's 32 KB operand space free in
+// EpiCtx::xstage).
 struct EpiCtx {
     uint32_t taddr;        // TMEM address of this thread's row, column 0
     int row, m0, n0, z;    // tile row owned by this thread, tile origin, K split
@@ -168,6 +190,7 @@ struct EpiCtx {
     uint32_t oplane = 0;   // split form: bytes from the hi to the lo plane of the staged output
     uint64_t* ofree = nullptr;  // split persistent form: completes when the staging buffers are free
     uint32_t ofree_phase = 0;
+    uint8_t* xstage = nullptr;  // one-tile kernel, run_x: 32 KB of free shared memory, or null
 
     // In-place split form (Epi::INPLACE): the tile's FP32 epilogue operand sits in the box
     // buffers as 32-column chunks (128 rows x 128 B, 128-byte swizzle, chunk c at c x 16 KB), and
@@ -324,8 +347,8 @@ template <class Epi>
 __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmO,
-                   const __grid_constant__ CUtensorMap tmX, GemmGrid g, typename Epi::Params ep,
-                   int* __restrict__ err) {
+                   const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX2, GemmGrid g,
+                   typename Epi::Params ep, int* __restrict__ err) {
     constexpr int BN = Epi::BN;
     constexpr int STAGES = Epi::STAGES;
     constexpr int BOX_B = Epi::BOX_B;
@@ -370,10 +393,24 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                               X_OFF + xprod_bytes<Epi>() <= TILE_REGION),
                   "a trailing product multiplies the whole staged tile by a 64-column operand");
     constexpr uint32_t XDESC = idesc_bf16(kTileM, XN > 0 ? XN : 64, false, true);
+    // second trailing product: (staged output)^T x tmX2's tile, 128 output columns per group
+    constexpr int X2 = Epi::XPROD2;
+    constexpr int X2G = BN / EPASS / 128;                        // groups per pass
+    constexpr uint32_t X2_BYTES = (uint32_t)PL * kTileM * 128;  // 128 rows x 64 BF16 per plane
+    constexpr uint32_t X2DESC = idesc_bf16(kTileM, 64, true, true);
+    static_assert(X2 == 0 || (XN == 64 && BN % (128 * EPASS) == 0 && X2_BYTES <= xprod_bytes<Epi>() &&
+                              64 + 64 * EPASS * X2G <= (int)tmem_cols_for(MSUB * BN)),
+                  "the second trailing product reuses the first one's operand space and free TMEM columns");
+    constexpr bool X2PRE = x2_pre_bytes<Epi>() > 0;  // its B tile preloaded into a region of its own
+    constexpr uint32_t Q_OFF = X2PRE ? TILE_REGION : X_OFF;
+    static_assert(X2 == 0 || xprod_bytes<Epi>() >= 32768, "run_x's staging space is the first product's operand");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + TILE_REGION);
+    uint8_t* bar_base = smem + TILE_REGION;
+    if constexpr (X2PRE)  // compact layout (see gemm_smem_bytes)
+        bar_base = smem - smem_raw >= 256 ? smem - 256 : smem + TILE_REGION + x2_pre_bytes<Epi>();
+    uint64_t* full = reinterpret_cast<uint64_t*>(bar_base);
     uint64_t* empty = full + STAGES;
     uint64_t* accum = empty + STAGES;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
@@ -384,10 +421,13 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     uint64_t* x_staged = ebar + 9;  //   the staged output is complete
     uint64_t* x_done = ebar + 10;   //   its MMAs have completed
     uint64_t* p_free = ebar + 11;   // epilogue pass: its staged output has been read by its stores
-    float* scratch = reinterpret_cast<float*>(smem + TILE_REGION + 256);
-    static_assert(STAGES * 16 + 8 + 16 + 12 * 8 <= 256, "barriers fit their 256 bytes");
-    bool x_on = false;
+    uint64_t* q_loaded = ebar + 12;  // second trailing product: its B operand arrived
+    uint64_t* k_done = ebar + 13;    //   its MMAs have completed
+    float* scratch = X2PRE ? nullptr : reinterpret_cast<float*>(smem + TILE_REGION + 256);
+    static_assert(STAGES * 16 + 8 + 16 + 14 * 8 <= 256, "barriers fit their 256 bytes");
+    bool x_on = false, x2_on = false;
     if constexpr (XN > 0) x_on = Epi::x_active(ep);
+    if constexpr (X2 > 0) x2_on = x_on && Epi::x2_active(ep);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * MSUB * kTileM;
@@ -408,6 +448,10 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
             mbar_init(x_staged, 1);
             mbar_init(x_done, 1);
         }
+        if (X2 > 0) {
+            mbar_init(q_loaded, 1);
+            mbar_init(k_done, 1);
+        }
         if (EPASS > 1) mbar_init(p_free, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -423,6 +467,16 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     if (warp == 0) {
         if (lane == 0) {
             // ---- TMA producer ----
+            if (X2 > 0 && x2_on) {  // the second trailing product's tile: loaded now, or to L2 now
+                if (X2PRE) {
+                    mbar_expect_tx(q_loaded, X2_BYTES);
+                    tma_load(smem + Q_OFF, &tmX2, q_loaded, 0, m0, SPLIT ? 0 : -1);
+                } else if (SPLIT) {
+                    tma_prefetch_3d(&tmX2, 0, m0, 0);
+                } else {
+                    tma_prefetch_2d(&tmX2, 0, m0);
+                }
+            }
             int issued = 0;
             for (int i = 0; i < nk; ++i) {
                 const int s = i % STAGES;
@@ -481,9 +535,13 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 if (mbar_wait(accum, 0, abort_flag) && !*abort_flag) {
                     prefetch_tmap(&tmE);
                     for (int h = 0; h < EPASS; ++h) {
+                        // a second product whose tile shares the first one's operand space runs
+                        // first in the later passes, on the tile pass 0 left there
+                        const bool swap = X2 > 0 && !X2PRE && x2_on && h > 0;
                         // pass h reuses pass h - 1's buffers once its stores and products read them
                         if (h > 0 && (!mbar_wait(p_free, (uint32_t)(h - 1) & 1u, abort_flag) ||
-                                      (XN > 0 && x_on && !mbar_wait(x_done, (uint32_t)(h - 1) & 1u, abort_flag)))) {
+                                      (XN > 0 && x_on && !mbar_wait(x_done, (uint32_t)(h - 1) & 1u, abort_flag)) ||
+                                      (X2 > 0 && x2_on && !mbar_wait(k_done, (uint32_t)(h - 1) & 1u, abort_flag)))) {
                             *abort_flag = 1;
                             break;
                         }
@@ -493,7 +551,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                                 tma_load(smem + (z * EB + b) * (kTileM * 128), &tmE, &ebar[b], n0 + 64 * (h * EB + b),
                                          m0, SPLIT ? z : -1);
                         }
-                        if (XN > 0 && x_on) {
+                        auto load_x = [&]() {
                             // the trailing product's B rows of the pass (both planes per box when split)
                             mbar_expect_tx(x_loaded, xprod_bytes<Epi>());
                             for (int c = 0; c < XC; ++c) {
@@ -503,14 +561,33 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                                 else
                                     tma_load_2d(dst, &tmX, x_loaded, 0, n0 + 64 * (h * XC + c));
                             }
-                        }
+                        };
+                        if (XN > 0 && x_on && !swap) load_x();
                         for (int b = 0; b < EB; ++b) (void)mbar_wait(&ebar[b], (uint32_t)h & 1u, nullptr);
-                        if (XN > 0 && x_on) (void)mbar_wait(x_loaded, (uint32_t)h & 1u, nullptr);
+                        if (XN > 0 && x_on && !swap) (void)mbar_wait(x_loaded, (uint32_t)h & 1u, nullptr);
+                        if (X2 > 0 && !X2PRE && x2_on) {
+                            // pass 0: the first product has read its operand, the second's tile
+                            // takes its place (both planes in one box when split); later passes:
+                            // the second product has read the tile, the first one's operand returns
+                            if (!mbar_wait(swap ? k_done : x_done, (uint32_t)h & 1u, abort_flag)) {
+                                *abort_flag = 1;
+                                break;
+                            }
+                            if (swap) {
+                                load_x();
+                                (void)mbar_wait(x_loaded, (uint32_t)h & 1u, nullptr);
+                            } else {
+                                mbar_expect_tx(q_loaded, X2_BYTES);
+                                tma_load(smem + X_OFF, &tmX2, q_loaded, 0, m0, SPLIT ? 0 : -1);
+                                (void)mbar_wait(q_loaded, 0, nullptr);
+                            }
+                        }
                     }
                 } else {
                     *abort_flag = 1;
                 }
             }
+            if (X2 > 0 && X2PRE && x2_on) (void)mbar_wait(q_loaded, 0, nullptr);  // no copy left in flight
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -554,10 +631,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 // trailing product into columns 0 .. XN - 1, once the epilogue has read them
                 // (x_staged) and the pass's staged slice and B operand are in shared memory;
                 // each pass adds its K (atoms) slice into the same accumulator
-                for (int h = 0; h < EPASS; ++h) {
-                    const uint32_t ph = (uint32_t)h & 1u;
-                    const bool go = ok && mbar_wait(x_loaded, ph, abort_flag) && mbar_wait(x_staged, ph, abort_flag) &&
-                                    !*abort_flag;
+                auto first = [&](int h, bool go) {
                     if (go) {
                         tc_fence_after();
                         const uint32_t so = smem_u32(smem);         // staged output, hi plane (then lo)
@@ -575,6 +649,43 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                             }
                     }
                     mma_commit(x_done);  // at once when nothing was issued
+                };
+                // (staged output)^T x tile: group G of 128 output columns (two 64-column boxes,
+                // MN-major) over the tile's 128 rows into TMEM columns 64 + 64 G
+                auto second = [&](int h, bool go) {
+                    if (go) {
+                        tc_fence_after();
+                        const uint32_t so = smem_u32(smem);
+                        const uint32_t sq = smem_u32(smem + Q_OFF);
+                        constexpr uint32_t OPL = (uint32_t)OB * kTileABytes;
+#pragma unroll
+                        for (int gi = 0; gi < X2G; ++gi)
+#pragma unroll
+                            for (int kk = 0; kk < kTileM / 16; ++kk) {
+                                const uint32_t oa = so + (uint32_t)(2 * gi) * kTileABytes + kk * 16 * 128;
+                                const uint32_t qb = sq + kk * 16 * 128;
+                                mma_step<SPLIT>(tmem_base + 64u + 64u * (uint32_t)(h * X2G + gi),
+                                                mn128_desc(oa, kTileABytes), mn128_desc(oa + OPL, kTileABytes),
+                                                mn128_desc(qb), mn128_desc(qb + kTileM * 128), X2DESC,
+                                                kk > 0 ? 1u : 0u);
+                            }
+                    }
+                    mma_commit(k_done);  // at once when nothing was issued
+                };
+                for (int h = 0; h < EPASS; ++h) {
+                    const uint32_t ph = (uint32_t)h & 1u;
+                    if (X2 > 0 && !X2PRE && x2_on && h > 0) {
+                        // later passes: the second product first, on the tile pass 0 left in the
+                        // operand space, then the first one once its operand has replaced it
+                        const bool go2 = ok && mbar_wait(x_staged, ph, abort_flag) && !*abort_flag;
+                        second(h, go2);
+                        first(h, go2 && mbar_wait(x_loaded, ph, abort_flag) && !*abort_flag);
+                        continue;
+                    }
+                    const bool go = ok && mbar_wait(x_loaded, ph, abort_flag) && mbar_wait(x_staged, ph, abort_flag) &&
+                                    !*abort_flag;
+                    first(h, go);
+                    if (X2 > 0 && x2_on) second(h, go && mbar_wait(q_loaded, 0, abort_flag) && !*abort_flag);
                 }
             }
         }
@@ -612,7 +723,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 epi_sync(128 * Epi::EPI_WG);
                 if (threadIdx.x == 64) {
                     if (XN > 0 && x_on) mbar_arrive(x_staged);  // the slice is staged (or abandoned)
-                    if (out_boxes > 0 && !*abort_flag) {
+                    if (out_boxes > 0 && !*abort_flag && !x2_on) {  // (consumed on chip otherwise)
                         for (int b = 0; b < out_boxes && b < OB; ++b)
                             for (int z = 0; z < PL; ++z)
                                 tma_store(&tmO, smem + (z * OB + b) * kTileABytes, n0 + ec.col0 + 64 * b, m0,
@@ -632,7 +743,20 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
                 if (threadIdx.x == 64) *decision = (*decision && any_boxes > 0 && !*abort_flag) ? 1 : 0;
                 epi_sync(128 * Epi::EPI_WG);
                 tc_fence_after();
+                // the first product's operand space is free once its last pass completed (with a
+                // second product, that one completed before: preloaded, or run first in that pass)
+                if (X2 > 0 && x2_on && (X2PRE || EPASS > 1)) ec.xstage = smem + X_OFF;
                 if (*decision) Epi::run_x(ep, ec);
+                if constexpr (X2 > 0) {
+                    if (x2_on) {
+                        if (!mbar_wait(k_done, (uint32_t)(EPASS - 1) & 1u, abort_flag)) *abort_flag = 1;
+                        epi_sync(128 * Epi::EPI_WG);
+                        if (threadIdx.x == 64) *decision = (*decision && !*abort_flag) ? 1 : 0;
+                        epi_sync(128 * Epi::EPI_WG);
+                        tc_fence_after();
+                        if (*decision) Epi::run_k(ep, ec, (int)blockIdx.x);
+                    }
+                }
             }
         }
         tc_fence_before();
@@ -640,7 +764,14 @@ __global__ void __launch_bounds__(gemm_threads(Epi::EPI_WG), Epi::MIN_BLOCKS)
     __syncthreads();
     if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
     // an abandoned pipeline may still have MMAs in flight: let them finish before freeing TMEM
-    if (*abort_flag && warp == 1 && lane == 0) (void)mbar_wait(accum, 0, nullptr);
+    if (*abort_flag && warp == 1 && lane == 0) {
+        (void)mbar_wait(accum, 0, nullptr);
+        if (XN > 0 && x_on) {
+            // the trailing products' MMAs too: one more commit tracks everything this thread issued
+            mma_commit(accum);
+            (void)mbar_wait(accum, 1, nullptr);
+        }
+    }
     __syncwarp();
     if (warp == 1) {
         tc_fence_after();

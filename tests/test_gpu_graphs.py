@@ -100,8 +100,9 @@ def test_autotuned_splits_change_only_summation_order(api):
         res = [api.decode_loss_bwd(ctx, Q, K, V, V, F, mask, precision=api.BF16) for _ in range(2)]
         out.append([t.cpu().numpy() for t in res[-1]])
         choices = ctx.autotune_choices()
-        if tune:  # one choice per reduction over pixels: dV (tile shape and split) and dK (split)
-            assert sorted(c["reduction"] for c in choices) == [5, 6]
+        if tune:  # one choice per reduction over pixels: dV (tile shape and split); dK (M <= 512)
+            # comes from per-tile partials of the dA -> dS kernel, with no split to choose
+            assert sorted(c["reduction"] for c in choices) == [5]
             for c in choices:
                 assert (c["n"], c["M"], c["D"]) == (s.camera.n_pixels, s.M, s.D)
                 assert c["tile"] in ((0, 1) if c["reduction"] == 5 else (0,))
