@@ -212,8 +212,10 @@ LATENTAM_API latentam_status latentam_graphs_enable(latentam_ctx* ctx, int32_t e
 LATENTAM_API latentam_status latentam_test_wait_timeout(latentam_ctx* ctx, int32_t which);
 
 /* Autotuning of the tensor-core decode (on by default): the first time a context meets a shape
- * (pixel count, M, D) outside stream capture, the launch shape of each of the two reductions
- * over pixels (dV = A^T dFhat and dK = c dS^T Q) is chosen by timing its candidates with CUDA
+ * (pixel count, M, D) outside stream capture, the launch shape of each GEMM reduction over
+ * pixels (dV = A^T dFhat always; dK = c dS^T Q only where it is a GEMM of its own, M > 512 or
+ * no dQ requested: otherwise the dA -> dS kernel computes it per 128-pixel tile and a fixed
+ * reduction sums the tiles in order) is chosen by timing its candidates with CUDA
  * events on the caller's stream (this synchronises that stream once): for dV the CTA tile
  * (256 atoms x 256 features, the pixel block read once for both 128-atom halves, or 128 x 256
  * on twice the CTAs), for both the pixel split (the one-wave split of that tile, half and twice
