@@ -205,6 +205,54 @@ __global__ void __launch_bounds__(32 * W, W >= 32 ? 2 : 8)
     }
 }
 
+// The same sums (the same order per output) with each lane owning four consecutive outputs of
+// one row: 16-byte loads, for the wide dV partials (ncols and ld multiples of 4, part 16-byte
+// aligned).
+template <int W>
+__global__ void __launch_bounds__(32 * W, 8)
+    tc_reduce_parts4(const float* __restrict__ part, int splits, int rows, int ld, int ncols, float scale,
+                     const float* __restrict__ coef, const float* __restrict__ V, const float* __restrict__ V0,
+                     float* __restrict__ out) {
+    __shared__ float4 acc[W][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = 4 * ((int64_t)blockIdx.x * 32 + lane);  // first of the lane's four outputs
+    const bool live = e < (int64_t)rows * ncols;
+    const int j = live ? (int)(e / ncols) : 0, k = live ? (int)(e % ncols) : 0;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+        const int64_t step = (int64_t)W * rows * ld;  // W splits
+        const float* p = part + (int64_t)j * ld + k + (int64_t)w * rows * ld;
+#pragma unroll 4
+        for (int z = w; z < splits; z += W, p += step) {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+            s.x += u.x;
+            s.y += u.y;
+            s.z += u.z;
+            s.w += u.w;
+        }
+    }
+    acc[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && live) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const float4 u = acc[q][lane];
+            t.x += u.x;
+            t.y += u.y;
+            t.z += u.z;
+            t.w += u.w;
+        }
+        t = make_float4(t.x * scale, t.y * scale, t.z * scale, t.w * scale);
+        if (coef) {
+            const float c = coef[j];
+            const float4 v = *reinterpret_cast<const float4*>(V + e), v0 = *reinterpret_cast<const float4*>(V0 + e);
+            t = make_float4(t.x + c * (v.x - v0.x), t.y + c * (v.y - v0.y), t.z + c * (v.z - v0.z), t.w + c * (v.w - v0.w));
+        }
+        *reinterpret_cast<float4*>(out + e) = t;
+    }
+}
+
 __global__ void tc_finalize(const double* __restrict__ acc, const int* __restrict__ err, int D, latentam_loss_cfg cfg,
                             double* __restrict__ parts) {
     const double nv = acc[3];
@@ -1324,8 +1372,14 @@ latentam_status tc_loss_bwd(latentam_ctx* ctx, const DecodeArgs& a, cudaStream_t
     // G5: dV = A^T dFhat (+ trust region), both operands pixel-major (MN-major); each candidate
     // the tuner times includes the reduction of its partials (more splits, more partials to sum)
     auto reduce_dV = [&](int z) -> latentam_status {
-        tc_reduce_parts<8><<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, z, M, D, D, 1.0f, b.coef, a.V, a.V0,
-                                                                     a.dV);
+        const bool v4 = D % 4 == 0 && !(reinterpret_cast<uintptr_t>(a.dV) & 15u) &&
+                        !(reinterpret_cast<uintptr_t>(a.V) & 15u) && !(reinterpret_cast<uintptr_t>(a.V0) & 15u);
+        if (v4)
+            tc_reduce_parts4<8><<<cdiv((int64_t)M * D, 128), 256, 0, st>>>(b.part, z, M, D, D, 1.0f, b.coef, a.V,
+                                                                          a.V0, a.dV);
+        else
+            tc_reduce_parts<8><<<cdiv((int64_t)M * D, 32), 256, 0, st>>>(b.part, z, M, D, D, 1.0f, b.coef, a.V, a.V0,
+                                                                         a.dV);
         LAT_CHECK_LAUNCH("tc_reduce_parts");
         return LATENTAM_OK;
     };
