@@ -440,16 +440,17 @@ def _measure(args, world, rank, local, scene, prec, dist, views=None, masks=None
                                f"{sm_mhz:.0f} MHz (max SM clock)"}
     elif form == "fp32":
         peak = float(peaks["bf16_tflops_sustained"]) / 3.0
-        roof = {"bound": "tensor", "kernel": "decode stage: the six contractions on tcgen05 (four GEMM kernels; dQ "
-                                             "and dK as trailing products of the dA -> dS kernel), operands split "
+        roof = {"bound": "tensor", "kernel": "decode stage: the six contractions on tcgen05 (for M <= 512 four GEMM "
+                                             "kernels, dQ and dK as trailing products of the dA -> dS kernel; six "
+                                             "above), operands split "
                                              "into BF16 hi/lo planes, three MMAs per FP32 product",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"bf16 sustained ({peak_src}) / 3: each FP32 product is three BF16 MMAs",
                 "executed_bf16_tflops": 3.0 * flops / dec_avg_s / 1e12}
     else:
         peak = float(peaks["bf16_tflops_sustained"])
-        roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 GEMM kernels + their epilogues; dQ and dK as "
-                                             "trailing products of the dA -> dS kernel)",
+        roof = {"bound": "tensor", "kernel": "decode stage (tcgen05 GEMM kernels + their epilogues; for M <= 512 "
+                                             "dQ and dK as trailing products of the dA -> dS kernel)",
                 "achieved": flops / dec_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"bf16 sustained ({peak_src})" + (
                     "; the FP8 form is quoted against this BF16 peak: five of its six contractions are BF16 and no "
