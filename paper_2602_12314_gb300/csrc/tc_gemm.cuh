@@ -161,14 +161,14 @@ struct GemmGrid {
 // [EpiCtx::col0, col0 + BN / EPASS) and is called once per pass); static constexpr int XPROD2
 // (0, or 1 with XPROD: a second trailing product of the staged output, transposed: its 128-column
 // groups (MN-major, M = the output's columns) times tmX2's 128 x 64 tile at (0, m0) (MN-major,
-// K = the tile's rows), group G into TMEM columns 64 + 64 G once the first product of the pass has
-// freed the shared memory its operand is loaded into (or with X2PRE, below, at once); static
-// __device__ bool x2_active(const
-// Params&) says whether this launch takes it, and then the staged output is not stored; static
-// __device__ void run_k(const Params&, const EpiCtx&, int tile) reads it at the end; with
-// static constexpr int X2PRE = 1 that tile has 16 KB (per plane) of shared memory of its own, is
-// loaded when the CTA starts, and run_x finds the first product's 32 KB operand space free in
-// EpiCtx::xstage).
+// K = the tile's rows), group G into TMEM columns 64 + 64 G; static __device__ bool
+// x2_active(const Params&) says whether this launch takes it, and then the staged output is not
+// stored; static __device__ void run_k(const Params&, const EpiCtx&, int tile) reads it at the
+// end.  With static constexpr int X2PRE = 1 the tile has 16 KB (per plane) of shared memory of
+// its own and is loaded when the CTA starts; otherwise it takes the first product's operand
+// space once pass 0's first product has read it, and later passes run the second product first,
+// on that tile, before the first product's operand returns.  Either way run_x then finds the
+// first product's 32 KB operand space free in EpiCtx::xstage).
 struct EpiCtx {
     uint32_t taddr;        // TMEM address of this thread's row, column 0
     int row, m0, n0, z;    // tile row owned by this thread, tile origin, K split
